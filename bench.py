@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Throughput of the transient F-statistic map on GB300.
+
+Metric: F-map (t0, tau)-SFT terms per second: over all templates and all
+cells with >= 2 SFTs in their window, the number of SFTs inside the window
+(App. A, Eq. Nsums-exp for the exponential window), per second of device
+time.  One step = one fmap_compute_* call over the whole workload with the
+inputs resident in HBM (map and summaries written).  Default workload: the
+16-template exponential F-map (2000 merged SFTs of 2 detectors, 1000 x 1000
+(t0, tau) cells, 1 injected template); see synth.config_exp16.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--precision bf16x3|tf32|fp32|fp64] [--workload exp16|batch_rect]
+For N > 1 run under torch.distributed.run: every rank computes its own
+workload (different seeds; weak scaling), timing is max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    "exp16": "exp-window F-map, 16 templates, 2000 merged SFTs (2 detectors, 10% gaps each), "
+             "1000 x 1000 (t0, tau) cells at T_sft steps, tau in [T_sft, 1000 T_sft], cut at 3 tau",
+    "batch_rect": "rect-window F-map, 1024 templates x 5000 SFTs, 2000 x 2000 (t0, tau) cells",
+}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_workload(name, rank):
+    if name == "exp16":
+        return synth.config_exp16(seed=synth.BASE_SEED + 1 + 1000 * rank)
+    if name == "batch_rect":
+        return synth.config_batched(window=synth.RECT, seed=synth.BASE_SEED + 2 + 1000 * rank)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region (200 ms period)."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+        self.thread = None
+        self.error = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError as e:
+            self.error = str(e)
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if self.error:
+            return {"error": self.error}
+        rows = [r for r in self.rows if not self.uuid or self.uuid in r[0]] or self.rows
+        if not rows:
+            return {"error": "no nvidia-smi samples"}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v and
+                          "Not" not in v})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ cpu baseline --
+
+def cpu_baseline(inst, target_s=12.0):
+    """The CPU oracle (fast mode, FP64, OpenMP on all host cores) on a bounded
+    sample of the workload: every k-th t0 row, all tau, all templates."""
+    import oracle
+
+    oracle.build()
+    g = inst.grid
+
+    def sample_grid(rows):
+        stride = max(1, g.n_t0 // rows)
+        return synth.Grid(g.t0_min + stride // 2 * g.dt0, g.dt0 * stride,
+                          min(rows, g.n_t0), g.tau_min, g.dtau, g.n_tau, g.window, g.t_sft)
+
+    def run(rows):
+        sg = sample_grid(rows)
+        t0 = time.perf_counter()
+        oracle.fmap(inst.t, inst.antenna, inst.fafb, sg.as_tuple(), mode="fast")
+        return time.perf_counter() - t0, sg
+
+    import paper_1805_05652_gb300 as fm
+
+    rows = 2
+    dt, sg = run(rows)
+    while dt < 0.5 and rows < g.n_t0:
+        rows = min(g.n_t0, rows * 4)
+        dt, sg = run(rows)
+    per_row = dt / sg.n_t0
+    rows = int(min(g.n_t0, max(1, target_s / max(per_row, 1e-9))))
+    dt, sg = run(rows)
+    terms = fm.fmap_count_terms(sg, inst.t)[0] * inst.n_templates
+    return {"value": terms / dt, "unit": "terms/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{sg.n_t0} of {g.n_t0} t0 rows (every {g.n_t0 // max(1, sg.n_t0)}th), "
+                      f"all {g.n_tau} tau, all {inst.n_templates} templates; "
+                      f"{terms:.3e} terms in {dt:.2f} s"}, sg, terms
+
+
+# -------------------------------------------------------------------- main --
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--workload", default="exp16", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--also", default="fp32",
+                    help="comma list of extra precisions timed beside the headline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+
+    import paper_1805_05652_gb300 as fm
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl", device_id=dev)
+    fm.build()
+
+    inst = make_workload(args.workload, rank)
+    g = inst.grid
+    window = g.window
+    precision = args.precision
+    if precision is None:
+        precision = "fp64" if window == synth.RECT else "bf16x3"
+    try:
+        plan = fm.Plan(g, inst.n_sft, inst.n_templates, precision)
+    except fm.FmapError as e:
+        if e.status != fm.FMAP_ERR_UNSUPPORTED or args.precision is not None:
+            raise
+        precision = "fp32"
+        plan = fm.Plan(g, inst.n_sft, inst.n_templates, precision)
+
+    stream = torch.cuda.current_stream(dev)
+    t = torch.from_numpy(inst.t).to(dev)
+    ant = torch.from_numpy(inst.antenna).to(dev)
+    x = torch.from_numpy(inst.fafb).to(dev)
+    T = inst.n_templates
+    out_map = torch.empty((T, g.n_t0, g.n_tau), dtype=torch.float32, device=dev)
+    out_sum = torch.empty((T, 32), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    terms_per_tmpl, cells2 = fm.fmap_count_terms(g, inst.t)
+    terms = terms_per_tmpl * T
+
+    def step(p):
+        p.compute(t, ant, x, out_map=out_map, out_summary=out_sum, stream=stream)
+
+    def timed(p, steps, warmup):
+        for _ in range(warmup):
+            step(p)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        fm.fmap_plan_enable_timing(p.handle, True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))                     # untimed: evict the L2
+            evs[k][0].record(stream)
+            step(p)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        per = [a.elapsed_time(b) for a, b in evs]
+        ph, calls, launches = fm.fmap_plan_read_timing(p.handle)
+        fm.fmap_plan_enable_timing(p.handle, False)
+        return per, ph / max(calls, 1), launches
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    per, phase_ms, launches = timed(plan, args.steps, args.warmup)
+    clocks.stop()
+    torch.cuda.synchronize()
+    st = plan.status()
+    if st != fm.FMAP_OK:
+        raise SystemExit(f"device status {fm.status_string(st)}")
+
+    total_ms = sum(per)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = terms * world * args.steps / (total_ms / 1e3)
+
+    extra = {}
+    for alt in [a for a in args.also.split(",") if a and a != precision]:
+        try:
+            p2 = fm.Plan(g, inst.n_sft, inst.n_templates, alt)
+        except fm.FmapError:
+            continue
+        per2, ph2, _ = timed(p2, max(3, args.steps // 3), 3)
+        extra[alt] = {"value": terms * world / (statistics.mean(per2) / 1e3),
+                      "ms_per_step": statistics.mean(per2),
+                      "contraction_ms": float(ph2[2])}
+        p2.close()
+
+    result = None
+    if rank == 0:
+        peaks, peak_src = load_peaks()
+        dom_ms = float(phase_ms[2])
+        flops = 2.0 * terms * 4            # multiply + add per (cell, SFT, data column) x 4 columns
+        if window == synth.EXP and precision in ("bf16x3", "tf32"):
+            if precision == "bf16x3":
+                peak, unit_peak = peaks["bf16_tflops"], "TFLOP/s (bf16, %s)" % peak_src
+            else:
+                peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+                unit_peak = "TFLOP/s (tf32 = bf16 x 1.1/2.25 nominal, %s)" % peak_src
+            ach = flops / (dom_ms / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "kernel": "exp contraction (phase 2)",
+                    "peak_source": unit_peak}
+        elif window == synth.EXP:
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            ach = flops / (dom_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "kernel": "exp contraction (phase 2)",
+                    "peak_source": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock"}
+        else:
+            byts = T * g.n_t0 * g.n_tau * 4.0
+            ach = byts / (dom_ms / 1e3) / 1e9
+            peak = peaks["hbm_gbs"]
+            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "kernel": "rect cells (phase 2)",
+                    "peak_source": peak_src}
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu, _, _ = cpu_baseline(inst)
+        e2e = None
+        if not args.no_e2e:
+            e2e = end_to_end(fm, inst, precision, terms, args)
+        srt = sorted(per)
+        result = {
+            "metric": "F-map (t0,tau)-SFT terms/s",
+            "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16x3": "bf16x3"}[precision],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                       "precision": precision, "templates": T, "n_sft": inst.n_sft,
+                       "n_t0": g.n_t0, "n_tau": g.n_tau, "terms_per_step": terms,
+                       "cells_with_2plus_sft": cells2,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world} (templates sharded by rank)"},
+            "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1,
+                                                                  int(math.ceil(0.99 * len(srt))) - 1)],
+                           "max": srt[-1]},
+            "phases_ms": {"index": float(phase_ms[0]), "antenna": float(phase_ms[1]),
+                          "contraction": float(phase_ms[2]), "reduce": float(phase_ms[3])},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "also": extra,
+        }
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if result is not None:
+        print(json.dumps(result), flush=True)
+
+
+def end_to_end(fm, inst, precision, terms, args):
+    """Same metric through fmap_compute_host: pinned host atoms in, map and
+    summaries out, copies inside the timed region (host wall clock)."""
+    import torch
+
+    g = inst.grid
+    T = inst.n_templates
+    plan = fm.Plan(g, inst.n_sft, T, precision)
+    h_t = torch.from_numpy(inst.t).pin_memory()
+    h_a = torch.from_numpy(inst.antenna).pin_memory()
+    h_x = torch.from_numpy(inst.fafb).pin_memory()
+    h_m = torch.empty((T, g.n_t0, g.n_tau), dtype=torch.float32).pin_memory()
+    h_s = torch.empty((T, 32), dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.current_stream()
+    atoms = fm.make_atoms(inst.n_sft, T, True, h_t, h_a, h_x)
+    for _ in range(3):
+        fm.fmap_compute_host(plan.handle, atoms, h_m, h_s, stream)
+    n = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        fm.fmap_compute_host(plan.handle, atoms, h_m, h_s, stream)
+    dt = (time.perf_counter() - t0) / n
+    plan.close()
+    h2d = h_t.numel() * 8 + h_a.numel() * 4 + h_x.numel() * 4
+    d2h = h_m.numel() * 4 + h_s.numel()
+    return {"value": terms / dt, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
+            "api": "fmap_compute_host (pinned host buffers)"}
+
+
+def reference_arm(args, rank, world):
+    """The CPU oracle as the reference implementation, on the host cores."""
+    if rank != 0:
+        return
+    inst = make_workload(args.workload, 0)
+    info, sg, terms = cpu_baseline(inst, target_s=min(4.0, 150.0 / (args.steps + args.warmup)))
+    import oracle
+
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.fmap(inst.t, inst.antenna, inst.fafb, sg.as_tuple(), mode="fast")
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    mean = statistics.mean(times)
+    value = terms / mean
+    info["value"] = value
+    res = {"impl": "reference", "metric": "F-map (t0,tau)-SFT terms/s", "value": value,
+           "unit": "terms/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                      "sample": info["sample"]},
+           "cpu_baseline": info,
+           "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * fmap -- transient F-statistic maps on one GB300 (sm_103a).
+ *
+ * C ABI of libfmap.so.  The operation (Keitel & Ashton, arXiv:1805.05652):
+ * from per-SFT atoms {a^2, b^2, ab, Fa, Fb} (Sec. 2 after Eq. F_xMx; Sec. 3
+ * sends them to the GPU as a 7 x N_SFT real matrix) compute, for every cell
+ * (t0_m, tau_n) of a uniform grid (Eq. Fmn), the windowed sums
+ *   A = sum w^2 a^2, B = sum w^2 b^2, C = sum w^2 ab, Fa = sum w Fa_a,
+ *   Fb = sum w Fb_a
+ * with the rectangular window of Eq. (winrect) or the exponential window of
+ * Eq. (winexp) (cut after 3 tau), the determinant D = A B - C^2 and
+ * 2F from Eq. (F_FaFb); fused with the per-template reductions max 2F,
+ * argmax (m, n) and the log Bayes factor marginalised over (t0, tau)
+ * (Sec. 2 Eq. F_OSG; App. A).
+ *
+ * Conventions shared by every entry point:
+ *   - Times are integer seconds (int64).  An SFT that starts at t is inside the
+ *     window of (t0, tau) when t0 <= t and t + T_sft <= t0 + L, L = tau (rect)
+ *     or 3 tau (exp).  Windows past the end of the data are truncated
+ *     (App. A, non-embedded convention).
+ *   - A cell with fewer than 2 SFTs in its window (Sec. 4.1) or with D <= 0
+ *     is invalid: its 2F is 0 and it is left out of max, argmax and logB.
+ *   - logB = ln((1/N_valid) sum_valid e^{2F/2}) + log_prior_const.
+ *   - argmax ties go to the lowest m * n_tau + n.
+ *   - Device buffers are caller-owned plain device pointers; the plan owns
+ *     its workspace.  Compute calls are asynchronous on the given stream and
+ *     never throw; errors are status codes.  Data errors found on the device
+ *     (non-increasing timestamps, a time span >= 2^31 s) are latched in the
+ *     plan and returned by fmap_plan_status().
+ *   - A plan serialises its own calls: do not use one plan from two host
+ *     threads at once, nor on two streams whose work overlaps.
+ */
+#ifndef FMAP_H
+#define FMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st* fmap_stream;
+
+typedef enum {
+  FMAP_OK = 0,
+  FMAP_PENDING = 1,          /* fmap_poll: not finished yet */
+  FMAP_ERR_ARG = -1,         /* invalid argument (sizes, grid, null pointer) */
+  FMAP_ERR_NOMEM = -2,       /* device or host allocation failed / over budget */
+  FMAP_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  FMAP_ERR_TIMEOUT = -4,     /* a bounded wait gave up */
+  FMAP_ERR_BUSY = -5,        /* server full / ticket unknown */
+  FMAP_ERR_DATA = -6,        /* timestamps not strictly increasing or span >= 2^31 s */
+  FMAP_ERR_UNSUPPORTED = -7  /* valid request this build cannot serve */
+} fmap_status;
+
+typedef enum { FMAP_RECT = 0, FMAP_EXP = 1 } fmap_window;
+
+/*
+ * Arithmetic of the windowed sums (the determinant, the 2F coefficients and
+ * the log-Bayes reduction are FP64 in every mode):
+ *   FMAP_FP64   rect: FP64 prefix sums, differences in compensated FP32;
+ *               exp:  FP64 contraction on the CUDA cores.
+ *   FMAP_FP32   rect: one thread per t0 row with FP32 running sums (the
+ *               paper's rectangular kernel, Sec. 3);
+ *               exp:  FP32 contraction on the CUDA cores (the plain path).
+ *   FMAP_TF32   exp only: tensor-core contraction (tcgen05, kind::tf32) with
+ *               both operands split hi + lo, three products, FP32 accumulate.
+ *   FMAP_BF16X3 exp only: tensor-core contraction (tcgen05, kind::f16, bf16)
+ *               with hi*hi + hi*lo + lo*hi, FP32 accumulate.
+ */
+typedef enum { FMAP_FP64 = 0, FMAP_FP32 = 1, FMAP_TF32 = 2, FMAP_BF16X3 = 3 } fmap_precision;
+
+/* Grid of Eq. (Fmn): t0_m = t0_min + m dt0 (m < n_t0), tau_n = tau_min + n dtau
+ * (n < n_tau).  Needs n_t0, n_tau >= 0, tau_min > 0, t_sft > 0, dtau > 0 when
+ * n_tau > 1, dt0 > 0 when n_t0 > 1, 3 tau_max < 2^31. */
+typedef struct {
+  int64_t t0_min;
+  int64_t dt0;
+  int32_t n_t0;
+  int64_t tau_min;
+  int64_t dtau;
+  int32_t n_tau;
+  int64_t t_sft;
+  int32_t window; /* fmap_window */
+} fmap_grid;
+
+/* Atoms (Sec. 3: 3 real rows a^2, b^2, ab and 2 complex rows Fa, Fb).
+ * t        [n_sft] int64, strictly increasing SFT start times;
+ * antenna  [3][n_sft] float (a^2, b^2, ab) if shared_antenna, else [T][3][n_sft];
+ * fafb     [T][4][n_sft] float (Re Fa, Im Fa, Re Fb, Im Fb).
+ * Device pointers for fmap_compute_*, host pointers for fmap_compute_host and
+ * fmap_submit.  Rows need no alignment beyond 4 bytes. */
+typedef struct {
+  int32_t n_sft;
+  int32_t n_templates;
+  int32_t shared_antenna;
+  const int64_t* t;
+  const float* antenna;
+  const float* fafb;
+} fmap_atoms;
+
+/* Per-template result (32 bytes).  n_valid = 0 gives max2F = 0, m = n = -1,
+ * logB = NaN. */
+typedef struct {
+  float max2F;
+  int32_t m;
+  int32_t n;
+  int32_t reserved;
+  double logB;
+  int64_t n_valid;
+} fmap_summary;
+
+/* fmap_plan flags */
+enum {
+  /* atoms carry antenna rows per template ([T][3][n_sft]); workspace for the
+   * per-template 2F coefficients grows by a factor T */
+  FMAP_PLAN_PER_TEMPLATE_ANTENNA = 1u
+};
+
+typedef struct fmap_plan_s fmap_plan_t;
+typedef struct fmap_server_s fmap_server_t;
+
+/*
+ * fmap_plan: create a plan for one grid, SFT count and template count
+ * (the F-map problem statement of Sec. 3: atoms + window + grid).  The plan
+ * allocates its workspace (fmap_workspace_bytes) on the current device.
+ * flags: 0 or FMAP_PLAN_PER_TEMPLATE_ANTENNA.  Returns FMAP_ERR_ARG on an invalid grid or size,
+ * FMAP_ERR_UNSUPPORTED for a precision the window does not offer,
+ * FMAP_ERR_NOMEM when the workspace cannot be allocated.
+ */
+fmap_status fmap_plan(fmap_plan_t** plan, const fmap_grid* grid, int32_t n_sft,
+                      int32_t n_templates, fmap_precision precision, uint32_t flags);
+void fmap_plan_destroy(fmap_plan_t* plan);
+
+/* Workspace a plan of these sizes allocates (bytes). */
+size_t fmap_workspace_bytes(const fmap_grid* grid, int32_t n_sft, int32_t n_templates,
+                            fmap_precision precision);
+
+/* Additive constant of logB (prior normalisation; default 0). */
+fmap_status fmap_plan_set_log_prior(fmap_plan_t* plan, double log_prior_const);
+
+/*
+ * fmap_compute_rect / fmap_compute_exp: the F-map of Eq. (Fmn) for every
+ * template with the rectangular (Eq. winrect) or exponential (Eq. winexp)
+ * window; the grid's window field must match.  Sec. 3 (the two kernels, D
+ * and F inside the GPU), Eq. (F_FaFb).
+ *   atoms      device atoms, n_sft / n_templates equal to the plan's;
+ *   d_2F       nullable device [T][n_t0][n_tau] float, 2F per cell (n fastest);
+ *   d_summary  nullable device [T] fmap_summary.
+ * Asynchronous on stream.  FMAP_ERR_ARG on mismatched sizes or window.
+ */
+fmap_status fmap_compute_rect(fmap_plan_t* plan, const fmap_atoms* atoms, float* d_2F,
+                              fmap_summary* d_summary, fmap_stream stream);
+fmap_status fmap_compute_exp(fmap_plan_t* plan, const fmap_atoms* atoms, float* d_2F,
+                             fmap_summary* d_summary, fmap_stream stream);
+
+/*
+ * fmap_marginalise: the reductions alone (max 2F, argmax, marginalised logB;
+ * Sec. 2 Eq. F_OSG, App. A) over a given map.
+ *   d_2F      device [T][n_t0][n_tau] float (T = the plan's template count);
+ *   d_valid   nullable device [T][n_t0][n_tau] uint8 (nonzero = valid); NULL
+ *             treats every cell as valid;
+ *   d_summary device [T].
+ */
+fmap_status fmap_marginalise(fmap_plan_t* plan, const float* d_2F, const uint8_t* d_valid,
+                             fmap_summary* d_summary, fmap_stream stream);
+
+/*
+ * fmap_compute_host: one synchronous end-to-end call with HOST buffers:
+ * copies the atoms to plan-owned device staging (pinned host memory makes
+ * the copies asynchronous), runs the window's compute, copies the map
+ * (nullable h_2F) and the summaries (nullable h_summary) back, and waits.
+ */
+fmap_status fmap_compute_host(fmap_plan_t* plan, const fmap_atoms* host_atoms, float* h_2F,
+                              fmap_summary* h_summary, fmap_stream stream);
+
+/* Per-phase device timing of a plan's compute calls, taken with CUDA events
+ * recorded on each call's stream.  Phases (FMAP_N_PHASES):
+ *   0 input checks and window index tables,
+ *   1 antenna sums / prefix sums (rect: FP64 scans; exp: FP64 suffix sums and
+ *     the per-cell 2F coefficients),
+ *   2 the windowed contraction with the fused 2F epilogue (the dominant
+ *     kernel),
+ *   3 the final per-template reduction.
+ * fmap_plan_enable_timing(plan, 1) starts recording (and clears the totals);
+ * fmap_plan_read_timing waits for the recorded calls and returns the summed
+ * milliseconds per phase, the number of timed calls and the number of
+ * kernels the plan launched since timing was enabled. */
+#define FMAP_N_PHASES 4
+fmap_status fmap_plan_enable_timing(fmap_plan_t* plan, int32_t enable);
+fmap_status fmap_plan_read_timing(fmap_plan_t* plan, double* ms, int64_t* calls,
+                                  int64_t* launches);
+
+/* Waits for the plan's last stream and returns (then clears) a latched data
+ * or CUDA error, else FMAP_OK. */
+fmap_status fmap_plan_status(fmap_plan_t* plan);
+
+/* Host-side window bookkeeping for throughput accounting: over all cells,
+ * the total number of (cell, SFT) terms (sum of atoms per window, App. A
+ * Eq. Nsums-exp for exp windows) and the number of cells with >= 2 atoms.
+ * t is a HOST pointer. */
+fmap_status fmap_count_terms(const fmap_grid* grid, const int64_t* t, int32_t n_sft,
+                             int64_t* n_terms, int64_t* n_cells_2plus);
+
+const char* fmap_status_string(fmap_status status);
+/* Message of the last error on this host thread ("" if none). */
+const char* fmap_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMAP_H */

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libfmap (the C ABI in include/fmap.h).
+
+Argument marshalling only: every step of the F-map runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors passed by ``data_ptr()``;
+streams are torch streams passed by their ``cuda_stream`` handle.  There is no
+CPU fallback: if ``_lib/libfmap.so`` is missing, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import lib_path
+
+c_i32, c_i64, c_u32, c_f32, c_f64 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                     ctypes.c_float, ctypes.c_double)
+c_vp, c_size = ctypes.c_void_p, ctypes.c_size_t
+
+# fmap_status
+FMAP_OK, FMAP_PENDING = 0, 1
+FMAP_ERR_ARG, FMAP_ERR_NOMEM, FMAP_ERR_CUDA, FMAP_ERR_TIMEOUT = -1, -2, -3, -4
+FMAP_ERR_BUSY, FMAP_ERR_DATA, FMAP_ERR_UNSUPPORTED = -5, -6, -7
+# fmap_window / fmap_precision / plan flags
+FMAP_RECT, FMAP_EXP = 0, 1
+FMAP_FP64, FMAP_FP32, FMAP_TF32, FMAP_BF16X3 = 0, 1, 2, 3
+FMAP_PLAN_PER_TEMPLATE_ANTENNA = 1
+
+PRECISIONS = {"fp64": FMAP_FP64, "fp32": FMAP_FP32, "tf32": FMAP_TF32, "bf16x3": FMAP_BF16X3}
+
+
+class fmap_grid(ctypes.Structure):
+    _fields_ = [("t0_min", c_i64), ("dt0", c_i64), ("n_t0", c_i32), ("tau_min", c_i64),
+                ("dtau", c_i64), ("n_tau", c_i32), ("t_sft", c_i64), ("window", c_i32)]
+
+
+class fmap_atoms(ctypes.Structure):
+    _fields_ = [("n_sft", c_i32), ("n_templates", c_i32), ("shared_antenna", c_i32),
+                ("t", c_vp), ("antenna", c_vp), ("fafb", c_vp)]
+
+
+class fmap_summary(ctypes.Structure):
+    _fields_ = [("max2F", c_f32), ("m", c_i32), ("n", c_i32), ("reserved", c_i32),
+                ("logB", c_f64), ("n_valid", c_i64)]
+
+
+SUMMARY_DTYPE = np.dtype([("max2F", "<f4"), ("m", "<i4"), ("n", "<i4"), ("reserved", "<i4"),
+                          ("logB", "<f8"), ("n_valid", "<i8")])
+assert SUMMARY_DTYPE.itemsize == ctypes.sizeof(fmap_summary) == 32
+
+EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_set_log_prior",
+           "fmap_compute_rect", "fmap_compute_exp", "fmap_marginalise", "fmap_compute_host",
+           "fmap_plan_status", "fmap_count_terms", "fmap_status_string", "fmap_last_error",
+           "fmap_plan_enable_timing", "fmap_plan_read_timing")
+FMAP_N_PHASES = 4
+
+
+class FmapError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} {message}".strip())
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libfmap; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfmap.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    L.fmap_plan.argtypes = [P(c_vp), P(fmap_grid), c_i32, c_i32, ctypes.c_int, c_u32]
+    L.fmap_plan_destroy.argtypes = [c_vp]
+    L.fmap_plan_destroy.restype = None
+    L.fmap_workspace_bytes.argtypes = [P(fmap_grid), c_i32, c_i32, ctypes.c_int]
+    L.fmap_workspace_bytes.restype = c_size
+    L.fmap_plan_set_log_prior.argtypes = [c_vp, c_f64]
+    for f in ("fmap_compute_rect", "fmap_compute_exp", "fmap_compute_host"):
+        getattr(L, f).argtypes = [c_vp, P(fmap_atoms), c_vp, c_vp, c_vp]
+    L.fmap_marginalise.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp]
+    L.fmap_plan_status.argtypes = [c_vp]
+    L.fmap_count_terms.argtypes = [P(fmap_grid), c_vp, c_i32, P(c_i64), P(c_i64)]
+    L.fmap_plan_enable_timing.argtypes = [c_vp, c_i32]
+    L.fmap_plan_read_timing.argtypes = [c_vp, c_vp, P(c_i64), P(c_i64)]
+    L.fmap_status_string.argtypes = [ctypes.c_int]
+    L.fmap_status_string.restype = ctypes.c_char_p
+    L.fmap_last_error.argtypes = []
+    L.fmap_last_error.restype = ctypes.c_char_p
+    for f in ("fmap_plan", "fmap_plan_set_log_prior", "fmap_compute_rect", "fmap_compute_exp",
+              "fmap_compute_host", "fmap_marginalise", "fmap_plan_status", "fmap_count_terms",
+              "fmap_plan_enable_timing", "fmap_plan_read_timing"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def status_string(status: int) -> str:
+    return lib().fmap_status_string(int(status)).decode()
+
+
+def last_error() -> str:
+    return lib().fmap_last_error().decode()
+
+
+def _check(status: int, where: str):
+    if status != FMAP_OK:
+        raise FmapError(status, where, last_error())
+
+
+def make_grid(grid) -> fmap_grid:
+    """``grid``: an object with t0_min, dt0, n_t0, tau_min, dtau, n_tau, window,
+    t_sft attributes, or the tuple (t0_min, dt0, n_t0, tau_min, dtau, n_tau,
+    t_sft, window)."""
+    if isinstance(grid, fmap_grid):
+        return grid
+    if isinstance(grid, (tuple, list)):
+        t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft, window = grid
+    else:
+        t0_min, dt0, n_t0 = grid.t0_min, grid.dt0, grid.n_t0
+        tau_min, dtau, n_tau = grid.tau_min, grid.dtau, grid.n_tau
+        t_sft, window = grid.t_sft, grid.window
+    return fmap_grid(int(t0_min), int(dt0), int(n_t0), int(tau_min), int(dtau), int(n_tau),
+                     int(t_sft), int(window))
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def make_atoms(n_sft, n_templates, shared_antenna, t, antenna, fafb) -> fmap_atoms:
+    return fmap_atoms(int(n_sft), int(n_templates), int(bool(shared_antenna)), _ptr(t),
+                      _ptr(antenna), _ptr(fafb))
+
+
+# ---- the C ABI under its own names ----------------------------------------
+
+def fmap_plan(grid, n_sft: int, n_templates: int, precision=FMAP_FP64, flags: int = 0) -> int:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    h = c_vp()
+    g = make_grid(grid)
+    _check(lib().fmap_plan(ctypes.byref(h), ctypes.byref(g), int(n_sft), int(n_templates),
+                           int(precision), int(flags)), "fmap_plan")
+    return h.value
+
+
+def fmap_plan_destroy(plan: int):
+    if plan:
+        lib().fmap_plan_destroy(c_vp(plan))
+
+
+def fmap_workspace_bytes(grid, n_sft, n_templates, precision=FMAP_FP64) -> int:
+    g = make_grid(grid)
+    return int(lib().fmap_workspace_bytes(ctypes.byref(g), int(n_sft), int(n_templates),
+                                          int(precision)))
+
+
+def fmap_plan_set_log_prior(plan: int, c: float):
+    _check(lib().fmap_plan_set_log_prior(c_vp(plan), float(c)), "fmap_plan_set_log_prior")
+
+
+def fmap_compute_rect(plan: int, atoms: fmap_atoms, d_2F, d_summary, stream=None):
+    _check(lib().fmap_compute_rect(c_vp(plan), ctypes.byref(atoms), _ptr(d_2F), _ptr(d_summary),
+                                   _stream(stream)), "fmap_compute_rect")
+
+
+def fmap_compute_exp(plan: int, atoms: fmap_atoms, d_2F, d_summary, stream=None):
+    _check(lib().fmap_compute_exp(c_vp(plan), ctypes.byref(atoms), _ptr(d_2F), _ptr(d_summary),
+                                  _stream(stream)), "fmap_compute_exp")
+
+
+def fmap_compute_host(plan: int, atoms: fmap_atoms, h_2F, h_summary, stream=None):
+    _check(lib().fmap_compute_host(c_vp(plan), ctypes.byref(atoms), _ptr(h_2F), _ptr(h_summary),
+                                   _stream(stream)), "fmap_compute_host")
+
+
+def fmap_marginalise(plan: int, d_2F, d_valid, d_summary, stream=None):
+    _check(lib().fmap_marginalise(c_vp(plan), _ptr(d_2F), _ptr(d_valid), _ptr(d_summary),
+                                  _stream(stream)), "fmap_marginalise")
+
+
+def fmap_plan_status(plan: int) -> int:
+    return int(lib().fmap_plan_status(c_vp(plan)))
+
+
+def fmap_plan_enable_timing(plan: int, enable: bool = True):
+    _check(lib().fmap_plan_enable_timing(c_vp(plan), int(bool(enable))), "fmap_plan_enable_timing")
+
+
+def fmap_plan_read_timing(plan: int):
+    """(ms per phase [4], timed calls, kernels launched)."""
+    ms = np.zeros(FMAP_N_PHASES, dtype=np.float64)
+    calls, launches = c_i64(), c_i64()
+    _check(lib().fmap_plan_read_timing(c_vp(plan), _ptr(ms), ctypes.byref(calls),
+                                       ctypes.byref(launches)), "fmap_plan_read_timing")
+    return ms, int(calls.value), int(launches.value)
+
+
+def fmap_count_terms(grid, t_host: np.ndarray):
+    g = make_grid(grid)
+    t = np.ascontiguousarray(t_host, dtype=np.int64)
+    a, b = c_i64(), c_i64()
+    _check(lib().fmap_count_terms(ctypes.byref(g), _ptr(t), int(t.shape[0]), ctypes.byref(a),
+                                  ctypes.byref(b)), "fmap_count_terms")
+    return int(a.value), int(b.value)
+
+
+# ---- convenience wrapper on torch tensors ---------------------------------
+
+def summary_to_numpy(buf) -> np.ndarray:
+    """Device or host summary buffer (uint8 [T, 32] tensor or ndarray) -> records."""
+    if hasattr(buf, "cpu"):
+        buf = buf.cpu().numpy()
+    return np.frombuffer(np.ascontiguousarray(buf).tobytes(), dtype=SUMMARY_DTYPE)
+
+
+@dataclass
+class Plan:
+    """Owns one fmap plan; ``compute`` takes torch CUDA tensors."""
+
+    grid: object
+    n_sft: int
+    n_templates: int
+    precision: int = FMAP_FP64
+    flags: int = 0
+
+    def __post_init__(self):
+        if isinstance(self.precision, str):
+            self.precision = PRECISIONS[self.precision]
+        self.g = make_grid(self.grid)
+        self.handle = fmap_plan(self.g, self.n_sft, self.n_templates, self.precision, self.flags)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fmap_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def atoms(self, t, antenna, fafb) -> fmap_atoms:
+        shared = antenna.dim() == 2
+        return make_atoms(self.n_sft, self.n_templates, shared, t, antenna, fafb)
+
+    def compute(self, t, antenna, fafb, want_map=True, want_summary=True, out_map=None,
+                out_summary=None, stream=None):
+        """Run the plan's window; returns (map [T, n_t0, n_tau] or None,
+        summary uint8 [T, 32] or None) as device tensors."""
+        import torch
+
+        dev = t.device
+        T = self.n_templates
+        m = out_map
+        if m is None and want_map:
+            m = torch.empty((T, self.g.n_t0, self.g.n_tau), dtype=torch.float32, device=dev)
+        s = out_summary
+        if s is None and want_summary:
+            s = torch.empty((T, 32), dtype=torch.uint8, device=dev)
+        a = self.atoms(t, antenna, fafb)
+        if self.g.window == FMAP_RECT:
+            fmap_compute_rect(self.handle, a, m, s, stream)
+        else:
+            fmap_compute_exp(self.handle, a, m, s, stream)
+        return m, s
+
+    def compute_host(self, t, antenna, fafb, h_map=None, h_summary=None, stream=None):
+        """End-to-end call with host (numpy or pinned torch) buffers."""
+        shared = antenna.ndim == 2 if hasattr(antenna, "ndim") else antenna.dim() == 2
+        a = make_atoms(self.n_sft, self.n_templates, shared, t, antenna, fafb)
+        fmap_compute_host(self.handle, a, h_map, h_summary, stream)
+        return h_map, h_summary
+
+    def marginalise(self, d_map, d_valid=None, out_summary=None, stream=None):
+        import torch
+
+        s = out_summary
+        if s is None:
+            s = torch.empty((self.n_templates, 32), dtype=torch.uint8, device=d_map.device)
+        fmap_marginalise(self.handle, d_map, d_valid, s, stream)
+        return s
+
+    def status(self) -> int:
+        return fmap_plan_status(self.handle)
+
+    def set_log_prior(self, c: float):
+        fmap_plan_set_log_prior(self.handle, c)

@@ -1,0 +1,456 @@
+// Host side of libfmap: plans, validation, workspace layout, dispatch of the
+// compute paths and the C ABI of include/fmap.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fmap_internal.h"
+
+namespace fmap {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+fmap_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return FMAP_ERR_CUDA;
+}
+
+static fmap_status arg_fail(const std::string& msg) {
+  set_error(msg);
+  return FMAP_ERR_ARG;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Grid checks (Eq. Fmn with integer seconds).
+static bool grid_valid(const fmap_grid* g, std::string* why) {
+  if (!g) return *why = "grid is NULL", false;
+  if (g->n_t0 < 0 || g->n_tau < 0) return *why = "n_t0 and n_tau must be >= 0", false;
+  if (g->window != FMAP_RECT && g->window != FMAP_EXP) return *why = "unknown window", false;
+  if (g->t_sft <= 0) return *why = "t_sft must be > 0", false;
+  if (g->tau_min <= 0) return *why = "tau_min must be > 0", false;
+  if (g->n_tau > 1 && g->dtau <= 0) return *why = "dtau must be > 0 when n_tau > 1", false;
+  if (g->n_t0 > 1 && g->dt0 <= 0) return *why = "dt0 must be > 0 when n_t0 > 1", false;
+  const int64_t cells = (int64_t)g->n_t0 * g->n_tau;
+  if (cells >= (int64_t)0x7fffffff) return *why = "n_t0 * n_tau must be < 2^31", false;
+  const double tau_max = (double)g->tau_min + (double)std::max(0, g->n_tau - 1) * (double)g->dtau;
+  if (3.0 * tau_max >= 2147483647.0) return *why = "3 tau_max must be < 2^31 s", false;
+  const double t0_ext = std::fabs((double)g->t0_min) +
+                        (double)std::max(0, g->n_t0 - 1) * std::fabs((double)g->dt0);
+  if (t0_ext > 4.0e18) return *why = "t0 grid out of int64 range", false;
+  return true;
+}
+
+static bool precision_supported(int window, fmap_precision prec) {
+  if (window == FMAP_RECT) return prec == FMAP_FP64 || prec == FMAP_FP32;
+  if (prec == FMAP_TF32 || prec == FMAP_BF16X3) return exp_tc_available(prec);
+  return prec == FMAP_FP64 || prec == FMAP_FP32;
+}
+
+struct Layout {
+  size_t rel_t, t_base, dev_err, i0, jend, coef, parts, pa, px, esuf, xop, total;
+  int64_t n_tiles;
+  int32_t tau_chunk;
+};
+
+static constexpr size_t kEsufBudget = size_t(1) << 30;
+
+static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_precision prec,
+                        uint32_t flags) {
+  Layout L{};
+  const size_t A = 256;
+  const int64_t cells = (int64_t)g->n_t0 * g->n_tau;
+  const int64_t t_ant = (flags & FMAP_PLAN_PER_TEMPLATE_ANTENNA) ? T : 1;
+  int64_t tiles = std::max<int64_t>(marg_tiles(*g), 1);
+  if (g->window == FMAP_RECT) {
+    tiles = std::max<int64_t>(tiles, rect_tiles(*g));
+    tiles = std::max<int64_t>(tiles, (g->n_t0 + 127) / 128);
+  } else {
+    tiles = std::max<int64_t>(tiles, exp_tiles(*g));
+  }
+  L.n_tiles = tiles;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), A);
+    return at;
+  };
+  L.rel_t = take(sizeof(int32_t) * std::max<int32_t>(n_sft, 1));
+  L.t_base = take(sizeof(int64_t));
+  L.dev_err = take(sizeof(uint32_t));
+  L.i0 = take(sizeof(int32_t) * std::max<int32_t>(g->n_t0, 1));
+  L.jend = take(sizeof(int32_t) * std::max<int64_t>(cells, 1));
+  L.parts = take(sizeof(Partial) * (size_t)std::max<int32_t>(T, 1) * (size_t)tiles);
+  L.pa = L.px = L.esuf = L.coef = L.xop = 0;
+  const size_t np1 = (size_t)n_sft + 1;
+  if (g->window == FMAP_RECT) {
+    L.pa = take(sizeof(double) * 4 * np1 * (size_t)t_ant);
+    L.px = take(2 * sizeof(float4) * np1 * (size_t)std::max<int32_t>(T, 1));
+  } else {
+    L.coef = take(sizeof(Coef) * (size_t)std::max<int64_t>(cells, 1) * (size_t)t_ant);
+    const size_t per_tau = 3 * sizeof(double) * np1;
+    int64_t chunk = (int64_t)std::max<size_t>(1, kEsufBudget / per_tau);
+    chunk = std::min<int64_t>(chunk, std::max<int32_t>(g->n_tau, 1));
+    L.tau_chunk = (int32_t)chunk;
+    L.esuf = take(per_tau * (size_t)chunk);
+    if (prec == FMAP_TF32 || prec == FMAP_BF16X3)
+      L.xop = take(exp_tc_operand_bytes(*g, n_sft, T, prec));
+  }
+  L.total = off;
+  return L;
+}
+
+}  // namespace fmap
+
+using namespace fmap;
+
+static_assert(sizeof(fmap_summary) == 32, "fmap_summary layout");
+static_assert(sizeof(fmap_grid) == 64, "fmap_grid layout");
+static_assert(sizeof(fmap_atoms) == 40, "fmap_atoms layout");
+
+extern "C" {
+
+const char* fmap_status_string(fmap_status s) {
+  switch (s) {
+    case FMAP_OK: return "FMAP_OK";
+    case FMAP_PENDING: return "FMAP_PENDING";
+    case FMAP_ERR_ARG: return "FMAP_ERR_ARG";
+    case FMAP_ERR_NOMEM: return "FMAP_ERR_NOMEM";
+    case FMAP_ERR_CUDA: return "FMAP_ERR_CUDA";
+    case FMAP_ERR_TIMEOUT: return "FMAP_ERR_TIMEOUT";
+    case FMAP_ERR_BUSY: return "FMAP_ERR_BUSY";
+    case FMAP_ERR_DATA: return "FMAP_ERR_DATA";
+    case FMAP_ERR_UNSUPPORTED: return "FMAP_ERR_UNSUPPORTED";
+  }
+  return "FMAP_UNKNOWN";
+}
+
+const char* fmap_last_error(void) { return g_last_error.c_str(); }
+
+size_t fmap_workspace_bytes(const fmap_grid* grid, int32_t n_sft, int32_t n_templates,
+                            fmap_precision precision) {
+  std::string why;
+  if (!grid_valid(grid, &why) || n_sft < 0 || n_templates < 0) return 0;
+  return layout_of(grid, n_sft, n_templates, precision, 0).total;
+}
+
+fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
+                      int32_t n_templates, fmap_precision precision, uint32_t flags) {
+  set_error("");
+  if (!out) return arg_fail("plan output pointer is NULL");
+  *out = nullptr;
+  std::string why;
+  if (!grid_valid(grid, &why)) return arg_fail(why);
+  if (n_sft < 0) return arg_fail("n_sft must be >= 0");
+  if (n_templates < 0 || n_templates > 65535) return arg_fail("n_templates must be in [0, 65535]");
+  if (precision < FMAP_FP64 || precision > FMAP_BF16X3) return arg_fail("unknown precision");
+  if (flags & ~(uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA) return arg_fail("unknown plan flags");
+  if (!precision_supported(grid->window, precision)) {
+    set_error("precision not offered for this window (tensor-core forms are exp-only)");
+    return FMAP_ERR_UNSUPPORTED;
+  }
+  fmap_plan_s* p = new (std::nothrow) fmap_plan_s();
+  if (!p) return FMAP_ERR_NOMEM;
+  p->grid = *grid;
+  p->n_sft = n_sft;
+  p->n_templates = n_templates;
+  p->precision = precision;
+  p->flags = flags;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  const Layout L = layout_of(grid, n_sft, n_templates, precision, flags);
+  p->n_tiles = L.n_tiles;
+  p->tau_chunk = L.tau_chunk;
+  void* base = nullptr;
+  e = cudaMalloc(&base, L.total);
+  if (e != cudaSuccess) {
+    delete p;
+    cudaGetLastError();
+    set_error("workspace allocation of " + std::to_string(L.total) + " bytes failed");
+    return FMAP_ERR_NOMEM;
+  }
+  char* b = (char*)base;
+  Workspace& w = p->ws;
+  w.base = base;
+  w.bytes = L.total;
+  w.rel_t = (int32_t*)(b + L.rel_t);
+  w.t_base = (int64_t*)(b + L.t_base);
+  w.dev_err = (uint32_t*)(b + L.dev_err);
+  w.i0 = (int32_t*)(b + L.i0);
+  w.jend = (int32_t*)(b + L.jend);
+  w.partials = (Partial*)(b + L.parts);
+  if (grid->window == FMAP_RECT) {
+    w.pa = (double*)(b + L.pa);
+    w.px = (float4*)(b + L.px);
+  } else {
+    w.coef = (Coef*)(b + L.coef);
+    w.esuf = (double*)(b + L.esuf);
+    if (L.xop) w.xop = (void*)(b + L.xop);
+  }
+  e = cudaMemset(w.dev_err, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    delete p;
+    return cuda_fail(e, "cudaMemset");
+  }
+  *out = p;
+  return FMAP_OK;
+}
+
+static void drop_events(fmap_plan_s* p) {
+  for (auto e : p->events) cudaEventDestroy(e);
+  p->events.clear();
+}
+
+static void free_staging(fmap_plan_s* p) {
+  Workspace& w = p->ws;
+  cudaFree(w.st_t);
+  cudaFree(w.st_ant);
+  cudaFree(w.st_x);
+  cudaFree(w.st_map);
+  cudaFree(w.st_sum);
+  w.st_t = nullptr;
+  w.st_ant = w.st_x = w.st_map = nullptr;
+  w.st_sum = nullptr;
+}
+
+void fmap_plan_destroy(fmap_plan_t* p) {
+  if (!p) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device) cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  drop_events(p);
+  free_staging(p);
+  cudaFree(p->ws.base);
+  if (cur != p->device) cudaSetDevice(cur);
+  delete p;
+}
+
+fmap_status fmap_plan_set_log_prior(fmap_plan_t* p, double c) {
+  if (!p) return arg_fail("plan is NULL");
+  if (!std::isfinite(c)) return arg_fail("log prior constant must be finite");
+  p->log_prior = c;
+  return FMAP_OK;
+}
+
+static fmap_status check_atoms(const fmap_plan_s* p, const fmap_atoms* a) {
+  if (!a) return arg_fail("atoms is NULL");
+  if (a->n_sft != p->n_sft) return arg_fail("atoms.n_sft differs from the plan");
+  if (a->n_templates != p->n_templates) return arg_fail("atoms.n_templates differs from the plan");
+  if (!a->shared_antenna && !(p->flags & FMAP_PLAN_PER_TEMPLATE_ANTENNA))
+    return arg_fail("per-template antenna rows need a plan made with FMAP_PLAN_PER_TEMPLATE_ANTENNA");
+  if (p->n_sft > 0 && (!a->t || !a->antenna || (p->n_templates > 0 && !a->fafb)))
+    return arg_fail("atom pointers must be non-NULL when n_sft > 0");
+  return FMAP_OK;
+}
+
+static fmap_status check_device(const fmap_plan_s* p) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != p->device) return arg_fail("current device differs from the plan's device");
+  return FMAP_OK;
+}
+
+static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
+                           fmap_summary* d_summary, cudaStream_t s, int window) {
+  set_error("");
+  if (!p) return arg_fail("plan is NULL");
+  if (p->grid.window != window)
+    return arg_fail("the plan's grid window does not match this compute call");
+  fmap_status st = check_atoms(p, a);
+  if (st != FMAP_OK) return st;
+  st = check_device(p);
+  if (st != FMAP_OK) return st;
+  p->last_stream = s;
+  if (!d_2F && !d_summary) return FMAP_OK;
+  cudaEvent_t ev[FMAP_N_PHASES + 1] = {};
+  if (p->timing) {
+    for (auto& e : ev) FMAP_CUDA(cudaEventCreate(&e));
+    for (auto e : ev) p->events.push_back(e);
+    FMAP_CUDA(cudaEventRecord(ev[0], s));
+  }
+  FMAP_CUDA(launch_prep(p, a->t, s));
+  FMAP_CUDA(launch_index(p, a->t, s));
+  if (ev[1]) FMAP_CUDA(cudaEventRecord(ev[1], s));
+  int64_t tiles = 0;
+  if (window == FMAP_RECT) {
+    FMAP_CUDA(launch_rect(p, a, d_2F, s, &tiles, ev[2]));
+    if (ev[2] && p->precision == FMAP_FP32) FMAP_CUDA(cudaEventRecord(ev[2], s));
+  } else {
+    FMAP_CUDA(launch_exp_coef(p, a, s));
+    if (ev[2]) FMAP_CUDA(cudaEventRecord(ev[2], s));
+    if (p->precision == FMAP_TF32 || p->precision == FMAP_BF16X3) {
+      FMAP_CUDA(launch_exp_tc(p, a, d_2F, s, &tiles));
+    } else {
+      FMAP_CUDA(launch_exp_plain(p, a, d_2F, s, &tiles));
+    }
+  }
+  if (ev[3]) FMAP_CUDA(cudaEventRecord(ev[3], s));
+  FMAP_CUDA(launch_final_reduce(p, tiles, d_summary, s));
+  if (ev[4]) FMAP_CUDA(cudaEventRecord(ev[4], s));
+  return FMAP_OK;
+}
+
+fmap_status fmap_compute_rect(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
+                              fmap_summary* d_summary, fmap_stream stream) {
+  return compute(p, a, d_2F, d_summary, (cudaStream_t)stream, FMAP_RECT);
+}
+
+fmap_status fmap_compute_exp(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
+                             fmap_summary* d_summary, fmap_stream stream) {
+  return compute(p, a, d_2F, d_summary, (cudaStream_t)stream, FMAP_EXP);
+}
+
+fmap_status fmap_marginalise(fmap_plan_t* p, const float* d_2F, const uint8_t* d_valid,
+                             fmap_summary* d_summary, fmap_stream stream) {
+  set_error("");
+  if (!p) return arg_fail("plan is NULL");
+  const int64_t cells = (int64_t)p->grid.n_t0 * p->grid.n_tau;
+  if (!d_summary) return arg_fail("summary output is NULL");
+  if (cells > 0 && p->n_templates > 0 && !d_2F) return arg_fail("map is NULL");
+  fmap_status st = check_device(p);
+  if (st != FMAP_OK) return st;
+  p->last_stream = (cudaStream_t)stream;
+  FMAP_CUDA(launch_marginalise(p, d_2F, d_valid, d_summary, (cudaStream_t)stream));
+  return FMAP_OK;
+}
+
+fmap_status fmap_plan_enable_timing(fmap_plan_t* p, int32_t enable) {
+  if (!p) return arg_fail("plan is NULL");
+  drop_events(p);
+  p->timing = enable != 0;
+  p->launches = 0;
+  return FMAP_OK;
+}
+
+fmap_status fmap_plan_read_timing(fmap_plan_t* p, double* ms, int64_t* calls, int64_t* launches) {
+  if (!p) return arg_fail("plan is NULL");
+  const size_t per = FMAP_N_PHASES + 1;
+  double acc[FMAP_N_PHASES] = {0, 0, 0, 0};
+  const size_t n_calls = p->events.size() / per;
+  for (size_t c = 0; c < n_calls; ++c) {
+    cudaEvent_t* e = &p->events[c * per];
+    FMAP_CUDA(cudaEventSynchronize(e[per - 1]));
+    for (int k = 0; k < FMAP_N_PHASES; ++k) {
+      float t = 0.f;
+      FMAP_CUDA(cudaEventElapsedTime(&t, e[k], e[k + 1]));
+      acc[k] += t;
+    }
+  }
+  if (ms)
+    for (int k = 0; k < FMAP_N_PHASES; ++k) ms[k] = acc[k];
+  if (calls) *calls = (int64_t)n_calls;
+  if (launches) *launches = p->launches;
+  return FMAP_OK;
+}
+
+fmap_status fmap_plan_status(fmap_plan_t* p) {
+  if (!p) return arg_fail("plan is NULL");
+  FMAP_CUDA(cudaStreamSynchronize(p->last_stream));
+  uint32_t bits = 0;
+  FMAP_CUDA(cudaMemcpy(&bits, p->ws.dev_err, sizeof(bits), cudaMemcpyDeviceToHost));
+  if (bits) {
+    FMAP_CUDA(cudaMemset(p->ws.dev_err, 0, sizeof(uint32_t)));
+    std::string m;
+    if (bits & DEV_ERR_ORDER) m += "timestamps are not strictly increasing; ";
+    if (bits & DEV_ERR_SPAN) m += "timestamp span is >= 2^31 s; ";
+    set_error(m);
+    return FMAP_ERR_DATA;
+  }
+  return FMAP_OK;
+}
+
+fmap_status fmap_compute_host(fmap_plan_t* p, const fmap_atoms* h, float* h_2F,
+                              fmap_summary* h_summary, fmap_stream stream) {
+  set_error("");
+  if (!p) return arg_fail("plan is NULL");
+  fmap_status st = check_atoms(p, h);
+  if (st != FMAP_OK) return st;
+  st = check_device(p);
+  if (st != FMAP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = p->ws;
+  const size_t n = (size_t)p->n_sft, T = (size_t)p->n_templates;
+  const size_t n_ant = h->shared_antenna ? 1 : T;
+  const size_t cells = (size_t)p->grid.n_t0 * (size_t)p->grid.n_tau;
+  if (!w.st_t) {
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&w.st_t, sizeof(int64_t) * std::max<size_t>(n, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&w.st_ant, sizeof(float) * 3 * std::max<size_t>(n, 1) *
+                                                        (p->flags & FMAP_PLAN_PER_TEMPLATE_ANTENNA ? std::max<size_t>(T, 1) : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&w.st_x, sizeof(float) * 4 * std::max<size_t>(n * T, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&w.st_map, sizeof(float) * std::max<size_t>(cells * T, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&w.st_sum, sizeof(fmap_summary) * std::max<size_t>(T, 1));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_staging(p);
+      set_error("staging allocation failed");
+      return FMAP_ERR_NOMEM;
+    }
+  }
+  if (n > 0) {
+    FMAP_CUDA(cudaMemcpyAsync(w.st_t, h->t, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+    FMAP_CUDA(cudaMemcpyAsync(w.st_ant, h->antenna, sizeof(float) * 3 * n * n_ant,
+                              cudaMemcpyHostToDevice, s));
+    if (T > 0)
+      FMAP_CUDA(cudaMemcpyAsync(w.st_x, h->fafb, sizeof(float) * 4 * n * T,
+                                cudaMemcpyHostToDevice, s));
+  }
+  fmap_atoms d = *h;
+  d.t = w.st_t;
+  d.antenna = w.st_ant;
+  d.fafb = w.st_x;
+  st = compute(p, &d, h_2F ? w.st_map : nullptr, h_summary ? w.st_sum : nullptr, s,
+               p->grid.window);
+  if (st != FMAP_OK) return st;
+  if (h_2F && cells * T > 0)
+    FMAP_CUDA(cudaMemcpyAsync(h_2F, w.st_map, sizeof(float) * cells * T, cudaMemcpyDeviceToHost, s));
+  if (h_summary && T > 0)
+    FMAP_CUDA(cudaMemcpyAsync(h_summary, w.st_sum, sizeof(fmap_summary) * T,
+                              cudaMemcpyDeviceToHost, s));
+  FMAP_CUDA(cudaStreamSynchronize(s));
+  return FMAP_OK;
+}
+
+fmap_status fmap_count_terms(const fmap_grid* g, const int64_t* t, int32_t n_sft, int64_t* n_terms,
+                             int64_t* n_cells_2plus) {
+  set_error("");
+  std::string why;
+  if (!grid_valid(g, &why)) return arg_fail(why);
+  if (n_sft < 0 || (n_sft > 0 && !t)) return arg_fail("bad timestamps");
+  if (!n_terms || !n_cells_2plus) return arg_fail("outputs are NULL");
+  const int64_t lmul = g->window == FMAP_RECT ? 1 : 3;
+  int64_t terms = 0, cells2 = 0;
+  for (int32_t m = 0; m < g->n_t0; ++m) {
+    const int64_t t0 = g->t0_min + (int64_t)m * g->dt0;
+    const int64_t i0 = std::lower_bound(t, t + n_sft, t0) - t;
+    int64_t j = i0;
+    for (int32_t nn = 0; nn < g->n_tau; ++nn) {
+      const int64_t lim = t0 + lmul * (g->tau_min + (int64_t)nn * g->dtau) - g->t_sft;
+      while (j < n_sft && t[j] <= lim) ++j;
+      const int64_t c = j - i0;
+      if (c >= 2) {
+        terms += c;
+        ++cells2;
+      }
+    }
+  }
+  *n_terms = terms;
+  *n_cells_2plus = cells2;
+  return FMAP_OK;
+}
+
+}  // extern "C"

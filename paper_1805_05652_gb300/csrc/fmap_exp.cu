@@ -1,0 +1,292 @@
+// Exponential-window F-map (Eq. winexp, cut after 3 tau).
+//
+// Antenna part (shared by every template of a sky position): A, B, C with the
+// squared weight w^2 = e^{-2(t - t0)/tau}, in FP64, from a decayed suffix
+// sum per tau:
+//     E[i] = x_i + e^{-2(t_{i+1} - t_i)/tau} E[i+1],   E[N] = 0,
+//     A(t0, tau) = e^{-2(t_{i0} - t0)/tau} (E[i0] - e^{-2(t_j - t_{i0})/tau} E[j])
+// for the window's atoms [i0, j).  The recurrence is contractive, so the
+// subtraction loses at most a factor 1/(1 - e^{-6}) of relative accuracy.
+// Then D = AB - C^2 in FP64 and the per-cell 2F coefficients.
+//
+// Data part: Fa, Fb = sum_a w(t_a) X[a, col] over the window, a contraction
+// of the weight matrix W[(t0, tau), a] with the 4T data columns.  Here the
+// plain CUDA-core form (the paper's brute-force exp kernel, Sec. 3, restated
+// with shared-memory staging and one thread per cell): FP32 or FP64
+// accumulation.  The tensor-core form lives in fmap_exp_tc.cu.
+#include <math.h>
+
+#include <type_traits>
+
+#include "fmap_device.cuh"
+
+namespace fmap {
+
+constexpr int kSufThreads = 256;
+
+// Decayed suffix sums of the three antenna rows for one tau (block) of a
+// tau chunk; parallel backward scan of the affine maps E -> x + rho E.
+__global__ void __launch_bounds__(kSufThreads)
+k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restrict__ ant,
+             fmap_grid g, int32_t n_lo, double* __restrict__ esuf) {
+  __shared__ double sR[kSufThreads / 32];
+  __shared__ double sS[3][kSufThreads / 32];
+  const int ni = blockIdx.x;
+  const double tau = (double)(g.tau_min + (int64_t)(n_lo + ni) * g.dtau);
+  const double inv_s = 2.0 / tau;
+  double* E = esuf + (int64_t)ni * 3 * ((int64_t)n + 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = (n + kSufThreads - 1) / kSufThreads;
+  const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
+  auto rho_at = [&](int i) -> double {
+    return (i + 1 < n) ? exp(-(double)(rel_t[i + 1] - rel_t[i]) * inv_s) : 0.0;
+  };
+  // phase 1: compose this thread's chunk: E[s0] = S + R E[e0]
+  double R = 1.0, S0 = 0.0, S1 = 0.0, S2 = 0.0;
+  for (int i = e0 - 1; i >= s0; --i) {
+    const double r = rho_at(i);
+    S0 = (double)ant[i] + r * S0;
+    S1 = (double)ant[n + i] + r * S1;
+    S2 = (double)ant[2 * (int64_t)n + i] + r * S2;
+    R *= r;
+  }
+  // phase 2: inclusive suffix composition within the warp (self o later)
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double Ro = __shfl_down_sync(0xffffffffu, R, d);
+    const double So0 = __shfl_down_sync(0xffffffffu, S0, d);
+    const double So1 = __shfl_down_sync(0xffffffffu, S1, d);
+    const double So2 = __shfl_down_sync(0xffffffffu, S2, d);
+    if (lane + d < 32) {
+      S0 += R * So0;
+      S1 += R * So1;
+      S2 += R * So2;
+      R *= Ro;
+    }
+  }
+  // exclusive within the warp: composition of lanes lane+1 .. 31
+  double hR = __shfl_down_sync(0xffffffffu, R, 1);
+  double hS0 = __shfl_down_sync(0xffffffffu, S0, 1);
+  double hS1 = __shfl_down_sync(0xffffffffu, S1, 1);
+  double hS2 = __shfl_down_sync(0xffffffffu, S2, 1);
+  if (lane == 31) {
+    hR = 1.0;
+    hS0 = hS1 = hS2 = 0.0;
+  }
+  if (lane == 0) {
+    sR[warp] = R;
+    sS[0][warp] = S0;
+    sS[1][warp] = S1;
+    sS[2][warp] = S2;
+  }
+  __syncthreads();
+  // composition of the later warps, applied to E[N] = 0: only its S matters
+  double lR = 1.0, lS0 = 0.0, lS1 = 0.0, lS2 = 0.0;
+  for (int v = kSufThreads / 32 - 1; v > warp; --v) {
+    lS0 = sS[0][v] + sR[v] * lS0;
+    lS1 = sS[1][v] + sR[v] * lS1;
+    lS2 = sS[2][v] + sR[v] * lS2;
+    lR *= sR[v];
+  }
+  (void)lR;
+  double e_0 = hS0 + hR * lS0, e_1 = hS1 + hR * lS1, e_2 = hS2 + hR * lS2;
+  // phase 3: recompute the chunk from its carry E[e0] and store
+  const int64_t np1 = (int64_t)n + 1;
+  for (int i = e0 - 1; i >= s0; --i) {
+    const double r = rho_at(i);
+    e_0 = (double)ant[i] + r * e_0;
+    e_1 = (double)ant[n + i] + r * e_1;
+    e_2 = (double)ant[2 * (int64_t)n + i] + r * e_2;
+    E[i] = e_0;
+    E[np1 + i] = e_1;
+    E[2 * np1 + i] = e_2;
+  }
+  if (tid == 0) {
+    E[n] = 0.0;
+    E[np1 + n] = 0.0;
+    E[2 * np1 + n] = 0.0;
+  }
+}
+
+// Per-cell coefficients of the cells of one tau chunk.
+__global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base,
+                           int32_t n, fmap_grid g, int32_t n_lo, int32_t n_chunk,
+                           const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+                           const double* __restrict__ esuf, Coef* __restrict__ coef) {
+  const int64_t total = (int64_t)g.n_t0 * n_chunk;
+  const int64_t np1 = (int64_t)n + 1;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = c / n_chunk;
+    const int32_t nl = (int32_t)(c - m * n_chunk);
+    const int64_t nn = n_lo + nl;
+    const int64_t cell = m * g.n_tau + nn;
+    const int32_t i0 = i0tab[m];
+    const int32_t j = jend[cell];
+    const int32_t count = j - i0;
+    double A = 0.0, B = 0.0, C = 0.0;
+    if (count > 0) {
+      const double tau = (double)(g.tau_min + nn * g.dtau);
+      const double inv_s = 2.0 / tau;
+      const int64_t t0rel = g.t0_min + m * g.dt0 - *t_base;
+      const double pre = exp(-(double)((int64_t)rel_t[i0] - t0rel) * inv_s);
+      const double tail = (j < n) ? exp(-(double)(rel_t[j] - rel_t[i0]) * inv_s) : 0.0;
+      const double* E = esuf + (int64_t)nl * 3 * np1;
+      A = pre * (E[i0] - tail * E[j]);
+      B = pre * (E[np1 + i0] - tail * E[np1 + j]);
+      C = pre * (E[2 * np1 + i0] - tail * E[2 * np1 + j]);
+    }
+    coef[cell] = make_coef(A, B, C, count);
+  }
+}
+
+cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
+  const fmap_grid& g = p->grid;
+  if ((int64_t)g.n_t0 * g.n_tau == 0) return cudaSuccess;
+  const int n_ant = a->shared_antenna ? 1 : p->n_templates;
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  for (int ta = 0; ta < n_ant; ++ta) {
+    const float* ant = a->antenna + (int64_t)ta * 3 * p->n_sft;
+    for (int32_t lo = 0; lo < g.n_tau; lo += p->tau_chunk) {
+      const int32_t len = std::min<int32_t>(p->tau_chunk, g.n_tau - lo);
+      if (p->n_sft > 0) {
+        k_exp_suffix<<<len, kSufThreads, 0, s>>>(p->ws.rel_t, p->n_sft, ant, g, lo, p->ws.esuf);
+        p->launches += 1;
+      }
+      const int64_t total = (int64_t)g.n_t0 * len;
+      const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
+      k_exp_coef<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, lo, len, p->ws.i0,
+                                        p->ws.jend, p->ws.esuf, p->ws.coef + ta * cells);
+      p->launches += 1;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Plain contraction on the CUDA cores.  Tile = 128 cells: one t0 row m and
+// 128 consecutive tau; they share i0, so the tile's atoms are [i0, max j).
+// The weights are computed once per (cell, atom) and reused for the TC
+// templates of the block; atoms are staged KC at a time in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kExpCells = 128;
+constexpr int kKC = 32;
+
+int64_t exp_tiles(const fmap_grid& g) {
+  return (int64_t)g.n_t0 * ((g.n_tau + kExpCells - 1) / kExpCells);
+}
+
+template <typename Acc, int TC>
+__global__ void __launch_bounds__(kExpCells)
+k_exp_plain(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base,
+            int32_t n_sft, fmap_grid g, const int32_t* __restrict__ i0tab,
+            const int32_t* __restrict__ jend, const Coef* __restrict__ coef,
+            int32_t shared_antenna, const float* __restrict__ fafb, int32_t n_templates,
+            float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
+  constexpr int NCOL = 4 * TC;
+  constexpr int LD = NCOL + 4;
+  __shared__ __align__(16) float sx[kKC][LD];
+  __shared__ int32_t srel[kKC];
+  __shared__ Partial scratch[kExpCells / 32];
+  __shared__ int32_t s_jmax;
+  const int64_t tile = blockIdx.x;
+  const int32_t nblk = (g.n_tau + kExpCells - 1) / kExpCells;
+  const int32_t m = (int32_t)(tile / nblk);
+  const int32_t nn = (int32_t)(tile - (int64_t)m * nblk) * kExpCells + threadIdx.x;
+  const bool in_grid = nn < g.n_tau;
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const int64_t cell = (int64_t)m * g.n_tau + (in_grid ? nn : 0);
+  const int32_t tq0 = blockIdx.y * TC;
+  const int32_t i0 = i0tab[m];
+  const int32_t jc = in_grid ? jend[cell] : i0;
+  if (threadIdx.x == 0) s_jmax = i0;
+  __syncthreads();
+  const int32_t jw = __reduce_max_sync(0xffffffffu, jc);
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_jmax, jw);
+  __syncthreads();
+  const int32_t jmax = s_jmax;
+  int32_t t0rel = 0;
+  if (jmax > i0) t0rel = (int32_t)(g.t0_min + (int64_t)m * g.dt0 - *t_base);
+  const double tau = (double)(g.tau_min + (int64_t)(in_grid ? nn : 0) * g.dtau);
+  const float c2 = (float)(-1.4426950408889634 / tau);
+  Acc acc[NCOL];
+#pragma unroll
+  for (int q = 0; q < NCOL; ++q) acc[q] = Acc(0);
+  for (int32_t k0 = i0; k0 < jmax; k0 += kKC) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < NCOL * kKC; e += kExpCells) {
+      const int col = e / kKC, kk = e - col * kKC;
+      const int32_t a = k0 + kk;
+      const int32_t tq = tq0 + (col >> 2);
+      float v = 0.0f;
+      if (a < jmax && tq < n_templates) v = fafb[((int64_t)tq * 4 + (col & 3)) * n_sft + a];
+      sx[kk][col] = v;
+    }
+    if (threadIdx.x < kKC) {
+      const int32_t a = k0 + threadIdx.x;
+      srel[threadIdx.x] = a < jmax ? rel_t[a] : 0;
+    }
+    __syncthreads();
+    const int kend = min(kKC, jmax - k0);
+    for (int kk = 0; kk < kend; ++kk) {
+      const int32_t d = srel[kk] - t0rel;
+      Acc w;
+      if constexpr (std::is_same<Acc, double>::value) {
+        w = (k0 + kk < jc) ? exp(-(double)d / tau) : 0.0;
+      } else {
+        w = (k0 + kk < jc) ? exp2f((float)d * c2) : 0.0f;
+      }
+      const float4* row = reinterpret_cast<const float4*>(&sx[kk][0]);
+#pragma unroll
+      for (int q = 0; q < NCOL / 4; ++q) {
+        const float4 v = row[q];
+        acc[4 * q + 0] += w * (Acc)v.x;
+        acc[4 * q + 1] += w * (Acc)v.y;
+        acc[4 * q + 2] += w * (Acc)v.z;
+        acc[4 * q + 3] += w * (Acc)v.w;
+      }
+    }
+  }
+  const Coef cf0 = coef[cell];
+#pragma unroll
+  for (int q = 0; q < TC; ++q) {
+    const int32_t tq = tq0 + q;
+    if (tq >= n_templates) break;
+    const Coef cf = shared_antenna ? cf0 : coef[(int64_t)tq * cells + cell];
+    const float v = two_f(cf, (float)acc[4 * q], (float)acc[4 * q + 1], (float)acc[4 * q + 2],
+                          (float)acc[4 * q + 3]);
+    const bool ok = in_grid && cf.valid != 0.0f;
+    if (map && in_grid) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
+    Partial pt = partial_empty();
+    partial_add(pt, v, (int32_t)cell, ok);
+    pt = partial_block_reduce<kExpCells / 32>(pt, scratch);
+    if (threadIdx.x == 0) parts[(int64_t)tq * stride + tile] = pt;
+  }
+}
+
+cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
+                             int64_t* tiles_used) {
+  const fmap_grid& g = p->grid;
+  const int64_t tiles = exp_tiles(g);
+  *tiles_used = tiles;
+  if (tiles == 0 || p->n_templates == 0) return cudaSuccess;
+  if (p->precision == FMAP_FP64) {
+    constexpr int TC = 8;
+    dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + TC - 1) / TC));
+    k_exp_plain<double, TC><<<grid, kExpCells, 0, s>>>(
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend, p->ws.coef,
+        a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->n_tiles);
+  } else {
+    constexpr int TC = 16;
+    dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + TC - 1) / TC));
+    k_exp_plain<float, TC><<<grid, kExpCells, 0, s>>>(
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend, p->ws.coef,
+        a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->n_tiles);
+  }
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace fmap

@@ -1,0 +1,132 @@
+// Internal declarations of libfmap: the plan, its workspace, the per-tile
+// reduction partials and the device helpers every kernel shares.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fmap.h"
+
+namespace fmap {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+fmap_status cuda_fail(cudaError_t e, const char* what);
+
+#define FMAP_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ::fmap::cuda_fail(e_, #call); \
+  } while (0)
+
+// Device-side error bits latched in the plan's status word.
+enum : uint32_t { DEV_ERR_ORDER = 1u, DEV_ERR_SPAN = 2u };
+
+// ---------------------------------------------------------------------------
+// Reduction partial of one tile and one template.  sum = sum over the tile's
+// valid cells of exp(F - F_max) with F = 2F/2 and F_max = max2F/2; arg is the
+// lowest linear index m*n_tau+n holding max2F; nvalid = 0 marks an empty
+// partial (max2F = -1, arg = INT32_MAX, sum = 0).
+// ---------------------------------------------------------------------------
+struct __align__(16) Partial {
+  float max2F;
+  int32_t arg;
+  float sum;
+  int32_t nvalid;
+};
+
+// Per-cell 2F coefficients.  2F = k1 |Fa|^2 + k2 |Fb - beta Fa|^2, which is
+// Eq. (F_FaFb) times two with k1 = 2/A, beta = C/A, k2 = 2A/D (completing the
+// square in Fa).  valid = 1 when the cell has >= 2 atoms and D > 0 in FP64;
+// invalid cells have k1 = k2 = 0.
+struct __align__(16) Coef {
+  float k1;
+  float beta;
+  float k2;
+  float valid;
+};
+
+// Workspace of a plan (all device memory, owned by the plan).
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+  int32_t* rel_t = nullptr;      // [N] t - t[0]
+  int64_t* t_base = nullptr;     // [1] t[0]
+  uint32_t* dev_err = nullptr;   // [1] latched device error bits
+  int32_t* i0 = nullptr;         // [n_t0] first atom with t >= t0_m
+  int32_t* jend = nullptr;       // [n_t0][n_tau] one past the last atom of each window
+  Coef* coef = nullptr;          // [T_ant][n_t0][n_tau]
+  Partial* partials = nullptr;   // [T][n_tiles]
+  // rect
+  double* pa = nullptr;          // [T_ant][N+1][4] FP64 antenna prefix (a2, b2, ab, pad)
+  float4* px = nullptr;          // [T][N+1][2] float-float data prefix (hi4, lo4)
+  // exp
+  double* esuf = nullptr;        // [tau_chunk][3][N+1] FP64 decayed suffix sums
+  // tensor-core operands
+  void* xop = nullptr;           // split X operands (layout per precision)
+  // host-API staging
+  int64_t* st_t = nullptr;
+  float* st_ant = nullptr;
+  float* st_x = nullptr;
+  float* st_map = nullptr;
+  fmap_summary* st_sum = nullptr;
+};
+
+}  // namespace fmap
+
+struct fmap_plan_s {
+  fmap_grid grid;
+  int32_t n_sft = 0;
+  int32_t n_templates = 0;
+  fmap_precision precision = FMAP_FP64;
+  uint32_t flags = 0;
+  double log_prior = 0.0;
+  int device = 0;
+  int n_sm = 0;
+  int64_t n_tiles = 0;        // partial slots per template
+  int32_t tau_chunk = 0;      // exp: tau values per suffix launch
+  size_t xop_bytes = 0;
+  bool host_staging = false;
+  cudaStream_t last_stream = nullptr;
+  fmap::Workspace ws;
+  // timing (fmap_plan_enable_timing)
+  bool timing = false;
+  int64_t launches = 0;       // kernels launched since timing was enabled
+  std::vector<cudaEvent_t> events;  // FMAP_N_PHASES + 1 per timed call
+};
+
+namespace fmap {
+
+// ---- host launchers (each returns cudaGetLastError of its launches and
+// adds the number of kernels it launched to p->launches) -------------------
+cudaError_t launch_prep(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s);
+cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s);
+// Each compute launcher reports how many partial slots per template it wrote.
+// launch_rect records `mark` (if non-null) between its prefix scans and the
+// per-cell kernel.
+cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
+                        int64_t* tiles_used, cudaEvent_t mark);
+cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
+cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
+                             int64_t* tiles_used);
+cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
+                          int64_t* tiles_used);
+cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, fmap_summary* d_summary,
+                                cudaStream_t s);
+cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t* d_valid,
+                               fmap_summary* d_summary, cudaStream_t s);
+
+// Tile counts of each kernel family (partials per template).
+int64_t rect_tiles(const fmap_grid& g);
+int64_t exp_tiles(const fmap_grid& g);
+int64_t marg_tiles(const fmap_grid& g);
+bool exp_tc_available(fmap_precision prec);
+size_t exp_tc_operand_bytes(const fmap_grid& g, int32_t n_sft, int32_t n_templates,
+                            fmap_precision prec);
+
+}  // namespace fmap

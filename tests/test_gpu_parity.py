@@ -1,0 +1,207 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs, element by element, plus the reductions, edge cases and
+the device-side data checks."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import EXP, RECT, T_SFT, Grid
+from tests.parity_util import LOGB_TOL, TOL, check_map, check_summary, oracle_map, rel_err, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1805_05652_gb300 as fm  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    fm.build()
+    oracle.build()
+
+
+def _f_err(got, ref, valid):
+    return 0.5 * float(np.abs(got - ref)[valid].max()) if valid.any() else 0.0
+
+
+def _parity(inst, prec, mode="fast"):
+    ref, valid, _ = oracle_map(inst, mode)
+    got, gs = run_gpu(inst, prec)
+    worst = check_map(got, ref, valid, TOL[prec])
+    fe = 0.0 if prec == "fp64" else _f_err(got, ref, valid)
+    check_summary(gs, ref, valid, TOL[prec], LOGB_TOL, fe)
+    return worst
+
+
+# ---------------------------------------------------------------- rect --------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rect_small_config(prec):
+    """200 single-detector SFTs with 10% gaps, 200 x 200 cells, one injection."""
+    inst = synth.config_small_rect()
+    _parity(inst, prec, mode="direct")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rect_ragged_tiles_offgrid_per_template_antenna(prec):
+    """n_tau spanning two 256-cell tiles and a ragged tail, t0 before the data
+    and windows past its end, off-grid steps, per-template antenna rows."""
+    grid = Grid(-7000, 1000, 37, 700, 1900, 600, RECT)
+    inst = synth.make_instance(41, n_det=2, presence=0.85, n_merged=700, n_templates=3,
+                               grid=grid, shared_antenna=False,
+                               injections=[(1, RECT, 30000, 200000, 150.0)])
+    _parity(inst, prec)
+
+
+# ----------------------------------------------------------------- exp --------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
+def test_exp_ragged(prec):
+    """Exp windows: 11 templates (ragged template chunks), n_tau = 300 (two
+    128-cell tiles and a tail), off-grid t0 and tau steps, 2 detectors."""
+    grid = Grid(-2500, 1000, 29, 900, 1300, 300, EXP)
+    inst = synth.make_instance(43, n_det=2, presence=0.9, n_merged=400, n_templates=11,
+                               grid=grid, injections=[(0, EXP, 20000, 60000, 200.0)])
+    try:
+        _parity(inst, prec)
+    except fm.FmapError as e:
+        if e.status == fm.FMAP_ERR_UNSUPPORTED:
+            pytest.skip(f"{prec} not built")
+        raise
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_exp_per_template_antenna(prec):
+    grid = Grid(0, T_SFT, 20, T_SFT, T_SFT, 140, EXP)
+    inst = synth.make_instance(44, n_det=1, presence=0.9, n_merged=200, n_templates=3,
+                               grid=grid, shared_antenna=False)
+    _parity(inst, prec)
+
+
+# ------------------------------------------------------- reductions, API ------
+
+def test_marginalise_matches_oracle():
+    rng = np.random.default_rng(5)
+    T, n_t0, n_tau = 3, 70, 130
+    m = (rng.chisquare(4, size=(T, n_t0, n_tau)) * 2).astype(np.float32)
+    m[1, 10, 20] = m[1, 30, 40] = 77.0          # tie: lowest index wins
+    v = rng.random(m.shape) > 0.2
+    v[2] = False                                  # a template with no valid cell
+    grid = (0, T_SFT, n_t0, T_SFT, T_SFT, n_tau, T_SFT, RECT)
+    plan = fm.Plan(grid, 10, T, "fp64")
+    dm = torch.from_numpy(m).cuda()
+    dv = torch.from_numpy(v.astype(np.uint8)).cuda()
+    gs = fm.summary_to_numpy(plan.marginalise(dm, dv))
+    rs = oracle.summary(m.astype(np.float64), v)
+    assert np.array_equal(gs["n_valid"], rs["n_valid"])
+    for j in range(2):
+        assert (gs["m"][j], gs["n"][j]) == (rs["m"][j], rs["n"][j])
+        assert gs["max2F"][j] == np.float32(rs["max2F"][j])
+        assert abs(gs["logB"][j] - rs["logB"][j]) < 1e-6
+    assert gs["m"][2] == -1 and np.isnan(gs["logB"][2])
+    gs2 = fm.summary_to_numpy(plan.marginalise(dm, None))
+    rs2 = oracle.summary(m.astype(np.float64), np.ones_like(v))
+    assert np.allclose(gs2["logB"], rs2["logB"], atol=1e-6, rtol=0)
+    plan.close()
+
+
+def test_log_prior_constant_shifts_logB():
+    inst = synth.config_small_rect()
+    _, gs0 = run_gpu(inst, "fp64")
+    import paper_1805_05652_gb300 as fm2
+    t = torch.from_numpy(inst.t).cuda()
+    a = torch.from_numpy(inst.antenna).cuda()
+    x = torch.from_numpy(inst.fafb).cuda()
+    plan = fm2.Plan(inst.grid, inst.n_sft, 1, "fp64")
+    plan.set_log_prior(-2.5)
+    _, s = plan.compute(t, a, x, want_map=False)
+    gs = fm2.summary_to_numpy(s)
+    assert abs(gs["logB"][0] - (gs0["logB"][0] - 2.5)) < 1e-12
+    plan.close()
+
+
+@pytest.mark.parametrize("window,prec", [(RECT, "fp64"), (EXP, "fp32")])
+def test_host_api_equals_device_api(window, prec):
+    """fmap_compute_host (host buffers, copies inside) gives the same bits as
+    the device entry point."""
+    grid = Grid(0, T_SFT, 30, 2 * T_SFT, T_SFT, 90, window)
+    inst = synth.make_instance(9, n_slots=150, n_templates=4, grid=grid)
+    got, gs = run_gpu(inst, prec)
+    plan = fm.Plan(grid, inst.n_sft, inst.n_templates, prec)
+    hm = np.zeros((4, 30, 90), dtype=np.float32)
+    hs = np.zeros(4, dtype=fm.SUMMARY_DTYPE)
+    plan.compute_host(inst.t, inst.antenna, inst.fafb, hm, hs)
+    assert np.array_equal(hm.astype(np.float64), got)
+    assert hs.tobytes() == gs.tobytes()
+    plan.close()
+
+
+@pytest.mark.parametrize("window,prec", [(RECT, "fp64"), (EXP, "fp64"), (EXP, "fp32")])
+def test_deterministic(window, prec):
+    grid = Grid(0, T_SFT, 25, T_SFT, T_SFT, 140, window)
+    inst = synth.make_instance(12, n_slots=120, n_templates=5, grid=grid)
+    a, sa = run_gpu(inst, prec)
+    b, sb = run_gpu(inst, prec)
+    assert np.array_equal(a, b) and sa.tobytes() == sb.tobytes()
+
+
+# ----------------------------------------------------------------- edges -----
+
+@pytest.mark.parametrize("window", [RECT, EXP])
+@pytest.mark.parametrize("case", ["one_sft", "grid_after_data", "too_short", "empty_grid",
+                                  "no_sft"])
+def test_degenerate_inputs(window, case):
+    n = {"one_sft": 1, "no_sft": 0}.get(case, 40)
+    grid = Grid(0, T_SFT, 12, T_SFT if window == EXP else 2 * T_SFT, T_SFT, 9, window)
+    if case == "grid_after_data":
+        grid = Grid(10**6, T_SFT, 12, T_SFT, T_SFT, 9, window)
+    if case == "too_short":
+        grid = Grid(0, T_SFT, 12, 100, 50, 9, window)        # windows shorter than an SFT
+    if case == "empty_grid":
+        grid = Grid(0, T_SFT, 0, T_SFT, T_SFT, 9, window)
+    if n > 0:
+        inst = synth.make_instance(13, n_slots=n, n_templates=2, grid=grid)
+    else:
+        inst = synth.Instance(np.zeros(0, np.int64), np.zeros((3, 0), np.float32),
+                              np.zeros((2, 4, 0), np.float32), grid)
+    for prec in ("fp64", "fp32"):
+        got, gs = run_gpu(inst, prec)
+        assert np.all(got == 0.0)
+        assert np.all(gs["n_valid"] == 0) and np.all(gs["m"] == -1)
+        assert np.all(np.isnan(gs["logB"]))
+
+
+def test_nonincreasing_timestamps_reported():
+    grid = Grid(0, T_SFT, 5, T_SFT, T_SFT, 5, EXP)
+    inst = synth.make_instance(14, n_slots=30, grid=grid)
+    t = inst.t.copy()
+    t[10] = t[9]
+    plan = fm.Plan(grid, inst.n_sft, 1, "fp32")
+    plan.compute(torch.from_numpy(t).cuda(), torch.from_numpy(inst.antenna).cuda(),
+                 torch.from_numpy(inst.fafb).cuda())
+    assert plan.status() == fm.FMAP_ERR_DATA
+    assert plan.status() == fm.FMAP_OK            # latched error was cleared
+    plan.close()
+
+
+def test_mismatched_calls_rejected():
+    grid = Grid(0, T_SFT, 5, T_SFT, T_SFT, 5, RECT)
+    inst = synth.make_instance(15, n_slots=30, grid=grid)
+    plan = fm.Plan(grid, inst.n_sft, 1, "fp64")
+    t = torch.from_numpy(inst.t).cuda()
+    a = torch.from_numpy(inst.antenna).cuda()
+    x = torch.from_numpy(inst.fafb).cuda()
+    atoms = plan.atoms(t, a, x)
+    out = torch.empty(25, device="cuda")
+    with pytest.raises(fm.FmapError) as e:
+        fm.fmap_compute_exp(plan.handle, atoms, out, None)
+    assert e.value.status == fm.FMAP_ERR_ARG
+    bad = fm.make_atoms(inst.n_sft + 1, 1, 1, t, a, x)
+    with pytest.raises(fm.FmapError):
+        fm.fmap_compute_rect(plan.handle, bad, out, None)
+    plan.close()
