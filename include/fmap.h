@@ -58,17 +58,23 @@ typedef enum {
 typedef enum { FMAP_RECT = 0, FMAP_EXP = 1 } fmap_window;
 
 /*
- * Arithmetic of the windowed sums (the determinant, the 2F coefficients and
- * the log-Bayes reduction are FP64 in every mode):
- *   FMAP_FP64   rect: FP64 prefix sums, differences in compensated FP32;
+ * Arithmetic of the windowed sums.  In every mode the antenna sums A, B, C,
+ * the determinant D = AB - C^2, the 2F coefficients and the log-Bayes
+ * reduction are FP64 (D and the coefficients once per cell):
+ *   FMAP_FP64   rect: FP64 prefix sums over SFTs (data rows kept as float
+ *               pairs), O(1) compensated differences per cell;
  *               exp:  FP64 contraction on the CUDA cores.
- *   FMAP_FP32   rect: one thread per t0 row with FP32 running sums (the
- *               paper's rectangular kernel, Sec. 3);
+ *   FMAP_FP32   rect: one thread per t0 row with FP32 running sums of Fa, Fb
+ *               (the paper's rectangular kernel, Sec. 3);
  *               exp:  FP32 contraction on the CUDA cores (the plain path).
  *   FMAP_TF32   exp only: tensor-core contraction (tcgen05, kind::tf32) with
  *               both operands split hi + lo, three products, FP32 accumulate.
  *   FMAP_BF16X3 exp only: tensor-core contraction (tcgen05, kind::f16, bf16)
  *               with hi*hi + hi*lo + lo*hi, FP32 accumulate.
+ * Cells whose antenna matrix is ill-conditioned (A B / D > 100: windows of a
+ * few SFTs of one detector, where any FP32 sum loses ~1e-7 sqrt(AB/D) of
+ * relative accuracy in 2F) are recomputed in FP64 from their atoms in every
+ * mode.
  */
 typedef enum { FMAP_FP64 = 0, FMAP_FP32 = 1, FMAP_TF32 = 2, FMAP_BF16X3 = 3 } fmap_precision;
 
@@ -183,7 +189,8 @@ fmap_status fmap_compute_host(fmap_plan_t* plan, const fmap_atoms* host_atoms, f
  *     the per-cell 2F coefficients),
  *   2 the windowed contraction with the fused 2F epilogue (the dominant
  *     kernel),
- *   3 the final per-template reduction.
+ *   3 the FP64 recomputation of ill-conditioned cells and the final
+ *     per-template reduction.
  * fmap_plan_enable_timing(plan, 1) starts recording (and clears the totals);
  * fmap_plan_read_timing waits for the recorded calls and returns the summed
  * milliseconds per phase, the number of timed calls and the number of

@@ -55,7 +55,8 @@ static bool precision_supported(int window, fmap_precision prec) {
 }
 
 struct Layout {
-  size_t rel_t, t_base, dev_err, i0, jend, coef, parts, pa, px, esuf, xop, total;
+  size_t rel_t, t_base, dev_err, i0, jend, coef, parts, flag_blocks, n_flag, flag_list, pa, px,
+      esuf, xop, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -82,19 +83,23 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     off = align_up(off + std::max<size_t>(bytes, 1), A);
     return at;
   };
-  L.rel_t = take(sizeof(int32_t) * std::max<int32_t>(n_sft, 1));
+  L.rel_t = take(sizeof(int32_t) * (size_t)rel_t_entries(n_sft));
   L.t_base = take(sizeof(int64_t));
   L.dev_err = take(sizeof(uint32_t));
   L.i0 = take(sizeof(int32_t) * std::max<int32_t>(g->n_t0, 1));
   L.jend = take(sizeof(int32_t) * std::max<int64_t>(cells, 1));
-  L.parts = take(sizeof(Partial) * (size_t)std::max<int32_t>(T, 1) * (size_t)tiles);
-  L.pa = L.px = L.esuf = L.coef = L.xop = 0;
+  L.parts = take(sizeof(Partial) * (size_t)std::max<int32_t>(T, 1) * (size_t)(tiles + kFixSlots));
+  const size_t entries = (size_t)std::max<int64_t>(cells, 1) * (size_t)t_ant;
+  L.coef = take(sizeof(Coef) * entries);
+  L.flag_blocks = take(sizeof(int32_t) * ((entries + 1023) / 1024));
+  L.n_flag = take(sizeof(int32_t));
+  L.flag_list = take(sizeof(int64_t) * entries);
+  L.pa = L.px = L.esuf = L.xop = 0;
   const size_t np1 = (size_t)n_sft + 1;
   if (g->window == FMAP_RECT) {
     L.pa = take(sizeof(double) * 4 * np1 * (size_t)t_ant);
     L.px = take(2 * sizeof(float4) * np1 * (size_t)std::max<int32_t>(T, 1));
   } else {
-    L.coef = take(sizeof(Coef) * (size_t)std::max<int64_t>(cells, 1) * (size_t)t_ant);
     const size_t per_tau = 3 * sizeof(double) * np1;
     int64_t chunk = (int64_t)std::max<size_t>(1, kEsufBudget / per_tau);
     chunk = std::min<int64_t>(chunk, std::max<int32_t>(g->n_tau, 1));
@@ -171,6 +176,7 @@ fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
   }
   const Layout L = layout_of(grid, n_sft, n_templates, precision, flags);
   p->n_tiles = L.n_tiles;
+  p->part_stride = L.n_tiles + kFixSlots;
   p->tau_chunk = L.tau_chunk;
   void* base = nullptr;
   e = cudaMalloc(&base, L.total);
@@ -190,11 +196,14 @@ fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
   w.i0 = (int32_t*)(b + L.i0);
   w.jend = (int32_t*)(b + L.jend);
   w.partials = (Partial*)(b + L.parts);
+  w.coef = (Coef*)(b + L.coef);
+  w.flag_blocks = (int32_t*)(b + L.flag_blocks);
+  w.n_flag = (int32_t*)(b + L.n_flag);
+  w.flag_list = (int64_t*)(b + L.flag_list);
   if (grid->window == FMAP_RECT) {
     w.pa = (double*)(b + L.pa);
     w.px = (float4*)(b + L.px);
   } else {
-    w.coef = (Coef*)(b + L.coef);
     w.esuf = (double*)(b + L.esuf);
     if (L.xop) w.xop = (void*)(b + L.xop);
   }
@@ -287,8 +296,8 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   if (ev[1]) FMAP_CUDA(cudaEventRecord(ev[1], s));
   int64_t tiles = 0;
   if (window == FMAP_RECT) {
+    FMAP_CUDA(launch_rect_coef(p, a, s));
     FMAP_CUDA(launch_rect(p, a, d_2F, s, &tiles, ev[2]));
-    if (ev[2] && p->precision == FMAP_FP32) FMAP_CUDA(cudaEventRecord(ev[2], s));
   } else {
     FMAP_CUDA(launch_exp_coef(p, a, s));
     if (ev[2]) FMAP_CUDA(cudaEventRecord(ev[2], s));
@@ -299,7 +308,8 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
     }
   }
   if (ev[3]) FMAP_CUDA(cudaEventRecord(ev[3], s));
-  FMAP_CUDA(launch_final_reduce(p, tiles, d_summary, s));
+  FMAP_CUDA(launch_flag_and_fixup(p, a, d_2F, s));
+  FMAP_CUDA(launch_final_reduce(p, tiles, true, d_summary, s));
   if (ev[4]) FMAP_CUDA(cudaEventRecord(ev[4], s));
   return FMAP_OK;
 }
@@ -367,8 +377,9 @@ fmap_status fmap_plan_status(fmap_plan_t* p) {
     std::string m;
     if (bits & DEV_ERR_ORDER) m += "timestamps are not strictly increasing; ";
     if (bits & DEV_ERR_SPAN) m += "timestamp span is >= 2^31 s; ";
+    if (bits & DEV_ERR_TIMEOUT) m += "a bounded device wait gave up; ";
     set_error(m);
-    return FMAP_ERR_DATA;
+    return (bits & DEV_ERR_TIMEOUT) ? FMAP_ERR_TIMEOUT : FMAP_ERR_DATA;
   }
   return FMAP_OK;
 }

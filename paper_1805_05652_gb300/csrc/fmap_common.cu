@@ -9,9 +9,13 @@ namespace fmap {
 
 // t -> t - t[0] as int32, with the data checks (strictly increasing,
 // span < 2^31 s) latched into the plan's status word.
-__global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t* __restrict__ rel_t,
-                       int64_t* __restrict__ t_base, uint32_t* __restrict__ err) {
+__global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc,
+                       int32_t* __restrict__ rel_t, int64_t* __restrict__ t_base,
+                       uint32_t* __restrict__ err) {
   const int64_t base = t[0];
+  for (int64_t i = n + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_alloc;
+       i += (int64_t)gridDim.x * blockDim.x)
+    rel_t[i] = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t ti = t[i];
@@ -49,7 +53,8 @@ cudaError_t launch_prep(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
   if (p->n_sft <= 0) return cudaSuccess;
   const int threads = 256;
   const int blocks = (int)std::min<int64_t>((p->n_sft + threads - 1) / threads, 4096);
-  k_prep<<<blocks, threads, 0, s>>>(d_t, p->n_sft, p->ws.rel_t, p->ws.t_base, p->ws.dev_err);
+  k_prep<<<blocks, threads, 0, s>>>(d_t, p->n_sft, rel_t_entries(p->n_sft), p->ws.rel_t,
+                                    p->ws.t_base, p->ws.dev_err);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -72,8 +77,8 @@ cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
 constexpr int kRedThreads = 256;
 
 __global__ void __launch_bounds__(kRedThreads)
-k_final_reduce(const Partial* __restrict__ parts, int64_t n_tiles, int64_t stride,
-               int32_t n_tau, double log_prior, fmap_summary* __restrict__ out) {
+k_final_reduce(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
+               int64_t stride, int32_t n_tau, double log_prior, fmap_summary* __restrict__ out) {
   __shared__ float s_max[kRedThreads];
   __shared__ long long s_cnt[kRedThreads];
   __shared__ double s_sum[kRedThreads];
@@ -82,8 +87,10 @@ k_final_reduce(const Partial* __restrict__ parts, int64_t n_tiles, int64_t strid
   const Partial* pp = parts + (int64_t)blockIdx.x * stride;
   float mx = -1.0f;
   long long cnt = 0;
-  for (int64_t b = tid; b < n_tiles; b += kRedThreads) {
-    const Partial q = pp[b];
+  const int64_t n_all = n_tiles + n_fix;
+  auto slot = [&](int64_t b) { return b < n_tiles ? pp[b] : pp[fix0 + (b - n_tiles)]; };
+  for (int64_t b = tid; b < n_all; b += kRedThreads) {
+    const Partial q = slot(b);
     if (q.nvalid > 0) {
       mx = fmaxf(mx, q.max2F);
       cnt += q.nvalid;
@@ -105,8 +112,8 @@ k_final_reduce(const Partial* __restrict__ parts, int64_t n_tiles, int64_t strid
   double sum = 0.0;
   int32_t arg = kNoArg;
   if (N > 0) {
-    for (int64_t b = tid; b < n_tiles; b += kRedThreads) {
-      const Partial q = pp[b];
+    for (int64_t b = tid; b < n_all; b += kRedThreads) {
+      const Partial q = slot(b);
       if (q.nvalid > 0) {
         sum += (double)q.sum * exp(0.5 * ((double)q.max2F - (double)M));
         if (q.max2F == M && q.arg < arg) arg = q.arg;
@@ -142,12 +149,13 @@ k_final_reduce(const Partial* __restrict__ parts, int64_t n_tiles, int64_t strid
   }
 }
 
-cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, fmap_summary* d_summary,
-                                cudaStream_t s) {
+cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, bool with_fix,
+                                fmap_summary* d_summary, cudaStream_t s) {
   if (!d_summary || p->n_templates == 0) return cudaSuccess;
+  const bool fix = with_fix && (int64_t)p->grid.n_t0 * p->grid.n_tau > 0;
   k_final_reduce<<<p->n_templates, kRedThreads, 0, s>>>(
-      p->ws.partials, n_tiles, p->n_tiles, p->grid.n_tau > 0 ? p->grid.n_tau : 1, p->log_prior,
-      d_summary);
+      p->ws.partials, n_tiles, p->n_tiles, fix ? kFixSlots : 0, p->part_stride,
+      p->grid.n_tau > 0 ? p->grid.n_tau : 1, p->log_prior, d_summary);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -191,13 +199,13 @@ cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t*
   const int64_t tiles = marg_tiles(p->grid);
   if (tiles > 0 && p->n_templates > 0) {
     dim3 grid((unsigned)tiles, (unsigned)p->n_templates);
-    k_marg_partials<<<grid, kMargThreads, 0, s>>>(d_2F, d_valid, cells, p->n_tiles,
+    k_marg_partials<<<grid, kMargThreads, 0, s>>>(d_2F, d_valid, cells, p->part_stride,
                                                   p->ws.partials);
     p->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return launch_final_reduce(p, tiles, d_summary, s);
+  return launch_final_reduce(p, tiles, false, d_summary, s);
 }
 
 }  // namespace fmap

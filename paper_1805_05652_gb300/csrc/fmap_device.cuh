@@ -114,7 +114,7 @@ __device__ __forceinline__ Coef make_coef(double A, double B, double C, int32_t 
     c.k1 = 2.0f / af;
     c.beta = cf / af;
     c.k2 = 2.0f * af / df;
-    c.valid = 1.0f;
+    c.valid = (A * B > kCondThreshold * D) ? 2.0f : 1.0f;
   } else {
     c.k1 = 0.0f;
     c.beta = 0.0f;

@@ -257,8 +257,8 @@ k_exp_plain(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_bas
     const Coef cf = shared_antenna ? cf0 : coef[(int64_t)tq * cells + cell];
     const float v = two_f(cf, (float)acc[4 * q], (float)acc[4 * q + 1], (float)acc[4 * q + 2],
                           (float)acc[4 * q + 3]);
-    const bool ok = in_grid && cf.valid != 0.0f;
-    if (map && in_grid) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
+    const bool ok = in_grid && cf.valid == 1.0f;
+    if (map && in_grid && cf.valid != 2.0f) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
     Partial pt = partial_empty();
     partial_add(pt, v, (int32_t)cell, ok);
     pt = partial_block_reduce<kExpCells / 32>(pt, scratch);
@@ -277,13 +277,13 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
     dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + TC - 1) / TC));
     k_exp_plain<double, TC><<<grid, kExpCells, 0, s>>>(
         p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend, p->ws.coef,
-        a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->n_tiles);
+        a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->part_stride);
   } else {
     constexpr int TC = 16;
     dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + TC - 1) / TC));
     k_exp_plain<float, TC><<<grid, kExpCells, 0, s>>>(
         p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend, p->ws.coef,
-        a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->n_tiles);
+        a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->part_stride);
   }
   p->launches += 1;
   return cudaGetLastError();

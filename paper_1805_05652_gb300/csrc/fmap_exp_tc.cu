@@ -1,17 +1,581 @@
-// Tensor-core (tcgen05) contraction of the exponential window: placeholder
-// until the sm_103a kernels land; the plan refuses these precisions.
+// Exponential-window contraction on the 5th-generation tensor cores (tcgen05).
+//
+// S[(m, n), c] = sum_a W[(m, n), a] X[a, c] with W = e^{-(t_a - t0_m)/tau_n}
+// inside the window (Eq. winexp) and X = the 4T data columns (Re Fa, Im Fa,
+// Re Fb, Im Fb of each template).  A tile is 128 cells (one t0 row, 128
+// consecutive tau) x N data columns (N = 4 x templates of the chunk, <= 256).
+//
+// Per K-tile of KT atoms (128 bytes of one operand row):
+//   * eight "generator" warps compute W for their rows in registers (one
+//     exp2 per element), split it into hi + lo (TF32 or BF16) and store both
+//     into tensor memory, which is the MMA's A operand;
+//   * one warp streams the hi and lo K-major X tiles into shared memory with
+//     TMA (128-byte swizzle), the MMA's B operand;
+//   * one thread issues hi*hi + hi*lo + lo*hi (3 MMAs per K step) into an
+//     FP32 accumulator in tensor memory; tcgen05.commit frees the stage.
+// Then the generator warps read the accumulator back (tcgen05.ld), apply the
+// per-cell FP64-derived 2F coefficients, write the map and the per-template
+// (max, argmax, log-sum-exp) partials.  K-tiles outside the union of the
+// tile's windows are never visited; W is zero outside each cell's window.
+//
+// Every wait on an mbarrier is bounded by %globaltimer; on expiry the kernel
+// latches an error bit in the plan's status word and winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+
 #include "fmap_device.cuh"
 
 namespace fmap {
+namespace tc {
 
-bool exp_tc_available(fmap_precision) { return false; }
+constexpr int kGenWarps = 8;
+constexpr int kMmaWarp = 8;
+constexpr int kTmaWarp = 9;
+constexpr int kThreads = 320;
+constexpr int kStages = 3;
+constexpr int kRows = 128;
+constexpr int kAColsPerStage = 64;   // hi (32 columns) + lo (32 columns)
+constexpr uint64_t kWaitNs = 2000000000ull;
 
-size_t exp_tc_operand_bytes(const fmap_grid&, int32_t, int32_t, fmap_precision) { return 0; }
+// ---------------------------------------------------------------- PTX ------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on timeout or when another role already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <bool BF16>
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  if constexpr (BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return y;
+}
+// Pack (lo_elem -> bits 15:0, hi_elem -> bits 31:16) as bf16x2, round to nearest.
+__device__ __forceinline__ uint32_t pack_bf16(float even, float odd) {
+  uint32_t y;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(y) : "f"(odd), "f"(even));
+  return y;
+}
 
-cudaError_t launch_exp_tc(fmap_plan_s*, const fmap_atoms*, float*, cudaStream_t,
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes in 8-row (1024-byte) groups.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading-dimension offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride between 8-row groups
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B both TF32 or both BF16,
+// K-major A and B, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_of(bool bf16, int n) {
+  return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+struct Params {
+  const int32_t* rel_t;
+  const int64_t* t_base;
+  fmap_grid g;
+  const int32_t* i0tab;
+  const int32_t* jend;
+  const Coef* coef;
+  int32_t shared_antenna;
+  int32_t n_templates;
+  int32_t n_cols;      // N of this launch (multiple of 64, <= 256)
+  int32_t tmem_cols;   // power of two >= n_cols + kStages * kAColsPerStage
+  int32_t nblk;        // 128-cell blocks per t0 row
+  float* map;
+  Partial* parts;
+  int64_t stride;
+  uint32_t* err;
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreads, 1)
+k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+         const Params p) {
+  constexpr int KT = BF16 ? 64 : 32;          // atoms per K-tile (128-byte operand rows)
+  constexpr int HALF = KT / 2;                // atoms per generator warp and K-tile
+  constexpr int KSTEP = BF16 ? 16 : 8;        // atoms per MMA
+  constexpr int NKS = KT / KSTEP;             // MMAs per product and K-tile
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t bar_full_b[kStages], bar_full_a[kStages], bar_empty[kStages], bar_acc;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ int32_t s_jmax;
+  __shared__ Partial s_red[4][64];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int N = p.n_cols;
+  const uint32_t op_bytes = (uint32_t)N * 128u;
+  const fmap_grid& g = p.g;
+  const int32_t nb = p.nblk - 1 - (int32_t)(blockIdx.x / g.n_t0);   // heavy tiles first
+  const int32_t m = (int32_t)(blockIdx.x % g.n_t0);
+  const int chunk = blockIdx.y;
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const int64_t tile = (int64_t)m * p.nblk + nb;
+  const int32_t i0 = p.i0tab[m];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&bar_full_b[s], 1);
+      mbar_init(&bar_full_a[s], kGenWarps);
+      mbar_init(&bar_empty[s], 1);
+    }
+    mbar_init(&bar_acc, 1);
+    s_abort = 0;
+    s_jmax = i0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp < 4) {
+    const int32_t n = nb * kRows + warp * 32 + lane;
+    const int32_t jc = n < g.n_tau ? p.jend[(int64_t)m * g.n_tau + n] : i0;
+    const int32_t jw = __reduce_max_sync(0xffffffffu, jc);
+    if (lane == 0) atomicMax(&s_jmax, jw);
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, (uint32_t)p.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int32_t jmax = s_jmax;
+  const int32_t k_begin = (i0 / KT) * KT;
+  const int n_kt = jmax > i0 ? (jmax - k_begin + KT - 1) / KT : 0;
+  const uint32_t a_col0 = (uint32_t)N;   // A stages follow the accumulator columns
+
+  if (warp == kTmaWarp) {
+    // ---------------- TMA producer of the X tiles ----------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < n_kt; ++it) {
+        const int s = it % kStages;
+        if (it >= kStages && !mbar_wait(&bar_empty[s], ((it / kStages) + 1) & 1, &s_abort)) {
+          atomicExch(&s_abort, 1);
+          break;
+        }
+        if (s_abort) break;
+        uint8_t* dst = smem + (size_t)s * 2 * op_bytes;
+        mbar_arrive_expect_tx(&bar_full_b[s], 2 * op_bytes);
+        tma_load_2d(dst, &tm_hi, &bar_full_b[s], k_begin + it * KT, chunk * N);
+        tma_load_2d(dst + op_bytes, &tm_lo, &bar_full_b[s], k_begin + it * KT, chunk * N);
+        issued = it + 1;
+      }
+      if (s_abort) {
+        // let the copies already in flight land before the block exits
+        for (int it = issued - kStages > 0 ? issued - kStages : 0; it < issued; ++it) {
+          volatile int never = 0;
+          mbar_wait(&bar_full_b[it % kStages], (it / kStages) & 1, &never);
+        }
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_of(BF16, N);
+      int done = 0;
+      for (int it = 0; it < n_kt; ++it) {
+        const int s = it % kStages;
+        const uint32_t par = (it / kStages) & 1;
+        if (!mbar_wait(&bar_full_b[s], par, &s_abort) || !mbar_wait(&bar_full_a[s], par, &s_abort)) {
+          atomicExch(&s_abort, 1);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_hi = tmem + a_col0 + (uint32_t)(s * kAColsPerStage);
+        const uint32_t a_lo = a_hi + 32u;
+        const uint32_t sb = smem_u32(smem + (size_t)s * 2 * op_bytes);
+        const uint64_t b_hi = sdesc_sw128(sb);
+        const uint64_t b_lo = sdesc_sw128(sb + op_bytes);
+#pragma unroll
+        for (int ks = 0; ks < NKS; ++ks) {
+          const uint32_t ac = (uint32_t)(ks * 8);          // 8 TMEM columns per MMA K step
+          const uint64_t bk = (uint64_t)((ks * 32) >> 4);  // 32 bytes per MMA K step
+          mma_ts<BF16>(tmem, a_hi + ac, b_hi + bk, idesc, (it | ks) != 0);
+          mma_ts<BF16>(tmem, a_hi + ac, b_lo + bk, idesc, 1u);
+          mma_ts<BF16>(tmem, a_lo + ac, b_hi + bk, idesc, 1u);
+        }
+        mma_commit(&bar_empty[s]);
+        done = it + 1;
+      }
+      if (n_kt > 0) mma_commit(&bar_acc);
+      (void)done;
+    }
+  } else {
+    // ---------------- W generators, then the epilogue ----------------
+    const int q = warp & 3, h = warp >> 2;
+    const int row = q * 32 + lane;
+    const int32_t n = nb * kRows + row;
+    const bool in_grid = n < g.n_tau;
+    const int64_t cell = (int64_t)m * g.n_tau + (in_grid ? n : 0);
+    const int32_t jc = in_grid ? p.jend[cell] : i0;
+    const double tau = (double)(g.tau_min + (int64_t)(in_grid ? n : 0) * g.dtau);
+    const float c2 = (float)(-1.4426950408889634 / tau);
+    int32_t t0rel = 0;
+    if (jmax > i0) t0rel = (int32_t)(g.t0_min + (int64_t)m * g.dt0 - *p.t_base);
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    bool ok_run = true;
+    for (int it = 0; it < n_kt; ++it) {
+      const int s = it % kStages;
+      if (it >= kStages && !mbar_wait(&bar_empty[s], ((it / kStages) + 1) & 1, &s_abort)) {
+        atomicExch(&s_abort, 1);
+        ok_run = false;
+        break;
+      }
+      const int32_t a0 = k_begin + it * KT + h * HALF;
+      int32_t rt[HALF];
+      const int4* rp = reinterpret_cast<const int4*>(p.rel_t + a0);
+#pragma unroll
+      for (int v = 0; v < HALF / 4; ++v) {
+        const int4 r4 = __ldg(rp + v);
+        rt[4 * v] = r4.x;
+        rt[4 * v + 1] = r4.y;
+        rt[4 * v + 2] = r4.z;
+        rt[4 * v + 3] = r4.w;
+      }
+      float w[HALF];
+#pragma unroll
+      for (int j = 0; j < HALF; ++j) {
+        const int32_t a = a0 + j;
+        const float e = ex2(c2 * (float)(rt[j] - t0rel));
+        w[j] = (a >= i0 && a < jc) ? e : 0.0f;
+      }
+      uint32_t vhi[16], vlo[16];
+      if constexpr (BF16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t hp = pack_bf16(w[2 * j], w[2 * j + 1]);
+          const float he = __uint_as_float(hp << 16), ho = __uint_as_float(hp & 0xffff0000u);
+          vhi[j] = hp;
+          vlo[j] = pack_bf16(w[2 * j] - he, w[2 * j + 1] - ho);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t hb = to_tf32(w[j]);
+          vhi[j] = hb;
+          vlo[j] = to_tf32(w[j] - __uint_as_float(hb));
+        }
+      }
+      const uint32_t col = a_col0 + (uint32_t)(s * kAColsPerStage + h * 16);
+      tmem_st16(tmem + lane_off + col, vhi);
+      tmem_st16(tmem + lane_off + col + 32u, vlo);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_full_a[s]);
+    }
+    // ---- epilogue: accumulator -> 2F -> map + partials ----
+    bool have_acc = n_kt > 0 && ok_run;
+    if (have_acc) {
+      volatile int* ab = &s_abort;
+      have_acc = mbar_wait(&bar_acc, 0, ab);
+      if (!have_acc) atomicExch(&s_abort, 1);
+    }
+    tc_fence_after();
+    const int tmpl_per_warp = N / 8;          // this half's templates
+    const Coef cf0 = p.coef[cell];
+    for (int g8 = 0; g8 < tmpl_per_warp; g8 += 8) {
+      float acc[32];
+      if (have_acc) {
+        tmem_ld32(tmem + lane_off + (uint32_t)(h * (N / 2) + g8 * 4), acc);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int tl = h * tmpl_per_warp + g8 + k;       // template within the chunk
+        const int32_t tq = chunk * (N / 4) + tl;
+        if (g8 + k >= tmpl_per_warp) break;
+        const bool exists = tq < p.n_templates;
+        const Coef cf = (p.shared_antenna || !exists) ? cf0 : p.coef[(int64_t)tq * cells + cell];
+        const float v = two_f(cf, acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+        const bool ok = in_grid && exists && cf.valid == 1.0f;
+        if (p.map && in_grid && exists && cf.valid != 2.0f)
+          p.map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
+        Partial pt = partial_empty();
+        partial_add(pt, v, (int32_t)cell, ok);
+        pt = partial_warp_reduce(pt);
+        if (lane == 0) s_red[q][tl] = pt;
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory");
+    const int gt = threadIdx.x;              // 0 .. 255
+    if (gt < N / 4) {
+      const int32_t tq = chunk * (N / 4) + gt;
+      if (tq < p.n_templates) {
+        Partial r = partial_merge(partial_merge(s_red[0][gt], s_red[1][gt]),
+                                  partial_merge(s_red[2][gt], s_red[3][gt]));
+        p.parts[(int64_t)tq * p.stride + tile] = r;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicOr(p.err, DEV_ERR_TIMEOUT);
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)p.tmem_cols);
+  }
+}
+
+// Split X into hi + lo operands ([4T][n_pad], zero padded): TF32 (stored as
+// FP32 bit patterns with 13 low zero bits) or BF16.
+template <bool BF16>
+__global__ void k_split_x(const float* __restrict__ fafb, int32_t n_sft, int32_t ncols,
+                          int32_t n_pad, void* __restrict__ hi, void* __restrict__ lo) {
+  const int64_t total = (int64_t)ncols * n_pad;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / n_pad;
+    const int32_t a = (int32_t)(i - c * n_pad);
+    const float x = a < n_sft ? fafb[c * n_sft + a] : 0.0f;
+    if constexpr (BF16) {
+      const uint32_t hp = pack_bf16(x, 0.0f);
+      const float hx = __uint_as_float(hp << 16);
+      const uint32_t lp = pack_bf16(x - hx, 0.0f);
+      ((uint16_t*)hi)[i] = (uint16_t)(hp & 0xffffu);
+      ((uint16_t*)lo)[i] = (uint16_t)(lp & 0xffffu);
+    } else {
+      const uint32_t hb = to_tf32(x);
+      ((uint32_t*)hi)[i] = hb;
+      ((uint32_t*)lo)[i] = to_tf32(x - __uint_as_float(hb));
+    }
+  }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- host -----
+
+static int n_pad_of(int32_t n_sft) { return ((std::max(n_sft, 1) + 63) / 64) * 64; }
+// N of the MMA: 4 columns per template, a multiple of 64 (the epilogue reads
+// the accumulator 32 columns at a time per half), at most 256.
+static int n_cols_of(int32_t T) { return std::min(256, ((4 * std::max(T, 1) + 63) / 64) * 64); }
+
+bool exp_tc_available(fmap_precision prec) { return prec == FMAP_TF32 || prec == FMAP_BF16X3; }
+
+size_t exp_tc_operand_bytes(const fmap_grid&, int32_t n_sft, int32_t n_templates,
+                            fmap_precision prec) {
+  const size_t elem = prec == FMAP_BF16X3 ? 2 : 4;
+  return 2 * elem * (size_t)4 * (size_t)std::max(n_templates, 1) * (size_t)n_pad_of(n_sft) + 256;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+static cudaError_t encode_map(CUtensorMap* map, void* base, bool bf16, int32_t n_pad,
+                              int32_t rows, int32_t box_rows) {
+  auto enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)n_pad * (bf16 ? 2 : 4)};
+  const cuuint32_t box[2] = {(cuuint32_t)(bf16 ? 64 : 32), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                           int64_t* tiles_used) {
-  *tiles_used = 0;
-  return cudaErrorNotSupported;
+  const fmap_grid& g = p->grid;
+  const int64_t tiles = exp_tiles(g);
+  *tiles_used = tiles;
+  if (tiles == 0 || p->n_templates == 0) return cudaSuccess;
+  const bool bf16 = p->precision == FMAP_BF16X3;
+  const int32_t T = p->n_templates;
+  const int32_t n_pad = n_pad_of(p->n_sft);
+  const int32_t ncols = 4 * T;
+  const int N = n_cols_of(T);
+  const size_t elem = bf16 ? 2 : 4;
+  uint8_t* hi = (uint8_t*)p->ws.xop;
+  uint8_t* lo = hi + (size_t)ncols * n_pad * elem;
+  {
+    const int64_t total = (int64_t)ncols * n_pad;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 8);
+    if (bf16)
+      tc::k_split_x<true><<<blocks, 256, 0, s>>>(a->fafb, p->n_sft, ncols, n_pad, hi, lo);
+    else
+      tc::k_split_x<false><<<blocks, 256, 0, s>>>(a->fafb, p->n_sft, ncols, n_pad, hi, lo);
+    p->launches += 1;
+  }
+  if (!p->tmaps_ready) {
+    cudaError_t e = encode_map((CUtensorMap*)p->tmap_hi, hi, bf16, n_pad, ncols, N);
+    if (e == cudaSuccess) e = encode_map((CUtensorMap*)p->tmap_lo, lo, bf16, n_pad, ncols, N);
+    if (e != cudaSuccess) return e;
+    p->tmaps_ready = true;
+  }
+  tc::Params prm;
+  prm.rel_t = p->ws.rel_t;
+  prm.t_base = p->ws.t_base;
+  prm.g = g;
+  prm.i0tab = p->ws.i0;
+  prm.jend = p->ws.jend;
+  prm.coef = p->ws.coef;
+  prm.shared_antenna = a->shared_antenna;
+  prm.n_templates = T;
+  prm.n_cols = N;
+  int tcols = 32;
+  while (tcols < N + tc::kStages * tc::kAColsPerStage) tcols *= 2;
+  prm.tmem_cols = tcols;
+  prm.nblk = (g.n_tau + tc::kRows - 1) / tc::kRows;
+  prm.map = d_2F;
+  prm.parts = p->ws.partials;
+  prm.stride = p->part_stride;
+  prm.err = p->ws.dev_err;
+  // shared memory: 3 stages x (hi + lo) x N rows x 128 B; at least enough to
+  // keep the resident CTAs within the 512 TMEM columns of an SM
+  size_t smem = (size_t)tc::kStages * 2 * N * 128 + 1024;
+  const size_t min_smem = tcols > 256 ? 120 * 1024 : 80 * 1024;
+  smem = std::max(smem, min_smem);
+  const int chunks = (ncols + N - 1) / N;
+  dim3 grid((unsigned)tiles, (unsigned)chunks);
+  const CUtensorMap* mh = (const CUtensorMap*)p->tmap_hi;
+  const CUtensorMap* ml = (const CUtensorMap*)p->tmap_lo;
+  if (bf16) {
+    cudaFuncSetAttribute(tc::k_exp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tc::k_exp_tc<true><<<grid, tc::kThreads, smem, s>>>(*mh, *ml, prm);
+  } else {
+    cudaFuncSetAttribute(tc::k_exp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    tc::k_exp_tc<false><<<grid, tc::kThreads, smem, s>>>(*mh, *ml, prm);
+  }
+  p->launches += 1;
+  return cudaGetLastError();
 }
 
 }  // namespace fmap

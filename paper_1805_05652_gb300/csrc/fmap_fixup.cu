@@ -1,0 +1,181 @@
+// Ill-conditioned cells.
+//
+// 2F depends on the component of (Fa, Fb) along the weak eigenvector of the
+// 2x2 antenna matrix; for a window of a few SFTs of one detector the matrix is
+// nearly singular (A B / D up to ~1e7), and any sum rounded to FP32 loses
+// ~eps_32 sqrt(AB/D) of relative accuracy in 2F.  The per-cell coefficient
+// step marks cells with AB/D > kCondThreshold (Coef.valid = 2); these are
+// rare (well below 1% of the cells of the workloads) and always short
+// windows in practice.  The fast kernels leave them out, and this file:
+//   1. compacts the marked cells into a list in a deterministic order
+//      (per-block counts, one exclusive scan, ordered writes);
+//   2. recomputes each listed cell for every template by the plain FP64
+//      definition over its window (Sec. 2: windowed sums, Eq. F_FaFb), writes
+//      its 2F and adds it to per-block reduction partials kept in their own
+//      slots, merged by the final reduction.
+#include <math.h>
+
+#include "fmap_device.cuh"
+
+namespace fmap {
+
+constexpr int kFlagBlock = 1024;
+constexpr int kFixThreads = 128;
+constexpr int kFixWeights = 256;
+
+// Per block of kFlagBlock entries: number of entries with valid == 2.
+__global__ void __launch_bounds__(kFlagBlock)
+k_flag_count(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt) {
+  const int64_t e = (int64_t)blockIdx.x * kFlagBlock + threadIdx.x;
+  const bool f = e < n_entries && coef[e].valid == 2.0f;
+  const int c = __syncthreads_count(f);
+  if (threadIdx.x == 0) blockcnt[blockIdx.x] = c;
+}
+
+// Exclusive scan of the block counts (one block); total into *n_flag.
+__global__ void __launch_bounds__(1024)
+k_flag_scan(int32_t* __restrict__ blockcnt, int64_t n_blocks, int32_t* __restrict__ n_flag) {
+  __shared__ int32_t warp_sum[32];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = 0; base < n_blocks; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const int32_t v = i < n_blocks ? blockcnt[i] : 0;
+    int32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int32_t w = warp_sum[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= d) w += y;
+      }
+      warp_sum[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    const int32_t excl = carry + (warp > 0 ? warp_sum[warp - 1] : 0) + x - v;
+    if (i < n_blocks) blockcnt[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_flag = carry;
+}
+
+// Ordered writes of the marked entries.
+__global__ void __launch_bounds__(kFlagBlock)
+k_flag_write(const Coef* __restrict__ coef, int64_t n_entries,
+             const int32_t* __restrict__ blockoff, int64_t* __restrict__ list) {
+  __shared__ int32_t warp_cnt[kFlagBlock / 32];
+  const int64_t e = (int64_t)blockIdx.x * kFlagBlock + threadIdx.x;
+  const bool f = e < n_entries && coef[e].valid == 2.0f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t bal = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) warp_cnt[warp] = __popc(bal);
+  __syncthreads();
+  if (f) {
+    int32_t off = blockoff[blockIdx.x];
+    for (int w = 0; w < warp; ++w) off += warp_cnt[w];
+    off += __popc(bal & ((1u << lane) - 1u));
+    list[off] = e;
+  }
+}
+
+// FP64 recomputation of listed entries.  Entry = cell (shared antenna: every
+// template) or template * cells + cell (per-template antenna: that template).
+// Block (b, y): entries [b n / G, (b + 1) n / G), templates y*128 + tid.
+__global__ void __launch_bounds__(kFixThreads)
+k_fixup(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
+        int32_t shared_antenna, const int32_t* __restrict__ rel_t,
+        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g,
+        const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+        const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
+        float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0) {
+  __shared__ double sw[kFixWeights];
+  const int64_t n = *n_flag;
+  const int64_t lo = (int64_t)blockIdx.x * n / G, hi = (int64_t)(blockIdx.x + 1) * n / G;
+  const int32_t tq = blockIdx.y * kFixThreads + threadIdx.x;
+  const bool active_t = tq < n_templates;
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  Partial acc = partial_empty();
+  for (int64_t k = lo; k < hi; ++k) {
+    const int64_t entry = list[k];
+    const int64_t cell = shared_antenna ? entry : entry % cells;
+    const int32_t only = shared_antenna ? -1 : (int32_t)(entry / cells);
+    const int32_t m = (int32_t)(cell / g.n_tau), nn = (int32_t)(cell % g.n_tau);
+    const int32_t i0 = i0tab[m], j = jend[cell];
+    const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - *t_base;
+    const double tau = (double)(g.tau_min + (int64_t)nn * g.dtau);
+    const bool mine = active_t && (only < 0 || only == tq);
+    const int32_t ta = shared_antenna ? 0 : tq;
+    const float* ant = antenna + (int64_t)ta * 3 * n_sft;
+    const float* x = fafb + (int64_t)(active_t ? tq : 0) * 4 * n_sft;
+    double A = 0, B = 0, C = 0, far = 0, fai = 0, fbr = 0, fbi = 0;
+    for (int32_t a0 = i0; a0 < j; a0 += kFixWeights) {
+      __syncthreads();
+      for (int32_t u = threadIdx.x; u < kFixWeights; u += kFixThreads) {
+        const int32_t a = a0 + u;
+        double w = 0.0;
+        if (a < j) w = (g.window == FMAP_RECT) ? 1.0 : exp(-(double)((int64_t)rel_t[a] - t0rel) / tau);
+        sw[u] = w;
+      }
+      __syncthreads();
+      if (mine) {
+        const int32_t len = min(kFixWeights, j - a0);
+        for (int32_t u = 0; u < len; ++u) {
+          const int32_t a = a0 + u;
+          const double w = sw[u], w2 = w * w;
+          A += w2 * (double)ant[a];
+          B += w2 * (double)ant[n_sft + a];
+          C += w2 * (double)ant[2 * (int64_t)n_sft + a];
+          far += w * (double)x[a];
+          fai += w * (double)x[n_sft + a];
+          fbr += w * (double)x[2 * (int64_t)n_sft + a];
+          fbi += w * (double)x[3 * (int64_t)n_sft + a];
+        }
+      }
+    }
+    if (mine) {
+      const double D = A * B - C * C;
+      const bool ok = (j - i0) >= 2 && D > 0.0;
+      double v = 0.0;
+      if (ok)
+        v = 2.0 * (B * (far * far + fai * fai) + A * (fbr * fbr + fbi * fbi) -
+                   2.0 * C * (far * fbr + fai * fbi)) / D;
+      if (map) map[(int64_t)tq * cells + cell] = (float)v;
+      partial_add(acc, (float)v, (int32_t)cell, ok);
+    }
+  }
+  if (active_t) parts[(int64_t)tq * stride + slot0 + blockIdx.x] = acc;
+}
+
+cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
+                                  cudaStream_t s) {
+  const int64_t cells = (int64_t)p->grid.n_t0 * p->grid.n_tau;
+  const int64_t n_ant = a->shared_antenna ? 1 : p->n_templates;
+  const int64_t n_entries = cells * n_ant;
+  if (n_entries == 0 || p->n_templates == 0) return cudaSuccess;
+  const int64_t n_blocks = (n_entries + kFlagBlock - 1) / kFlagBlock;
+  k_flag_count<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.coef, n_entries, p->ws.flag_blocks);
+  k_flag_scan<<<1, 1024, 0, s>>>(p->ws.flag_blocks, n_blocks, p->ws.n_flag);
+  k_flag_write<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.coef, n_entries, p->ws.flag_blocks,
+                                                         p->ws.flag_list);
+  dim3 grid((unsigned)kFixSlots, (unsigned)((p->n_templates + kFixThreads - 1) / kFixThreads));
+  k_fixup<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
+                                       a->shared_antenna, p->ws.rel_t, p->ws.t_base, p->n_sft,
+                                       p->grid, p->ws.i0, p->ws.jend, a->antenna, a->fafb,
+                                       p->n_templates, d_2F, p->ws.partials, p->part_stride,
+                                       p->n_tiles);
+  p->launches += 4;
+  return cudaGetLastError();
+}
+
+}  // namespace fmap

@@ -25,7 +25,7 @@ fmap_status cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 // Device-side error bits latched in the plan's status word.
-enum : uint32_t { DEV_ERR_ORDER = 1u, DEV_ERR_SPAN = 2u };
+enum : uint32_t { DEV_ERR_ORDER = 1u, DEV_ERR_SPAN = 2u, DEV_ERR_TIMEOUT = 4u };
 
 // ---------------------------------------------------------------------------
 // Reduction partial of one tile and one template.  sum = sum over the tile's
@@ -42,8 +42,12 @@ struct __align__(16) Partial {
 
 // Per-cell 2F coefficients.  2F = k1 |Fa|^2 + k2 |Fb - beta Fa|^2, which is
 // Eq. (F_FaFb) times two with k1 = 2/A, beta = C/A, k2 = 2A/D (completing the
-// square in Fa).  valid = 1 when the cell has >= 2 atoms and D > 0 in FP64;
-// invalid cells have k1 = k2 = 0.
+// square in Fa).  valid: 0 = invalid (fewer than 2 atoms or D <= 0 in FP64;
+// k1 = k2 = 0), 1 = evaluated by the fast kernels, 2 = ill-conditioned
+// (A B / D > kCondThreshold): left to the FP64 fix-up of fmap_fixup.cu.
+constexpr double kCondThreshold = 100.0;
+// Reduction slots per template written by the fix-up kernel.
+constexpr int kFixSlots = 512;
 struct __align__(16) Coef {
   float k1;
   float beta;
@@ -55,13 +59,16 @@ struct __align__(16) Coef {
 struct Workspace {
   void* base = nullptr;
   size_t bytes = 0;
-  int32_t* rel_t = nullptr;      // [N] t - t[0]
+  int32_t* rel_t = nullptr;      // [round_up(N, 64) + 64] t - t[0], zero padded
   int64_t* t_base = nullptr;     // [1] t[0]
   uint32_t* dev_err = nullptr;   // [1] latched device error bits
   int32_t* i0 = nullptr;         // [n_t0] first atom with t >= t0_m
   int32_t* jend = nullptr;       // [n_t0][n_tau] one past the last atom of each window
   Coef* coef = nullptr;          // [T_ant][n_t0][n_tau]
-  Partial* partials = nullptr;   // [T][n_tiles]
+  Partial* partials = nullptr;   // [T][n_tiles + kFixSlots]
+  int32_t* flag_blocks = nullptr;  // [ceil(T_ant cells / 1024)] counts, then offsets
+  int32_t* n_flag = nullptr;       // [1] number of ill-conditioned entries
+  int64_t* flag_list = nullptr;    // [T_ant cells] their indices, ascending
   // rect
   double* pa = nullptr;          // [T_ant][N+1][4] FP64 antenna prefix (a2, b2, ab, pad)
   float4* px = nullptr;          // [T][N+1][2] float-float data prefix (hi4, lo4)
@@ -88,10 +95,15 @@ struct fmap_plan_s {
   double log_prior = 0.0;
   int device = 0;
   int n_sm = 0;
-  int64_t n_tiles = 0;        // partial slots per template
+  int64_t n_tiles = 0;        // partial slots per template of the main kernels
+  int64_t part_stride = 0;    // n_tiles + kFixSlots
   int32_t tau_chunk = 0;      // exp: tau values per suffix launch
   size_t xop_bytes = 0;
   bool host_staging = false;
+  // TMA descriptors (CUtensorMap, 128 bytes each) of the split X operands
+  alignas(64) unsigned char tmap_hi[128] = {};
+  alignas(64) unsigned char tmap_lo[128] = {};
+  bool tmaps_ready = false;
   cudaStream_t last_stream = nullptr;
   fmap::Workspace ws;
   // timing (fmap_plan_enable_timing)
@@ -116,10 +128,17 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
                              int64_t* tiles_used);
 cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                           int64_t* tiles_used);
-cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, fmap_summary* d_summary,
-                                cudaStream_t s);
+cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
+cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
+                                  cudaStream_t s);
+// Reduces partial slots [0, n_tiles) and, when with_fix, the fix-up slots.
+cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, bool with_fix,
+                                fmap_summary* d_summary, cudaStream_t s);
 cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t* d_valid,
                                fmap_summary* d_summary, cudaStream_t s);
+
+// Entries of the padded relative-time array.
+inline int32_t rel_t_entries(int32_t n_sft) { return ((n_sft + 63) / 64) * 64 + 64; }
 
 // Tile counts of each kernel family (partials per template).
 int64_t rect_tiles(const fmap_grid& g);

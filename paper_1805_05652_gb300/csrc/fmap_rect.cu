@@ -149,14 +149,32 @@ k_rect_scan_antenna(const float* __restrict__ antenna, int32_t n, D4* __restrict
   }
 }
 
+// Per-cell coefficients (shared by the templates of one antenna set) from the
+// FP64 antenna prefixes: A, B, C, D = AB - C^2 in FP64.
+__global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+                            const D4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
+                            int32_t n_ant, Coef* __restrict__ coef) {
+  const int64_t cells = (int64_t)n_t0 * n_tau;
+  const int64_t total = cells * n_ant;
+  const int64_t np1 = (int64_t)n_sft + 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ta = e / cells, cell = e - ta * cells;
+    const int32_t i0 = i0tab[cell / n_tau], j = jend[cell];
+    const D4 pj = pa[ta * np1 + j], pi = pa[ta * np1 + i0];
+    coef[e] = make_coef(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z, j - i0);
+  }
+}
+
 // One thread per cell (m, n); the block covers 256 consecutive n of one row
 // and loops over the templates.  Per template: two float-pair gathers,
 // compensated differences, 2F, map store and one block partial.
+// Ill-conditioned cells (valid == 2) are left to the FP64 fix-up.
 __global__ void __launch_bounds__(kCellThreads)
 k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-             const D4* __restrict__ pa, const float4* __restrict__ px, int32_t n_sft,
+             const Coef* __restrict__ coef, const float4* __restrict__ px, int32_t n_sft,
              int32_t n_t0, int32_t n_tau, int32_t n_templates, int32_t shared_antenna,
-             float* __restrict__ map, Partial* __restrict__ parts, int64_t n_tiles) {
+             float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
   __shared__ Partial scratch[kCellThreads / 32];
   const int64_t tile = blockIdx.x;
   const int32_t nblk = (n_tau + kCellThreads - 1) / kCellThreads;
@@ -167,17 +185,10 @@ k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend
   const int64_t cell = (int64_t)m * n_tau + (in_grid ? nn : 0);
   const int32_t i0 = i0tab[m];
   const int32_t j = in_grid ? jend[cell] : i0;
-  const int32_t count = j - i0;
   const int64_t np1 = (int64_t)n_sft + 1;
-  Coef cf;
-  auto coef_of = [&](int64_t ta) {
-    const D4 pj = pa[ta * np1 + j];
-    const D4 pi = pa[ta * np1 + i0];
-    return make_coef(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z, count);
-  };
-  if (shared_antenna) cf = coef_of(0);
+  Coef cf = coef[cell];
   for (int32_t tm = 0; tm < n_templates; ++tm) {
-    if (!shared_antenna) cf = coef_of(tm);
+    if (!shared_antenna) cf = coef[(int64_t)tm * cells + cell];
     const float4* pt = px + (int64_t)tm * 2 * np1;
     const float4 hj = pt[2 * (int64_t)j], lj = pt[2 * (int64_t)j + 1];
     const float4 hi = pt[2 * (int64_t)i0], li = pt[2 * (int64_t)i0 + 1];
@@ -186,56 +197,72 @@ k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend
     const float fb_re = (hj.z - hi.z) + (lj.z - li.z);
     const float fb_im = (hj.w - hi.w) + (lj.w - li.w);
     const float v = two_f(cf, fa_re, fa_im, fb_re, fb_im);
-    const bool ok = in_grid && cf.valid != 0.0f;
-    if (map && in_grid) map[(int64_t)tm * cells + cell] = ok ? v : 0.0f;
+    const bool ok = in_grid && cf.valid == 1.0f;
+    if (map && in_grid && cf.valid != 2.0f) map[(int64_t)tm * cells + cell] = ok ? v : 0.0f;
     Partial p = partial_empty();
     partial_add(p, v, (int32_t)cell, ok);
     p = partial_block_reduce<kCellThreads / 32>(p, scratch);
-    if (threadIdx.x == 0) parts[(int64_t)tm * n_tiles + tile] = p;
+    if (threadIdx.x == 0) parts[(int64_t)tm * stride + tile] = p;
   }
 }
 
-// The paper's rectangular kernel in FP32: one thread per (template, t0 row),
-// running sums extended as tau grows; D in FP64 from the FP32 sums.
+// The paper's rectangular kernel (Sec. 3) for the data rows: one thread per
+// (template, t0 row), FP32 running sums of Fa, Fb extended as tau grows; the
+// antenna part comes from the FP64 coefficients.
 constexpr int kRowThreads = 128;
 
 __global__ void __launch_bounds__(kRowThreads)
 k_rect_rows_fp32(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-                 const float* __restrict__ antenna, const float* __restrict__ fafb,
-                 int32_t n_sft, int32_t n_t0, int32_t n_tau, int32_t shared_antenna,
-                 float* __restrict__ map, Partial* __restrict__ parts, int64_t n_tiles) {
+                 const Coef* __restrict__ coef, const float* __restrict__ fafb, int32_t n_sft,
+                 int32_t n_t0, int32_t n_tau, int32_t shared_antenna, float* __restrict__ map,
+                 Partial* __restrict__ parts, int64_t stride) {
   __shared__ Partial scratch[kRowThreads / 32];
   const int32_t m = blockIdx.x * kRowThreads + threadIdx.x;
   const int64_t tm = blockIdx.y;
   const int64_t cells = (int64_t)n_t0 * n_tau;
-  const float* ant = antenna + (shared_antenna ? 0 : tm * 3 * (int64_t)n_sft);
   const float* x = fafb + tm * 4 * (int64_t)n_sft;
+  const Coef* cp = coef + (shared_antenna ? 0 : tm * cells);
   Partial acc = partial_empty();
   if (m < n_t0) {
-    float s[7] = {0, 0, 0, 0, 0, 0, 0};
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
     int32_t a = i0tab[m];
-    const int32_t i0 = a;
     for (int32_t nn = 0; nn < n_tau; ++nn) {
       const int64_t cell = (int64_t)m * n_tau + nn;
       const int32_t j = jend[cell];
       for (; a < j; ++a) {
-        s[0] += ant[a];
-        s[1] += ant[n_sft + a];
-        s[2] += ant[2 * (int64_t)n_sft + a];
-        s[3] += x[a];
-        s[4] += x[n_sft + a];
-        s[5] += x[2 * (int64_t)n_sft + a];
-        s[6] += x[3 * (int64_t)n_sft + a];
+        s0 += x[a];
+        s1 += x[n_sft + a];
+        s2 += x[2 * (int64_t)n_sft + a];
+        s3 += x[3 * (int64_t)n_sft + a];
       }
-      const Coef cf = make_coef((double)s[0], (double)s[1], (double)s[2], j - i0);
-      const float v = two_f(cf, s[3], s[4], s[5], s[6]);
-      const bool ok = cf.valid != 0.0f;
-      if (map) map[tm * cells + cell] = ok ? v : 0.0f;
+      const Coef cf = cp[cell];
+      const float v = two_f(cf, s0, s1, s2, s3);
+      const bool ok = cf.valid == 1.0f;
+      if (map && cf.valid != 2.0f) map[tm * cells + cell] = ok ? v : 0.0f;
       partial_add(acc, v, (int32_t)cell, ok);
     }
   }
   acc = partial_block_reduce<kRowThreads / 32>(acc, scratch);
-  if (threadIdx.x == 0) parts[tm * n_tiles + blockIdx.x] = acc;
+  if (threadIdx.x == 0) parts[tm * stride + blockIdx.x] = acc;
+}
+
+cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
+  const fmap_grid& g = p->grid;
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  if (cells == 0) return cudaSuccess;
+  const int n_ant = a->shared_antenna ? 1 : p->n_templates;
+  if (n_ant == 0) return cudaSuccess;
+  if (p->n_sft > 0) {
+    k_rect_scan_antenna<<<n_ant, kScanThreads, 0, s>>>(a->antenna, p->n_sft, (D4*)p->ws.pa);
+  } else {
+    cudaMemsetAsync(p->ws.pa, 0, sizeof(D4) * n_ant, s);
+  }
+  const int64_t total = cells * n_ant;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
+  k_rect_coef<<<blocks, 256, 0, s>>>(p->ws.i0, p->ws.jend, (const D4*)p->ws.pa, p->n_sft, g.n_t0,
+                                     g.n_tau, n_ant, p->ws.coef);
+  p->launches += (p->n_sft > 0) ? 2 : 1;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
@@ -245,21 +272,19 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
   *tiles_used = 0;
   if (cells == 0 || p->n_templates == 0) return cudaSuccess;
   if (p->precision == FMAP_FP32) {
+    if (mark) cudaEventRecord(mark, s);
     dim3 grid((unsigned)((g.n_t0 + kRowThreads - 1) / kRowThreads), (unsigned)p->n_templates);
     *tiles_used = grid.x;
-    k_rect_rows_fp32<<<grid, kRowThreads, 0, s>>>(p->ws.i0, p->ws.jend, a->antenna, a->fafb,
+    k_rect_rows_fp32<<<grid, kRowThreads, 0, s>>>(p->ws.i0, p->ws.jend, p->ws.coef, a->fafb,
                                                   p->n_sft, g.n_t0, g.n_tau, a->shared_antenna,
-                                                  d_2F, p->ws.partials, p->n_tiles);
+                                                  d_2F, p->ws.partials, p->part_stride);
     p->launches += 1;
     return cudaGetLastError();
   }
-  const int n_ant = a->shared_antenna ? 1 : p->n_templates;
   if (p->n_sft > 0) {
-    k_rect_scan_antenna<<<n_ant, kScanThreads, 0, s>>>(a->antenna, p->n_sft, (D4*)p->ws.pa);
     k_rect_scan_data<<<p->n_templates, kScanThreads, 0, s>>>(a->fafb, p->n_sft, p->ws.px);
-    p->launches += 2;
+    p->launches += 1;
   } else {
-    cudaMemsetAsync(p->ws.pa, 0, sizeof(D4) * n_ant, s);
     cudaMemsetAsync(p->ws.px, 0, 2 * sizeof(float4) * p->n_templates, s);
   }
   cudaError_t e = cudaGetLastError();
@@ -268,8 +293,8 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
   const int64_t tiles = rect_tiles(g);
   *tiles_used = tiles;
   k_rect_cells<<<(unsigned)tiles, kCellThreads, 0, s>>>(
-      p->ws.i0, p->ws.jend, (const D4*)p->ws.pa, p->ws.px, p->n_sft, g.n_t0, g.n_tau,
-      p->n_templates, a->shared_antenna, d_2F, p->ws.partials, p->n_tiles);
+      p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, p->n_templates,
+      a->shared_antenna, d_2F, p->ws.partials, p->part_stride);
   p->launches += 1;
   return cudaGetLastError();
 }
