@@ -55,7 +55,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 }
 
 struct Layout {
-  size_t rel_t, t_base, dev_err, i0, jend, coef, parts, flag_blocks, n_flag, flag_list, pa, px,
+  size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
       esuf, xop, total;
   int64_t n_tiles;
   int32_t tau_chunk;
@@ -89,6 +89,8 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
   L.i0 = take(sizeof(int32_t) * std::max<int32_t>(g->n_t0, 1));
   L.jend = take(sizeof(int32_t) * std::max<int64_t>(cells, 1));
   L.parts = take(sizeof(Partial) * (size_t)std::max<int32_t>(T, 1) * (size_t)(tiles + kFixSlots));
+  L.groups = take(kGroupBytes * (size_t)std::max<int32_t>(T, 1) *
+                  (size_t)reduce_groups_of(tiles + kFixSlots));
   const size_t entries = (size_t)std::max<int64_t>(cells, 1) * (size_t)t_ant;
   L.coef = take(sizeof(Coef) * entries);
   L.flag_blocks = take(sizeof(int32_t) * ((entries + 1023) / 1024));
@@ -196,6 +198,7 @@ fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
   w.i0 = (int32_t*)(b + L.i0);
   w.jend = (int32_t*)(b + L.jend);
   w.partials = (Partial*)(b + L.parts);
+  w.groups = (void*)(b + L.groups);
   w.coef = (Coef*)(b + L.coef);
   w.flag_blocks = (int32_t*)(b + L.flag_blocks);
   w.n_flag = (int32_t*)(b + L.n_flag);

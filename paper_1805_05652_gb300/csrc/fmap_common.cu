@@ -71,26 +71,36 @@ cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Final reduction: one block per template over its tile partials, in FP64.
-// Fixed per-thread order plus a fixed tree: the result is deterministic.
+// Final reduction in two levels, FP64 throughout: level 1 merges groups of
+// kRedGroup tile partials per template (many blocks), level 2 merges the
+// groups of one template (one block).  Each level fixes the order of its
+// additions (per-thread strided loop, then a fixed tree), so the result is
+// deterministic.
 // ---------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
+constexpr int kRedGroup = 2048;
 
-__global__ void __launch_bounds__(kRedThreads)
-k_final_reduce(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
-               int64_t stride, int32_t n_tau, double log_prior, fmap_summary* __restrict__ out) {
+struct __align__(32) Partial64 {
+  double sum;      // sum of exp(F - max2F/2) over the group's valid cells
+  float max2F;
+  int32_t arg;
+  long long nvalid;
+  long long pad;
+};
+
+// Block-wide (max, count) then (sum, min arg at max) over items get(b),
+// b in [0, n).  Returns the block's merged partial in thread 0.
+template <typename Get>
+__device__ __forceinline__ Partial64 block_merge(int64_t n, Get get) {
   __shared__ float s_max[kRedThreads];
   __shared__ long long s_cnt[kRedThreads];
   __shared__ double s_sum[kRedThreads];
   __shared__ int32_t s_arg[kRedThreads];
   const int tid = threadIdx.x;
-  const Partial* pp = parts + (int64_t)blockIdx.x * stride;
   float mx = -1.0f;
   long long cnt = 0;
-  const int64_t n_all = n_tiles + n_fix;
-  auto slot = [&](int64_t b) { return b < n_tiles ? pp[b] : pp[fix0 + (b - n_tiles)]; };
-  for (int64_t b = tid; b < n_all; b += kRedThreads) {
-    const Partial q = slot(b);
+  for (int64_t b = tid; b < n; b += kRedThreads) {
+    const Partial64 q = get(b);
     if (q.nvalid > 0) {
       mx = fmaxf(mx, q.max2F);
       cnt += q.nvalid;
@@ -112,10 +122,10 @@ k_final_reduce(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0,
   double sum = 0.0;
   int32_t arg = kNoArg;
   if (N > 0) {
-    for (int64_t b = tid; b < n_all; b += kRedThreads) {
-      const Partial q = slot(b);
+    for (int64_t b = tid; b < n; b += kRedThreads) {
+      const Partial64 q = get(b);
       if (q.nvalid > 0) {
-        sum += (double)q.sum * exp(0.5 * ((double)q.max2F - (double)M));
+        sum += q.sum * exp(0.5 * ((double)q.max2F - (double)M));
         if (q.max2F == M && q.arg < arg) arg = q.arg;
       }
     }
@@ -130,34 +140,87 @@ k_final_reduce(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0,
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    fmap_summary r;
-    r.reserved = 0;
-    r.n_valid = N;
-    if (N == 0) {
-      r.max2F = 0.0f;
-      r.m = -1;
-      r.n = -1;
-      r.logB = nan("");
+  Partial64 r;
+  r.sum = s_sum[0];
+  r.max2F = M;
+  r.arg = s_arg[0];
+  r.nvalid = N;
+  r.pad = 0;
+  return r;
+}
+
+__device__ __forceinline__ Partial64 widen(const Partial& q) {
+  Partial64 r;
+  r.sum = (double)q.sum;
+  r.max2F = q.max2F;
+  r.arg = q.arg;
+  r.nvalid = q.nvalid;
+  r.pad = 0;
+  return r;
+}
+
+// Level 1: block (g, t) merges slots [g*kRedGroup, (g+1)*kRedGroup) of the
+// concatenation [main tiles 0..n_tiles) ++ [fix-up slots fix0..fix0+n_fix).
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_groups(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
+                int64_t stride, int64_t n_groups, Partial64* __restrict__ groups) {
+  const Partial* pp = parts + (int64_t)blockIdx.y * stride;
+  const int64_t n_all = n_tiles + n_fix;
+  const int64_t lo = (int64_t)blockIdx.x * kRedGroup;
+  const int64_t n = max((int64_t)0, min((int64_t)kRedGroup, n_all - lo));
+  const Partial64 r = block_merge(n, [&](int64_t b) {
+    const int64_t k = lo + b;
+    return widen(k < n_tiles ? pp[k] : pp[fix0 + (k - n_tiles)]);
+  });
+  if (threadIdx.x == 0) groups[(int64_t)blockIdx.y * n_groups + blockIdx.x] = r;
+}
+
+// Level 2: one block per template over its groups; writes the summary.
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_final(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n_tau,
+               double log_prior, fmap_summary* __restrict__ out) {
+  const Partial64* gp = groups + (int64_t)blockIdx.x * n_groups;
+  const Partial64 r = block_merge(n_groups, [&](int64_t b) { return gp[b]; });
+  if (threadIdx.x == 0) {
+    fmap_summary o;
+    o.reserved = 0;
+    o.n_valid = r.nvalid;
+    if (r.nvalid == 0) {
+      o.max2F = 0.0f;
+      o.m = -1;
+      o.n = -1;
+      o.logB = nan("");
     } else {
-      r.max2F = M;
-      r.m = s_arg[0] / n_tau;
-      r.n = s_arg[0] % n_tau;
-      r.logB = 0.5 * (double)M + log(s_sum[0]) - log((double)N) + log_prior;
+      o.max2F = r.max2F;
+      o.m = r.arg / n_tau;
+      o.n = r.arg % n_tau;
+      o.logB = 0.5 * (double)r.max2F + log(r.sum) - log((double)r.nvalid) + log_prior;
     }
-    out[blockIdx.x] = r;
+    out[blockIdx.x] = o;
   }
+}
+
+int64_t reduce_groups_of(int64_t slots) { return std::max<int64_t>(1, (slots + kRedGroup - 1) / kRedGroup); }
+
+static cudaError_t reduce_into(const Partial* parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
+                               int64_t stride, int32_t T, int32_t n_tau, double log_prior,
+                               Partial64* groups, fmap_summary* d_summary, cudaStream_t s) {
+  const int64_t n_groups = reduce_groups_of(n_tiles + n_fix);
+  k_reduce_groups<<<dim3((unsigned)n_groups, (unsigned)T), kRedThreads, 0, s>>>(
+      parts, n_tiles, fix0, n_fix, stride, n_groups, groups);
+  k_reduce_final<<<T, kRedThreads, 0, s>>>(groups, n_groups, n_tau > 0 ? n_tau : 1, log_prior,
+                                           d_summary);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, bool with_fix,
                                 fmap_summary* d_summary, cudaStream_t s) {
   if (!d_summary || p->n_templates == 0) return cudaSuccess;
   const bool fix = with_fix && (int64_t)p->grid.n_t0 * p->grid.n_tau > 0;
-  k_final_reduce<<<p->n_templates, kRedThreads, 0, s>>>(
-      p->ws.partials, n_tiles, p->n_tiles, fix ? kFixSlots : 0, p->part_stride,
-      p->grid.n_tau > 0 ? p->grid.n_tau : 1, p->log_prior, d_summary);
-  p->launches += 1;
-  return cudaGetLastError();
+  p->launches += 2;
+  return reduce_into(p->ws.partials, n_tiles, p->n_tiles, fix ? kFixSlots : 0, p->part_stride,
+                     p->n_templates, p->grid.n_tau, p->log_prior, (Partial64*)p->ws.groups,
+                     d_summary, s);
 }
 
 // ---------------------------------------------------------------------------

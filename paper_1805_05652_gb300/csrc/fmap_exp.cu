@@ -24,6 +24,23 @@ namespace fmap {
 
 constexpr int kSufThreads = 256;
 
+// r^k for small k >= 1 by binary powering (relative error ~k ulp).
+__device__ __forceinline__ double ipow(double r, int k) {
+  double acc = 1.0;
+  while (k) {
+    if (k & 1) acc *= r;
+    r *= r;
+    k >>= 1;
+  }
+  return acc;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Decayed suffix sums of the three antenna rows for one tau (block) of a
 // tau chunk; parallel backward scan of the affine maps E -> x + rho E.
 __global__ void __launch_bounds__(kSufThreads)
@@ -38,8 +55,17 @@ k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restri
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int C = (n + kSufThreads - 1) / kSufThreads;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
+  // Decay over one gap: e^{-2 gap / tau}.  Gaps that are whole multiples k of
+  // T_sft (the usual case) take the k-th power of the one-SFT decay; others
+  // use exp directly.
+  const double rho1 = exp(-(double)g.t_sft * inv_s);
+  const float inv_tsft = 1.0f / (float)g.t_sft;
   auto rho_at = [&](int i) -> double {
-    return (i + 1 < n) ? exp(-(double)(rel_t[i + 1] - rel_t[i]) * inv_s) : 0.0;
+    if (i + 1 >= n) return 0.0;
+    const int32_t gap = rel_t[i + 1] - rel_t[i];
+    const int32_t k = __float2int_rn((float)gap * inv_tsft);
+    if (k >= 1 && k <= 64 && (int64_t)k * g.t_sft == gap) return k == 1 ? rho1 : ipow(rho1, k);
+    return exp(-(double)gap * inv_s);
   };
   // phase 1: compose this thread's chunk: E[s0] = S + R E[e0]
   double R = 1.0, S0 = 0.0, S1 = 0.0, S2 = 0.0;
@@ -127,10 +153,15 @@ __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __r
     double A = 0.0, B = 0.0, C = 0.0;
     if (count > 0) {
       const double tau = (double)(g.tau_min + nn * g.dtau);
-      const double inv_s = 2.0 / tau;
       const int64_t t0rel = g.t0_min + m * g.dt0 - *t_base;
-      const double pre = exp(-(double)((int64_t)rel_t[i0] - t0rel) * inv_s);
-      const double tail = (j < n) ? exp(-(double)(rel_t[j] - rel_t[i0]) * inv_s) : 0.0;
+      // The prefactor scales A, B, C alike (F changes by its relative error
+      // only) and the tail term is ~e^{-6} of the window sum: FP32 exp2 is
+      // accurate enough for both.
+      const float c2 = (float)(-2.8853900817779268 / tau);   // -2 log2(e) / tau
+      const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
+      const double pre = d0 == 0 ? 1.0 : (double)ex2_approx(c2 * (float)d0);
+      const double tail =
+          (j < n) ? (double)ex2_approx(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0;
       const double* E = esuf + (int64_t)nl * 3 * np1;
       A = pre * (E[i0] - tail * E[j]);
       B = pre * (E[np1 + i0] - tail * E[np1 + j]);

@@ -66,6 +66,7 @@ struct Workspace {
   int32_t* jend = nullptr;       // [n_t0][n_tau] one past the last atom of each window
   Coef* coef = nullptr;          // [T_ant][n_t0][n_tau]
   Partial* partials = nullptr;   // [T][n_tiles + kFixSlots]
+  void* groups = nullptr;        // [T][reduce_groups_of(n_tiles + kFixSlots)] FP64 group merges
   int32_t* flag_blocks = nullptr;  // [ceil(T_ant cells / 1024)] counts, then offsets
   int32_t* n_flag = nullptr;       // [1] number of ill-conditioned entries
   int64_t* flag_list = nullptr;    // [T_ant cells] their indices, ascending
@@ -136,6 +137,11 @@ cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, bool with_fix,
                                 fmap_summary* d_summary, cudaStream_t s);
 cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t* d_valid,
                                fmap_summary* d_summary, cudaStream_t s);
+
+
+// First-level groups of the final reduction for `slots` partials.
+int64_t reduce_groups_of(int64_t slots);
+constexpr size_t kGroupBytes = 32;
 
 // Entries of the padded relative-time array.
 inline int32_t rel_t_entries(int32_t n_sft) { return ((n_sft + 63) / 64) * 64 + 64; }
