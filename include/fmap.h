@@ -174,6 +174,32 @@ fmap_status fmap_marginalise(fmap_plan_t* plan, const float* d_2F, const uint8_t
                              fmap_summary* d_summary, fmap_stream stream);
 
 /*
+ * fmap_marginalise_noalloc: fmap_marginalise without a plan and without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory once they are running -- a
+ * latency-bound serving loop (cudaMalloc/cudaFree may synchronise the device
+ * and take milliseconds) or a host application whose own allocator owns all
+ * device memory.  Its reduction scratch is a fixed 8 MiB array inside the
+ * library (fmap_noalloc_scratch_bytes()), held by every GPU that loads the
+ * library until the process exits.  Limit: about 16 bytes per template and
+ * 2048 cells (n_templates * ceil(n_t0 * n_tau / 2048) * 16 bytes plus a
+ * small second-level area within 8 MiB, ~500k template-tiles), else
+ * FMAP_ERR_ARG with a message.
+ * The first call on each device (with that device current) looks up the
+ * array's device address; make it before any stream capture.  All calls
+ * share the array, so calls whose work overlaps on the GPU race: serialise
+ * them.  Nothing in the array needs clearing between calls.
+ *   grid      the map's grid (window field unused); d_2F [T][n_t0][n_tau];
+ *   d_valid   nullable [T][n_t0][n_tau] uint8, NULL = every cell valid;
+ *   d_summary device [T]; asynchronous on stream.
+ */
+fmap_status fmap_marginalise_noalloc(const fmap_grid* grid, int32_t n_templates,
+                                     const float* d_2F, const uint8_t* d_valid,
+                                     double log_prior_const, fmap_summary* d_summary,
+                                     fmap_stream stream);
+size_t fmap_noalloc_scratch_bytes(void);
+
+/*
  * fmap_compute_host: one synchronous end-to-end call with HOST buffers:
  * copies the atoms to plan-owned device staging (pinned host memory makes
  * the copies asynchronous), runs the window's compute, copies the map

@@ -54,7 +54,8 @@ assert SUMMARY_DTYPE.itemsize == ctypes.sizeof(fmap_summary) == 32
 EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_set_log_prior",
            "fmap_compute_rect", "fmap_compute_exp", "fmap_marginalise", "fmap_compute_host",
            "fmap_plan_status", "fmap_count_terms", "fmap_status_string", "fmap_last_error",
-           "fmap_plan_enable_timing", "fmap_plan_read_timing")
+           "fmap_plan_enable_timing", "fmap_plan_read_timing", "fmap_marginalise_noalloc",
+           "fmap_noalloc_scratch_bytes")
 FMAP_N_PHASES = 4
 
 
@@ -90,6 +91,10 @@ def lib():
     L.fmap_count_terms.argtypes = [P(fmap_grid), c_vp, c_i32, P(c_i64), P(c_i64)]
     L.fmap_plan_enable_timing.argtypes = [c_vp, c_i32]
     L.fmap_plan_read_timing.argtypes = [c_vp, c_vp, P(c_i64), P(c_i64)]
+    L.fmap_marginalise_noalloc.argtypes = [P(fmap_grid), c_i32, c_vp, c_vp, c_f64, c_vp, c_vp]
+    L.fmap_marginalise_noalloc.restype = ctypes.c_int
+    L.fmap_noalloc_scratch_bytes.argtypes = []
+    L.fmap_noalloc_scratch_bytes.restype = c_size
     L.fmap_status_string.argtypes = [ctypes.c_int]
     L.fmap_status_string.restype = ctypes.c_char_p
     L.fmap_last_error.argtypes = []
@@ -202,6 +207,20 @@ def fmap_compute_host(plan: int, atoms: fmap_atoms, h_2F, h_summary, stream=None
 def fmap_marginalise(plan: int, d_2F, d_valid, d_summary, stream=None):
     _check(lib().fmap_marginalise(c_vp(plan), _ptr(d_2F), _ptr(d_valid), _ptr(d_summary),
                                   _stream(stream)), "fmap_marginalise")
+
+
+def fmap_marginalise_noalloc(grid, n_templates: int, d_2F, d_valid, log_prior_const: float,
+                             d_summary, stream=None):
+    """Marginalisation without a plan or any device allocation (fixed 8 MiB
+    library scratch; serialise calls that could overlap on the GPU)."""
+    g = make_grid(grid)
+    _check(lib().fmap_marginalise_noalloc(ctypes.byref(g), int(n_templates), _ptr(d_2F),
+                                          _ptr(d_valid), float(log_prior_const), _ptr(d_summary),
+                                          _stream(stream)), "fmap_marginalise_noalloc")
+
+
+def fmap_noalloc_scratch_bytes() -> int:
+    return int(lib().fmap_noalloc_scratch_bytes())
 
 
 def fmap_plan_status(plan: int) -> int:

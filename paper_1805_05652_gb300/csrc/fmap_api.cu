@@ -48,6 +48,8 @@ static bool grid_valid(const fmap_grid* g, std::string* why) {
   return true;
 }
 
+bool grid_is_valid(const fmap_grid* g, std::string* why) { return grid_valid(g, why); }
+
 static bool precision_supported(int window, fmap_precision prec) {
   if (window == FMAP_RECT) return prec == FMAP_FP64 || prec == FMAP_FP32;
   if (prec == FMAP_TF32 || prec == FMAP_BF16X3) return exp_tc_available(prec);

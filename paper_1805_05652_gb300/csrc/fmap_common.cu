@@ -256,6 +256,25 @@ k_marg_partials(const float* __restrict__ map, const uint8_t* __restrict__ valid
   if (threadIdx.x == 0) parts[tmpl * stride + tile] = acc;
 }
 
+cudaError_t launch_marginalise_into(const fmap_grid& g, int32_t n_templates, const float* d_2F,
+                                    const uint8_t* d_valid, Partial* parts, double log_prior,
+                                    fmap_summary* d_summary, cudaStream_t s) {
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const int64_t tiles = marg_tiles(g);
+  if (n_templates == 0) return cudaSuccess;
+  if (tiles > 0) {
+    dim3 grid((unsigned)tiles, (unsigned)n_templates);
+    k_marg_partials<<<grid, kMargThreads, 0, s>>>(d_2F, d_valid, cells, tiles, parts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // the group results of the first level follow the tile partials
+  Partial64* groups = (Partial64*)(parts + (int64_t)n_templates * tiles);
+  groups = (Partial64*)(((uintptr_t)groups + 31) & ~(uintptr_t)31);
+  return reduce_into(parts, tiles, 0, 0, tiles, n_templates, g.n_tau, log_prior, groups,
+                     d_summary, s);
+}
+
 cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t* d_valid,
                                fmap_summary* d_summary, cudaStream_t s) {
   const int64_t cells = (int64_t)p->grid.n_t0 * p->grid.n_tau;

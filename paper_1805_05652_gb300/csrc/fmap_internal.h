@@ -137,7 +137,12 @@ cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, bool with_fix,
                                 fmap_summary* d_summary, cudaStream_t s);
 cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t* d_valid,
                                fmap_summary* d_summary, cudaStream_t s);
-
+// Marginalisation with caller-provided partial storage: marg_tiles(g) slots
+// per template, packed ([T][marg_tiles(g)]).
+cudaError_t launch_marginalise_into(const fmap_grid& g, int32_t n_templates, const float* d_2F,
+                                    const uint8_t* d_valid, Partial* parts, double log_prior,
+                                    fmap_summary* d_summary, cudaStream_t s);
+bool grid_is_valid(const fmap_grid* g, std::string* why);
 
 // First-level groups of the final reduction for `slots` partials.
 int64_t reduce_groups_of(int64_t slots);
