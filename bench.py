@@ -183,6 +183,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--also", default="fp32",
                     help="comma list of extra precisions timed beside the headline")
+    ap.add_argument("--serving-requests", type=int, default=1000,
+                    help="requests of the serving measurement added to the line (0: skip)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -325,6 +327,12 @@ def main():
         e2e = None
         if not args.no_e2e:
             e2e = end_to_end(fm, inst, precision, terms, args)
+        serve = None
+        if world == 1 and args.serving_requests > 0:
+            try:
+                serve = serving(fm, n_requests=args.serving_requests)
+            except Exception as e:  # reported, never fatal to the headline
+                serve = {"error": repr(e)}
         srt = sorted(per)
         result = {
             "metric": "F-map (t0,tau)-SFT terms/s",
@@ -350,6 +358,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "also": extra,
+            "serving": serve,
         }
     plan.close()
     if dist:
@@ -387,6 +396,74 @@ def end_to_end(fm, inst, precision, terms, args):
     return {"value": terms / dt, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
             "api": "fmap_compute_host (pinned host buffers)"}
+
+
+def serving(fm, n_requests=1000, rate_hz=200.0, max_inflight=8, pool_size=64, seed=None):
+    """Serving workload: Poisson arrivals of F-map requests with the uneven
+    batch's size mix and 1-64 templates each, through fmap_submit/fmap_poll.
+    Latency = scheduled arrival -> the poller sees the request finished."""
+    import threading as th
+
+    kw = {} if seed is None else {"seed": seed}
+    arrivals, specs = synth.config_serving_stream(n_requests=n_requests, rate_hz=rate_hz, **kw)
+    pool = [synth.instance_from_spec(sp) for sp in specs[:pool_size]]
+    terms = [fm.fmap_count_terms(inst.grid, inst.t)[0] * inst.n_templates for inst in pool]
+
+    def run(inflight):
+        srv = fm.Server(device_mem_budget=24 << 30, pinned_bytes=2 << 30, max_inflight=inflight)
+        tickets = [None] * n_requests
+        done = [0.0] * n_requests
+        lock = th.Lock()
+        t0 = time.perf_counter() + 0.05
+
+        def submitter():
+            for i in range(n_requests):
+                dt = t0 + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                inst = pool[i % pool_size]
+                while True:
+                    try:
+                        tk = srv.submit(inst.grid, inst.t, inst.antenna, inst.fafb)
+                        break
+                    except fm.FmapError as e:
+                        if e.status != fm.FMAP_ERR_BUSY:
+                            raise
+                        time.sleep(1e-4)
+                with lock:
+                    tickets[i] = tk
+
+        sub = th.Thread(target=submitter)
+        sub.start()
+        pending = set(range(n_requests))
+        while pending:
+            progressed = False
+            for i in list(pending):
+                with lock:
+                    tk = tickets[i]
+                if tk is None:
+                    continue
+                st, _, _ = srv.poll(tk, wait_us=0)
+                if st == fm.FMAP_OK:
+                    done[i] = time.perf_counter()
+                    pending.discard(i)
+                    progressed = True
+            if not progressed:
+                time.sleep(5e-5)
+        sub.join()
+        srv.close()
+        lat = np.array([done[i] - (t0 + arrivals[i]) for i in range(n_requests)]) * 1e3
+        span = max(done) - t0
+        tot = sum(terms[i % pool_size] for i in range(n_requests))
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "throughput_terms_per_s": tot / span,
+                "requests_per_s": n_requests / span, "max_inflight": inflight}
+
+    cont = run(max_inflight)
+    serial = run(1)
+    return {"requests": n_requests, "rate_hz": rate_hz, "distinct_request_shapes": pool_size,
+            "continuous_batching": cont, "one_at_a_time": serial,
+            "precision": {"exp": "bf16x3", "rect": "fp64"}}
 
 
 def reference_arm(args, rank, world):

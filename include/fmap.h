@@ -230,6 +230,54 @@ fmap_status fmap_plan_read_timing(fmap_plan_t* plan, double* ms, int64_t* calls,
  * or CUDA error, else FMAP_OK. */
 fmap_status fmap_plan_status(fmap_plan_t* plan);
 
+/*
+ * Serving (continuous batching of F-map requests).  A server owns a device
+ * memory pool of device_mem_budget bytes and a pinned host arena of
+ * pinned_bytes, both allocated once by fmap_server_create, and a worker
+ * thread.  fmap_submit copies a request's HOST atoms into the pinned arena
+ * and queues it (the caller's buffers can be reused at once).  The worker
+ * admits queued requests in arrival order whenever one of max_inflight
+ * stream slots is free and the request's device footprint (plan workspace,
+ * atoms, outputs) fits in the pool; each admitted request runs on its own
+ * stream, so requests arriving while others are on the GPU overlap with
+ * them.  A request's results do not depend on what else is in flight.
+ * Precisions: exp_precision for exponential windows, rect_precision for
+ * rectangular ones (fmap_precision values valid for that window).
+ * The paper computes one F-map per template on demand (Sec. 3, Sec. 4.2);
+ * the server is the request loop around that operation.
+ */
+typedef struct {
+  size_t device_mem_budget;
+  size_t pinned_bytes;
+  int32_t max_inflight;        /* 1..64 */
+  fmap_precision exp_precision;
+  fmap_precision rect_precision;
+} fmap_server_config;
+
+/* fmap_submit flags */
+enum { FMAP_SUBMIT_MAP = 1u /* also return the 2F map */ };
+
+fmap_status fmap_server_create(fmap_server_t** server, const fmap_server_config* config);
+/* Stops the worker after the running requests finish; frees everything. */
+void fmap_server_destroy(fmap_server_t* server);
+/* grid: the request's grid (its window selects the path); host_atoms: HOST
+ * pointers.  Returns a ticket.  FMAP_ERR_BUSY when the pinned arena is full
+ * (poll finished requests, then resubmit); FMAP_ERR_NOMEM when the request
+ * alone exceeds the device pool; FMAP_ERR_ARG / FMAP_ERR_UNSUPPORTED as
+ * fmap_plan. */
+fmap_status fmap_submit(fmap_server_t* server, const fmap_grid* grid,
+                        const fmap_atoms* host_atoms, uint32_t flags, uint64_t* ticket);
+/* Waits up to wait_us microseconds (0: no wait, < 0: until done) for a
+ * ticket.  FMAP_PENDING: not finished.  Otherwise the request's status; on
+ * FMAP_OK copies the summaries (h_summary, [T], nullable) and, if submitted
+ * with FMAP_SUBMIT_MAP, the map (h_2F, [T][n_t0][n_tau], nullable).  A
+ * finished ticket is released by this call; FMAP_ERR_BUSY for an unknown
+ * ticket. */
+fmap_status fmap_poll(fmap_server_t* server, uint64_t ticket, fmap_summary* h_summary,
+                      float* h_2F, int64_t wait_us);
+fmap_status fmap_server_stats(fmap_server_t* server, int64_t* queued, int64_t* running,
+                              int64_t* completed);
+
 /* Host-side window bookkeeping for throughput accounting: over all cells,
  * the total number of (cell, SFT) terms (sum of atoms per window, App. A
  * Eq. Nsums-exp for exp windows) and the number of cells with >= 2 atoms.

@@ -55,8 +55,15 @@ EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_
            "fmap_compute_rect", "fmap_compute_exp", "fmap_marginalise", "fmap_compute_host",
            "fmap_plan_status", "fmap_count_terms", "fmap_status_string", "fmap_last_error",
            "fmap_plan_enable_timing", "fmap_plan_read_timing", "fmap_marginalise_noalloc",
-           "fmap_noalloc_scratch_bytes")
+           "fmap_noalloc_scratch_bytes", "fmap_server_create", "fmap_server_destroy",
+           "fmap_submit", "fmap_poll", "fmap_server_stats")
 FMAP_N_PHASES = 4
+FMAP_SUBMIT_MAP = 1
+
+
+class fmap_server_config(ctypes.Structure):
+    _fields_ = [("device_mem_budget", c_size), ("pinned_bytes", c_size), ("max_inflight", c_i32),
+                ("exp_precision", ctypes.c_int), ("rect_precision", ctypes.c_int)]
 
 
 class FmapError(RuntimeError):
@@ -95,6 +102,16 @@ def lib():
     L.fmap_marginalise_noalloc.restype = ctypes.c_int
     L.fmap_noalloc_scratch_bytes.argtypes = []
     L.fmap_noalloc_scratch_bytes.restype = c_size
+    L.fmap_server_create.argtypes = [P(c_vp), P(fmap_server_config)]
+    L.fmap_server_create.restype = ctypes.c_int
+    L.fmap_server_destroy.argtypes = [c_vp]
+    L.fmap_server_destroy.restype = None
+    L.fmap_submit.argtypes = [c_vp, P(fmap_grid), P(fmap_atoms), c_u32, P(ctypes.c_uint64)]
+    L.fmap_submit.restype = ctypes.c_int
+    L.fmap_poll.argtypes = [c_vp, ctypes.c_uint64, c_vp, c_vp, c_i64]
+    L.fmap_poll.restype = ctypes.c_int
+    L.fmap_server_stats.argtypes = [c_vp, P(c_i64), P(c_i64), P(c_i64)]
+    L.fmap_server_stats.restype = ctypes.c_int
     L.fmap_status_string.argtypes = [ctypes.c_int]
     L.fmap_status_string.restype = ctypes.c_char_p
     L.fmap_last_error.argtypes = []
@@ -247,6 +264,92 @@ def fmap_count_terms(grid, t_host: np.ndarray):
     _check(lib().fmap_count_terms(ctypes.byref(g), _ptr(t), int(t.shape[0]), ctypes.byref(a),
                                   ctypes.byref(b)), "fmap_count_terms")
     return int(a.value), int(b.value)
+
+
+def fmap_server_create(device_mem_budget: int, pinned_bytes: int, max_inflight: int,
+                       exp_precision=FMAP_BF16X3, rect_precision=FMAP_FP64) -> int:
+    if isinstance(exp_precision, str):
+        exp_precision = PRECISIONS[exp_precision]
+    if isinstance(rect_precision, str):
+        rect_precision = PRECISIONS[rect_precision]
+    cfg = fmap_server_config(int(device_mem_budget), int(pinned_bytes), int(max_inflight),
+                             int(exp_precision), int(rect_precision))
+    h = c_vp()
+    _check(lib().fmap_server_create(ctypes.byref(h), ctypes.byref(cfg)), "fmap_server_create")
+    return h.value
+
+
+def fmap_server_destroy(server: int):
+    if server:
+        lib().fmap_server_destroy(c_vp(server))
+
+
+def fmap_submit(server: int, grid, atoms: fmap_atoms, flags: int = 0) -> int:
+    g = make_grid(grid)
+    t = ctypes.c_uint64()
+    _check(lib().fmap_submit(c_vp(server), ctypes.byref(g), ctypes.byref(atoms), int(flags),
+                             ctypes.byref(t)), "fmap_submit")
+    return int(t.value)
+
+
+def fmap_poll(server: int, ticket: int, h_summary=None, h_2F=None, wait_us: int = -1) -> int:
+    """FMAP_OK (results copied) or FMAP_PENDING; raises on a failed request."""
+    st = int(lib().fmap_poll(c_vp(server), ctypes.c_uint64(ticket), _ptr(h_summary), _ptr(h_2F),
+                             int(wait_us)))
+    if st not in (FMAP_OK, FMAP_PENDING):
+        raise FmapError(st, "fmap_poll", last_error())
+    return st
+
+
+def fmap_server_stats(server: int):
+    q, r, c = c_i64(), c_i64(), c_i64()
+    _check(lib().fmap_server_stats(c_vp(server), ctypes.byref(q), ctypes.byref(r),
+                                   ctypes.byref(c)), "fmap_server_stats")
+    return int(q.value), int(r.value), int(c.value)
+
+
+class Server:
+    """Owns one fmap server; submit() takes host numpy atoms."""
+
+    def __init__(self, device_mem_budget=8 << 30, pinned_bytes=512 << 20, max_inflight=8,
+                 exp_precision="bf16x3", rect_precision="fp64"):
+        self.handle = fmap_server_create(device_mem_budget, pinned_bytes, max_inflight,
+                                         exp_precision, rect_precision)
+        self.meta = {}
+
+    def submit(self, grid, t, antenna, fafb, want_map=False) -> int:
+        t = np.ascontiguousarray(t, dtype=np.int64)
+        antenna = np.ascontiguousarray(antenna, dtype=np.float32)
+        fafb = np.ascontiguousarray(fafb, dtype=np.float32)
+        a = make_atoms(t.shape[0], fafb.shape[0], antenna.ndim == 2, t, antenna, fafb)
+        g = make_grid(grid)
+        tk = fmap_submit(self.handle, g, a, FMAP_SUBMIT_MAP if want_map else 0)
+        self.meta[tk] = (fafb.shape[0], g.n_t0, g.n_tau, want_map)
+        return tk
+
+    def poll(self, ticket: int, wait_us: int = -1):
+        """(status, summary records, map or None)."""
+        T, n_t0, n_tau, want_map = self.meta[ticket]
+        hs = np.zeros(T, dtype=SUMMARY_DTYPE)
+        hm = np.zeros((T, n_t0, n_tau), dtype=np.float32) if want_map else None
+        st = fmap_poll(self.handle, ticket, hs, hm, wait_us)
+        if st == FMAP_OK:
+            del self.meta[ticket]
+        return st, hs, hm
+
+    def stats(self):
+        return fmap_server_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fmap_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience wrapper on torch tensors ---------------------------------

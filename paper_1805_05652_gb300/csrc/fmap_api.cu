@@ -150,11 +150,13 @@ size_t fmap_workspace_bytes(const fmap_grid* grid, int32_t n_sft, int32_t n_temp
   return layout_of(grid, n_sft, n_templates, precision, 0).total;
 }
 
-fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
-                      int32_t n_templates, fmap_precision precision, uint32_t flags) {
-  set_error("");
-  if (!out) return arg_fail("plan output pointer is NULL");
-  *out = nullptr;
+}  // extern "C"
+
+namespace fmap {
+
+// Validation shared by every way of making a plan.
+static fmap_status plan_args_ok(const fmap_grid* grid, int32_t n_sft, int32_t n_templates,
+                                fmap_precision precision, uint32_t flags) {
   std::string why;
   if (!grid_valid(grid, &why)) return arg_fail(why);
   if (n_sft < 0) return arg_fail("n_sft must be >= 0");
@@ -165,8 +167,21 @@ fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
     set_error("precision not offered for this window (tensor-core forms are exp-only)");
     return FMAP_ERR_UNSUPPORTED;
   }
-  fmap_plan_s* p = new (std::nothrow) fmap_plan_s();
-  if (!p) return FMAP_ERR_NOMEM;
+  return FMAP_OK;
+}
+
+fmap_status plan_footprint(const fmap_grid* grid, int32_t n_sft, int32_t n_templates,
+                           fmap_precision precision, uint32_t flags, size_t* bytes) {
+  const fmap_status st = plan_args_ok(grid, n_sft, n_templates, precision, flags);
+  if (st != FMAP_OK) return st;
+  *bytes = layout_of(grid, n_sft, n_templates, precision, flags).total;
+  return FMAP_OK;
+}
+
+fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int32_t n_templates,
+                      fmap_precision precision, uint32_t flags, void* base, size_t bytes) {
+  fmap_status st = plan_args_ok(grid, n_sft, n_templates, precision, flags);
+  if (st != FMAP_OK) return st;
   p->grid = *grid;
   p->n_sft = n_sft;
   p->n_templates = n_templates;
@@ -174,22 +189,12 @@ fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
   p->flags = flags;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "cudaGetDevice");
-  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   const Layout L = layout_of(grid, n_sft, n_templates, precision, flags);
+  if (!base || bytes < L.total) return arg_fail("workspace smaller than the plan's footprint");
   p->n_tiles = L.n_tiles;
   p->part_stride = L.n_tiles + kFixSlots;
   p->tau_chunk = L.tau_chunk;
-  void* base = nullptr;
-  e = cudaMalloc(&base, L.total);
-  if (e != cudaSuccess) {
-    delete p;
-    cudaGetLastError();
-    set_error("workspace allocation of " + std::to_string(L.total) + " bytes failed");
-    return FMAP_ERR_NOMEM;
-  }
   char* b = (char*)base;
   Workspace& w = p->ws;
   w.base = base;
@@ -212,12 +217,39 @@ fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
     w.esuf = (double*)(b + L.esuf);
     if (L.xop) w.xop = (void*)(b + L.xop);
   }
-  e = cudaMemset(w.dev_err, 0, sizeof(uint32_t));
+  p->needs_err_reset = true;
+  return FMAP_OK;
+}
+
+}  // namespace fmap
+
+extern "C" {
+
+fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
+                      int32_t n_templates, fmap_precision precision, uint32_t flags) {
+  set_error("");
+  if (!out) return arg_fail("plan output pointer is NULL");
+  *out = nullptr;
+  size_t total = 0;
+  fmap_status st = plan_footprint(grid, n_sft, n_templates, precision, flags, &total);
+  if (st != FMAP_OK) return st;
+  fmap_plan_s* p = new (std::nothrow) fmap_plan_s();
+  if (!p) return FMAP_ERR_NOMEM;
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, total);
   if (e != cudaSuccess) {
+    delete p;
+    cudaGetLastError();
+    set_error("workspace allocation of " + std::to_string(total) + " bytes failed");
+    return FMAP_ERR_NOMEM;
+  }
+  st = plan_init(p, grid, n_sft, n_templates, precision, flags, base, total);
+  if (st != FMAP_OK) {
     cudaFree(base);
     delete p;
-    return cuda_fail(e, "cudaMemset");
+    return st;
   }
+  p->owns_ws = true;
   *out = p;
   return FMAP_OK;
 }
@@ -239,15 +271,25 @@ static void free_staging(fmap_plan_s* p) {
   w.st_sum = nullptr;
 }
 
+}  // extern "C"
+
+namespace fmap {
+void plan_release(fmap_plan_s* p) {
+  drop_events(p);
+  free_staging(p);
+}
+}  // namespace fmap
+
+extern "C" {
+
 void fmap_plan_destroy(fmap_plan_t* p) {
   if (!p) return;
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != p->device) cudaSetDevice(p->device);
   cudaDeviceSynchronize();
-  drop_events(p);
-  free_staging(p);
-  cudaFree(p->ws.base);
+  plan_release(p);
+  if (p->owns_ws) cudaFree(p->ws.base);
   if (cur != p->device) cudaSetDevice(cur);
   delete p;
 }
@@ -290,6 +332,10 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   if (st != FMAP_OK) return st;
   p->last_stream = s;
   if (!d_2F && !d_summary) return FMAP_OK;
+  if (p->needs_err_reset) {
+    FMAP_CUDA(cudaMemsetAsync(p->ws.dev_err, 0, sizeof(uint32_t), s));
+    p->needs_err_reset = false;
+  }
   cudaEvent_t ev[FMAP_N_PHASES + 1] = {};
   if (p->timing) {
     for (auto& e : ev) FMAP_CUDA(cudaEventCreate(&e));
@@ -339,6 +385,10 @@ fmap_status fmap_marginalise(fmap_plan_t* p, const float* d_2F, const uint8_t* d
   fmap_status st = check_device(p);
   if (st != FMAP_OK) return st;
   p->last_stream = (cudaStream_t)stream;
+  if (p->needs_err_reset) {
+    FMAP_CUDA(cudaMemsetAsync(p->ws.dev_err, 0, sizeof(uint32_t), (cudaStream_t)stream));
+    p->needs_err_reset = false;
+  }
   FMAP_CUDA(launch_marginalise(p, d_2F, d_valid, d_summary, (cudaStream_t)stream));
   return FMAP_OK;
 }

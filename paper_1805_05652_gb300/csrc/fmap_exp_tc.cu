@@ -37,6 +37,8 @@ constexpr int kStages = 3;
 constexpr int kRows = 128;
 constexpr int kAColsPerStage = 64;   // hi (32 columns) + lo (32 columns)
 constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr int kDtCap = 4096;          // atoms of relative times staged per refill (16 KB)
+constexpr float kFar = 1.0e30f;       // relative time of atoms outside every window
 
 // ---------------------------------------------------------------- PTX ------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -219,6 +221,7 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
   constexpr int NKS = KT / KSTEP;             // MMAs per product and K-tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* s_dt = (float*)(smem + (size_t)kStages * 2 * p.n_cols * 128);
   __shared__ uint64_t bar_full_b[kStages], bar_full_a[kStages], bar_empty[kStages], bar_acc;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
@@ -334,47 +337,68 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
     int32_t t0rel = 0;
     if (jmax > i0) t0rel = (int32_t)(g.t0_min + (int64_t)m * g.dt0 - *p.t_base);
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const int gtid = threadIdx.x;          // 0 .. 255 over the generator warps
     bool ok_run = true;
     for (int it = 0; it < n_kt; ++it) {
       const int s = it % kStages;
+      const int pos = (it * KT) % kDtCap;
+      if (pos == 0) {
+        // Stage the next kDtCap atoms' times relative to t0 (shared by all 128
+        // rows of the tile).  Atoms before the tile's t0 or past the union of
+        // its windows get kFar, whose weight ex2(c2 kFar) underflows to 0.
+        asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory");
+        for (int idx = gtid; idx < kDtCap; idx += kGenWarps * 32) {
+          const int32_t a = k_begin + it * KT + idx;
+          float v = kFar;
+          if (a >= i0 && a < jmax) v = (float)(p.rel_t[a] - t0rel);
+          s_dt[idx] = v;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory");
+      }
+      // after a timeout keep looping (without work) so that every generator
+      // warp reaches the same shared-memory barriers
+      if (!ok_run || s_abort) continue;
       if (it >= kStages && !mbar_wait(&bar_empty[s], ((it / kStages) + 1) & 1, &s_abort)) {
         atomicExch(&s_abort, 1);
         ok_run = false;
-        break;
+        continue;
       }
       const int32_t a0 = k_begin + it * KT + h * HALF;
-      int32_t rt[HALF];
-      const int4* rp = reinterpret_cast<const int4*>(p.rel_t + a0);
-#pragma unroll
-      for (int v = 0; v < HALF / 4; ++v) {
-        const int4 r4 = __ldg(rp + v);
-        rt[4 * v] = r4.x;
-        rt[4 * v + 1] = r4.y;
-        rt[4 * v + 2] = r4.z;
-        rt[4 * v + 3] = r4.w;
-      }
-      float w[HALF];
-#pragma unroll
-      for (int j = 0; j < HALF; ++j) {
-        const int32_t a = a0 + j;
-        const float e = ex2(c2 * (float)(rt[j] - t0rel));
-        w[j] = (a >= i0 && a < jc) ? e : 0.0f;
-      }
+      const int32_t cnt = jc - a0;                     // leading atoms inside this row's window
       uint32_t vhi[16], vlo[16];
-      if constexpr (BF16) {
+      if (__all_sync(0xffffffffu, cnt <= 0)) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t hp = pack_bf16(w[2 * j], w[2 * j + 1]);
-          const float he = __uint_as_float(hp << 16), ho = __uint_as_float(hp & 0xffff0000u);
-          vhi[j] = hp;
-          vlo[j] = pack_bf16(w[2 * j] - he, w[2 * j + 1] - ho);
-        }
+        for (int j = 0; j < 16; ++j) vhi[j] = vlo[j] = 0u;
       } else {
+        float w[HALF];
+        const float4* dp = reinterpret_cast<const float4*>(s_dt + pos + h * HALF);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t hb = to_tf32(w[j]);
-          vhi[j] = hb;
-          vlo[j] = to_tf32(w[j] - __uint_as_float(hb));
+        for (int v = 0; v < HALF / 4; ++v) {
+          const float4 d4 = dp[v];
+          w[4 * v] = ex2(c2 * d4.x);
+          w[4 * v + 1] = ex2(c2 * d4.y);
+          w[4 * v + 2] = ex2(c2 * d4.z);
+          w[4 * v + 3] = ex2(c2 * d4.w);
+        }
+        if (!__all_sync(0xffffffffu, cnt >= HALF)) {
+#pragma unroll
+          for (int j = 0; j < HALF; ++j) w[j] = j < cnt ? w[j] : 0.0f;
+        }
+        if constexpr (BF16) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t hp = pack_bf16(w[2 * j], w[2 * j + 1]);
+            const float he = __uint_as_float(hp << 16), ho = __uint_as_float(hp & 0xffff0000u);
+            vhi[j] = hp;
+            vlo[j] = pack_bf16(w[2 * j] - he, w[2 * j + 1] - ho);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t hb = to_tf32(w[j]);
+            vhi[j] = hb;
+            vlo[j] = to_tf32(w[j] - __uint_as_float(hb));
+          }
         }
       }
       const uint32_t col = a_col0 + (uint32_t)(s * kAColsPerStage + h * 16);
@@ -559,7 +583,7 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   prm.err = p->ws.dev_err;
   // shared memory: 3 stages x (hi + lo) x N rows x 128 B; at least enough to
   // keep the resident CTAs within the 512 TMEM columns of an SM
-  size_t smem = (size_t)tc::kStages * 2 * N * 128 + 1024;
+  size_t smem = (size_t)tc::kStages * 2 * N * 128 + sizeof(float) * tc::kDtCap + 1024;
   const size_t min_smem = tcols > 256 ? 120 * 1024 : 80 * 1024;
   smem = std::max(smem, min_smem);
   const int chunks = (ncols + N - 1) / N;

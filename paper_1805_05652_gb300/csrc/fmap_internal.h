@@ -105,6 +105,8 @@ struct fmap_plan_s {
   alignas(64) unsigned char tmap_hi[128] = {};
   alignas(64) unsigned char tmap_lo[128] = {};
   bool tmaps_ready = false;
+  bool owns_ws = false;          // workspace allocated by fmap_plan (else caller-provided)
+  bool needs_err_reset = true;   // status word not yet cleared on the device
   cudaStream_t last_stream = nullptr;
   fmap::Workspace ws;
   // timing (fmap_plan_enable_timing)
@@ -143,6 +145,14 @@ cudaError_t launch_marginalise_into(const fmap_grid& g, int32_t n_templates, con
                                     const uint8_t* d_valid, Partial* parts, double log_prior,
                                     fmap_summary* d_summary, cudaStream_t s);
 bool grid_is_valid(const fmap_grid* g, std::string* why);
+// Plans in caller-provided workspace (used by the server): the footprint,
+// initialisation without allocation, and release of what a plan holds besides
+// its workspace.
+fmap_status plan_footprint(const fmap_grid* grid, int32_t n_sft, int32_t n_templates,
+                           fmap_precision precision, uint32_t flags, size_t* bytes);
+fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int32_t n_templates,
+                      fmap_precision precision, uint32_t flags, void* base, size_t bytes);
+void plan_release(fmap_plan_s* p);
 
 // First-level groups of the final reduction for `slots` partials.
 int64_t reduce_groups_of(int64_t slots);
