@@ -181,7 +181,7 @@ def main():
     ap.add_argument("--workload", default="exp16", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--also", default="fp32",
+    ap.add_argument("--also", default="fp32,tf32,rec",
                     help="comma list of extra precisions timed beside the headline")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="requests of the serving measurement added to the line (0: skip)")
@@ -213,13 +213,18 @@ def main():
     precision = args.precision
     if precision is None:
         precision = "fp64" if window == synth.RECT else "bf16x3"
+    def make_plan(prec):
+        if prec == "rec":
+            return fm.Plan(g, inst.n_sft, inst.n_templates, "fp64", fm.FMAP_PLAN_EXP_RECURRENCE)
+        return fm.Plan(g, inst.n_sft, inst.n_templates, prec)
+
     try:
-        plan = fm.Plan(g, inst.n_sft, inst.n_templates, precision)
+        plan = make_plan(precision)
     except fm.FmapError as e:
         if e.status != fm.FMAP_ERR_UNSUPPORTED or args.precision is not None:
             raise
         precision = "fp32"
-        plan = fm.Plan(g, inst.n_sft, inst.n_templates, precision)
+        plan = make_plan(precision)
 
     stream = torch.cuda.current_stream(dev)
     t = torch.from_numpy(inst.t).to(dev)
@@ -283,7 +288,7 @@ def main():
     extra = {}
     for alt in [a for a in args.also.split(",") if a and a != precision]:
         try:
-            p2 = fm.Plan(g, inst.n_sft, inst.n_templates, alt)
+            p2 = make_plan(alt)
         except fm.FmapError:
             continue
         per2, ph2, _ = timed(p2, max(3, args.steps // 3), 3)
@@ -339,7 +344,8 @@ def main():
             "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16x3": "bf16x3"}[precision],
+            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16x3": "bf16x3",
+                      "rec": "f32x2"}[precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                        "precision": precision, "templates": T, "n_sft": inst.n_sft,
@@ -375,7 +381,10 @@ def end_to_end(fm, inst, precision, terms, args):
 
     g = inst.grid
     T = inst.n_templates
-    plan = fm.Plan(g, inst.n_sft, T, precision)
+    if precision == "rec":
+        plan = fm.Plan(g, inst.n_sft, T, "fp64", fm.FMAP_PLAN_EXP_RECURRENCE)
+    else:
+        plan = fm.Plan(g, inst.n_sft, T, precision)
     h_t = torch.from_numpy(inst.t).pin_memory()
     h_a = torch.from_numpy(inst.antenna).pin_memory()
     h_x = torch.from_numpy(inst.fafb).pin_memory()

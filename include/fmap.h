@@ -122,7 +122,15 @@ typedef struct {
 enum {
   /* atoms carry antenna rows per template ([T][3][n_sft]); workspace for the
    * per-template 2F coefficients grows by a factor T */
-  FMAP_PLAN_PER_TEMPLATE_ANTENNA = 1u
+  FMAP_PLAN_PER_TEMPLATE_ANTENNA = 1u,
+  /* exponential windows only, with FMAP_FP64: the data sums by the decayed
+   * suffix recurrence E[i] = x_i + e^{-(t_{i+1} - t_i)/tau} E[i+1] (an exact
+   * rearrangement of Eq. winexp's window sums: window [i0, j) =
+   * e^{-(t_i0 - t0)/tau} (E[i0] - e^{-(t_j - t_i0)/tau} E[j])), one scan per
+   * (tau, data column) in compensated FP32 instead of a sum per cell:
+   * O(N_tau N_SFT + cells) per template.  Needs n_sft <= 12000
+   * (FMAP_ERR_UNSUPPORTED otherwise). */
+  FMAP_PLAN_EXP_RECURRENCE = 2u
 };
 
 typedef struct fmap_plan_s fmap_plan_t;
@@ -132,7 +140,7 @@ typedef struct fmap_server_s fmap_server_t;
  * fmap_plan: create a plan for one grid, SFT count and template count
  * (the F-map problem statement of Sec. 3: atoms + window + grid).  The plan
  * allocates its workspace (fmap_workspace_bytes) on the current device.
- * flags: 0 or FMAP_PLAN_PER_TEMPLATE_ANTENNA.  Returns FMAP_ERR_ARG on an invalid grid or size,
+ * flags: FMAP_PLAN_* bits.  Returns FMAP_ERR_ARG on an invalid grid or size,
  * FMAP_ERR_UNSUPPORTED for a precision the window does not offer,
  * FMAP_ERR_NOMEM when the workspace cannot be allocated.
  */

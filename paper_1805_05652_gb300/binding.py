@@ -28,6 +28,7 @@ FMAP_ERR_BUSY, FMAP_ERR_DATA, FMAP_ERR_UNSUPPORTED = -5, -6, -7
 FMAP_RECT, FMAP_EXP = 0, 1
 FMAP_FP64, FMAP_FP32, FMAP_TF32, FMAP_BF16X3 = 0, 1, 2, 3
 FMAP_PLAN_PER_TEMPLATE_ANTENNA = 1
+FMAP_PLAN_EXP_RECURRENCE = 2
 
 PRECISIONS = {"fp64": FMAP_FP64, "fp32": FMAP_FP32, "tf32": FMAP_TF32, "bf16x3": FMAP_BF16X3}
 

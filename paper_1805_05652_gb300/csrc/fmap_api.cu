@@ -77,6 +77,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     tiles = std::max<int64_t>(tiles, (g->n_t0 + 127) / 128);
   } else {
     tiles = std::max<int64_t>(tiles, exp_tiles(*g));
+    if (flags & FMAP_PLAN_EXP_RECURRENCE) tiles = std::max<int64_t>(tiles, g->n_tau);
   }
   L.n_tiles = tiles;
   size_t off = 0;
@@ -162,7 +163,17 @@ static fmap_status plan_args_ok(const fmap_grid* grid, int32_t n_sft, int32_t n_
   if (n_sft < 0) return arg_fail("n_sft must be >= 0");
   if (n_templates < 0 || n_templates > 65535) return arg_fail("n_templates must be in [0, 65535]");
   if (precision < FMAP_FP64 || precision > FMAP_BF16X3) return arg_fail("unknown precision");
-  if (flags & ~(uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA) return arg_fail("unknown plan flags");
+  if (flags & ~(uint32_t)(FMAP_PLAN_PER_TEMPLATE_ANTENNA | FMAP_PLAN_EXP_RECURRENCE))
+    return arg_fail("unknown plan flags");
+  if (flags & FMAP_PLAN_EXP_RECURRENCE) {
+    if (grid->window != FMAP_EXP) return arg_fail("FMAP_PLAN_EXP_RECURRENCE is for exponential windows");
+    if (precision != FMAP_FP64)
+      return arg_fail("FMAP_PLAN_EXP_RECURRENCE computes in compensated FP32 (FMAP_FP64 class)");
+    if (!exp_rec_supported(n_sft)) {
+      set_error("FMAP_PLAN_EXP_RECURRENCE keeps a template's suffix sums in shared memory: n_sft too large");
+      return FMAP_ERR_UNSUPPORTED;
+    }
+  }
   if (!precision_supported(grid->window, precision)) {
     set_error("precision not offered for this window (tensor-core forms are exp-only)");
     return FMAP_ERR_UNSUPPORTED;
@@ -352,7 +363,9 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   } else {
     FMAP_CUDA(launch_exp_coef(p, a, s));
     if (ev[2]) FMAP_CUDA(cudaEventRecord(ev[2], s));
-    if (p->precision == FMAP_TF32 || p->precision == FMAP_BF16X3) {
+    if (p->flags & FMAP_PLAN_EXP_RECURRENCE) {
+      FMAP_CUDA(launch_exp_rec(p, a, d_2F, s, &tiles));
+    } else if (p->precision == FMAP_TF32 || p->precision == FMAP_BF16X3) {
       FMAP_CUDA(launch_exp_tc(p, a, d_2F, s, &tiles));
     } else {
       FMAP_CUDA(launch_exp_plain(p, a, d_2F, s, &tiles));

@@ -1,0 +1,218 @@
+// Exponential window by the decayed suffix recurrence (plan flag
+// FMAP_PLAN_EXP_RECURRENCE).
+//
+// The exponential weight factorises in t0: for the atoms [i0, j) of a window,
+//   sum_a e^{-(t_a - t0)/tau} x_a = e^{-(t_{i0} - t0)/tau} (E[i0] - e^{-(t_j - t_{i0})/tau} E[j]),
+//   E[i] = x_i + e^{-(t_{i+1} - t_i)/tau} E[i+1],  E[N] = 0,
+// an exact rearrangement of the window sums of Eq. (winexp).  One recurrence
+// per (tau, data column) replaces the per-cell sums: O(N_tau N_SFT) work per
+// column instead of O(sum of window lengths).  The recurrence runs as a
+// parallel backward scan of the affine maps E -> x + rho E in compensated
+// FP32 (float pairs, ~2^-44 relative), and E is rounded to FP32 only for the
+// per-cell differences, which then carry the same ~1e-7 relative error as the
+// rectangular window's prefix differences.
+//
+// One block per (tau_n, template): the suffix sums of the template's 4 data
+// columns live in shared memory; the block then evaluates the column of cells
+// (t0_m, tau_n) for every m.  Blocks run tau-fastest, so the blocks writing
+// neighbouring tau of the same map rows run together and their stores merge
+// in L2.
+#include <math.h>
+
+#include "fmap_device.cuh"
+
+namespace fmap {
+
+constexpr int kRecThreads = 256;
+constexpr int kRecMaxSft = 12000;
+
+struct FF {
+  float h, l;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.h, -p);
+  return fast_two_sum(p, e + fmaf(a.h, b.l, a.l * b.h));
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const FF s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, s.l + a.l + b.l);
+}
+// x + r e
+__device__ __forceinline__ FF ff_axpy(FF r, FF e, float x) {
+  const float p = r.h * e.h;
+  const float pe = fmaf(r.h, e.h, -p);
+  const FF s = two_sum(x, p);
+  return fast_two_sum(s.h, s.l + pe + fmaf(r.h, e.l, r.l * e.h));
+}
+__device__ __forceinline__ FF ff_shfl_down(FF v, int d) {
+  return {__shfl_down_sync(0xffffffffu, v.h, d), __shfl_down_sync(0xffffffffu, v.l, d)};
+}
+
+__device__ __forceinline__ double rec_ipow(double r, int k) {
+  double acc = 1.0;
+  while (k) {
+    if (k & 1) acc *= r;
+    r *= r;
+    k >>= 1;
+  }
+  return acc;
+}
+
+__device__ __forceinline__ float rec_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__global__ void __launch_bounds__(kRecThreads)
+k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
+          fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+          const Coef* __restrict__ coef, int32_t shared_antenna, const float* __restrict__ fafb,
+          int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
+          int64_t stride) {
+  extern __shared__ float s_e[];  // [4][n + 1]
+  __shared__ float sR[2][kRecThreads / 32];
+  __shared__ float sS[4][2][kRecThreads / 32];
+  __shared__ Partial scratch[kRecThreads / 32];
+  const int ni = blockIdx.x;
+  const int tq = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
+  const double inv_tau = 1.0 / tau;
+  const double rho1 = exp(-(double)g.t_sft * inv_tau);
+  const float inv_tsft = 1.0f / (float)g.t_sft;
+  const float* x = fafb + (int64_t)tq * 4 * n;
+  const int64_t np1 = (int64_t)n + 1;
+  // decay over the gap after atom i, as a float pair
+  auto rho_at = [&](int i) -> FF {
+    if (i + 1 >= n) return {0.0f, 0.0f};
+    const int32_t gap = rel_t[i + 1] - rel_t[i];
+    const int32_t k = __float2int_rn((float)gap * inv_tsft);
+    double r;
+    if (k >= 1 && k <= 64 && (int64_t)k * g.t_sft == gap)
+      r = k == 1 ? rho1 : rec_ipow(rho1, k);
+    else
+      r = exp(-(double)gap * inv_tau);
+    const float h = (float)r;
+    return {h, (float)(r - (double)h)};
+  };
+  const int C = (n + kRecThreads - 1) / kRecThreads;
+  const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
+  // phase 1: this thread's chunk as one affine map, E[s0] = S + R E[e0]
+  FF R = {1.0f, 0.0f}, S[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (int i = e0 - 1; i >= s0; --i) {
+    const FF r = rho_at(i);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) S[c] = ff_axpy(r, S[c], x[(int64_t)c * n + i]);
+    R = ff_mul(r, R);
+  }
+  // phase 2: suffix composition within the warp (self o later)
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const FF Ro = ff_shfl_down(R, d);
+    FF So[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) So[c] = ff_shfl_down(S[c], d);
+    if (lane + d < 32) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) S[c] = ff_add(S[c], ff_mul(R, So[c]));
+      R = ff_mul(R, Ro);
+    }
+  }
+  FF hR = ff_shfl_down(R, 1), hS[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) hS[c] = ff_shfl_down(S[c], 1);
+  if (lane == 31) {
+    hR = {1.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) hS[c] = {0.0f, 0.0f};
+  }
+  if (lane == 0) {
+    sR[0][warp] = R.h;
+    sR[1][warp] = R.l;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      sS[c][0][warp] = S[c].h;
+      sS[c][1][warp] = S[c].l;
+    }
+  }
+  __syncthreads();
+  // later warps applied to E[N] = 0
+  FF lS[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (int v = kRecThreads / 32 - 1; v > warp; --v) {
+    const FF Rv = {sR[0][v], sR[1][v]};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) lS[c] = ff_add({sS[c][0][v], sS[c][1][v]}, ff_mul(Rv, lS[c]));
+  }
+  FF e[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) e[c] = ff_add(hS[c], ff_mul(hR, lS[c]));
+  // phase 3: recompute the chunk from its carry and keep E (rounded) in smem
+  for (int i = e0 - 1; i >= s0; --i) {
+    const FF r = rho_at(i);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      e[c] = ff_axpy(r, e[c], x[(int64_t)c * n + i]);
+      s_e[c * np1 + i] = e[c].h + e[c].l;
+    }
+  }
+  if (tid < 4) s_e[tid * np1 + n] = 0.0f;
+  __syncthreads();
+  // cells (t0_m, tau_n), all m
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const float c2 = (float)(-1.4426950408889634 * inv_tau);
+  const int64_t tb = *t_base;
+  Partial acc = partial_empty();
+  for (int32_t m = tid; m < g.n_t0; m += kRecThreads) {
+    const int64_t cell = (int64_t)m * g.n_tau + ni;
+    const int32_t i0 = i0tab[m], j = jend[cell];
+    const Coef cf = shared_antenna ? coef[cell] : coef[(int64_t)tq * cells + cell];
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    if (j > i0) {
+      const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
+      const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
+      const float pre = d0 == 0 ? 1.0f : rec_ex2(c2 * (float)d0);
+      const float tail = j < n ? rec_ex2(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) f[c] = pre * fmaf(-tail, s_e[c * np1 + j], s_e[c * np1 + i0]);
+    }
+    const float v = two_f(cf, f[0], f[1], f[2], f[3]);
+    const bool ok = cf.valid == 1.0f;
+    if (map && cf.valid != 2.0f) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
+    partial_add(acc, v, (int32_t)cell, ok);
+  }
+  acc = partial_block_reduce<kRecThreads / 32>(acc, scratch);
+  if (tid == 0) parts[(int64_t)tq * stride + ni] = acc;
+}
+
+bool exp_rec_supported(int32_t n_sft) { return n_sft <= kRecMaxSft; }
+
+cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
+                           int64_t* tiles_used) {
+  const fmap_grid& g = p->grid;
+  *tiles_used = 0;
+  if ((int64_t)g.n_t0 * g.n_tau == 0 || p->n_templates == 0) return cudaSuccess;
+  *tiles_used = g.n_tau;
+  const size_t smem = sizeof(float) * 4 * ((size_t)p->n_sft + 1);
+  cudaFuncSetAttribute(k_exp_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)g.n_tau, (unsigned)p->n_templates);
+  k_exp_rec<<<grid, kRecThreads, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0,
+                                            p->ws.jend, p->ws.coef, a->shared_antenna, a->fafb,
+                                            p->n_templates, d_2F, p->ws.partials,
+                                            p->part_stride);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace fmap

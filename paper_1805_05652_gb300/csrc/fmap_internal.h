@@ -131,6 +131,9 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
                              int64_t* tiles_used);
 cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                           int64_t* tiles_used);
+cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
+                           int64_t* tiles_used);
+bool exp_rec_supported(int32_t n_sft);
 cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
                                   cudaStream_t s);

@@ -7,7 +7,9 @@ import oracle
 
 # Relative 2F tolerance, |d2F| / max(|2F_oracle|, 1): 1e-5 for the FP64-assisted
 # path, 1e-3 for the FP32 sums and the tensor-core forms.
-TOL = {"fp64": 1e-5, "fp32": 1e-3, "tf32": 1e-3, "bf16x3": 1e-3}
+TOL = {"fp64": 1e-5, "rec": 1e-5, "fp32": 1e-3, "tf32": 1e-3, "bf16x3": 1e-3}
+# precision forms held to the FP64 bar (strict logB tolerance)
+FP64_CLASS = ("fp64", "rec")
 LOGB_TOL = 1e-4
 
 
@@ -21,6 +23,8 @@ def run_gpu(inst, precision, want_map=True, plan_flags=0, stream=None):
     ant = torch.from_numpy(np.ascontiguousarray(inst.antenna, dtype=np.float32)).to(dev)
     x = torch.from_numpy(np.ascontiguousarray(inst.fafb, dtype=np.float32)).to(dev)
     flags = plan_flags | (0 if inst.shared_antenna else fm.FMAP_PLAN_PER_TEMPLATE_ANTENNA)
+    if precision == "rec":          # decayed-suffix recurrence for exponential windows
+        precision, flags = "fp64", flags | fm.FMAP_PLAN_EXP_RECURRENCE
     plan = fm.Plan(inst.grid, inst.n_sft, inst.n_templates, precision, flags)
     m, s = plan.compute(t, ant, x, want_map=want_map, stream=stream)
     torch.cuda.synchronize()

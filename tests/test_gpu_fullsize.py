@@ -16,7 +16,8 @@ import pytest
 import oracle
 import synth
 from synth import EXP, RECT
-from tests.parity_util import LOGB_TOL, TOL, check_map, check_summary, rel_err, run_gpu
+from tests.parity_util import (FP64_CLASS, LOGB_TOL, TOL, check_map, check_summary, rel_err,
+                               run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +36,7 @@ def exp16():
     return inst, ref, valid
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3", "fp64", "rec"])
 def test_exp16_full_map(exp16, prec):
     inst, ref, valid = exp16
     try:
@@ -45,7 +46,7 @@ def test_exp16_full_map(exp16, prec):
             pytest.skip(f"{prec} not built")
         raise
     worst = check_map(got, ref, valid, TOL[prec])
-    fe = 0.0 if prec == "fp64" else 0.5 * float(np.abs(got - ref)[valid].max())
+    fe = 0.0 if prec in FP64_CLASS else 0.5 * float(np.abs(got - ref)[valid].max())
     check_summary(gs, ref, valid, TOL[prec], LOGB_TOL, fe)
     inj = inst.injections[0]
     # the injected template peaks near its true (t0, tau)
@@ -88,15 +89,18 @@ def batch_exp():
     return synth.config_batched(window=EXP)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3", "rec"])
 def test_batched_exp_sampled_cells(batch_exp, prec):
     inst = batch_exp
     dev = torch.device("cuda:0")
     t = torch.from_numpy(inst.t).to(dev)
     a = torch.from_numpy(inst.antenna).to(dev)
     x = torch.from_numpy(inst.fafb).to(dev)
+    flags = 0
+    if prec == "rec":
+        prec, flags = "fp64", fm.FMAP_PLAN_EXP_RECURRENCE
     try:
-        plan = fm.Plan(inst.grid, inst.n_sft, inst.n_templates, prec)
+        plan = fm.Plan(inst.grid, inst.n_sft, inst.n_templates, prec, flags)
     except fm.FmapError as e:
         if e.status == fm.FMAP_ERR_UNSUPPORTED:
             pytest.skip(f"{prec} not built")
@@ -120,7 +124,7 @@ def test_batched_exp_sampled_cells(batch_exp, prec):
     ref0, valid0, _ = oracle.fmap(sub.t, sub.antenna, sub.fafb, g.as_tuple(), mode="fast")
     got0 = m[0:1].cpu().numpy().astype(np.float64)
     check_map(got0, ref0, valid0, TOL[prec])
-    fe = 0.5 * float(np.abs(got0 - ref0)[valid0].max())
+    fe = 0.0 if flags else 0.5 * float(np.abs(got0 - ref0)[valid0].max())
     check_summary(gs[:1], ref0, valid0, TOL[prec], LOGB_TOL, fe)
     del m
     plan.close()

@@ -8,7 +8,8 @@ import pytest
 import oracle
 import synth
 from synth import EXP, RECT, T_SFT, Grid
-from tests.parity_util import LOGB_TOL, TOL, check_map, check_summary, oracle_map, rel_err, run_gpu
+from tests.parity_util import (FP64_CLASS, LOGB_TOL, TOL, check_map, check_summary, oracle_map,
+                               rel_err, run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +34,7 @@ def _parity(inst, prec, mode="fast"):
     ref, valid, _ = oracle_map(inst, mode)
     got, gs = run_gpu(inst, prec)
     worst = check_map(got, ref, valid, TOL[prec])
-    fe = 0.0 if prec == "fp64" else _f_err(got, ref, valid)
+    fe = 0.0 if prec in FP64_CLASS else _f_err(got, ref, valid)
     check_summary(gs, ref, valid, TOL[prec], LOGB_TOL, fe)
     return worst
 
@@ -60,7 +61,7 @@ def test_rect_ragged_tiles_offgrid_per_template_antenna(prec):
 
 # ----------------------------------------------------------------- exp --------
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3", "rec"])
 def test_exp_ragged(prec):
     """Exp windows: 11 templates (ragged template chunks), n_tau = 300 (two
     128-cell tiles and a tail), off-grid t0 and tau steps, 2 detectors."""
@@ -75,7 +76,7 @@ def test_exp_ragged(prec):
         raise
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "rec"])
 def test_exp_per_template_antenna(prec):
     grid = Grid(0, T_SFT, 20, T_SFT, T_SFT, 140, EXP)
     inst = synth.make_instance(44, n_det=1, presence=0.9, n_merged=200, n_templates=3,
@@ -187,6 +188,16 @@ def test_nonincreasing_timestamps_reported():
     assert plan.status() == fm.FMAP_ERR_DATA
     assert plan.status() == fm.FMAP_OK            # latched error was cleared
     plan.close()
+
+
+def test_recurrence_flag_validation():
+    grid = Grid(0, T_SFT, 5, T_SFT, T_SFT, 5, EXP)
+    for args, status in (((grid.with_window(RECT), 10, 1, "fp64"), fm.FMAP_ERR_ARG),
+                         ((grid, 10, 1, "bf16x3"), fm.FMAP_ERR_ARG),
+                         ((grid, 20000, 1, "fp64"), fm.FMAP_ERR_UNSUPPORTED)):
+        with pytest.raises(fm.FmapError) as e:
+            fm.fmap_plan(*args, flags=fm.FMAP_PLAN_EXP_RECURRENCE)
+        assert e.value.status == status
 
 
 def test_mismatched_calls_rejected():
