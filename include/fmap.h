@@ -128,8 +128,9 @@ enum {
    * rearrangement of Eq. winexp's window sums: window [i0, j) =
    * e^{-(t_i0 - t0)/tau} (E[i0] - e^{-(t_j - t_i0)/tau} E[j])), one scan per
    * (tau, data column) in compensated FP32 instead of a sum per cell:
-   * O(N_tau N_SFT + cells) per template.  Needs n_sft <= 12000
-   * (FMAP_ERR_UNSUPPORTED otherwise). */
+   * O(N_tau N_SFT + cells) per template.  Needs n_sft <= 9000 and
+   * 24 n_sft + 32 n_t0 <= ~220 KB of shared memory (FMAP_ERR_UNSUPPORTED
+   * otherwise). */
   FMAP_PLAN_EXP_RECURRENCE = 2u
 };
 
@@ -285,6 +286,45 @@ fmap_status fmap_poll(fmap_server_t* server, uint64_t ticket, fmap_summary* h_su
                       float* h_2F, int64_t wait_us);
 fmap_status fmap_server_stats(fmap_server_t* server, int64_t* queued, int64_t* running,
                               int64_t* completed);
+
+/*
+ * Uneven batches: many independent F-map instances (each with its own atoms,
+ * grid, window and template count; Sec. 3's per-template F-map, batched) run
+ * by one captured CUDA graph.  Rectangular instances use the FP64 prefix
+ * path, exponential ones the decayed-suffix recurrence (FMAP_FP64 accuracy
+ * class, n_sft <= 9000).  Each phase of the pipeline is one persistent launch
+ * over the work units of all instances (atomic work counter, heaviest
+ * instances first); instances are grouped in waves whose workspace fits
+ * workspace_budget (0: 8 GiB).  FMAP_BATCH_AUTOTUNE times the candidate
+ * occupancies of each phase and the templates per block of the recurrence on
+ * the batch itself (cached per batch shape) before the graph is captured.
+ * The items' device pointers are baked into the graph: keep them valid, and
+ * rerun fmap_batch_run after changing the atoms' values in place.
+ */
+typedef struct {
+  fmap_grid grid;
+  fmap_atoms atoms;          /* device pointers */
+  float* d_2F;               /* nullable [T][n_t0][n_tau] */
+  fmap_summary* d_summary;   /* nullable [T] */
+} fmap_batch_item;
+
+enum { FMAP_BATCH_AUTOTUNE = 1u };
+
+typedef struct fmap_batch_s fmap_batch_t;
+
+fmap_status fmap_batch_plan(fmap_batch_t** batch, const fmap_batch_item* items, int32_t n_items,
+                            size_t workspace_budget, uint32_t flags);
+/* Launches the batch's graph on stream (asynchronous). */
+fmap_status fmap_batch_run(fmap_batch_t* batch, fmap_stream stream);
+/* Waits for stream; returns (then clears) a latched data error or timeout of
+ * any instance. */
+fmap_status fmap_batch_status(fmap_batch_t* batch, fmap_stream stream);
+/* Waves, kernel launches per run, workspace bytes, chosen occupancy per phase
+ * (14 entries, nullable) and templates per block of the recurrence. */
+fmap_status fmap_batch_info(fmap_batch_t* batch, int32_t* n_waves, int64_t* launches_per_run,
+                            size_t* workspace_bytes, int32_t* occupancy,
+                            int32_t* rec_templates_per_block);
+void fmap_batch_destroy(fmap_batch_t* batch);
 
 /* Host-side window bookkeeping for throughput accounting: over all cells,
  * the total number of (cell, SFT) terms (sum of atoms per window, App. A

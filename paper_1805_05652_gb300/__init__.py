@@ -6,5 +6,5 @@ The Python layer is a thin ctypes binding (``binding``) with the C names;
 """
 
 from .binding import *  # noqa: F401,F403
-from .binding import Plan, Server, FmapError, SUMMARY_DTYPE, summary_to_numpy, lib  # noqa: F401
+from .binding import Plan, Server, Batch, FmapError, SUMMARY_DTYPE, summary_to_numpy, lib  # noqa: F401
 from .build import build, lib_path  # noqa: F401

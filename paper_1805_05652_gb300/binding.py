@@ -48,6 +48,10 @@ class fmap_summary(ctypes.Structure):
                 ("logB", c_f64), ("n_valid", c_i64)]
 
 
+class fmap_batch_item(ctypes.Structure):
+    _fields_ = [("grid", fmap_grid), ("atoms", fmap_atoms), ("d_2F", c_vp), ("d_summary", c_vp)]
+
+
 SUMMARY_DTYPE = np.dtype([("max2F", "<f4"), ("m", "<i4"), ("n", "<i4"), ("reserved", "<i4"),
                           ("logB", "<f8"), ("n_valid", "<i8")])
 assert SUMMARY_DTYPE.itemsize == ctypes.sizeof(fmap_summary) == 32
@@ -57,7 +61,10 @@ EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_
            "fmap_plan_status", "fmap_count_terms", "fmap_status_string", "fmap_last_error",
            "fmap_plan_enable_timing", "fmap_plan_read_timing", "fmap_marginalise_noalloc",
            "fmap_noalloc_scratch_bytes", "fmap_server_create", "fmap_server_destroy",
-           "fmap_submit", "fmap_poll", "fmap_server_stats")
+           "fmap_submit", "fmap_poll", "fmap_server_stats", "fmap_batch_plan", "fmap_batch_run",
+           "fmap_batch_status", "fmap_batch_info", "fmap_batch_destroy")
+FMAP_BATCH_AUTOTUNE = 1
+N_BATCH_PHASES = 14
 FMAP_N_PHASES = 4
 FMAP_SUBMIT_MAP = 1
 
@@ -113,6 +120,14 @@ def lib():
     L.fmap_poll.restype = ctypes.c_int
     L.fmap_server_stats.argtypes = [c_vp, P(c_i64), P(c_i64), P(c_i64)]
     L.fmap_server_stats.restype = ctypes.c_int
+    L.fmap_batch_plan.argtypes = [P(c_vp), c_vp, c_i32, c_size, c_u32]
+    L.fmap_batch_run.argtypes = [c_vp, c_vp]
+    L.fmap_batch_status.argtypes = [c_vp, c_vp]
+    L.fmap_batch_info.argtypes = [c_vp, P(c_i32), P(c_i64), P(c_size), c_vp, P(c_i32)]
+    for f in ("fmap_batch_plan", "fmap_batch_run", "fmap_batch_status", "fmap_batch_info"):
+        getattr(L, f).restype = ctypes.c_int
+    L.fmap_batch_destroy.argtypes = [c_vp]
+    L.fmap_batch_destroy.restype = None
     L.fmap_status_string.argtypes = [ctypes.c_int]
     L.fmap_status_string.restype = ctypes.c_char_p
     L.fmap_last_error.argtypes = []
@@ -307,6 +322,81 @@ def fmap_server_stats(server: int):
     _check(lib().fmap_server_stats(c_vp(server), ctypes.byref(q), ctypes.byref(r),
                                    ctypes.byref(c)), "fmap_server_stats")
     return int(q.value), int(r.value), int(c.value)
+
+
+def fmap_batch_plan(items, workspace_budget: int = 0, flags: int = 0) -> int:
+    """items: sequence of fmap_batch_item (device pointers)."""
+    arr = (fmap_batch_item * len(items))(*items)
+    h = c_vp()
+    _check(lib().fmap_batch_plan(ctypes.byref(h), ctypes.cast(arr, c_vp), len(items),
+                                 int(workspace_budget), int(flags)), "fmap_batch_plan")
+    return h.value
+
+
+def fmap_batch_run(batch: int, stream=None):
+    _check(lib().fmap_batch_run(c_vp(batch), _stream(stream)), "fmap_batch_run")
+
+
+def fmap_batch_status(batch: int, stream=None) -> int:
+    return int(lib().fmap_batch_status(c_vp(batch), _stream(stream)))
+
+
+def fmap_batch_info(batch: int):
+    w, l, b, t = c_i32(), c_i64(), c_size(), c_i32()
+    occ = np.zeros(N_BATCH_PHASES, dtype=np.int32)
+    _check(lib().fmap_batch_info(c_vp(batch), ctypes.byref(w), ctypes.byref(l), ctypes.byref(b),
+                                 _ptr(occ), ctypes.byref(t)), "fmap_batch_info")
+    return dict(waves=int(w.value), launches_per_run=int(l.value), workspace_bytes=int(b.value),
+                occupancy=occ.tolist(), rec_templates_per_block=int(t.value))
+
+
+def fmap_batch_destroy(batch: int):
+    if batch:
+        lib().fmap_batch_destroy(c_vp(batch))
+
+
+class Batch:
+    """Owns a batch plan over torch CUDA tensors (kept alive here)."""
+
+    def __init__(self, instances, want_map=True, workspace_budget=0, autotune=True):
+        import torch
+
+        self.keep = []
+        self.maps, self.sums = [], []
+        items = []
+        for (grid, t, antenna, fafb) in instances:
+            g = make_grid(grid)
+            T = int(fafb.shape[0])
+            m = (torch.empty((T, g.n_t0, g.n_tau), dtype=torch.float32, device=t.device)
+                 if want_map else None)
+            s = torch.empty((max(T, 1), 32), dtype=torch.uint8, device=t.device)
+            a = make_atoms(int(t.shape[0]), T, antenna.dim() == 2, t, antenna, fafb)
+            items.append(fmap_batch_item(g, a, _ptr(m), _ptr(s)))
+            self.keep += [t, antenna, fafb]
+            self.maps.append(m)
+            self.sums.append(s)
+        self.handle = fmap_batch_plan(items, workspace_budget,
+                                      FMAP_BATCH_AUTOTUNE if autotune else 0)
+
+    def run(self, stream=None):
+        fmap_batch_run(self.handle, stream)
+
+    def status(self, stream=None) -> int:
+        return fmap_batch_status(self.handle, stream)
+
+    def info(self):
+        return fmap_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fmap_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

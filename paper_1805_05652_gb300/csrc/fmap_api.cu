@@ -109,7 +109,8 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     int64_t chunk = (int64_t)std::max<size_t>(1, kEsufBudget / per_tau);
     chunk = std::min<int64_t>(chunk, std::max<int32_t>(g->n_tau, 1));
     L.tau_chunk = (int32_t)chunk;
-    L.esuf = take(per_tau * (size_t)chunk);
+    // the suffix sums live in shared memory when the data set fits there
+    L.esuf = take(exp_antenna_fits(n_sft) ? 8 : per_tau * (size_t)chunk);
     if (prec == FMAP_TF32 || prec == FMAP_BF16X3)
       L.xop = take(exp_tc_operand_bytes(*g, n_sft, T, prec));
   }
@@ -169,8 +170,9 @@ static fmap_status plan_args_ok(const fmap_grid* grid, int32_t n_sft, int32_t n_
     if (grid->window != FMAP_EXP) return arg_fail("FMAP_PLAN_EXP_RECURRENCE is for exponential windows");
     if (precision != FMAP_FP64)
       return arg_fail("FMAP_PLAN_EXP_RECURRENCE computes in compensated FP32 (FMAP_FP64 class)");
-    if (!exp_rec_supported(n_sft)) {
-      set_error("FMAP_PLAN_EXP_RECURRENCE keeps a template's suffix sums in shared memory: n_sft too large");
+    if (!exp_rec_supported(n_sft, grid->n_t0)) {
+      set_error("FMAP_PLAN_EXP_RECURRENCE keeps a template's suffix sums and the per-cell data of "
+                "one tau in shared memory: n_sft or n_t0 too large");
       return FMAP_ERR_UNSUPPORTED;
     }
   }

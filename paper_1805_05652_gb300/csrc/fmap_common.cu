@@ -3,21 +3,23 @@
 // per-template reduction and the standalone marginalisation.
 #include <math.h>
 
+#include "fmap_batch.cuh"
 #include "fmap_device.cuh"
 
 namespace fmap {
 
 // t -> t - t[0] as int32, with the data checks (strictly increasing,
 // span < 2^31 s) latched into the plan's status word.
-__global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc,
+__device__ __forceinline__ void prep_body(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc,
                        int32_t* __restrict__ rel_t, int64_t* __restrict__ t_base,
-                       uint32_t* __restrict__ err) {
+                       uint32_t* __restrict__ err,
+    const uint3 bid, const dim3 gdim) {
   const int64_t base = t[0];
-  for (int64_t i = n + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_alloc;
-       i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = n + bid.x * (int64_t)blockDim.x + threadIdx.x; i < n_alloc;
+       i += (int64_t)gdim.x * blockDim.x)
     rel_t[i] = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bid.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gdim.x * blockDim.x) {
     const int64_t ti = t[i];
     const int64_t d = ti - base;
     uint32_t e = 0;
@@ -29,15 +31,22 @@ __global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc
   }
 }
 
+__global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc,
+                       int32_t* __restrict__ rel_t, int64_t* __restrict__ t_base,
+                       uint32_t* __restrict__ err) {
+  prep_body(t, n, n_alloc, rel_t, t_base, err, blockIdx, gridDim);
+}
+
 // Window index tables: i0[m] = first atom with t >= t0_m; jend[m][n] = one
 // past the last atom whose SFT ends by t0_m + L_n (L = tau or 3 tau),
 // clamped to >= i0[m], so the window holds atoms [i0, jend).
-__global__ void k_index(const int64_t* __restrict__ t, int32_t n_sft, fmap_grid g,
-                        int32_t* __restrict__ i0tab, int32_t* __restrict__ jend) {
+__device__ __forceinline__ void index_body(const int64_t* __restrict__ t, int32_t n_sft, fmap_grid g,
+                        int32_t* __restrict__ i0tab, int32_t* __restrict__ jend,
+    const uint3 bid, const dim3 gdim) {
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const int64_t lmul = (g.window == FMAP_RECT) ? 1 : 3;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cells;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t c = bid.x * (int64_t)blockDim.x + threadIdx.x; c < cells;
+       c += (int64_t)gdim.x * blockDim.x) {
     const int64_t m = c / g.n_tau, nn = c - m * g.n_tau;
     const int64_t t0 = g.t0_min + m * g.dt0;
     const int64_t tau = g.tau_min + nn * g.dtau;
@@ -47,6 +56,11 @@ __global__ void k_index(const int64_t* __restrict__ t, int32_t n_sft, fmap_grid 
     jend[c] = j;
     if (nn == 0) i0tab[m] = i0;
   }
+}
+
+__global__ void k_index(const int64_t* __restrict__ t, int32_t n_sft, fmap_grid g,
+                        int32_t* __restrict__ i0tab, int32_t* __restrict__ jend) {
+  index_body(t, n_sft, g, i0tab, jend, blockIdx, gridDim);
 }
 
 cudaError_t launch_prep(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
@@ -161,25 +175,31 @@ __device__ __forceinline__ Partial64 widen(const Partial& q) {
 
 // Level 1: block (g, t) merges slots [g*kRedGroup, (g+1)*kRedGroup) of the
 // concatenation [main tiles 0..n_tiles) ++ [fix-up slots fix0..fix0+n_fix).
-__global__ void __launch_bounds__(kRedThreads)
-k_reduce_groups(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
-                int64_t stride, int64_t n_groups, Partial64* __restrict__ groups) {
-  const Partial* pp = parts + (int64_t)blockIdx.y * stride;
+__device__ __forceinline__ void reduce_groups_body(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
+                int64_t stride, int64_t n_groups, Partial64* __restrict__ groups,
+    const uint3 bid, const dim3 gdim) {
+  const Partial* pp = parts + (int64_t)bid.y * stride;
   const int64_t n_all = n_tiles + n_fix;
-  const int64_t lo = (int64_t)blockIdx.x * kRedGroup;
+  const int64_t lo = (int64_t)bid.x * kRedGroup;
   const int64_t n = max((int64_t)0, min((int64_t)kRedGroup, n_all - lo));
   const Partial64 r = block_merge(n, [&](int64_t b) {
     const int64_t k = lo + b;
     return widen(k < n_tiles ? pp[k] : pp[fix0 + (k - n_tiles)]);
   });
-  if (threadIdx.x == 0) groups[(int64_t)blockIdx.y * n_groups + blockIdx.x] = r;
+  if (threadIdx.x == 0) groups[(int64_t)bid.y * n_groups + bid.x] = r;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_groups(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
+                int64_t stride, int64_t n_groups, Partial64* __restrict__ groups) {
+  reduce_groups_body(parts, n_tiles, fix0, n_fix, stride, n_groups, groups, blockIdx, gridDim);
 }
 
 // Level 2: one block per template over its groups; writes the summary.
-__global__ void __launch_bounds__(kRedThreads)
-k_reduce_final(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n_tau,
-               double log_prior, fmap_summary* __restrict__ out) {
-  const Partial64* gp = groups + (int64_t)blockIdx.x * n_groups;
+__device__ __forceinline__ void reduce_final_body(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n_tau,
+               double log_prior, fmap_summary* __restrict__ out,
+    const uint3 bid, const dim3 gdim) {
+  const Partial64* gp = groups + (int64_t)bid.x * n_groups;
   const Partial64 r = block_merge(n_groups, [&](int64_t b) { return gp[b]; });
   if (threadIdx.x == 0) {
     fmap_summary o;
@@ -196,8 +216,14 @@ k_reduce_final(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n
       o.n = r.arg % n_tau;
       o.logB = 0.5 * (double)r.max2F + log(r.sum) - log((double)r.nvalid) + log_prior;
     }
-    out[blockIdx.x] = o;
+    out[bid.x] = o;
   }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_final(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n_tau,
+               double log_prior, fmap_summary* __restrict__ out) {
+  reduce_final_body(groups, n_groups, n_tau, log_prior, out, blockIdx, gridDim);
 }
 
 int64_t reduce_groups_of(int64_t slots) { return std::max<int64_t>(1, (slots + kRedGroup - 1) / kRedGroup); }
@@ -288,6 +314,48 @@ cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t*
     if (e != cudaSuccess) return e;
   }
   return launch_final_reduce(p, tiles, false, d_summary, s);
+}
+
+
+// ---- persistent multi-instance dispatchers (uneven batches) ----
+__global__ void __launch_bounds__(256) kb_prep(const BItem* __restrict__ items, BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    prep_body(it.t, it.n_sft, it.n_alloc, it.rel_t, it.t_base, it.dev_err,
+              make_uint3((unsigned)k, 0, 0), dim3((unsigned)((it.n_alloc + 255) / 256)));
+  });
+}
+__global__ void __launch_bounds__(256) kb_index(const BItem* __restrict__ items, BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    index_body(it.t, it.n_sft, it.g, it.i0, it.jend, make_uint3((unsigned)k, 0, 0),
+               dim3((unsigned)((it.cells + 255) / 256)));
+  });
+}
+__global__ void __launch_bounds__(kRedThreads) kb_red_groups(const BItem* __restrict__ items,
+                                                             BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    const int64_t fix = it.cells > 0 ? kFixSlots : 0;
+    reduce_groups_body(it.partials, it.tiles_used, it.n_tiles, fix, it.part_stride, it.red_groups,
+                       (Partial64*)it.red_buf,
+                       make_uint3((unsigned)(k % it.red_groups), (unsigned)(k / it.red_groups), 0),
+                       dim3((unsigned)it.red_groups, (unsigned)it.T));
+  });
+}
+__global__ void __launch_bounds__(kRedThreads) kb_red_final(const BItem* __restrict__ items,
+                                                            BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    reduce_final_body((const Partial64*)it.red_buf, it.red_groups, it.g.n_tau > 0 ? it.g.n_tau : 1,
+                      it.log_prior, it.summary, make_uint3((unsigned)k, 0, 0),
+                      dim3((unsigned)it.T));
+  });
+}
+const void* batch_kernel_common(int phase) {
+  switch (phase) {
+    case BP_PREP: return (const void*)kb_prep;
+    case BP_INDEX: return (const void*)kb_index;
+    case BP_RED_GROUPS: return (const void*)kb_red_groups;
+    case BP_RED_FINAL: return (const void*)kb_red_final;
+  }
+  return nullptr;
 }
 
 }  // namespace fmap

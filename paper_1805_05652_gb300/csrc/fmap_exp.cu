@@ -18,6 +18,7 @@
 
 #include <type_traits>
 
+#include "fmap_batch.cuh"
 #include "fmap_device.cuh"
 
 namespace fmap {
@@ -41,17 +42,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Decayed suffix sums of the three antenna rows for one tau (block) of a
-// tau chunk; parallel backward scan of the affine maps E -> x + rho E.
-__global__ void __launch_bounds__(kSufThreads)
-k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restrict__ ant,
-             fmap_grid g, int32_t n_lo, double* __restrict__ esuf) {
-  __shared__ double sR[kSufThreads / 32];
-  __shared__ double sS[3][kSufThreads / 32];
-  const int ni = blockIdx.x;
-  const double tau = (double)(g.tau_min + (int64_t)(n_lo + ni) * g.dtau);
+// Decayed suffix sums of the three antenna rows for one tau, by a parallel
+// backward scan of the affine maps E -> x + rho E over the block's threads;
+// E[c * (n + 1) + i] for c = a2, b2, ab and i = 0..n (E[n] = 0).  E may be in
+// global or shared memory; the block must call it together.
+__device__ __forceinline__ void antenna_suffix(const int32_t* __restrict__ rel_t, int32_t n,
+                                               const float* __restrict__ ant, const fmap_grid& g,
+                                               double tau, double* E, double* sR,
+                                               double (*sS)[kSufThreads / 32]) {
   const double inv_s = 2.0 / tau;
-  double* E = esuf + (int64_t)ni * 3 * ((int64_t)n + 1);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int C = (n + kSufThreads - 1) / kSufThreads;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
@@ -107,14 +106,12 @@ k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restri
   }
   __syncthreads();
   // composition of the later warps, applied to E[N] = 0: only its S matters
-  double lR = 1.0, lS0 = 0.0, lS1 = 0.0, lS2 = 0.0;
+  double lS0 = 0.0, lS1 = 0.0, lS2 = 0.0;
   for (int v = kSufThreads / 32 - 1; v > warp; --v) {
     lS0 = sS[0][v] + sR[v] * lS0;
     lS1 = sS[1][v] + sR[v] * lS1;
     lS2 = sS[2][v] + sR[v] * lS2;
-    lR *= sR[v];
   }
-  (void)lR;
   double e_0 = hS0 + hR * lS0, e_1 = hS1 + hR * lS1, e_2 = hS2 + hR * lS2;
   // phase 3: recompute the chunk from its carry E[e0] and store
   const int64_t np1 = (int64_t)n + 1;
@@ -134,40 +131,91 @@ k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restri
   }
 }
 
-// Per-cell coefficients of the cells of one tau chunk.
+// Global-memory suffix sums for one tau of a tau chunk (long data sets).
+__global__ void __launch_bounds__(kSufThreads)
+k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restrict__ ant,
+             fmap_grid g, int32_t n_lo, double* __restrict__ esuf) {
+  __shared__ double sR[kSufThreads / 32];
+  __shared__ double sS[3][kSufThreads / 32];
+  const int ni = blockIdx.x;
+  const double tau = (double)(g.tau_min + (int64_t)(n_lo + ni) * g.dtau);
+  antenna_suffix(rel_t, n, ant, g, tau, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
+}
+
+// A, B, C of a cell from the suffix sums E of its tau, then its coefficients.
+__device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t, int32_t n,
+                                              const fmap_grid& g, int64_t m, int64_t nn,
+                                              int32_t i0, int32_t j, int64_t t_base,
+                                              const double* E) {
+  const int32_t count = j - i0;
+  double A = 0.0, B = 0.0, C = 0.0;
+  if (count > 0) {
+    const double tau = (double)(g.tau_min + nn * g.dtau);
+    const int64_t t0rel = g.t0_min + m * g.dt0 - t_base;
+    const int64_t np1 = (int64_t)n + 1;
+    // The prefactor scales A, B, C alike (F changes by its relative error
+    // only) and the tail term is ~e^{-6} of the window sum: FP32 exp2 is
+    // accurate enough for both.
+    const float c2 = (float)(-2.8853900817779268 / tau);   // -2 log2(e) / tau
+    const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
+    const double pre = d0 == 0 ? 1.0 : (double)ex2_approx(c2 * (float)d0);
+    const double tail = (j < n) ? (double)ex2_approx(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0;
+    A = pre * (E[i0] - tail * E[j]);
+    B = pre * (E[np1 + i0] - tail * E[np1 + j]);
+    C = pre * (E[2 * np1 + i0] - tail * E[2 * np1 + j]);
+  }
+  return make_coef(A, B, C, count);
+}
+
+// Fused antenna step for data sets that fit shared memory: one block per
+// (tau_n, antenna set) keeps the suffix sums in shared memory and writes the
+// coefficients of every cell (t0_m, tau_n).  Blocks run tau-fastest, so their
+// strided coefficient stores merge in L2.
+__device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
+              fmap_grid g, const float* __restrict__ antenna, const int32_t* __restrict__ i0tab,
+              const int32_t* __restrict__ jend, Coef* __restrict__ coef,
+    const uint3 bid, const dim3 gdim) {
+  extern __shared__ double s_E[];
+  __shared__ double sR[kSufThreads / 32];
+  __shared__ double sS[3][kSufThreads / 32];
+  const int ni = bid.x, ta = bid.y;
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
+  antenna_suffix(rel_t, n, antenna + (int64_t)ta * 3 * n, g, tau, s_E, sR, sS);
+  __syncthreads();
+  const int64_t tb = n > 0 ? *t_base : 0;
+  for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
+    const int64_t cell = (int64_t)m * g.n_tau + ni;
+    coef[(int64_t)ta * cells + cell] =
+        exp_cell_coef(rel_t, n, g, m, ni, i0tab[m], jend[cell], tb, s_E);
+  }
+}
+
+__global__ void __launch_bounds__(kSufThreads)
+k_exp_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
+              fmap_grid g, const float* __restrict__ antenna, const int32_t* __restrict__ i0tab,
+              const int32_t* __restrict__ jend, Coef* __restrict__ coef) {
+  exp_antenna_body(rel_t, t_base, n, g, antenna, i0tab, jend, coef, blockIdx, gridDim);
+}
+
+constexpr int kAntennaSmemMaxSft = 9000;   // 3 x (n + 1) doubles <= 216 KB
+
+// Per-cell coefficients of the cells of one tau chunk (global suffix sums).
 __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base,
                            int32_t n, fmap_grid g, int32_t n_lo, int32_t n_chunk,
                            const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
                            const double* __restrict__ esuf, Coef* __restrict__ coef) {
   const int64_t total = (int64_t)g.n_t0 * n_chunk;
   const int64_t np1 = (int64_t)n + 1;
+  const int64_t tb = n > 0 ? *t_base : 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = c / n_chunk;
     const int32_t nl = (int32_t)(c - m * n_chunk);
     const int64_t nn = n_lo + nl;
     const int64_t cell = m * g.n_tau + nn;
-    const int32_t i0 = i0tab[m];
-    const int32_t j = jend[cell];
-    const int32_t count = j - i0;
-    double A = 0.0, B = 0.0, C = 0.0;
-    if (count > 0) {
-      const double tau = (double)(g.tau_min + nn * g.dtau);
-      const int64_t t0rel = g.t0_min + m * g.dt0 - *t_base;
-      // The prefactor scales A, B, C alike (F changes by its relative error
-      // only) and the tail term is ~e^{-6} of the window sum: FP32 exp2 is
-      // accurate enough for both.
-      const float c2 = (float)(-2.8853900817779268 / tau);   // -2 log2(e) / tau
-      const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
-      const double pre = d0 == 0 ? 1.0 : (double)ex2_approx(c2 * (float)d0);
-      const double tail =
-          (j < n) ? (double)ex2_approx(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0;
-      const double* E = esuf + (int64_t)nl * 3 * np1;
-      A = pre * (E[i0] - tail * E[j]);
-      B = pre * (E[np1 + i0] - tail * E[np1 + j]);
-      C = pre * (E[2 * np1 + i0] - tail * E[2 * np1 + j]);
-    }
-    coef[cell] = make_coef(A, B, C, count);
+    coef[cell] = exp_cell_coef(rel_t, n, g, m, nn, i0tab[m], jend[cell], tb,
+                               esuf + (int64_t)nl * 3 * np1);
   }
 }
 
@@ -176,6 +224,14 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
   if ((int64_t)g.n_t0 * g.n_tau == 0) return cudaSuccess;
   const int n_ant = a->shared_antenna ? 1 : p->n_templates;
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  if (p->n_sft <= kAntennaSmemMaxSft) {
+    const size_t smem = sizeof(double) * 3 * ((size_t)p->n_sft + 1);
+    cudaFuncSetAttribute(k_exp_antenna, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_exp_antenna<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), kSufThreads, smem, s>>>(
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, a->antenna, p->ws.i0, p->ws.jend, p->ws.coef);
+    p->launches += 1;
+    return cudaGetLastError();
+  }
   for (int ta = 0; ta < n_ant; ++ta) {
     const float* ant = a->antenna + (int64_t)ta * 3 * p->n_sft;
     for (int32_t lo = 0; lo < g.n_tau; lo += p->tau_chunk) {
@@ -319,5 +375,21 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
   p->launches += 1;
   return cudaGetLastError();
 }
+
+
+// ---- persistent multi-instance dispatcher (uneven batches) ----
+__global__ void __launch_bounds__(kSufThreads) kb_exp_ant(const BItem* __restrict__ items,
+                                                          BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.antenna, it.i0, it.jend, it.coef,
+                     make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
+                     dim3((unsigned)it.g.n_tau, (unsigned)it.n_ant));
+  });
+}
+const void* batch_kernel_exp(int phase) {
+  return phase == BP_EXP_ANT ? (const void*)kb_exp_ant : nullptr;
+}
+size_t exp_antenna_smem(int32_t n_sft) { return sizeof(double) * 3 * ((size_t)n_sft + 1); }
+bool exp_antenna_fits(int32_t n_sft) { return n_sft <= kAntennaSmemMaxSft; }
 
 }  // namespace fmap

@@ -12,19 +12,28 @@
 // per-cell differences, which then carry the same ~1e-7 relative error as the
 // rectangular window's prefix differences.
 //
-// One block per (tau_n, template): the suffix sums of the template's 4 data
-// columns live in shared memory; the block then evaluates the column of cells
-// (t0_m, tau_n) for every m.  Blocks run tau-fastest, so the blocks writing
-// neighbouring tau of the same map rows run together and their stores merge
-// in L2.
+// One block per (tau_n, group of templates): the per-SFT decays of tau_n are
+// computed once (FP64, split into float pairs) into shared memory; for each
+// template of the group the block scans the 4 data columns into shared memory
+// and evaluates the column of cells (t0_m, tau_n) for every m.  Blocks run
+// tau-fastest, so the blocks writing neighbouring tau of the same map rows run
+// together and their stores merge in L2.
 #include <math.h>
 
+#include "fmap_batch.cuh"
 #include "fmap_device.cuh"
 
 namespace fmap {
 
 constexpr int kRecThreads = 256;
-constexpr int kRecMaxSft = 12000;
+constexpr int kRecChunk = 8;        // SFTs of data prefetched per serial run of the scan
+constexpr int kRecMaxSft = 9000;    // decays + one template's suffix sums in shared memory
+
+struct __align__(16) CellRec {
+  int32_t i0, j;
+  float pre, tail;
+  Coef cf;
+};
 
 struct FF {
   float h, l;
@@ -75,128 +84,193 @@ __device__ __forceinline__ float rec_ex2(float x) {
   return y;
 }
 
+__device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
+          fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+          const Coef* __restrict__ coef, int32_t shared_antenna, const float* __restrict__ fafb,
+          int32_t n_templates, int32_t n_groups, float* __restrict__ map,
+          Partial* __restrict__ parts, int64_t stride,
+    const uint3 bid, const dim3 gdim) {
+  extern __shared__ __align__(16) float s_dyn[];
+  float* s_rh = s_dyn;                 // [n] decay after atom i, high part
+  float* s_rl = s_dyn + n;             // [n] low part
+  float* s_e = s_dyn + 2 * (int64_t)n; // [4][n + 1] suffix sums of one template
+  // per cell (t0_m, tau_n): the window [i0, j), prefactor, tail factor and the
+  // 2F coefficients -- the same for every template, so staged once
+  CellRec* s_cell = (CellRec*)(s_e + 4 * ((int64_t)n + 1) + ((4 - (6 * n + 4) % 4) % 4));
+  __shared__ float sR[2][kRecThreads / 32];
+  __shared__ float sS[4][2][kRecThreads / 32];
+  __shared__ Partial scratch[kRecThreads / 32];
+  const int ni = bid.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
+  const double inv_tau = 1.0 / tau;
+  const int64_t np1 = (int64_t)n + 1;
+  // Decays of this tau, once for all the block's templates: whole multiples k
+  // of T_sft take the k-th power of the one-SFT decay, other gaps use exp.
+  {
+    const double rho1 = exp(-(double)g.t_sft * inv_tau);
+    const float inv_tsft = 1.0f / (float)g.t_sft;
+    for (int i = tid; i < n; i += kRecThreads) {
+      double r = 0.0;
+      if (i + 1 < n) {
+        const int32_t gap = rel_t[i + 1] - rel_t[i];
+        const int32_t k = __float2int_rn((float)gap * inv_tsft);
+        if (k >= 1 && k <= 64 && (int64_t)k * g.t_sft == gap)
+          r = k == 1 ? rho1 : rec_ipow(rho1, k);
+        else
+          r = exp(-(double)gap * inv_tau);
+      }
+      const float h = (float)r;
+      s_rh[i] = h;
+      s_rl[i] = (float)(r - (double)h);
+    }
+  }
+  const int C = (n + kRecThreads - 1) / kRecThreads;
+  const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const float c2 = (float)(-1.4426950408889634 * inv_tau);
+  const int64_t tb = n > 0 ? *t_base : 0;
+  for (int32_t m = tid; m < g.n_t0; m += kRecThreads) {
+    const int64_t cell = (int64_t)m * g.n_tau + ni;
+    CellRec r;
+    r.i0 = i0tab[m];
+    r.j = jend[cell];
+    r.pre = 0.0f;
+    r.tail = 0.0f;
+    if (r.j > r.i0) {
+      const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
+      const int64_t d0 = (int64_t)rel_t[r.i0] - t0rel;
+      r.pre = d0 == 0 ? 1.0f : rec_ex2(c2 * (float)d0);
+      r.tail = r.j < n ? rec_ex2(c2 * (float)(rel_t[r.j] - rel_t[r.i0])) : 0.0f;
+    }
+    r.cf = coef[cell];
+    s_cell[m] = r;
+  }
+  const int32_t t_lo = (int32_t)((int64_t)bid.y * n_templates / n_groups);
+  const int32_t t_hi = (int32_t)((int64_t)(bid.y + 1) * n_templates / n_groups);
+  for (int32_t tq = t_lo; tq < t_hi; ++tq) {
+    __syncthreads();   // decays ready; previous template's cells done with s_e
+    const float* x = fafb + (int64_t)tq * 4 * n;
+    // phase 1: this thread's chunk as one affine map, E[s0] = S + R E[e0];
+    // the data of each run of kRecChunk SFTs is loaded before its serial chain
+    FF R = {1.0f, 0.0f}, S[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    float xv[kRecChunk][4];
+    for (int b0 = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk; e0 > s0 && b0 >= s0;
+         b0 -= kRecChunk) {
+#pragma unroll
+      for (int q = 0; q < kRecChunk; ++q) {
+        const int i = b0 + q;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xv[q][c] = (i < e0) ? __ldg(x + (int64_t)c * n + i) : 0.0f;
+      }
+#pragma unroll
+      for (int q = kRecChunk - 1; q >= 0; --q) {
+        const int i = b0 + q;
+        if (i >= e0) continue;
+        const FF r = {s_rh[i], s_rl[i]};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) S[c] = ff_axpy(r, S[c], xv[q][c]);
+        R = ff_mul(r, R);
+      }
+    }
+    // phase 2: suffix composition within the warp (self o later)
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const FF Ro = ff_shfl_down(R, d);
+      FF So[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) So[c] = ff_shfl_down(S[c], d);
+      if (lane + d < 32) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) S[c] = ff_add(S[c], ff_mul(R, So[c]));
+        R = ff_mul(R, Ro);
+      }
+    }
+    FF hR = ff_shfl_down(R, 1), hS[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) hS[c] = ff_shfl_down(S[c], 1);
+    if (lane == 31) {
+      hR = {1.0f, 0.0f};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) hS[c] = {0.0f, 0.0f};
+    }
+    if (lane == 0) {
+      sR[0][warp] = R.h;
+      sR[1][warp] = R.l;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        sS[c][0][warp] = S[c].h;
+        sS[c][1][warp] = S[c].l;
+      }
+    }
+    __syncthreads();
+    // later warps applied to E[N] = 0
+    FF lS[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int v = kRecThreads / 32 - 1; v > warp; --v) {
+      const FF Rv = {sR[0][v], sR[1][v]};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) lS[c] = ff_add({sS[c][0][v], sS[c][1][v]}, ff_mul(Rv, lS[c]));
+    }
+    FF e[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) e[c] = ff_add(hS[c], ff_mul(hR, lS[c]));
+    // phase 3: recompute the chunk from its carry and keep E (rounded) in smem
+    for (int b0 = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk; e0 > s0 && b0 >= s0;
+         b0 -= kRecChunk) {
+#pragma unroll
+      for (int q = 0; q < kRecChunk; ++q) {
+        const int i = b0 + q;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xv[q][c] = (i < e0) ? __ldg(x + (int64_t)c * n + i) : 0.0f;
+      }
+#pragma unroll
+      for (int q = kRecChunk - 1; q >= 0; --q) {
+        const int i = b0 + q;
+        if (i >= e0) continue;
+        const FF r = {s_rh[i], s_rl[i]};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          e[c] = ff_axpy(r, e[c], xv[q][c]);
+          s_e[c * np1 + i] = e[c].h + e[c].l;
+        }
+      }
+    }
+    if (tid < 4) s_e[tid * np1 + n] = 0.0f;
+    __syncthreads();
+    // cells (t0_m, tau_n), all m
+    Partial acc = partial_empty();
+    for (int32_t m = tid; m < g.n_t0; m += kRecThreads) {
+      const int64_t cell = (int64_t)m * g.n_tau + ni;
+      const CellRec r = s_cell[m];
+      const Coef cf = shared_antenna ? r.cf : coef[(int64_t)tq * cells + cell];
+      float f[4] = {0.f, 0.f, 0.f, 0.f};
+      if (r.j > r.i0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          f[c] = r.pre * fmaf(-r.tail, s_e[c * np1 + r.j], s_e[c * np1 + r.i0]);
+      }
+      const float v = two_f(cf, f[0], f[1], f[2], f[3]);
+      const bool ok = cf.valid == 1.0f;
+      if (map && cf.valid != 2.0f) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
+      partial_add(acc, v, (int32_t)cell, ok);
+    }
+    acc = partial_block_reduce<kRecThreads / 32>(acc, scratch);
+    if (tid == 0) parts[(int64_t)tq * stride + ni] = acc;
+  }
+}
+
 __global__ void __launch_bounds__(kRecThreads)
 k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float* __restrict__ fafb,
-          int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
-          int64_t stride) {
-  extern __shared__ float s_e[];  // [4][n + 1]
-  __shared__ float sR[2][kRecThreads / 32];
-  __shared__ float sS[4][2][kRecThreads / 32];
-  __shared__ Partial scratch[kRecThreads / 32];
-  const int ni = blockIdx.x;
-  const int tq = blockIdx.y;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
-  const double inv_tau = 1.0 / tau;
-  const double rho1 = exp(-(double)g.t_sft * inv_tau);
-  const float inv_tsft = 1.0f / (float)g.t_sft;
-  const float* x = fafb + (int64_t)tq * 4 * n;
-  const int64_t np1 = (int64_t)n + 1;
-  // decay over the gap after atom i, as a float pair
-  auto rho_at = [&](int i) -> FF {
-    if (i + 1 >= n) return {0.0f, 0.0f};
-    const int32_t gap = rel_t[i + 1] - rel_t[i];
-    const int32_t k = __float2int_rn((float)gap * inv_tsft);
-    double r;
-    if (k >= 1 && k <= 64 && (int64_t)k * g.t_sft == gap)
-      r = k == 1 ? rho1 : rec_ipow(rho1, k);
-    else
-      r = exp(-(double)gap * inv_tau);
-    const float h = (float)r;
-    return {h, (float)(r - (double)h)};
-  };
-  const int C = (n + kRecThreads - 1) / kRecThreads;
-  const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
-  // phase 1: this thread's chunk as one affine map, E[s0] = S + R E[e0]
-  FF R = {1.0f, 0.0f}, S[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-  for (int i = e0 - 1; i >= s0; --i) {
-    const FF r = rho_at(i);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) S[c] = ff_axpy(r, S[c], x[(int64_t)c * n + i]);
-    R = ff_mul(r, R);
-  }
-  // phase 2: suffix composition within the warp (self o later)
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const FF Ro = ff_shfl_down(R, d);
-    FF So[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) So[c] = ff_shfl_down(S[c], d);
-    if (lane + d < 32) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) S[c] = ff_add(S[c], ff_mul(R, So[c]));
-      R = ff_mul(R, Ro);
-    }
-  }
-  FF hR = ff_shfl_down(R, 1), hS[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) hS[c] = ff_shfl_down(S[c], 1);
-  if (lane == 31) {
-    hR = {1.0f, 0.0f};
-#pragma unroll
-    for (int c = 0; c < 4; ++c) hS[c] = {0.0f, 0.0f};
-  }
-  if (lane == 0) {
-    sR[0][warp] = R.h;
-    sR[1][warp] = R.l;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      sS[c][0][warp] = S[c].h;
-      sS[c][1][warp] = S[c].l;
-    }
-  }
-  __syncthreads();
-  // later warps applied to E[N] = 0
-  FF lS[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-  for (int v = kRecThreads / 32 - 1; v > warp; --v) {
-    const FF Rv = {sR[0][v], sR[1][v]};
-#pragma unroll
-    for (int c = 0; c < 4; ++c) lS[c] = ff_add({sS[c][0][v], sS[c][1][v]}, ff_mul(Rv, lS[c]));
-  }
-  FF e[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) e[c] = ff_add(hS[c], ff_mul(hR, lS[c]));
-  // phase 3: recompute the chunk from its carry and keep E (rounded) in smem
-  for (int i = e0 - 1; i >= s0; --i) {
-    const FF r = rho_at(i);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      e[c] = ff_axpy(r, e[c], x[(int64_t)c * n + i]);
-      s_e[c * np1 + i] = e[c].h + e[c].l;
-    }
-  }
-  if (tid < 4) s_e[tid * np1 + n] = 0.0f;
-  __syncthreads();
-  // cells (t0_m, tau_n), all m
-  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
-  const float c2 = (float)(-1.4426950408889634 * inv_tau);
-  const int64_t tb = *t_base;
-  Partial acc = partial_empty();
-  for (int32_t m = tid; m < g.n_t0; m += kRecThreads) {
-    const int64_t cell = (int64_t)m * g.n_tau + ni;
-    const int32_t i0 = i0tab[m], j = jend[cell];
-    const Coef cf = shared_antenna ? coef[cell] : coef[(int64_t)tq * cells + cell];
-    float f[4] = {0.f, 0.f, 0.f, 0.f};
-    if (j > i0) {
-      const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
-      const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
-      const float pre = d0 == 0 ? 1.0f : rec_ex2(c2 * (float)d0);
-      const float tail = j < n ? rec_ex2(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0f;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) f[c] = pre * fmaf(-tail, s_e[c * np1 + j], s_e[c * np1 + i0]);
-    }
-    const float v = two_f(cf, f[0], f[1], f[2], f[3]);
-    const bool ok = cf.valid == 1.0f;
-    if (map && cf.valid != 2.0f) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
-    partial_add(acc, v, (int32_t)cell, ok);
-  }
-  acc = partial_block_reduce<kRecThreads / 32>(acc, scratch);
-  if (tid == 0) parts[(int64_t)tq * stride + ni] = acc;
+          int32_t n_templates, int32_t n_groups, float* __restrict__ map,
+          Partial* __restrict__ parts, int64_t stride) {
+  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, fafb, n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
-bool exp_rec_supported(int32_t n_sft) { return n_sft <= kRecMaxSft; }
+bool exp_rec_supported(int32_t n_sft, int32_t n_t0) {
+  return n_sft <= kRecMaxSft && exp_rec_smem(n_sft, n_t0) <= 220 * 1024;
+}
 
 cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                            int64_t* tiles_used) {
@@ -204,15 +278,38 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
   *tiles_used = 0;
   if ((int64_t)g.n_t0 * g.n_tau == 0 || p->n_templates == 0) return cudaSuccess;
   *tiles_used = g.n_tau;
-  const size_t smem = sizeof(float) * 4 * ((size_t)p->n_sft + 1);
+  const size_t smem = exp_rec_smem(p->n_sft, g.n_t0);
   cudaFuncSetAttribute(k_exp_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((unsigned)g.n_tau, (unsigned)p->n_templates);
+  // split the templates over enough blocks to fill the GPU a few times
+  const int64_t want = (int64_t)p->n_sm * 4;
+  const int32_t groups = (int32_t)std::max<int64_t>(
+      1, std::min<int64_t>(p->n_templates, (want + g.n_tau - 1) / g.n_tau));
+  dim3 grid((unsigned)g.n_tau, (unsigned)groups);
   k_exp_rec<<<grid, kRecThreads, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0,
                                             p->ws.jend, p->ws.coef, a->shared_antenna, a->fafb,
-                                            p->n_templates, d_2F, p->ws.partials,
+                                            p->n_templates, groups, d_2F, p->ws.partials,
                                             p->part_stride);
   p->launches += 1;
   return cudaGetLastError();
+}
+
+
+// ---- persistent multi-instance dispatcher (uneven batches) ----
+__global__ void __launch_bounds__(kRecThreads) kb_exp_rec(const BItem* __restrict__ items,
+                                                          BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    exp_rec_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared, it.fafb,
+                 it.T, it.groups, it.map, it.partials, it.part_stride,
+                 make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
+                 dim3((unsigned)it.g.n_tau, (unsigned)it.groups));
+  });
+}
+const void* batch_kernel_exp_rec(int phase) {
+  return phase == BP_EXP_REC ? (const void*)kb_exp_rec : nullptr;
+}
+size_t exp_rec_smem(int32_t n_sft, int32_t n_t0) {
+  return sizeof(float) * (2 * (size_t)n_sft + 4 * ((size_t)n_sft + 1)) + 16 +
+         sizeof(CellRec) * (size_t)n_t0;
 }
 
 }  // namespace fmap

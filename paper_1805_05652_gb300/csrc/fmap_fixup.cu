@@ -15,6 +15,7 @@
 //      slots, merged by the final reduction.
 #include <math.h>
 
+#include "fmap_batch.cuh"
 #include "fmap_device.cuh"
 
 namespace fmap {
@@ -24,17 +25,22 @@ constexpr int kFixThreads = 128;
 constexpr int kFixWeights = 256;
 
 // Per block of kFlagBlock entries: number of entries with valid == 2.
-__global__ void __launch_bounds__(kFlagBlock)
-k_flag_count(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt) {
-  const int64_t e = (int64_t)blockIdx.x * kFlagBlock + threadIdx.x;
+__device__ __forceinline__ void flag_count_body(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt,
+    const uint3 bid, const dim3 gdim) {
+  const int64_t e = (int64_t)bid.x * kFlagBlock + threadIdx.x;
   const bool f = e < n_entries && coef[e].valid == 2.0f;
   const int c = __syncthreads_count(f);
-  if (threadIdx.x == 0) blockcnt[blockIdx.x] = c;
+  if (threadIdx.x == 0) blockcnt[bid.x] = c;
+}
+
+__global__ void __launch_bounds__(kFlagBlock)
+k_flag_count(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt) {
+  flag_count_body(coef, n_entries, blockcnt, blockIdx, gridDim);
 }
 
 // Exclusive scan of the block counts (one block); total into *n_flag.
-__global__ void __launch_bounds__(1024)
-k_flag_scan(int32_t* __restrict__ blockcnt, int64_t n_blocks, int32_t* __restrict__ n_flag) {
+__device__ __forceinline__ void flag_scan_body(int32_t* __restrict__ blockcnt, int64_t n_blocks, int32_t* __restrict__ n_flag,
+    const uint3 bid, const dim3 gdim) {
   __shared__ int32_t warp_sum[32];
   __shared__ int32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -70,41 +76,53 @@ k_flag_scan(int32_t* __restrict__ blockcnt, int64_t n_blocks, int32_t* __restric
   if (threadIdx.x == 0) *n_flag = carry;
 }
 
+__global__ void __launch_bounds__(1024)
+k_flag_scan(int32_t* __restrict__ blockcnt, int64_t n_blocks, int32_t* __restrict__ n_flag) {
+  flag_scan_body(blockcnt, n_blocks, n_flag, blockIdx, gridDim);
+}
+
 // Ordered writes of the marked entries.
-__global__ void __launch_bounds__(kFlagBlock)
-k_flag_write(const Coef* __restrict__ coef, int64_t n_entries,
-             const int32_t* __restrict__ blockoff, int64_t* __restrict__ list) {
+__device__ __forceinline__ void flag_write_body(const Coef* __restrict__ coef, int64_t n_entries,
+             const int32_t* __restrict__ blockoff, int64_t* __restrict__ list,
+    const uint3 bid, const dim3 gdim) {
   __shared__ int32_t warp_cnt[kFlagBlock / 32];
-  const int64_t e = (int64_t)blockIdx.x * kFlagBlock + threadIdx.x;
+  const int64_t e = (int64_t)bid.x * kFlagBlock + threadIdx.x;
   const bool f = e < n_entries && coef[e].valid == 2.0f;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t bal = __ballot_sync(0xffffffffu, f);
   if (lane == 0) warp_cnt[warp] = __popc(bal);
   __syncthreads();
   if (f) {
-    int32_t off = blockoff[blockIdx.x];
+    int64_t off = blockoff[bid.x];
     for (int w = 0; w < warp; ++w) off += warp_cnt[w];
     off += __popc(bal & ((1u << lane) - 1u));
-    list[off] = e;
+    if (off < n_entries) list[off] = e;   // the list holds at most n_entries
   }
+}
+
+__global__ void __launch_bounds__(kFlagBlock)
+k_flag_write(const Coef* __restrict__ coef, int64_t n_entries,
+             const int32_t* __restrict__ blockoff, int64_t* __restrict__ list) {
+  flag_write_body(coef, n_entries, blockoff, list, blockIdx, gridDim);
 }
 
 // FP64 recomputation of listed entries.  Entry = cell (shared antenna: every
 // template) or template * cells + cell (per-template antenna: that template).
 // Block (b, y): entries [b n / G, (b + 1) n / G), templates y*128 + tid.
-__global__ void __launch_bounds__(kFixThreads)
-k_fixup(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
+__device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
         int32_t shared_antenna, const int32_t* __restrict__ rel_t,
         const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g,
         const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
-        float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0) {
+        float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
+    const uint3 bid, const dim3 gdim) {
   __shared__ double sw[kFixWeights];
-  const int64_t n = *n_flag;
-  const int64_t lo = (int64_t)blockIdx.x * n / G, hi = (int64_t)(blockIdx.x + 1) * n / G;
-  const int32_t tq = blockIdx.y * kFixThreads + threadIdx.x;
-  const bool active_t = tq < n_templates;
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const int64_t cap = shared_antenna ? cells : cells * n_templates;   // list capacity
+  const int64_t n = min((int64_t)*n_flag, cap);
+  const int64_t lo = (int64_t)bid.x * n / G, hi = (int64_t)(bid.x + 1) * n / G;
+  const int32_t tq = bid.y * kFixThreads + threadIdx.x;
+  const bool active_t = tq < n_templates;
   Partial acc = partial_empty();
   for (int64_t k = lo; k < hi; ++k) {
     const int64_t entry = list[k];
@@ -154,7 +172,17 @@ k_fixup(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, in
       partial_add(acc, (float)v, (int32_t)cell, ok);
     }
   }
-  if (active_t) parts[(int64_t)tq * stride + slot0 + blockIdx.x] = acc;
+  if (active_t) parts[(int64_t)tq * stride + slot0 + bid.x] = acc;
+}
+
+__global__ void __launch_bounds__(kFixThreads)
+k_fixup(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
+        int32_t shared_antenna, const int32_t* __restrict__ rel_t,
+        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g,
+        const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+        const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
+        float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0) {
+  fixup_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, i0tab, jend, antenna, fafb, n_templates, map, parts, stride, slot0, blockIdx, gridDim);
 }
 
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
@@ -176,6 +204,47 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
                                        p->n_tiles);
   p->launches += 4;
   return cudaGetLastError();
+}
+
+
+// ---- persistent multi-instance dispatchers (uneven batches) ----
+__global__ void __launch_bounds__(kFlagBlock) kb_flag_count(const BItem* __restrict__ items,
+                                                            BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    flag_count_body(it.coef, it.flag_entries, it.flag_blocks, make_uint3((unsigned)k, 0, 0),
+                    dim3(1));
+  });
+}
+__global__ void __launch_bounds__(1024) kb_flag_scan(const BItem* __restrict__ items, BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t) {
+    flag_scan_body(it.flag_blocks, (it.flag_entries + kFlagBlock - 1) / kFlagBlock, it.n_flag,
+                   make_uint3(0, 0, 0), dim3(1));
+  });
+}
+__global__ void __launch_bounds__(kFlagBlock) kb_flag_write(const BItem* __restrict__ items,
+                                                            BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    flag_write_body(it.coef, it.flag_entries, it.flag_blocks, it.flag_list,
+                    make_uint3((unsigned)k, 0, 0), dim3(1));
+  });
+}
+__global__ void __launch_bounds__(kFixThreads) kb_fixup(const BItem* __restrict__ items,
+                                                        BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft, it.g,
+               it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials, it.part_stride,
+               it.n_tiles, make_uint3((unsigned)(k % kFixSlots), (unsigned)(k / kFixSlots), 0),
+               dim3((unsigned)kFixSlots, (unsigned)((it.T + kFixThreads - 1) / kFixThreads)));
+  });
+}
+const void* batch_kernel_fixup(int phase) {
+  switch (phase) {
+    case BP_FLAG_COUNT: return (const void*)kb_flag_count;
+    case BP_FLAG_SCAN: return (const void*)kb_flag_scan;
+    case BP_FLAG_WRITE: return (const void*)kb_flag_write;
+    case BP_FIXUP: return (const void*)kb_fixup;
+  }
+  return nullptr;
 }
 
 }  // namespace fmap

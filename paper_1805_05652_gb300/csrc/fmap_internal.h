@@ -133,7 +133,16 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
                           int64_t* tiles_used);
 cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                            int64_t* tiles_used);
-bool exp_rec_supported(int32_t n_sft);
+bool exp_rec_supported(int32_t n_sft, int32_t n_t0);
+bool exp_antenna_fits(int32_t n_sft);
+size_t exp_antenna_smem(int32_t n_sft);
+size_t exp_rec_smem(int32_t n_sft, int32_t n_t0);
+// Dispatcher kernels of the batch phases, by file (nullptr: not that file's).
+const void* batch_kernel_common(int phase);
+const void* batch_kernel_rect(int phase);
+const void* batch_kernel_exp(int phase);
+const void* batch_kernel_exp_rec(int phase);
+const void* batch_kernel_fixup(int phase);
 cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
                                   cudaStream_t s);

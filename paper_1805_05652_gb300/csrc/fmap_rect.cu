@@ -10,6 +10,7 @@
 //   adds atom after atom to FP32 running sums as tau grows.
 #include <math.h>
 
+#include "fmap_batch.cuh"
 #include "fmap_device.cuh"
 
 namespace fmap {
@@ -57,11 +58,11 @@ __device__ __forceinline__ void block_exscan(const double (&v)[NC], double (&exc
 
 // Prefix of the data rows of one template: px[t][i] = (hi[4], lo[4]) of
 // sum_{a < i} x_a for i = 0..N.
-__global__ void __launch_bounds__(kScanThreads)
-k_rect_scan_data(const float* __restrict__ fafb, int32_t n, float4* __restrict__ px) {
+__device__ __forceinline__ void rect_scan_data_body(const float* __restrict__ fafb, int32_t n, float4* __restrict__ px,
+    const uint3 bid, const dim3 gdim) {
   __shared__ float tile[4][kScanTile];
   __shared__ double sh[4][kScanThreads];
-  const int64_t tm = blockIdx.x;
+  const int64_t tm = bid.x;
   const float* x = fafb + tm * 4 * (int64_t)n;
   float4* out = px + tm * 2 * (int64_t)(n + 1);
   const int tid = threadIdx.x;
@@ -108,12 +109,17 @@ k_rect_scan_data(const float* __restrict__ fafb, int32_t n, float4* __restrict__
   }
 }
 
-// FP64 prefix of the antenna rows: pa[ta][i] = (sum a2, sum b2, sum ab, 0).
 __global__ void __launch_bounds__(kScanThreads)
-k_rect_scan_antenna(const float* __restrict__ antenna, int32_t n, D4* __restrict__ pa) {
+k_rect_scan_data(const float* __restrict__ fafb, int32_t n, float4* __restrict__ px) {
+  rect_scan_data_body(fafb, n, px, blockIdx, gridDim);
+}
+
+// FP64 prefix of the antenna rows: pa[ta][i] = (sum a2, sum b2, sum ab, 0).
+__device__ __forceinline__ void rect_scan_antenna_body(const float* __restrict__ antenna, int32_t n, D4* __restrict__ pa,
+    const uint3 bid, const dim3 gdim) {
   __shared__ float tile[3][kScanTile];
   __shared__ double sh[3][kScanThreads];
-  const int64_t ta = blockIdx.x;
+  const int64_t ta = bid.x;
   const float* x = antenna + ta * 3 * (int64_t)n;
   D4* out = pa + ta * (int64_t)(n + 1);
   const int tid = threadIdx.x;
@@ -149,16 +155,22 @@ k_rect_scan_antenna(const float* __restrict__ antenna, int32_t n, D4* __restrict
   }
 }
 
+__global__ void __launch_bounds__(kScanThreads)
+k_rect_scan_antenna(const float* __restrict__ antenna, int32_t n, D4* __restrict__ pa) {
+  rect_scan_antenna_body(antenna, n, pa, blockIdx, gridDim);
+}
+
 // Per-cell coefficients (shared by the templates of one antenna set) from the
 // FP64 antenna prefixes: A, B, C, D = AB - C^2 in FP64.
-__global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+__device__ __forceinline__ void rect_coef_body(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
                             const D4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
-                            int32_t n_ant, Coef* __restrict__ coef) {
+                            int32_t n_ant, Coef* __restrict__ coef,
+    const uint3 bid, const dim3 gdim) {
   const int64_t cells = (int64_t)n_t0 * n_tau;
   const int64_t total = cells * n_ant;
   const int64_t np1 = (int64_t)n_sft + 1;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = bid.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gdim.x * blockDim.x) {
     const int64_t ta = e / cells, cell = e - ta * cells;
     const int32_t i0 = i0tab[cell / n_tau], j = jend[cell];
     const D4 pj = pa[ta * np1 + j], pi = pa[ta * np1 + i0];
@@ -166,17 +178,23 @@ __global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __
   }
 }
 
+__global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+                            const D4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
+                            int32_t n_ant, Coef* __restrict__ coef) {
+  rect_coef_body(i0tab, jend, pa, n_sft, n_t0, n_tau, n_ant, coef, blockIdx, gridDim);
+}
+
 // One thread per cell (m, n); the block covers 256 consecutive n of one row
 // and loops over the templates.  Per template: two float-pair gathers,
 // compensated differences, 2F, map store and one block partial.
 // Ill-conditioned cells (valid == 2) are left to the FP64 fix-up.
-__global__ void __launch_bounds__(kCellThreads)
-k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+__device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
              const Coef* __restrict__ coef, const float4* __restrict__ px, int32_t n_sft,
              int32_t n_t0, int32_t n_tau, int32_t n_templates, int32_t shared_antenna,
-             float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
+             float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
+    const uint3 bid, const dim3 gdim) {
   __shared__ Partial scratch[kCellThreads / 32];
-  const int64_t tile = blockIdx.x;
+  const int64_t tile = bid.x;
   const int32_t nblk = (n_tau + kCellThreads - 1) / kCellThreads;
   const int32_t m = (int32_t)(tile / nblk);
   const int32_t nn = (int32_t)(tile - (int64_t)m * nblk) * kCellThreads + threadIdx.x;
@@ -204,6 +222,14 @@ k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend
     p = partial_block_reduce<kCellThreads / 32>(p, scratch);
     if (threadIdx.x == 0) parts[(int64_t)tm * stride + tile] = p;
   }
+}
+
+__global__ void __launch_bounds__(kCellThreads)
+k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+             const Coef* __restrict__ coef, const float4* __restrict__ px, int32_t n_sft,
+             int32_t n_t0, int32_t n_tau, int32_t n_templates, int32_t shared_antenna,
+             float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
+  rect_cells_body(i0tab, jend, coef, px, n_sft, n_t0, n_tau, n_templates, shared_antenna, map, parts, stride, blockIdx, gridDim);
 }
 
 // The paper's rectangular kernel (Sec. 3) for the data rows: one thread per
@@ -297,6 +323,47 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
       a->shared_antenna, d_2F, p->ws.partials, p->part_stride);
   p->launches += 1;
   return cudaGetLastError();
+}
+
+
+// ---- persistent multi-instance dispatchers (uneven batches) ----
+__global__ void __launch_bounds__(kScanThreads) kb_rect_ant(const BItem* __restrict__ items,
+                                                            BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    rect_scan_antenna_body(it.antenna, it.n_sft, (D4*)it.pa, make_uint3((unsigned)k, 0, 0),
+                           dim3((unsigned)it.n_ant));
+  });
+}
+__global__ void __launch_bounds__(256) kb_rect_coef(const BItem* __restrict__ items, BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    rect_coef_body(it.i0, it.jend, (const D4*)it.pa, it.n_sft, it.g.n_t0, it.g.n_tau, it.n_ant,
+                   it.coef, make_uint3((unsigned)k, 0, 0),
+                   dim3((unsigned)((it.cells * it.n_ant + 255) / 256)));
+  });
+}
+__global__ void __launch_bounds__(kScanThreads) kb_rect_data(const BItem* __restrict__ items,
+                                                             BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    rect_scan_data_body(it.fafb, it.n_sft, it.px, make_uint3((unsigned)k, 0, 0),
+                        dim3((unsigned)it.T));
+  });
+}
+__global__ void __launch_bounds__(kCellThreads) kb_rect_cells(const BItem* __restrict__ items,
+                                                              BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    rect_cells_body(it.i0, it.jend, it.coef, it.px, it.n_sft, it.g.n_t0, it.g.n_tau, it.T,
+                    it.shared, it.map, it.partials, it.part_stride, make_uint3((unsigned)k, 0, 0),
+                    dim3((unsigned)it.tiles_used));
+  });
+}
+const void* batch_kernel_rect(int phase) {
+  switch (phase) {
+    case BP_RECT_ANT: return (const void*)kb_rect_ant;
+    case BP_RECT_COEF: return (const void*)kb_rect_coef;
+    case BP_RECT_DATA: return (const void*)kb_rect_data;
+    case BP_RECT_CELLS: return (const void*)kb_rect_cells;
+  }
+  return nullptr;
 }
 
 }  // namespace fmap

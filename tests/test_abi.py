@@ -46,6 +46,8 @@ def test_struct_sizes_match_header(L):
     assert ctypes.sizeof(fm.binding.fmap_summary) == 32
     assert ctypes.sizeof(fm.binding.fmap_grid) == 64
     assert ctypes.sizeof(fm.binding.fmap_atoms) == 40
+    assert ctypes.sizeof(fm.binding.fmap_batch_item) == 120
+    assert ctypes.sizeof(fm.binding.fmap_server_config) == 32
 
 
 def test_status_strings(L):
