@@ -46,11 +46,13 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def make_workload(name, rank):
+def make_workload(name, rank, templates=None):
     if name == "exp16":
-        return synth.config_exp16(seed=synth.BASE_SEED + 1 + 1000 * rank)
+        kw = {} if templates is None else {"n_templates": templates}
+        return synth.config_exp16(seed=synth.BASE_SEED + 1 + 1000 * rank, **kw)
     if name == "batch_rect":
-        return synth.config_batched(window=synth.RECT, seed=synth.BASE_SEED + 2 + 1000 * rank)
+        kw = {} if templates is None else {"n_templates": templates}
+        return synth.config_batched(window=synth.RECT, seed=synth.BASE_SEED + 2 + 1000 * rank, **kw)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -183,6 +185,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--also", default="fp32,tf32,rec",
                     help="comma list of extra precisions timed beside the headline")
+    ap.add_argument("--templates", type=int, default=None,
+                    help="override the workload's template count (profiling runs)")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="requests of the serving measurement added to the line (0: skip)")
     args = ap.parse_args()
@@ -207,7 +211,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     fm.build()
 
-    inst = make_workload(args.workload, rank)
+    inst = make_workload(args.workload, rank, args.templates)
     g = inst.grid
     window = g.window
     precision = args.precision
