@@ -115,7 +115,7 @@ static int64_t units_of(const fmap_plan_s* p, const fmap_batch_item& it, int ph,
     case BP_RECT_COEF: return rect && cells > 0 ? (cells * n_ant + 255) / 256 : 0;
     case BP_RECT_DATA: return rect && work && p->n_sft > 0 ? T : 0;
     case BP_EXP_REC: return !rect && work ? g.n_tau * ((T + rec_tpb - 1) / rec_tpb) : 0;
-    case BP_RECT_CELLS: return rect && work ? rect_tiles(g) : 0;
+    case BP_RECT_CELLS: return rect && work ? rect_blocks(g, (int32_t)T) : 0;
     case BP_FLAG_COUNT:
     case BP_FLAG_WRITE: return work ? (cells * n_ant + 1023) / 1024 : 0;
     case BP_FLAG_SCAN: return work ? 1 : 0;
@@ -189,6 +189,7 @@ static fmap_status build_wave_tables(fmap_batch_s* B, Wave& wv, const Tuning& tn
           wv.dyn_smem[ph] = std::max(wv.dyn_smem[ph], exp_antenna_smem(p->n_sft));
         if (ph == BP_EXP_REC)
           wv.dyn_smem[ph] = std::max(wv.dyn_smem[ph], exp_rec_smem(p->n_sft, p->grid.n_t0));
+        if (ph == BP_RECT_CELLS) wv.dyn_smem[ph] = rect_cells_smem();
       }
     }
   }

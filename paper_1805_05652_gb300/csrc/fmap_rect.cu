@@ -24,8 +24,13 @@ struct __align__(32) D4 {
   double x, y, z, w;
 };
 
+constexpr int kTileRows = 4;    // t0 rows of a warp tile of the cells kernel
+constexpr int kTileCols = 64;   // tau columns of a warp tile
+
+// Warp tiles of the cells kernel: one partial per (template, tile).
 int64_t rect_tiles(const fmap_grid& g) {
-  return (int64_t)g.n_t0 * ((g.n_tau + kCellThreads - 1) / kCellThreads);
+  return (int64_t)((g.n_t0 + kTileRows - 1) / kTileRows) *
+         ((g.n_tau + kTileCols - 1) / kTileCols);
 }
 
 // Exclusive block scan of NC doubles per thread (sums of each thread's
@@ -184,52 +189,234 @@ __global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __
   rect_coef_body(i0tab, jend, pa, n_sft, n_t0, n_tau, n_ant, coef, blockIdx, gridDim);
 }
 
-// One thread per cell (m, n); the block covers 256 consecutive n of one row
-// and loops over the templates.  Per template: two float-pair gathers,
-// compensated differences, 2F, map store and one block partial.
-// Ill-conditioned cells (valid == 2) are left to the FP64 fix-up.
-__device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-             const Coef* __restrict__ coef, const float4* __restrict__ px, int32_t n_sft,
-             int32_t n_t0, int32_t n_tau, int32_t n_templates, int32_t shared_antenna,
-             float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
-    const uint3 bid, const dim3 gdim) {
-  __shared__ Partial scratch[kCellThreads / 32];
-  const int64_t tile = bid.x;
-  const int32_t nblk = (n_tau + kCellThreads - 1) / kCellThreads;
-  const int32_t m = (int32_t)(tile / nblk);
-  const int32_t nn = (int32_t)(tile - (int64_t)m * nblk) * kCellThreads + threadIdx.x;
-  const bool in_grid = nn < n_tau;
+// Cells, one warp per unit of (warp tile, template chunk).
+//
+// A warp tile is kTileRows t0 rows x kTileCols tau columns; lane l holds the
+// cells (m0 + r, n0 + l + 32 q), r < kTileRows, q < 2, with their
+// coefficients in registers, and runs over the kWarpTemplates templates of
+// its chunk.  For each template the prefix entries the tile needs (the rows'
+// window starts i0 and the contiguous range of window ends) are copied to
+// the warp's shared memory with cp.async one template ahead, then rebased to
+// the tile's first start b = i0(m0): Q[k] = (hi_k - hi_b) + (lo_k - lo_b).
+// A window sum is Q[j] - Q[i0]; its rounding error is relative to the sums
+// over [b, j) and [b, i0), i.e. to the window plus the few atoms between the
+// tile's rows, so the staged form is used only when those rows span at most
+// kMaxRowSpread atoms (and the entries fit the stage); other tiles difference
+// the float pairs straight from global memory.
+//
+// Per template the warp stores the 2F of its cells (coalesced 128-byte
+// rows) and writes one partial: the warp maximum by an integer max over the
+// 2F bit patterns (2F >= 0), then the lanes' exp-sums rescaled to it, the
+// lowest cell index attaining it, and the valid count.  Invalid and
+// ill-conditioned cells carry k1 = NaN, so their 2F is NaN: fmaxf drops it
+// from the maximum and the exp-sum, it never equals the maximum, and the map
+// gets 0 (the FP64 fix-up later rewrites the ill-conditioned ones).
+constexpr int kLaneCells = kTileRows * (kTileCols / 32);
+constexpr int kWarpTemplates = 16;
+constexpr int kStageEntries = 192;
+constexpr int kMaxRowSpread = 64;
+constexpr int kCellWarps = kCellThreads / 32;
+constexpr size_t kWarpStageBytes = (size_t)kStageEntries * (32 + 16);
+
+size_t rect_cells_smem() { return kWarpStageBytes * kCellWarps; }
+
+int64_t rect_blocks(const fmap_grid& g, int32_t n_templates) {
+  const int64_t units = rect_tiles(g) * ((n_templates + kWarpTemplates - 1) / kWarpTemplates);
+  return (units + kCellWarps - 1) / kCellWarps;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;\n" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ void st_stream(float* p, float v) {
+  asm volatile("st.global.cs.f32 [%0], %1;\n" ::"l"(p), "f"(v) : "memory");
+}
+
+template <bool kShared>
+__device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0tab,
+    const int32_t* __restrict__ jend, const Coef* __restrict__ coef,
+    const float4* __restrict__ px, int32_t n_sft, int32_t n_t0, int32_t n_tau,
+    int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
+    int64_t blk, unsigned char* smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t n_rg = (n_t0 + kTileRows - 1) / kTileRows;
+  const int32_t n_ct = (n_tau + kTileCols - 1) / kTileCols;
+  const int32_t n_wc = (n_templates + kWarpTemplates - 1) / kWarpTemplates;
+  const int64_t unit = blk * kCellWarps + warp;
+  if (n_wc == 0 || unit >= (int64_t)n_rg * n_ct * n_wc) return;
+  // Chunks of one tile are neighbours (coefficients shared through L1/L2);
+  // tiles run down a column of row groups (nearby prefix ranges in flight).
+  const int32_t wc = (int32_t)(unit % n_wc);
+  const int64_t wt = unit / n_wc;
+  const int32_t ct = (int32_t)(wt / n_rg), rg = (int32_t)(wt - (int64_t)ct * n_rg);
+  const int32_t m0 = rg * kTileRows, n0 = ct * kTileCols;
+  const int32_t rows = min(kTileRows, n_t0 - m0);
   const int64_t cells = (int64_t)n_t0 * n_tau;
-  const int64_t cell = (int64_t)m * n_tau + (in_grid ? nn : 0);
-  const int32_t i0 = i0tab[m];
-  const int32_t j = in_grid ? jend[cell] : i0;
   const int64_t np1 = (int64_t)n_sft + 1;
-  Coef cf = coef[cell];
-  for (int32_t tm = 0; tm < n_templates; ++tm) {
-    if (!shared_antenna) cf = coef[(int64_t)tm * cells + cell];
+  const int64_t cell0 = (int64_t)m0 * n_tau + n0 + lane;   // lane's cell in row 0, q = 0
+  const int32_t jmin = jend[(int64_t)m0 * n_tau + n0];
+  const int32_t jmax = jend[(int64_t)(m0 + rows - 1) * n_tau + min(n0 + kTileCols, n_tau) - 1];
+  const int32_t rj = jmax - jmin + 1;
+  const bool staged = kTileRows + rj <= kStageEntries &&
+                      i0tab[m0 + rows - 1] - i0tab[m0] <= kMaxRowSpread;
+
+  unsigned char* wsm = smem + (size_t)warp * kWarpStageBytes;
+  float4* raw = (float4*)wsm;                               // staged: [entry][hi, lo]
+  float4* Q = (float4*)(wsm + (size_t)kStageEntries * 32);  // staged: rebased prefixes
+  const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(raw);
+
+  const bool col0 = n0 + lane < n_tau, col1 = n0 + lane + 32 < n_tau;
+  auto in_grid = [&](int i) { return (i >> 1) < rows && ((i & 1) ? col1 : col0); };
+  auto cell_off = [&](int i) { return (int64_t)(i >> 1) * n_tau + 32 * (i & 1); };
+
+  // Staged: the lane's window ends as entries of Q, two 16-bit indices per word.
+  uint32_t jp[kLaneCells / 2];
+#pragma unroll
+  for (int r = 0; r < kTileRows; ++r) {
+    uint32_t w = 0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = 2 * r + q;
+      const int32_t j = in_grid(i) ? jend[cell0 + cell_off(i)] : jmin;
+      w |= (uint32_t)(kTileRows + (j - jmin)) << (16 * q);
+    }
+    jp[r] = staged ? w : 0u;
+  }
+
+  float k1[kLaneCells], be[kLaneCells], k2[kLaneCells];
+  int32_t nval = 0;
+  auto load_coef = [&](const Coef* __restrict__ cb) {
+    int32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < kLaneCells; ++i) {
+      Coef cf{0.0f, 0.0f, 0.0f, 0.0f};
+      if (in_grid(i)) cf = cb[cell0 + cell_off(i)];
+      const bool ok = cf.valid == 1.0f;
+      k1[i] = ok ? cf.k1 : __int_as_float(0x7fc00000);
+      be[i] = cf.beta;
+      k2[i] = cf.k2;
+      c += ok ? 1 : 0;
+    }
+    nval = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)c);
+  };
+  if (kShared) load_coef(coef);
+
+  auto issue = [&](int32_t tm) {
     const float4* pt = px + (int64_t)tm * 2 * np1;
-    const float4 hj = pt[2 * (int64_t)j], lj = pt[2 * (int64_t)j + 1];
-    const float4 hi = pt[2 * (int64_t)i0], li = pt[2 * (int64_t)i0 + 1];
-    const float fa_re = (hj.x - hi.x) + (lj.x - li.x);
-    const float fa_im = (hj.y - hi.y) + (lj.y - li.y);
-    const float fb_re = (hj.z - hi.z) + (lj.z - li.z);
-    const float fb_im = (hj.w - hi.w) + (lj.w - li.w);
-    const float v = two_f(cf, fa_re, fa_im, fb_re, fb_im);
-    const bool ok = in_grid && cf.valid == 1.0f;
-    if (map && in_grid && cf.valid != 2.0f) map[(int64_t)tm * cells + cell] = ok ? v : 0.0f;
-    Partial p = partial_empty();
-    partial_add(p, v, (int32_t)cell, ok);
-    p = partial_block_reduce<kCellThreads / 32>(p, scratch);
-    if (threadIdx.x == 0) parts[(int64_t)tm * stride + tile] = p;
+    const int n_chunk = 2 * (kTileRows + rj);
+    for (int c = lane; c < n_chunk; c += 32) {
+      const int e = c >> 1;
+      const int32_t idx = e < kTileRows ? i0tab[m0 + min(e, rows - 1)] : jmin + (e - kTileRows);
+      cp_async16(raw_s + (uint32_t)c * 16u, pt + 2 * (int64_t)idx + (c & 1));
+    }
+    cp_async_commit();
+  };
+
+  const int32_t t_begin = wc * kWarpTemplates;
+  const int32_t t_end = min(n_templates, t_begin + kWarpTemplates);
+  if (staged) issue(t_begin);
+  constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
+  for (int32_t tm = t_begin; tm < t_end; ++tm) {
+    if (!kShared) load_coef(coef + (int64_t)tm * cells);
+    if (staged) {
+      cp_async_wait_all();
+      __syncwarp();
+      const float4 hb = raw[0], lb = raw[1];
+      for (int e = lane; e < kTileRows + rj; e += 32) {
+        const float4 h = raw[2 * e], l = raw[2 * e + 1];
+        Q[e] = make_float4((h.x - hb.x) + (l.x - lb.x), (h.y - hb.y) + (l.y - lb.y),
+                           (h.z - hb.z) + (l.z - lb.z), (h.w - hb.w) + (l.w - lb.w));
+      }
+      __syncwarp();
+      if (tm + 1 < t_end) issue(tm + 1);
+    } else {
+      // Window sums of the lane's cells from the float pairs in global
+      // memory, parked in the (unused) stage buffer: raw[i * 32 + lane].
+      const float4* pt = px + (int64_t)tm * 2 * np1;
+      __syncwarp();
+#pragma unroll 1
+      for (int i = 0; i < kLaneCells; ++i) {
+        const int32_t mr = m0 + min(i >> 1, rows - 1);
+        const int32_t i0 = i0tab[mr];
+        const int32_t j = in_grid(i) ? jend[cell0 + cell_off(i)] : i0;
+        const float4 hi = pt[2 * (int64_t)i0], li = pt[2 * (int64_t)i0 + 1];
+        const float4 hj = pt[2 * (int64_t)j], lj = pt[2 * (int64_t)j + 1];
+        raw[i * 32 + lane] = make_float4((hj.x - hi.x) + (lj.x - li.x), (hj.y - hi.y) + (lj.y - li.y),
+                                         (hj.z - hi.z) + (lj.z - li.z), (hj.w - hi.w) + (lj.w - li.w));
+      }
+      __syncwarp();
+    }
+    float v[kLaneCells];
+    float mx = -1.0f;
+#pragma unroll
+    for (int i = 0; i < kLaneCells; ++i) {
+      float4 w;
+      if (staged) {
+        const float4 qi = Q[i >> 1];
+        const float4 qj = Q[(jp[i >> 1] >> (16 * (i & 1))) & 0xffffu];
+        w = make_float4(qj.x - qi.x, qj.y - qi.y, qj.z - qi.z, qj.w - qi.w);
+      } else {
+        w = raw[i * 32 + lane];
+      }
+      const Coef cf{k1[i], be[i], k2[i], 1.0f};
+      v[i] = two_f(cf, w.x, w.y, w.z, w.w);
+      mx = fmaxf(mx, v[i]);
+    }
+    if (map) {
+      float* mt = map + (int64_t)tm * cells + cell0;
+#pragma unroll
+      for (int i = 0; i < kLaneCells; ++i)
+        if (in_grid(i)) st_stream(mt + cell_off(i), fmaxf(v[i], 0.0f));
+    }
+    // 2F >= 0, so its bit pattern orders like the value; 0 marks "no valid cell".
+    const unsigned mu = __reduce_max_sync(0xffffffffu, mx >= 0.0f ? __float_as_uint(mx) + 1u : 0u);
+    if (mu == 0u) {
+      if (lane == 0) parts[(int64_t)tm * stride + wt] = partial_empty();
+      continue;
+    }
+    const float M = __uint_as_float(mu - 1u);
+    const float mc = -M * kHalfLog2e;
+    float s = 0.0f;
+    int32_t arg = kNoArg;
+#pragma unroll
+    for (int i = kLaneCells - 1; i >= 0; --i) {
+      s += fmaxf(ex2_approx(fmaf(v[i], kHalfLog2e, mc)), 0.0f);
+      if (v[i] == M) arg = (int32_t)(cell0 + cell_off(i));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    arg = (int32_t)__reduce_min_sync(0xffffffffu, (unsigned)arg);
+    if (lane == 0) {
+      Partial p;
+      p.max2F = M;
+      p.arg = arg;
+      p.sum = s;
+      p.nvalid = nval;
+      parts[(int64_t)tm * stride + wt] = p;
+    }
   }
 }
 
-__global__ void __launch_bounds__(kCellThreads)
+template <bool kShared>
+__global__ void __launch_bounds__(kCellThreads, 2)
 k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
              const Coef* __restrict__ coef, const float4* __restrict__ px, int32_t n_sft,
-             int32_t n_t0, int32_t n_tau, int32_t n_templates, int32_t shared_antenna,
-             float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
-  rect_cells_body(i0tab, jend, coef, px, n_sft, n_t0, n_tau, n_templates, shared_antenna, map, parts, stride, blockIdx, gridDim);
+             int32_t n_t0, int32_t n_tau, int32_t n_templates, float* __restrict__ map,
+             Partial* __restrict__ parts, int64_t stride) {
+  extern __shared__ __align__(16) unsigned char s_cells[];
+  rect_cells_body<kShared>(i0tab, jend, coef, px, n_sft, n_t0, n_tau, n_templates, map, parts,
+                           stride, blockIdx.x, s_cells);
 }
 
 // The paper's rectangular kernel (Sec. 3) for the data rows: one thread per
@@ -316,11 +503,20 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mark) cudaEventRecord(mark, s);
-  const int64_t tiles = rect_tiles(g);
-  *tiles_used = tiles;
-  k_rect_cells<<<(unsigned)tiles, kCellThreads, 0, s>>>(
-      p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, p->n_templates,
-      a->shared_antenna, d_2F, p->ws.partials, p->part_stride);
+  *tiles_used = rect_tiles(g);
+  const int64_t blocks = rect_blocks(g, p->n_templates);
+  if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  const void* kfn = a->shared_antenna ? (const void*)k_rect_cells<true> : (const void*)k_rect_cells<false>;
+  e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rect_cells_smem());
+  if (e != cudaSuccess) return e;
+  if (a->shared_antenna)
+    k_rect_cells<true><<<(unsigned)blocks, kCellThreads, rect_cells_smem(), s>>>(
+        p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, p->n_templates,
+        d_2F, p->ws.partials, p->part_stride);
+  else
+    k_rect_cells<false><<<(unsigned)blocks, kCellThreads, rect_cells_smem(), s>>>(
+        p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, p->n_templates,
+        d_2F, p->ws.partials, p->part_stride);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -348,12 +544,16 @@ __global__ void __launch_bounds__(kScanThreads) kb_rect_data(const BItem* __rest
                         dim3((unsigned)it.T));
   });
 }
-__global__ void __launch_bounds__(kCellThreads) kb_rect_cells(const BItem* __restrict__ items,
-                                                              BUnits u) {
+__global__ void __launch_bounds__(kCellThreads, 2) kb_rect_cells(const BItem* __restrict__ items,
+                                                                 BUnits u) {
+  extern __shared__ __align__(16) unsigned char s_cells[];
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    rect_cells_body(it.i0, it.jend, it.coef, it.px, it.n_sft, it.g.n_t0, it.g.n_tau, it.T,
-                    it.shared, it.map, it.partials, it.part_stride, make_uint3((unsigned)k, 0, 0),
-                    dim3((unsigned)it.tiles_used));
+    if (it.shared)
+      rect_cells_body<true>(it.i0, it.jend, it.coef, it.px, it.n_sft, it.g.n_t0, it.g.n_tau,
+                            it.T, it.map, it.partials, it.part_stride, k, s_cells);
+    else
+      rect_cells_body<false>(it.i0, it.jend, it.coef, it.px, it.n_sft, it.g.n_t0, it.g.n_tau,
+                             it.T, it.map, it.partials, it.part_stride, k, s_cells);
   });
 }
 const void* batch_kernel_rect(int phase) {
