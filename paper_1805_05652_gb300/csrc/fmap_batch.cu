@@ -115,14 +115,16 @@ static int64_t units_of(const fmap_plan_s* p, const fmap_batch_item& it, int ph,
     case BP_RECT_COEF: return rect && cells > 0 ? (cells * n_ant + 255) / 256 : 0;
     case BP_RECT_DATA: return rect && work && p->n_sft > 0 ? T : 0;
     case BP_EXP_REC: return !rect && work ? g.n_tau * ((T + rec_tpb - 1) / rec_tpb) : 0;
-    case BP_RECT_CELLS: return rect && work ? rect_blocks(g, (int32_t)T) : 0;
+    case BP_RECT_CELLS:
+      return rect && work ? rect_cells_blocks(g, (int32_t)T, it.atoms.shared_antenna) : 0;
     case BP_FLAG_COUNT:
     case BP_FLAG_WRITE: return work ? (cells * n_ant + 1023) / 1024 : 0;
     case BP_FLAG_SCAN: return work ? 1 : 0;
     case BP_FIXUP: return work ? (int64_t)kFixSlots * ((T + 127) / 128) : 0;
     case BP_RED_GROUPS: {
       if (!it.d_summary || T == 0) return 0;
-      const int64_t used = cells > 0 ? (rect ? rect_tiles(g) : g.n_tau) : 0;
+      const int64_t used =
+          cells > 0 ? (rect ? rect_partial_slots(g, (int32_t)T, it.atoms.shared_antenna) : g.n_tau) : 0;
       return reduce_groups_of(used + (cells > 0 ? kFixSlots : 0)) * T;
     }
     case BP_RED_FINAL: return it.d_summary && T > 0 ? T : 0;
@@ -144,7 +146,7 @@ static BItem make_bitem(const fmap_plan_s* p, const fmap_batch_item& it, uint32_
   b.cells = (int64_t)g.n_t0 * g.n_tau;
   b.n_tiles = p->n_tiles;
   b.part_stride = p->part_stride;
-  b.tiles_used = b.cells > 0 ? (g.window == FMAP_RECT ? rect_tiles(g) : g.n_tau) : 0;
+  b.tiles_used = b.cells > 0 ? (g.window == FMAP_RECT ? rect_partial_slots(g, b.T, b.shared) : g.n_tau) : 0;
   b.red_groups = reduce_groups_of(b.tiles_used + (b.cells > 0 ? kFixSlots : 0));
   b.flag_entries = b.cells * b.n_ant;
   b.log_prior = p->log_prior;
@@ -189,7 +191,8 @@ static fmap_status build_wave_tables(fmap_batch_s* B, Wave& wv, const Tuning& tn
           wv.dyn_smem[ph] = std::max(wv.dyn_smem[ph], exp_antenna_smem(p->n_sft));
         if (ph == BP_EXP_REC)
           wv.dyn_smem[ph] = std::max(wv.dyn_smem[ph], exp_rec_smem(p->n_sft, p->grid.n_t0));
-        if (ph == BP_RECT_CELLS) wv.dyn_smem[ph] = rect_cells_smem();
+        if (ph == BP_RECT_CELLS)
+          wv.dyn_smem[ph] = std::max(wv.dyn_smem[ph], rect_cells_smem(p->n_templates, B->items[i].atoms.shared_antenna));
       }
     }
   }

@@ -85,7 +85,7 @@ cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Final reduction in two levels, FP64 throughout: level 1 merges groups of
+// Final reduction in two levels, accumulated in FP64: level 1 merges groups of
 // kRedGroup tile partials per template (many blocks), level 2 merges the
 // groups of one template (one block).  Each level fixes the order of its
 // additions (per-thread strided loop, then a fixed tree), so the result is
@@ -139,7 +139,12 @@ __device__ __forceinline__ Partial64 block_merge(int64_t n, Get get) {
     for (int64_t b = tid; b < n; b += kRedThreads) {
       const Partial64 q = get(b);
       if (q.nvalid > 0) {
-        sum += q.sum * exp(0.5 * ((double)q.max2F - (double)M));
+        // Rescale factor exp((max2F - M) / 2) <= 1 in FP32 (relative error
+        // ~1e-7, the order of the FP32 tile sums themselves), accumulated in
+        // FP64; factors below 2^-126 flush to 0.
+        float f;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"((q.max2F - M) * 0.72134752044448170368f));
+        sum += q.sum * (double)f;
         if (q.max2F == M && q.arg < arg) arg = q.arg;
       }
     }

@@ -175,10 +175,11 @@ inline int32_t rel_t_entries(int32_t n_sft) { return ((n_sft + 63) / 64) * 64 + 
 
 // Tile counts of each kernel family (partials per template).
 int64_t rect_tiles(const fmap_grid& g);
-// Blocks of the rectangular cells kernel (warp units of tile x template
-// chunk, eight per block) and its dynamic shared memory.
-int64_t rect_blocks(const fmap_grid& g, int32_t n_templates);
-size_t rect_cells_smem();
+// The rectangular cells phase: partial slots per template, blocks and
+// dynamic shared memory of its kernel.
+int64_t rect_partial_slots(const fmap_grid& g, int32_t n_templates, int32_t shared_antenna);
+int64_t rect_cells_blocks(const fmap_grid& g, int32_t n_templates, int32_t shared_antenna);
+size_t rect_cells_smem(int32_t n_templates, int32_t shared_antenna);
 int64_t exp_tiles(const fmap_grid& g);
 int64_t marg_tiles(const fmap_grid& g);
 bool exp_tc_available(fmap_precision prec);

@@ -189,51 +189,63 @@ __global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __
   rect_coef_body(i0tab, jend, pa, n_sft, n_t0, n_tau, n_ant, coef, blockIdx, gridDim);
 }
 
-// Cells, one warp per unit of (warp tile, template chunk).
+// Cells.  The unit of work is a warp tile of kTileRows t0 rows x kTileCols
+// tau columns and one template; lane l holds the cells (m0 + r, n0 + l +
+// 32 q), r < kTileRows, q < 2, with their coefficients in registers, and
+// each (template, warp tile) gets one partial.
 //
-// A warp tile is kTileRows t0 rows x kTileCols tau columns; lane l holds the
-// cells (m0 + r, n0 + l + 32 q), r < kTileRows, q < 2, with their
-// coefficients in registers, and runs over the kWarpTemplates templates of
-// its chunk.  For each template the prefix entries the tile needs (the rows'
-// window starts i0 and the contiguous range of window ends) are copied to
-// the warp's shared memory with cp.async one template ahead, then rebased to
-// the tile's first start b = i0(m0): Q[k] = (hi_k - hi_b) + (lo_k - lo_b).
-// A window sum is Q[j] - Q[i0]; its rounding error is relative to the sums
-// over [b, j) and [b, i0), i.e. to the window plus the few atoms between the
-// tile's rows, so the staged form is used only when those rows span at most
-// kMaxRowSpread atoms (and the entries fit the stage); other tiles difference
-// the float pairs straight from global memory.
+// Two warp tiles stacked in rows form a group of kGroupRows rows that share
+// one rebase.  A block holds 4 / tl groups and tl template lanes per warp
+// tile (tl = 4, 2 or 1 by the template count, so small batches still fill
+// the block), and runs a chunk of kBlockTemplates templates in stages of
+// 2 tl templates.  A stage has kSlots (group, template) slots, slot w owned
+// by warp w; for each, the prefix entries of the group's row starts and of
+// its contiguous range of window ends are fetched with two bulk copies (TMA,
+// completing on the slot's mbarrier) one stage ahead, then rebased by the
+// owner warp to the group's first start b: Q[k] = (hi_k - hi_b) +
+// (lo_k - lo_b), into one of two Q buffers; the two warps of a tile pair
+// that read each other's slots meet at a named barrier.  A window sum is Q[j] - Q[i0], one FP32 difference whose
+// rounding error is relative to the sums over [b, j) and [b, i0): the
+// window plus the few atoms between the group's rows.  Blocks whose groups
+// span more than kMaxRowSpread atoms between rows, or whose entries do not
+// fit a slot, difference the float pairs straight from global memory.
 //
-// Per template the warp stores the 2F of its cells (coalesced 128-byte
-// rows) and writes one partial: the warp maximum by an integer max over the
-// 2F bit patterns (2F >= 0), then the lanes' exp-sums rescaled to it, the
-// lowest cell index attaining it, and the valid count.  Invalid and
-// ill-conditioned cells carry k1 = NaN, so their 2F is NaN: fmaxf drops it
-// from the maximum and the exp-sum, it never equals the maximum, and the map
-// gets 0 (the FP64 fix-up later rewrites the ill-conditioned ones).
+// Per template a warp stores the 2F of its cells (128-byte row pieces,
+// streaming stores) and writes one partial: the warp maximum by an integer
+// max over the 2F bit patterns (2F >= 0), the lanes' exp-sums rescaled to
+// it, the lowest cell index attaining it and the valid count.  Invalid and
+// ill-conditioned cells carry k1 = -inf (|Fa|^2 is kept >= 1e-30 so the
+// product is -inf, never NaN): the maximum ignores them, their exp-term is
+// 0, they never equal the maximum, and the map gets 0 (the FP64 fix-up later
+// rewrites the ill-conditioned ones).  The quadratic form runs on packed
+// f32x2 arithmetic (re, im pairs).
 constexpr int kLaneCells = kTileRows * (kTileCols / 32);
-constexpr int kWarpTemplates = 16;
-constexpr int kStageEntries = 192;
-constexpr int kMaxRowSpread = 64;
 constexpr int kCellWarps = kCellThreads / 32;
-constexpr size_t kWarpStageBytes = (size_t)kStageEntries * (32 + 16);
+constexpr int kGroupRows = 2 * kTileRows;
+constexpr int kSlots = 8;
+constexpr int kRowCap = 40;            // row-start entries of a slot
+constexpr int kJCap = 152;             // window-end entries of a slot
+constexpr int kSlotEntries = kRowCap + kJCap;
+constexpr int kMaxRowSpread = 32;      // atoms between a group's first and last row start
+constexpr int kBlockTemplates = 32;
+constexpr size_t kRawBytes = (size_t)kSlots * kSlotEntries * 32;
+constexpr size_t kQBytes = (size_t)kSlots * kSlotEntries * 16;
+static_assert((size_t)kCellWarps * kLaneCells * 32 * 16 <= kRawBytes,
+              "global-path window sums must fit in the stage buffer");
 
-size_t rect_cells_smem() { return kWarpStageBytes * kCellWarps; }
-
-int64_t rect_blocks(const fmap_grid& g, int32_t n_templates) {
-  const int64_t units = rect_tiles(g) * ((n_templates + kWarpTemplates - 1) / kWarpTemplates);
-  return (units + kCellWarps - 1) / kCellWarps;
+// Template lanes per warp tile.
+__host__ __device__ __forceinline__ int rect_tlanes(int32_t n_templates) {
+  return n_templates >= 4 ? 4 : (n_templates >= 2 ? 2 : 1);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+static size_t rect_cmaj_smem() { return kRawBytes + 2 * kQBytes; }
+
+static int64_t rect_cmaj_blocks(const fmap_grid& g, int32_t n_templates) {
+  const int32_t brows = kGroupRows * (4 / rect_tlanes(n_templates));
+  return (int64_t)((g.n_t0 + brows - 1) / brows) * ((g.n_tau + kTileCols - 1) / kTileCols) *
+         ((n_templates + kBlockTemplates - 1) / kBlockTemplates);
 }
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;\n" : "=f"(y) : "f"(x));
@@ -242,59 +254,126 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ void st_stream(float* p, float v) {
   asm volatile("st.global.cs.f32 [%0], %1;\n" ::"l"(p), "f"(v) : "memory");
 }
+// f32x2 pairs: .x in the low half.
+__device__ __forceinline__ void lds_pairs(uint32_t a, uint64_t& xy, uint64_t& zw) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];\n" : "=l"(xy), "=l"(zw) : "r"(a));
+}
+__device__ __forceinline__ uint64_t pk2(float x, float y) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};\n" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void up2(uint64_t a, float& x, float& y) {
+  asm("mov.b64 {%0, %1}, %2;\n" : "=f"(x), "=f"(y) : "l"(a));
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;\n" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;\n" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;\n" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;\n" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// 2F of one cell from its window sums (fa, fb as f32x2 re/im pairs);
+// nb2 = (-beta, -beta); k1 = -inf marks a cell that takes no part.
+__device__ __forceinline__ float two_f_pairs(uint64_t fa, uint64_t fb, uint64_t nb2, float k1,
+                                             float k2) {
+  const uint64_t e = fma2(nb2, fa, fb);
+  const uint64_t pa = fma2(fa, fa, pk2(1e-30f, 1e-30f));
+  const uint64_t pe = mul2(e, e);
+  float a0, a1, e0, e1;
+  up2(pa, a0, a1);
+  up2(pe, e0, e1);
+  return fmaf(k1, a0 + a1, k2 * (e0 + e1));
+}
 
 template <bool kShared>
 __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0tab,
     const int32_t* __restrict__ jend, const Coef* __restrict__ coef,
     const float4* __restrict__ px, int32_t n_sft, int32_t n_t0, int32_t n_tau,
     int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
-    int64_t blk, unsigned char* smem) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int32_t n_rg = (n_t0 + kTileRows - 1) / kTileRows;
+    uint32_t* __restrict__ err, int64_t blk, unsigned char* smem) {
+  __shared__ uint64_t s_bar[kSlots];   // one per slot: warp w owns slot w
+  __shared__ int4 s_grp[4];   // per group: first row start, row entries, first end, end entries
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tl = rect_tlanes(n_templates);
+  const int n_grp = 4 / tl;
+  const int st_t = 2 * tl;                      // templates per stage
+  const int32_t brows = kGroupRows * n_grp;
+  const int32_t n_rb = (n_t0 + brows - 1) / brows;
   const int32_t n_ct = (n_tau + kTileCols - 1) / kTileCols;
-  const int32_t n_wc = (n_templates + kWarpTemplates - 1) / kWarpTemplates;
-  const int64_t unit = blk * kCellWarps + warp;
-  if (n_wc == 0 || unit >= (int64_t)n_rg * n_ct * n_wc) return;
-  // Chunks of one tile are neighbours (coefficients shared through L1/L2);
-  // tiles run down a column of row groups (nearby prefix ranges in flight).
-  const int32_t wc = (int32_t)(unit % n_wc);
-  const int64_t wt = unit / n_wc;
-  const int32_t ct = (int32_t)(wt / n_rg), rg = (int32_t)(wt - (int64_t)ct * n_rg);
-  const int32_t m0 = rg * kTileRows, n0 = ct * kTileCols;
-  const int32_t rows = min(kTileRows, n_t0 - m0);
+  const int32_t n_bc = (n_templates + kBlockTemplates - 1) / kBlockTemplates;
+  if (n_bc == 0 || blk >= (int64_t)n_rb * n_ct * n_bc) return;   // whole block
+  // Chunks of one block tile are neighbours (coefficients shared through
+  // L2); block tiles run down a column (nearby prefix ranges in flight).
+  const int32_t bc = (int32_t)(blk % n_bc);
+  const int64_t bt = blk / n_bc;
+  const int32_t ct = (int32_t)(bt / n_rb), rb = (int32_t)(bt - (int64_t)ct * n_rb);
+  const int32_t M0 = rb * brows, n0 = ct * kTileCols;
+  const int32_t nl = min(n0 + kTileCols, n_tau) - 1;
+  const int grp = warp / (2 * tl), wi = warp - grp * 2 * tl;
+  const int half = wi / tl, tlane = wi - half * tl;
+  const int32_t m0 = M0 + grp * kGroupRows + half * kTileRows;
+  const int32_t rows = max(0, min(kTileRows, n_t0 - m0));
+  const int64_t wt = (int64_t)ct * ((n_t0 + kTileRows - 1) / kTileRows) + m0 / kTileRows;
   const int64_t cells = (int64_t)n_t0 * n_tau;
   const int64_t np1 = (int64_t)n_sft + 1;
   const int64_t cell0 = (int64_t)m0 * n_tau + n0 + lane;   // lane's cell in row 0, q = 0
-  const int32_t jmin = jend[(int64_t)m0 * n_tau + n0];
-  const int32_t jmax = jend[(int64_t)(m0 + rows - 1) * n_tau + min(n0 + kTileCols, n_tau) - 1];
-  const int32_t rj = jmax - jmin + 1;
-  const bool staged = kTileRows + rj <= kStageEntries &&
-                      i0tab[m0 + rows - 1] - i0tab[m0] <= kMaxRowSpread;
 
-  unsigned char* wsm = smem + (size_t)warp * kWarpStageBytes;
-  float4* raw = (float4*)wsm;                               // staged: [entry][hi, lo]
-  float4* Q = (float4*)(wsm + (size_t)kStageEntries * 32);  // staged: rebased prefixes
-  const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(raw);
+  fence_proxy_async_smem();   // earlier generic writes of the stage buffer vs the copies below
+  if (tid < n_grp) {
+    const int32_t mg = M0 + tid * kGroupRows;
+    const int32_t gr = min(kGroupRows, n_t0 - mg);
+    int4 e = make_int4(0, 0, 0, 0);
+    if (gr > 0) {
+      const int32_t ia = i0tab[mg], jmin = jend[(int64_t)mg * n_tau + n0];
+      e = make_int4(ia, i0tab[mg + gr - 1] - ia + 1, jmin,
+                    jend[(int64_t)(mg + gr - 1) * n_tau + nl] - jmin + 1);
+    }
+    s_grp[tid] = e;
+  }
+  if (tid < kSlots) mbar_init(&s_bar[tid], 1);
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  bool staged = true;
+  for (int k = 0; k < n_grp; ++k) {
+    const int4 e = s_grp[k];
+    if (e.y > 0 && (e.y - 1 > kMaxRowSpread || e.y > kRowCap || e.w > kJCap)) staged = false;
+  }
+  const int4 G = s_grp[grp];
 
+  const uint32_t raw_s = smem_u32(smem);
+  const uint32_t q_s0 = raw_s + (uint32_t)kRawBytes;
   const bool col0 = n0 + lane < n_tau, col1 = n0 + lane + 32 < n_tau;
   auto in_grid = [&](int i) { return (i >> 1) < rows && ((i & 1) ? col1 : col0); };
   auto cell_off = [&](int i) { return (int64_t)(i >> 1) * n_tau + 32 * (i & 1); };
 
-  // Staged: the lane's window ends as entries of Q, two 16-bit indices per word.
-  uint32_t jp[kLaneCells / 2];
+  // Byte offsets within a slot's Q of the lane's window ends and row starts.
+  uint32_t qo[kLaneCells], ro[kTileRows];
 #pragma unroll
-  for (int r = 0; r < kTileRows; ++r) {
-    uint32_t w = 0;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = 2 * r + q;
-      const int32_t j = in_grid(i) ? jend[cell0 + cell_off(i)] : jmin;
-      w |= (uint32_t)(kTileRows + (j - jmin)) << (16 * q);
-    }
-    jp[r] = staged ? w : 0u;
+  for (int i = 0; i < kLaneCells; ++i) {
+    const int32_t j = in_grid(i) ? jend[cell0 + cell_off(i)] : G.z;
+    qo[i] = 16u * (uint32_t)(kRowCap + j - G.z);
   }
+#pragma unroll
+  for (int r = 0; r < kTileRows; ++r)
+    ro[r] = rows > 0 ? 16u * (uint32_t)(i0tab[m0 + min(r, rows - 1)] - G.x) : 0u;
 
-  float k1[kLaneCells], be[kLaneCells], k2[kLaneCells];
+  float k1[kLaneCells], k2[kLaneCells];
+  uint64_t nb2[kLaneCells];
   int32_t nval = 0;
   auto load_coef = [&](const Coef* __restrict__ cb) {
     int32_t c = 0;
@@ -303,109 +382,158 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
       Coef cf{0.0f, 0.0f, 0.0f, 0.0f};
       if (in_grid(i)) cf = cb[cell0 + cell_off(i)];
       const bool ok = cf.valid == 1.0f;
-      k1[i] = ok ? cf.k1 : __int_as_float(0x7fc00000);
-      be[i] = cf.beta;
-      k2[i] = cf.k2;
+      k1[i] = ok ? cf.k1 : -INFINITY;
+      k2[i] = ok ? cf.k2 : 0.0f;
+      nb2[i] = pk2(-cf.beta, -cf.beta);
       c += ok ? 1 : 0;
     }
     nval = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)c);
   };
   if (kShared) load_coef(coef);
 
-  auto issue = [&](int32_t tm) {
-    const float4* pt = px + (int64_t)tm * 2 * np1;
-    const int n_chunk = 2 * (kTileRows + rj);
-    for (int c = lane; c < n_chunk; c += 32) {
-      const int e = c >> 1;
-      const int32_t idx = e < kTileRows ? i0tab[m0 + min(e, rows - 1)] : jmin + (e - kTileRows);
-      cp_async16(raw_s + (uint32_t)c * 16u, pt + 2 * (int64_t)idx + (c & 1));
-    }
-    cp_async_commit();
-  };
-
-  const int32_t t_begin = wc * kWarpTemplates;
-  const int32_t t_end = min(n_templates, t_begin + kWarpTemplates);
-  if (staged) issue(t_begin);
-  constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
-  for (int32_t tm = t_begin; tm < t_end; ++tm) {
-    if (!kShared) load_coef(coef + (int64_t)tm * cells);
-    if (staged) {
-      cp_async_wait_all();
-      __syncwarp();
-      const float4 hb = raw[0], lb = raw[1];
-      for (int e = lane; e < kTileRows + rj; e += 32) {
-        const float4 h = raw[2 * e], l = raw[2 * e + 1];
-        Q[e] = make_float4((h.x - hb.x) + (l.x - lb.x), (h.y - hb.y) + (l.y - lb.y),
-                           (h.z - hb.z) + (l.z - lb.z), (h.w - hb.w) + (l.w - lb.w));
-      }
-      __syncwarp();
-      if (tm + 1 < t_end) issue(tm + 1);
-    } else {
-      // Window sums of the lane's cells from the float pairs in global
-      // memory, parked in the (unused) stage buffer: raw[i * 32 + lane].
+  const int32_t t_begin = bc * kBlockTemplates;
+  const int32_t t_end = min(n_templates, t_begin + kBlockTemplates);
+  const int n_st = (t_end - t_begin + st_t - 1) / st_t;
+  // Warp w owns slot w of every stage: the slot's template is the w-th of
+  // the stage (wi), its group is the warp's own.  Lane 0 fetches the slot's
+  // prefix entries for stage st; the owner rebases them, and the two warps
+  // of a (group, template lane) pair, which read each other's slots, meet
+  // at a named barrier.
+  auto issue = [&](int st) {
+    const int32_t tm = t_begin + st * st_t + wi;
+    if (lane == 0 && G.y > 0 && tm < t_end) {
       const float4* pt = px + (int64_t)tm * 2 * np1;
-      __syncwarp();
-#pragma unroll 1
-      for (int i = 0; i < kLaneCells; ++i) {
-        const int32_t mr = m0 + min(i >> 1, rows - 1);
-        const int32_t i0 = i0tab[mr];
-        const int32_t j = in_grid(i) ? jend[cell0 + cell_off(i)] : i0;
-        const float4 hi = pt[2 * (int64_t)i0], li = pt[2 * (int64_t)i0 + 1];
-        const float4 hj = pt[2 * (int64_t)j], lj = pt[2 * (int64_t)j + 1];
-        raw[i * 32 + lane] = make_float4((hj.x - hi.x) + (lj.x - li.x), (hj.y - hi.y) + (lj.y - li.y),
-                                         (hj.z - hi.z) + (lj.z - li.z), (hj.w - hi.w) + (lj.w - li.w));
-      }
-      __syncwarp();
+      const uint32_t dst = raw_s + (uint32_t)(warp * kSlotEntries * 32);
+      mbar_arrive_expect_tx(&s_bar[warp], 32u * (uint32_t)(G.y + G.w));
+      bulk_g2s(dst, pt + 2 * (int64_t)G.x, 32u * (uint32_t)G.y, &s_bar[warp]);
+      bulk_g2s(dst + kRowCap * 32, pt + 2 * (int64_t)G.z, 32u * (uint32_t)G.w, &s_bar[warp]);
     }
-    float v[kLaneCells];
-    float mx = -1.0f;
-#pragma unroll
-    for (int i = 0; i < kLaneCells; ++i) {
-      float4 w;
+  };
+  const int pair_bar = 1 + grp * tl + tlane;   // named barrier of the warp pair (ids 1..4)
+
+  constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
+  if (staged) issue(0);
+  for (int st = 0; st < n_st; ++st) {
+    const uint32_t qs = q_s0 + (uint32_t)((st & 1) * kQBytes);
+    if (staged) {
+      if (G.y > 0 && t_begin + st * st_t + wi < t_end) {
+        mbar_wait_or_abort(&s_bar[warp], (uint32_t)(st & 1), err);
+        const uint32_t rs = raw_s + (uint32_t)(warp * kSlotEntries * 32);
+        const uint32_t qd = qs + (uint32_t)(warp * kSlotEntries * 16);
+        uint64_t hb0, hb1, lb0, lb1;
+        lds_pairs(rs, hb0, hb1);
+        lds_pairs(rs + 16, lb0, lb1);
+        const int n_live = G.y + G.w;
+        for (int k = lane; k < n_live; k += 32) {
+          const int e = k < G.y ? k : kRowCap + (k - G.y);
+          uint64_t h0, h1, l0, l1;
+          lds_pairs(rs + 32 * e, h0, h1);
+          lds_pairs(rs + 32 * e + 16, l0, l1);
+          const uint64_t q0 = add2(sub2(h0, hb0), sub2(l0, lb0));
+          const uint64_t q1 = add2(sub2(h1, hb1), sub2(l1, lb1));
+          asm volatile("st.shared.v2.b64 [%0], {%1, %2};\n" ::"r"(qd + (uint32_t)(e * 16)),
+                       "l"(q0), "l"(q1) : "memory");
+        }
+        fence_proxy_async_smem();   // the reads of raw above vs the next copy into it
+        __syncwarp();
+        if (st + 1 < n_st) issue(st + 1);
+      }
+      asm volatile("bar.sync %0, 64;" ::"r"(pair_bar) : "memory");
+    }
+    if (rows == 0) continue;   // warp below the grid: barriers only
+    for (int g = tlane; g < st_t; g += tl) {
+      const int32_t tm = t_begin + st * st_t + g;
+      if (tm >= t_end) break;
+      if (!kShared) load_coef(coef + (int64_t)tm * cells);
+      float v[kLaneCells];
       if (staged) {
-        const float4 qi = Q[i >> 1];
-        const float4 qj = Q[(jp[i >> 1] >> (16 * (i & 1))) & 0xffffu];
-        w = make_float4(qj.x - qi.x, qj.y - qi.y, qj.z - qi.z, qj.w - qi.w);
+        const uint32_t sq = qs + (uint32_t)((grp * st_t + g) * kSlotEntries * 16);
+#pragma unroll
+        for (int r = 0; r < kTileRows; ++r) {
+          uint64_t ia, ib;
+          lds_pairs(sq + ro[r], ia, ib);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int i = 2 * r + q;
+            uint64_t ja, jb;
+            lds_pairs(sq + qo[i], ja, jb);
+            v[i] = two_f_pairs(sub2(ja, ia), sub2(jb, ib), nb2[i], k1[i], k2[i]);
+          }
+        }
       } else {
-        w = raw[i * 32 + lane];
+        // Window sums from the float pairs in global memory, parked in the
+        // warp's part of the (unused) stage buffer.
+        const float4* pt = px + (int64_t)tm * 2 * np1;
+        const uint32_t wb = raw_s + (uint32_t)(warp * kLaneCells * 32 * 16 + lane * 16);
+        __syncwarp();
+#pragma unroll 1
+        for (int i = 0; i < kLaneCells; ++i) {
+          const int32_t i0 = i0tab[m0 + min(i >> 1, rows - 1)];
+          const int32_t j = in_grid(i) ? jend[cell0 + cell_off(i)] : i0;
+          const float4 hi = pt[2 * (int64_t)i0], li = pt[2 * (int64_t)i0 + 1];
+          const float4 hj = pt[2 * (int64_t)j], lj = pt[2 * (int64_t)j + 1];
+          const uint64_t a = add2(sub2(pk2(hj.x, hj.y), pk2(hi.x, hi.y)), sub2(pk2(lj.x, lj.y), pk2(li.x, li.y)));
+          const uint64_t b = add2(sub2(pk2(hj.z, hj.w), pk2(hi.z, hi.w)), sub2(pk2(lj.z, lj.w), pk2(li.z, li.w)));
+          asm volatile("st.shared.v2.b64 [%0], {%1, %2};\n" ::"r"(wb + (uint32_t)(i * 32 * 16)),
+                       "l"(a), "l"(b) : "memory");
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < kLaneCells; ++i) {
+          uint64_t a, b;
+          lds_pairs(wb + (uint32_t)(i * 32 * 16), a, b);
+          v[i] = two_f_pairs(a, b, nb2[i], k1[i], k2[i]);
+        }
       }
-      const Coef cf{k1[i], be[i], k2[i], 1.0f};
-      v[i] = two_f(cf, w.x, w.y, w.z, w.w);
-      mx = fmaxf(mx, v[i]);
-    }
-    if (map) {
-      float* mt = map + (int64_t)tm * cells + cell0;
+      const float mx = fmaxf(fmaxf(fmaxf(v[0], v[1]), fmaxf(v[2], v[3])),
+                             fmaxf(fmaxf(v[4], v[5]), fmaxf(v[6], v[7])));
+      if (map) {
+        float* mr = map + (int64_t)tm * cells + cell0;
+        if (rows == kTileRows && col1) {
 #pragma unroll
-      for (int i = 0; i < kLaneCells; ++i)
-        if (in_grid(i)) st_stream(mt + cell_off(i), fmaxf(v[i], 0.0f));
-    }
-    // 2F >= 0, so its bit pattern orders like the value; 0 marks "no valid cell".
-    const unsigned mu = __reduce_max_sync(0xffffffffu, mx >= 0.0f ? __float_as_uint(mx) + 1u : 0u);
-    if (mu == 0u) {
-      if (lane == 0) parts[(int64_t)tm * stride + wt] = partial_empty();
-      continue;
-    }
-    const float M = __uint_as_float(mu - 1u);
-    const float mc = -M * kHalfLog2e;
-    float s = 0.0f;
-    int32_t arg = kNoArg;
+          for (int r = 0; r < kTileRows; ++r, mr += n_tau) {
+            st_stream(mr, fmaxf(v[2 * r], 0.0f));
+            st_stream(mr + 32, fmaxf(v[2 * r + 1], 0.0f));
+          }
+        } else {
 #pragma unroll
-    for (int i = kLaneCells - 1; i >= 0; --i) {
-      s += fmaxf(ex2_approx(fmaf(v[i], kHalfLog2e, mc)), 0.0f);
-      if (v[i] == M) arg = (int32_t)(cell0 + cell_off(i));
-    }
+          for (int i = 0; i < kLaneCells; ++i)
+            if (in_grid(i)) st_stream(mr + cell_off(i), fmaxf(v[i], 0.0f));
+        }
+      }
+      // 2F >= 0, so its bit pattern orders like the value; 0 marks "no valid cell".
+      const unsigned mu = __reduce_max_sync(0xffffffffu, mx >= 0.0f ? __float_as_uint(mx) + 1u : 0u);
+      if (mu == 0u) {
+        if (lane == 0) parts[(int64_t)tm * stride + wt] = partial_empty();
+        continue;
+      }
+      const float M = __uint_as_float(mu - 1u);
+      const float mc = -M * kHalfLog2e;
+      float e[kLaneCells];
+      unsigned hit = 0;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-    arg = (int32_t)__reduce_min_sync(0xffffffffu, (unsigned)arg);
-    if (lane == 0) {
-      Partial p;
-      p.max2F = M;
-      p.arg = arg;
-      p.sum = s;
-      p.nvalid = nval;
-      parts[(int64_t)tm * stride + wt] = p;
+      for (int i = 0; i < kLaneCells; ++i) {
+        e[i] = ex2_approx(fmaf(v[i], kHalfLog2e, mc));
+        hit |= (v[i] == M ? 1u : 0u) << i;
+      }
+      float s = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]));
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+      const int first = __ffs(hit) - 1;
+      const int32_t arg = (int32_t)__reduce_min_sync(
+          0xffffffffu, hit ? (unsigned)(cell0 + cell_off(first)) : (unsigned)kNoArg);
+      if (lane == 0) {
+        Partial p;
+        p.max2F = M;
+        p.arg = arg;
+        p.sum = s;
+        p.nvalid = nval;
+        parts[(int64_t)tm * stride + wt] = p;
+      }
     }
   }
+  __syncthreads();   // every wait on the mbarriers is done before they are retired
+  if (tid < kSlots) mbar_inval(&s_bar[tid]);
 }
 
 template <bool kShared>
@@ -413,11 +541,17 @@ __global__ void __launch_bounds__(kCellThreads, 2)
 k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
              const Coef* __restrict__ coef, const float4* __restrict__ px, int32_t n_sft,
              int32_t n_t0, int32_t n_tau, int32_t n_templates, float* __restrict__ map,
-             Partial* __restrict__ parts, int64_t stride) {
-  extern __shared__ __align__(16) unsigned char s_cells[];
+             Partial* __restrict__ parts, int64_t stride, uint32_t* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char s_cells[];
   rect_cells_body<kShared>(i0tab, jend, coef, px, n_sft, n_t0, n_tau, n_templates, map, parts,
-                           stride, blockIdx.x, s_cells);
+                           stride, err, blockIdx.x, s_cells);
 }
+
+int64_t rect_partial_slots(const fmap_grid& g, int32_t, int32_t) { return rect_tiles(g); }
+int64_t rect_cells_blocks(const fmap_grid& g, int32_t n_templates, int32_t) {
+  return rect_cmaj_blocks(g, n_templates);
+}
+size_t rect_cells_smem(int32_t, int32_t) { return rect_cmaj_smem(); }
 
 // The paper's rectangular kernel (Sec. 3) for the data rows: one thread per
 // (template, t0 row), FP32 running sums of Fa, Fb extended as tau grows; the
@@ -503,20 +637,22 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mark) cudaEventRecord(mark, s);
-  *tiles_used = rect_tiles(g);
-  const int64_t blocks = rect_blocks(g, p->n_templates);
+  const int32_t T = p->n_templates, sh = a->shared_antenna ? 1 : 0;
+  *tiles_used = rect_partial_slots(g, T, sh);
+  const int64_t blocks = rect_cells_blocks(g, T, sh);
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-  const void* kfn = a->shared_antenna ? (const void*)k_rect_cells<true> : (const void*)k_rect_cells<false>;
-  e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rect_cells_smem());
+  const size_t smem = rect_cells_smem(T, sh);
+  const void* kfn = sh ? (const void*)k_rect_cells<true> : (const void*)k_rect_cells<false>;
+  e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (a->shared_antenna)
-    k_rect_cells<true><<<(unsigned)blocks, kCellThreads, rect_cells_smem(), s>>>(
-        p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, p->n_templates,
-        d_2F, p->ws.partials, p->part_stride);
+  if (sh)
+    k_rect_cells<true><<<(unsigned)blocks, kCellThreads, smem, s>>>(
+        p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, T,
+        d_2F, p->ws.partials, p->part_stride, p->ws.dev_err);
   else
-    k_rect_cells<false><<<(unsigned)blocks, kCellThreads, rect_cells_smem(), s>>>(
-        p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, p->n_templates,
-        d_2F, p->ws.partials, p->part_stride);
+    k_rect_cells<false><<<(unsigned)blocks, kCellThreads, smem, s>>>(
+        p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, T,
+        d_2F, p->ws.partials, p->part_stride, p->ws.dev_err);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -546,14 +682,14 @@ __global__ void __launch_bounds__(kScanThreads) kb_rect_data(const BItem* __rest
 }
 __global__ void __launch_bounds__(kCellThreads, 2) kb_rect_cells(const BItem* __restrict__ items,
                                                                  BUnits u) {
-  extern __shared__ __align__(16) unsigned char s_cells[];
+  extern __shared__ __align__(128) unsigned char s_cells[];
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     if (it.shared)
       rect_cells_body<true>(it.i0, it.jend, it.coef, it.px, it.n_sft, it.g.n_t0, it.g.n_tau,
-                            it.T, it.map, it.partials, it.part_stride, k, s_cells);
+                            it.T, it.map, it.partials, it.part_stride, it.dev_err, k, s_cells);
     else
       rect_cells_body<false>(it.i0, it.jend, it.coef, it.px, it.n_sft, it.g.n_t0, it.g.n_tau,
-                             it.T, it.map, it.partials, it.part_stride, k, s_cells);
+                             it.T, it.map, it.partials, it.part_stride, it.dev_err, k, s_cells);
   });
 }
 const void* batch_kernel_rect(int phase) {

@@ -36,6 +36,14 @@ def _instances(k, seed=2024):
                                    n_templates=T, grid=g, shared_antenna=(i % 7 != 3),
                                    injections=[(0, window, 10 * T_SFT, 30 * T_SFT, 150.0)])
         out.append(inst)
+    # many templates over shared antenna rows (the template-major cells
+    # kernel): T_sft steps (staged prefixes) and coarse t0 steps (global path)
+    g3 = Grid(-2 * T_SFT, T_SFT, 21, 2 * T_SFT, T_SFT, 90, RECT)
+    out.append(synth.make_instance(seed + 502, n_det=2, presence=0.9, n_merged=260,
+                                   n_templates=40, grid=g3,
+                                   injections=[(35, RECT, 5 * T_SFT, 40 * T_SFT, 150.0)]))
+    g4 = Grid(0, 30 * T_SFT, 17, 2 * T_SFT, 2 * T_SFT, 70, RECT)
+    out.append(synth.make_instance(seed + 503, n_merged=600, n_templates=33, grid=g4))
     # edge cases: a single SFT, an empty grid
     g1 = Grid(0, T_SFT, 10, T_SFT, T_SFT, 10, EXP)
     out.append(synth.make_instance(seed + 500, n_slots=1, n_templates=2, grid=g1))

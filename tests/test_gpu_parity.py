@@ -61,15 +61,19 @@ def test_rect_ragged_tiles_offgrid_per_template_antenna(prec):
 
 @pytest.mark.parametrize("shared", [True, False])
 @pytest.mark.parametrize("dt0_sfts", [1, 25])
-def test_rect_template_chunks(shared, dt0_sfts):
-    """37 templates (two full 16-template chunks and a ragged one) over 2
-    detectors with gaps; t0 steps of one SFT keep the prefix entries of a
-    tile in shared memory, steps of 25 SFTs spread its rows too far apart and
-    take the global float-pair path; ragged tiles in both directions."""
+@pytest.mark.parametrize("n_templates", [2, 5, 37])
+def test_rect_template_chunks(shared, dt0_sfts, n_templates):
+    """2, 5 and 37 templates (one, two or four template lanes per tile; 37
+    spans a full 32-template chunk and a ragged one) over 2 detectors with
+    gaps; t0 steps of one SFT keep a group's prefix entries in shared memory,
+    steps of 25 SFTs spread its rows too far apart and take the global
+    float-pair path; ragged tiles in both directions."""
     grid = Grid(-3 * T_SFT, dt0_sfts * T_SFT, 45, 2 * T_SFT, T_SFT, 150, RECT)
-    inj = [(5, RECT, 10 * T_SFT, 40 * T_SFT, 120.0), (33, RECT, 2 * T_SFT, 90 * T_SFT, 200.0)]
+    inj = [(1, RECT, 10 * T_SFT, 40 * T_SFT, 120.0)]
+    if n_templates > 33:
+        inj.append((33, RECT, 2 * T_SFT, 90 * T_SFT, 200.0))
     inst = synth.make_instance(43 + dt0_sfts, n_det=2, presence=0.9, n_merged=420,
-                               n_templates=37, grid=grid, shared_antenna=shared,
+                               n_templates=n_templates, grid=grid, shared_antenna=shared,
                                injections=inj)
     _parity(inst, "fp64")
 
