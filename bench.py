@@ -10,7 +10,7 @@ inputs resident in HBM (map and summaries written).  Default workload: the
 (t0, tau) cells, 1 injected template); see synth.config_exp16.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--precision bf16x3|tf32|fp32|fp64] [--workload exp16|batch_rect]
+                       [--precision bf16x3|tf32|fp32|fp64] [--workload exp16|batch_rect|uneven]
 For N > 1 run under torch.distributed.run: every rank computes its own
 workload (different seeds; weak scaling), timing is max over ranks.
 """
@@ -38,6 +38,9 @@ WORKLOADS = {
     "exp16": "exp-window F-map, 16 templates, 2000 merged SFTs (2 detectors, 10% gaps each), "
              "1000 x 1000 (t0, tau) cells at T_sft steps, tau in [T_sft, 1000 T_sft], cut at 3 tau",
     "batch_rect": "rect-window F-map, 1024 templates x 5000 SFTs, 2000 x 2000 (t0, tau) cells",
+    "uneven": "uneven batch: 4096 single-template instances, N_SFT log-uniform in [100, 8000], "
+              "N_t0, N_tau uniform in {50..2000}, rect/exp 50/50, 5% injected; one captured "
+              "graph of persistent per-phase launches (fmap_batch_run), autotuned",
 }
 L2_FLUSH_BYTES = 256 << 20
 
@@ -189,6 +192,10 @@ def main():
                     help="override the workload's template count (profiling runs)")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="requests of the serving measurement added to the line (0: skip)")
+    ap.add_argument("--instances", type=int, default=4096,
+                    help="instances of the uneven workload")
+    ap.add_argument("--budget-gb", type=float, default=24.0,
+                    help="uneven workload: batch workspace budget (GB)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -210,6 +217,15 @@ def main():
         import torch.distributed as dist  # noqa: F811
         dist.init_process_group("nccl", device_id=dev)
     fm.build()
+
+    if args.workload == "uneven":
+        result = run_uneven(args, fm, torch, dev, dist, rank, world)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        if result is not None:
+            print(json.dumps(result), flush=True)
+        return
 
     inst = make_workload(args.workload, rank, args.templates)
     g = inst.grid
@@ -376,6 +392,132 @@ def main():
         dist.destroy_process_group()
     if result is not None:
         print(json.dumps(result), flush=True)
+
+
+def uneven_instances(n, rank):
+    specs = synth.config_uneven(n_instances=n, seed=synth.BASE_SEED + 3 + 1000 * rank)
+    return [synth.instance_from_spec(sp) for sp in specs]
+
+
+def run_uneven(args, fm, torch, dev, dist, rank, world):
+    """The uneven batch through fmap_batch_plan / fmap_batch_run: all
+    instances' atoms resident, maps and summaries written, one graph launch
+    per step."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    t_build = time.perf_counter()
+    insts = uneven_instances(args.instances, rank)
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        counts = list(ex.map(lambda i: fm.fmap_count_terms(i.grid, i.t), insts))
+    terms = sum(c[0] * i.n_templates for c, i in zip(counts, insts))
+    cells = sum(i.grid.n_t0 * i.grid.n_tau * i.n_templates for i in insts)
+    items = [(i.grid, torch.from_numpy(i.t).to(dev), torch.from_numpy(i.antenna).to(dev),
+              torch.from_numpy(i.fafb).to(dev)) for i in insts]
+    t_plan = time.perf_counter()
+    batch = fm.Batch(items, want_map=True, workspace_budget=int(args.budget_gb * (1 << 30)),
+                     autotune=True)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t_plan
+    info = batch.info()
+    log(f"uneven: {len(insts)} instances built in {t_plan - t_build:.1f} s, planned+tuned in "
+        f"{plan_s:.1f} s; {info}")
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        batch.run(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        batch.run(stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    if dist:
+        dist.barrier()
+    st = batch.status(stream)
+    if st != fm.FMAP_OK:
+        raise SystemExit(f"batch status {fm.status_string(st)}")
+    per = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(per)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = terms * world * args.steps / (total_ms / 1e3)
+    result = None
+    if rank == 0:
+        peaks, peak_src = load_peaks()
+        map_bytes = cells * 4.0
+        ach = map_bytes / (ms_per_step / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "whole batch step (all phases; map bytes / step time)",
+                "peak_source": peak_src}
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = uneven_cpu_baseline(fm, insts, counts)
+        srt = sorted(per)
+        n_rect = sum(1 for i in insts if i.grid.window == synth.RECT)
+        result = {
+            "metric": "F-map (t0,tau)-SFT terms/s",
+            "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32x2",
+            "data": "synthetic",
+            "config": {"workload": "uneven", "description": WORKLOADS["uneven"],
+                       "instances": len(insts), "rect_instances": n_rect,
+                       "terms_per_step": terms, "cells_per_step": cells,
+                       "precision": "rect fp64 prefix sums; exp decayed-suffix recurrence",
+                       "waves": info["waves"], "launches_per_run": info["launches_per_run"],
+                       "workspace_bytes": info["workspace_bytes"],
+                       "autotune_occupancy": info["occupancy"],
+                       "rec_templates_per_block": info["rec_templates_per_block"],
+                       "plan_and_tune_s": plan_s,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": srt[len(srt) // 2], "max": srt[-1]},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": None,
+            "gpu_launches": int(info["launches_per_run"]) * args.steps,
+            "clocks": clocks.summary(),
+        }
+    batch.close()
+    return result
+
+
+def uneven_cpu_baseline(fm, insts, counts, target_s=12.0):
+    """The oracle (fast mode, all host cores) over the first instances of the
+    uneven batch until about target_s of CPU work."""
+    import oracle
+
+    oracle.build()
+    done, terms, t_all = 0, 0, 0.0
+    for inst, c in zip(insts, counts):
+        t0 = time.perf_counter()
+        oracle.fmap(inst.t, inst.antenna, inst.fafb, inst.grid.as_tuple(), mode="fast")
+        t_all += time.perf_counter() - t0
+        terms += c[0] * inst.n_templates
+        done += 1
+        if t_all > target_s:
+            break
+    return {"value": terms / t_all, "unit": "terms/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"first {done} of {len(insts)} instances, {terms:.3e} terms in {t_all:.2f} s"}
 
 
 def end_to_end(fm, inst, precision, terms, args):

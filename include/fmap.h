@@ -128,9 +128,10 @@ enum {
    * rearrangement of Eq. winexp's window sums: window [i0, j) =
    * e^{-(t_i0 - t0)/tau} (E[i0] - e^{-(t_j - t_i0)/tau} E[j])), one scan per
    * (tau, data column) in compensated FP32 instead of a sum per cell:
-   * O(N_tau N_SFT + cells) per template.  Needs n_sft <= 9000 and
-   * 24 n_sft + 32 n_t0 <= ~220 KB of shared memory (FMAP_ERR_UNSUPPORTED
-   * otherwise). */
+   * O(N_tau N_SFT + cells) per template.  Needs n_sft <= 9000 (one
+   * template's suffix sums in shared memory; FMAP_ERR_UNSUPPORTED otherwise);
+   * the per-cell window records of one tau are staged there too when
+   * 24 n_sft + 32 n_t0 <= ~220 KB, else recomputed per template. */
   FMAP_PLAN_EXP_RECURRENCE = 2u
 };
 

@@ -171,8 +171,8 @@ static fmap_status plan_args_ok(const fmap_grid* grid, int32_t n_sft, int32_t n_
     if (precision != FMAP_FP64)
       return arg_fail("FMAP_PLAN_EXP_RECURRENCE computes in compensated FP32 (FMAP_FP64 class)");
     if (!exp_rec_supported(n_sft, grid->n_t0)) {
-      set_error("FMAP_PLAN_EXP_RECURRENCE keeps a template's suffix sums and the per-cell data of "
-                "one tau in shared memory: n_sft or n_t0 too large");
+      set_error("FMAP_PLAN_EXP_RECURRENCE keeps a template's suffix sums in shared memory: "
+                "n_sft > 9000");
       return FMAP_ERR_UNSUPPORTED;
     }
   }

@@ -27,13 +27,24 @@ namespace fmap {
 
 constexpr int kRecThreads = 256;
 constexpr int kRecChunk = 8;        // SFTs of data prefetched per serial run of the scan
-constexpr int kRecMaxSft = 9000;    // decays + one template's suffix sums in shared memory
+constexpr int kRecMaxSft = 9000;    // decays + one template's suffix sums in shared memory (216 KB)
 
 struct __align__(16) CellRec {
   int32_t i0, j;
   float pre, tail;
   Coef cf;
 };
+
+constexpr size_t kRecSmemCap = 220 * 1024;
+
+// Shared memory of the recurrence: decays and one template's suffix sums,
+// plus the staged per-cell records of one tau when they fit.
+__host__ __device__ __forceinline__ size_t rec_smem_base(int32_t n_sft) {
+  return sizeof(float) * (2 * (size_t)n_sft + 4 * ((size_t)n_sft + 1)) + 16;
+}
+__host__ __device__ __forceinline__ bool rec_stage_cells(int32_t n_sft, int32_t n_t0) {
+  return rec_smem_base(n_sft) + sizeof(CellRec) * (size_t)n_t0 <= kRecSmemCap;
+}
 
 struct FF {
   float h, l;
@@ -130,7 +141,10 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const float c2 = (float)(-1.4426950408889634 * inv_tau);
   const int64_t tb = n > 0 ? *t_base : 0;
-  for (int32_t m = tid; m < g.n_t0; m += kRecThreads) {
+  // Per cell (t0_m, tau_n): the window, its prefactor and tail factor and the
+  // coefficients; staged once per block when they fit, else recomputed per
+  // template (large n_sft x n_t0).
+  auto cell_rec = [&](int32_t m) {
     const int64_t cell = (int64_t)m * g.n_tau + ni;
     CellRec r;
     r.i0 = i0tab[m];
@@ -144,8 +158,11 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
       r.tail = r.j < n ? rec_ex2(c2 * (float)(rel_t[r.j] - rel_t[r.i0])) : 0.0f;
     }
     r.cf = coef[cell];
-    s_cell[m] = r;
-  }
+    return r;
+  };
+  const bool stage = rec_stage_cells(n, g.n_t0);
+  if (stage)
+    for (int32_t m = tid; m < g.n_t0; m += kRecThreads) s_cell[m] = cell_rec(m);
   const int32_t t_lo = (int32_t)((int64_t)bid.y * n_templates / n_groups);
   const int32_t t_hi = (int32_t)((int64_t)(bid.y + 1) * n_templates / n_groups);
   for (int32_t tq = t_lo; tq < t_hi; ++tq) {
@@ -241,7 +258,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     Partial acc = partial_empty();
     for (int32_t m = tid; m < g.n_t0; m += kRecThreads) {
       const int64_t cell = (int64_t)m * g.n_tau + ni;
-      const CellRec r = s_cell[m];
+      const CellRec r = stage ? s_cell[m] : cell_rec(m);
       const Coef cf = shared_antenna ? r.cf : coef[(int64_t)tq * cells + cell];
       float f[4] = {0.f, 0.f, 0.f, 0.f};
       if (r.j > r.i0) {
@@ -268,9 +285,7 @@ k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base,
   exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, fafb, n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
-bool exp_rec_supported(int32_t n_sft, int32_t n_t0) {
-  return n_sft <= kRecMaxSft && exp_rec_smem(n_sft, n_t0) <= 220 * 1024;
-}
+bool exp_rec_supported(int32_t n_sft, int32_t) { return n_sft <= kRecMaxSft; }
 
 cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                            int64_t* tiles_used) {
@@ -308,8 +323,7 @@ const void* batch_kernel_exp_rec(int phase) {
   return phase == BP_EXP_REC ? (const void*)kb_exp_rec : nullptr;
 }
 size_t exp_rec_smem(int32_t n_sft, int32_t n_t0) {
-  return sizeof(float) * (2 * (size_t)n_sft + 4 * ((size_t)n_sft + 1)) + 16 +
-         sizeof(CellRec) * (size_t)n_t0;
+  return rec_smem_base(n_sft) + (rec_stage_cells(n_sft, n_t0) ? sizeof(CellRec) * (size_t)n_t0 : 0);
 }
 
 }  // namespace fmap

@@ -103,6 +103,16 @@ def test_exp_per_template_antenna(prec):
     _parity(inst, prec)
 
 
+def test_exp_recurrence_cells_not_staged():
+    """6000 SFTs and 2500 t0 rows: the recurrence's per-cell window records of
+    one tau no longer fit shared memory beside the suffix sums
+    (24 n_sft + 32 n_t0 > 220 KB) and are recomputed per template."""
+    grid = Grid(-5 * T_SFT, 2 * T_SFT, 2500, T_SFT, 2 * T_SFT, 12, EXP)
+    inst = synth.make_instance(45, n_det=1, presence=0.95, n_merged=6000, n_templates=2,
+                               grid=grid, injections=[(1, EXP, 900 * T_SFT, 9 * T_SFT, 150.0)])
+    _parity(inst, "rec")
+
+
 # ------------------------------------------------------- reductions, API ------
 
 def test_marginalise_matches_oracle():
