@@ -451,6 +451,7 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
     if st != fm.FMAP_OK:
         raise SystemExit(f"batch status {fm.status_string(st)}")
     per = [a.elapsed_time(b) for a, b in evs]
+    phases = batch.profile(stream)          # untimed: one extra run, phase by phase
     total_ms = sum(per)
     if dist:
         tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -490,6 +491,7 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": srt[len(srt) // 2], "max": srt[-1]},
+            "phases_ms": {k: v for k, v in phases.items() if v > 0},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": None,

@@ -320,11 +320,24 @@ fmap_status fmap_batch_run(fmap_batch_t* batch, fmap_stream stream);
 /* Waits for stream; returns (then clears) a latched data error or timeout of
  * any instance. */
 fmap_status fmap_batch_status(fmap_batch_t* batch, fmap_stream stream);
+/* Phases of a batch run, in launch order (FMAP_BATCH_N_PHASES entries):
+ * input checks, index tables, rect antenna prefixes, exp antenna sums and
+ * coefficients, rect coefficients, rect data prefixes, exp recurrence and
+ * cells, rect cells, three steps of the ill-conditioned cell compaction,
+ * FP64 fix-up, two reduction levels. */
+#define FMAP_BATCH_N_PHASES 14
 /* Waves, kernel launches per run, workspace bytes, chosen occupancy per phase
- * (14 entries, nullable) and templates per block of the recurrence. */
+ * (FMAP_BATCH_N_PHASES entries, nullable) and templates per block of the
+ * recurrence. */
 fmap_status fmap_batch_info(fmap_batch_t* batch, int32_t* n_waves, int64_t* launches_per_run,
                             size_t* workspace_bytes, int32_t* occupancy,
                             int32_t* rec_templates_per_block);
+/* Profiling: runs the batch once phase by phase on stream (the same launches
+ * as fmap_batch_run, outside the graph), times each with events and ADDS the
+ * device milliseconds of each phase, summed over waves, to phase_ms
+ * (FMAP_BATCH_N_PHASES entries).  Synchronous; writes the same outputs as a
+ * run; must not overlap a run of the same batch (they share work counters). */
+fmap_status fmap_batch_profile(fmap_batch_t* batch, fmap_stream stream, float* phase_ms);
 void fmap_batch_destroy(fmap_batch_t* batch);
 
 /* Host-side window bookkeeping for throughput accounting: over all cells,

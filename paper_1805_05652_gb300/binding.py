@@ -62,7 +62,7 @@ EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_
            "fmap_plan_enable_timing", "fmap_plan_read_timing", "fmap_marginalise_noalloc",
            "fmap_noalloc_scratch_bytes", "fmap_server_create", "fmap_server_destroy",
            "fmap_submit", "fmap_poll", "fmap_server_stats", "fmap_batch_plan", "fmap_batch_run",
-           "fmap_batch_status", "fmap_batch_info", "fmap_batch_destroy")
+           "fmap_batch_status", "fmap_batch_info", "fmap_batch_profile", "fmap_batch_destroy")
 FMAP_BATCH_AUTOTUNE = 1
 N_BATCH_PHASES = 14
 FMAP_N_PHASES = 4
@@ -124,7 +124,9 @@ def lib():
     L.fmap_batch_run.argtypes = [c_vp, c_vp]
     L.fmap_batch_status.argtypes = [c_vp, c_vp]
     L.fmap_batch_info.argtypes = [c_vp, P(c_i32), P(c_i64), P(c_size), c_vp, P(c_i32)]
-    for f in ("fmap_batch_plan", "fmap_batch_run", "fmap_batch_status", "fmap_batch_info"):
+    L.fmap_batch_profile.argtypes = [c_vp, c_vp, c_vp]
+    for f in ("fmap_batch_plan", "fmap_batch_run", "fmap_batch_status", "fmap_batch_info",
+              "fmap_batch_profile"):
         getattr(L, f).restype = ctypes.c_int
     L.fmap_batch_destroy.argtypes = [c_vp]
     L.fmap_batch_destroy.restype = None
@@ -350,6 +352,17 @@ def fmap_batch_info(batch: int):
                 occupancy=occ.tolist(), rec_templates_per_block=int(t.value))
 
 
+def fmap_batch_profile(batch: int, stream=None):
+    ms = np.zeros(N_BATCH_PHASES, dtype=np.float32)
+    _check(lib().fmap_batch_profile(c_vp(batch), _stream(stream), _ptr(ms)), "fmap_batch_profile")
+    return ms
+
+
+BATCH_PHASES = ("prep", "index", "rect_antenna", "exp_antenna", "rect_coef", "rect_data",
+                "exp_recurrence", "rect_cells", "flag_count", "flag_scan", "flag_write", "fixup",
+                "reduce_groups", "reduce_final")
+
+
 def fmap_batch_destroy(batch: int):
     if batch:
         lib().fmap_batch_destroy(c_vp(batch))
@@ -386,6 +399,10 @@ class Batch:
 
     def info(self):
         return fmap_batch_info(self.handle)
+
+    def profile(self, stream=None):
+        """Per-phase device milliseconds of one run (summed over waves)."""
+        return dict(zip(BATCH_PHASES, fmap_batch_profile(self.handle, stream).tolist()))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -105,7 +105,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.pa = take(sizeof(double) * 4 * np1 * (size_t)t_ant);
     L.px = take(2 * sizeof(float4) * np1 * (size_t)std::max<int32_t>(T, 1));
   } else {
-    const size_t per_tau = 3 * sizeof(double) * np1;
+    const size_t per_tau = 3 * sizeof(float2) * np1;
     int64_t chunk = (int64_t)std::max<size_t>(1, kEsufBudget / per_tau);
     chunk = std::min<int64_t>(chunk, std::max<int32_t>(g->n_tau, 1));
     L.tau_chunk = (int32_t)chunk;
@@ -227,7 +227,7 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
     w.pa = (double*)(b + L.pa);
     w.px = (float4*)(b + L.px);
   } else {
-    w.esuf = (double*)(b + L.esuf);
+    w.esuf = (float2*)(b + L.esuf);
     if (L.xop) w.xop = (void*)(b + L.xop);
   }
   p->needs_err_reset = true;

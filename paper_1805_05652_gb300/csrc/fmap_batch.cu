@@ -109,7 +109,7 @@ static int64_t units_of(const fmap_plan_s* p, const fmap_batch_item& it, int ph,
   const bool work = cells > 0 && T > 0;
   switch (ph) {
     case BP_PREP: return p->n_sft > 0 ? (rel_t_entries(p->n_sft) + 255) / 256 : 0;
-    case BP_INDEX: return cells > 0 ? (cells + 255) / 256 : 0;
+    case BP_INDEX: return cells > 0 ? g.n_t0 : 0;
     case BP_RECT_ANT: return rect && cells > 0 && p->n_sft > 0 ? n_ant : 0;
     case BP_EXP_ANT: return !rect && cells > 0 ? g.n_tau * n_ant : 0;
     case BP_RECT_COEF: return rect && cells > 0 ? (cells * n_ant + 255) / 256 : 0;
@@ -120,7 +120,7 @@ static int64_t units_of(const fmap_plan_s* p, const fmap_batch_item& it, int ph,
     case BP_FLAG_COUNT:
     case BP_FLAG_WRITE: return work ? (cells * n_ant + 1023) / 1024 : 0;
     case BP_FLAG_SCAN: return work ? 1 : 0;
-    case BP_FIXUP: return work ? (int64_t)kFixSlots * ((T + 127) / 128) : 0;
+    case BP_FIXUP: return work ? (int64_t)kFixSlots * fixup_blocks_y((int32_t)T) : 0;
     case BP_RED_GROUPS: {
       if (!it.d_summary || T == 0) return 0;
       const int64_t used =
@@ -406,22 +406,37 @@ fmap_status fmap_batch_plan(fmap_batch_t** out, const fmap_batch_item* items, in
                                                     : (double)it.grid.n_tau * it.atoms.n_sft;
     B->cost[i] = (double)it.atoms.n_sft + (cells + sums) * std::max(1, it.atoms.n_templates);
   }
-  // heaviest first, then greedy waves within the budget
+  // Shared-memory class of an instance: the exp phases launch with the
+  // largest dynamic shared memory of their wave, so instances are grouped by
+  // the number of blocks per SM that their exp kernels allow (rect instances
+  // take the first class).  Within a class, heaviest first; waves are filled
+  // greedily within the budget and never mix classes.
+  std::vector<int> cls(n_items, 0);
+  for (int32_t i = 0; i < n_items; ++i) {
+    const fmap_batch_item& it = items[i];
+    if (it.grid.window != FMAP_EXP) continue;
+    const size_t sm = std::max(exp_rec_smem(it.atoms.n_sft, it.grid.n_t0),
+                               exp_antenna_smem(it.atoms.n_sft));
+    cls[i] = sm <= (56u << 10) ? 0 : sm <= (75u << 10) ? 1 : sm <= (113u << 10) ? 2 : 3;
+  }
   std::vector<int32_t> order(n_items);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int32_t a, int32_t b) { return B->cost[a] > B->cost[b]; });
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return cls[a] != cls[b] ? cls[a] < cls[b] : B->cost[a] > B->cost[b];
+  });
   const size_t budget = workspace_budget ? workspace_budget : (size_t)8 << 30;
   size_t cur = 0, peak = 0;
+  int cur_cls = -1;
   for (int32_t i : order) {
     if (foot[i] > budget) {
       batch_free(B);
       return batch_fail("instance " + std::to_string(i) + " alone exceeds the workspace budget",
                         FMAP_ERR_NOMEM);
     }
-    if (B->waves.empty() || cur + foot[i] > budget) {
+    if (B->waves.empty() || cur + foot[i] > budget || cls[i] != cur_cls) {
       B->waves.emplace_back();
       cur = 0;
+      cur_cls = cls[i];
     }
     B->waves.back().items.push_back(i);
     cur += foot[i];
@@ -508,6 +523,34 @@ fmap_status fmap_batch_info(fmap_batch_t* B, int32_t* n_waves, int64_t* launches
     for (int ph = 0; ph < BP_COUNT; ++ph) occupancy[ph] = B->tune.occ[ph];
   if (rec_templates_per_block) *rec_templates_per_block = B->tune.rec_tpb;
   return FMAP_OK;
+}
+
+fmap_status fmap_batch_profile(fmap_batch_t* B, fmap_stream stream, float* phase_ms) {
+  set_error("");
+  if (!B || !phase_ms) return batch_fail("fmap_batch_profile: NULL argument");
+  static_assert(FMAP_BATCH_N_PHASES == BP_COUNT, "phase count");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t launches = B->n_launches;
+  std::vector<cudaEvent_t> ev(2 * B->waves.size() * BP_COUNT, nullptr);
+  for (auto& e : ev) FMAP_CUDA(cudaEventCreate(&e));
+  fmap_status st = FMAP_OK;
+  for (size_t w = 0; w < B->waves.size() && st == FMAP_OK; ++w)
+    for (int ph = 0; ph < BP_COUNT && st == FMAP_OK; ++ph) {
+      cudaEventRecord(ev[2 * (w * BP_COUNT + ph)], s);
+      st = enqueue_phase(B, (int)w, ph, B->tune.occ[ph], s);
+      cudaEventRecord(ev[2 * (w * BP_COUNT + ph) + 1], s);
+    }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st == FMAP_OK && e != cudaSuccess) st = cuda_fail(e, "fmap_batch_profile");
+  for (size_t w = 0; w < B->waves.size() && st == FMAP_OK; ++w)
+    for (int ph = 0; ph < BP_COUNT; ++ph) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * (w * BP_COUNT + ph)], ev[2 * (w * BP_COUNT + ph) + 1]);
+      phase_ms[ph] += ms;
+    }
+  for (auto& x : ev) cudaEventDestroy(x);
+  B->n_launches = launches;
+  return st;
 }
 
 void fmap_batch_destroy(fmap_batch_t* B) {

@@ -39,28 +39,64 @@ __global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc
 
 // Window index tables: i0[m] = first atom with t >= t0_m; jend[m][n] = one
 // past the last atom whose SFT ends by t0_m + L_n (L = tau or 3 tau),
-// clamped to >= i0[m], so the window holds atoms [i0, jend).
-__device__ __forceinline__ void index_body(const int64_t* __restrict__ t, int32_t n_sft, fmap_grid g,
-                        int32_t* __restrict__ i0tab, int32_t* __restrict__ jend,
-    const uint3 bid, const dim3 gdim) {
-  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
-  const int64_t lmul = (g.window == FMAP_RECT) ? 1 : 3;
-  for (int64_t c = bid.x * (int64_t)blockDim.x + threadIdx.x; c < cells;
-       c += (int64_t)gdim.x * blockDim.x) {
-    const int64_t m = c / g.n_tau, nn = c - m * g.n_tau;
-    const int64_t t0 = g.t0_min + m * g.dt0;
-    const int64_t tau = g.tau_min + nn * g.dtau;
-    const int32_t i0 = lower_bound_i64(t, n_sft, t0);
-    int32_t j = upper_bound_i64(t, n_sft, t0 + lmul * tau - g.t_sft);
-    if (j < i0) j = i0;
-    jend[c] = j;
-    if (nn == 0) i0tab[m] = i0;
+// clamped to >= i0[m], so the window holds atoms [i0, jend).  One block per
+// t0 row: the row's atom range [i0, j(n_tau - 1)) of relative times is
+// staged in shared memory (coalesced) and every tau searches it there;
+// longer ranges search the relative times in global memory.
+constexpr int kIdxThreads = 256;
+constexpr int kIdxCap = 8192;   // staged relative times (32 KB)
+
+// First index in [lo, hi) of the ascending int32 times with t > x (int64).
+__device__ __forceinline__ int32_t upper_bound_i32(const int32_t* t, int32_t lo, int32_t hi,
+                                                   int64_t x) {
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if ((int64_t)t[mid] <= x) lo = mid + 1; else hi = mid;
   }
+  return lo;
 }
 
-__global__ void k_index(const int64_t* __restrict__ t, int32_t n_sft, fmap_grid g,
-                        int32_t* __restrict__ i0tab, int32_t* __restrict__ jend) {
-  index_body(t, n_sft, g, i0tab, jend, blockIdx, gridDim);
+__device__ __forceinline__ void index_body(const int32_t* __restrict__ rel_t,
+                                           const int64_t* __restrict__ t_base, int32_t n_sft,
+                                           fmap_grid g, int32_t* __restrict__ i0tab,
+                                           int32_t* __restrict__ jend, int32_t m) {
+  __shared__ int32_t s_t[kIdxCap];
+  __shared__ int32_t s_lo, s_hi;
+  const int tid = threadIdx.x;
+  const int64_t lmul = (g.window == FMAP_RECT) ? 1 : 3;
+  const int64_t tb = n_sft > 0 ? *t_base : 0;
+  const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
+  if (tid == 0) {
+    int32_t lo = 0, hi = n_sft;   // first atom with t >= t0
+    while (lo < hi) {
+      const int32_t mid = (lo + hi) >> 1;
+      if ((int64_t)rel_t[mid] < t0rel) lo = mid + 1; else hi = mid;
+    }
+    s_lo = lo;
+    const int64_t lim = t0rel + lmul * (g.tau_min + (int64_t)(g.n_tau - 1) * g.dtau) - g.t_sft;
+    s_hi = max(lo, upper_bound_i32(rel_t, lo, n_sft, lim));
+    i0tab[m] = lo;
+  }
+  __syncthreads();
+  const int32_t i0 = s_lo, span = s_hi - s_lo;
+  const bool staged = span <= kIdxCap;
+  if (staged)
+    for (int k = tid; k < span; k += kIdxThreads) s_t[k] = rel_t[i0 + k];
+  __syncthreads();
+  int32_t* row = jend + (int64_t)m * g.n_tau;
+  for (int32_t nn = tid; nn < g.n_tau; nn += kIdxThreads) {
+    const int64_t lim = t0rel + lmul * (g.tau_min + (int64_t)nn * g.dtau) - g.t_sft;
+    row[nn] = staged ? i0 + upper_bound_i32(s_t, 0, span, lim)
+                     : upper_bound_i32(rel_t, i0, i0 + span, lim);
+  }
+  __syncthreads();   // s_t, s_lo and s_hi are reused by the block's next row
+}
+
+__global__ void __launch_bounds__(kIdxThreads)
+k_index(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n_sft,
+        fmap_grid g, int32_t* __restrict__ i0tab, int32_t* __restrict__ jend) {
+  for (int32_t m = blockIdx.x; m < g.n_t0; m += gridDim.x)
+    index_body(rel_t, t_base, n_sft, g, i0tab, jend, m);
 }
 
 cudaError_t launch_prep(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
@@ -74,12 +110,12 @@ cudaError_t launch_prep(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
 }
 
 cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
+  (void)d_t;
   const int64_t cells = (int64_t)p->grid.n_t0 * p->grid.n_tau;
   if (cells == 0) return cudaSuccess;
-  const int threads = 256;
-  const int64_t want = (cells + threads - 1) / threads;
-  const int blocks = (int)std::min<int64_t>(want, (int64_t)p->n_sm * 16);
-  k_index<<<blocks, threads, 0, s>>>(d_t, p->n_sft, p->grid, p->ws.i0, p->ws.jend);
+  const int blocks = (int)std::min<int64_t>(p->grid.n_t0, (int64_t)p->n_sm * 8);
+  k_index<<<blocks, kIdxThreads, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, p->grid, p->ws.i0,
+                                         p->ws.jend);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -329,10 +365,9 @@ __global__ void __launch_bounds__(256) kb_prep(const BItem* __restrict__ items, 
               make_uint3((unsigned)k, 0, 0), dim3((unsigned)((it.n_alloc + 255) / 256)));
   });
 }
-__global__ void __launch_bounds__(256) kb_index(const BItem* __restrict__ items, BUnits u) {
+__global__ void __launch_bounds__(kIdxThreads) kb_index(const BItem* __restrict__ items, BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    index_body(it.t, it.n_sft, it.g, it.i0, it.jend, make_uint3((unsigned)k, 0, 0),
-               dim3((unsigned)((it.cells + 255) / 256)));
+    index_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, (int32_t)k);
   });
 }
 __global__ void __launch_bounds__(kRedThreads) kb_red_groups(const BItem* __restrict__ items,

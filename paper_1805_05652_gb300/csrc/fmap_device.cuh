@@ -84,6 +84,52 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// ---- float-float (compensated FP32) arithmetic: a value is h + l with
+// |l| <= ulp(h)/2, about 2^-44 relative after a chain of operations.  Built
+// from the error-free transformations TwoSum (Knuth) and FMA-based TwoProd.
+struct FF {
+  float h, l;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.h, -p);
+  return fast_two_sum(p, e + fmaf(a.h, b.l, a.l * b.h));
+}
+__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
+  const float p = a.h * b;
+  const float e = fmaf(a.h, b, -p);
+  return fast_two_sum(p, fmaf(a.l, b, e));
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const FF s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, s.l + a.l + b.l);
+}
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.h, -b.l}); }
+// x + r e
+__device__ __forceinline__ FF ff_axpy(FF r, FF e, float x) {
+  const float p = r.h * e.h;
+  const float pe = fmaf(r.h, e.h, -p);
+  const FF s = two_sum(x, p);
+  return fast_two_sum(s.h, s.l + pe + fmaf(r.h, e.l, r.l * e.h));
+}
+__device__ __forceinline__ FF ff_shfl_down(FF v, int d) {
+  return {__shfl_down_sync(0xffffffffu, v.h, d), __shfl_down_sync(0xffffffffu, v.l, d)};
+}
+__device__ __forceinline__ FF ff_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+
 __device__ __forceinline__ Partial partial_empty() {
   Partial p;
   p.max2F = -1.0f;
@@ -194,6 +240,30 @@ __device__ __forceinline__ Coef make_coef(double A, double B, double C, int32_t 
     c.k2 = 0.0f;
     c.valid = 0.0f;
   }
+  return c;
+}
+
+// Coefficients from float-float sums: D = AB - C^2 from exact FMA products
+// (relative error ~2^-44 AB, so ~1e-11 of D for AB/D <= 100); the
+// divisions in FP32.  A cell whose D is not clearly positive or whose
+// AB/D > 100 goes to the FP64 fix-up, which decides its validity from
+// FP64 sums.
+__device__ __forceinline__ Coef make_coef_ff(FF A, FF B, FF C, int32_t count) {
+  Coef c{0.0f, 0.0f, 0.0f, 0.0f};
+  if (count < 2) return c;
+  const FF D = ff_sub(ff_mul(A, B), ff_mul(C, C));
+  const float af = A.h, cf = C.h, df = D.h;
+  if (!(af > 0.0f)) {
+    c.valid = 2.0f;
+    return c;
+  }
+  c.k1 = 2.0f / af;
+  c.beta = cf / af;
+  c.k2 = 2.0f * af / df;
+  // A B > 100 D, compared in float-float
+  const FF ab = ff_mul(A, B), d100 = ff_mul_f(D, kCondThreshold);
+  const FF gap = ff_sub(d100, ab);
+  c.valid = (df > 0.0f && gap.h + gap.l >= 0.0f) ? 1.0f : 2.0f;
   return c;
 }
 

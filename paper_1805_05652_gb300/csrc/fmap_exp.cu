@@ -43,100 +43,139 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // Decayed suffix sums of the three antenna rows for one tau, by a parallel
-// backward scan of the affine maps E -> x + rho E over the block's threads;
-// E[c * (n + 1) + i] for c = a2, b2, ab and i = 0..n (E[n] = 0).  E may be in
-// global or shared memory; the block must call it together.
+// backward scan of the affine maps E -> x + rho E over the block's threads,
+// in float-float arithmetic (the FP32 pipe; GB300's FP64 rate is 1/64 of
+// it): E[c * (n + 1) + i] for c = a2, b2, ab and i = 0..n (E[n] = 0), each as
+// an (h, l) pair.  E may be in global or shared memory; the block must call
+// it together.
 __device__ __forceinline__ void antenna_suffix(const int32_t* __restrict__ rel_t, int32_t n,
                                                const float* __restrict__ ant, const fmap_grid& g,
-                                               double tau, double* E, double* sR,
-                                               double (*sS)[kSufThreads / 32]) {
+                                               double tau, float2* E, float (*sR)[kSufThreads / 32],
+                                               float (*sS)[2][kSufThreads / 32]) {
   const double inv_s = 2.0 / tau;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int C = (n + kSufThreads - 1) / kSufThreads;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   // Decay over one gap: e^{-2 gap / tau}.  Gaps that are whole multiples k of
-  // T_sft (the usual case) take the k-th power of the one-SFT decay; others
-  // use exp directly.
-  const double rho1 = exp(-(double)g.t_sft * inv_s);
+  // T_sft (the usual case) take the k-th power of the one-SFT decay (in
+  // float-float); others use FP64 exp.
+  const FF rho1 = ff_of(exp(-(double)g.t_sft * inv_s));
   const float inv_tsft = 1.0f / (float)g.t_sft;
-  auto rho_at = [&](int i) -> double {
-    if (i + 1 >= n) return 0.0;
-    const int32_t gap = rel_t[i + 1] - rel_t[i];
+  auto rho_of_gap = [&](int32_t gap) -> FF {
     const int32_t k = __float2int_rn((float)gap * inv_tsft);
-    if (k >= 1 && k <= 64 && (int64_t)k * g.t_sft == gap) return k == 1 ? rho1 : ipow(rho1, k);
-    return exp(-(double)gap * inv_s);
+    if (k == 1 && g.t_sft == gap) return rho1;
+    if (k >= 2 && k <= 64 && (int64_t)k * g.t_sft == gap) {
+      FF acc{1.0f, 0.0f}, r = rho1;
+      for (int q = k; q; q >>= 1) {
+        if (q & 1) acc = ff_mul(acc, r);
+        r = ff_mul(r, r);
+      }
+      return acc;
+    }
+    return ff_of(exp(-(double)gap * inv_s));
   };
+  // The chunk's atoms are read kSufChunk at a time ahead of each serial run
+  // (times for the gaps and the three antenna rows), so the chain does not
+  // wait on memory per atom.
+  constexpr int kSufChunk = 8;
+  float xa[kSufChunk][3];
+  int32_t gap[kSufChunk];
+  auto load_chunk = [&](int b0) {
+#pragma unroll
+    for (int q = 0; q < kSufChunk; ++q) {
+      const int i = b0 + q;
+      const bool in = i < e0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xa[q][c] = in ? __ldg(ant + (int64_t)c * n + i) : 0.0f;
+      gap[q] = (in && i + 1 < n) ? __ldg(rel_t + i + 1) - __ldg(rel_t + i) : -1;
+    }
+  };
+  auto rho_q = [&](int q) -> FF { return gap[q] < 0 ? FF{0.0f, 0.0f} : rho_of_gap(gap[q]); };
   // phase 1: compose this thread's chunk: E[s0] = S + R E[e0]
-  double R = 1.0, S0 = 0.0, S1 = 0.0, S2 = 0.0;
-  for (int i = e0 - 1; i >= s0; --i) {
-    const double r = rho_at(i);
-    S0 = (double)ant[i] + r * S0;
-    S1 = (double)ant[n + i] + r * S1;
-    S2 = (double)ant[2 * (int64_t)n + i] + r * S2;
-    R *= r;
+  FF R{1.0f, 0.0f}, S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int b0 = s0 + ((e0 - s0 - 1) / kSufChunk) * kSufChunk; e0 > s0 && b0 >= s0;
+       b0 -= kSufChunk) {
+    load_chunk(b0);
+#pragma unroll
+    for (int q = kSufChunk - 1; q >= 0; --q) {
+      if (b0 + q >= e0) continue;
+      const FF r = rho_q(q);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) S[c] = ff_axpy(r, S[c], xa[q][c]);
+      R = ff_mul(r, R);
+    }
   }
   // phase 2: inclusive suffix composition within the warp (self o later)
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const double Ro = __shfl_down_sync(0xffffffffu, R, d);
-    const double So0 = __shfl_down_sync(0xffffffffu, S0, d);
-    const double So1 = __shfl_down_sync(0xffffffffu, S1, d);
-    const double So2 = __shfl_down_sync(0xffffffffu, S2, d);
+    const FF Ro = ff_shfl_down(R, d);
+    FF So[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) So[c] = ff_shfl_down(S[c], d);
     if (lane + d < 32) {
-      S0 += R * So0;
-      S1 += R * So1;
-      S2 += R * So2;
-      R *= Ro;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) S[c] = ff_add(S[c], ff_mul(R, So[c]));
+      R = ff_mul(R, Ro);
     }
   }
   // exclusive within the warp: composition of lanes lane+1 .. 31
-  double hR = __shfl_down_sync(0xffffffffu, R, 1);
-  double hS0 = __shfl_down_sync(0xffffffffu, S0, 1);
-  double hS1 = __shfl_down_sync(0xffffffffu, S1, 1);
-  double hS2 = __shfl_down_sync(0xffffffffu, S2, 1);
+  FF hR = ff_shfl_down(R, 1), hS[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) hS[c] = ff_shfl_down(S[c], 1);
   if (lane == 31) {
-    hR = 1.0;
-    hS0 = hS1 = hS2 = 0.0;
+    hR = {1.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) hS[c] = {0.0f, 0.0f};
   }
   if (lane == 0) {
-    sR[warp] = R;
-    sS[0][warp] = S0;
-    sS[1][warp] = S1;
-    sS[2][warp] = S2;
+    sR[0][warp] = R.h;
+    sR[1][warp] = R.l;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      sS[c][0][warp] = S[c].h;
+      sS[c][1][warp] = S[c].l;
+    }
   }
   __syncthreads();
   // composition of the later warps, applied to E[N] = 0: only its S matters
-  double lS0 = 0.0, lS1 = 0.0, lS2 = 0.0;
+  FF lS[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   for (int v = kSufThreads / 32 - 1; v > warp; --v) {
-    lS0 = sS[0][v] + sR[v] * lS0;
-    lS1 = sS[1][v] + sR[v] * lS1;
-    lS2 = sS[2][v] + sR[v] * lS2;
+    const FF Rv{sR[0][v], sR[1][v]};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lS[c] = ff_add(FF{sS[c][0][v], sS[c][1][v]}, ff_mul(Rv, lS[c]));
   }
-  double e_0 = hS0 + hR * lS0, e_1 = hS1 + hR * lS1, e_2 = hS2 + hR * lS2;
+  FF e[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) e[c] = ff_add(hS[c], ff_mul(hR, lS[c]));
   // phase 3: recompute the chunk from its carry E[e0] and store
   const int64_t np1 = (int64_t)n + 1;
-  for (int i = e0 - 1; i >= s0; --i) {
-    const double r = rho_at(i);
-    e_0 = (double)ant[i] + r * e_0;
-    e_1 = (double)ant[n + i] + r * e_1;
-    e_2 = (double)ant[2 * (int64_t)n + i] + r * e_2;
-    E[i] = e_0;
-    E[np1 + i] = e_1;
-    E[2 * np1 + i] = e_2;
+  for (int b0 = s0 + ((e0 - s0 - 1) / kSufChunk) * kSufChunk; e0 > s0 && b0 >= s0;
+       b0 -= kSufChunk) {
+    load_chunk(b0);
+#pragma unroll
+    for (int q = kSufChunk - 1; q >= 0; --q) {
+      const int i = b0 + q;
+      if (i >= e0) continue;
+      const FF r = rho_q(q);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        e[c] = ff_axpy(r, e[c], xa[q][c]);
+        E[c * np1 + i] = make_float2(e[c].h, e[c].l);
+      }
+    }
   }
   if (tid == 0) {
-    E[n] = 0.0;
-    E[np1 + n] = 0.0;
-    E[2 * np1 + n] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) E[c * np1 + n] = make_float2(0.0f, 0.0f);
   }
 }
 
 // Global-memory suffix sums for one tau of a tau chunk (long data sets).
 __global__ void __launch_bounds__(kSufThreads)
 k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restrict__ ant,
-             fmap_grid g, int32_t n_lo, double* __restrict__ esuf) {
-  __shared__ double sR[kSufThreads / 32];
-  __shared__ double sS[3][kSufThreads / 32];
+             fmap_grid g, int32_t n_lo, float2* __restrict__ esuf) {
+  __shared__ float sR[2][kSufThreads / 32];
+  __shared__ float sS[3][2][kSufThreads / 32];
   const int ni = blockIdx.x;
   const double tau = (double)(g.tau_min + (int64_t)(n_lo + ni) * g.dtau);
   antenna_suffix(rel_t, n, ant, g, tau, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
@@ -146,9 +185,9 @@ k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restri
 __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t, int32_t n,
                                               const fmap_grid& g, int64_t m, int64_t nn,
                                               int32_t i0, int32_t j, int64_t t_base,
-                                              const double* E) {
+                                              const float2* E) {
   const int32_t count = j - i0;
-  double A = 0.0, B = 0.0, C = 0.0;
+  FF S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   if (count > 0) {
     const double tau = (double)(g.tau_min + nn * g.dtau);
     const int64_t t0rel = g.t0_min + m * g.dt0 - t_base;
@@ -158,13 +197,15 @@ __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t,
     // accurate enough for both.
     const float c2 = (float)(-2.8853900817779268 / tau);   // -2 log2(e) / tau
     const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
-    const double pre = d0 == 0 ? 1.0 : (double)ex2_approx(c2 * (float)d0);
-    const double tail = (j < n) ? (double)ex2_approx(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0;
-    A = pre * (E[i0] - tail * E[j]);
-    B = pre * (E[np1 + i0] - tail * E[np1 + j]);
-    C = pre * (E[2 * np1 + i0] - tail * E[2 * np1 + j]);
+    const float pre = d0 == 0 ? 1.0f : ex2_approx(c2 * (float)d0);
+    const float tail = (j < n) ? ex2_approx(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 a = E[c * np1 + i0], b = E[c * np1 + j];
+      S[c] = ff_mul_f(ff_sub(FF{a.x, a.y}, ff_mul_f(FF{b.x, b.y}, tail)), pre);
+    }
   }
-  return make_coef(A, B, C, count);
+  return make_coef_ff(S[0], S[1], S[2], count);
 }
 
 // Fused antenna step for data sets that fit shared memory: one block per
@@ -175,9 +216,9 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
               fmap_grid g, const float* __restrict__ antenna, const int32_t* __restrict__ i0tab,
               const int32_t* __restrict__ jend, Coef* __restrict__ coef,
     const uint3 bid, const dim3 gdim) {
-  extern __shared__ double s_E[];
-  __shared__ double sR[kSufThreads / 32];
-  __shared__ double sS[3][kSufThreads / 32];
+  extern __shared__ float2 s_E[];
+  __shared__ float sR[2][kSufThreads / 32];
+  __shared__ float sS[3][2][kSufThreads / 32];
   const int ni = bid.x, ta = bid.y;
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
@@ -198,13 +239,13 @@ k_exp_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_b
   exp_antenna_body(rel_t, t_base, n, g, antenna, i0tab, jend, coef, blockIdx, gridDim);
 }
 
-constexpr int kAntennaSmemMaxSft = 9000;   // 3 x (n + 1) doubles <= 216 KB
+constexpr int kAntennaSmemMaxSft = 9000;   // 3 x (n + 1) float pairs <= 216 KB
 
 // Per-cell coefficients of the cells of one tau chunk (global suffix sums).
 __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base,
                            int32_t n, fmap_grid g, int32_t n_lo, int32_t n_chunk,
                            const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-                           const double* __restrict__ esuf, Coef* __restrict__ coef) {
+                           const float2* __restrict__ esuf, Coef* __restrict__ coef) {
   const int64_t total = (int64_t)g.n_t0 * n_chunk;
   const int64_t np1 = (int64_t)n + 1;
   const int64_t tb = n > 0 ? *t_base : 0;
@@ -225,7 +266,7 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
   const int n_ant = a->shared_antenna ? 1 : p->n_templates;
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   if (p->n_sft <= kAntennaSmemMaxSft) {
-    const size_t smem = sizeof(double) * 3 * ((size_t)p->n_sft + 1);
+    const size_t smem = exp_antenna_smem(p->n_sft);
     cudaFuncSetAttribute(k_exp_antenna, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_exp_antenna<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), kSufThreads, smem, s>>>(
         p->ws.rel_t, p->ws.t_base, p->n_sft, g, a->antenna, p->ws.i0, p->ws.jend, p->ws.coef);
@@ -378,7 +419,7 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
 
 
 // ---- persistent multi-instance dispatcher (uneven batches) ----
-__global__ void __launch_bounds__(kSufThreads) kb_exp_ant(const BItem* __restrict__ items,
+__global__ void __launch_bounds__(kSufThreads, 3) kb_exp_ant(const BItem* __restrict__ items,
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.antenna, it.i0, it.jend, it.coef,
@@ -389,7 +430,7 @@ __global__ void __launch_bounds__(kSufThreads) kb_exp_ant(const BItem* __restric
 const void* batch_kernel_exp(int phase) {
   return phase == BP_EXP_ANT ? (const void*)kb_exp_ant : nullptr;
 }
-size_t exp_antenna_smem(int32_t n_sft) { return sizeof(double) * 3 * ((size_t)n_sft + 1); }
+size_t exp_antenna_smem(int32_t n_sft) { return sizeof(float2) * 3 * ((size_t)n_sft + 1); }
 bool exp_antenna_fits(int32_t n_sft) { return n_sft <= kAntennaSmemMaxSft; }
 
 }  // namespace fmap

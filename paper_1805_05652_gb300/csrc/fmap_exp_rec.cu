@@ -46,49 +46,6 @@ __host__ __device__ __forceinline__ bool rec_stage_cells(int32_t n_sft, int32_t 
   return rec_smem_base(n_sft) + sizeof(CellRec) * (size_t)n_t0 <= kRecSmemCap;
 }
 
-struct FF {
-  float h, l;
-};
-
-__device__ __forceinline__ FF two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ FF fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ FF ff_mul(FF a, FF b) {
-  const float p = a.h * b.h;
-  const float e = fmaf(a.h, b.h, -p);
-  return fast_two_sum(p, e + fmaf(a.h, b.l, a.l * b.h));
-}
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  const FF s = two_sum(a.h, b.h);
-  return fast_two_sum(s.h, s.l + a.l + b.l);
-}
-// x + r e
-__device__ __forceinline__ FF ff_axpy(FF r, FF e, float x) {
-  const float p = r.h * e.h;
-  const float pe = fmaf(r.h, e.h, -p);
-  const FF s = two_sum(x, p);
-  return fast_two_sum(s.h, s.l + pe + fmaf(r.h, e.l, r.l * e.h));
-}
-__device__ __forceinline__ FF ff_shfl_down(FF v, int d) {
-  return {__shfl_down_sync(0xffffffffu, v.h, d), __shfl_down_sync(0xffffffffu, v.l, d)};
-}
-
-__device__ __forceinline__ double rec_ipow(double r, int k) {
-  double acc = 1.0;
-  while (k) {
-    if (k & 1) acc *= r;
-    r *= r;
-    k >>= 1;
-  }
-  return acc;
-}
-
 __device__ __forceinline__ float rec_ex2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -118,22 +75,30 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   const int64_t np1 = (int64_t)n + 1;
   // Decays of this tau, once for all the block's templates: whole multiples k
   // of T_sft take the k-th power of the one-SFT decay, other gaps use exp.
+  // (float-float powers of the one-SFT decay; FP64 exp only off the lattice)
   {
-    const double rho1 = exp(-(double)g.t_sft * inv_tau);
+    const FF rho1 = ff_of(exp(-(double)g.t_sft * inv_tau));
     const float inv_tsft = 1.0f / (float)g.t_sft;
     for (int i = tid; i < n; i += kRecThreads) {
-      double r = 0.0;
+      FF r{0.0f, 0.0f};
       if (i + 1 < n) {
         const int32_t gap = rel_t[i + 1] - rel_t[i];
         const int32_t k = __float2int_rn((float)gap * inv_tsft);
-        if (k >= 1 && k <= 64 && (int64_t)k * g.t_sft == gap)
-          r = k == 1 ? rho1 : rec_ipow(rho1, k);
-        else
-          r = exp(-(double)gap * inv_tau);
+        if (k == 1 && gap == g.t_sft) {
+          r = rho1;
+        } else if (k >= 2 && k <= 64 && (int64_t)k * g.t_sft == gap) {
+          FF acc{1.0f, 0.0f}, p = rho1;
+          for (int q = k; q; q >>= 1) {
+            if (q & 1) acc = ff_mul(acc, p);
+            p = ff_mul(p, p);
+          }
+          r = acc;
+        } else {
+          r = ff_of(exp(-(double)gap * inv_tau));
+        }
       }
-      const float h = (float)r;
-      s_rh[i] = h;
-      s_rl[i] = (float)(r - (double)h);
+      s_rh[i] = r.h;
+      s_rl[i] = r.l;
     }
   }
   const int C = (n + kRecThreads - 1) / kRecThreads;
@@ -310,7 +275,7 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
 
 
 // ---- persistent multi-instance dispatcher (uneven batches) ----
-__global__ void __launch_bounds__(kRecThreads) kb_exp_rec(const BItem* __restrict__ items,
+__global__ void __launch_bounds__(kRecThreads, 3) kb_exp_rec(const BItem* __restrict__ items,
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     exp_rec_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared, it.fafb,

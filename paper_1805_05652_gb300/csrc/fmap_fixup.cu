@@ -23,6 +23,7 @@ namespace fmap {
 constexpr int kFlagBlock = 1024;
 constexpr int kFixThreads = 128;
 constexpr int kFixWeights = 256;
+constexpr int kFixCellModeT = 32;   // below: threads over entries, not templates
 
 // Per block of kFlagBlock entries: number of entries with valid == 2.
 __device__ __forceinline__ void flag_count_body(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt,
@@ -175,6 +176,79 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
   if (active_t) parts[(int64_t)tq * stride + slot0 + bid.x] = acc;
 }
 
+// Few templates (T < kFixCellModeT): threads over the listed entries
+// instead of templates.  Block (b, tq): entries [b n / G, (b + 1) n / G) for
+// template tq, one thread per entry summing its own window in FP64 (the
+// windows of ill-conditioned cells are a few SFTs long), then a fixed-order
+// block reduction of the thread partials.
+__device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ list,
+        const int32_t* __restrict__ n_flag, int32_t G, int32_t shared_antenna,
+        const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n_sft,
+        fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+        const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
+        float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
+        int32_t b, int32_t tq) {
+  __shared__ Partial scratch[kFixThreads / 32];
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const int64_t cap = shared_antenna ? cells : cells * n_templates;
+  const int64_t n = min((int64_t)*n_flag, cap);
+  const int64_t lo = (int64_t)b * n / G, hi = (int64_t)(b + 1) * n / G;
+  const int64_t tb = n_sft > 0 ? *t_base : 0;
+  const float* ant = antenna + (int64_t)(shared_antenna ? 0 : tq) * 3 * n_sft;
+  const float* x = fafb + (int64_t)tq * 4 * n_sft;
+  Partial acc = partial_empty();
+  for (int64_t k = lo + threadIdx.x; k < hi; k += kFixThreads) {
+    const int64_t entry = list[k];
+    const int64_t cell = shared_antenna ? entry : entry % cells;
+    if (!shared_antenna && entry / cells != tq) continue;
+    const int32_t m = (int32_t)(cell / g.n_tau), nn = (int32_t)(cell % g.n_tau);
+    const int32_t i0 = i0tab[m], j = jend[cell];
+    const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
+    const double inv_tau = 1.0 / (double)(g.tau_min + (int64_t)nn * g.dtau);
+    double A = 0, B = 0, C = 0, far = 0, fai = 0, fbr = 0, fbi = 0;
+    for (int32_t a = i0; a < j; ++a) {
+      const double w = (g.window == FMAP_RECT) ? 1.0
+                                                : exp(-(double)((int64_t)rel_t[a] - t0rel) * inv_tau);
+      const double w2 = w * w;
+      A += w2 * (double)ant[a];
+      B += w2 * (double)ant[n_sft + a];
+      C += w2 * (double)ant[2 * (int64_t)n_sft + a];
+      far += w * (double)x[a];
+      fai += w * (double)x[n_sft + a];
+      fbr += w * (double)x[2 * (int64_t)n_sft + a];
+      fbi += w * (double)x[3 * (int64_t)n_sft + a];
+    }
+    const double D = A * B - C * C;
+    const bool ok = (j - i0) >= 2 && D > 0.0;
+    double v = 0.0;
+    if (ok)
+      v = 2.0 * (B * (far * far + fai * fai) + A * (fbr * fbr + fbi * fbi) -
+                 2.0 * C * (far * fbr + fai * fbi)) / D;
+    if (map) map[(int64_t)tq * cells + cell] = (float)v;
+    partial_add(acc, (float)v, (int32_t)cell, ok);
+  }
+  acc = partial_block_reduce<kFixThreads / 32>(acc, scratch);
+  if (threadIdx.x == 0) parts[(int64_t)tq * stride + slot0 + b] = acc;
+}
+
+__global__ void __launch_bounds__(kFixThreads)
+k_fixup_cells(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
+              int32_t shared_antenna, const int32_t* __restrict__ rel_t,
+              const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g,
+              const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+              const float* __restrict__ antenna, const float* __restrict__ fafb,
+              int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
+              int64_t stride, int64_t slot0) {
+  fixup_cells_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, i0tab, jend, antenna,
+                   fafb, n_templates, map, parts, stride, slot0, blockIdx.x, blockIdx.y);
+}
+
+// Fix-up blocks of one plan (the y extent: templates, or template blocks).
+int64_t fixup_blocks_y(int32_t n_templates) {
+  return n_templates < kFixCellModeT ? n_templates
+                                     : (n_templates + kFixThreads - 1) / kFixThreads;
+}
+
 __global__ void __launch_bounds__(kFixThreads)
 k_fixup(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
         int32_t shared_antenna, const int32_t* __restrict__ rel_t,
@@ -196,12 +270,19 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
   k_flag_scan<<<1, 1024, 0, s>>>(p->ws.flag_blocks, n_blocks, p->ws.n_flag);
   k_flag_write<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.coef, n_entries, p->ws.flag_blocks,
                                                          p->ws.flag_list);
-  dim3 grid((unsigned)kFixSlots, (unsigned)((p->n_templates + kFixThreads - 1) / kFixThreads));
-  k_fixup<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
-                                       a->shared_antenna, p->ws.rel_t, p->ws.t_base, p->n_sft,
-                                       p->grid, p->ws.i0, p->ws.jend, a->antenna, a->fafb,
-                                       p->n_templates, d_2F, p->ws.partials, p->part_stride,
-                                       p->n_tiles);
+  dim3 grid((unsigned)kFixSlots, (unsigned)fixup_blocks_y(p->n_templates));
+  if (p->n_templates < kFixCellModeT)
+    k_fixup_cells<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
+                                               a->shared_antenna, p->ws.rel_t, p->ws.t_base,
+                                               p->n_sft, p->grid, p->ws.i0, p->ws.jend,
+                                               a->antenna, a->fafb, p->n_templates, d_2F,
+                                               p->ws.partials, p->part_stride, p->n_tiles);
+  else
+    k_fixup<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
+                                         a->shared_antenna, p->ws.rel_t, p->ws.t_base, p->n_sft,
+                                         p->grid, p->ws.i0, p->ws.jend, a->antenna, a->fafb,
+                                         p->n_templates, d_2F, p->ws.partials, p->part_stride,
+                                         p->n_tiles);
   p->launches += 4;
   return cudaGetLastError();
 }
@@ -231,10 +312,17 @@ __global__ void __launch_bounds__(kFlagBlock) kb_flag_write(const BItem* __restr
 __global__ void __launch_bounds__(kFixThreads) kb_fixup(const BItem* __restrict__ items,
                                                         BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft, it.g,
-               it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials, it.part_stride,
-               it.n_tiles, make_uint3((unsigned)(k % kFixSlots), (unsigned)(k / kFixSlots), 0),
-               dim3((unsigned)kFixSlots, (unsigned)((it.T + kFixThreads - 1) / kFixThreads)));
+    if (it.T < kFixCellModeT)
+      fixup_cells_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base,
+                       it.n_sft, it.g, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
+                       it.partials, it.part_stride, it.n_tiles, (int32_t)(k % kFixSlots),
+                       (int32_t)(k / kFixSlots));
+    else
+      fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft,
+                 it.g, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,
+                 it.part_stride, it.n_tiles,
+                 make_uint3((unsigned)(k % kFixSlots), (unsigned)(k / kFixSlots), 0),
+                 dim3((unsigned)kFixSlots, (unsigned)((it.T + kFixThreads - 1) / kFixThreads)));
   });
 }
 const void* batch_kernel_fixup(int phase) {

@@ -74,7 +74,7 @@ struct Workspace {
   double* pa = nullptr;          // [T_ant][N+1][4] FP64 antenna prefix (a2, b2, ab, pad)
   float4* px = nullptr;          // [T][N+1][2] float-float data prefix (hi4, lo4)
   // exp
-  double* esuf = nullptr;        // [tau_chunk][3][N+1] FP64 decayed suffix sums
+  float2* esuf = nullptr;        // [tau_chunk][3][N+1] float-float decayed suffix sums
   // tensor-core operands
   void* xop = nullptr;           // split X operands (layout per precision)
   // host-API staging
@@ -175,6 +175,8 @@ inline int32_t rel_t_entries(int32_t n_sft) { return ((n_sft + 63) / 64) * 64 + 
 
 // Tile counts of each kernel family (partials per template).
 int64_t rect_tiles(const fmap_grid& g);
+// y extent of the FP64 fix-up grid (kFixSlots x this) for a template count.
+int64_t fixup_blocks_y(int32_t n_templates);
 // The rectangular cells phase: partial slots per template, blocks and
 // dynamic shared memory of its kernel.
 int64_t rect_partial_slots(const fmap_grid& g, int32_t n_templates, int32_t shared_antenna);

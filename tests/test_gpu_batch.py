@@ -106,6 +106,26 @@ def test_batch_equals_single_plans_and_oracle(insts, budget, autotune):
     b.close()
 
 
+def test_batch_profile_times_phases_and_matches_run(insts):
+    devs = [_dev(i) for i in insts[:12]]
+    b = fm.Batch(devs, want_map=True, workspace_budget=3 << 20, autotune=False)
+    b.run()
+    assert b.status() == fm.FMAP_OK
+    ref = [m.cpu().numpy().copy() for m in b.maps]
+    launches = b.info()["launches_per_run"]
+    for m in b.maps:
+        m.fill_(-7.0)
+    ph = b.profile()
+    torch.cuda.synchronize()
+    assert b.status() == fm.FMAP_OK
+    assert set(ph) == set(fm.binding.BATCH_PHASES)
+    assert all(v >= 0.0 for v in ph.values()) and ph["index"] > 0.0
+    assert b.info()["launches_per_run"] == launches
+    for k, m in enumerate(b.maps):
+        assert np.array_equal(m.cpu().numpy(), ref[k]), k
+    b.close()
+
+
 def test_batch_reports_bad_timestamps(insts):
     inst = insts[1]
     grid, t, a, x = _dev(inst)
