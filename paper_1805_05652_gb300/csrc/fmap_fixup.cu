@@ -23,7 +23,7 @@ namespace fmap {
 constexpr int kFlagBlock = 1024;
 constexpr int kFixThreads = 128;
 constexpr int kFixWeights = 256;
-constexpr int kFixCellModeT = 32;   // below: threads over entries, not templates
+constexpr int kFixCellModeT = 8;    // below: threads over entries, not templates
 
 // Per block of kFlagBlock entries: number of entries with valid == 2.
 __device__ __forceinline__ void flag_count_body(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt,
