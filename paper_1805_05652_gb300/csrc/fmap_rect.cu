@@ -227,7 +227,7 @@ constexpr int kRowCap = 40;            // row-start entries of a slot
 constexpr int kJCap = 152;             // window-end entries of a slot
 constexpr int kSlotEntries = kRowCap + kJCap;
 constexpr int kMaxRowSpread = 32;      // atoms between a group's first and last row start
-constexpr int kBlockTemplates = 32;
+constexpr int kBlockTemplates = 128;
 constexpr size_t kRawBytes = (size_t)kSlots * kSlotEntries * 32;
 constexpr size_t kQBytes = (size_t)kSlots * kSlotEntries * 16;
 static_assert((size_t)kCellWarps * kLaneCells * 32 * 16 <= kRawBytes,
@@ -290,9 +290,9 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
 // 2F of one cell from its window sums (fa, fb as f32x2 re/im pairs);
 // nb2 = (-beta, -beta); k1 = -inf marks a cell that takes no part.
 __device__ __forceinline__ float two_f_pairs(uint64_t fa, uint64_t fb, uint64_t nb2, float k1,
-                                             float k2) {
+                                             float k2, uint64_t tiny2) {
   const uint64_t e = fma2(nb2, fa, fb);
-  const uint64_t pa = fma2(fa, fa, pk2(1e-30f, 1e-30f));
+  const uint64_t pa = fma2(fa, fa, tiny2);
   const uint64_t pe = mul2(e, e);
   float a0, a1, e0, e1;
   up2(pa, a0, a1);
@@ -319,9 +319,11 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
   if (n_bc == 0 || blk >= (int64_t)n_rb * n_ct * n_bc) return;   // whole block
   // Chunks of one block tile are neighbours (coefficients shared through
   // L2); block tiles run down a column (nearby prefix ranges in flight).
-  const int32_t bc = (int32_t)(blk % n_bc);
-  const int64_t bt = blk / n_bc;
-  const int32_t ct = (int32_t)(bt / n_rb), rb = (int32_t)(bt - (int64_t)ct * n_rb);
+  // (The block count fits 31 bits: the launch checks it.)
+  const uint32_t ub = (uint32_t)blk;
+  const int32_t bc = (int32_t)(ub % (uint32_t)n_bc);
+  const uint32_t bt = ub / (uint32_t)n_bc;
+  const int32_t ct = (int32_t)(bt / (uint32_t)n_rb), rb = (int32_t)(bt - (uint32_t)ct * (uint32_t)n_rb);
   const int32_t M0 = rb * brows, n0 = ct * kTileCols;
   const int32_t nl = min(n0 + kTileCols, n_tau) - 1;
   const int grp = warp / (2 * tl), wi = warp - grp * 2 * tl;
@@ -412,6 +414,7 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
   const int pair_bar = 1 + grp * tl + tlane;   // named barrier of the warp pair (ids 1..4)
 
   constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
+  const uint64_t tiny2 = pk2(1e-30f, 1e-30f);
   if (staged) issue(0);
   for (int st = 0; st < n_st; ++st) {
     const uint32_t qs = q_s0 + (uint32_t)((st & 1) * kQBytes);
@@ -423,9 +426,7 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
         uint64_t hb0, hb1, lb0, lb1;
         lds_pairs(rs, hb0, hb1);
         lds_pairs(rs + 16, lb0, lb1);
-        const int n_live = G.y + G.w;
-        for (int k = lane; k < n_live; k += 32) {
-          const int e = k < G.y ? k : kRowCap + (k - G.y);
+        auto rebase = [&](int e) {
           uint64_t h0, h1, l0, l1;
           lds_pairs(rs + 32 * e, h0, h1);
           lds_pairs(rs + 32 * e + 16, l0, l1);
@@ -433,7 +434,9 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
           const uint64_t q1 = add2(sub2(h1, hb1), sub2(l1, lb1));
           asm volatile("st.shared.v2.b64 [%0], {%1, %2};\n" ::"r"(qd + (uint32_t)(e * 16)),
                        "l"(q0), "l"(q1) : "memory");
-        }
+        };
+        for (int e = lane; e < G.y; e += 32) rebase(e);
+        for (int e = kRowCap + lane; e < kRowCap + G.w; e += 32) rebase(e);
         fence_proxy_async_smem();   // the reads of raw above vs the next copy into it
         __syncwarp();
         if (st + 1 < n_st) issue(st + 1);
@@ -457,7 +460,7 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
             const int i = 2 * r + q;
             uint64_t ja, jb;
             lds_pairs(sq + qo[i], ja, jb);
-            v[i] = two_f_pairs(sub2(ja, ia), sub2(jb, ib), nb2[i], k1[i], k2[i]);
+            v[i] = two_f_pairs(sub2(ja, ia), sub2(jb, ib), nb2[i], k1[i], k2[i], tiny2);
           }
         }
       } else {
@@ -482,7 +485,7 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
         for (int i = 0; i < kLaneCells; ++i) {
           uint64_t a, b;
           lds_pairs(wb + (uint32_t)(i * 32 * 16), a, b);
-          v[i] = two_f_pairs(a, b, nb2[i], k1[i], k2[i]);
+          v[i] = two_f_pairs(a, b, nb2[i], k1[i], k2[i], tiny2);
         }
       }
       const float mx = fmaxf(fmaxf(fmaxf(v[0], v[1]), fmaxf(v[2], v[3])),
@@ -510,25 +513,25 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
       const float M = __uint_as_float(mu - 1u);
       const float mc = -M * kHalfLog2e;
       float e[kLaneCells];
-      unsigned hit = 0;
 #pragma unroll
-      for (int i = 0; i < kLaneCells; ++i) {
-        e[i] = ex2_approx(fmaf(v[i], kHalfLog2e, mc));
-        hit |= (v[i] == M ? 1u : 0u) << i;
+      for (int i = 0; i < kLaneCells; ++i) e[i] = ex2_approx(fmaf(v[i], kHalfLog2e, mc));
+      // The lane's sum is in [0, 8] (every term <= 1); summed over the warp in
+      // 2^-23 fixed point by an integer reduction (absolute error <= 32 x
+      // 2^-24 against a sum >= 1, the maximum cell's own term).
+      const float sl = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]));
+      const unsigned sfix = __reduce_add_sync(0xffffffffu, __float2uint_rn(sl * 8388608.0f));
+      // Only lanes holding the maximum look for their first cell at it.
+      unsigned cand = (unsigned)kNoArg;
+      if (mx == M) {
+#pragma unroll
+        for (int i = kLaneCells - 1; i >= 0; --i)
+          if (v[i] == M) cand = (unsigned)(cell0 + cell_off(i));
       }
-      float s = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]));
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-      const int first = __ffs(hit) - 1;
-      const int32_t arg = (int32_t)__reduce_min_sync(
-          0xffffffffu, hit ? (unsigned)(cell0 + cell_off(first)) : (unsigned)kNoArg);
+      const int32_t arg = (int32_t)__reduce_min_sync(0xffffffffu, cand);
       if (lane == 0) {
-        Partial p;
-        p.max2F = M;
-        p.arg = arg;
-        p.sum = s;
-        p.nvalid = nval;
-        parts[(int64_t)tm * stride + wt] = p;
+        const float4 pv = make_float4(M, __int_as_float(arg), (float)sfix * (1.0f / 8388608.0f),
+                                      __int_as_float(nval));
+        *reinterpret_cast<float4*>(parts + (int64_t)tm * stride + wt) = pv;
       }
     }
   }
