@@ -363,11 +363,13 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
             vlo[j] = pack_bf16(w[2 * j] - he, w[2 * j + 1] - ho);
           }
         } else {
+          // the MMA reads TF32 operands as FP32 bit patterns and ignores the
+          // low 13 bits, so the remainder needs no conversion of its own
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const uint32_t hb = to_tf32(w[j]);
             vhi[j] = hb;
-            vlo[j] = to_tf32(w[j] - __uint_as_float(hb));
+            vlo[j] = __float_as_uint(w[j] - __uint_as_float(hb));
           }
         }
       }
