@@ -410,9 +410,22 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
         const bool ok = in_grid && exists && cf.valid == 1.0f;
         if (p.map && in_grid && exists && cf.valid != 2.0f)
           p.map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
+        // The warp's partial over its 32 cells by integer reductions: the
+        // maximum over the 2F bit patterns (2F >= 0; 0 = no valid cell), the
+        // exp-terms in 2^-26 fixed point (each <= 1, the sum >= 1), the
+        // lowest cell index at the maximum, the valid count.
+        const unsigned mu = __reduce_max_sync(0xffffffffu, ok ? __float_as_uint(v) + 1u : 0u);
         Partial pt = partial_empty();
-        partial_add(pt, v, (int32_t)cell, ok);
-        pt = partial_warp_reduce(pt);
+        if (mu != 0u) {
+          const float M = __uint_as_float(mu - 1u);
+          const float e = ok ? __expf(0.5f * (v - M)) : 0.0f;
+          const unsigned sfix = __reduce_add_sync(0xffffffffu, __float2uint_rn(e * 67108864.0f));
+          pt.max2F = M;
+          pt.arg = (int32_t)__reduce_min_sync(0xffffffffu,
+                                              ok && v == M ? (unsigned)cell : (unsigned)kNoArg);
+          pt.sum = (float)sfix * (1.0f / 67108864.0f);
+          pt.nvalid = (int32_t)__reduce_add_sync(0xffffffffu, ok ? 1u : 0u);
+        }
         if (lane == 0) s_red[q][tl] = pt;
       }
     }
