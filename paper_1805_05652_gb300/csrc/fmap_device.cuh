@@ -182,23 +182,30 @@ __device__ __forceinline__ void partial_add(Partial& p, float twoF, int32_t idx,
   p.nvalid += 1;
 }
 
-__device__ __forceinline__ Partial partial_shfl_down(const Partial& p, int delta) {
-  Partial q;
-  q.max2F = __shfl_down_sync(0xffffffffu, p.max2F, delta);
-  q.arg = __shfl_down_sync(0xffffffffu, p.arg, delta);
-  q.sum = __shfl_down_sync(0xffffffffu, p.sum, delta);
-  q.nvalid = __shfl_down_sync(0xffffffffu, p.nvalid, delta);
-  return q;
-}
-
+// Warp-wide merge (all 32 lanes; the result in every lane).  2F >= 0, so a
+// valid partial's maximum orders like its bit pattern: the warp maximum is
+// one integer max reduction, each lane rescales its sum to it (one exp),
+// the sums add in a fixed butterfly order, and the lowest index among the
+// lanes at the maximum and the valid count are integer reductions.
 __device__ __forceinline__ Partial partial_warp_reduce(Partial p) {
+  const bool has = p.nvalid > 0;
+  const unsigned mu = __reduce_max_sync(0xffffffffu, has ? __float_as_uint(p.max2F) + 1u : 0u);
+  if (mu == 0u) return partial_empty();
+  const float M = __uint_as_float(mu - 1u);
+  float s = has ? p.sum * __expf(0.5f * (p.max2F - M)) : 0.0f;
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) p = partial_merge(p, partial_shfl_down(p, d));
-  return p;
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  Partial r;
+  r.max2F = M;
+  r.arg = (int32_t)__reduce_min_sync(0xffffffffu,
+                                     has && p.max2F == M ? (unsigned)p.arg : (unsigned)kNoArg);
+  r.sum = s;
+  r.nvalid = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)p.nvalid);
+  return r;
 }
 
-// Block-wide reduction into lane 0 of warp 0; scratch holds >= nwarps entries.
-// All threads of the block must call it.
+// Block-wide reduction into lane 0 of warp 0 (warp partials merged by warp
+// 0); scratch holds >= nwarps entries.  All threads of the block must call it.
 template <int NWARPS>
 __device__ __forceinline__ Partial partial_block_reduce(Partial p, Partial* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
