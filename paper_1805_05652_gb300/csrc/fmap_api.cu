@@ -102,7 +102,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
   L.pa = L.px = L.esuf = L.xop = 0;
   const size_t np1 = (size_t)n_sft + 1;
   if (g->window == FMAP_RECT) {
-    L.pa = take(sizeof(double) * 4 * np1 * (size_t)t_ant);
+    L.pa = take(sizeof(float) * 8 * np1 * (size_t)t_ant);   // (a2, b2, ab, 0) float pairs
     L.px = take(2 * sizeof(float4) * np1 * (size_t)std::max<int32_t>(T, 1));
   } else {
     const size_t per_tau = 3 * sizeof(float2) * np1;

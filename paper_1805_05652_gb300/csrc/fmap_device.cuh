@@ -130,6 +130,32 @@ __device__ __forceinline__ FF ff_of(double x) {
   return {h, (float)(x - (double)h)};
 }
 
+// Decay constants of one tau for a weight e^{-s (t - t0) / tau} (s = 1 for
+// the data weight w, s = 2 for the antenna weight w^2): the one-SFT decay as
+// a float pair, s / tau in FP64 (for gaps off the T_sft lattice) and the
+// FP32 exp2 slope -s log2(e) / tau.  GB300 runs FP64 at 1/64 of the FP32
+// rate, so a block computes these once (one thread) and shares them.
+struct TauDecay {
+  FF rho1;
+  double inv_s;
+  float c2;
+};
+__device__ __forceinline__ TauDecay tau_decay(double tau, double s, int32_t t_sft) {
+  TauDecay d;
+  d.inv_s = s / tau;
+  d.rho1 = ff_of(exp(-(double)t_sft * d.inv_s));
+  d.c2 = (float)(-1.4426950408889634 * d.inv_s);
+  return d;
+}
+// The block's copy of tau_decay(tau, s, t_sft) through shared memory slot
+// *slot; every thread of the block calls it (it synchronises the block).
+__device__ __forceinline__ TauDecay tau_decay_block(double tau, double s, int32_t t_sft,
+                                                    TauDecay* slot) {
+  if (threadIdx.x == 0) *slot = tau_decay(tau, s, t_sft);
+  __syncthreads();
+  return *slot;
+}
+
 __device__ __forceinline__ Partial partial_empty() {
   Partial p;
   p.max2F = -1.0f;
@@ -229,25 +255,6 @@ __device__ __forceinline__ float two_f(const Coef& c, float fa_re, float fa_im, 
   const float fa2 = fmaf(fa_re, fa_re, fa_im * fa_im);
   const float e2 = fmaf(e_re, e_re, e_im * e_im);
   return fmaf(c.k1, fa2, c.k2 * e2);
-}
-
-// Coefficients from FP64 sums (D in FP64, the divisions in FP32).
-__device__ __forceinline__ Coef make_coef(double A, double B, double C, int32_t count) {
-  Coef c;
-  const double D = A * B - C * C;
-  if (count >= 2 && D > 0.0 && A > 0.0) {
-    const float af = (float)A, cf = (float)C, df = (float)D;
-    c.k1 = 2.0f / af;
-    c.beta = cf / af;
-    c.k2 = 2.0f * af / df;
-    c.valid = (A * B > kCondThreshold * D) ? 2.0f : 1.0f;
-  } else {
-    c.k1 = 0.0f;
-    c.beta = 0.0f;
-    c.k2 = 0.0f;
-    c.valid = 0.0f;
-  }
-  return c;
 }
 
 // Coefficients from float-float sums: D = AB - C^2 from exact FMA products

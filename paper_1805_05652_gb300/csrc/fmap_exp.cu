@@ -50,16 +50,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // it together.
 __device__ __forceinline__ void antenna_suffix(const int32_t* __restrict__ rel_t, int32_t n,
                                                const float* __restrict__ ant, const fmap_grid& g,
-                                               double tau, float2* E, float (*sR)[kSufThreads / 32],
+                                               const TauDecay& td, float2* E,
+                                               float (*sR)[kSufThreads / 32],
                                                float (*sS)[2][kSufThreads / 32]) {
-  const double inv_s = 2.0 / tau;
+  const double inv_s = td.inv_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int C = (n + kSufThreads - 1) / kSufThreads;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   // Decay over one gap: e^{-2 gap / tau}.  Gaps that are whole multiples k of
   // T_sft (the usual case) take the k-th power of the one-SFT decay (in
   // float-float); others use FP64 exp.
-  const FF rho1 = ff_of(exp(-(double)g.t_sft * inv_s));
+  const FF rho1 = td.rho1;
   const float inv_tsft = 1.0f / (float)g.t_sft;
   auto rho_of_gap = [&](int32_t gap) -> FF {
     const int32_t k = __float2int_rn((float)gap * inv_tsft);
@@ -176,26 +177,27 @@ k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restri
              fmap_grid g, int32_t n_lo, float2* __restrict__ esuf) {
   __shared__ float sR[2][kSufThreads / 32];
   __shared__ float sS[3][2][kSufThreads / 32];
+  __shared__ TauDecay s_td;
   const int ni = blockIdx.x;
   const double tau = (double)(g.tau_min + (int64_t)(n_lo + ni) * g.dtau);
-  antenna_suffix(rel_t, n, ant, g, tau, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
+  const TauDecay td = tau_decay_block(tau, 2.0, g.t_sft, &s_td);
+  antenna_suffix(rel_t, n, ant, g, td, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
 }
 
-// A, B, C of a cell from the suffix sums E of its tau, then its coefficients.
+// A, B, C of a cell from the suffix sums E of its tau, then its coefficients;
+// c2 = -2 log2(e) / tau.
 __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t, int32_t n,
-                                              const fmap_grid& g, int64_t m, int64_t nn,
+                                              const fmap_grid& g, int64_t m, float c2,
                                               int32_t i0, int32_t j, int64_t t_base,
                                               const float2* E) {
   const int32_t count = j - i0;
   FF S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   if (count > 0) {
-    const double tau = (double)(g.tau_min + nn * g.dtau);
     const int64_t t0rel = g.t0_min + m * g.dt0 - t_base;
     const int64_t np1 = (int64_t)n + 1;
     // The prefactor scales A, B, C alike (F changes by its relative error
     // only) and the tail term is ~e^{-6} of the window sum: FP32 exp2 is
     // accurate enough for both.
-    const float c2 = (float)(-2.8853900817779268 / tau);   // -2 log2(e) / tau
     const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
     const float pre = d0 == 0 ? 1.0f : ex2_approx(c2 * (float)d0);
     const float tail = (j < n) ? ex2_approx(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0f;
@@ -219,16 +221,18 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
   extern __shared__ float2 s_E[];
   __shared__ float sR[2][kSufThreads / 32];
   __shared__ float sS[3][2][kSufThreads / 32];
+  __shared__ TauDecay s_td;
   const int ni = bid.x, ta = bid.y;
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
-  antenna_suffix(rel_t, n, antenna + (int64_t)ta * 3 * n, g, tau, s_E, sR, sS);
+  const TauDecay td = tau_decay_block(tau, 2.0, g.t_sft, &s_td);
+  antenna_suffix(rel_t, n, antenna + (int64_t)ta * 3 * n, g, td, s_E, sR, sS);
   __syncthreads();
   const int64_t tb = n > 0 ? *t_base : 0;
   for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
     const int64_t cell = (int64_t)m * g.n_tau + ni;
     coef[(int64_t)ta * cells + cell] =
-        exp_cell_coef(rel_t, n, g, m, ni, i0tab[m], jend[cell], tb, s_E);
+        exp_cell_coef(rel_t, n, g, m, td.c2, i0tab[m], jend[cell], tb, s_E);
   }
 }
 
@@ -255,7 +259,8 @@ __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __r
     const int32_t nl = (int32_t)(c - m * n_chunk);
     const int64_t nn = n_lo + nl;
     const int64_t cell = m * g.n_tau + nn;
-    coef[cell] = exp_cell_coef(rel_t, n, g, m, nn, i0tab[m], jend[cell], tb,
+    const float c2 = (float)(-2.8853900817779268 / (double)(g.tau_min + nn * g.dtau));
+    coef[cell] = exp_cell_coef(rel_t, n, g, m, c2, i0tab[m], jend[cell], tb,
                                esuf + (int64_t)nl * 3 * np1);
   }
 }

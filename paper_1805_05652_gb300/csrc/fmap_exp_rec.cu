@@ -68,16 +68,18 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   __shared__ float sR[2][kRecThreads / 32];
   __shared__ float sS[4][2][kRecThreads / 32];
   __shared__ Partial scratch[kRecThreads / 32];
+  __shared__ TauDecay s_td;
   const int ni = bid.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
-  const double inv_tau = 1.0 / tau;
+  const TauDecay td = tau_decay_block(tau, 1.0, g.t_sft, &s_td);
+  const double inv_tau = td.inv_s;
   const int64_t np1 = (int64_t)n + 1;
   // Decays of this tau, once for all the block's templates: whole multiples k
   // of T_sft take the k-th power of the one-SFT decay, other gaps use exp.
   // (float-float powers of the one-SFT decay; FP64 exp only off the lattice)
   {
-    const FF rho1 = ff_of(exp(-(double)g.t_sft * inv_tau));
+    const FF rho1 = td.rho1;
     const float inv_tsft = 1.0f / (float)g.t_sft;
     for (int i = tid; i < n; i += kRecThreads) {
       FF r{0.0f, 0.0f};
@@ -104,7 +106,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   const int C = (n + kRecThreads - 1) / kRecThreads;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
-  const float c2 = (float)(-1.4426950408889634 * inv_tau);
+  const float c2 = td.c2;
   const int64_t tb = n > 0 ? *t_base : 0;
   // Per cell (t0_m, tau_n): the window, its prefactor and tail factor and the
   // coefficients; staged once per block when they fit, else recomputed per

@@ -1,11 +1,13 @@
 // Rectangular-window F-map (Eq. winrect).
 //
 // FMAP_FP64: prefix sums over SFTs in FP64, then O(1) differencing per cell.
-//   The antenna rows keep FP64 prefixes (A, B, C and D = AB - C^2 in FP64,
-//   once per cell).  The data rows keep each FP64 prefix as an unevaluated
-//   float pair hi + lo; a window sum is (hi_j - hi_i) + (lo_j - lo_i), whose
-//   rounding error is relative to the window sum itself and not to the
-//   (possibly much larger) prefix.
+//   Every FP64 prefix is kept as an unevaluated float pair hi + lo; a window
+//   sum is (hi_j - hi_i) + (lo_j - lo_i), whose rounding error is relative
+//   to the window sum itself and not to the (possibly much larger) prefix.
+//   The antenna sums A, B, C are differenced in float-float (~2^-44 of the
+//   prefix) and D = AB - C^2 formed from exact FMA products; cells with
+//   AB > 100 D go to the FP64 fix-up.  (GB300 runs FP64 at 1/64 of the FP32
+//   rate, so the per-cell work stays off the FP64 pipe.)
 // FMAP_FP32: the paper's rectangular kernel (Sec. 3): one thread per t0 row
 //   adds atom after atom to FP32 running sums as tau grows.
 #include <math.h>
@@ -20,8 +22,9 @@ constexpr int kScanPer = 8;
 constexpr int kScanTile = kScanThreads * kScanPer;
 constexpr int kCellThreads = 256;
 
-struct __align__(32) D4 {
-  double x, y, z, w;
+// Antenna prefix entry: (sum a2, sum b2, sum ab, 0) as float pairs.
+struct __align__(32) P4 {
+  float4 hi, lo;
 };
 
 constexpr int kTileRows = 4;    // t0 rows of a warp tile of the cells kernel
@@ -119,17 +122,18 @@ k_rect_scan_data(const float* __restrict__ fafb, int32_t n, float4* __restrict__
   rect_scan_data_body(fafb, n, px, blockIdx, gridDim);
 }
 
-// FP64 prefix of the antenna rows: pa[ta][i] = (sum a2, sum b2, sum ab, 0).
-__device__ __forceinline__ void rect_scan_antenna_body(const float* __restrict__ antenna, int32_t n, D4* __restrict__ pa,
+// FP64 prefix of the antenna rows, stored as float pairs: pa[ta][i] =
+// (sum a2, sum b2, sum ab, 0) over a < i.
+__device__ __forceinline__ void rect_scan_antenna_body(const float* __restrict__ antenna, int32_t n, P4* __restrict__ pa,
     const uint3 bid, const dim3 gdim) {
   __shared__ float tile[3][kScanTile];
   __shared__ double sh[3][kScanThreads];
   const int64_t ta = bid.x;
   const float* x = antenna + ta * 3 * (int64_t)n;
-  D4* out = pa + ta * (int64_t)(n + 1);
+  P4* out = pa + ta * (int64_t)(n + 1);
   const int tid = threadIdx.x;
   double carry[3] = {0.0, 0.0, 0.0};
-  if (tid == 0) out[0] = D4{0.0, 0.0, 0.0, 0.0};
+  if (tid == 0) out[0] = P4{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
   for (int64_t base = 0; base < n; base += kScanTile) {
     for (int k = tid; k < kScanTile; k += kScanThreads) {
       const int64_t a = base + k;
@@ -152,7 +156,15 @@ __device__ __forceinline__ void rect_scan_antenna_body(const float* __restrict__
       const int64_t a = base + tid * kScanPer + e;
 #pragma unroll
       for (int c = 0; c < 3; ++c) run[c] += (double)tile[c][tid * kScanPer + e];
-      if (a < n) out[a + 1] = D4{run[0], run[1], run[2], 0.0};
+      if (a < n) {
+        float hi[3], lo[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          hi[c] = (float)run[c];
+          lo[c] = (float)(run[c] - (double)hi[c]);
+        }
+        out[a + 1] = P4{make_float4(hi[0], hi[1], hi[2], 0.f), make_float4(lo[0], lo[1], lo[2], 0.f)};
+      }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) carry[c] += tot[c];
@@ -161,30 +173,51 @@ __device__ __forceinline__ void rect_scan_antenna_body(const float* __restrict__
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_rect_scan_antenna(const float* __restrict__ antenna, int32_t n, D4* __restrict__ pa) {
+k_rect_scan_antenna(const float* __restrict__ antenna, int32_t n, P4* __restrict__ pa) {
   rect_scan_antenna_body(antenna, n, pa, blockIdx, gridDim);
 }
 
 // Per-cell coefficients (shared by the templates of one antenna set) from the
-// FP64 antenna prefixes: A, B, C, D = AB - C^2 in FP64.
+// antenna prefixes: A, B, C as float-float differences, D = AB - C^2 from
+// exact FMA products.
+__device__ __forceinline__ Coef rect_cell_coef(const P4* __restrict__ pa, int64_t e_i0,
+                                               int64_t e_j, int32_t count) {
+  const P4 pj = pa[e_j], pi = pa[e_i0];
+  const FF A = ff_sub(FF{pj.hi.x, pj.lo.x}, FF{pi.hi.x, pi.lo.x});
+  const FF B = ff_sub(FF{pj.hi.y, pj.lo.y}, FF{pi.hi.y, pi.lo.y});
+  const FF C = ff_sub(FF{pj.hi.z, pj.lo.z}, FF{pi.hi.z, pi.lo.z});
+  return make_coef_ff(A, B, C, count);
+}
+
 __device__ __forceinline__ void rect_coef_body(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-                            const D4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
+                            const P4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
                             int32_t n_ant, Coef* __restrict__ coef,
     const uint3 bid, const dim3 gdim) {
   const int64_t cells = (int64_t)n_t0 * n_tau;
   const int64_t total = cells * n_ant;
   const int64_t np1 = (int64_t)n_sft + 1;
-  for (int64_t e = bid.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gdim.x * blockDim.x) {
+  const int64_t step = (int64_t)gdim.x * blockDim.x;
+  const int64_t e0 = bid.x * (int64_t)blockDim.x + threadIdx.x;
+  if (total <= 0xffffffffll) {
+    // 32-bit index arithmetic (the usual case)
+    const uint32_t ucells = (uint32_t)cells, utau = (uint32_t)n_tau;
+    for (int64_t e = e0; e < total; e += step) {
+      const uint32_t ue = (uint32_t)e;
+      const uint32_t ta = ue / ucells, cell = ue - ta * ucells;
+      const int32_t i0 = i0tab[cell / utau], j = jend[cell];
+      coef[e] = rect_cell_coef(pa, ta * np1 + i0, ta * np1 + j, j - i0);
+    }
+    return;
+  }
+  for (int64_t e = e0; e < total; e += step) {
     const int64_t ta = e / cells, cell = e - ta * cells;
     const int32_t i0 = i0tab[cell / n_tau], j = jend[cell];
-    const D4 pj = pa[ta * np1 + j], pi = pa[ta * np1 + i0];
-    coef[e] = make_coef(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z, j - i0);
+    coef[e] = rect_cell_coef(pa, ta * np1 + i0, ta * np1 + j, j - i0);
   }
 }
 
 __global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-                            const D4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
+                            const P4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
                             int32_t n_ant, Coef* __restrict__ coef) {
   rect_coef_body(i0tab, jend, pa, n_sft, n_t0, n_tau, n_ant, coef, blockIdx, gridDim);
 }
@@ -603,13 +636,13 @@ cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s
   const int n_ant = a->shared_antenna ? 1 : p->n_templates;
   if (n_ant == 0) return cudaSuccess;
   if (p->n_sft > 0) {
-    k_rect_scan_antenna<<<n_ant, kScanThreads, 0, s>>>(a->antenna, p->n_sft, (D4*)p->ws.pa);
+    k_rect_scan_antenna<<<n_ant, kScanThreads, 0, s>>>(a->antenna, p->n_sft, (P4*)p->ws.pa);
   } else {
-    cudaMemsetAsync(p->ws.pa, 0, sizeof(D4) * n_ant, s);
+    cudaMemsetAsync(p->ws.pa, 0, sizeof(P4) * n_ant, s);
   }
   const int64_t total = cells * n_ant;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
-  k_rect_coef<<<blocks, 256, 0, s>>>(p->ws.i0, p->ws.jend, (const D4*)p->ws.pa, p->n_sft, g.n_t0,
+  k_rect_coef<<<blocks, 256, 0, s>>>(p->ws.i0, p->ws.jend, (const P4*)p->ws.pa, p->n_sft, g.n_t0,
                                      g.n_tau, n_ant, p->ws.coef);
   p->launches += (p->n_sft > 0) ? 2 : 1;
   return cudaGetLastError();
@@ -665,13 +698,13 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
 __global__ void __launch_bounds__(kScanThreads) kb_rect_ant(const BItem* __restrict__ items,
                                                             BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    rect_scan_antenna_body(it.antenna, it.n_sft, (D4*)it.pa, make_uint3((unsigned)k, 0, 0),
+    rect_scan_antenna_body(it.antenna, it.n_sft, (P4*)it.pa, make_uint3((unsigned)k, 0, 0),
                            dim3((unsigned)it.n_ant));
   });
 }
 __global__ void __launch_bounds__(256) kb_rect_coef(const BItem* __restrict__ items, BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    rect_coef_body(it.i0, it.jend, (const D4*)it.pa, it.n_sft, it.g.n_t0, it.g.n_tau, it.n_ant,
+    rect_coef_body(it.i0, it.jend, (const P4*)it.pa, it.n_sft, it.g.n_t0, it.g.n_tau, it.n_ant,
                    it.coef, make_uint3((unsigned)k, 0, 0),
                    dim3((unsigned)((it.cells * it.n_ant + 255) / 256)));
   });
