@@ -321,11 +321,11 @@ fmap_status fmap_batch_run(fmap_batch_t* batch, fmap_stream stream);
  * any instance. */
 fmap_status fmap_batch_status(fmap_batch_t* batch, fmap_stream stream);
 /* Phases of a batch run, in launch order (FMAP_BATCH_N_PHASES entries):
- * input checks, index tables, rect antenna prefixes, exp antenna sums and
- * coefficients, rect coefficients, rect data prefixes, exp recurrence and
- * cells, rect cells, three steps of the ill-conditioned cell compaction,
- * FP64 fix-up, two reduction levels. */
-#define FMAP_BATCH_N_PHASES 14
+ * input checks, index tables, exp chunk-major atom copies, rect antenna
+ * prefixes, exp antenna sums and coefficients, rect coefficients, rect data
+ * prefixes, exp recurrence and cells, rect cells, three steps of the
+ * ill-conditioned cell compaction, FP64 fix-up, two reduction levels. */
+#define FMAP_BATCH_N_PHASES 15
 /* Waves, kernel launches per run, workspace bytes, chosen occupancy per phase
  * (FMAP_BATCH_N_PHASES entries, nullable) and templates per block of the
  * recurrence. */

@@ -64,7 +64,7 @@ EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_
            "fmap_submit", "fmap_poll", "fmap_server_stats", "fmap_batch_plan", "fmap_batch_run",
            "fmap_batch_status", "fmap_batch_info", "fmap_batch_profile", "fmap_batch_destroy")
 FMAP_BATCH_AUTOTUNE = 1
-N_BATCH_PHASES = 14
+N_BATCH_PHASES = 15
 FMAP_N_PHASES = 4
 FMAP_SUBMIT_MAP = 1
 
@@ -358,7 +358,7 @@ def fmap_batch_profile(batch: int, stream=None):
     return ms
 
 
-BATCH_PHASES = ("prep", "index", "rect_antenna", "exp_antenna", "rect_coef", "rect_data",
+BATCH_PHASES = ("prep", "index", "exp_copy", "rect_antenna", "exp_antenna", "rect_coef", "rect_data",
                 "exp_recurrence", "rect_cells", "flag_count", "flag_scan", "flag_write", "fixup",
                 "reduce_groups", "reduce_final")
 

@@ -58,7 +58,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
-      esuf, xop, total;
+      esuf, xop, perm_ant, perm_x, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -96,10 +96,10 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
                   (size_t)reduce_groups_of(tiles + kFixSlots));
   const size_t entries = (size_t)std::max<int64_t>(cells, 1) * (size_t)t_ant;
   L.coef = take(sizeof(Coef) * entries);
-  L.flag_blocks = take(sizeof(int32_t) * ((entries + 1023) / 1024));
+  L.flag_blocks = take(sizeof(int32_t) * ((entries + kFlagUnit - 1) / kFlagUnit));
   L.n_flag = take(sizeof(int32_t));
   L.flag_list = take(sizeof(int64_t) * entries);
-  L.pa = L.px = L.esuf = L.xop = 0;
+  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = 0;
   const size_t np1 = (size_t)n_sft + 1;
   if (g->window == FMAP_RECT) {
     L.pa = take(sizeof(float) * 8 * np1 * (size_t)t_ant);   // (a2, b2, ab, 0) float pairs
@@ -111,6 +111,9 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.tau_chunk = (int32_t)chunk;
     // the suffix sums live in shared memory when the data set fits there
     L.esuf = take(exp_antenna_fits(n_sft) ? 8 : per_tau * (size_t)chunk);
+    const size_t perm = sizeof(float4) * (size_t)perm_entries(n_sft);
+    L.perm_ant = take(perm * (size_t)t_ant);
+    if (flags & FMAP_PLAN_EXP_RECURRENCE) L.perm_x = take(perm * (size_t)std::max<int32_t>(T, 1));
     if (prec == FMAP_TF32 || prec == FMAP_BF16X3)
       L.xop = take(exp_tc_operand_bytes(*g, n_sft, T, prec));
   }
@@ -224,10 +227,12 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
   w.n_flag = (int32_t*)(b + L.n_flag);
   w.flag_list = (int64_t*)(b + L.flag_list);
   if (grid->window == FMAP_RECT) {
-    w.pa = (double*)(b + L.pa);
+    w.pa = (float4*)(b + L.pa);
     w.px = (float4*)(b + L.px);
   } else {
     w.esuf = (float2*)(b + L.esuf);
+    w.perm_ant = (float4*)(b + L.perm_ant);
+    if (L.perm_x) w.perm_x = (float4*)(b + L.perm_x);
     if (L.xop) w.xop = (void*)(b + L.xop);
   }
   p->needs_err_reset = true;
@@ -363,6 +368,7 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
     FMAP_CUDA(launch_rect_coef(p, a, s));
     FMAP_CUDA(launch_rect(p, a, d_2F, s, &tiles, ev[2]));
   } else {
+    FMAP_CUDA(launch_exp_perm(p, a, s));
     FMAP_CUDA(launch_exp_coef(p, a, s));
     if (ev[2]) FMAP_CUDA(cudaEventRecord(ev[2], s));
     if (p->flags & FMAP_PLAN_EXP_RECURRENCE) {

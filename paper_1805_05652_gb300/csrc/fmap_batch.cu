@@ -109,18 +109,24 @@ static int64_t units_of(const fmap_plan_s* p, const fmap_batch_item& it, int ph,
   const bool work = cells > 0 && T > 0;
   switch (ph) {
     case BP_PREP: return p->n_sft > 0 ? (rel_t_entries(p->n_sft) + 255) / 256 : 0;
-    case BP_INDEX: return cells > 0 ? g.n_t0 : 0;
+    case BP_INDEX: return cells > 0 ? (g.n_t0 + kIdxRowsPerUnit - 1) / kIdxRowsPerUnit : 0;
+    case BP_EXP_PERM: {
+      if (rect || cells == 0 || p->n_sft <= 0) return 0;
+      const int64_t sets = n_ant + ((p->flags & FMAP_PLAN_EXP_RECURRENCE) ? T : 0);
+      return (perm_entries(p->n_sft) * sets + kPermPerUnit - 1) / kPermPerUnit;
+    }
     case BP_RECT_ANT: return rect && cells > 0 && p->n_sft > 0 ? n_ant : 0;
     case BP_EXP_ANT: return !rect && cells > 0 ? g.n_tau * n_ant : 0;
-    case BP_RECT_COEF: return rect && cells > 0 ? (cells * n_ant + 255) / 256 : 0;
+    case BP_RECT_COEF:
+      return rect && cells > 0 ? (cells * n_ant + 256 * kCoefBlocksPerUnit - 1) / (256 * kCoefBlocksPerUnit) : 0;
     case BP_RECT_DATA: return rect && work && p->n_sft > 0 ? T : 0;
     case BP_EXP_REC: return !rect && work ? g.n_tau * ((T + rec_tpb - 1) / rec_tpb) : 0;
     case BP_RECT_CELLS:
       return rect && work ? rect_cells_blocks(g, (int32_t)T, it.atoms.shared_antenna) : 0;
     case BP_FLAG_COUNT:
-    case BP_FLAG_WRITE: return work ? (cells * n_ant + 1023) / 1024 : 0;
+    case BP_FLAG_WRITE: return work ? (cells * n_ant + kFlagUnit - 1) / kFlagUnit : 0;
     case BP_FLAG_SCAN: return work ? 1 : 0;
-    case BP_FIXUP: return work ? (int64_t)kFixSlots * fixup_blocks_y((int32_t)T) : 0;
+    case BP_FIXUP: return work ? (int64_t)(kFixSlots / kFixSlotsPerUnit) * fixup_blocks_y((int32_t)T) : 0;
     case BP_RED_GROUPS: {
       if (!it.d_summary || T == 0) return 0;
       const int64_t used =
@@ -168,6 +174,8 @@ static BItem make_bitem(const fmap_plan_s* p, const fmap_batch_item& it, uint32_
   b.n_flag = w.n_flag;
   b.flag_list = w.flag_list;
   b.pa = w.pa;
+  b.perm_ant = w.perm_ant;
+  b.perm_x = w.perm_x;
   b.px = w.px;
   return b;
 }

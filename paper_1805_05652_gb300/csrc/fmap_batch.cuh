@@ -33,7 +33,9 @@ struct BItem {
   int32_t* flag_blocks;
   int32_t* n_flag;
   int64_t* flag_list;
-  double* pa;
+  float4* pa;
+  float4* perm_ant;
+  float4* perm_x;
   float4* px;
 };
 
@@ -44,10 +46,20 @@ struct BUnits {
   unsigned long long* counter;
 };
 
+// Work of one unit in the phases whose natural unit is small (so that the
+// per-unit claim and instance lookup stay a small share): rectangular
+// coefficients in 256-entry blocks, index-table rows, fix-up slots.
+constexpr int kCoefBlocksPerUnit = 8;
+constexpr int kIdxRowsPerUnit = 4;
+constexpr int kFixSlotsPerUnit = 16;
+constexpr int kPermPerUnit = 4096;   // chunk-major copy entries per unit
+static_assert(kFixSlots % kFixSlotsPerUnit == 0, "fix-up slot groups");
+
 // Phases of the batch pipeline, in launch order.
 enum BPhase {
   BP_PREP = 0,
   BP_INDEX,
+  BP_EXP_PERM,
   BP_RECT_ANT,
   BP_EXP_ANT,
   BP_RECT_COEF,
@@ -63,22 +75,41 @@ enum BPhase {
   BP_COUNT
 };
 
+// A block claims units in increasing order, so the instance of its next
+// unit is at or after that of its last one: thread 0 gallops forward from
+// there (usually a step or two) and shares the result with the unit.
 template <class F>
 __device__ __forceinline__ void batch_loop(const BItem* __restrict__ items, const BUnits& u,
                                            F&& run) {
   __shared__ long long s_w;
+  __shared__ int s_item;
+  int last = 0;   // thread 0: instance of the previous unit
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_w = (long long)atomicAdd(u.counter, 1ull);
+    if (threadIdx.x == 0) {
+      const long long w = (long long)atomicAdd(u.counter, 1ull);
+      s_w = w;
+      if (w < u.total) {
+        // last instance with offsets[i] <= w, searched in [last, n_items)
+        int lo = last, step = 1;
+        while (lo + step < u.n_items && u.offsets[lo + step] <= w) {
+          lo += step;
+          step <<= 1;
+        }
+        int hi = min(lo + step, u.n_items) - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (u.offsets[mid] <= w) lo = mid; else hi = mid - 1;
+        }
+        last = lo;
+        s_item = lo;
+      }
+    }
     __syncthreads();
     const int64_t w = s_w;
     if (w >= u.total) return;
-    int lo = 0, hi = u.n_items - 1;   // last instance with offsets[i] <= w
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (u.offsets[mid] <= w) lo = mid; else hi = mid - 1;
-    }
-    run(items[lo], w - u.offsets[lo]);
+    const int i = s_item;
+    run(items[i], w - u.offsets[i]);
   }
 }
 

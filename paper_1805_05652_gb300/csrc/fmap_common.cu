@@ -367,7 +367,9 @@ __global__ void __launch_bounds__(256) kb_prep(const BItem* __restrict__ items, 
 }
 __global__ void __launch_bounds__(kIdxThreads) kb_index(const BItem* __restrict__ items, BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    index_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, (int32_t)k);
+    const int32_t m_end = min(it.g.n_t0, (int32_t)(k + 1) * kIdxRowsPerUnit);
+    for (int32_t m = (int32_t)k * kIdxRowsPerUnit; m < m_end; ++m)
+      index_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, m);
   });
 }
 __global__ void __launch_bounds__(kRedThreads) kb_red_groups(const BItem* __restrict__ items,

@@ -156,6 +156,62 @@ __device__ __forceinline__ TauDecay tau_decay_block(double tau, double s, int32_
   return *slot;
 }
 
+// Decays over gaps of k whole SFTs, k < kPowTab: tab[k] = rho1^k as a float
+// pair (binary powering in float-float, ~k ulp of 2^-48); tab[0] = 1.  The
+// block's threads 0..kPowTab-1 fill it; the caller synchronises after.
+constexpr int kPowTab = 16;
+__device__ __forceinline__ void decay_table_fill(FF rho1, float2* tab) {
+  const int k = threadIdx.x;
+  if (k < kPowTab) {
+    FF acc{1.0f, 0.0f}, r = rho1;
+    for (int q = k; q; q >>= 1) {
+      if (q & 1) acc = ff_mul(acc, r);
+      r = ff_mul(r, r);
+    }
+    tab[k] = make_float2(acc.h, acc.l);
+  }
+}
+// Decay over one gap between consecutive atoms: a table entry for gaps of
+// 1..kPowTab-1 whole SFTs (branch-free for the usual spacings), FP64 exp
+// otherwise (gaps off the T_sft lattice; inv_s = s / tau).
+__device__ __forceinline__ FF gap_decay(int32_t gap, int32_t t_sft, float inv_tsft,
+                                        const float2* tab, double inv_s) {
+  const int32_t k = __float2int_rn((float)gap * inv_tsft);
+  if (k >= 1 && k < kPowTab && k * t_sft == gap) {
+    const float2 v = tab[k];
+    return {v.x, v.y};
+  }
+  return ff_of(exp(-(double)gap * inv_s));
+}
+
+// Compensated recurrence E <- x + r E (Horner's rule with error-free
+// transformations, after Graillat, Langlois and Louvet's compensated Horner
+// scheme): E = h + c with h the plain FP32 recurrence and c carrying its
+// rounding errors (the TwoProd error of r.h h, the TwoSum error of adding x,
+// and the low part r.l of the decay).  The pair is left unnormalised between
+// calls; ch_norm folds c back into h.
+__device__ __forceinline__ void ch_step(FF r, float x, float& h, float& c) {
+  const float p = r.h * h;
+  const float pe = fmaf(r.h, h, -p);
+  const float s = p + x;
+  const float bb = s - p;
+  const float se = (p - (s - bb)) + (x - bb);
+  c = fmaf(r.h, c, fmaf(r.l, h, pe + se));
+  h = s;
+}
+// R <- r R for the compensated running product of the decays.
+__device__ __forceinline__ void ch_mul(FF r, float& h, float& c) {
+  const float p = r.h * h;
+  const float pe = fmaf(r.h, h, -p);
+  c = fmaf(r.h, c, fmaf(r.l, h, pe));
+  h = p;
+}
+__device__ __forceinline__ void ch_norm(float& h, float& c) {
+  const float s = h + c;
+  c = c - (s - h);
+  h = s;
+}
+
 __device__ __forceinline__ Partial partial_empty() {
   Partial p;
   p.max2F = -1.0f;

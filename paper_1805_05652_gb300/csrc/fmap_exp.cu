@@ -48,11 +48,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // it): E[c * (n + 1) + i] for c = a2, b2, ab and i = 0..n (E[n] = 0), each as
 // an (h, l) pair.  E may be in global or shared memory; the block must call
 // it together.
-__device__ __forceinline__ void antenna_suffix(const int32_t* __restrict__ rel_t, int32_t n,
-                                               const float* __restrict__ ant, const fmap_grid& g,
+__device__ __forceinline__ void antenna_suffix(const float4* __restrict__ perm, int32_t n,
+                                               const fmap_grid& g,
                                                const TauDecay& td, float2* E,
                                                float (*sR)[kSufThreads / 32],
                                                float (*sS)[2][kSufThreads / 32]) {
+  static_assert(kSufThreads == kScanLanes, "chunk-major copy layout");
   const double inv_s = td.inv_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int C = (n + kSufThreads - 1) / kSufThreads;
@@ -75,9 +76,10 @@ __device__ __forceinline__ void antenna_suffix(const int32_t* __restrict__ rel_t
     }
     return ff_of(exp(-(double)gap * inv_s));
   };
-  // The chunk's atoms are read kSufChunk at a time ahead of each serial run
-  // (times for the gaps and the three antenna rows), so the chain does not
-  // wait on memory per atom.
+  // The chunk's atoms (three antenna rows and the gap to the next atom) are
+  // read kSufChunk at a time ahead of each serial run, so the chain does not
+  // wait on memory per atom; the chunk-major copy makes each of these loads
+  // one contiguous 512-byte row per warp.
   constexpr int kSufChunk = 8;
   float xa[kSufChunk][3];
   int32_t gap[kSufChunk];
@@ -86,9 +88,12 @@ __device__ __forceinline__ void antenna_suffix(const int32_t* __restrict__ rel_t
     for (int q = 0; q < kSufChunk; ++q) {
       const int i = b0 + q;
       const bool in = i < e0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) xa[q][c] = in ? __ldg(ant + (int64_t)c * n + i) : 0.0f;
-      gap[q] = (in && i + 1 < n) ? __ldg(rel_t + i + 1) - __ldg(rel_t + i) : -1;
+      const float4 v = in ? __ldg(perm + (int64_t)(i - s0) * kSufThreads + tid)
+                          : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+      xa[q][0] = v.x;
+      xa[q][1] = v.y;
+      xa[q][2] = v.z;
+      gap[q] = __float_as_int(v.w);
     }
   };
   auto rho_q = [&](int q) -> FF { return gap[q] < 0 ? FF{0.0f, 0.0f} : rho_of_gap(gap[q]); };
@@ -173,15 +178,15 @@ __device__ __forceinline__ void antenna_suffix(const int32_t* __restrict__ rel_t
 
 // Global-memory suffix sums for one tau of a tau chunk (long data sets).
 __global__ void __launch_bounds__(kSufThreads)
-k_exp_suffix(const int32_t* __restrict__ rel_t, int32_t n, const float* __restrict__ ant,
-             fmap_grid g, int32_t n_lo, float2* __restrict__ esuf) {
+k_exp_suffix(const float4* __restrict__ perm, int32_t n, fmap_grid g, int32_t n_lo,
+             float2* __restrict__ esuf) {
   __shared__ float sR[2][kSufThreads / 32];
   __shared__ float sS[3][2][kSufThreads / 32];
   __shared__ TauDecay s_td;
   const int ni = blockIdx.x;
   const double tau = (double)(g.tau_min + (int64_t)(n_lo + ni) * g.dtau);
   const TauDecay td = tau_decay_block(tau, 2.0, g.t_sft, &s_td);
-  antenna_suffix(rel_t, n, ant, g, td, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
+  antenna_suffix(perm, n, g, td, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
 }
 
 // A, B, C of a cell from the suffix sums E of its tau, then its coefficients;
@@ -215,7 +220,7 @@ __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t,
 // coefficients of every cell (t0_m, tau_n).  Blocks run tau-fastest, so their
 // strided coefficient stores merge in L2.
 __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
-              fmap_grid g, const float* __restrict__ antenna, const int32_t* __restrict__ i0tab,
+              fmap_grid g, const float4* __restrict__ perm_ant, const int32_t* __restrict__ i0tab,
               const int32_t* __restrict__ jend, Coef* __restrict__ coef,
     const uint3 bid, const dim3 gdim) {
   extern __shared__ float2 s_E[];
@@ -226,7 +231,7 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
   const TauDecay td = tau_decay_block(tau, 2.0, g.t_sft, &s_td);
-  antenna_suffix(rel_t, n, antenna + (int64_t)ta * 3 * n, g, td, s_E, sR, sS);
+  antenna_suffix(perm_ant + (int64_t)ta * perm_entries(n), n, g, td, s_E, sR, sS);
   __syncthreads();
   const int64_t tb = n > 0 ? *t_base : 0;
   for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
@@ -238,9 +243,65 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
 
 __global__ void __launch_bounds__(kSufThreads)
 k_exp_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
-              fmap_grid g, const float* __restrict__ antenna, const int32_t* __restrict__ i0tab,
+              fmap_grid g, const float4* __restrict__ perm_ant, const int32_t* __restrict__ i0tab,
               const int32_t* __restrict__ jend, Coef* __restrict__ coef) {
-  exp_antenna_body(rel_t, t_base, n, g, antenna, i0tab, jend, coef, blockIdx, gridDim);
+  exp_antenna_body(rel_t, t_base, n, g, perm_ant, i0tab, jend, coef, blockIdx, gridDim);
+}
+
+// Chunk-major copies of one instance's atoms for the scans: entry
+// q kScanLanes + t of a set holds atom i = t C + q (zeros past the last atom):
+// sets 0..n_ant-1 the antenna rows with the gap to the next atom, sets
+// n_ant.. the data rows of each template (when perm_x is given).
+__device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t, int32_t n,
+                                              const float* __restrict__ antenna, int32_t n_ant,
+                                              const float* __restrict__ fafb, int32_t n_x,
+                                              float4* __restrict__ perm_ant,
+                                              float4* __restrict__ perm_x, int64_t e_begin,
+                                              int64_t e_end, int64_t e_step) {
+  const int64_t P = perm_entries(n), C = scan_chunk(n);
+  for (int64_t e = e_begin; e < e_end; e += e_step) {
+    const int64_t set = e / P, r = e - set * P;
+    const int64_t q = r / kScanLanes, t = r - q * kScanLanes;
+    const int64_t i = t * C + q;
+    const bool in = i < n;
+    if (set < n_ant) {
+      const float* a = antenna + set * 3 * (int64_t)n;
+      float4 v = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+      if (in) {
+        const int32_t gap = i + 1 < n ? rel_t[i + 1] - rel_t[i] : -1;
+        v = make_float4(a[i], a[n + i], a[2 * (int64_t)n + i], __int_as_float(gap));
+      }
+      perm_ant[e] = v;
+    } else {
+      const int64_t tq = set - n_ant;
+      const float* x = fafb + tq * 4 * (int64_t)n;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (in) v = make_float4(x[i], x[n + i], x[2 * (int64_t)n + i], x[3 * (int64_t)n + i]);
+      perm_x[tq * P + r] = v;
+    }
+  }
+}
+
+__global__ void k_exp_perm(const int32_t* __restrict__ rel_t, int32_t n,
+                           const float* __restrict__ antenna, int32_t n_ant,
+                           const float* __restrict__ fafb, int32_t n_x,
+                           float4* __restrict__ perm_ant, float4* __restrict__ perm_x) {
+  const int64_t total = perm_entries(n) * (int64_t)(n_ant + n_x);
+  exp_perm_body(rel_t, n, antenna, n_ant, fafb, n_x, perm_ant, perm_x,
+                (int64_t)blockIdx.x * blockDim.x + threadIdx.x, total,
+                (int64_t)gridDim.x * blockDim.x);
+}
+
+cudaError_t launch_exp_perm(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
+  if (p->n_sft <= 0 || (int64_t)p->grid.n_t0 * p->grid.n_tau == 0) return cudaSuccess;
+  const int32_t n_ant = a->shared_antenna ? 1 : p->n_templates;
+  const int32_t n_x = p->ws.perm_x ? p->n_templates : 0;
+  const int64_t total = perm_entries(p->n_sft) * (int64_t)(n_ant + n_x);
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
+  k_exp_perm<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->n_sft, a->antenna, n_ant, a->fafb, n_x,
+                                    p->ws.perm_ant, p->ws.perm_x);
+  p->launches += 1;
+  return cudaGetLastError();
 }
 
 constexpr int kAntennaSmemMaxSft = 9000;   // 3 x (n + 1) float pairs <= 216 KB
@@ -274,16 +335,16 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
     const size_t smem = exp_antenna_smem(p->n_sft);
     cudaFuncSetAttribute(k_exp_antenna, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_exp_antenna<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), kSufThreads, smem, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, a->antenna, p->ws.i0, p->ws.jend, p->ws.coef);
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.i0, p->ws.jend, p->ws.coef);
     p->launches += 1;
     return cudaGetLastError();
   }
   for (int ta = 0; ta < n_ant; ++ta) {
-    const float* ant = a->antenna + (int64_t)ta * 3 * p->n_sft;
+    const float4* perm = p->ws.perm_ant + (int64_t)ta * perm_entries(p->n_sft);
     for (int32_t lo = 0; lo < g.n_tau; lo += p->tau_chunk) {
       const int32_t len = std::min<int32_t>(p->tau_chunk, g.n_tau - lo);
       if (p->n_sft > 0) {
-        k_exp_suffix<<<len, kSufThreads, 0, s>>>(p->ws.rel_t, p->n_sft, ant, g, lo, p->ws.esuf);
+        k_exp_suffix<<<len, kSufThreads, 0, s>>>(perm, p->n_sft, g, lo, p->ws.esuf);
         p->launches += 1;
       }
       const int64_t total = (int64_t)g.n_t0 * len;
@@ -424,15 +485,25 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
 
 
 // ---- persistent multi-instance dispatcher (uneven batches) ----
+__global__ void __launch_bounds__(256) kb_exp_perm(const BItem* __restrict__ items, BUnits u) {
+  batch_loop(items, u, [&](const BItem& it, int64_t k) {
+    const int32_t n_x = it.perm_x ? it.T : 0;
+    const int64_t total = perm_entries(it.n_sft) * (int64_t)(it.n_ant + n_x);
+    const int64_t e0 = k * kPermPerUnit;
+    exp_perm_body(it.rel_t, it.n_sft, it.antenna, it.n_ant, it.fafb, n_x, it.perm_ant, it.perm_x,
+                  e0 + threadIdx.x, min(total, e0 + kPermPerUnit), 256);
+  });
+}
 __global__ void __launch_bounds__(kSufThreads, 3) kb_exp_ant(const BItem* __restrict__ items,
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.antenna, it.i0, it.jend, it.coef,
+    exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.perm_ant, it.i0, it.jend, it.coef,
                      make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                      dim3((unsigned)it.g.n_tau, (unsigned)it.n_ant));
   });
 }
 const void* batch_kernel_exp(int phase) {
+  if (phase == BP_EXP_PERM) return (const void*)kb_exp_perm;
   return phase == BP_EXP_ANT ? (const void*)kb_exp_ant : nullptr;
 }
 size_t exp_antenna_smem(int32_t n_sft) { return sizeof(float2) * 3 * ((size_t)n_sft + 1); }

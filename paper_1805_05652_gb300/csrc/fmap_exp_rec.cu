@@ -54,10 +54,11 @@ __device__ __forceinline__ float rec_ex2(float x) {
 
 __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-          const Coef* __restrict__ coef, int32_t shared_antenna, const float* __restrict__ fafb,
+          const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
           int32_t n_templates, int32_t n_groups, float* __restrict__ map,
           Partial* __restrict__ parts, int64_t stride,
     const uint3 bid, const dim3 gdim) {
+  static_assert(kRecThreads == kScanLanes, "chunk-major copy layout");
   extern __shared__ __align__(16) float s_dyn[];
   float* s_rh = s_dyn;                 // [n] decay after atom i, high part
   float* s_rl = s_dyn + n;             // [n] low part
@@ -69,36 +70,22 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   __shared__ float sS[4][2][kRecThreads / 32];
   __shared__ Partial scratch[kRecThreads / 32];
   __shared__ TauDecay s_td;
+  __shared__ float2 s_tab[kPowTab];
   const int ni = bid.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
   const TauDecay td = tau_decay_block(tau, 1.0, g.t_sft, &s_td);
-  const double inv_tau = td.inv_s;
+  decay_table_fill(td.rho1, s_tab);
+  __syncthreads();
   const int64_t np1 = (int64_t)n + 1;
-  // Decays of this tau, once for all the block's templates: whole multiples k
-  // of T_sft take the k-th power of the one-SFT decay, other gaps use exp.
-  // (float-float powers of the one-SFT decay; FP64 exp only off the lattice)
+  // Decays of this tau, once for all the block's templates: gaps of k whole
+  // SFTs from the table of float-float powers of the one-SFT decay, other
+  // gaps by FP64 exp.
   {
-    const FF rho1 = td.rho1;
     const float inv_tsft = 1.0f / (float)g.t_sft;
     for (int i = tid; i < n; i += kRecThreads) {
       FF r{0.0f, 0.0f};
-      if (i + 1 < n) {
-        const int32_t gap = rel_t[i + 1] - rel_t[i];
-        const int32_t k = __float2int_rn((float)gap * inv_tsft);
-        if (k == 1 && gap == g.t_sft) {
-          r = rho1;
-        } else if (k >= 2 && k <= 64 && (int64_t)k * g.t_sft == gap) {
-          FF acc{1.0f, 0.0f}, p = rho1;
-          for (int q = k; q; q >>= 1) {
-            if (q & 1) acc = ff_mul(acc, p);
-            p = ff_mul(p, p);
-          }
-          r = acc;
-        } else {
-          r = ff_of(exp(-(double)gap * inv_tau));
-        }
-      }
+      if (i + 1 < n) r = gap_decay(rel_t[i + 1] - rel_t[i], g.t_sft, inv_tsft, s_tab, td.inv_s);
       s_rh[i] = r.h;
       s_rl[i] = r.l;
     }
@@ -134,29 +121,41 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   const int32_t t_hi = (int32_t)((int64_t)(bid.y + 1) * n_templates / n_groups);
   for (int32_t tq = t_lo; tq < t_hi; ++tq) {
     __syncthreads();   // decays ready; previous template's cells done with s_e
-    const float* x = fafb + (int64_t)tq * 4 * n;
-    // phase 1: this thread's chunk as one affine map, E[s0] = S + R E[e0];
-    // the data of each run of kRecChunk SFTs is loaded before its serial chain
-    FF R = {1.0f, 0.0f}, S[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    const float4* x = perm_x + (int64_t)tq * perm_entries(n);   // chunk-major data rows
+    // phase 1: this thread's chunk as one affine map, E[s0] = S + R E[e0],
+    // by the compensated recurrence (folded back every kRecChunk atoms); the
+    // data of each run of kRecChunk SFTs is loaded before its serial chain,
+    // and positions past the chunk's end are identity steps (x = 0, r = 1)
+    float Rh = 1.0f, Rc = 0.0f, Sh[4] = {0.f, 0.f, 0.f, 0.f}, Sc[4] = {0.f, 0.f, 0.f, 0.f};
     float xv[kRecChunk][4];
-    for (int b0 = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk; e0 > s0 && b0 >= s0;
-         b0 -= kRecChunk) {
+    auto load_chunk = [&](int b0) {
 #pragma unroll
       for (int q = 0; q < kRecChunk; ++q) {
         const int i = b0 + q;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) xv[q][c] = (i < e0) ? __ldg(x + (int64_t)c * n + i) : 0.0f;
+        const float4 v = (i < e0) ? __ldg(x + (int64_t)(i - s0) * kRecThreads + tid)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        xv[q][0] = v.x;
+        xv[q][1] = v.y;
+        xv[q][2] = v.z;
+        xv[q][3] = v.w;
       }
+    };
+    auto decay = [&](int i) { return i < e0 ? FF{s_rh[i], s_rl[i]} : FF{1.0f, 0.0f}; };
+    for (int b0 = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk; e0 > s0 && b0 >= s0;
+         b0 -= kRecChunk) {
+      load_chunk(b0);
 #pragma unroll
       for (int q = kRecChunk - 1; q >= 0; --q) {
-        const int i = b0 + q;
-        if (i >= e0) continue;
-        const FF r = {s_rh[i], s_rl[i]};
+        const FF r = decay(b0 + q);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) S[c] = ff_axpy(r, S[c], xv[q][c]);
-        R = ff_mul(r, R);
+        for (int c = 0; c < 4; ++c) ch_step(r, xv[q][c], Sh[c], Sc[c]);
+        ch_mul(r, Rh, Rc);
       }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ch_norm(Sh[c], Sc[c]);
+      ch_norm(Rh, Rc);
     }
+    FF R = {Rh, Rc}, S[4] = {{Sh[0], Sc[0]}, {Sh[1], Sc[1]}, {Sh[2], Sc[2]}, {Sh[3], Sc[3]}};
     // phase 2: suffix composition within the warp (self o later)
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -195,29 +194,29 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
 #pragma unroll
       for (int c = 0; c < 4; ++c) lS[c] = ff_add({sS[c][0][v], sS[c][1][v]}, ff_mul(Rv, lS[c]));
     }
-    FF e[4];
+    float eh[4], ec[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) e[c] = ff_add(hS[c], ff_mul(hR, lS[c]));
+    for (int c = 0; c < 4; ++c) {
+      const FF e = ff_add(hS[c], ff_mul(hR, lS[c]));
+      eh[c] = e.h;
+      ec[c] = e.l;
+    }
     // phase 3: recompute the chunk from its carry and keep E (rounded) in smem
     for (int b0 = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk; e0 > s0 && b0 >= s0;
          b0 -= kRecChunk) {
-#pragma unroll
-      for (int q = 0; q < kRecChunk; ++q) {
-        const int i = b0 + q;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) xv[q][c] = (i < e0) ? __ldg(x + (int64_t)c * n + i) : 0.0f;
-      }
+      load_chunk(b0);
 #pragma unroll
       for (int q = kRecChunk - 1; q >= 0; --q) {
         const int i = b0 + q;
-        if (i >= e0) continue;
-        const FF r = {s_rh[i], s_rl[i]};
+        const FF r = decay(i);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          e[c] = ff_axpy(r, e[c], xv[q][c]);
-          s_e[c * np1 + i] = e[c].h + e[c].l;
+          ch_step(r, xv[q][c], eh[c], ec[c]);
+          if (i < e0) s_e[c * np1 + i] = eh[c] + ec[c];
         }
       }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ch_norm(eh[c], ec[c]);
     }
     if (tid < 4) s_e[tid * np1 + n] = 0.0f;
     __syncthreads();
@@ -246,10 +245,10 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
 __global__ void __launch_bounds__(kRecThreads)
 k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-          const Coef* __restrict__ coef, int32_t shared_antenna, const float* __restrict__ fafb,
+          const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
           int32_t n_templates, int32_t n_groups, float* __restrict__ map,
           Partial* __restrict__ parts, int64_t stride) {
-  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, fafb, n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
+  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
 bool exp_rec_supported(int32_t n_sft, int32_t) { return n_sft <= kRecMaxSft; }
@@ -268,7 +267,7 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
       1, std::min<int64_t>(p->n_templates, (want + g.n_tau - 1) / g.n_tau));
   dim3 grid((unsigned)g.n_tau, (unsigned)groups);
   k_exp_rec<<<grid, kRecThreads, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0,
-                                            p->ws.jend, p->ws.coef, a->shared_antenna, a->fafb,
+                                            p->ws.jend, p->ws.coef, a->shared_antenna, p->ws.perm_x,
                                             p->n_templates, groups, d_2F, p->ws.partials,
                                             p->part_stride);
   p->launches += 1;
@@ -280,7 +279,7 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
 __global__ void __launch_bounds__(kRecThreads, 3) kb_exp_rec(const BItem* __restrict__ items,
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    exp_rec_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared, it.fafb,
+    exp_rec_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared, it.perm_x,
                  it.T, it.groups, it.map, it.partials, it.part_stride,
                  make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                  dim3((unsigned)it.g.n_tau, (unsigned)it.groups));

@@ -25,13 +25,26 @@ constexpr int kFixThreads = 128;
 constexpr int kFixWeights = 256;
 constexpr int kFixCellModeT = 8;    // below: threads over entries, not templates
 
-// Per block of kFlagBlock entries: number of entries with valid == 2.
+// Per unit of kFlagUnit entries (kFlagPer per thread, strided by the block):
+// number of entries with valid == 2.
+constexpr int kFlagPer = kFlagUnit / kFlagBlock;
 __device__ __forceinline__ void flag_count_body(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt,
     const uint3 bid, const dim3 gdim) {
-  const int64_t e = (int64_t)bid.x * kFlagBlock + threadIdx.x;
-  const bool f = e < n_entries && coef[e].valid == 2.0f;
-  const int c = __syncthreads_count(f);
-  if (threadIdx.x == 0) blockcnt[bid.x] = c;
+  __shared__ int32_t warp_cnt[kFlagBlock / 32];
+  const int64_t base = (int64_t)bid.x * kFlagUnit + threadIdx.x;
+  unsigned c = 0;
+#pragma unroll
+  for (int q = 0; q < kFlagPer; ++q) {
+    const int64_t e = base + q * kFlagBlock;
+    c += (e < n_entries && coef[e].valid == 2.0f) ? 1u : 0u;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) warp_cnt[threadIdx.x >> 5] = (int32_t)c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const unsigned t = __reduce_add_sync(0xffffffffu, (unsigned)warp_cnt[threadIdx.x]);
+    if (threadIdx.x == 0) blockcnt[bid.x] = (int32_t)t;
+  }
 }
 
 __global__ void __launch_bounds__(kFlagBlock)
@@ -82,22 +95,41 @@ k_flag_scan(int32_t* __restrict__ blockcnt, int64_t n_blocks, int32_t* __restric
   flag_scan_body(blockcnt, n_blocks, n_flag, blockIdx, gridDim);
 }
 
-// Ordered writes of the marked entries.
+// Ordered writes of the marked entries of one unit: kFlagPer rounds of
+// kFlagBlock consecutive entries, each placed by a warp ballot and an
+// exclusive scan of the warps' counts.
 __device__ __forceinline__ void flag_write_body(const Coef* __restrict__ coef, int64_t n_entries,
              const int32_t* __restrict__ blockoff, int64_t* __restrict__ list,
     const uint3 bid, const dim3 gdim) {
   __shared__ int32_t warp_cnt[kFlagBlock / 32];
-  const int64_t e = (int64_t)bid.x * kFlagBlock + threadIdx.x;
-  const bool f = e < n_entries && coef[e].valid == 2.0f;
+  __shared__ int32_t warp_off[kFlagBlock / 32];
+  __shared__ int32_t s_total;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t bal = __ballot_sync(0xffffffffu, f);
-  if (lane == 0) warp_cnt[warp] = __popc(bal);
-  __syncthreads();
-  if (f) {
-    int64_t off = blockoff[bid.x];
-    for (int w = 0; w < warp; ++w) off += warp_cnt[w];
-    off += __popc(bal & ((1u << lane) - 1u));
-    if (off < n_entries) list[off] = e;   // the list holds at most n_entries
+  int64_t run = blockoff[bid.x];
+#pragma unroll 1
+  for (int q = 0; q < kFlagPer; ++q) {
+    const int64_t e = (int64_t)bid.x * kFlagUnit + q * kFlagBlock + threadIdx.x;
+    const bool f = e < n_entries && coef[e].valid == 2.0f;
+    const uint32_t bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_cnt[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+      const int32_t v = warp_cnt[lane];
+      int32_t x = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+      }
+      warp_off[lane] = x - v;
+      if (lane == 31) s_total = x;
+    }
+    __syncthreads();
+    if (f) {
+      const int64_t off = run + warp_off[warp] + __popc(bal & ((1u << lane) - 1u));
+      if (off < n_entries) list[off] = e;   // the list holds at most n_entries
+    }
+    run += s_total;
   }
 }
 
@@ -206,9 +238,20 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
     const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
     const double inv_tau = 1.0 / (double)(g.tau_min + (int64_t)nn * g.dtau);
     double A = 0, B = 0, C = 0, far = 0, fai = 0, fbr = 0, fbi = 0;
+    // Exponential weights along the window by products of the per-gap
+    // decays (one exp for the first atom and one for the one-SFT decay;
+    // relative error ~(j - i0) ulp), the FP64 pipe being 1/64 of FP32 rate.
+    const bool ex = g.window != FMAP_RECT;
+    double w = 1.0, rho1 = 0.0;
+    if (ex && j > i0) {
+      w = exp(-(double)((int64_t)rel_t[i0] - t0rel) * inv_tau);
+      rho1 = exp(-(double)g.t_sft * inv_tau);
+    }
     for (int32_t a = i0; a < j; ++a) {
-      const double w = (g.window == FMAP_RECT) ? 1.0
-                                                : exp(-(double)((int64_t)rel_t[a] - t0rel) * inv_tau);
+      if (ex && a > i0) {
+        const int32_t gap = rel_t[a] - rel_t[a - 1];
+        w *= gap == g.t_sft ? rho1 : (gap == 2 * g.t_sft ? rho1 * rho1 : exp(-(double)gap * inv_tau));
+      }
       const double w2 = w * w;
       A += w2 * (double)ant[a];
       B += w2 * (double)ant[n_sft + a];
@@ -265,7 +308,7 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
   const int64_t n_ant = a->shared_antenna ? 1 : p->n_templates;
   const int64_t n_entries = cells * n_ant;
   if (n_entries == 0 || p->n_templates == 0) return cudaSuccess;
-  const int64_t n_blocks = (n_entries + kFlagBlock - 1) / kFlagBlock;
+  const int64_t n_blocks = (n_entries + kFlagUnit - 1) / kFlagUnit;
   k_flag_count<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.coef, n_entries, p->ws.flag_blocks);
   k_flag_scan<<<1, 1024, 0, s>>>(p->ws.flag_blocks, n_blocks, p->ws.n_flag);
   k_flag_write<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.coef, n_entries, p->ws.flag_blocks,
@@ -298,7 +341,7 @@ __global__ void __launch_bounds__(kFlagBlock) kb_flag_count(const BItem* __restr
 }
 __global__ void __launch_bounds__(1024) kb_flag_scan(const BItem* __restrict__ items, BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t) {
-    flag_scan_body(it.flag_blocks, (it.flag_entries + kFlagBlock - 1) / kFlagBlock, it.n_flag,
+    flag_scan_body(it.flag_blocks, (it.flag_entries + kFlagUnit - 1) / kFlagUnit, it.n_flag,
                    make_uint3(0, 0, 0), dim3(1));
   });
 }
@@ -311,18 +354,23 @@ __global__ void __launch_bounds__(kFlagBlock) kb_flag_write(const BItem* __restr
 }
 __global__ void __launch_bounds__(kFixThreads) kb_fixup(const BItem* __restrict__ items,
                                                         BUnits u) {
+  // unit k: slots [sg * kFixSlotsPerUnit, ...) of template (block) y
+  constexpr int kGroups = kFixSlots / kFixSlotsPerUnit;
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    if (it.T < kFixCellModeT)
-      fixup_cells_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base,
-                       it.n_sft, it.g, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
-                       it.partials, it.part_stride, it.n_tiles, (int32_t)(k % kFixSlots),
-                       (int32_t)(k / kFixSlots));
-    else
-      fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft,
-                 it.g, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,
-                 it.part_stride, it.n_tiles,
-                 make_uint3((unsigned)(k % kFixSlots), (unsigned)(k / kFixSlots), 0),
-                 dim3((unsigned)kFixSlots, (unsigned)((it.T + kFixThreads - 1) / kFixThreads)));
+    const int32_t sg = (int32_t)(k % kGroups), y = (int32_t)(k / kGroups);
+    for (int q = 0; q < kFixSlotsPerUnit; ++q) {
+      const int32_t b = sg * kFixSlotsPerUnit + q;
+      if (it.T < kFixCellModeT)
+        fixup_cells_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base,
+                         it.n_sft, it.g, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
+                         it.partials, it.part_stride, it.n_tiles, b, y);
+      else
+        fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft,
+                   it.g, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,
+                   it.part_stride, it.n_tiles, make_uint3((unsigned)b, (unsigned)y, 0),
+                   dim3((unsigned)kFixSlots, (unsigned)((it.T + kFixThreads - 1) / kFixThreads)));
+      __syncthreads();   // the bodies' shared scratch is reused by the next slot
+    }
   });
 }
 const void* batch_kernel_fixup(int phase) {

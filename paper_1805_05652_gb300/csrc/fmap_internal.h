@@ -42,12 +42,22 @@ struct __align__(16) Partial {
 
 // Per-cell 2F coefficients.  2F = k1 |Fa|^2 + k2 |Fb - beta Fa|^2, which is
 // Eq. (F_FaFb) times two with k1 = 2/A, beta = C/A, k2 = 2A/D (completing the
-// square in Fa).  valid: 0 = invalid (fewer than 2 atoms or D <= 0 in FP64;
-// k1 = k2 = 0), 1 = evaluated by the fast kernels, 2 = ill-conditioned
-// (A B / D > kCondThreshold): left to the FP64 fix-up of fmap_fixup.cu.
+// square in Fa).  valid: 0 = invalid (fewer than 2 atoms; k1 = k2 = 0),
+// 1 = evaluated by the fast kernels, 2 = ill-conditioned or undecided
+// (A B / D > kCondThreshold, or D not clearly positive in float-float): left
+// to the FP64 fix-up of fmap_fixup.cu, which also decides D > 0.
 constexpr double kCondThreshold = 100.0;
 // Reduction slots per template written by the fix-up kernel.
 constexpr int kFixSlots = 512;
+// Entries per count of the marked-entry compaction (1024 threads x 8).
+constexpr int kFlagUnit = 8192;
+// Threads of the exponential-window scans.  Thread t of a scan owns the atoms
+// [t C, t C + C), C = ceil(N / kScanLanes); the scans read the atoms from a
+// chunk-major copy (entry q kScanLanes + t holds atom t C + q), so the loads
+// of a warp at one chunk position are contiguous.
+constexpr int kScanLanes = 256;
+__host__ __device__ inline int64_t scan_chunk(int32_t n_sft) { return ((int64_t)n_sft + kScanLanes - 1) / kScanLanes; }
+__host__ __device__ inline int64_t perm_entries(int32_t n_sft) { return scan_chunk(n_sft) * kScanLanes; }
 struct __align__(16) Coef {
   float k1;
   float beta;
@@ -67,12 +77,15 @@ struct Workspace {
   Coef* coef = nullptr;          // [T_ant][n_t0][n_tau]
   Partial* partials = nullptr;   // [T][n_tiles + kFixSlots]
   void* groups = nullptr;        // [T][reduce_groups_of(n_tiles + kFixSlots)] FP64 group merges
-  int32_t* flag_blocks = nullptr;  // [ceil(T_ant cells / 1024)] counts, then offsets
+  int32_t* flag_blocks = nullptr;  // [ceil(T_ant cells / kFlagUnit)] counts, then offsets
   int32_t* n_flag = nullptr;       // [1] number of ill-conditioned entries
   int64_t* flag_list = nullptr;    // [T_ant cells] their indices, ascending
   // rect
-  double* pa = nullptr;          // [T_ant][N+1][4] FP64 antenna prefix (a2, b2, ab, pad)
+  float4* pa = nullptr;          // [T_ant][N+1][2] FP64 antenna prefix (a2, b2, ab, 0) as hi4, lo4
   float4* px = nullptr;          // [T][N+1][2] float-float data prefix (hi4, lo4)
+  // exp: chunk-major copies of the atoms (perm_entries(N) per set)
+  float4* perm_ant = nullptr;    // [T_ant][.] (a2, b2, ab, gap to the next atom as int bits; -1 last)
+  float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
   // exp
   float2* esuf = nullptr;        // [tau_chunk][3][N+1] float-float decayed suffix sums
   // tensor-core operands
@@ -127,6 +140,7 @@ cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s);
 cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                         int64_t* tiles_used, cudaEvent_t mark);
 cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
+cudaError_t launch_exp_perm(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
 cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                              int64_t* tiles_used);
 cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,

@@ -704,9 +704,10 @@ __global__ void __launch_bounds__(kScanThreads) kb_rect_ant(const BItem* __restr
 }
 __global__ void __launch_bounds__(256) kb_rect_coef(const BItem* __restrict__ items, BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    rect_coef_body(it.i0, it.jend, (const P4*)it.pa, it.n_sft, it.g.n_t0, it.g.n_tau, it.n_ant,
-                   it.coef, make_uint3((unsigned)k, 0, 0),
-                   dim3((unsigned)((it.cells * it.n_ant + 255) / 256)));
+    const unsigned nb = (unsigned)((it.cells * it.n_ant + 255) / 256);
+    for (int q = 0; q < kCoefBlocksPerUnit; ++q)
+      rect_coef_body(it.i0, it.jend, (const P4*)it.pa, it.n_sft, it.g.n_t0, it.g.n_tau, it.n_ant,
+                     it.coef, make_uint3((unsigned)(k * kCoefBlocksPerUnit + q), 0, 0), dim3(nb));
   });
 }
 __global__ void __launch_bounds__(kScanThreads) kb_rect_data(const BItem* __restrict__ items,
