@@ -111,9 +111,10 @@ static int64_t units_of(const fmap_plan_s* p, const fmap_batch_item& it, int ph,
     case BP_PREP: return p->n_sft > 0 ? (rel_t_entries(p->n_sft) + 255) / 256 : 0;
     case BP_INDEX: return cells > 0 ? (g.n_t0 + kIdxRowsPerUnit - 1) / kIdxRowsPerUnit : 0;
     case BP_EXP_PERM: {
-      if (rect || cells == 0 || p->n_sft <= 0) return 0;
-      const int64_t sets = n_ant + ((p->flags & FMAP_PLAN_EXP_RECURRENCE) ? T : 0);
-      return (perm_entries(p->n_sft) * sets + kPermPerUnit - 1) / kPermPerUnit;
+      if (rect || cells == 0) return 0;
+      const int32_t n_x = (p->flags & FMAP_PLAN_EXP_RECURRENCE) ? (int32_t)T : 0;
+      return (exp_copy_entries(p->n_sft, (int32_t)n_ant, n_x, g.n_tau) + kPermPerUnit - 1) /
+             kPermPerUnit;
     }
     case BP_RECT_ANT: return rect && cells > 0 && p->n_sft > 0 ? n_ant : 0;
     case BP_EXP_ANT: return !rect && cells > 0 ? g.n_tau * n_ant : 0;
@@ -176,6 +177,7 @@ static BItem make_bitem(const fmap_plan_s* p, const fmap_batch_item& it, uint32_
   b.pa = w.pa;
   b.perm_ant = w.perm_ant;
   b.perm_x = w.perm_x;
+  b.tauc = w.tauc;
   b.px = w.px;
   return b;
 }

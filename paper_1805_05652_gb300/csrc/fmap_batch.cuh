@@ -36,6 +36,7 @@ struct BItem {
   float4* pa;
   float4* perm_ant;
   float4* perm_x;
+  TauTab* tauc;
   float4* px;
 };
 

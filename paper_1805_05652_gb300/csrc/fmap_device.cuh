@@ -130,52 +130,33 @@ __device__ __forceinline__ FF ff_of(double x) {
   return {h, (float)(x - (double)h)};
 }
 
-// Decay constants of one tau for a weight e^{-s (t - t0) / tau} (s = 1 for
-// the data weight w, s = 2 for the antenna weight w^2): the one-SFT decay as
-// a float pair, s / tau in FP64 (for gaps off the T_sft lattice) and the
-// FP32 exp2 slope -s log2(e) / tau.  GB300 runs FP64 at 1/64 of the FP32
-// rate, so a block computes these once (one thread) and shares them.
-struct TauDecay {
-  FF rho1;
-  double inv_s;
-  float c2;
-};
-__device__ __forceinline__ TauDecay tau_decay(double tau, double s, int32_t t_sft) {
-  TauDecay d;
-  d.inv_s = s / tau;
-  d.rho1 = ff_of(exp(-(double)t_sft * d.inv_s));
-  d.c2 = (float)(-1.4426950408889634 * d.inv_s);
-  return d;
-}
-// The block's copy of tau_decay(tau, s, t_sft) through shared memory slot
-// *slot; every thread of the block calls it (it synchronises the block).
-__device__ __forceinline__ TauDecay tau_decay_block(double tau, double s, int32_t t_sft,
-                                                    TauDecay* slot) {
-  if (threadIdx.x == 0) *slot = tau_decay(tau, s, t_sft);
-  __syncthreads();
-  return *slot;
-}
-
-// Decays over gaps of k whole SFTs, k < kPowTab: tab[k] = rho1^k as a float
-// pair (binary powering in float-float, ~k ulp of 2^-48); tab[0] = 1.  The
-// block's threads 0..kPowTab-1 fill it; the caller synchronises after.
-constexpr int kPowTab = 16;
-__device__ __forceinline__ void decay_table_fill(FF rho1, float2* tab) {
-  const int k = threadIdx.x;
-  if (k < kPowTab) {
-    FF acc{1.0f, 0.0f}, r = rho1;
-    for (int q = k; q; q >>= 1) {
-      if (q & 1) acc = ff_mul(acc, r);
-      r = ff_mul(r, r);
+// Fills the per-tau constants of tau_n (one thread).  The one-SFT decay is
+// an FP64 exp split into a float pair; its powers come by binary powering in
+// float-float (~k ulp of 2^-48).
+__device__ __forceinline__ void tau_tab_fill(const fmap_grid& g, int64_t ni, TauTab* out) {
+  TauTab t;
+  t.inv_tau = 1.0 / (double)(g.tau_min + ni * g.dtau);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double inv_s = (double)(s + 1) * t.inv_tau;
+    t.c2[s] = (float)(-1.4426950408889634 * inv_s);
+    const FF rho1 = ff_of(exp(-(double)g.t_sft * inv_s));
+    for (int k = 0; k < kPowTab; ++k) {
+      FF acc{1.0f, 0.0f}, r = rho1;
+      for (int q = k; q; q >>= 1) {
+        if (q & 1) acc = ff_mul(acc, r);
+        r = ff_mul(r, r);
+      }
+      t.pw[s][k] = make_float2(acc.h, acc.l);
     }
-    tab[k] = make_float2(acc.h, acc.l);
   }
+  *out = t;
 }
-// Decay over one gap between consecutive atoms: a table entry for gaps of
-// 1..kPowTab-1 whole SFTs (branch-free for the usual spacings), FP64 exp
-// otherwise (gaps off the T_sft lattice; inv_s = s / tau).
+// Decay over one gap between consecutive atoms: a table entry (pw of the
+// tau's TauTab) for gaps of 1..kPowTab-1 whole SFTs, FP64 exp otherwise
+// (gaps off the T_sft lattice; inv_s = s / tau).
 __device__ __forceinline__ FF gap_decay(int32_t gap, int32_t t_sft, float inv_tsft,
-                                        const float2* tab, double inv_s) {
+                                        const float2* __restrict__ tab, double inv_s) {
   const int32_t k = __float2int_rn((float)gap * inv_tsft);
   if (k >= 1 && k < kPowTab && k * t_sft == gap) {
     const float2 v = tab[k];
@@ -327,9 +308,12 @@ __device__ __forceinline__ Coef make_coef_ff(FF A, FF B, FF C, int32_t count) {
     c.valid = 2.0f;
     return c;
   }
-  c.k1 = 2.0f / af;
-  c.beta = cf / af;
-  c.k2 = 2.0f * af / df;
+  // two correctly rounded reciprocals instead of three divisions (k1 is
+  // exact as before; beta and k2 within 1.5 ulp)
+  const float ia = __frcp_rn(af);
+  c.k1 = 2.0f * ia;
+  c.beta = cf * ia;
+  c.k2 = (2.0f * af) * __frcp_rn(df);
   // A B > 100 D, compared in float-float
   const FF ab = ff_mul(A, B), d100 = ff_mul_f(D, kCondThreshold);
   const FF gap = ff_sub(d100, ab);

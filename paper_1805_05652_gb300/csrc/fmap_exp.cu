@@ -50,31 +50,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // it together.
 __device__ __forceinline__ void antenna_suffix(const float4* __restrict__ perm, int32_t n,
                                                const fmap_grid& g,
-                                               const TauDecay& td, float2* E,
+                                               const TauTab* __restrict__ tt, float2* E,
                                                float (*sR)[kSufThreads / 32],
                                                float (*sS)[2][kSufThreads / 32]) {
   static_assert(kSufThreads == kScanLanes, "chunk-major copy layout");
-  const double inv_s = td.inv_s;
+  const double inv_s = 2.0 * tt->inv_tau;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int C = (n + kSufThreads - 1) / kSufThreads;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
-  // Decay over one gap: e^{-2 gap / tau}.  Gaps that are whole multiples k of
-  // T_sft (the usual case) take the k-th power of the one-SFT decay (in
-  // float-float); others use FP64 exp.
-  const FF rho1 = td.rho1;
+  // Decay over one gap: e^{-2 gap / tau}, from the tau's table of powers of
+  // the one-SFT decay (FP64 exp off the T_sft lattice).
   const float inv_tsft = 1.0f / (float)g.t_sft;
   auto rho_of_gap = [&](int32_t gap) -> FF {
-    const int32_t k = __float2int_rn((float)gap * inv_tsft);
-    if (k == 1 && g.t_sft == gap) return rho1;
-    if (k >= 2 && k <= 64 && (int64_t)k * g.t_sft == gap) {
-      FF acc{1.0f, 0.0f}, r = rho1;
-      for (int q = k; q; q >>= 1) {
-        if (q & 1) acc = ff_mul(acc, r);
-        r = ff_mul(r, r);
-      }
-      return acc;
-    }
-    return ff_of(exp(-(double)gap * inv_s));
+    return gap_decay(gap, g.t_sft, inv_tsft, tt->pw[1], inv_s);
   };
   // The chunk's atoms (three antenna rows and the gap to the next atom) are
   // read kSufChunk at a time ahead of each serial run, so the chain does not
@@ -178,15 +166,12 @@ __device__ __forceinline__ void antenna_suffix(const float4* __restrict__ perm, 
 
 // Global-memory suffix sums for one tau of a tau chunk (long data sets).
 __global__ void __launch_bounds__(kSufThreads)
-k_exp_suffix(const float4* __restrict__ perm, int32_t n, fmap_grid g, int32_t n_lo,
-             float2* __restrict__ esuf) {
+k_exp_suffix(const float4* __restrict__ perm, const TauTab* __restrict__ tauc, int32_t n,
+             fmap_grid g, int32_t n_lo, float2* __restrict__ esuf) {
   __shared__ float sR[2][kSufThreads / 32];
   __shared__ float sS[3][2][kSufThreads / 32];
-  __shared__ TauDecay s_td;
   const int ni = blockIdx.x;
-  const double tau = (double)(g.tau_min + (int64_t)(n_lo + ni) * g.dtau);
-  const TauDecay td = tau_decay_block(tau, 2.0, g.t_sft, &s_td);
-  antenna_suffix(perm, n, g, td, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
+  antenna_suffix(perm, n, g, tauc + n_lo + ni, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
 }
 
 // A, B, C of a cell from the suffix sums E of its tau, then its coefficients;
@@ -220,46 +205,52 @@ __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t,
 // coefficients of every cell (t0_m, tau_n).  Blocks run tau-fastest, so their
 // strided coefficient stores merge in L2.
 __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
-              fmap_grid g, const float4* __restrict__ perm_ant, const int32_t* __restrict__ i0tab,
-              const int32_t* __restrict__ jend, Coef* __restrict__ coef,
-    const uint3 bid, const dim3 gdim) {
+              fmap_grid g, const float4* __restrict__ perm_ant, const TauTab* __restrict__ tauc,
+              const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+              Coef* __restrict__ coef, const uint3 bid, const dim3 gdim) {
   extern __shared__ float2 s_E[];
   __shared__ float sR[2][kSufThreads / 32];
   __shared__ float sS[3][2][kSufThreads / 32];
-  __shared__ TauDecay s_td;
   const int ni = bid.x, ta = bid.y;
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
-  const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
-  const TauDecay td = tau_decay_block(tau, 2.0, g.t_sft, &s_td);
-  antenna_suffix(perm_ant + (int64_t)ta * perm_entries(n), n, g, td, s_E, sR, sS);
+  const TauTab* tt = tauc + ni;
+  antenna_suffix(perm_ant + (int64_t)ta * perm_entries(n), n, g, tt, s_E, sR, sS);
   __syncthreads();
   const int64_t tb = n > 0 ? *t_base : 0;
   for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
     const int64_t cell = (int64_t)m * g.n_tau + ni;
     coef[(int64_t)ta * cells + cell] =
-        exp_cell_coef(rel_t, n, g, m, td.c2, i0tab[m], jend[cell], tb, s_E);
+        exp_cell_coef(rel_t, n, g, m, tt->c2[1], i0tab[m], jend[cell], tb, s_E);
   }
 }
 
 __global__ void __launch_bounds__(kSufThreads)
 k_exp_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
-              fmap_grid g, const float4* __restrict__ perm_ant, const int32_t* __restrict__ i0tab,
-              const int32_t* __restrict__ jend, Coef* __restrict__ coef) {
-  exp_antenna_body(rel_t, t_base, n, g, perm_ant, i0tab, jend, coef, blockIdx, gridDim);
+              fmap_grid g, const float4* __restrict__ perm_ant, const TauTab* __restrict__ tauc,
+              const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+              Coef* __restrict__ coef) {
+  exp_antenna_body(rel_t, t_base, n, g, perm_ant, tauc, i0tab, jend, coef, blockIdx, gridDim);
 }
 
 // Chunk-major copies of one instance's atoms for the scans: entry
 // q kScanLanes + t of a set holds atom i = t C + q (zeros past the last atom):
 // sets 0..n_ant-1 the antenna rows with the gap to the next atom, sets
-// n_ant.. the data rows of each template (when perm_x is given).
+// n_ant.. the data rows of each template (when perm_x is given); then the
+// per-tau constants (n_tau more entries).
 __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t, int32_t n,
                                               const float* __restrict__ antenna, int32_t n_ant,
                                               const float* __restrict__ fafb, int32_t n_x,
                                               float4* __restrict__ perm_ant,
-                                              float4* __restrict__ perm_x, int64_t e_begin,
+                                              float4* __restrict__ perm_x, const fmap_grid& g,
+                                              TauTab* __restrict__ tauc, int64_t e_begin,
                                               int64_t e_end, int64_t e_step) {
   const int64_t P = perm_entries(n), C = scan_chunk(n);
+  const int64_t n_copy = P * (int64_t)(n_ant + n_x);
   for (int64_t e = e_begin; e < e_end; e += e_step) {
+    if (e >= n_copy) {   // entries past the copies: the per-tau constants
+      tau_tab_fill(g, e - n_copy, tauc + (e - n_copy));
+      continue;
+    }
     const int64_t set = e / P, r = e - set * P;
     const int64_t q = r / kScanLanes, t = r - q * kScanLanes;
     const int64_t i = t * C + q;
@@ -285,21 +276,22 @@ __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t,
 __global__ void k_exp_perm(const int32_t* __restrict__ rel_t, int32_t n,
                            const float* __restrict__ antenna, int32_t n_ant,
                            const float* __restrict__ fafb, int32_t n_x,
-                           float4* __restrict__ perm_ant, float4* __restrict__ perm_x) {
-  const int64_t total = perm_entries(n) * (int64_t)(n_ant + n_x);
-  exp_perm_body(rel_t, n, antenna, n_ant, fafb, n_x, perm_ant, perm_x,
+                           float4* __restrict__ perm_ant, float4* __restrict__ perm_x,
+                           fmap_grid g, TauTab* __restrict__ tauc) {
+  const int64_t total = exp_copy_entries(n, n_ant, n_x, g.n_tau);
+  exp_perm_body(rel_t, n, antenna, n_ant, fafb, n_x, perm_ant, perm_x, g, tauc,
                 (int64_t)blockIdx.x * blockDim.x + threadIdx.x, total,
                 (int64_t)gridDim.x * blockDim.x);
 }
 
 cudaError_t launch_exp_perm(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
-  if (p->n_sft <= 0 || (int64_t)p->grid.n_t0 * p->grid.n_tau == 0) return cudaSuccess;
+  if ((int64_t)p->grid.n_t0 * p->grid.n_tau == 0) return cudaSuccess;
   const int32_t n_ant = a->shared_antenna ? 1 : p->n_templates;
   const int32_t n_x = p->ws.perm_x ? p->n_templates : 0;
-  const int64_t total = perm_entries(p->n_sft) * (int64_t)(n_ant + n_x);
+  const int64_t total = exp_copy_entries(p->n_sft, n_ant, n_x, p->grid.n_tau);
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
   k_exp_perm<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->n_sft, a->antenna, n_ant, a->fafb, n_x,
-                                    p->ws.perm_ant, p->ws.perm_x);
+                                    p->ws.perm_ant, p->ws.perm_x, p->grid, p->ws.tauc);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -335,7 +327,8 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
     const size_t smem = exp_antenna_smem(p->n_sft);
     cudaFuncSetAttribute(k_exp_antenna, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_exp_antenna<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), kSufThreads, smem, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.i0, p->ws.jend, p->ws.coef);
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.tauc, p->ws.i0, p->ws.jend,
+        p->ws.coef);
     p->launches += 1;
     return cudaGetLastError();
   }
@@ -344,7 +337,7 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
     for (int32_t lo = 0; lo < g.n_tau; lo += p->tau_chunk) {
       const int32_t len = std::min<int32_t>(p->tau_chunk, g.n_tau - lo);
       if (p->n_sft > 0) {
-        k_exp_suffix<<<len, kSufThreads, 0, s>>>(perm, p->n_sft, g, lo, p->ws.esuf);
+        k_exp_suffix<<<len, kSufThreads, 0, s>>>(perm, p->ws.tauc, p->n_sft, g, lo, p->ws.esuf);
         p->launches += 1;
       }
       const int64_t total = (int64_t)g.n_t0 * len;
@@ -488,16 +481,17 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
 __global__ void __launch_bounds__(256) kb_exp_perm(const BItem* __restrict__ items, BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     const int32_t n_x = it.perm_x ? it.T : 0;
-    const int64_t total = perm_entries(it.n_sft) * (int64_t)(it.n_ant + n_x);
+    const int64_t total = exp_copy_entries(it.n_sft, it.n_ant, n_x, it.g.n_tau);
     const int64_t e0 = k * kPermPerUnit;
     exp_perm_body(it.rel_t, it.n_sft, it.antenna, it.n_ant, it.fafb, n_x, it.perm_ant, it.perm_x,
-                  e0 + threadIdx.x, min(total, e0 + kPermPerUnit), 256);
+                  it.g, it.tauc, e0 + threadIdx.x, min(total, e0 + kPermPerUnit), 256);
   });
 }
 __global__ void __launch_bounds__(kSufThreads, 3) kb_exp_ant(const BItem* __restrict__ items,
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.perm_ant, it.i0, it.jend, it.coef,
+    exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.perm_ant, it.tauc, it.i0, it.jend,
+                     it.coef,
                      make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                      dim3((unsigned)it.g.n_tau, (unsigned)it.n_ant));
   });

@@ -55,8 +55,8 @@ __device__ __forceinline__ float rec_ex2(float x) {
 __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          int32_t n_templates, int32_t n_groups, float* __restrict__ map,
-          Partial* __restrict__ parts, int64_t stride,
+          const TauTab* __restrict__ tauc, int32_t n_templates, int32_t n_groups,
+          float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
     const uint3 bid, const dim3 gdim) {
   static_assert(kRecThreads == kScanLanes, "chunk-major copy layout");
   extern __shared__ __align__(16) float s_dyn[];
@@ -69,23 +69,19 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   __shared__ float sR[2][kRecThreads / 32];
   __shared__ float sS[4][2][kRecThreads / 32];
   __shared__ Partial scratch[kRecThreads / 32];
-  __shared__ TauDecay s_td;
-  __shared__ float2 s_tab[kPowTab];
   const int ni = bid.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double tau = (double)(g.tau_min + (int64_t)ni * g.dtau);
-  const TauDecay td = tau_decay_block(tau, 1.0, g.t_sft, &s_td);
-  decay_table_fill(td.rho1, s_tab);
-  __syncthreads();
+  const TauTab* tt = tauc + ni;
   const int64_t np1 = (int64_t)n + 1;
   // Decays of this tau, once for all the block's templates: gaps of k whole
-  // SFTs from the table of float-float powers of the one-SFT decay, other
-  // gaps by FP64 exp.
+  // SFTs from the tau's table of float-float powers of the one-SFT decay,
+  // other gaps by FP64 exp.
   {
     const float inv_tsft = 1.0f / (float)g.t_sft;
+    const double inv_tau = tt->inv_tau;
     for (int i = tid; i < n; i += kRecThreads) {
       FF r{0.0f, 0.0f};
-      if (i + 1 < n) r = gap_decay(rel_t[i + 1] - rel_t[i], g.t_sft, inv_tsft, s_tab, td.inv_s);
+      if (i + 1 < n) r = gap_decay(rel_t[i + 1] - rel_t[i], g.t_sft, inv_tsft, tt->pw[0], inv_tau);
       s_rh[i] = r.h;
       s_rl[i] = r.l;
     }
@@ -93,7 +89,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   const int C = (n + kRecThreads - 1) / kRecThreads;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
-  const float c2 = td.c2;
+  const float c2 = tt->c2[0];
   const int64_t tb = n > 0 ? *t_base : 0;
   // Per cell (t0_m, tau_n): the window, its prefactor and tail factor and the
   // coefficients; staged once per block when they fit, else recomputed per
@@ -246,9 +242,10 @@ __global__ void __launch_bounds__(kRecThreads)
 k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          int32_t n_templates, int32_t n_groups, float* __restrict__ map,
-          Partial* __restrict__ parts, int64_t stride) {
-  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
+          const TauTab* __restrict__ tauc, int32_t n_templates, int32_t n_groups,
+          float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
+  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, tauc, n_templates,
+               n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
 bool exp_rec_supported(int32_t n_sft, int32_t) { return n_sft <= kRecMaxSft; }
@@ -268,6 +265,7 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
   dim3 grid((unsigned)g.n_tau, (unsigned)groups);
   k_exp_rec<<<grid, kRecThreads, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0,
                                             p->ws.jend, p->ws.coef, a->shared_antenna, p->ws.perm_x,
+                                            p->ws.tauc,
                                             p->n_templates, groups, d_2F, p->ws.partials,
                                             p->part_stride);
   p->launches += 1;
@@ -280,6 +278,7 @@ __global__ void __launch_bounds__(kRecThreads, 3) kb_exp_rec(const BItem* __rest
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     exp_rec_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared, it.perm_x,
+                 it.tauc,
                  it.T, it.groups, it.map, it.partials, it.part_stride,
                  make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                  dim3((unsigned)it.g.n_tau, (unsigned)it.groups));

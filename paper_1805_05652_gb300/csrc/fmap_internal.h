@@ -58,6 +58,22 @@ constexpr int kFlagUnit = 8192;
 constexpr int kScanLanes = 256;
 __host__ __device__ inline int64_t scan_chunk(int32_t n_sft) { return ((int64_t)n_sft + kScanLanes - 1) / kScanLanes; }
 __host__ __device__ inline int64_t perm_entries(int32_t n_sft) { return scan_chunk(n_sft) * kScanLanes; }
+// Entries of the exp copy step: the chunk-major copies, then one per tau.
+__host__ __device__ inline int64_t exp_copy_entries(int32_t n_sft, int32_t n_ant, int32_t n_x,
+                                                    int32_t n_tau) {
+  return perm_entries(n_sft) * (int64_t)(n_ant + n_x) + n_tau;
+}
+// Per-tau constants of the exponential window, for the weight w (s = 1) and
+// the antenna weight w^2 (s = 2): the decays over gaps of k = 0..kPowTab-1
+// whole SFTs as float pairs, pw[s-1][k] = e^{-s k T_sft / tau} (powers of the
+// one-SFT decay in float-float), the exp2 slopes c2[s-1] = -s log2(e) / tau,
+// and 1 / tau.  Filled once per plan run by the exp copy step.
+constexpr int kPowTab = 16;
+struct __align__(16) TauTab {
+  double inv_tau;
+  float c2[2];
+  float2 pw[2][kPowTab];
+};
 struct __align__(16) Coef {
   float k1;
   float beta;
@@ -86,6 +102,7 @@ struct Workspace {
   // exp: chunk-major copies of the atoms (perm_entries(N) per set)
   float4* perm_ant = nullptr;    // [T_ant][.] (a2, b2, ab, gap to the next atom as int bits; -1 last)
   float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
+  TauTab* tauc = nullptr;        // [n_tau] per-tau decay constants
   // exp
   float2* esuf = nullptr;        // [tau_chunk][3][N+1] float-float decayed suffix sums
   // tensor-core operands
