@@ -49,10 +49,12 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def make_workload(name, rank, templates=None):
+def make_workload(name, rank, templates=None, exp_cut8=0):
     if name == "exp16":
         kw = {} if templates is None else {"n_templates": templates}
-        return synth.config_exp16(seed=synth.BASE_SEED + 1 + 1000 * rank, **kw)
+        inst = synth.config_exp16(seed=synth.BASE_SEED + 1 + 1000 * rank, **kw)
+        inst.grid.exp_cut8 = exp_cut8   # window length exp_cut8 tau / 8 (0: 3 tau)
+        return inst
     if name == "batch_rect":
         kw = {} if templates is None else {"n_templates": templates}
         return synth.config_batched(window=synth.RECT, seed=synth.BASE_SEED + 2 + 1000 * rank, **kw)
@@ -148,7 +150,8 @@ def cpu_baseline(inst, target_s=12.0):
     def sample_grid(rows):
         stride = max(1, g.n_t0 // rows)
         return synth.Grid(g.t0_min + stride // 2 * g.dt0, g.dt0 * stride,
-                          min(rows, g.n_t0), g.tau_min, g.dtau, g.n_tau, g.window, g.t_sft)
+                          min(rows, g.n_t0), g.tau_min, g.dtau, g.n_tau, g.window, g.t_sft,
+                          g.exp_cut8)
 
     def run(rows):
         sg = sample_grid(rows)
@@ -184,6 +187,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None)
     ap.add_argument("--workload", default="exp16", choices=sorted(WORKLOADS))
+    ap.add_argument("--exp-cut8", type=int, default=0,
+                    help="exp16: window length in eighths of tau (0: 3 tau, Eq. winexp)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--also", default="fp32,tf32,rec",
@@ -227,7 +232,7 @@ def main():
             print(json.dumps(result), flush=True)
         return
 
-    inst = make_workload(args.workload, rank, args.templates)
+    inst = make_workload(args.workload, rank, args.templates, args.exp_cut8)
     g = inst.grid
     window = g.window
     precision = args.precision
@@ -371,6 +376,8 @@ def main():
                        "precision": precision, "templates": T, "n_sft": inst.n_sft,
                        "n_t0": g.n_t0, "n_tau": g.n_tau, "terms_per_step": terms,
                        "cells_with_2plus_sft": cells2,
+                       **({"exp_window_len": f"{g.exp_cut8}/8 tau" if g.exp_cut8 else "3 tau"}
+                          if g.window == synth.EXP else {}),
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (templates sharded by rank)"},
             "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1,
@@ -636,7 +643,7 @@ def reference_arm(args, rank, world):
     """The CPU oracle as the reference implementation, on the host cores."""
     if rank != 0:
         return
-    inst = make_workload(args.workload, 0)
+    inst = make_workload(args.workload, 0, None, args.exp_cut8)
     info, sg, terms = cpu_baseline(inst, target_s=min(4.0, 150.0 / (args.steps + args.warmup)))
     import oracle
 
@@ -654,6 +661,7 @@ def reference_arm(args, rank, world):
            "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                      "exp_window_len": (f"{args.exp_cut8}/8 tau" if args.exp_cut8 else "3 tau"),
                       "sample": info["sample"]},
            "cpu_baseline": info,
            "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0,

@@ -8,7 +8,7 @@
  *   A = sum w^2 a^2, B = sum w^2 b^2, C = sum w^2 ab, Fa = sum w Fa_a,
  *   Fb = sum w Fb_a
  * with the rectangular window of Eq. (winrect) or the exponential window of
- * Eq. (winexp) (cut after 3 tau), the determinant D = A B - C^2 and
+ * Eq. (winexp) (cut after 3 tau by default), the determinant D = A B - C^2 and
  * 2F from Eq. (F_FaFb); fused with the per-template reductions max 2F,
  * argmax (m, n) and the log Bayes factor marginalised over (t0, tau)
  * (Sec. 2 Eq. F_OSG; App. A).
@@ -16,7 +16,7 @@
  * Conventions shared by every entry point:
  *   - Times are integer seconds (int64).  An SFT that starts at t is inside the
  *     window of (t0, tau) when t0 <= t and t + T_sft <= t0 + L, L = tau (rect)
- *     or 3 tau (exp).  Windows past the end of the data are truncated
+ *     or L = 3 tau (exp; exp_cut8 / 8 tau in general).  Windows past the end of the data are truncated
  *     (App. A, non-embedded convention).
  *   - A cell with fewer than 2 SFTs in its window (Sec. 4.1) or with D <= 0
  *     is invalid: its 2F is 0 and it is left out of max, argmax and logB.
@@ -80,7 +80,11 @@ typedef enum { FMAP_FP64 = 0, FMAP_FP32 = 1, FMAP_TF32 = 2, FMAP_BF16X3 = 3 } fm
 
 /* Grid of Eq. (Fmn): t0_m = t0_min + m dt0 (m < n_t0), tau_n = tau_min + n dtau
  * (n < n_tau).  Needs n_t0, n_tau >= 0, tau_min > 0, t_sft > 0, dtau > 0 when
- * n_tau > 1, dt0 > 0 when n_t0 > 1, 3 tau_max < 2^31. */
+ * n_tau > 1, dt0 > 0 when n_t0 > 1, L(tau_max) < 2^31.
+ * exp_cut8: length of the exponential window in eighths of tau, L(tau) =
+ * floor(exp_cut8 tau / 8) seconds (Eq. winexp is cut after 3 tau: 0 selects
+ * the default 24; 1..1024 allowed); ignored for rect windows (L = tau).  It
+ * sits in what was padding, so a zero-initialised grid keeps the 3 tau cut. */
 typedef struct {
   int64_t t0_min;
   int64_t dt0;
@@ -89,7 +93,8 @@ typedef struct {
   int64_t dtau;
   int32_t n_tau;
   int64_t t_sft;
-  int32_t window; /* fmap_window */
+  int32_t window;   /* fmap_window */
+  int32_t exp_cut8; /* exp window length in tau / 8 (0: 24, i.e. 3 tau) */
 } fmap_grid;
 
 /* Atoms (Sec. 3: 3 real rows a^2, b^2, ab and 2 complex rows Fa, Fb).

@@ -51,9 +51,12 @@ def _p(a):
 
 def _grid_array(grid, inclusive=False):
     g = list(grid)
-    if len(g) != 8:
-        raise ValueError("grid must be (t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft, window)")
-    return np.array(g + [1 if inclusive else 0], dtype=np.int64)
+    if len(g) == 8:
+        g.append(0)
+    if len(g) != 9:
+        raise ValueError("grid must be (t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft, window"
+                         "[, exp_cut8])")
+    return np.array(g[:8] + [1 if inclusive else 0, g[8]], dtype=np.int64)
 
 
 def _atoms(t, antenna, fafb):

@@ -22,15 +22,18 @@
  *
  * Readings where the paper is silent (each is tested and documented):
  *   - an atom is evaluated at its SFT start t; it is inside the window when
- *     t0 <= t and t + T_sft <= t0 + L (L = tau, or 3 tau for exp).  The
- *     literal reading t in [t0, t0 + L] is available with inclusive = 1;
+ *     t0 <= t and t + T_sft <= t0 + L (L = tau, or 3 tau for exp, Eq.
+ *     winexp's cut; exp lengths floor(c tau / 8) for other cuts c given in
+ *     eighths of tau).  The literal reading t in [t0, t0 + L] is available
+ *     with inclusive = 1;
  *   - a cell with fewer than 2 atoms (Sec. 4.1) or D <= 0 is invalid: 2F = 0
  *     and it is left out of max, argmax and the Bayes factor;
  *   - logB = ln( (1/N_valid) sum_valid e^{F_mn} ) + log_prior_const;
  *   - argmax ties go to the lowest linear index m * N_tau + n.
  *
- * Grid array g (int64[9]): t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft,
- * window (0 rect, 1 exp), inclusive (0 / 1).
+ * Grid array g (int64[10]): t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft,
+ * window (0 rect, 1 exp), inclusive (0 / 1), exp cut in eighths of tau (0:
+ * 24, i.e. 3 tau).
  * Atom layout: t[N] ascending (the direct mode accepts any order);
  * antenna [3][N] (a^2, b^2, ab) shared by all templates, or [T][3][N];
  * fafb [T][4][N] (Re Fa, Im Fa, Re Fb, Im Fb).
@@ -43,7 +46,7 @@
 #include <omp.h>
 #endif
 
-enum { G_T0MIN, G_DT0, G_NT0, G_TAUMIN, G_DTAU, G_NTAU, G_TSFT, G_WIN, G_INCL };
+enum { G_T0MIN, G_DT0, G_NT0, G_TAUMIN, G_DTAU, G_NTAU, G_TSFT, G_WIN, G_INCL, G_CUT };
 
 static void set_threads(int n_threads) {
 #ifdef _OPENMP
@@ -63,7 +66,8 @@ int oracle_max_threads(void) {
 
 /* Window weight of Eq. (winrect) / (winexp); 0 outside the window. */
 static int inside_window(const int64_t* g, int64_t t, int64_t t0, int64_t tau) {
-  int64_t len = (g[G_WIN] == 0) ? tau : 3 * tau;
+  const int64_t cut8 = g[G_CUT] > 0 ? g[G_CUT] : 24;
+  int64_t len = (g[G_WIN] == 0) ? tau : cut8 * tau / 8;
   if (t < t0) return 0;
   if (g[G_INCL]) return t <= t0 + len;
   return t + g[G_TSFT] <= t0 + len;

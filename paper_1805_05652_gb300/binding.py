@@ -35,7 +35,8 @@ PRECISIONS = {"fp64": FMAP_FP64, "fp32": FMAP_FP32, "tf32": FMAP_TF32, "bf16x3":
 
 class fmap_grid(ctypes.Structure):
     _fields_ = [("t0_min", c_i64), ("dt0", c_i64), ("n_t0", c_i32), ("tau_min", c_i64),
-                ("dtau", c_i64), ("n_tau", c_i32), ("t_sft", c_i64), ("window", c_i32)]
+                ("dtau", c_i64), ("n_tau", c_i32), ("t_sft", c_i64), ("window", c_i32),
+                ("exp_cut8", c_i32)]
 
 
 class fmap_atoms(ctypes.Structure):
@@ -162,13 +163,15 @@ def make_grid(grid) -> fmap_grid:
     if isinstance(grid, fmap_grid):
         return grid
     if isinstance(grid, (tuple, list)):
-        t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft, window = grid
+        t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft, window = grid[:8]
+        exp_cut8 = grid[8] if len(grid) > 8 else 0
     else:
         t0_min, dt0, n_t0 = grid.t0_min, grid.dt0, grid.n_t0
         tau_min, dtau, n_tau = grid.tau_min, grid.dtau, grid.n_tau
         t_sft, window = grid.t_sft, grid.window
+        exp_cut8 = getattr(grid, "exp_cut8", 0)
     return fmap_grid(int(t0_min), int(dt0), int(n_t0), int(tau_min), int(dtau), int(n_tau),
-                     int(t_sft), int(window))
+                     int(t_sft), int(window), int(exp_cut8))
 
 
 def _ptr(x) -> int:

@@ -41,7 +41,10 @@ static bool grid_valid(const fmap_grid* g, std::string* why) {
   const int64_t cells = (int64_t)g->n_t0 * g->n_tau;
   if (cells >= (int64_t)0x7fffffff) return *why = "n_t0 * n_tau must be < 2^31", false;
   const double tau_max = (double)g->tau_min + (double)std::max(0, g->n_tau - 1) * (double)g->dtau;
-  if (3.0 * tau_max >= 2147483647.0) return *why = "3 tau_max must be < 2^31 s", false;
+  if (g->window == FMAP_EXP && (g->exp_cut8 < 0 || g->exp_cut8 > 1024))
+    return *why = "exp_cut8 must be in 0..1024", false;
+  const double lmax = g->window == FMAP_RECT ? tau_max : tau_max * exp_cut8_of(*g) / 8.0;
+  if (lmax >= 2147483647.0) return *why = "the window length at tau_max must be < 2^31 s", false;
   const double t0_ext = std::fabs((double)g->t0_min) +
                         (double)std::max(0, g->n_t0 - 1) * std::fabs((double)g->dt0);
   if (t0_ext > 4.0e18) return *why = "t0 grid out of int64 range", false;
@@ -521,14 +524,13 @@ fmap_status fmap_count_terms(const fmap_grid* g, const int64_t* t, int32_t n_sft
   if (!grid_valid(g, &why)) return arg_fail(why);
   if (n_sft < 0 || (n_sft > 0 && !t)) return arg_fail("bad timestamps");
   if (!n_terms || !n_cells_2plus) return arg_fail("outputs are NULL");
-  const int64_t lmul = g->window == FMAP_RECT ? 1 : 3;
   int64_t terms = 0, cells2 = 0;
   for (int32_t m = 0; m < g->n_t0; ++m) {
     const int64_t t0 = g->t0_min + (int64_t)m * g->dt0;
     const int64_t i0 = std::lower_bound(t, t + n_sft, t0) - t;
     int64_t j = i0;
     for (int32_t nn = 0; nn < g->n_tau; ++nn) {
-      const int64_t lim = t0 + lmul * (g->tau_min + (int64_t)nn * g->dtau) - g->t_sft;
+      const int64_t lim = t0 + window_len(*g, g->tau_min + (int64_t)nn * g->dtau) - g->t_sft;
       while (j < n_sft && t[j] <= lim) ++j;
       const int64_t c = j - i0;
       if (c >= 2) {

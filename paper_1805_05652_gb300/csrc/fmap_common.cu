@@ -38,7 +38,7 @@ __global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc
 }
 
 // Window index tables: i0[m] = first atom with t >= t0_m; jend[m][n] = one
-// past the last atom whose SFT ends by t0_m + L_n (L = tau or 3 tau),
+// past the last atom whose SFT ends by t0_m + L_n (L = window_len(tau_n)),
 // clamped to >= i0[m], so the window holds atoms [i0, jend).  One block per
 // t0 row: the row's atom range [i0, j(n_tau - 1)) of relative times is
 // staged in shared memory (coalesced) and every tau searches it there;
@@ -63,7 +63,6 @@ __device__ __forceinline__ void index_body(const int32_t* __restrict__ rel_t,
   __shared__ int32_t s_t[kIdxCap];
   __shared__ int32_t s_lo, s_hi;
   const int tid = threadIdx.x;
-  const int64_t lmul = (g.window == FMAP_RECT) ? 1 : 3;
   const int64_t tb = n_sft > 0 ? *t_base : 0;
   const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
   if (tid == 0) {
@@ -73,7 +72,7 @@ __device__ __forceinline__ void index_body(const int32_t* __restrict__ rel_t,
       if ((int64_t)rel_t[mid] < t0rel) lo = mid + 1; else hi = mid;
     }
     s_lo = lo;
-    const int64_t lim = t0rel + lmul * (g.tau_min + (int64_t)(g.n_tau - 1) * g.dtau) - g.t_sft;
+    const int64_t lim = t0rel + window_len(g, g.tau_min + (int64_t)(g.n_tau - 1) * g.dtau) - g.t_sft;
     s_hi = max(lo, upper_bound_i32(rel_t, lo, n_sft, lim));
     i0tab[m] = lo;
   }
@@ -85,7 +84,7 @@ __device__ __forceinline__ void index_body(const int32_t* __restrict__ rel_t,
   __syncthreads();
   int32_t* row = jend + (int64_t)m * g.n_tau;
   for (int32_t nn = tid; nn < g.n_tau; nn += kIdxThreads) {
-    const int64_t lim = t0rel + lmul * (g.tau_min + (int64_t)nn * g.dtau) - g.t_sft;
+    const int64_t lim = t0rel + window_len(g, g.tau_min + (int64_t)nn * g.dtau) - g.t_sft;
     row[nn] = staged ? i0 + upper_bound_i32(s_t, 0, span, lim)
                      : upper_bound_i32(rel_t, i0, i0 + span, lim);
   }

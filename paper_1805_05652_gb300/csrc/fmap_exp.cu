@@ -174,27 +174,39 @@ k_exp_suffix(const float4* __restrict__ perm, const TauTab* __restrict__ tauc, i
   antenna_suffix(perm, n, g, tauc + n_lo + ni, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
 }
 
+// Tail factors above this size are taken from FP64 exp as float pairs: the
+// window sum E[i0] - tail E[j] then loses 1 / (1 - tail) of relative accuracy
+// to the tail's own error, which the ill-conditioned D = AB - C^2 amplifies
+// further (windows cut well before 3 tau, or starting in a long gap).
+constexpr float kTailExact = 1.0f / 32.0f;
+
 // A, B, C of a cell from the suffix sums E of its tau, then its coefficients;
-// c2 = -2 log2(e) / tau.
+// c2 = -2 log2(e) / tau, inv_tau = 1 / tau.
 __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t, int32_t n,
                                               const fmap_grid& g, int64_t m, float c2,
-                                              int32_t i0, int32_t j, int64_t t_base,
-                                              const float2* E) {
+                                              double inv_tau, int32_t i0, int32_t j,
+                                              int64_t t_base, const float2* E) {
   const int32_t count = j - i0;
   FF S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   if (count > 0) {
     const int64_t t0rel = g.t0_min + m * g.dt0 - t_base;
     const int64_t np1 = (int64_t)n + 1;
     // The prefactor scales A, B, C alike (F changes by its relative error
-    // only) and the tail term is ~e^{-6} of the window sum: FP32 exp2 is
-    // accurate enough for both.
+    // only): FP32 exp2 is accurate enough.  The tail is FP32 exp2 while it is
+    // small (~e^{-6} of the window sum for the default 3 tau cut), FP64 exp
+    // otherwise.
     const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
     const float pre = d0 == 0 ? 1.0f : ex2_approx(c2 * (float)d0);
-    const float tail = (j < n) ? ex2_approx(c2 * (float)(rel_t[j] - rel_t[i0])) : 0.0f;
+    FF tail{0.0f, 0.0f};
+    if (j < n) {
+      const int32_t dj = rel_t[j] - rel_t[i0];
+      tail.h = ex2_approx(c2 * (float)dj);
+      if (tail.h > kTailExact) tail = ff_of(exp(-2.0 * (double)dj * inv_tau));
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float2 a = E[c * np1 + i0], b = E[c * np1 + j];
-      S[c] = ff_mul_f(ff_sub(FF{a.x, a.y}, ff_mul_f(FF{b.x, b.y}, tail)), pre);
+      S[c] = ff_mul_f(ff_sub(FF{a.x, a.y}, ff_mul(FF{b.x, b.y}, tail)), pre);
     }
   }
   return make_coef_ff(S[0], S[1], S[2], count);
@@ -220,7 +232,7 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
   for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
     const int64_t cell = (int64_t)m * g.n_tau + ni;
     coef[(int64_t)ta * cells + cell] =
-        exp_cell_coef(rel_t, n, g, m, tt->c2[1], i0tab[m], jend[cell], tb, s_E);
+        exp_cell_coef(rel_t, n, g, m, tt->c2[1], tt->inv_tau, i0tab[m], jend[cell], tb, s_E);
   }
 }
 
@@ -302,7 +314,8 @@ constexpr int kAntennaSmemMaxSft = 9000;   // 3 x (n + 1) float pairs <= 216 KB
 __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base,
                            int32_t n, fmap_grid g, int32_t n_lo, int32_t n_chunk,
                            const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-                           const float2* __restrict__ esuf, Coef* __restrict__ coef) {
+                           const float2* __restrict__ esuf, const TauTab* __restrict__ tauc,
+                           Coef* __restrict__ coef) {
   const int64_t total = (int64_t)g.n_t0 * n_chunk;
   const int64_t np1 = (int64_t)n + 1;
   const int64_t tb = n > 0 ? *t_base : 0;
@@ -312,9 +325,8 @@ __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __r
     const int32_t nl = (int32_t)(c - m * n_chunk);
     const int64_t nn = n_lo + nl;
     const int64_t cell = m * g.n_tau + nn;
-    const float c2 = (float)(-2.8853900817779268 / (double)(g.tau_min + nn * g.dtau));
-    coef[cell] = exp_cell_coef(rel_t, n, g, m, c2, i0tab[m], jend[cell], tb,
-                               esuf + (int64_t)nl * 3 * np1);
+    coef[cell] = exp_cell_coef(rel_t, n, g, m, tauc[nn].c2[1], tauc[nn].inv_tau, i0tab[m],
+                               jend[cell], tb, esuf + (int64_t)nl * 3 * np1);
   }
 }
 
@@ -343,7 +355,7 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
       const int64_t total = (int64_t)g.n_t0 * len;
       const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
       k_exp_coef<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, lo, len, p->ws.i0,
-                                        p->ws.jend, p->ws.esuf, p->ws.coef + ta * cells);
+                                        p->ws.jend, p->ws.esuf, p->ws.tauc, p->ws.coef + ta * cells);
       p->launches += 1;
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;

@@ -105,7 +105,14 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
       const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
       const int64_t d0 = (int64_t)rel_t[r.i0] - t0rel;
       r.pre = d0 == 0 ? 1.0f : rec_ex2(c2 * (float)d0);
-      r.tail = r.j < n ? rec_ex2(c2 * (float)(rel_t[r.j] - rel_t[r.i0])) : 0.0f;
+      if (r.j < n) {
+        // FP32 exp2 while the tail is small (~e^{-3} of the window sum for
+        // the default 3 tau cut); FP64 exp when a short cut makes it large,
+        // where the difference E[i0] - tail E[j] loses 1 / (1 - tail).
+        const int32_t dj = rel_t[r.j] - rel_t[r.i0];
+        r.tail = rec_ex2(c2 * (float)dj);
+        if (r.tail > 0.125f) r.tail = (float)exp(-(double)dj * tt->inv_tau);
+      }
     }
     r.cf = coef[cell];
     return r;

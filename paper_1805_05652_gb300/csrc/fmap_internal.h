@@ -49,6 +49,15 @@ struct __align__(16) Partial {
 constexpr double kCondThreshold = 100.0;
 // Reduction slots per template written by the fix-up kernel.
 constexpr int kFixSlots = 512;
+// Window length L(tau) in seconds: tau (rect) or floor(cut8 tau / 8) (exp,
+// cut8 = 24 by default: Eq. winexp's 3 tau).  An atom belongs to the window
+// of (t0, tau) iff t0 <= t and t + T_sft <= t0 + L(tau).
+__host__ __device__ inline int32_t exp_cut8_of(const fmap_grid& g) {
+  return g.exp_cut8 > 0 ? g.exp_cut8 : 24;
+}
+__host__ __device__ inline int64_t window_len(const fmap_grid& g, int64_t tau) {
+  return g.window == FMAP_RECT ? tau : (int64_t)exp_cut8_of(g) * tau / 8;
+}
 // Entries per count of the marked-entry compaction (1024 threads x 8).
 constexpr int kFlagUnit = 8192;
 // Threads of the exponential-window scans.  Thread t of a scan owns the atoms

@@ -77,7 +77,8 @@ def envelope(window, t, t0, tau, t_sft=T_SFT):
 @dataclass
 class Grid:
     """Uniform (t0, tau) grid: t0_m = t0_min + m dt0, tau_n = tau_min + n dtau
-    (integer seconds, Eq. Fmn)."""
+    (integer seconds, Eq. Fmn).  exp_cut8: exponential window length in
+    eighths of tau (0: Eq. winexp's 3 tau)."""
 
     t0_min: int
     dt0: int
@@ -87,6 +88,7 @@ class Grid:
     n_tau: int
     window: int = RECT
     t_sft: int = T_SFT
+    exp_cut8: int = 0
 
     def t0(self) -> np.ndarray:
         return self.t0_min + self.dt0 * np.arange(self.n_t0, dtype=np.int64)
@@ -100,11 +102,17 @@ class Grid:
 
     def with_window(self, window: int) -> "Grid":
         return Grid(self.t0_min, self.dt0, self.n_t0, self.tau_min, self.dtau,
-                    self.n_tau, window, self.t_sft)
+                    self.n_tau, window, self.t_sft, self.exp_cut8)
+
+    def window_len(self, tau):
+        """L(tau) in seconds: tau (rect) or floor(exp_cut8 tau / 8) (exp)."""
+        if self.window == RECT:
+            return tau
+        return (self.exp_cut8 or 24) * tau // 8
 
     def as_tuple(self):
         return (self.t0_min, self.dt0, self.n_t0, self.tau_min, self.dtau,
-                self.n_tau, self.t_sft, self.window)
+                self.n_tau, self.t_sft, self.window, self.exp_cut8)
 
 
 @dataclass

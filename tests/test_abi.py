@@ -58,14 +58,18 @@ def test_status_strings(L):
 
 @pytest.mark.parametrize("bad", [
     dict(n_t0=-1), dict(tau_min=0), dict(t_sft=0), dict(dtau=0), dict(dt0=-5), dict(window=7),
-    dict(n_t0=70000, n_tau=70000), dict(tau_min=800_000_000),
+    dict(n_t0=70000, n_tau=70000), dict(tau_min=2_200_000_000),
+    dict(window=EXP, tau_min=800_000_000), dict(window=EXP, exp_cut8=8, tau_min=2_200_000_000),
+    dict(window=EXP, exp_cut8=-1), dict(window=EXP, exp_cut8=1025),
 ])
 def test_plan_rejects_bad_grids(L, bad):
+    """Grid checks, including the window length L(tau_max) < 2^31 s (rect
+    L = tau, exp L = exp_cut8 tau / 8, default 3 tau) and the cut's range."""
     g = dict(t0_min=0, dt0=T_SFT, n_t0=10, tau_min=T_SFT, dtau=T_SFT, n_tau=10, t_sft=T_SFT,
-             window=RECT)
+             window=RECT, exp_cut8=0)
     g.update(bad)
     grid = (g["t0_min"], g["dt0"], g["n_t0"], g["tau_min"], g["dtau"], g["n_tau"], g["t_sft"],
-            g["window"])
+            g["window"], g["exp_cut8"])
     with pytest.raises(fm.FmapError) as e:
         fm.fmap_plan(grid, 100, 1, fm.FMAP_FP64)
     assert e.value.status == fm.FMAP_ERR_ARG

@@ -95,6 +95,23 @@ def test_exp_ragged(prec):
         raise
 
 
+@pytest.mark.parametrize("cut8", [1, 8, 20, 40])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "rec"])
+def test_exp_window_cut(cut8, prec):
+    """Exp windows cut at L = cut8 tau / 8 instead of 3 tau (tau / 8, tau,
+    2.5 tau, 5 tau): every path against the oracle's definition with the same
+    cut; short cuts leave many cells with < 2 SFTs."""
+    grid = Grid(-2500, 1000, 29, 900, 1300, 150, EXP, T_SFT, cut8)
+    inst = synth.make_instance(44, n_det=2, presence=0.9, n_merged=300, n_templates=5,
+                               grid=grid, injections=[(1, EXP, 20000, 60000, 200.0)])
+    try:
+        _parity(inst, prec)
+    except fm.FmapError as e:
+        if e.status == fm.FMAP_ERR_UNSUPPORTED:
+            pytest.skip(f"{prec} not built")
+        raise
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "rec"])
 def test_exp_per_template_antenna(prec):
     grid = Grid(0, T_SFT, 20, T_SFT, T_SFT, 140, EXP)

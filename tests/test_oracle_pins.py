@@ -65,6 +65,43 @@ def test_counts_match_appendix_formulas(window):
     assert np.array_equal(cnt, expect)
 
 
+@pytest.mark.parametrize("cut8", [1, 8, 20, 40])
+def test_counts_with_other_exp_cuts(cut8):
+    """The exp window cut as a parameter: L(tau) = floor(cut8 tau / 8) in
+    place of 3 tau in the per-cell count floor(min(T_data - t0, L) / T_sft)
+    of App. A (gap-free data, windows past the data end included)."""
+    n = 40
+    grid = Grid(0, 900, 90, 500, 1300, 70, EXP, T_SFT, cut8)
+    inst = _gapfree(n, grid=grid)
+    _, cnt = oracle.sums(inst.t, inst.antenna, inst.fafb, grid.as_tuple())
+    t_data = n * T_SFT
+    t0 = grid.t0()[:, None]
+    L = cut8 * grid.tau()[None, :] // 8
+    first = -(-t0 // T_SFT) * T_SFT
+    expect = np.clip(np.minimum(t_data - first, (t0 + L) - first) // T_SFT, 0, None)
+    expect = np.where(first < t_data, expect, 0)
+    assert np.array_equal(cnt, expect)
+    # the default (0) is the 3 tau cut of Eq. winexp
+    _, c3 = oracle.sums(inst.t, inst.antenna, inst.fafb, Grid(0, 900, 90, 500, 1300, 70, EXP).as_tuple())
+    _, c24 = oracle.sums(inst.t, inst.antenna, inst.fafb,
+                         Grid(0, 900, 90, 500, 1300, 70, EXP, T_SFT, 24).as_tuple())
+    assert np.array_equal(c3, c24)
+
+
+def test_host_count_terms_follow_the_cut():
+    """fmap_count_terms (host code of the library) counts the same windows as
+    the oracle for several cuts."""
+    fm = pytest.importorskip("paper_1805_05652_gb300")
+    fm.build()
+    inst = synth.make_instance(12, n_det=2, presence=0.8, n_merged=90,
+                               grid=Grid(0, 1, 1, 1, 1, 1, EXP), dtype=np.float64)
+    for cut8 in (0, 3, 8, 17, 64):
+        grid = Grid(-4000, 1500, 40, 900, 2100, 33, EXP, T_SFT, cut8)
+        _, cnt = oracle.sums(inst.t, inst.antenna, inst.fafb, grid.as_tuple())
+        terms, cells2 = fm.fmap_count_terms(grid, inst.t)
+        assert terms == int(cnt[cnt >= 2].sum()) and cells2 == int((cnt >= 2).sum())
+
+
 def test_counts_on_grid_equal_paper_sum():
     """On the paper's T_sft-step grids the total count equals Eq. (Nsums-exp)
     and its embedded-case closed form 3 N_t0 N_tau (tau_min + Delta_tau/2)/T_sft."""
@@ -241,7 +278,8 @@ def test_injection_recovered_in_noise():
     assert s["max2F"][0] > 60
 
 
-def test_exp_sums_match_decayed_suffix_recurrence():
+@pytest.mark.parametrize("cut8", [0, 8, 40])
+def test_exp_sums_match_decayed_suffix_recurrence(cut8):
     """A different algorithm for the exponential sums: the backward
     recurrence E[i] = x_i + e^{-(t_{i+1} - t_i)/s} E[i+1] gives
     sum_{i0 <= a < j} e^{-(t_a - t0)/s} x_a
@@ -249,10 +287,11 @@ def test_exp_sums_match_decayed_suffix_recurrence():
     with s = tau for Fa, Fb and tau / 2 for the squared weights."""
     inst = synth.make_instance(31, n_det=2, presence=0.7, n_merged=150, n_templates=2,
                                grid=Grid(0, 1, 1, 1, 1, 1, EXP), dtype=np.float64)
-    grid = Grid(-3000, 2500, 30, 700, 4100, 25, EXP)
+    grid = Grid(-3000, 2500, 30, 700, 4100, 25, EXP, T_SFT, cut8)
     s, cnt = oracle.sums(inst.t, inst.antenna, inst.fafb, grid.as_tuple())
     t = inst.t.astype(np.float64)
     n = inst.n_sft
+    L8 = cut8 or 24
 
     def suffix(x, scale):
         E = np.zeros(n + 1)
@@ -267,7 +306,7 @@ def test_exp_sums_match_decayed_suffix_recurrence():
         for mi, t0 in enumerate(grid.t0()):
             i0 = int(np.searchsorted(inst.t, t0, side="left"))
             j = i0
-            while j < n and inst.t[j] + T_SFT <= t0 + 3 * tau:
+            while j < n and 8 * (inst.t[j] + T_SFT - t0) <= L8 * tau:
                 j += 1
             assert cnt[mi, ni] == j - i0
             if j == i0:
