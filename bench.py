@@ -49,16 +49,42 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def make_workload(name, rank, templates=None, exp_cut8=0):
+def jitter_axes(grid, seed):
+    """Explicit axes for a uniform grid: every t0 and tau moved later by a
+    seeded offset in [0, step / 2), so the values stay strictly increasing
+    but the steps are no longer uniform."""
+    g = synth.philox(seed, 5)
+    t0 = grid.t0() + g.integers(0, max(1, grid.dt0 // 2), size=grid.n_t0)
+    tau = grid.tau() + g.integers(0, max(1, grid.dtau // 2), size=grid.n_tau)
+    grid.t0_values = tuple(int(v) for v in t0)
+    grid.tau_values = tuple(int(v) for v in tau)
+
+
+def make_workload(name, rank, templates=None, exp_cut8=0, axes=False):
     if name == "exp16":
         kw = {} if templates is None else {"n_templates": templates}
         inst = synth.config_exp16(seed=synth.BASE_SEED + 1 + 1000 * rank, **kw)
         inst.grid.exp_cut8 = exp_cut8   # window length exp_cut8 tau / 8 (0: 3 tau)
+        if axes:
+            jitter_axes(inst.grid, synth.BASE_SEED + 1 + 1000 * rank)
         return inst
     if name == "batch_rect":
         kw = {} if templates is None else {"n_templates": templates}
         return synth.config_batched(window=synth.RECT, seed=synth.BASE_SEED + 2 + 1000 * rank, **kw)
     raise SystemExit(f"unknown workload {name}")
+
+
+def count_terms(grid, t):
+    """(terms, cells with >= 2 SFTs) of a grid: the library's host count for
+    uniform grids; for explicit axes the same rule with numpy searches."""
+    if not grid.has_axes:
+        return fm.fmap_count_terms(grid, t)
+    t0 = grid.t0()
+    i0 = np.searchsorted(t, t0, side="left")
+    lim = t0[:, None] + np.array([grid.window_len(int(v)) for v in grid.tau()])[None, :] - grid.t_sft
+    j = np.maximum(np.searchsorted(t, lim, side="right"), i0[:, None])
+    c = j - i0[:, None]
+    return int(c[c >= 2].sum()), int((c >= 2).sum())
 
 
 def load_peaks():
@@ -149,9 +175,14 @@ def cpu_baseline(inst, target_s=12.0):
 
     def sample_grid(rows):
         stride = max(1, g.n_t0 // rows)
-        return synth.Grid(g.t0_min + stride // 2 * g.dt0, g.dt0 * stride,
-                          min(rows, g.n_t0), g.tau_min, g.dtau, g.n_tau, g.window, g.t_sft,
-                          g.exp_cut8)
+        sg = synth.Grid(g.t0_min + stride // 2 * g.dt0, g.dt0 * stride,
+                        min(rows, g.n_t0), g.tau_min, g.dtau, g.n_tau, g.window, g.t_sft,
+                        g.exp_cut8)
+        if g.has_axes:   # every stride-th t0 of the explicit axes
+            sg.t0_values = tuple(g.t0_values[stride // 2::stride][:sg.n_t0])
+            sg.n_t0 = len(sg.t0_values)
+            sg.tau_values = g.tau_values
+        return sg
 
     def run(rows):
         sg = sample_grid(rows)
@@ -169,7 +200,7 @@ def cpu_baseline(inst, target_s=12.0):
     per_row = dt / sg.n_t0
     rows = int(min(g.n_t0, max(1, target_s / max(per_row, 1e-9))))
     dt, sg = run(rows)
-    terms = fm.fmap_count_terms(sg, inst.t)[0] * inst.n_templates
+    terms = count_terms(sg, inst.t)[0] * inst.n_templates
     return {"value": terms / dt, "unit": "terms/s", "cores": oracle.max_threads(),
             "kind": "oracle",
             "sample": f"{sg.n_t0} of {g.n_t0} t0 rows (every {g.n_t0 // max(1, sg.n_t0)}th), "
@@ -189,6 +220,8 @@ def main():
     ap.add_argument("--workload", default="exp16", choices=sorted(WORKLOADS))
     ap.add_argument("--exp-cut8", type=int, default=0,
                     help="exp16: window length in eighths of tau (0: 3 tau, Eq. winexp)")
+    ap.add_argument("--grid-axes", action="store_true",
+                    help="exp16: explicit non-uniform (t0, tau) axes (seeded jitter of the steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--also", default="fp32,tf32,rec",
@@ -232,7 +265,7 @@ def main():
             print(json.dumps(result), flush=True)
         return
 
-    inst = make_workload(args.workload, rank, args.templates, args.exp_cut8)
+    inst = make_workload(args.workload, rank, args.templates, args.exp_cut8, args.grid_axes)
     g = inst.grid
     window = g.window
     precision = args.precision
@@ -259,7 +292,7 @@ def main():
     out_map = torch.empty((T, g.n_t0, g.n_tau), dtype=torch.float32, device=dev)
     out_sum = torch.empty((T, 32), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    terms_per_tmpl, cells2 = fm.fmap_count_terms(g, inst.t)
+    terms_per_tmpl, cells2 = plan.count_terms(inst.t)
     terms = terms_per_tmpl * T
 
     def step(p):
@@ -378,6 +411,8 @@ def main():
                        "cells_with_2plus_sft": cells2,
                        **({"exp_window_len": f"{g.exp_cut8}/8 tau" if g.exp_cut8 else "3 tau"}
                           if g.window == synth.EXP else {}),
+                       **({"grid": "explicit axes (steps jittered by [0, step/2))"}
+                          if g.has_axes else {}),
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (templates sharded by rank)"},
             "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1,
@@ -643,7 +678,7 @@ def reference_arm(args, rank, world):
     """The CPU oracle as the reference implementation, on the host cores."""
     if rank != 0:
         return
-    inst = make_workload(args.workload, 0, None, args.exp_cut8)
+    inst = make_workload(args.workload, 0, None, args.exp_cut8, args.grid_axes)
     info, sg, terms = cpu_baseline(inst, target_s=min(4.0, 150.0 / (args.steps + args.warmup)))
     import oracle
 

@@ -155,6 +155,21 @@ fmap_status fmap_plan(fmap_plan_t** plan, const fmap_grid* grid, int32_t n_sft,
                       int32_t n_templates, fmap_precision precision, uint32_t flags);
 void fmap_plan_destroy(fmap_plan_t* plan);
 
+/* Explicit (t0, tau) axes: a non-uniform or undersampled grid in place of
+ * Eq. (Fmn)'s uniform steps.  t0_values [n_t0] and tau_values [n_tau] are
+ * HOST arrays of strictly increasing integer seconds (tau > 0, the window
+ * length at the largest tau < 2^31 s, t0 within +-2^62); they are copied into
+ * the plan's workspace (synchronously, after the plan's last stream has
+ * drained).  While set, the grid's t0_min, dt0, tau_min and dtau are unused;
+ * n_t0, n_tau, t_sft, window and exp_cut8 still apply.  Both NULL restores the
+ * uniform grid.  Errors: FMAP_ERR_ARG (one NULL, bad values), FMAP_ERR_CUDA.
+ * Batches and the server take uniform grids only. */
+fmap_status fmap_plan_axes(fmap_plan_t* plan, const int64_t* t0_values,
+                           const int64_t* tau_values);
+/* fmap_count_terms for a plan's grid (its explicit axes if set). */
+fmap_status fmap_plan_count_terms(fmap_plan_t* plan, const int64_t* t, int32_t n_sft,
+                                  int64_t* n_terms, int64_t* n_cells_2plus);
+
 /* Workspace a plan of these sizes allocates (bytes). */
 size_t fmap_workspace_bytes(const fmap_grid* grid, int32_t n_sft, int32_t n_templates,
                             fmap_precision precision);

@@ -31,9 +31,12 @@
  *   - logB = ln( (1/N_valid) sum_valid e^{F_mn} ) + log_prior_const;
  *   - argmax ties go to the lowest linear index m * N_tau + n.
  *
- * Grid array g (int64[10]): t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft,
- * window (0 rect, 1 exp), inclusive (0 / 1), exp cut in eighths of tau (0:
- * 24, i.e. 3 tau).
+ * Grid array g (int64[11], or int64[11 + n_t0 + n_tau]): t0_min, dt0, n_t0,
+ * tau_min, dtau, n_tau, t_sft, window (0 rect, 1 exp), inclusive (0 / 1),
+ * exp cut in eighths of tau (0: 24, i.e. 3 tau), explicit axes (0 / 1).  With
+ * explicit axes the t0 values and then the tau values follow (a non-uniform
+ * grid; t0_min, dt0, tau_min and dtau are then unused); otherwise t0_m =
+ * t0_min + m dt0 and tau_n = tau_min + n dtau (Eq. Fmn).
  * Atom layout: t[N] ascending (the direct mode accepts any order);
  * antenna [3][N] (a^2, b^2, ab) shared by all templates, or [T][3][N];
  * fafb [T][4][N] (Re Fa, Im Fa, Re Fb, Im Fb).
@@ -46,7 +49,16 @@
 #include <omp.h>
 #endif
 
-enum { G_T0MIN, G_DT0, G_NT0, G_TAUMIN, G_DTAU, G_NTAU, G_TSFT, G_WIN, G_INCL, G_CUT };
+enum { G_T0MIN, G_DT0, G_NT0, G_TAUMIN, G_DTAU, G_NTAU, G_TSFT, G_WIN, G_INCL, G_CUT, G_AXES,
+       G_VALUES };
+
+/* Grid values t0_m and tau_n (Eq. Fmn, or the explicit axes). */
+static int64_t t0_at(const int64_t* g, int64_t m) {
+  return g[G_AXES] ? g[G_VALUES + m] : g[G_T0MIN] + m * g[G_DT0];
+}
+static int64_t tau_at(const int64_t* g, int64_t n) {
+  return g[G_AXES] ? g[G_VALUES + g[G_NT0] + n] : g[G_TAUMIN] + n * g[G_DTAU];
+}
 
 static void set_threads(int n_threads) {
 #ifdef _OPENMP
@@ -127,9 +139,9 @@ int oracle_sums(const int64_t* g, int n_sft, const int64_t* t, int n_templates,
     for (int64_t m = 0; m < n_t0; ++m) {
       const double* ant = shared_antenna ? antenna : antenna + j * 3 * (int64_t)n_sft;
       const double* x = fafb + j * 4 * (int64_t)n_sft;
-      int64_t t0 = g[G_T0MIN] + m * g[G_DT0];
+      int64_t t0 = t0_at(g, m);
       for (int64_t n = 0; n < n_tau; ++n) {
-        int64_t tau = g[G_TAUMIN] + n * g[G_DTAU];
+        int64_t tau = tau_at(g, n);
         int32_t c;
         double* s = sums + ((j * cells) + m * n_tau + n) * 7;
         cell_sums_direct(g, n_sft, t, ant, x, t0, tau, s, &c);
@@ -164,7 +176,7 @@ int oracle_fmap(int mode, const int64_t* g, int n_sft, const int64_t* t, int n_t
   set_threads(n_threads);
   const int64_t n_t0 = g[G_NT0], n_tau = g[G_NTAU];
   const int64_t cells = n_t0 * n_tau;
-  if (mode == 1 && g[G_WIN] == 0 && n_tau > 1 && g[G_DTAU] <= 0) return -1;
+  if (mode == 1 && g[G_WIN] == 0 && n_tau > 1 && tau_at(g, 1) <= tau_at(g, 0)) return -1;
   int err = 0;
 #pragma omp parallel
   {
@@ -177,12 +189,12 @@ int oracle_fmap(int mode, const int64_t* g, int n_sft, const int64_t* t, int n_t
     for (int64_t j = 0; j < (mode == 1 && g[G_WIN] == 1 ? 1 : n_templates); ++j) {
       for (int64_t m = 0; m < n_t0; ++m) {
         if (!acc) continue;
-        int64_t t0 = g[G_T0MIN] + m * g[G_DT0];
+        int64_t t0 = t0_at(g, m);
         if (mode == 0) {
           const double* ant = shared_antenna ? antenna : antenna + j * 3 * (int64_t)n_sft;
           const double* x = fafb + j * 4 * (int64_t)n_sft;
           for (int64_t n = 0; n < n_tau; ++n) {
-            int64_t tau = g[G_TAUMIN] + n * g[G_DTAU];
+            int64_t tau = tau_at(g, n);
             double s[7];
             int32_t c, v;
             cell_sums_direct(g, n_sft, t, ant, x, t0, tau, s, &c);
@@ -199,7 +211,7 @@ int oracle_fmap(int mode, const int64_t* g, int n_sft, const int64_t* t, int n_t
           double s[7] = {0, 0, 0, 0, 0, 0, 0};
           int32_t c = 0;
           for (int64_t n = 0; n < n_tau; ++n) {
-            int64_t tau = g[G_TAUMIN] + n * g[G_DTAU];
+            int64_t tau = tau_at(g, n);
             while (a < n_sft && inside_window(g, t[a], t0, tau)) {
               s[0] += ant[a];
               s[1] += ant[n_sft + a];
@@ -222,7 +234,7 @@ int oracle_fmap(int mode, const int64_t* g, int n_sft, const int64_t* t, int n_t
            * cell are shared by all templates */
           int a0 = first_at_or_after(n_sft, t, t0);
           for (int64_t n = 0; n < n_tau; ++n) {
-            int64_t tau = g[G_TAUMIN] + n * g[G_DTAU];
+            int64_t tau = tau_at(g, n);
             double sa[3] = {0, 0, 0};
             for (int k = 0; k < 4 * n_templates; ++k) acc[k] = 0.0;
             int32_t c = 0;
@@ -291,8 +303,8 @@ int oracle_cells(const int64_t* g, int n_sft, const int64_t* t, int n_templates,
     }
     const double* ant = shared_antenna ? antenna : antenna + j * 3 * (int64_t)n_sft;
     const double* x = fafb + j * 4 * (int64_t)n_sft;
-    int64_t t0 = g[G_T0MIN] + m * g[G_DT0];
-    int64_t tau = g[G_TAUMIN] + n * g[G_DTAU];
+    int64_t t0 = t0_at(g, m);
+    int64_t tau = tau_at(g, n);
     double s[7];
     int32_t c, v;
     cell_sums_direct(g, n_sft, t, ant, x, t0, tau, s, &c);

@@ -63,7 +63,8 @@ EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_
            "fmap_plan_enable_timing", "fmap_plan_read_timing", "fmap_marginalise_noalloc",
            "fmap_noalloc_scratch_bytes", "fmap_server_create", "fmap_server_destroy",
            "fmap_submit", "fmap_poll", "fmap_server_stats", "fmap_batch_plan", "fmap_batch_run",
-           "fmap_batch_status", "fmap_batch_info", "fmap_batch_profile", "fmap_batch_destroy")
+           "fmap_batch_status", "fmap_batch_info", "fmap_batch_profile", "fmap_batch_destroy",
+           "fmap_plan_axes", "fmap_plan_count_terms")
 FMAP_BATCH_AUTOTUNE = 1
 N_BATCH_PHASES = 15
 FMAP_N_PHASES = 4
@@ -105,6 +106,8 @@ def lib():
     L.fmap_marginalise.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp]
     L.fmap_plan_status.argtypes = [c_vp]
     L.fmap_count_terms.argtypes = [P(fmap_grid), c_vp, c_i32, P(c_i64), P(c_i64)]
+    L.fmap_plan_axes.argtypes = [c_vp, c_vp, c_vp]
+    L.fmap_plan_count_terms.argtypes = [c_vp, c_vp, c_i32, P(c_i64), P(c_i64)]
     L.fmap_plan_enable_timing.argtypes = [c_vp, c_i32]
     L.fmap_plan_read_timing.argtypes = [c_vp, c_vp, P(c_i64), P(c_i64)]
     L.fmap_marginalise_noalloc.argtypes = [P(fmap_grid), c_i32, c_vp, c_vp, c_f64, c_vp, c_vp]
@@ -276,6 +279,25 @@ def fmap_plan_read_timing(plan: int):
     _check(lib().fmap_plan_read_timing(c_vp(plan), _ptr(ms), ctypes.byref(calls),
                                        ctypes.byref(launches)), "fmap_plan_read_timing")
     return ms, int(calls.value), int(launches.value)
+
+
+def fmap_plan_axes(handle, t0_values, tau_values):
+    """Explicit (t0, tau) axes for a plan (host int64 arrays), or None, None
+    for the uniform grid."""
+    if t0_values is None:
+        _check(lib().fmap_plan_axes(handle, None, None), "fmap_plan_axes")
+        return
+    a = np.ascontiguousarray(t0_values, dtype=np.int64)
+    b = np.ascontiguousarray(tau_values, dtype=np.int64)
+    _check(lib().fmap_plan_axes(handle, _ptr(a), _ptr(b)), "fmap_plan_axes")
+
+
+def fmap_plan_count_terms(handle, t_host: np.ndarray):
+    t = np.ascontiguousarray(t_host, dtype=np.int64)
+    a, b = c_i64(), c_i64()
+    _check(lib().fmap_plan_count_terms(handle, _ptr(t), int(t.shape[0]), ctypes.byref(a),
+                                       ctypes.byref(b)), "fmap_plan_count_terms")
+    return int(a.value), int(b.value)
 
 
 def fmap_count_terms(grid, t_host: np.ndarray):
@@ -487,6 +509,14 @@ class Plan:
             self.precision = PRECISIONS[self.precision]
         self.g = make_grid(self.grid)
         self.handle = fmap_plan(self.g, self.n_sft, self.n_templates, self.precision, self.flags)
+        if getattr(self.grid, "t0_values", None) is not None:   # explicit axes
+            self.set_axes(self.grid.t0_values, self.grid.tau_values)
+
+    def set_axes(self, t0_values, tau_values):
+        fmap_plan_axes(self.handle, t0_values, tau_values)
+
+    def count_terms(self, t_host):
+        return fmap_plan_count_terms(self.handle, t_host)
 
     def close(self):
         if getattr(self, "handle", None):

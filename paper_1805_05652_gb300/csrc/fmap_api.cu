@@ -53,6 +53,30 @@ static bool grid_valid(const fmap_grid* g, std::string* why) {
 
 bool grid_is_valid(const fmap_grid* g, std::string* why) { return grid_valid(g, why); }
 
+// Terms (atoms summed over the windows with >= 2 atoms) and such cells of a
+// grid, uniform or with explicit axes ax (t0 values, then tau values); host.
+static void count_terms_of(const fmap_grid& g, const int64_t* ax, const int64_t* t, int32_t n_sft,
+                           int64_t* n_terms, int64_t* n_cells_2plus) {
+  int64_t terms = 0, cells2 = 0;
+  for (int32_t m = 0; m < g.n_t0; ++m) {
+    const int64_t t0 = ax ? ax[m] : g.t0_min + (int64_t)m * g.dt0;
+    const int64_t i0 = std::lower_bound(t, t + n_sft, t0) - t;
+    int64_t j = i0;
+    for (int32_t nn = 0; nn < g.n_tau; ++nn) {
+      const int64_t tau = ax ? ax[g.n_t0 + nn] : g.tau_min + (int64_t)nn * g.dtau;
+      const int64_t lim = t0 + window_len(g, tau) - g.t_sft;
+      while (j < n_sft && t[j] <= lim) ++j;
+      const int64_t c = j - i0;
+      if (c >= 2) {
+        terms += c;
+        ++cells2;
+      }
+    }
+  }
+  *n_terms = terms;
+  *n_cells_2plus = cells2;
+}
+
 static bool precision_supported(int window, fmap_precision prec) {
   if (window == FMAP_RECT) return prec == FMAP_FP64 || prec == FMAP_FP32;
   if (prec == FMAP_TF32 || prec == FMAP_BF16X3) return exp_tc_available(prec);
@@ -61,7 +85,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
-      esuf, xop, perm_ant, perm_x, tauc, total;
+      esuf, xop, perm_ant, perm_x, tauc, ax, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -94,6 +118,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
   L.dev_err = take(sizeof(uint32_t));
   L.i0 = take(sizeof(int32_t) * std::max<int32_t>(g->n_t0, 1));
   L.jend = take(sizeof(int32_t) * std::max<int64_t>(cells, 1));
+  L.ax = take(sizeof(int64_t) * std::max<int64_t>((int64_t)g->n_t0 + g->n_tau, 1));
   L.parts = take(sizeof(Partial) * (size_t)std::max<int32_t>(T, 1) * (size_t)(tiles + kFixSlots));
   L.groups = take(kGroupBytes * (size_t)std::max<int32_t>(T, 1) *
                   (size_t)reduce_groups_of(tiles + kFixSlots));
@@ -224,6 +249,7 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
   w.dev_err = (uint32_t*)(b + L.dev_err);
   w.i0 = (int32_t*)(b + L.i0);
   w.jend = (int32_t*)(b + L.jend);
+  w.ax = (int64_t*)(b + L.ax);
   w.partials = (Partial*)(b + L.parts);
   w.groups = (void*)(b + L.groups);
   w.coef = (Coef*)(b + L.coef);
@@ -524,23 +550,50 @@ fmap_status fmap_count_terms(const fmap_grid* g, const int64_t* t, int32_t n_sft
   if (!grid_valid(g, &why)) return arg_fail(why);
   if (n_sft < 0 || (n_sft > 0 && !t)) return arg_fail("bad timestamps");
   if (!n_terms || !n_cells_2plus) return arg_fail("outputs are NULL");
-  int64_t terms = 0, cells2 = 0;
-  for (int32_t m = 0; m < g->n_t0; ++m) {
-    const int64_t t0 = g->t0_min + (int64_t)m * g->dt0;
-    const int64_t i0 = std::lower_bound(t, t + n_sft, t0) - t;
-    int64_t j = i0;
-    for (int32_t nn = 0; nn < g->n_tau; ++nn) {
-      const int64_t lim = t0 + window_len(*g, g->tau_min + (int64_t)nn * g->dtau) - g->t_sft;
-      while (j < n_sft && t[j] <= lim) ++j;
-      const int64_t c = j - i0;
-      if (c >= 2) {
-        terms += c;
-        ++cells2;
-      }
-    }
+  count_terms_of(*g, nullptr, t, n_sft, n_terms, n_cells_2plus);
+  return FMAP_OK;
+}
+
+fmap_status fmap_plan_count_terms(fmap_plan_t* p, const int64_t* t, int32_t n_sft,
+                                  int64_t* n_terms, int64_t* n_cells_2plus) {
+  set_error("");
+  if (!p) return arg_fail("plan is NULL");
+  if (n_sft < 0 || (n_sft > 0 && !t)) return arg_fail("bad timestamps");
+  if (!n_terms || !n_cells_2plus) return arg_fail("outputs are NULL");
+  count_terms_of(p->grid, p->explicit_axes ? p->ax_host.data() : nullptr, t, n_sft, n_terms,
+                 n_cells_2plus);
+  return FMAP_OK;
+}
+
+fmap_status fmap_plan_axes(fmap_plan_t* p, const int64_t* t0_values, const int64_t* tau_values) {
+  set_error("");
+  if (!p) return arg_fail("plan is NULL");
+  if (!t0_values != !tau_values) return arg_fail("give both axes or neither");
+  if (p->last_stream) FMAP_CUDA(cudaStreamSynchronize(p->last_stream));
+  if (!t0_values) {
+    p->explicit_axes = false;
+    p->ax_host.clear();
+    return FMAP_OK;
   }
-  *n_terms = terms;
-  *n_cells_2plus = cells2;
+  const fmap_grid& g = p->grid;
+  for (int32_t m = 0; m < g.n_t0; ++m) {
+    if (t0_values[m] > ((int64_t)1 << 62) || t0_values[m] < -((int64_t)1 << 62))
+      return arg_fail("t0 value out of range");
+    if (m > 0 && t0_values[m] <= t0_values[m - 1]) return arg_fail("t0 values must increase");
+  }
+  for (int32_t n = 0; n < g.n_tau; ++n) {
+    if (tau_values[n] <= 0) return arg_fail("tau values must be > 0");
+    if (n > 0 && tau_values[n] <= tau_values[n - 1]) return arg_fail("tau values must increase");
+  }
+  if (g.n_tau > 0 && (double)window_len(g, tau_values[g.n_tau - 1]) >= 2147483647.0)
+    return arg_fail("the window length at the largest tau must be < 2^31 s");
+  std::vector<int64_t> ax((size_t)g.n_t0 + g.n_tau);
+  std::copy(t0_values, t0_values + g.n_t0, ax.begin());
+  std::copy(tau_values, tau_values + g.n_tau, ax.begin() + g.n_t0);
+  if (!ax.empty())
+    FMAP_CUDA(cudaMemcpy(p->ws.ax, ax.data(), sizeof(int64_t) * ax.size(), cudaMemcpyHostToDevice));
+  p->ax_host.swap(ax);
+  p->explicit_axes = true;
   return FMAP_OK;
 }
 

@@ -37,6 +37,7 @@ struct BItem {
   float4* perm_ant;
   float4* perm_x;
   TauTab* tauc;
+  int64_t* ax;
   float4* px;
 };
 

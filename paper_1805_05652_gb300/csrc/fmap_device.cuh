@@ -130,12 +130,12 @@ __device__ __forceinline__ FF ff_of(double x) {
   return {h, (float)(x - (double)h)};
 }
 
-// Fills the per-tau constants of tau_n (one thread).  The one-SFT decay is
+// Fills the per-tau constants of one tau value (one thread).  The one-SFT decay is
 // an FP64 exp split into a float pair; its powers come by binary powering in
 // float-float (~k ulp of 2^-48).
-__device__ __forceinline__ void tau_tab_fill(const fmap_grid& g, int64_t ni, TauTab* out) {
+__device__ __forceinline__ void tau_tab_fill(const fmap_grid& g, int64_t tau, TauTab* out) {
   TauTab t;
-  t.inv_tau = 1.0 / (double)(g.tau_min + ni * g.dtau);
+  t.inv_tau = 1.0 / (double)tau;
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const double inv_s = (double)(s + 1) * t.inv_tau;

@@ -180,16 +180,16 @@ k_exp_suffix(const float4* __restrict__ perm, const TauTab* __restrict__ tauc, i
 // further (windows cut well before 3 tau, or starting in a long gap).
 constexpr float kTailExact = 1.0f / 32.0f;
 
-// A, B, C of a cell from the suffix sums E of its tau, then its coefficients;
-// c2 = -2 log2(e) / tau, inv_tau = 1 / tau.
+// A, B, C of the cell (t0, tau) from the suffix sums E of its tau, then its
+// coefficients; c2 = -2 log2(e) / tau, inv_tau = 1 / tau.
 __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t, int32_t n,
-                                              const fmap_grid& g, int64_t m, float c2,
+                                              int64_t t0, float c2,
                                               double inv_tau, int32_t i0, int32_t j,
                                               int64_t t_base, const float2* E) {
   const int32_t count = j - i0;
   FF S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   if (count > 0) {
-    const int64_t t0rel = g.t0_min + m * g.dt0 - t_base;
+    const int64_t t0rel = t0 - t_base;
     const int64_t np1 = (int64_t)n + 1;
     // The prefactor scales A, B, C alike (F changes by its relative error
     // only): FP32 exp2 is accurate enough.  The tail is FP32 exp2 while it is
@@ -218,8 +218,9 @@ __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t,
 // strided coefficient stores merge in L2.
 __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
               fmap_grid g, const float4* __restrict__ perm_ant, const TauTab* __restrict__ tauc,
-              const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-              Coef* __restrict__ coef, const uint3 bid, const dim3 gdim) {
+              const int64_t* __restrict__ ax, const int32_t* __restrict__ i0tab,
+              const int32_t* __restrict__ jend, Coef* __restrict__ coef, const uint3 bid,
+              const dim3 gdim) {
   extern __shared__ float2 s_E[];
   __shared__ float sR[2][kSufThreads / 32];
   __shared__ float sS[3][2][kSufThreads / 32];
@@ -232,16 +233,16 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
   for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
     const int64_t cell = (int64_t)m * g.n_tau + ni;
     coef[(int64_t)ta * cells + cell] =
-        exp_cell_coef(rel_t, n, g, m, tt->c2[1], tt->inv_tau, i0tab[m], jend[cell], tb, s_E);
+        exp_cell_coef(rel_t, n, ax[m], tt->c2[1], tt->inv_tau, i0tab[m], jend[cell], tb, s_E);
   }
 }
 
 __global__ void __launch_bounds__(kSufThreads)
 k_exp_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
               fmap_grid g, const float4* __restrict__ perm_ant, const TauTab* __restrict__ tauc,
-              const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-              Coef* __restrict__ coef) {
-  exp_antenna_body(rel_t, t_base, n, g, perm_ant, tauc, i0tab, jend, coef, blockIdx, gridDim);
+              const int64_t* __restrict__ ax, const int32_t* __restrict__ i0tab,
+              const int32_t* __restrict__ jend, Coef* __restrict__ coef) {
+  exp_antenna_body(rel_t, t_base, n, g, perm_ant, tauc, ax, i0tab, jend, coef, blockIdx, gridDim);
 }
 
 // Chunk-major copies of one instance's atoms for the scans: entry
@@ -254,13 +255,14 @@ __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t,
                                               const float* __restrict__ fafb, int32_t n_x,
                                               float4* __restrict__ perm_ant,
                                               float4* __restrict__ perm_x, const fmap_grid& g,
+                                              const int64_t* __restrict__ ax,
                                               TauTab* __restrict__ tauc, int64_t e_begin,
                                               int64_t e_end, int64_t e_step) {
   const int64_t P = perm_entries(n), C = scan_chunk(n);
   const int64_t n_copy = P * (int64_t)(n_ant + n_x);
   for (int64_t e = e_begin; e < e_end; e += e_step) {
     if (e >= n_copy) {   // entries past the copies: the per-tau constants
-      tau_tab_fill(g, e - n_copy, tauc + (e - n_copy));
+      tau_tab_fill(g, ax[g.n_t0 + (e - n_copy)], tauc + (e - n_copy));
       continue;
     }
     const int64_t set = e / P, r = e - set * P;
@@ -289,9 +291,9 @@ __global__ void k_exp_perm(const int32_t* __restrict__ rel_t, int32_t n,
                            const float* __restrict__ antenna, int32_t n_ant,
                            const float* __restrict__ fafb, int32_t n_x,
                            float4* __restrict__ perm_ant, float4* __restrict__ perm_x,
-                           fmap_grid g, TauTab* __restrict__ tauc) {
+                           fmap_grid g, const int64_t* __restrict__ ax, TauTab* __restrict__ tauc) {
   const int64_t total = exp_copy_entries(n, n_ant, n_x, g.n_tau);
-  exp_perm_body(rel_t, n, antenna, n_ant, fafb, n_x, perm_ant, perm_x, g, tauc,
+  exp_perm_body(rel_t, n, antenna, n_ant, fafb, n_x, perm_ant, perm_x, g, ax, tauc,
                 (int64_t)blockIdx.x * blockDim.x + threadIdx.x, total,
                 (int64_t)gridDim.x * blockDim.x);
 }
@@ -303,7 +305,7 @@ cudaError_t launch_exp_perm(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
   const int64_t total = exp_copy_entries(p->n_sft, n_ant, n_x, p->grid.n_tau);
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
   k_exp_perm<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->n_sft, a->antenna, n_ant, a->fafb, n_x,
-                                    p->ws.perm_ant, p->ws.perm_x, p->grid, p->ws.tauc);
+                                    p->ws.perm_ant, p->ws.perm_x, p->grid, p->ws.ax, p->ws.tauc);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -315,7 +317,7 @@ __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __r
                            int32_t n, fmap_grid g, int32_t n_lo, int32_t n_chunk,
                            const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
                            const float2* __restrict__ esuf, const TauTab* __restrict__ tauc,
-                           Coef* __restrict__ coef) {
+                           const int64_t* __restrict__ ax, Coef* __restrict__ coef) {
   const int64_t total = (int64_t)g.n_t0 * n_chunk;
   const int64_t np1 = (int64_t)n + 1;
   const int64_t tb = n > 0 ? *t_base : 0;
@@ -325,7 +327,7 @@ __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __r
     const int32_t nl = (int32_t)(c - m * n_chunk);
     const int64_t nn = n_lo + nl;
     const int64_t cell = m * g.n_tau + nn;
-    coef[cell] = exp_cell_coef(rel_t, n, g, m, tauc[nn].c2[1], tauc[nn].inv_tau, i0tab[m],
+    coef[cell] = exp_cell_coef(rel_t, n, ax[m], tauc[nn].c2[1], tauc[nn].inv_tau, i0tab[m],
                                jend[cell], tb, esuf + (int64_t)nl * 3 * np1);
   }
 }
@@ -339,8 +341,8 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
     const size_t smem = exp_antenna_smem(p->n_sft);
     cudaFuncSetAttribute(k_exp_antenna, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_exp_antenna<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), kSufThreads, smem, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.tauc, p->ws.i0, p->ws.jend,
-        p->ws.coef);
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.tauc, p->ws.ax, p->ws.i0,
+        p->ws.jend, p->ws.coef);
     p->launches += 1;
     return cudaGetLastError();
   }
@@ -355,7 +357,8 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
       const int64_t total = (int64_t)g.n_t0 * len;
       const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
       k_exp_coef<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, lo, len, p->ws.i0,
-                                        p->ws.jend, p->ws.esuf, p->ws.tauc, p->ws.coef + ta * cells);
+                                        p->ws.jend, p->ws.esuf, p->ws.tauc, p->ws.ax,
+                                        p->ws.coef + ta * cells);
       p->launches += 1;
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
@@ -380,10 +383,11 @@ int64_t exp_tiles(const fmap_grid& g) {
 template <typename Acc, int TC>
 __global__ void __launch_bounds__(kExpCells)
 k_exp_plain(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base,
-            int32_t n_sft, fmap_grid g, const int32_t* __restrict__ i0tab,
-            const int32_t* __restrict__ jend, const Coef* __restrict__ coef,
-            int32_t shared_antenna, const float* __restrict__ fafb, int32_t n_templates,
-            float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
+            int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax,
+            const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+            const Coef* __restrict__ coef, int32_t shared_antenna, const float* __restrict__ fafb,
+            int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
+            int64_t stride) {
   constexpr int NCOL = 4 * TC;
   constexpr int LD = NCOL + 4;
   __shared__ __align__(16) float sx[kKC][LD];
@@ -407,8 +411,8 @@ k_exp_plain(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_bas
   __syncthreads();
   const int32_t jmax = s_jmax;
   int32_t t0rel = 0;
-  if (jmax > i0) t0rel = (int32_t)(g.t0_min + (int64_t)m * g.dt0 - *t_base);
-  const double tau = (double)(g.tau_min + (int64_t)(in_grid ? nn : 0) * g.dtau);
+  if (jmax > i0) t0rel = (int32_t)(ax[m] - *t_base);
+  const double tau = (double)ax[g.n_t0 + (in_grid ? nn : 0)];
   const float c2 = (float)(-1.4426950408889634 / tau);
   Acc acc[NCOL];
 #pragma unroll
@@ -475,13 +479,13 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
     constexpr int TC = 8;
     dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + TC - 1) / TC));
     k_exp_plain<double, TC><<<grid, kExpCells, 0, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend, p->ws.coef,
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.ax, p->ws.i0, p->ws.jend, p->ws.coef,
         a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->part_stride);
   } else {
     constexpr int TC = 16;
     dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + TC - 1) / TC));
     k_exp_plain<float, TC><<<grid, kExpCells, 0, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend, p->ws.coef,
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.ax, p->ws.i0, p->ws.jend, p->ws.coef,
         a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->part_stride);
   }
   p->launches += 1;
@@ -496,13 +500,14 @@ __global__ void __launch_bounds__(256) kb_exp_perm(const BItem* __restrict__ ite
     const int64_t total = exp_copy_entries(it.n_sft, it.n_ant, n_x, it.g.n_tau);
     const int64_t e0 = k * kPermPerUnit;
     exp_perm_body(it.rel_t, it.n_sft, it.antenna, it.n_ant, it.fafb, n_x, it.perm_ant, it.perm_x,
-                  it.g, it.tauc, e0 + threadIdx.x, min(total, e0 + kPermPerUnit), 256);
+                  it.g, it.ax, it.tauc, e0 + threadIdx.x, min(total, e0 + kPermPerUnit), 256);
   });
 }
 __global__ void __launch_bounds__(kSufThreads, 3) kb_exp_ant(const BItem* __restrict__ items,
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.perm_ant, it.tauc, it.i0, it.jend,
+    exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.perm_ant, it.tauc, it.ax, it.i0,
+                     it.jend,
                      it.coef,
                      make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                      dim3((unsigned)it.g.n_tau, (unsigned)it.n_ant));

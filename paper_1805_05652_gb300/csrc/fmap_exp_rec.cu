@@ -55,8 +55,8 @@ __device__ __forceinline__ float rec_ex2(float x) {
 __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          const TauTab* __restrict__ tauc, int32_t n_templates, int32_t n_groups,
-          float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
+          const TauTab* __restrict__ tauc, const int64_t* __restrict__ ax, int32_t n_templates,
+          int32_t n_groups, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
     const uint3 bid, const dim3 gdim) {
   static_assert(kRecThreads == kScanLanes, "chunk-major copy layout");
   extern __shared__ __align__(16) float s_dyn[];
@@ -102,7 +102,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     r.pre = 0.0f;
     r.tail = 0.0f;
     if (r.j > r.i0) {
-      const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
+      const int64_t t0rel = ax[m] - tb;
       const int64_t d0 = (int64_t)rel_t[r.i0] - t0rel;
       r.pre = d0 == 0 ? 1.0f : rec_ex2(c2 * (float)d0);
       if (r.j < n) {
@@ -249,10 +249,10 @@ __global__ void __launch_bounds__(kRecThreads)
 k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          const TauTab* __restrict__ tauc, int32_t n_templates, int32_t n_groups,
-          float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
-  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, tauc, n_templates,
-               n_groups, map, parts, stride, blockIdx, gridDim);
+          const TauTab* __restrict__ tauc, const int64_t* __restrict__ ax, int32_t n_templates,
+          int32_t n_groups, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
+  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, tauc, ax,
+               n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
 bool exp_rec_supported(int32_t n_sft, int32_t) { return n_sft <= kRecMaxSft; }
@@ -272,7 +272,7 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
   dim3 grid((unsigned)g.n_tau, (unsigned)groups);
   k_exp_rec<<<grid, kRecThreads, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0,
                                             p->ws.jend, p->ws.coef, a->shared_antenna, p->ws.perm_x,
-                                            p->ws.tauc,
+                                            p->ws.tauc, p->ws.ax,
                                             p->n_templates, groups, d_2F, p->ws.partials,
                                             p->part_stride);
   p->launches += 1;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kRecThreads, 3) kb_exp_rec(const BItem* __rest
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     exp_rec_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared, it.perm_x,
-                 it.tauc,
+                 it.tauc, it.ax,
                  it.T, it.groups, it.map, it.partials, it.part_stride,
                  make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                  dim3((unsigned)it.g.n_tau, (unsigned)it.groups));

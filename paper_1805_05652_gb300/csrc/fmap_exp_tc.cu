@@ -167,6 +167,7 @@ struct Params {
   const int32_t* rel_t;
   const int64_t* t_base;
   fmap_grid g;
+  const int64_t* ax;   // grid values: t0_m, then tau_n
   const int32_t* i0tab;
   const int32_t* jend;
   const Coef* coef;
@@ -304,9 +305,9 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
     const int32_t jc = in_grid ? p.jend[cell] : i0;
     // -log2(e) / tau by an FP32 division (within 1.5 ulp; FP64 runs at 1/64
     // of the FP32 rate on GB300)
-    const float c2 = -1.44269504088896341f / (float)(g.tau_min + (int64_t)(in_grid ? n : 0) * g.dtau);
+    const float c2 = -1.44269504088896341f / (float)p.ax[g.n_t0 + (in_grid ? n : 0)];
     int32_t t0rel = 0;
-    if (jmax > i0) t0rel = (int32_t)(g.t0_min + (int64_t)m * g.dt0 - *p.t_base);
+    if (jmax > i0) t0rel = (int32_t)(p.ax[m] - *p.t_base);
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int gtid = threadIdx.x;          // 0 .. 255 over the generator warps
     bool ok_run = true;
@@ -552,6 +553,7 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   tc::Params prm;
   prm.rel_t = p->ws.rel_t;
   prm.t_base = p->ws.t_base;
+  prm.ax = p->ws.ax;
   prm.g = g;
   prm.i0tab = p->ws.i0;
   prm.jend = p->ws.jend;

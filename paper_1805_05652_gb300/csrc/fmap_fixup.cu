@@ -144,7 +144,7 @@ k_flag_write(const Coef* __restrict__ coef, int64_t n_entries,
 // Block (b, y): entries [b n / G, (b + 1) n / G), templates y*128 + tid.
 __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
         int32_t shared_antenna, const int32_t* __restrict__ rel_t,
-        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g,
+        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax,
         const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
@@ -163,8 +163,8 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
     const int32_t only = shared_antenna ? -1 : (int32_t)(entry / cells);
     const int32_t m = (int32_t)(cell / g.n_tau), nn = (int32_t)(cell % g.n_tau);
     const int32_t i0 = i0tab[m], j = jend[cell];
-    const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - *t_base;
-    const double tau = (double)(g.tau_min + (int64_t)nn * g.dtau);
+    const int64_t t0rel = ax[m] - *t_base;
+    const double tau = (double)ax[g.n_t0 + nn];
     const bool mine = active_t && (only < 0 || only == tq);
     const int32_t ta = shared_antenna ? 0 : tq;
     const float* ant = antenna + (int64_t)ta * 3 * n_sft;
@@ -216,7 +216,7 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
 __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ list,
         const int32_t* __restrict__ n_flag, int32_t G, int32_t shared_antenna,
         const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n_sft,
-        fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+        fmap_grid g, const int64_t* __restrict__ ax, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
         int32_t b, int32_t tq) {
@@ -235,8 +235,8 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
     if (!shared_antenna && entry / cells != tq) continue;
     const int32_t m = (int32_t)(cell / g.n_tau), nn = (int32_t)(cell % g.n_tau);
     const int32_t i0 = i0tab[m], j = jend[cell];
-    const int64_t t0rel = g.t0_min + (int64_t)m * g.dt0 - tb;
-    const double inv_tau = 1.0 / (double)(g.tau_min + (int64_t)nn * g.dtau);
+    const int64_t t0rel = ax[m] - tb;
+    const double inv_tau = 1.0 / (double)ax[g.n_t0 + nn];
     double A = 0, B = 0, C = 0, far = 0, fai = 0, fbr = 0, fbi = 0;
     // Exponential weights along the window by products of the per-gap
     // decays (one exp for the first atom and one for the one-SFT decay;
@@ -277,12 +277,12 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
 __global__ void __launch_bounds__(kFixThreads)
 k_fixup_cells(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
               int32_t shared_antenna, const int32_t* __restrict__ rel_t,
-              const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g,
+              const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax,
               const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
               const float* __restrict__ antenna, const float* __restrict__ fafb,
               int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
               int64_t stride, int64_t slot0) {
-  fixup_cells_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, i0tab, jend, antenna,
+  fixup_cells_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, i0tab, jend, antenna,
                    fafb, n_templates, map, parts, stride, slot0, blockIdx.x, blockIdx.y);
 }
 
@@ -295,11 +295,11 @@ int64_t fixup_blocks_y(int32_t n_templates) {
 __global__ void __launch_bounds__(kFixThreads)
 k_fixup(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
         int32_t shared_antenna, const int32_t* __restrict__ rel_t,
-        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g,
+        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax,
         const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0) {
-  fixup_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, i0tab, jend, antenna, fafb, n_templates, map, parts, stride, slot0, blockIdx, gridDim);
+  fixup_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, i0tab, jend, antenna, fafb, n_templates, map, parts, stride, slot0, blockIdx, gridDim);
 }
 
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
@@ -317,13 +317,13 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
   if (p->n_templates < kFixCellModeT)
     k_fixup_cells<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
                                                a->shared_antenna, p->ws.rel_t, p->ws.t_base,
-                                               p->n_sft, p->grid, p->ws.i0, p->ws.jend,
+                                               p->n_sft, p->grid, p->ws.ax, p->ws.i0, p->ws.jend,
                                                a->antenna, a->fafb, p->n_templates, d_2F,
                                                p->ws.partials, p->part_stride, p->n_tiles);
   else
     k_fixup<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
                                          a->shared_antenna, p->ws.rel_t, p->ws.t_base, p->n_sft,
-                                         p->grid, p->ws.i0, p->ws.jend, a->antenna, a->fafb,
+                                         p->grid, p->ws.ax, p->ws.i0, p->ws.jend, a->antenna, a->fafb,
                                          p->n_templates, d_2F, p->ws.partials, p->part_stride,
                                          p->n_tiles);
   p->launches += 4;
@@ -362,11 +362,11 @@ __global__ void __launch_bounds__(kFixThreads) kb_fixup(const BItem* __restrict_
       const int32_t b = sg * kFixSlotsPerUnit + q;
       if (it.T < kFixCellModeT)
         fixup_cells_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base,
-                         it.n_sft, it.g, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
+                         it.n_sft, it.g, it.ax, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
                          it.partials, it.part_stride, it.n_tiles, b, y);
       else
         fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft,
-                   it.g, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,
+                   it.g, it.ax, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,
                    it.part_stride, it.n_tiles, make_uint3((unsigned)b, (unsigned)y, 0),
                    dim3((unsigned)kFixSlots, (unsigned)((it.T + kFixThreads - 1) / kFixThreads)));
       __syncthreads();   // the bodies' shared scratch is reused by the next slot

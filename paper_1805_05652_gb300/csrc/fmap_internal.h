@@ -112,6 +112,7 @@ struct Workspace {
   float4* perm_ant = nullptr;    // [T_ant][.] (a2, b2, ab, gap to the next atom as int bits; -1 last)
   float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
   TauTab* tauc = nullptr;        // [n_tau] per-tau decay constants
+  int64_t* ax = nullptr;         // [n_t0 + n_tau] the grid: t0_m values, then tau_n values
   // exp
   float2* esuf = nullptr;        // [tau_chunk][3][N+1] float-float decayed suffix sums
   // tensor-core operands
@@ -140,6 +141,10 @@ struct fmap_plan_s {
   int32_t tau_chunk = 0;      // exp: tau values per suffix launch
   size_t xop_bytes = 0;
   bool host_staging = false;
+  // explicit (t0, tau) axes set by fmap_plan_axes (else the uniform grid of
+  // Eq. Fmn, written to ws.ax by each run's prep step); host copy of the axes
+  bool explicit_axes = false;
+  std::vector<int64_t> ax_host;
   // TMA descriptors (CUtensorMap, 128 bytes each) of the split X operands
   alignas(64) unsigned char tmap_hi[128] = {};
   alignas(64) unsigned char tmap_lo[128] = {};

@@ -89,12 +89,24 @@ class Grid:
     window: int = RECT
     t_sft: int = T_SFT
     exp_cut8: int = 0
+    # explicit axes (a non-uniform grid): strictly increasing t0 and tau
+    # values replacing t0_min + m dt0 and tau_min + n dtau
+    t0_values: tuple | None = None
+    tau_values: tuple | None = None
 
     def t0(self) -> np.ndarray:
+        if self.t0_values is not None:
+            return np.asarray(self.t0_values, dtype=np.int64)
         return self.t0_min + self.dt0 * np.arange(self.n_t0, dtype=np.int64)
 
     def tau(self) -> np.ndarray:
+        if self.tau_values is not None:
+            return np.asarray(self.tau_values, dtype=np.int64)
         return self.tau_min + self.dtau * np.arange(self.n_tau, dtype=np.int64)
+
+    @property
+    def has_axes(self) -> bool:
+        return self.t0_values is not None
 
     @property
     def n_cells(self) -> int:
@@ -102,7 +114,8 @@ class Grid:
 
     def with_window(self, window: int) -> "Grid":
         return Grid(self.t0_min, self.dt0, self.n_t0, self.tau_min, self.dtau,
-                    self.n_tau, window, self.t_sft, self.exp_cut8)
+                    self.n_tau, window, self.t_sft, self.exp_cut8, self.t0_values,
+                    self.tau_values)
 
     def window_len(self, tau):
         """L(tau) in seconds: tau (rect) or floor(exp_cut8 tau / 8) (exp)."""
@@ -111,8 +124,12 @@ class Grid:
         return (self.exp_cut8 or 24) * tau // 8
 
     def as_tuple(self):
-        return (self.t0_min, self.dt0, self.n_t0, self.tau_min, self.dtau,
+        base = (self.t0_min, self.dt0, self.n_t0, self.tau_min, self.dtau,
                 self.n_tau, self.t_sft, self.window, self.exp_cut8)
+        if self.has_axes:
+            return base + (tuple(int(v) for v in self.t0_values),
+                           tuple(int(v) for v in self.tau_values))
+        return base
 
 
 @dataclass

@@ -112,6 +112,71 @@ def test_exp_window_cut(cut8, prec):
         raise
 
 
+def _axes_instance(window, seed):
+    """A non-uniform (t0, tau) grid: sorted random values with uneven steps,
+    t0 from before the data to past its end, 48 x 160 cells (several tiles
+    and ragged tails)."""
+    rng = np.random.default_rng(seed)
+    t0 = np.sort(rng.choice(np.arange(-4 * T_SFT, 300 * T_SFT, 211), size=48, replace=False))
+    lo = 2 * T_SFT if window == RECT else T_SFT // 2
+    tau = np.sort(rng.choice(np.arange(lo, 200 * T_SFT, 173), size=160, replace=False))
+    grid = Grid(0, 1, len(t0), 1, 1, len(tau), window, T_SFT, 0,
+                tuple(int(v) for v in t0), tuple(int(v) for v in tau))
+    return synth.make_instance(seed, n_det=2, presence=0.9, n_merged=300, n_templates=5,
+                               grid=grid, injections=[(2, window, 40 * T_SFT, 60 * T_SFT, 200.0)])
+
+
+@pytest.mark.parametrize("window,prec", [(RECT, "fp64"), (RECT, "fp32"), (EXP, "fp64"),
+                                         (EXP, "tf32"), (EXP, "bf16x3"), (EXP, "rec")])
+def test_explicit_axes(window, prec):
+    """Non-uniform grids through fmap_plan_axes: every path against the
+    oracle on the same axes."""
+    inst = _axes_instance(window, 61 + window)
+    try:
+        _parity(inst, prec)
+    except fm.FmapError as e:
+        if e.status == fm.FMAP_ERR_UNSUPPORTED:
+            pytest.skip(f"{prec} not built")
+        raise
+
+
+def test_explicit_axes_checks_count_and_reset():
+    """fmap_plan_axes rejects unsorted or non-positive values and a missing
+    axis; fmap_plan_count_terms counts the axes' windows; (NULL, NULL)
+    restores the uniform grid."""
+    import torch
+
+    inst = _axes_instance(EXP, 70)
+    g = inst.grid
+    plan = fm.Plan(g, inst.n_sft, inst.n_templates, "fp64")
+    t0, tau = np.array(g.t0_values), np.array(g.tau_values)
+    for bad_t0, bad_tau in ((t0[::-1], tau), (t0, tau[::-1]), (t0, np.r_[0, tau[1:]])):
+        with pytest.raises(fm.FmapError) as e:
+            plan.set_axes(bad_t0, bad_tau)
+        assert e.value.status == fm.FMAP_ERR_ARG
+    tau64 = np.ascontiguousarray(tau, dtype=np.int64)
+    assert fm.binding.lib().fmap_plan_axes(plan.handle, None, tau64.ctypes.data) == fm.FMAP_ERR_ARG
+    plan.set_axes(t0, tau)
+    _, cnt = oracle.sums(inst.t, inst.antenna, inst.fafb, g.as_tuple())
+    assert plan.count_terms(inst.t) == (int(cnt[cnt >= 2].sum()), int((cnt >= 2).sum()))
+    # back to the uniform grid of the struct fields
+    plan.set_axes(None, None)
+    uni = Grid(-T_SFT, 2 * T_SFT, g.n_t0, T_SFT, 3 * T_SFT, g.n_tau, EXP)
+    plan.close()
+    plan = fm.Plan(uni, inst.n_sft, inst.n_templates, "fp64")
+    dev = torch.device("cuda", 0)
+    args = (torch.from_numpy(inst.t).to(dev), torch.from_numpy(inst.antenna).to(dev),
+            torch.from_numpy(inst.fafb).to(dev))
+    m_uni, _ = plan.compute(*args)
+    plan.set_axes(uni.t0(), uni.tau())
+    m_ax, _ = plan.compute(*args)
+    plan.set_axes(None, None)
+    m_back, _ = plan.compute(*args)
+    torch.cuda.synchronize()
+    assert torch.equal(m_uni, m_ax) and torch.equal(m_uni, m_back)
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "rec"])
 def test_exp_per_template_antenna(prec):
     grid = Grid(0, T_SFT, 20, T_SFT, T_SFT, 140, EXP)

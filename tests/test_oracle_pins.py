@@ -414,3 +414,62 @@ def test_logB_special_cases_and_logsumexp():
     assert (s["m"][0], s["n"][0]) == (1, 3)
     s = oracle.summary(m, v, log_prior_const=-1.5)
     assert s["logB"][0] == pytest.approx(c - 1.5, abs=1e-13)
+
+
+def _axes_grid(window, cut8=0):
+    """A non-uniform grid: sorted random t0 values (some before the data,
+    some past its end) and tau values with uneven steps."""
+    rng = np.random.default_rng(5 + window)
+    t0 = np.sort(rng.choice(np.arange(-3 * T_SFT, 40 * T_SFT, 97), size=23, replace=False))
+    tau = np.sort(rng.choice(np.arange(T_SFT // 2, 30 * T_SFT, 113), size=17, replace=False))
+    return Grid(0, 1, len(t0), 1, 1, len(tau), window, T_SFT, cut8,
+                tuple(int(v) for v in t0), tuple(int(v) for v in tau))
+
+
+@pytest.mark.parametrize("window", [RECT, EXP])
+def test_explicit_axes_equal_uniform_grid(window):
+    """Explicit axes holding a uniform grid's own values give that grid's
+    sums and maps exactly (direct and per-row modes)."""
+    grid = Grid(-2000, 1700, 30, 900, 2300, 25, window)
+    inst = synth.make_instance(8, n_det=2, presence=0.8, n_merged=120, n_templates=2,
+                               grid=grid, dtype=np.float64)
+    ax = Grid(7, 3, grid.n_t0, 11, 5, grid.n_tau, window, T_SFT, 0,
+              tuple(int(v) for v in grid.t0()), tuple(int(v) for v in grid.tau()))
+    s_u, c_u = oracle.sums(inst.t, inst.antenna, inst.fafb, grid.as_tuple())
+    s_a, c_a = oracle.sums(inst.t, inst.antenna, inst.fafb, ax.as_tuple())
+    assert np.array_equal(c_u, c_a) and np.array_equal(s_u, s_a)
+    for mode in ("direct", "fast"):
+        m_u, v_u, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, grid.as_tuple(), mode=mode)
+        m_a, v_a, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, ax.as_tuple(), mode=mode)
+        assert np.array_equal(v_u, v_a) and np.array_equal(m_u, m_a)
+
+
+@pytest.mark.parametrize("window,cut8", [(RECT, 0), (EXP, 0), (EXP, 12)])
+def test_explicit_axes_brute_force(window, cut8):
+    """Window sums on a non-uniform grid against a plain double loop over the
+    atoms with the membership rule t0 <= t, t + T_sft <= t0 + L(tau) and the
+    weights of Eq. winrect / winexp (w for Fa, Fb; w^2 for A, B, C); the
+    per-row fast mode agrees with the direct one."""
+    grid = _axes_grid(window, cut8)
+    inst = synth.make_instance(9, n_det=2, presence=0.7, n_merged=30, n_templates=2,
+                               grid=Grid(0, 1, 1, 1, 1, 1, window), dtype=np.float64)
+    s, cnt = oracle.sums(inst.t, inst.antenna, inst.fafb, grid.as_tuple())
+    L8 = 8 if window == RECT else (cut8 or 24)
+    for mi, t0 in enumerate(grid.t0()):
+        for ni, tau in enumerate(grid.tau()):
+            ref = np.zeros((2, 7))
+            c = 0
+            for a, t in enumerate(inst.t):
+                if t < t0 or 8 * (t + T_SFT - t0) > L8 * tau:
+                    continue
+                w = 1.0 if window == RECT else math.exp(-(t - t0) / tau)
+                c += 1
+                for j in range(2):
+                    ref[j, :3] += w * w * inst.antenna[:, a]
+                    ref[j, 3:] += w * inst.fafb[j, :, a]
+            assert cnt[mi, ni] == c
+            assert np.allclose(s[:, mi, ni], ref, rtol=1e-12, atol=1e-13)
+    m_d, v_d, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, grid.as_tuple(), mode="direct")
+    m_f, v_f, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, grid.as_tuple(), mode="fast")
+    assert np.array_equal(v_d, v_f)
+    assert np.allclose(m_d, m_f, rtol=1e-10, atol=1e-10)
