@@ -60,13 +60,30 @@ def jitter_axes(grid, seed):
     grid.tau_values = tuple(int(v) for v in tau)
 
 
-def make_workload(name, rank, templates=None, exp_cut8=0, axes=False):
+def window_table(shape, cut8=0, n=1024):
+    """Samples of a generic window on [0, X], X = cut8 / 8 (default 3): "exp"
+    is e^{-x} (the exponential window through the generic path), "bump" a
+    rise over 0.4 then a decay."""
+    x = np.linspace(0.0, (cut8 or 24) / 8.0, n)
+    if shape == "exp":
+        w = np.exp(-x)
+    elif shape == "bump":
+        w = np.sin(np.pi * np.minimum(x / 0.4, 1.0) / 2) ** 2 * np.exp(-0.7 * x)
+    else:
+        raise SystemExit(f"unknown window table {shape}")
+    return tuple(float(v) for v in w.astype(np.float32))
+
+
+def make_workload(name, rank, templates=None, exp_cut8=0, axes=False, table=None):
     if name == "exp16":
         kw = {} if templates is None else {"n_templates": templates}
         inst = synth.config_exp16(seed=synth.BASE_SEED + 1 + 1000 * rank, **kw)
         inst.grid.exp_cut8 = exp_cut8   # window length exp_cut8 tau / 8 (0: 3 tau)
         if axes:
             jitter_axes(inst.grid, synth.BASE_SEED + 1 + 1000 * rank)
+        if table:
+            inst.grid.window = synth.TABLE
+            inst.grid.window_table = window_table(table, exp_cut8)
         return inst
     if name == "batch_rect":
         kw = {} if templates is None else {"n_templates": templates}
@@ -78,6 +95,7 @@ def count_terms(grid, t):
     """(terms, cells with >= 2 SFTs) of a grid: the library's host count for
     uniform grids; for explicit axes the same rule with numpy searches."""
     if not grid.has_axes:
+        import paper_1805_05652_gb300 as fm
         return fm.fmap_count_terms(grid, t)
     t0 = grid.t0()
     i0 = np.searchsorted(t, t0, side="left")
@@ -182,6 +200,7 @@ def cpu_baseline(inst, target_s=12.0):
             sg.t0_values = tuple(g.t0_values[stride // 2::stride][:sg.n_t0])
             sg.n_t0 = len(sg.t0_values)
             sg.tau_values = g.tau_values
+        sg.window_table = g.window_table
         return sg
 
     def run(rows):
@@ -222,6 +241,8 @@ def main():
                     help="exp16: window length in eighths of tau (0: 3 tau, Eq. winexp)")
     ap.add_argument("--grid-axes", action="store_true",
                     help="exp16: explicit non-uniform (t0, tau) axes (seeded jitter of the steps)")
+    ap.add_argument("--window-table", default=None, choices=["exp", "bump"],
+                    help="exp16: a generic (table) window of 1024 samples instead of exp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--also", default="fp32,tf32,rec",
@@ -265,7 +286,8 @@ def main():
             print(json.dumps(result), flush=True)
         return
 
-    inst = make_workload(args.workload, rank, args.templates, args.exp_cut8, args.grid_axes)
+    inst = make_workload(args.workload, rank, args.templates, args.exp_cut8, args.grid_axes,
+                         args.window_table)
     g = inst.grid
     window = g.window
     precision = args.precision
@@ -360,7 +382,8 @@ def main():
         peaks, peak_src = load_peaks()
         dom_ms = float(phase_ms[2])
         flops = 2.0 * terms * 4            # multiply + add per (cell, SFT, data column) x 4 columns
-        if window == synth.EXP and precision in ("bf16x3", "tf32"):
+        wname = "table" if window == synth.TABLE else "exp"
+        if window != synth.RECT and precision in ("bf16x3", "tf32"):
             if precision == "bf16x3":
                 peak, unit_peak = peaks["bf16_tflops"], "TFLOP/s (bf16, %s)" % peak_src
             else:
@@ -368,14 +391,14 @@ def main():
                 unit_peak = "TFLOP/s (tf32 = bf16 x 1.1/2.25 nominal, %s)" % peak_src
             ach = flops / (dom_ms / 1e3) / 1e12
             roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "kernel": "exp contraction (phase 2)",
+                    "frac": ach / peak, "traffic": None, "kernel": f"{wname} contraction (phase 2)",
                     "peak_source": unit_peak}
-        elif window == synth.EXP:
+        elif window != synth.RECT:
             sm_mhz = peaks.get("sm_max_mhz", 2070.0)
             peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
             ach = flops / (dom_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "kernel": "exp contraction (phase 2)",
+                    "frac": ach / peak, "traffic": None, "kernel": f"{wname} contraction (phase 2)",
                     "peak_source": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock"}
         else:
             byts = T * g.n_t0 * g.n_tau * 4.0
@@ -410,7 +433,9 @@ def main():
                        "n_t0": g.n_t0, "n_tau": g.n_tau, "terms_per_step": terms,
                        "cells_with_2plus_sft": cells2,
                        **({"exp_window_len": f"{g.exp_cut8}/8 tau" if g.exp_cut8 else "3 tau"}
-                          if g.window == synth.EXP else {}),
+                          if g.window != synth.RECT else {}),
+                       **({"window": f"table ({args.window_table}, 1024 samples)"}
+                          if g.window == synth.TABLE else {}),
                        **({"grid": "explicit axes (steps jittered by [0, step/2))"}
                           if g.has_axes else {}),
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
@@ -678,7 +703,7 @@ def reference_arm(args, rank, world):
     """The CPU oracle as the reference implementation, on the host cores."""
     if rank != 0:
         return
-    inst = make_workload(args.workload, 0, None, args.exp_cut8, args.grid_axes)
+    inst = make_workload(args.workload, 0, None, args.exp_cut8, args.grid_axes, args.window_table)
     info, sg, terms = cpu_baseline(inst, target_s=min(4.0, 150.0 / (args.steps + args.warmup)))
     import oracle
 

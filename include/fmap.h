@@ -55,7 +55,10 @@ typedef enum {
   FMAP_ERR_UNSUPPORTED = -7  /* valid request this build cannot serve */
 } fmap_status;
 
-typedef enum { FMAP_RECT = 0, FMAP_EXP = 1 } fmap_window;
+/* FMAP_TABLE: a generic window function w(x), x = (t - t0) / tau, given as a
+ * table of samples (fmap_plan_window_table), on the exponential window's
+ * support [t0, t0 + floor(exp_cut8 tau / 8)]. */
+typedef enum { FMAP_RECT = 0, FMAP_EXP = 1, FMAP_TABLE = 2 } fmap_window;
 
 /*
  * Arithmetic of the windowed sums.  In every mode the antenna sums A, B, C,
@@ -191,6 +194,25 @@ fmap_status fmap_compute_rect(fmap_plan_t* plan, const fmap_atoms* atoms, float*
                               fmap_summary* d_summary, fmap_stream stream);
 fmap_status fmap_compute_exp(fmap_plan_t* plan, const fmap_atoms* atoms, float* d_2F,
                              fmap_summary* d_summary, fmap_stream stream);
+
+/*
+ * Generic window functions (FMAP_TABLE grids): the paper's windowed sums
+ * with any amplitude envelope w in place of Eq. (winrect) / (winexp).
+ * fmap_plan_window_table: w sampled at n_points (2..1024) equally spaced
+ * x_k = k X / (n_points - 1), X = exp_cut8 / 8 (24 / 8 = 3 by default), as a
+ * HOST float array, copied into the plan (synchronously); between samples w
+ * is linear, beyond X it is 0.  The atom at t weighs w((t - t0) / tau) in Fa,
+ * Fb and w^2 in A, B, C (membership as for exp windows).  Errors: FMAP_ERR_ARG
+ * (not a table plan, bad size or non-finite values), FMAP_ERR_CUDA.
+ * fmap_compute_table: as fmap_compute_exp for a table plan (FMAP_FP64 and
+ * FMAP_FP32 on the CUDA cores, FMAP_TF32 and FMAP_BF16X3 on the tensor cores;
+ * the antenna sums A, B, C are float-float sums over each window); the table
+ * must be set first (else FMAP_ERR_ARG).  Batches and the server do not take
+ * table windows.
+ */
+fmap_status fmap_plan_window_table(fmap_plan_t* plan, const float* w, int32_t n_points);
+fmap_status fmap_compute_table(fmap_plan_t* plan, const fmap_atoms* atoms, float* d_2F,
+                               fmap_summary* d_summary, fmap_stream stream);
 
 /*
  * fmap_marginalise: the reductions alone (max 2F, argmax, marginalised logB;

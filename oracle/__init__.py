@@ -51,24 +51,34 @@ def _p(a):
 
 def _grid_array(grid, inclusive=False):
     """int64 grid array of the C oracle.  ``grid``: (t0_min, dt0, n_t0,
-    tau_min, dtau, n_tau, t_sft, window[, exp_cut8[, t0_values, tau_values]]);
-    explicit axes replace the uniform t0 and tau steps."""
+    tau_min, dtau, n_tau, t_sft, window[, exp_cut8[, t0_values, tau_values[,
+    window_table]]]); explicit axes (or None) replace the uniform t0 and tau
+    steps, a window table (float32 samples) defines window 2."""
     g = list(grid)
-    axes = None
+    axes, table = None, None
+    if len(g) == 12:
+        table = g[11]
+        g = g[:11]
     if len(g) == 11:
-        axes = (np.asarray(g[9], dtype=np.int64), np.asarray(g[10], dtype=np.int64))
+        if g[9] is not None:
+            axes = (np.asarray(g[9], dtype=np.int64), np.asarray(g[10], dtype=np.int64))
         g = g[:9]
     if len(g) == 8:
         g.append(0)
     if len(g) != 9:
         raise ValueError("grid must be (t0_min, dt0, n_t0, tau_min, dtau, n_tau, t_sft, window"
-                         "[, exp_cut8[, t0_values, tau_values]])")
-    head = [int(v) for v in g[:8]] + [1 if inclusive else 0, int(g[8]), 1 if axes else 0]
-    if axes is None:
-        return np.array(head, dtype=np.int64)
-    if axes[0].shape != (head[2],) or axes[1].shape != (head[5],):
-        raise ValueError("axes must hold n_t0 t0 values and n_tau tau values")
-    return np.concatenate([np.array(head, dtype=np.int64), axes[0], axes[1]])
+                         "[, exp_cut8[, t0_values, tau_values[, window_table]]])")
+    tab = None if table is None else np.ascontiguousarray(table, dtype=np.float32)
+    head = [int(v) for v in g[:8]] + [1 if inclusive else 0, int(g[8]), 1 if axes else 0,
+                                      0 if tab is None else int(tab.shape[0])]
+    parts = [np.array(head, dtype=np.int64)]
+    if axes is not None:
+        if axes[0].shape != (head[2],) or axes[1].shape != (head[5],):
+            raise ValueError("axes must hold n_t0 t0 values and n_tau tau values")
+        parts += [axes[0], axes[1]]
+    if tab is not None:
+        parts.append(tab.view(np.uint32).astype(np.int64))
+    return np.concatenate(parts)
 
 
 def _atoms(t, antenna, fafb):

@@ -31,12 +31,14 @@
  *   - logB = ln( (1/N_valid) sum_valid e^{F_mn} ) + log_prior_const;
  *   - argmax ties go to the lowest linear index m * N_tau + n.
  *
- * Grid array g (int64[11], or int64[11 + n_t0 + n_tau]): t0_min, dt0, n_t0,
- * tau_min, dtau, n_tau, t_sft, window (0 rect, 1 exp), inclusive (0 / 1),
- * exp cut in eighths of tau (0: 24, i.e. 3 tau), explicit axes (0 / 1).  With
- * explicit axes the t0 values and then the tau values follow (a non-uniform
- * grid; t0_min, dt0, tau_min and dtau are then unused); otherwise t0_m =
- * t0_min + m dt0 and tau_n = tau_min + n dtau (Eq. Fmn).
+ * Grid array g (int64[12 + ...]): t0_min, dt0, n_t0, tau_min, dtau, n_tau,
+ * t_sft, window (0 rect, 1 exp, 2 table), inclusive (0 / 1), exp / table cut
+ * in eighths of tau (0: 24, i.e. 3 tau), explicit axes (0 / 1), number of
+ * window-table samples (window 2).  With explicit axes the t0 values and then
+ * the tau values follow (a non-uniform grid; t0_min, dt0, tau_min and dtau are
+ * then unused); otherwise t0_m = t0_min + m dt0 and tau_n = tau_min + n dtau
+ * (Eq. Fmn).  A table window's samples follow last, each the IEEE bit
+ * pattern of a float32 value in an int64.
  * Atom layout: t[N] ascending (the direct mode accepts any order);
  * antenna [3][N] (a^2, b^2, ab) shared by all templates, or [T][3][N];
  * fafb [T][4][N] (Re Fa, Im Fa, Re Fb, Im Fb).
@@ -50,7 +52,7 @@
 #endif
 
 enum { G_T0MIN, G_DT0, G_NT0, G_TAUMIN, G_DTAU, G_NTAU, G_TSFT, G_WIN, G_INCL, G_CUT, G_AXES,
-       G_VALUES };
+       G_NTAB, G_VALUES };
 
 /* Grid values t0_m and tau_n (Eq. Fmn, or the explicit axes). */
 static int64_t t0_at(const int64_t* g, int64_t m) {
@@ -85,9 +87,32 @@ static int inside_window(const int64_t* g, int64_t t, int64_t t0, int64_t tau) {
   return t + g[G_TSFT] <= t0 + len;
 }
 
+/* Sample k of a table window (float32 bits stored in the grid array). */
+static double table_sample(const int64_t* g, int64_t k) {
+  const int64_t* tab = g + G_VALUES + (g[G_AXES] ? g[G_NT0] + g[G_NTAU] : 0);
+  uint32_t bits = (uint32_t)tab[k];
+  float v;
+  memcpy(&v, &bits, sizeof v);
+  return (double)v;
+}
+
+/* Generic window: the samples w_k at x_k = k X / (n - 1), X = cut / 8, joined
+ * linearly; 0 past X. */
+static double table_weight(const int64_t* g, int64_t t, int64_t t0, int64_t tau) {
+  const int64_t n = g[G_NTAB];
+  const int64_t cut8 = g[G_CUT] > 0 ? g[G_CUT] : 24;
+  const double u = (double)(t - t0) * ((double)(n - 1) * 8.0 / ((double)cut8 * (double)tau));
+  const double k = floor(u);
+  if (k >= (double)(n - 1)) return k > (double)(n - 1) ? 0.0 : table_sample(g, n - 1);
+  const int64_t i = (int64_t)k;
+  const double w0 = table_sample(g, i), w1 = table_sample(g, i + 1);
+  return w0 + (u - k) * (w1 - w0);
+}
+
 static double window_weight(const int64_t* g, int64_t t, int64_t t0, int64_t tau) {
   if (!inside_window(g, t, t0, tau)) return 0.0;
   if (g[G_WIN] == 0) return 1.0;
+  if (g[G_WIN] == 2) return table_weight(g, t, t0, tau);
   return exp(-(double)(t - t0) / (double)tau);
 }
 
@@ -230,7 +255,7 @@ int oracle_fmap(int mode, const int64_t* g, int n_sft, const int64_t* t, int n_t
             if (j == 0 && counts) counts[m * n_tau + n] = c;
           }
         } else {
-          /* exponential: each cell sums its own window; the weights of a
+          /* exponential or table window: each cell sums its own window; the weights of a
            * cell are shared by all templates */
           int a0 = first_at_or_after(n_sft, t, t0);
           for (int64_t n = 0; n < n_tau; ++n) {
@@ -239,7 +264,7 @@ int oracle_fmap(int mode, const int64_t* g, int n_sft, const int64_t* t, int n_t
             for (int k = 0; k < 4 * n_templates; ++k) acc[k] = 0.0;
             int32_t c = 0;
             for (int a = a0; a < n_sft && inside_window(g, t[a], t0, tau); ++a) {
-              double w = exp(-(double)(t[a] - t0) / (double)tau);
+              double w = window_weight(g, t[a], t0, tau);
               double w2 = w * w;
               if (shared_antenna) {
                 sa[0] += w2 * antenna[a];
@@ -261,7 +286,7 @@ int oracle_fmap(int mode, const int64_t* g, int n_sft, const int64_t* t, int n_t
                 const double* ant = antenna + (int64_t)jj * 3 * n_sft;
                 A = B = C = 0.0;
                 for (int a = a0; a < n_sft && inside_window(g, t[a], t0, tau); ++a) {
-                  double w = exp(-(double)(t[a] - t0) / (double)tau);
+                  double w = window_weight(g, t[a], t0, tau);
                   A += w * w * ant[a];
                   B += w * w * ant[n_sft + a];
                   C += w * w * ant[2 * n_sft + a];

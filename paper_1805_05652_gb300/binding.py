@@ -25,7 +25,7 @@ FMAP_OK, FMAP_PENDING = 0, 1
 FMAP_ERR_ARG, FMAP_ERR_NOMEM, FMAP_ERR_CUDA, FMAP_ERR_TIMEOUT = -1, -2, -3, -4
 FMAP_ERR_BUSY, FMAP_ERR_DATA, FMAP_ERR_UNSUPPORTED = -5, -6, -7
 # fmap_window / fmap_precision / plan flags
-FMAP_RECT, FMAP_EXP = 0, 1
+FMAP_RECT, FMAP_EXP, FMAP_TABLE = 0, 1, 2
 FMAP_FP64, FMAP_FP32, FMAP_TF32, FMAP_BF16X3 = 0, 1, 2, 3
 FMAP_PLAN_PER_TEMPLATE_ANTENNA = 1
 FMAP_PLAN_EXP_RECURRENCE = 2
@@ -64,7 +64,8 @@ EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_
            "fmap_noalloc_scratch_bytes", "fmap_server_create", "fmap_server_destroy",
            "fmap_submit", "fmap_poll", "fmap_server_stats", "fmap_batch_plan", "fmap_batch_run",
            "fmap_batch_status", "fmap_batch_info", "fmap_batch_profile", "fmap_batch_destroy",
-           "fmap_plan_axes", "fmap_plan_count_terms")
+           "fmap_plan_axes", "fmap_plan_count_terms", "fmap_plan_window_table",
+           "fmap_compute_table")
 FMAP_BATCH_AUTOTUNE = 1
 N_BATCH_PHASES = 15
 FMAP_N_PHASES = 4
@@ -101,12 +102,13 @@ def lib():
     L.fmap_workspace_bytes.argtypes = [P(fmap_grid), c_i32, c_i32, ctypes.c_int]
     L.fmap_workspace_bytes.restype = c_size
     L.fmap_plan_set_log_prior.argtypes = [c_vp, c_f64]
-    for f in ("fmap_compute_rect", "fmap_compute_exp", "fmap_compute_host"):
+    for f in ("fmap_compute_rect", "fmap_compute_exp", "fmap_compute_table", "fmap_compute_host"):
         getattr(L, f).argtypes = [c_vp, P(fmap_atoms), c_vp, c_vp, c_vp]
     L.fmap_marginalise.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp]
     L.fmap_plan_status.argtypes = [c_vp]
     L.fmap_count_terms.argtypes = [P(fmap_grid), c_vp, c_i32, P(c_i64), P(c_i64)]
     L.fmap_plan_axes.argtypes = [c_vp, c_vp, c_vp]
+    L.fmap_plan_window_table.argtypes = [c_vp, c_vp, c_i32]
     L.fmap_plan_count_terms.argtypes = [c_vp, c_vp, c_i32, P(c_i64), P(c_i64)]
     L.fmap_plan_enable_timing.argtypes = [c_vp, c_i32]
     L.fmap_plan_read_timing.argtypes = [c_vp, c_vp, P(c_i64), P(c_i64)]
@@ -238,6 +240,17 @@ def fmap_compute_rect(plan: int, atoms: fmap_atoms, d_2F, d_summary, stream=None
 def fmap_compute_exp(plan: int, atoms: fmap_atoms, d_2F, d_summary, stream=None):
     _check(lib().fmap_compute_exp(c_vp(plan), ctypes.byref(atoms), _ptr(d_2F), _ptr(d_summary),
                                   _stream(stream)), "fmap_compute_exp")
+
+
+def fmap_compute_table(plan: int, atoms: fmap_atoms, d_2F, d_summary, stream=None):
+    _check(lib().fmap_compute_table(c_vp(plan), ctypes.byref(atoms), _ptr(d_2F),
+                                    _ptr(d_summary), _stream(stream)), "fmap_compute_table")
+
+
+def fmap_plan_window_table(handle, w):
+    """Samples of a generic window (FMAP_TABLE plans), host float32."""
+    a = np.ascontiguousarray(w, dtype=np.float32)
+    _check(lib().fmap_plan_window_table(handle, _ptr(a), int(a.shape[0])), "fmap_plan_window_table")
 
 
 def fmap_compute_host(plan: int, atoms: fmap_atoms, h_2F, h_summary, stream=None):
@@ -511,6 +524,8 @@ class Plan:
         self.handle = fmap_plan(self.g, self.n_sft, self.n_templates, self.precision, self.flags)
         if getattr(self.grid, "t0_values", None) is not None:   # explicit axes
             self.set_axes(self.grid.t0_values, self.grid.tau_values)
+        if getattr(self.grid, "window_table", None) is not None:   # generic window
+            fmap_plan_window_table(self.handle, self.grid.window_table)
 
     def set_axes(self, t0_values, tau_values):
         fmap_plan_axes(self.handle, t0_values, tau_values)
@@ -548,7 +563,9 @@ class Plan:
         if s is None and want_summary:
             s = torch.empty((T, 32), dtype=torch.uint8, device=dev)
         a = self.atoms(t, antenna, fafb)
-        if self.g.window == FMAP_RECT:
+        if self.g.window == FMAP_TABLE:
+            fmap_compute_table(self.handle, a, m, s, stream)
+        elif self.g.window == FMAP_RECT:
             fmap_compute_rect(self.handle, a, m, s, stream)
         else:
             fmap_compute_exp(self.handle, a, m, s, stream)

@@ -33,7 +33,8 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 static bool grid_valid(const fmap_grid* g, std::string* why) {
   if (!g) return *why = "grid is NULL", false;
   if (g->n_t0 < 0 || g->n_tau < 0) return *why = "n_t0 and n_tau must be >= 0", false;
-  if (g->window != FMAP_RECT && g->window != FMAP_EXP) return *why = "unknown window", false;
+  if (g->window != FMAP_RECT && g->window != FMAP_EXP && g->window != FMAP_TABLE)
+    return *why = "unknown window", false;
   if (g->t_sft <= 0) return *why = "t_sft must be > 0", false;
   if (g->tau_min <= 0) return *why = "tau_min must be > 0", false;
   if (g->n_tau > 1 && g->dtau <= 0) return *why = "dtau must be > 0 when n_tau > 1", false;
@@ -41,7 +42,7 @@ static bool grid_valid(const fmap_grid* g, std::string* why) {
   const int64_t cells = (int64_t)g->n_t0 * g->n_tau;
   if (cells >= (int64_t)0x7fffffff) return *why = "n_t0 * n_tau must be < 2^31", false;
   const double tau_max = (double)g->tau_min + (double)std::max(0, g->n_tau - 1) * (double)g->dtau;
-  if (g->window == FMAP_EXP && (g->exp_cut8 < 0 || g->exp_cut8 > 1024))
+  if (g->window != FMAP_RECT && (g->exp_cut8 < 0 || g->exp_cut8 > 1024))
     return *why = "exp_cut8 must be in 0..1024", false;
   const double lmax = g->window == FMAP_RECT ? tau_max : tau_max * exp_cut8_of(*g) / 8.0;
   if (lmax >= 2147483647.0) return *why = "the window length at tau_max must be < 2^31 s", false;
@@ -85,7 +86,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
-      esuf, xop, perm_ant, perm_x, tauc, ax, total;
+      esuf, xop, perm_ant, perm_x, tauc, ax, wtab, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -127,7 +128,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
   L.flag_blocks = take(sizeof(int32_t) * ((entries + kFlagUnit - 1) / kFlagUnit));
   L.n_flag = take(sizeof(int32_t));
   L.flag_list = take(sizeof(int64_t) * entries);
-  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.tauc = 0;
+  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.tauc = L.wtab = 0;
   const size_t np1 = (size_t)n_sft + 1;
   if (g->window == FMAP_RECT) {
     L.pa = take(sizeof(float) * 8 * np1 * (size_t)t_ant);   // (a2, b2, ab, 0) float pairs
@@ -143,6 +144,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.perm_ant = take(perm * (size_t)t_ant);
     if (flags & FMAP_PLAN_EXP_RECURRENCE) L.perm_x = take(perm * (size_t)std::max<int32_t>(T, 1));
     L.tauc = take(sizeof(TauTab) * (size_t)std::max<int32_t>(g->n_tau, 1));
+    if (g->window == FMAP_TABLE) L.wtab = take(sizeof(float2) * (kTabMax + 1));
     if (prec == FMAP_TF32 || prec == FMAP_BF16X3)
       L.xop = take(exp_tc_operand_bytes(*g, n_sft, T, prec));
   }
@@ -263,6 +265,7 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
     w.esuf = (float2*)(b + L.esuf);
     w.perm_ant = (float4*)(b + L.perm_ant);
     if (L.perm_x) w.perm_x = (float4*)(b + L.perm_x);
+    if (L.wtab) w.wtab = (float2*)(b + L.wtab);
     w.tauc = (TauTab*)(b + L.tauc);
     if (L.xop) w.xop = (void*)(b + L.xop);
   }
@@ -375,6 +378,8 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   if (!p) return arg_fail("plan is NULL");
   if (p->grid.window != window)
     return arg_fail("the plan's grid window does not match this compute call");
+  if (window == FMAP_TABLE && p->n_tab < 2)
+    return arg_fail("fmap_plan_window_table has not been called on this plan");
   fmap_status st = check_atoms(p, a);
   if (st != FMAP_OK) return st;
   st = check_device(p);
@@ -398,6 +403,13 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   if (window == FMAP_RECT) {
     FMAP_CUDA(launch_rect_coef(p, a, s));
     FMAP_CUDA(launch_rect(p, a, d_2F, s, &tiles, ev[2]));
+  } else if (window == FMAP_TABLE) {
+    FMAP_CUDA(launch_table_antenna(p, a, s));
+    if (ev[2]) FMAP_CUDA(cudaEventRecord(ev[2], s));
+    if (p->precision == FMAP_TF32 || p->precision == FMAP_BF16X3)
+      FMAP_CUDA(launch_exp_tc(p, a, d_2F, s, &tiles));
+    else
+      FMAP_CUDA(launch_exp_plain(p, a, d_2F, s, &tiles));
   } else {
     FMAP_CUDA(launch_exp_perm(p, a, s));
     FMAP_CUDA(launch_exp_coef(p, a, s));
@@ -425,6 +437,29 @@ fmap_status fmap_compute_rect(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
 fmap_status fmap_compute_exp(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
                              fmap_summary* d_summary, fmap_stream stream) {
   return compute(p, a, d_2F, d_summary, (cudaStream_t)stream, FMAP_EXP);
+}
+
+fmap_status fmap_compute_table(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
+                               fmap_summary* d_summary, fmap_stream stream) {
+  return compute(p, a, d_2F, d_summary, (cudaStream_t)stream, FMAP_TABLE);
+}
+
+fmap_status fmap_plan_window_table(fmap_plan_t* p, const float* w, int32_t n_points) {
+  set_error("");
+  if (!p) return arg_fail("plan is NULL");
+  if (p->grid.window != FMAP_TABLE) return arg_fail("the plan's grid is not an FMAP_TABLE grid");
+  if (!w || n_points < 2 || n_points > kTabMax) return arg_fail("need 2..1024 window samples");
+  for (int32_t k = 0; k < n_points; ++k)
+    if (!std::isfinite(w[k])) return arg_fail("window samples must be finite");
+  if (p->last_stream) FMAP_CUDA(cudaStreamSynchronize(p->last_stream));
+  // (w_k, w_{k+1} - w_k) per sample interval, (w_last, 0), then the zero sentinel
+  std::vector<float2> tab((size_t)n_points + 1);
+  for (int32_t k = 0; k < n_points; ++k)
+    tab[k] = make_float2(w[k], k + 1 < n_points ? w[k + 1] - w[k] : 0.0f);
+  tab[n_points] = make_float2(0.0f, 0.0f);
+  FMAP_CUDA(cudaMemcpy(p->ws.wtab, tab.data(), sizeof(float2) * tab.size(), cudaMemcpyHostToDevice));
+  p->n_tab = n_points;
+  return FMAP_OK;
 }
 
 fmap_status fmap_marginalise(fmap_plan_t* p, const float* d_2F, const uint8_t* d_valid,

@@ -395,6 +395,10 @@ fmap_status fmap_batch_plan(fmap_batch_t** out, const fmap_batch_item* items, in
   std::vector<size_t> foot(n_items, 0);
   for (int32_t i = 0; i < n_items; ++i) {
     const fmap_batch_item& it = items[i];
+    if (it.grid.window == FMAP_TABLE) {
+      batch_free(B);
+      return batch_fail("instance " + std::to_string(i) + ": table windows are not batched");
+    }
     if (it.atoms.n_sft < 0 || it.atoms.n_templates < 0 ||
         (it.atoms.n_sft > 0 && (!it.atoms.t || !it.atoms.antenna ||
                                 (it.atoms.n_templates > 0 && !it.atoms.fafb)))) {

@@ -165,6 +165,25 @@ __device__ __forceinline__ FF gap_decay(int32_t gap, int32_t t_sft, float inv_ts
   return ff_of(exp(-(double)gap * inv_s));
 }
 
+// Generic window w(x) from its table (entries k = 0..n-1: (w_k, w_{k+1} -
+// w_k), then the sentinel (0, 0)): linear between samples, 0 past the last.
+// u = x (n - 1) / X is the position in sample units (u >= 0).
+__device__ __forceinline__ float tab_weight(float u, const float2* tab, int32_t n) {
+  const int32_t k = min(__float2int_rz(u), n);   // u beyond the table: the sentinel
+  const float2 e = tab[k];
+  return fmaf(u - (float)k, e.y, e.x);
+}
+__device__ __forceinline__ double tab_weight64(double u, const float2* tab, int32_t n) {
+  const double fk = floor(u);
+  const int32_t k = fk >= (double)n ? n : (int32_t)fk;
+  const float2 e = tab[k];
+  return (double)e.x + (u - (double)k) * (double)e.y;
+}
+// Sample units per second of (t - t0) for a tau: (n - 1) / (X tau), X = c / 8.
+__host__ __device__ __forceinline__ double tab_scale(int32_t n, int32_t cut8, int64_t tau) {
+  return (double)(n - 1) * 8.0 / ((double)cut8 * (double)tau);
+}
+
 // Compensated recurrence E <- x + r E (Horner's rule with error-free
 // transformations, after Graillat, Langlois and Louvet's compensated Horner
 // scheme): E = h + c with h the plain FP32 recurrence and c carrying its

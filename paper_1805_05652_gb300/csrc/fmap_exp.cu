@@ -380,10 +380,13 @@ int64_t exp_tiles(const fmap_grid& g) {
   return (int64_t)g.n_t0 * ((g.n_tau + kExpCells - 1) / kExpCells);
 }
 
-template <typename Acc, int TC>
+// TAB: the weights come from the window table wtab (n_tab samples; FMAP_TABLE
+// grids) instead of the exponential.
+template <typename Acc, int TC, bool TAB>
 __global__ void __launch_bounds__(kExpCells)
 k_exp_plain(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base,
-            int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax,
+            int32_t n_sft, fmap_grid g, const float2* __restrict__ wtab, int32_t n_tab,
+            const int64_t* __restrict__ ax,
             const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
             const Coef* __restrict__ coef, int32_t shared_antenna, const float* __restrict__ fafb,
             int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
@@ -414,6 +417,8 @@ k_exp_plain(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_bas
   if (jmax > i0) t0rel = (int32_t)(ax[m] - *t_base);
   const double tau = (double)ax[g.n_t0 + (in_grid ? nn : 0)];
   const float c2 = (float)(-1.4426950408889634 / tau);
+  const double su64 = TAB ? tab_scale(n_tab, exp_cut8_of(g), ax[g.n_t0 + (in_grid ? nn : 0)]) : 0.0;
+  const float su = (float)su64;
   Acc acc[NCOL];
 #pragma unroll
   for (int q = 0; q < NCOL; ++q) acc[q] = Acc(0);
@@ -436,7 +441,12 @@ k_exp_plain(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_bas
     for (int kk = 0; kk < kend; ++kk) {
       const int32_t d = srel[kk] - t0rel;
       Acc w;
-      if constexpr (std::is_same<Acc, double>::value) {
+      if constexpr (TAB) {
+        if constexpr (std::is_same<Acc, double>::value)
+          w = (k0 + kk < jc) ? tab_weight64((double)d * su64, wtab, n_tab) : 0.0;
+        else
+          w = (k0 + kk < jc) ? tab_weight((float)d * su, wtab, n_tab) : 0.0f;
+      } else if constexpr (std::is_same<Acc, double>::value) {
         w = (k0 + kk < jc) ? exp(-(double)d / tau) : 0.0;
       } else {
         w = (k0 + kk < jc) ? exp2f((float)d * c2) : 0.0f;
@@ -475,18 +485,17 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
   const int64_t tiles = exp_tiles(g);
   *tiles_used = tiles;
   if (tiles == 0 || p->n_templates == 0) return cudaSuccess;
+  const bool tab = g.window == FMAP_TABLE;
+  auto run = [&](auto kern, int tc) {
+    dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + tc - 1) / tc));
+    kern<<<grid, kExpCells, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.wtab, p->n_tab,
+                                    p->ws.ax, p->ws.i0, p->ws.jend, p->ws.coef, a->shared_antenna,
+                                    a->fafb, p->n_templates, d_2F, p->ws.partials, p->part_stride);
+  };
   if (p->precision == FMAP_FP64) {
-    constexpr int TC = 8;
-    dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + TC - 1) / TC));
-    k_exp_plain<double, TC><<<grid, kExpCells, 0, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.ax, p->ws.i0, p->ws.jend, p->ws.coef,
-        a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->part_stride);
+    if (tab) run(k_exp_plain<double, 8, true>, 8); else run(k_exp_plain<double, 8, false>, 8);
   } else {
-    constexpr int TC = 16;
-    dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + TC - 1) / TC));
-    k_exp_plain<float, TC><<<grid, kExpCells, 0, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.ax, p->ws.i0, p->ws.jend, p->ws.coef,
-        a->shared_antenna, a->fafb, p->n_templates, d_2F, p->ws.partials, p->part_stride);
+    if (tab) run(k_exp_plain<float, 16, true>, 16); else run(k_exp_plain<float, 16, false>, 16);
   }
   p->launches += 1;
   return cudaGetLastError();

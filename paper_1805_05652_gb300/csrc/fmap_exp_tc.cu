@@ -168,6 +168,8 @@ struct Params {
   const int64_t* t_base;
   fmap_grid g;
   const int64_t* ax;   // grid values: t0_m, then tau_n
+  const float2* wtab;  // FMAP_TABLE grids: the window table (n_tab samples + sentinel)
+  int32_t n_tab;
   const int32_t* i0tab;
   const int32_t* jend;
   const Coef* coef;
@@ -182,7 +184,9 @@ struct Params {
   uint32_t* err;
 };
 
-template <bool BF16>
+// TAB: weights from the window table (FMAP_TABLE grids) instead of exp2; the
+// table sits in shared memory after the staged relative times.
+template <bool BF16, bool TAB>
 __global__ void __launch_bounds__(kThreads, 1)
 k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
          const Params p) {
@@ -193,6 +197,7 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* s_dt = (float*)(smem + (size_t)kStages * 2 * p.n_cols * 128);
+  float2* s_tab = (float2*)(s_dt + kDtCap);   // TAB only
   __shared__ uint64_t bar_full_b[kStages], bar_full_a[kStages], bar_empty[kStages], bar_acc;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
@@ -310,6 +315,12 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
     if (jmax > i0) t0rel = (int32_t)(p.ax[m] - *p.t_base);
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int gtid = threadIdx.x;          // 0 .. 255 over the generator warps
+    float su = 0.0f;                       // TAB: table samples per second of t - t0
+    if constexpr (TAB) {
+      su = (float)tab_scale(p.n_tab, exp_cut8_of(g), p.ax[g.n_t0 + (in_grid ? n : 0)]);
+      for (int k = gtid; k <= p.n_tab; k += kGenWarps * 32) s_tab[k] = p.wtab[k];
+      asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory");
+    }
     bool ok_run = true;
     for (int it = 0; it < n_kt; ++it) {
       const int s = it % kStages;
@@ -347,10 +358,17 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
 #pragma unroll
         for (int v = 0; v < HALF / 4; ++v) {
           const float4 d4 = dp[v];
-          w[4 * v] = ex2(c2 * d4.x);
-          w[4 * v + 1] = ex2(c2 * d4.y);
-          w[4 * v + 2] = ex2(c2 * d4.z);
-          w[4 * v + 3] = ex2(c2 * d4.w);
+          if constexpr (TAB) {
+            w[4 * v] = tab_weight(su * d4.x, s_tab, p.n_tab);
+            w[4 * v + 1] = tab_weight(su * d4.y, s_tab, p.n_tab);
+            w[4 * v + 2] = tab_weight(su * d4.z, s_tab, p.n_tab);
+            w[4 * v + 3] = tab_weight(su * d4.w, s_tab, p.n_tab);
+          } else {
+            w[4 * v] = ex2(c2 * d4.x);
+            w[4 * v + 1] = ex2(c2 * d4.y);
+            w[4 * v + 2] = ex2(c2 * d4.z);
+            w[4 * v + 3] = ex2(c2 * d4.w);
+          }
         }
         if (!__all_sync(0xffffffffu, cnt >= HALF)) {
 #pragma unroll
@@ -554,6 +572,8 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   prm.rel_t = p->ws.rel_t;
   prm.t_base = p->ws.t_base;
   prm.ax = p->ws.ax;
+  prm.wtab = p->ws.wtab;
+  prm.n_tab = p->n_tab;
   prm.g = g;
   prm.i0tab = p->ws.i0;
   prm.jend = p->ws.jend;
@@ -571,20 +591,23 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   prm.err = p->ws.dev_err;
   // shared memory: 3 stages x (hi + lo) x N rows x 128 B; at least enough to
   // keep the resident CTAs within the 512 TMEM columns of an SM
-  size_t smem = (size_t)tc::kStages * 2 * N * 128 + sizeof(float) * tc::kDtCap + 1024;
+  const bool tab = g.window == FMAP_TABLE;
+  size_t smem = (size_t)tc::kStages * 2 * N * 128 + sizeof(float) * tc::kDtCap + 1024 +
+                (tab ? sizeof(float2) * (kTabMax + 1) : 0);
   const size_t min_smem = tcols > 256 ? 120 * 1024 : 80 * 1024;
   smem = std::max(smem, min_smem);
   const int chunks = (ncols + N - 1) / N;
   dim3 grid((unsigned)tiles, (unsigned)chunks);
   const CUtensorMap* mh = (const CUtensorMap*)p->tmap_hi;
   const CUtensorMap* ml = (const CUtensorMap*)p->tmap_lo;
+  auto run = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, tc::kThreads, smem, s>>>(*mh, *ml, prm);
+  };
   if (bf16) {
-    cudaFuncSetAttribute(tc::k_exp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tc::k_exp_tc<true><<<grid, tc::kThreads, smem, s>>>(*mh, *ml, prm);
+    if (tab) run(tc::k_exp_tc<true, true>); else run(tc::k_exp_tc<true, false>);
   } else {
-    cudaFuncSetAttribute(tc::k_exp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    tc::k_exp_tc<false><<<grid, tc::kThreads, smem, s>>>(*mh, *ml, prm);
+    if (tab) run(tc::k_exp_tc<false, true>); else run(tc::k_exp_tc<false, false>);
   }
   p->launches += 1;
   return cudaGetLastError();

@@ -144,7 +144,7 @@ k_flag_write(const Coef* __restrict__ coef, int64_t n_entries,
 // Block (b, y): entries [b n / G, (b + 1) n / G), templates y*128 + tid.
 __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
         int32_t shared_antenna, const int32_t* __restrict__ rel_t,
-        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax,
+        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab,
         const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
@@ -175,7 +175,12 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
       for (int32_t u = threadIdx.x; u < kFixWeights; u += kFixThreads) {
         const int32_t a = a0 + u;
         double w = 0.0;
-        if (a < j) w = (g.window == FMAP_RECT) ? 1.0 : exp(-(double)((int64_t)rel_t[a] - t0rel) / tau);
+        if (a < j) {
+          const double d = (double)((int64_t)rel_t[a] - t0rel);
+          w = g.window == FMAP_RECT ? 1.0
+              : g.window == FMAP_TABLE ? tab_weight64(d * tab_scale(n_tab, exp_cut8_of(g), ax[g.n_t0 + nn]), wtab, n_tab)
+                                       : exp(-d / tau);
+        }
         sw[u] = w;
       }
       __syncthreads();
@@ -216,7 +221,7 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
 __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ list,
         const int32_t* __restrict__ n_flag, int32_t G, int32_t shared_antenna,
         const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n_sft,
-        fmap_grid g, const int64_t* __restrict__ ax, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+        fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
         int32_t b, int32_t tq) {
@@ -241,7 +246,9 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
     // Exponential weights along the window by products of the per-gap
     // decays (one exp for the first atom and one for the one-SFT decay;
     // relative error ~(j - i0) ulp), the FP64 pipe being 1/64 of FP32 rate.
-    const bool ex = g.window != FMAP_RECT;
+    const bool ex = g.window == FMAP_EXP;
+    const bool tb_win = g.window == FMAP_TABLE;
+    const double su = tb_win ? tab_scale(n_tab, exp_cut8_of(g), ax[g.n_t0 + nn]) : 0.0;
     double w = 1.0, rho1 = 0.0;
     if (ex && j > i0) {
       w = exp(-(double)((int64_t)rel_t[i0] - t0rel) * inv_tau);
@@ -252,6 +259,7 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
         const int32_t gap = rel_t[a] - rel_t[a - 1];
         w *= gap == g.t_sft ? rho1 : (gap == 2 * g.t_sft ? rho1 * rho1 : exp(-(double)gap * inv_tau));
       }
+      if (tb_win) w = tab_weight64((double)((int64_t)rel_t[a] - t0rel) * su, wtab, n_tab);
       const double w2 = w * w;
       A += w2 * (double)ant[a];
       B += w2 * (double)ant[n_sft + a];
@@ -277,12 +285,12 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
 __global__ void __launch_bounds__(kFixThreads)
 k_fixup_cells(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
               int32_t shared_antenna, const int32_t* __restrict__ rel_t,
-              const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax,
+              const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab,
               const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
               const float* __restrict__ antenna, const float* __restrict__ fafb,
               int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
               int64_t stride, int64_t slot0) {
-  fixup_cells_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, i0tab, jend, antenna,
+  fixup_cells_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, wtab, n_tab, i0tab, jend, antenna,
                    fafb, n_templates, map, parts, stride, slot0, blockIdx.x, blockIdx.y);
 }
 
@@ -295,11 +303,11 @@ int64_t fixup_blocks_y(int32_t n_templates) {
 __global__ void __launch_bounds__(kFixThreads)
 k_fixup(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
         int32_t shared_antenna, const int32_t* __restrict__ rel_t,
-        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax,
+        const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab,
         const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0) {
-  fixup_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, i0tab, jend, antenna, fafb, n_templates, map, parts, stride, slot0, blockIdx, gridDim);
+  fixup_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, wtab, n_tab, i0tab, jend, antenna, fafb, n_templates, map, parts, stride, slot0, blockIdx, gridDim);
 }
 
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
@@ -317,13 +325,15 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
   if (p->n_templates < kFixCellModeT)
     k_fixup_cells<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
                                                a->shared_antenna, p->ws.rel_t, p->ws.t_base,
-                                               p->n_sft, p->grid, p->ws.ax, p->ws.i0, p->ws.jend,
+                                               p->n_sft, p->grid, p->ws.ax, p->ws.wtab, p->n_tab,
+                                               p->ws.i0, p->ws.jend,
                                                a->antenna, a->fafb, p->n_templates, d_2F,
                                                p->ws.partials, p->part_stride, p->n_tiles);
   else
     k_fixup<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
                                          a->shared_antenna, p->ws.rel_t, p->ws.t_base, p->n_sft,
-                                         p->grid, p->ws.ax, p->ws.i0, p->ws.jend, a->antenna, a->fafb,
+                                         p->grid, p->ws.ax, p->ws.wtab, p->n_tab, p->ws.i0, p->ws.jend,
+                                         a->antenna, a->fafb,
                                          p->n_templates, d_2F, p->ws.partials, p->part_stride,
                                          p->n_tiles);
   p->launches += 4;
@@ -362,11 +372,11 @@ __global__ void __launch_bounds__(kFixThreads) kb_fixup(const BItem* __restrict_
       const int32_t b = sg * kFixSlotsPerUnit + q;
       if (it.T < kFixCellModeT)
         fixup_cells_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base,
-                         it.n_sft, it.g, it.ax, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
+                         it.n_sft, it.g, it.ax, nullptr, 0, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
                          it.partials, it.part_stride, it.n_tiles, b, y);
       else
         fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft,
-                   it.g, it.ax, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,
+                   it.g, it.ax, nullptr, 0, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,
                    it.part_stride, it.n_tiles, make_uint3((unsigned)b, (unsigned)y, 0),
                    dim3((unsigned)kFixSlots, (unsigned)((it.T + kFixThreads - 1) / kFixThreads)));
       __syncthreads();   // the bodies' shared scratch is reused by the next slot

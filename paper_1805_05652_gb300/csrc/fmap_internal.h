@@ -58,6 +58,8 @@ __host__ __device__ inline int32_t exp_cut8_of(const fmap_grid& g) {
 __host__ __device__ inline int64_t window_len(const fmap_grid& g, int64_t tau) {
   return g.window == FMAP_RECT ? tau : (int64_t)exp_cut8_of(g) * tau / 8;
 }
+// Largest window table (samples) of FMAP_TABLE grids.
+constexpr int kTabMax = 1024;
 // Entries per count of the marked-entry compaction (1024 threads x 8).
 constexpr int kFlagUnit = 8192;
 // Threads of the exponential-window scans.  Thread t of a scan owns the atoms
@@ -112,6 +114,7 @@ struct Workspace {
   float4* perm_ant = nullptr;    // [T_ant][.] (a2, b2, ab, gap to the next atom as int bits; -1 last)
   float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
   TauTab* tauc = nullptr;        // [n_tau] per-tau decay constants
+  float2* wtab = nullptr;        // table windows: [kTabMax + 1] (w_k, w_{k+1} - w_k), then (0, 0)
   int64_t* ax = nullptr;         // [n_t0 + n_tau] the grid: t0_m values, then tau_n values
   // exp
   float2* esuf = nullptr;        // [tau_chunk][3][N+1] float-float decayed suffix sums
@@ -145,6 +148,7 @@ struct fmap_plan_s {
   // Eq. Fmn, written to ws.ax by each run's prep step); host copy of the axes
   bool explicit_axes = false;
   std::vector<int64_t> ax_host;
+  int32_t n_tab = 0;             // table windows: samples set by fmap_plan_window_table
   // TMA descriptors (CUtensorMap, 128 bytes each) of the split X operands
   alignas(64) unsigned char tmap_hi[128] = {};
   alignas(64) unsigned char tmap_lo[128] = {};
@@ -172,6 +176,7 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
                         int64_t* tiles_used, cudaEvent_t mark);
 cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
 cudaError_t launch_exp_perm(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
+cudaError_t launch_table_antenna(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
 cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,
                              int64_t* tiles_used);
 cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaStream_t s,

@@ -350,6 +350,11 @@ fmap_status fmap_submit(fmap_server_t* s, const fmap_grid* grid, const fmap_atom
     set_error("bad atoms");
     return FMAP_ERR_ARG;
   }
+  if (grid->window == FMAP_TABLE) {
+    delete r;
+    set_error("table windows are not served");
+    return FMAP_ERR_ARG;
+  }
   const fmap_precision prec = grid->window == FMAP_RECT ? s->cfg.rect_precision : s->cfg.exp_precision;
   const uint32_t pflags = r->shared ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA;
   fmap_status st = plan_footprint(grid, r->n_sft, r->T, prec, pflags, &r->ws_bytes);

@@ -1,0 +1,100 @@
+// Generic window functions (FMAP_TABLE grids).
+//
+// The paper's kernels take the rectangular and exponential windows; its
+// method is the same for any amplitude envelope w of the transient: the atoms
+// of a window enter Fa, Fb with the weight w((t - t0) / tau) and A, B, C with
+// w^2.  Here w is a table of samples on [0, X], X = exp_cut8 / 8 (linear
+// between samples, 0 past X), over the exponential window's support.
+//
+// The data sums go through the same contraction kernels as the exponential
+// window (W generated from the table instead of exp2).  The antenna sums
+// have no recurrence for a generic w, so this file sums them directly over
+// each window: one block per (t0 row, 128 tau cells, antenna set), the
+// block's atoms staged in shared memory, every cell accumulating its window
+// in float-float with exact products (the FP32 weights act as a slightly
+// perturbed window, the same for A, B and C; the sums themselves carry
+// ~2^-44 relative error, enough for D = AB - C^2 up to AB/D = 100).
+#include <math.h>
+
+#include "fmap_device.cuh"
+
+namespace fmap {
+
+constexpr int kTabCells = 128;   // tau cells of a block (one t0 row)
+constexpr int kTabKC = 64;       // atoms staged per round
+
+// S += a b, the product taken exactly (FMA TwoProd) into the float-float sum.
+__device__ __forceinline__ void ff_add_prod(FF& S, float a, float b) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  const FF s = two_sum(S.h, p);
+  S = fast_two_sum(s.h, s.l + (pe + S.l));
+}
+
+__global__ void __launch_bounds__(kTabCells)
+k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
+                fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab,
+                int32_t n_tab, const float* __restrict__ antenna,
+                const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
+                Coef* __restrict__ coef) {
+  __shared__ float s_t[kTabKC];
+  __shared__ float s_a[3][kTabKC];
+  __shared__ float2 s_tab[kTabMax + 1];
+  __shared__ int32_t s_jmax;
+  const int tid = threadIdx.x;
+  const int32_t nblk = (g.n_tau + kTabCells - 1) / kTabCells;
+  const int32_t m = (int32_t)(blockIdx.x / nblk);
+  const int32_t nn = (int32_t)(blockIdx.x - m * nblk) * kTabCells + tid;
+  const int ta = blockIdx.y;
+  const bool in_grid = nn < g.n_tau;
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const int64_t cell = (int64_t)m * g.n_tau + (in_grid ? nn : 0);
+  for (int k = tid; k <= n_tab; k += kTabCells) s_tab[k] = wtab[k];
+  const int32_t i0 = i0tab[m];
+  const int32_t jc = in_grid ? jend[cell] : i0;
+  if (tid == 0) s_jmax = i0;
+  __syncthreads();
+  const int32_t jw = __reduce_max_sync(0xffffffffu, (unsigned)jc);
+  if ((tid & 31) == 0) atomicMax(&s_jmax, jw);
+  __syncthreads();
+  const int32_t jmax = s_jmax;
+  const int64_t tb = n > 0 ? *t_base : 0;
+  const int64_t t0rel = ax[m] - tb;
+  const float su =
+      in_grid ? (float)tab_scale(n_tab, exp_cut8_of(g), ax[g.n_t0 + nn]) : 0.0f;
+  const float* ant = antenna + (int64_t)ta * 3 * n;
+  FF S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int32_t k0 = i0; k0 < jmax; k0 += kTabKC) {
+    __syncthreads();
+    for (int e = tid; e < kTabKC; e += kTabCells) {
+      const int32_t a = k0 + e;
+      const bool in = a < jmax;
+      s_t[e] = in ? (float)((int64_t)rel_t[a] - t0rel) : 0.0f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) s_a[c][e] = in ? ant[(int64_t)c * n + a] : 0.0f;
+    }
+    __syncthreads();
+    const int kend = min(kTabKC, jc - k0);   // this cell's atoms in the round
+    for (int kk = 0; kk < kend; ++kk) {
+      const float w = tab_weight(s_t[kk] * su, s_tab, n_tab);
+      const float w2 = w * w;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ff_add_prod(S[c], w2, s_a[c][kk]);
+    }
+  }
+  if (in_grid) coef[(int64_t)ta * cells + cell] = make_coef_ff(S[0], S[1], S[2], jc - i0);
+}
+
+cudaError_t launch_table_antenna(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
+  const fmap_grid& g = p->grid;
+  if ((int64_t)g.n_t0 * g.n_tau == 0) return cudaSuccess;
+  const int n_ant = a->shared_antenna ? 1 : p->n_templates;
+  const int64_t blocks = (int64_t)g.n_t0 * ((g.n_tau + kTabCells - 1) / kTabCells);
+  k_table_antenna<<<dim3((unsigned)blocks, (unsigned)n_ant), kTabCells, 0, s>>>(
+      p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.ax, p->ws.wtab, p->n_tab, a->antenna,
+      p->ws.i0, p->ws.jend, p->ws.coef);
+  p->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace fmap

@@ -19,6 +19,7 @@ from .atoms import (  # noqa: F401
     OMEGA_SID,
     RECT,
     EXP,
+    TABLE,
     BASE_SEED,
     Grid,
     Injection,

@@ -46,6 +46,7 @@ T_SFT = 1800
 OMEGA_SID = 2.0 * math.pi / 86164.0
 RECT = 0
 EXP = 1
+TABLE = 2   # generic window function given by samples
 BASE_SEED = 20180515
 
 
@@ -93,6 +94,8 @@ class Grid:
     # values replacing t0_min + m dt0 and tau_min + n dtau
     t0_values: tuple | None = None
     tau_values: tuple | None = None
+    # TABLE windows: samples of w on [0, exp_cut8 / 8] (x = (t - t0) / tau)
+    window_table: tuple | None = None
 
     def t0(self) -> np.ndarray:
         if self.t0_values is not None:
@@ -115,7 +118,7 @@ class Grid:
     def with_window(self, window: int) -> "Grid":
         return Grid(self.t0_min, self.dt0, self.n_t0, self.tau_min, self.dtau,
                     self.n_tau, window, self.t_sft, self.exp_cut8, self.t0_values,
-                    self.tau_values)
+                    self.tau_values, self.window_table)
 
     def window_len(self, tau):
         """L(tau) in seconds: tau (rect) or floor(exp_cut8 tau / 8) (exp)."""
@@ -126,6 +129,10 @@ class Grid:
     def as_tuple(self):
         base = (self.t0_min, self.dt0, self.n_t0, self.tau_min, self.dtau,
                 self.n_tau, self.t_sft, self.window, self.exp_cut8)
+        if self.window_table is not None:
+            axes = ((tuple(int(v) for v in self.t0_values), tuple(int(v) for v in self.tau_values))
+                    if self.has_axes else (None, None))
+            return base + axes + (tuple(float(v) for v in self.window_table),)
         if self.has_axes:
             return base + (tuple(int(v) for v in self.t0_values),
                            tuple(int(v) for v in self.tau_values))

@@ -177,6 +177,69 @@ def test_explicit_axes_checks_count_and_reset():
     plan.close()
 
 
+def _table_instance(seed, shared=True, cut8=0, n_points=64):
+    """A generic window: a smooth bump times a decay, sampled on [0, X] (rising
+    then falling, with a kink), on a grid spanning several tiles."""
+    X = (cut8 or 24) / 8.0
+    x = np.linspace(0.0, X, n_points)
+    w = (np.sin(np.pi * np.minimum(x / 0.4, 1.0) / 2) ** 2) * np.exp(-0.7 * x) + 0.05
+    grid = Grid(-2500, 1000, 29, 900, 1300, 300, synth.TABLE, T_SFT, cut8, None, None,
+                tuple(float(v) for v in w.astype(np.float32)))
+    return synth.make_instance(seed, n_det=2, presence=0.9, n_merged=400, n_templates=6,
+                               grid=grid, shared_antenna=shared,
+                               injections=[(1, EXP, 20000, 60000, 200.0)])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
+def test_table_window(prec):
+    """Generic (table) windows: every precision against the oracle's
+    definition (linear interpolation of the same samples)."""
+    try:
+        _parity(_table_instance(81), prec)
+    except fm.FmapError as e:
+        if e.status == fm.FMAP_ERR_UNSUPPORTED:
+            pytest.skip(f"{prec} not built")
+        raise
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_table_window_per_template_antenna_and_cut(prec):
+    """Table windows with per-template antenna rows and a 2 tau support."""
+    try:
+        _parity(_table_instance(82, shared=False, cut8=16, n_points=1024), prec)
+    except fm.FmapError as e:
+        if e.status == fm.FMAP_ERR_UNSUPPORTED:
+            pytest.skip(f"{prec} not built")
+        raise
+
+
+def test_table_window_api_checks():
+    """A table plan needs its samples before computing; samples are refused
+    for other windows and outside 2..1024."""
+    import torch
+
+    inst = _table_instance(83)
+    g = inst.grid
+    bare = Grid(g.t0_min, g.dt0, g.n_t0, g.tau_min, g.dtau, g.n_tau, synth.TABLE)
+    plan = fm.Plan(bare, inst.n_sft, inst.n_templates, "fp64")
+    dev = torch.device("cuda", 0)
+    args = (torch.from_numpy(inst.t).to(dev), torch.from_numpy(inst.antenna).to(dev),
+            torch.from_numpy(inst.fafb).to(dev))
+    with pytest.raises(fm.FmapError) as e:
+        plan.compute(*args)
+    assert e.value.status == fm.FMAP_ERR_ARG
+    for bad in (np.ones(1), np.ones(1025), np.array([1.0, np.nan])):
+        with pytest.raises(fm.FmapError) as e:
+            fm.binding.fmap_plan_window_table(plan.handle, bad)
+        assert e.value.status == fm.FMAP_ERR_ARG
+    plan.close()
+    ex = fm.Plan(Grid(0, T_SFT, 4, T_SFT, T_SFT, 4, EXP), inst.n_sft, 1, "fp64")
+    with pytest.raises(fm.FmapError) as e:
+        fm.binding.fmap_plan_window_table(ex.handle, np.ones(4))
+    assert e.value.status == fm.FMAP_ERR_ARG
+    ex.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "rec"])
 def test_exp_per_template_antenna(prec):
     grid = Grid(0, T_SFT, 20, T_SFT, T_SFT, 140, EXP)

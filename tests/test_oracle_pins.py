@@ -473,3 +473,78 @@ def test_explicit_axes_brute_force(window, cut8):
     m_f, v_f, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, grid.as_tuple(), mode="fast")
     assert np.array_equal(v_d, v_f)
     assert np.allclose(m_d, m_f, rtol=1e-10, atol=1e-10)
+
+
+def _table_grid(table, cut8=0, window=synth.TABLE):
+    return Grid(-2000, 1700, 30, 900, 2300, 25, window, T_SFT, cut8, None, None,
+                tuple(float(v) for v in table))
+
+
+@pytest.mark.parametrize("mode", ["direct", "fast"])
+def test_table_window_constant_is_rect(mode):
+    """A table window w = 1 on [0, 1] (cut 8 eighths: support [t0, t0 + tau])
+    is the rectangular window of Eq. winrect: identical sums and maps."""
+    inst = synth.make_instance(21, n_det=2, presence=0.8, n_merged=120, n_templates=2,
+                               grid=Grid(0, 1, 1, 1, 1, 1, RECT), dtype=np.float64)
+    rect = Grid(-2000, 1700, 30, 900, 2300, 25, RECT)
+    tab = _table_grid(np.ones(7), cut8=8)
+    s_r, c_r = oracle.sums(inst.t, inst.antenna, inst.fafb, rect.as_tuple())
+    s_t, c_t = oracle.sums(inst.t, inst.antenna, inst.fafb, tab.as_tuple())
+    assert np.array_equal(c_r, c_t) and np.array_equal(s_r, s_t)
+    m_r, v_r, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, rect.as_tuple(), mode=mode)
+    m_t, v_t, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, tab.as_tuple(), mode=mode)
+    assert np.array_equal(v_r, v_t) and np.array_equal(m_r, m_t)
+
+
+def test_table_window_sampled_exponential_within_interpolation_bound():
+    """Samples of e^{-x} on [0, 3] joined linearly reproduce the exponential
+    window of Eq. winexp to within the linear-interpolation bound h^2/8 max|w''|
+    (h the sample step) on every weight, plus the float32 rounding of the
+    samples: |S_table - S_exp| <= (bound) sum |x| per cell and row."""
+    n = 301
+    h = 3.0 / (n - 1)
+    w = np.exp(-np.linspace(0.0, 3.0, n))
+    inst = synth.make_instance(22, n_det=2, presence=0.85, n_merged=150, n_templates=2,
+                               grid=Grid(0, 1, 1, 1, 1, 1, EXP), dtype=np.float64)
+    ex = Grid(-2000, 1700, 30, 900, 2300, 25, EXP)
+    tab = _table_grid(w)
+    s_e, c_e = oracle.sums(inst.t, inst.antenna, inst.fafb, ex.as_tuple())
+    s_t, c_t = oracle.sums(inst.t, inst.antenna, inst.fafb, tab.as_tuple())
+    assert np.array_equal(c_e, c_t)
+    dw = h * h / 8.0 + 1.2e-7                       # per weight (w <= 1, w'' <= 1)
+    absx = np.abs(np.concatenate([inst.antenna, inst.fafb.reshape(-1, inst.n_sft)]))
+    # sum of |x| over each cell's window, by the oracle itself on |x| rows with w = 1
+    flat = Grid(-2000, 1700, 30, 900, 2300, 25, synth.TABLE, T_SFT, 0, None, None, (1.0, 1.0))
+    s_abs, _ = oracle.sums(inst.t, absx[:3], absx[3:].reshape(2, 4, -1), flat.as_tuple())
+    bound = np.concatenate([2 * dw * s_abs[..., :3], dw * s_abs[..., 3:]], axis=-1) + 1e-12
+    assert np.all(np.abs(s_t - s_e) <= bound)
+
+
+@pytest.mark.parametrize("cut8", [0, 12])
+def test_table_window_brute_force(cut8):
+    """Window sums of a random table window against a plain loop over the
+    atoms with numpy's linear interpolation of the samples (w for Fa, Fb;
+    w^2 for A, B, C; 0 past the support)."""
+    rng = np.random.default_rng(3)
+    table = rng.uniform(0.0, 2.0, size=17).astype(np.float32)
+    grid = Grid(-2500, 1300, 20, 700, 1900, 18, synth.TABLE, T_SFT, cut8, None, None,
+                tuple(float(v) for v in table))
+    inst = synth.make_instance(23, n_det=1, presence=0.8, n_merged=40, n_templates=2,
+                               grid=Grid(0, 1, 1, 1, 1, 1, EXP), dtype=np.float64)
+    s, cnt = oracle.sums(inst.t, inst.antenna, inst.fafb, grid.as_tuple())
+    X = (cut8 or 24) / 8.0
+    xs = np.linspace(0.0, X, len(table))
+    for mi, t0 in enumerate(grid.t0()):
+        for ni, tau in enumerate(grid.tau()):
+            ref = np.zeros((2, 7))
+            c = 0
+            for a, t in enumerate(inst.t):
+                if t < t0 or 8 * (t + T_SFT - t0) > (cut8 or 24) * tau:
+                    continue
+                w = float(np.interp((t - t0) / tau, xs, table.astype(np.float64)))
+                c += 1
+                for j in range(2):
+                    ref[j, :3] += w * w * inst.antenna[:, a]
+                    ref[j, 3:] += w * inst.fafb[j, :, a]
+            assert cnt[mi, ni] == c
+            assert np.allclose(s[:, mi, ni], ref, rtol=1e-10, atol=1e-12)
