@@ -105,6 +105,13 @@ def count_terms(grid, t):
     return int(c[c >= 2].sum()), int((c >= 2).sum())
 
 
+# DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
+# capture of the unchanged kernel on the workload (a 64-template cut of the
+# rect batch, scaled to its 1024 templates: the traffic grows with them).
+NCU_TRAFFIC = {("exp16", "bf16x3"): 32.0e6,
+               ("batch_rect", "fp64"): 1078.0e6 * 16}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -407,6 +414,11 @@ def main():
             roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "traffic": None, "kernel": "rect cells (phase 2)",
                     "peak_source": peak_src}
+        key = (args.workload, precision)
+        plain_workload = not (args.exp_cut8 or args.grid_axes or args.templates or args.window_table)
+        if plain_workload and key in NCU_TRAFFIC:
+            roof["traffic"] = NCU_TRAFFIC[key]
+            roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu, _, _ = cpu_baseline(inst)
@@ -535,6 +547,11 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
                 "frac": ach / peaks["hbm_gbs"], "traffic": None,
                 "kernel": "whole batch step (all phases; map bytes / step time)",
                 "peak_source": peak_src}
+        key = (args.workload, precision)
+        plain_workload = not (args.exp_cut8 or args.grid_axes or args.templates or args.window_table)
+        if plain_workload and key in NCU_TRAFFIC:
+            roof["traffic"] = NCU_TRAFFIC[key]
+            roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = uneven_cpu_baseline(fm, insts, counts)
