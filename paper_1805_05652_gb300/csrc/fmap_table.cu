@@ -11,9 +11,9 @@
 // have no recurrence for a generic w, so this file sums them directly over
 // each window: one block per (t0 row, 128 tau cells, antenna set), the
 // block's atoms staged in shared memory, every cell accumulating its window
-// in float-float with exact products (the FP32 weights act as a slightly
-// perturbed window, the same for A, B and C; the sums themselves carry
-// ~2^-44 relative error, enough for D = AB - C^2 up to AB/D = 100).
+// by cascaded (Sum2) summation with exact products (the FP32 weights act as a
+// slightly perturbed window, the same for A, B and C; the sums carry about
+// twice-working-precision accuracy, enough for D = AB - C^2 up to AB/D = 100).
 #include <math.h>
 
 #include "fmap_device.cuh"
@@ -23,13 +23,21 @@ namespace fmap {
 constexpr int kTabCells = 128;   // tau cells of a block (one t0 row)
 constexpr int kTabKC = 64;       // atoms staged per round
 
-// S += a b, the product taken exactly (FMA TwoProd) into the float-float sum.
+// S += a b in the cascaded form of Ogita, Rump and Oishi's Sum2 with an exact
+// product: S.h is the plain FP32 running sum, S.l collects the product's
+// FMA error and the TwoSum error of each addition (folded into S.h once, at
+// the end, by ff_fold); the result is as accurate as summing in twice the
+// working precision.
 __device__ __forceinline__ void ff_add_prod(FF& S, float a, float b) {
   const float p = a * b;
   const float pe = fmaf(a, b, -p);
-  const FF s = two_sum(S.h, p);
-  S = fast_two_sum(s.h, s.l + (pe + S.l));
+  const float s = S.h + p;
+  const float bb = s - S.h;
+  const float se = (S.h - (s - bb)) + (p - bb);
+  S.l += se + pe;
+  S.h = s;
 }
+__device__ __forceinline__ FF ff_fold(FF S) { return fast_two_sum(S.h, S.l); }
 
 __global__ void __launch_bounds__(kTabCells)
 k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
@@ -82,7 +90,8 @@ k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t
       for (int c = 0; c < 3; ++c) ff_add_prod(S[c], w2, s_a[c][kk]);
     }
   }
-  if (in_grid) coef[(int64_t)ta * cells + cell] = make_coef_ff(S[0], S[1], S[2], jc - i0);
+  if (in_grid)
+    coef[(int64_t)ta * cells + cell] = make_coef_ff(ff_fold(S[0]), ff_fold(S[1]), ff_fold(S[2]), jc - i0);
 }
 
 cudaError_t launch_table_antenna(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
