@@ -108,9 +108,7 @@ static int64_t units_of(const fmap_plan_s* p, const fmap_batch_item& it, int ph,
   const bool rect = g.window == FMAP_RECT;
   const bool work = cells > 0 && T > 0;
   switch (ph) {
-    case BP_PREP:
-      return (p->n_sft > 0 ? (rel_t_entries(p->n_sft) + 255) / 256 : 0) +
-             ((int64_t)g.n_t0 + g.n_tau + 255) / 256;
+    case BP_PREP: return p->n_sft > 0 ? (rel_t_entries(p->n_sft) + 255) / 256 : 0;
     case BP_INDEX: return cells > 0 ? (g.n_t0 + kIdxRowsPerUnit - 1) / kIdxRowsPerUnit : 0;
     case BP_EXP_PERM: {
       if (rect || cells == 0) return 0;
@@ -180,7 +178,7 @@ static BItem make_bitem(const fmap_plan_s* p, const fmap_batch_item& it, uint32_
   b.perm_ant = w.perm_ant;
   b.perm_x = w.perm_x;
   b.tauc = w.tauc;
-  b.ax = w.ax;
+  b.ax = nullptr;   // batches take uniform grids
   b.px = w.px;
   return b;
 }

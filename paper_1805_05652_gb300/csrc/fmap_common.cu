@@ -37,18 +37,6 @@ __global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc
   prep_body(t, n, n_alloc, rel_t, t_base, err, blockIdx, gridDim);
 }
 
-// The values of a uniform grid (Eq. Fmn): ax[m] = t0_min + m dt0 for
-// m < n_t0, then ax[n_t0 + n] = tau_min + n dtau; entries [e, e_end) by step.
-__device__ __forceinline__ void axes_body(const fmap_grid& g, int64_t* __restrict__ ax, int64_t e,
-                                          int64_t e_end, int64_t step) {
-  for (; e < e_end; e += step)
-    ax[e] = e < g.n_t0 ? g.t0_min + e * g.dt0 : g.tau_min + (e - g.n_t0) * g.dtau;
-}
-__global__ void k_axes(fmap_grid g, int64_t* __restrict__ ax) {
-  axes_body(g, ax, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)g.n_t0 + g.n_tau,
-            (int64_t)gridDim.x * blockDim.x);
-}
-
 // Window index tables: i0[m] = first atom with t >= t0_m; jend[m][n] = one
 // past the last atom whose SFT ends by t0_m + L_n (L = window_len(tau_n)),
 // clamped to >= i0[m], so the window holds atoms [i0, jend).  One block per
@@ -77,8 +65,7 @@ __device__ __forceinline__ void index_body(const int32_t* __restrict__ rel_t,
   __shared__ int32_t s_lo, s_hi;
   const int tid = threadIdx.x;
   const int64_t tb = n_sft > 0 ? *t_base : 0;
-  const int64_t t0rel = ax[m] - tb;
-  const int64_t* tau_v = ax + g.n_t0;
+  const int64_t t0rel = grid_t0(g, ax, m) - tb;
   if (tid == 0) {
     int32_t lo = 0, hi = n_sft;   // first atom with t >= t0
     while (lo < hi) {
@@ -86,7 +73,7 @@ __device__ __forceinline__ void index_body(const int32_t* __restrict__ rel_t,
       if ((int64_t)rel_t[mid] < t0rel) lo = mid + 1; else hi = mid;
     }
     s_lo = lo;
-    const int64_t lim = t0rel + window_len(g, tau_v[g.n_tau - 1]) - g.t_sft;
+    const int64_t lim = t0rel + window_len(g, grid_tau(g, ax, g.n_tau - 1)) - g.t_sft;
     s_hi = max(lo, upper_bound_i32(rel_t, lo, n_sft, lim));
     i0tab[m] = lo;
   }
@@ -98,7 +85,7 @@ __device__ __forceinline__ void index_body(const int32_t* __restrict__ rel_t,
   __syncthreads();
   int32_t* row = jend + (int64_t)m * g.n_tau;
   for (int32_t nn = tid; nn < g.n_tau; nn += kIdxThreads) {
-    const int64_t lim = t0rel + window_len(g, tau_v[nn]) - g.t_sft;
+    const int64_t lim = t0rel + window_len(g, grid_tau(g, ax, nn)) - g.t_sft;
     row[nn] = staged ? i0 + upper_bound_i32(s_t, 0, span, lim)
                      : upper_bound_i32(rel_t, i0, i0 + span, lim);
   }
@@ -114,12 +101,7 @@ k_index(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, i
 }
 
 cudaError_t launch_prep(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
-  const int64_t n_ax = (int64_t)p->grid.n_t0 + p->grid.n_tau;
-  if (!p->explicit_axes && n_ax > 0) {
-    k_axes<<<(unsigned)std::min<int64_t>((n_ax + 255) / 256, 1024), 256, 0, s>>>(p->grid, p->ws.ax);
-    p->launches += 1;
-  }
-  if (p->n_sft <= 0) return cudaGetLastError();
+  if (p->n_sft <= 0) return cudaSuccess;
   const int threads = 256;
   const int blocks = (int)std::min<int64_t>((p->n_sft + threads - 1) / threads, 4096);
   k_prep<<<blocks, threads, 0, s>>>(d_t, p->n_sft, rel_t_entries(p->n_sft), p->ws.rel_t,
@@ -133,7 +115,7 @@ cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
   const int64_t cells = (int64_t)p->grid.n_t0 * p->grid.n_tau;
   if (cells == 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>(p->grid.n_t0, (int64_t)p->n_sm * 8);
-  k_index<<<blocks, kIdxThreads, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, p->grid, p->ws.ax,
+  k_index<<<blocks, kIdxThreads, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, p->grid, plan_axes(p),
                                          p->ws.i0, p->ws.jend);
   p->launches += 1;
   return cudaGetLastError();
@@ -379,16 +361,9 @@ cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t*
 
 // ---- persistent multi-instance dispatchers (uneven batches) ----
 __global__ void __launch_bounds__(256) kb_prep(const BItem* __restrict__ items, BUnits u) {
-  // units [0, ru): relative times; then the uniform grid's axes
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    const int64_t ru = it.n_sft > 0 ? (it.n_alloc + 255) / 256 : 0;
-    if (k < ru) {
-      prep_body(it.t, it.n_sft, it.n_alloc, it.rel_t, it.t_base, it.dev_err,
-                make_uint3((unsigned)k, 0, 0), dim3((unsigned)ru));
-    } else {
-      const int64_t e0 = (k - ru) * 256;
-      axes_body(it.g, it.ax, e0 + threadIdx.x, min((int64_t)it.g.n_t0 + it.g.n_tau, e0 + 256), 256);
-    }
+    prep_body(it.t, it.n_sft, it.n_alloc, it.rel_t, it.t_base, it.dev_err,
+              make_uint3((unsigned)k, 0, 0), dim3((unsigned)((it.n_alloc + 255) / 256)));
   });
 }
 __global__ void __launch_bounds__(kIdxThreads) kb_index(const BItem* __restrict__ items, BUnits u) {

@@ -233,7 +233,7 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
   for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
     const int64_t cell = (int64_t)m * g.n_tau + ni;
     coef[(int64_t)ta * cells + cell] =
-        exp_cell_coef(rel_t, n, ax[m], tt->c2[1], tt->inv_tau, i0tab[m], jend[cell], tb, s_E);
+        exp_cell_coef(rel_t, n, grid_t0(g, ax, m), tt->c2[1], tt->inv_tau, i0tab[m], jend[cell], tb, s_E);
   }
 }
 
@@ -262,7 +262,7 @@ __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t,
   const int64_t n_copy = P * (int64_t)(n_ant + n_x);
   for (int64_t e = e_begin; e < e_end; e += e_step) {
     if (e >= n_copy) {   // entries past the copies: the per-tau constants
-      tau_tab_fill(g, ax[g.n_t0 + (e - n_copy)], tauc + (e - n_copy));
+      tau_tab_fill(g, grid_tau(g, ax, e - n_copy), tauc + (e - n_copy));
       continue;
     }
     const int64_t set = e / P, r = e - set * P;
@@ -305,7 +305,7 @@ cudaError_t launch_exp_perm(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
   const int64_t total = exp_copy_entries(p->n_sft, n_ant, n_x, p->grid.n_tau);
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
   k_exp_perm<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->n_sft, a->antenna, n_ant, a->fafb, n_x,
-                                    p->ws.perm_ant, p->ws.perm_x, p->grid, p->ws.ax, p->ws.tauc);
+                                    p->ws.perm_ant, p->ws.perm_x, p->grid, plan_axes(p), p->ws.tauc);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -327,7 +327,7 @@ __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __r
     const int32_t nl = (int32_t)(c - m * n_chunk);
     const int64_t nn = n_lo + nl;
     const int64_t cell = m * g.n_tau + nn;
-    coef[cell] = exp_cell_coef(rel_t, n, ax[m], tauc[nn].c2[1], tauc[nn].inv_tau, i0tab[m],
+    coef[cell] = exp_cell_coef(rel_t, n, grid_t0(g, ax, m), tauc[nn].c2[1], tauc[nn].inv_tau, i0tab[m],
                                jend[cell], tb, esuf + (int64_t)nl * 3 * np1);
   }
 }
@@ -341,7 +341,7 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
     const size_t smem = exp_antenna_smem(p->n_sft);
     cudaFuncSetAttribute(k_exp_antenna, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_exp_antenna<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), kSufThreads, smem, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.tauc, p->ws.ax, p->ws.i0,
+        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.tauc, plan_axes(p), p->ws.i0,
         p->ws.jend, p->ws.coef);
     p->launches += 1;
     return cudaGetLastError();
@@ -357,7 +357,7 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
       const int64_t total = (int64_t)g.n_t0 * len;
       const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
       k_exp_coef<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, lo, len, p->ws.i0,
-                                        p->ws.jend, p->ws.esuf, p->ws.tauc, p->ws.ax,
+                                        p->ws.jend, p->ws.esuf, p->ws.tauc, plan_axes(p),
                                         p->ws.coef + ta * cells);
       p->launches += 1;
       cudaError_t e = cudaGetLastError();
@@ -414,10 +414,10 @@ k_exp_plain(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_bas
   __syncthreads();
   const int32_t jmax = s_jmax;
   int32_t t0rel = 0;
-  if (jmax > i0) t0rel = (int32_t)(ax[m] - *t_base);
-  const double tau = (double)ax[g.n_t0 + (in_grid ? nn : 0)];
+  if (jmax > i0) t0rel = (int32_t)(grid_t0(g, ax, m) - *t_base);
+  const double tau = (double)grid_tau(g, ax, in_grid ? nn : 0);
   const float c2 = (float)(-1.4426950408889634 / tau);
-  const double su64 = TAB ? tab_scale(n_tab, exp_cut8_of(g), ax[g.n_t0 + (in_grid ? nn : 0)]) : 0.0;
+  const double su64 = TAB ? tab_scale(n_tab, exp_cut8_of(g), grid_tau(g, ax, in_grid ? nn : 0)) : 0.0;
   const float su = (float)su64;
   Acc acc[NCOL];
 #pragma unroll
@@ -489,7 +489,7 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
   auto run = [&](auto kern, int tc) {
     dim3 grid((unsigned)tiles, (unsigned)((p->n_templates + tc - 1) / tc));
     kern<<<grid, kExpCells, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.wtab, p->n_tab,
-                                    p->ws.ax, p->ws.i0, p->ws.jend, p->ws.coef, a->shared_antenna,
+                                    plan_axes(p), p->ws.i0, p->ws.jend, p->ws.coef, a->shared_antenna,
                                     a->fafb, p->n_templates, d_2F, p->ws.partials, p->part_stride);
   };
   if (p->precision == FMAP_FP64) {

@@ -310,14 +310,14 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
     const int32_t jc = in_grid ? p.jend[cell] : i0;
     // -log2(e) / tau by an FP32 division (within 1.5 ulp; FP64 runs at 1/64
     // of the FP32 rate on GB300)
-    const float c2 = -1.44269504088896341f / (float)p.ax[g.n_t0 + (in_grid ? n : 0)];
+    const float c2 = -1.44269504088896341f / (float)grid_tau(g, p.ax, (in_grid ? n : 0));
     int32_t t0rel = 0;
-    if (jmax > i0) t0rel = (int32_t)(p.ax[m] - *p.t_base);
+    if (jmax > i0) t0rel = (int32_t)(grid_t0(g, p.ax, m) - *p.t_base);
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int gtid = threadIdx.x;          // 0 .. 255 over the generator warps
     float su = 0.0f;                       // TAB: table samples per second of t - t0
     if constexpr (TAB) {
-      su = (float)tab_scale(p.n_tab, exp_cut8_of(g), p.ax[g.n_t0 + (in_grid ? n : 0)]);
+      su = (float)tab_scale(p.n_tab, exp_cut8_of(g), grid_tau(g, p.ax, (in_grid ? n : 0)));
       for (int k = gtid; k <= p.n_tab; k += kGenWarps * 32) s_tab[k] = p.wtab[k];
       asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory");
     }
@@ -571,7 +571,7 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   tc::Params prm;
   prm.rel_t = p->ws.rel_t;
   prm.t_base = p->ws.t_base;
-  prm.ax = p->ws.ax;
+  prm.ax = plan_axes(p);
   prm.wtab = p->ws.wtab;
   prm.n_tab = p->n_tab;
   prm.g = g;

@@ -163,8 +163,8 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
     const int32_t only = shared_antenna ? -1 : (int32_t)(entry / cells);
     const int32_t m = (int32_t)(cell / g.n_tau), nn = (int32_t)(cell % g.n_tau);
     const int32_t i0 = i0tab[m], j = jend[cell];
-    const int64_t t0rel = ax[m] - *t_base;
-    const double tau = (double)ax[g.n_t0 + nn];
+    const int64_t t0rel = grid_t0(g, ax, m) - *t_base;
+    const double tau = (double)grid_tau(g, ax, nn);
     const bool mine = active_t && (only < 0 || only == tq);
     const int32_t ta = shared_antenna ? 0 : tq;
     const float* ant = antenna + (int64_t)ta * 3 * n_sft;
@@ -178,7 +178,7 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
         if (a < j) {
           const double d = (double)((int64_t)rel_t[a] - t0rel);
           w = g.window == FMAP_RECT ? 1.0
-              : g.window == FMAP_TABLE ? tab_weight64(d * tab_scale(n_tab, exp_cut8_of(g), ax[g.n_t0 + nn]), wtab, n_tab)
+              : g.window == FMAP_TABLE ? tab_weight64(d * tab_scale(n_tab, exp_cut8_of(g), grid_tau(g, ax, nn)), wtab, n_tab)
                                        : exp(-d / tau);
         }
         sw[u] = w;
@@ -240,15 +240,15 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
     if (!shared_antenna && entry / cells != tq) continue;
     const int32_t m = (int32_t)(cell / g.n_tau), nn = (int32_t)(cell % g.n_tau);
     const int32_t i0 = i0tab[m], j = jend[cell];
-    const int64_t t0rel = ax[m] - tb;
-    const double inv_tau = 1.0 / (double)ax[g.n_t0 + nn];
+    const int64_t t0rel = grid_t0(g, ax, m) - tb;
+    const double inv_tau = 1.0 / (double)grid_tau(g, ax, nn);
     double A = 0, B = 0, C = 0, far = 0, fai = 0, fbr = 0, fbi = 0;
     // Exponential weights along the window by products of the per-gap
     // decays (one exp for the first atom and one for the one-SFT decay;
     // relative error ~(j - i0) ulp), the FP64 pipe being 1/64 of FP32 rate.
     const bool ex = g.window == FMAP_EXP;
     const bool tb_win = g.window == FMAP_TABLE;
-    const double su = tb_win ? tab_scale(n_tab, exp_cut8_of(g), ax[g.n_t0 + nn]) : 0.0;
+    const double su = tb_win ? tab_scale(n_tab, exp_cut8_of(g), grid_tau(g, ax, nn)) : 0.0;
     double w = 1.0, rho1 = 0.0;
     if (ex && j > i0) {
       w = exp(-(double)((int64_t)rel_t[i0] - t0rel) * inv_tau);
@@ -325,14 +325,14 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
   if (p->n_templates < kFixCellModeT)
     k_fixup_cells<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
                                                a->shared_antenna, p->ws.rel_t, p->ws.t_base,
-                                               p->n_sft, p->grid, p->ws.ax, p->ws.wtab, p->n_tab,
+                                               p->n_sft, p->grid, plan_axes(p), p->ws.wtab, p->n_tab,
                                                p->ws.i0, p->ws.jend,
                                                a->antenna, a->fafb, p->n_templates, d_2F,
                                                p->ws.partials, p->part_stride, p->n_tiles);
   else
     k_fixup<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
                                          a->shared_antenna, p->ws.rel_t, p->ws.t_base, p->n_sft,
-                                         p->grid, p->ws.ax, p->ws.wtab, p->n_tab, p->ws.i0, p->ws.jend,
+                                         p->grid, plan_axes(p), p->ws.wtab, p->n_tab, p->ws.i0, p->ws.jend,
                                          a->antenna, a->fafb,
                                          p->n_templates, d_2F, p->ws.partials, p->part_stride,
                                          p->n_tiles);

@@ -69,7 +69,16 @@ constexpr int kFlagUnit = 8192;
 constexpr int kScanLanes = 256;
 __host__ __device__ inline int64_t scan_chunk(int32_t n_sft) { return ((int64_t)n_sft + kScanLanes - 1) / kScanLanes; }
 __host__ __device__ inline int64_t perm_entries(int32_t n_sft) { return scan_chunk(n_sft) * kScanLanes; }
+// Grid values t0_m and tau_n: Eq. Fmn's uniform grid, or the plan's explicit
+// axes ax (t0 values, then tau values) when given (non-null).
+__host__ __device__ inline int64_t grid_t0(const fmap_grid& g, const int64_t* ax, int64_t m) {
+  return ax ? ax[m] : g.t0_min + m * g.dt0;
+}
+__host__ __device__ inline int64_t grid_tau(const fmap_grid& g, const int64_t* ax, int64_t n) {
+  return ax ? ax[g.n_t0 + n] : g.tau_min + n * g.dtau;
+}
 // Entries of the exp copy step: the chunk-major copies, then one per tau.
+// (plan_axes, after the plan struct: the axes to pass kernels, or null.)
 __host__ __device__ inline int64_t exp_copy_entries(int32_t n_sft, int32_t n_ant, int32_t n_x,
                                                     int32_t n_tau) {
   return perm_entries(n_sft) * (int64_t)(n_ant + n_x) + n_tau;
@@ -115,7 +124,7 @@ struct Workspace {
   float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
   TauTab* tauc = nullptr;        // [n_tau] per-tau decay constants
   float2* wtab = nullptr;        // table windows: [kTabMax + 1] (w_k, w_{k+1} - w_k), then (0, 0)
-  int64_t* ax = nullptr;         // [n_t0 + n_tau] the grid: t0_m values, then tau_n values
+  int64_t* ax = nullptr;         // [n_t0 + n_tau] explicit axes: t0 values, then tau values
   // exp
   float2* esuf = nullptr;        // [tau_chunk][3][N+1] float-float decayed suffix sums
   // tensor-core operands
@@ -144,8 +153,8 @@ struct fmap_plan_s {
   int32_t tau_chunk = 0;      // exp: tau values per suffix launch
   size_t xop_bytes = 0;
   bool host_staging = false;
-  // explicit (t0, tau) axes set by fmap_plan_axes (else the uniform grid of
-  // Eq. Fmn, written to ws.ax by each run's prep step); host copy of the axes
+  // explicit (t0, tau) axes set by fmap_plan_axes (in ws.ax; else the uniform
+  // grid of Eq. Fmn); host copy of the axes
   bool explicit_axes = false;
   std::vector<int64_t> ax_host;
   int32_t n_tab = 0;             // table windows: samples set by fmap_plan_window_table
@@ -164,6 +173,9 @@ struct fmap_plan_s {
 };
 
 namespace fmap {
+
+// The explicit axes of a plan for its kernels, or null for a uniform grid.
+inline const int64_t* plan_axes(const fmap_plan_s* p) { return p->explicit_axes ? p->ws.ax : nullptr; }
 
 // ---- host launchers (each returns cudaGetLastError of its launches and
 // adds the number of kernels it launched to p->launches) -------------------

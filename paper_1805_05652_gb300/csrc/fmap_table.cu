@@ -67,9 +67,9 @@ k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t
   __syncthreads();
   const int32_t jmax = s_jmax;
   const int64_t tb = n > 0 ? *t_base : 0;
-  const int64_t t0rel = ax[m] - tb;
+  const int64_t t0rel = grid_t0(g, ax, m) - tb;
   const float su =
-      in_grid ? (float)tab_scale(n_tab, exp_cut8_of(g), ax[g.n_t0 + nn]) : 0.0f;
+      in_grid ? (float)tab_scale(n_tab, exp_cut8_of(g), grid_tau(g, ax, nn)) : 0.0f;
   const float* ant = antenna + (int64_t)ta * 3 * n;
   FF S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   for (int32_t k0 = i0; k0 < jmax; k0 += kTabKC) {
@@ -100,7 +100,7 @@ cudaError_t launch_table_antenna(fmap_plan_s* p, const fmap_atoms* a, cudaStream
   const int n_ant = a->shared_antenna ? 1 : p->n_templates;
   const int64_t blocks = (int64_t)g.n_t0 * ((g.n_tau + kTabCells - 1) / kTabCells);
   k_table_antenna<<<dim3((unsigned)blocks, (unsigned)n_ant), kTabCells, 0, s>>>(
-      p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.ax, p->ws.wtab, p->n_tab, a->antenna,
+      p->ws.rel_t, p->ws.t_base, p->n_sft, g, plan_axes(p), p->ws.wtab, p->n_tab, a->antenna,
       p->ws.i0, p->ws.jend, p->ws.coef);
   p->launches += 1;
   return cudaGetLastError();
