@@ -86,7 +86,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
-      esuf, xop, perm_ant, perm_x, tauc, ax, wtab, total;
+      esuf, xop, perm_ant, perm_x, tauc, ax, wtab, flag_bits, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -126,6 +126,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
   const size_t entries = (size_t)std::max<int64_t>(cells, 1) * (size_t)t_ant;
   L.coef = take(sizeof(Coef) * entries);
   L.flag_blocks = take(sizeof(int32_t) * ((entries + kFlagUnit - 1) / kFlagUnit));
+  L.flag_bits = take(sizeof(uint32_t) * (size_t)flag_words((int64_t)entries));
   L.n_flag = take(sizeof(int32_t));
   L.flag_list = take(sizeof(int64_t) * entries);
   L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.tauc = L.wtab = 0;
@@ -256,6 +257,7 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
   w.groups = (void*)(b + L.groups);
   w.coef = (Coef*)(b + L.coef);
   w.flag_blocks = (int32_t*)(b + L.flag_blocks);
+  w.flag_bits = (uint32_t*)(b + L.flag_bits);
   w.n_flag = (int32_t*)(b + L.n_flag);
   w.flag_list = (int64_t*)(b + L.flag_list);
   if (grid->window == FMAP_RECT) {
@@ -397,6 +399,12 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
     FMAP_CUDA(cudaEventRecord(ev[0], s));
   }
   FMAP_CUDA(launch_prep(p, a->t, s));
+  {   // the bitmask of ill-conditioned entries, set by the coefficient kernels
+    const int64_t ent = (int64_t)p->grid.n_t0 * p->grid.n_tau *
+                        (a->shared_antenna ? 1 : std::max<int32_t>(p->n_templates, 1));
+    if (ent > 0)
+      FMAP_CUDA(cudaMemsetAsync(p->ws.flag_bits, 0, sizeof(uint32_t) * (size_t)flag_words(ent), s));
+  }
   FMAP_CUDA(launch_index(p, a->t, s));
   if (ev[1]) FMAP_CUDA(cudaEventRecord(ev[1], s));
   int64_t tiles = 0;

@@ -31,6 +31,7 @@ struct BItem {
   Partial* partials;
   void* red_buf;
   int32_t* flag_blocks;
+  uint32_t* flag_bits;
   int32_t* n_flag;
   int64_t* flag_list;
   float4* pa;
@@ -55,6 +56,7 @@ constexpr int kCoefBlocksPerUnit = 8;
 constexpr int kIdxRowsPerUnit = 4;
 constexpr int kFixSlotsPerUnit = 16;
 constexpr int kPermPerUnit = 4096;   // chunk-major copy entries per unit
+constexpr int kBitsPerUnit = 4096;   // marked-entry bitmask words cleared per unit
 static_assert(kFixSlots % kFixSlotsPerUnit == 0, "fix-up slot groups");
 
 // Phases of the batch pipeline, in launch order.

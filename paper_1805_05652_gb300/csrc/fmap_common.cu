@@ -361,9 +361,17 @@ cudaError_t launch_marginalise(fmap_plan_s* p, const float* d_2F, const uint8_t*
 
 // ---- persistent multi-instance dispatchers (uneven batches) ----
 __global__ void __launch_bounds__(256) kb_prep(const BItem* __restrict__ items, BUnits u) {
+  // units [0, ru): relative times; then the marked-entry bitmask is cleared
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    prep_body(it.t, it.n_sft, it.n_alloc, it.rel_t, it.t_base, it.dev_err,
-              make_uint3((unsigned)k, 0, 0), dim3((unsigned)((it.n_alloc + 255) / 256)));
+    const int64_t ru = it.n_sft > 0 ? (it.n_alloc + 255) / 256 : 0;
+    if (k < ru) {
+      prep_body(it.t, it.n_sft, it.n_alloc, it.rel_t, it.t_base, it.dev_err,
+                make_uint3((unsigned)k, 0, 0), dim3((unsigned)ru));
+    } else {
+      const int64_t w0 = (k - ru) * kBitsPerUnit;
+      const int64_t w1 = min(flag_words(it.flag_entries), w0 + kBitsPerUnit);
+      for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) it.flag_bits[w] = 0u;
+    }
   });
 }
 __global__ void __launch_bounds__(kIdxThreads) kb_index(const BItem* __restrict__ items, BUnits u) {

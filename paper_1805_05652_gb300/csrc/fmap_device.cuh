@@ -313,6 +313,14 @@ __device__ __forceinline__ float two_f(const Coef& c, float fa_re, float fa_im, 
   return fmaf(c.k1, fa2, c.k2 * e2);
 }
 
+// Stores the coefficients of entry e and marks it in the bitmask of the
+// ill-conditioned entries when it goes to the FP64 fix-up (valid == 2).
+__device__ __forceinline__ void store_coef(Coef* __restrict__ coef, uint32_t* __restrict__ bits,
+                                           int64_t e, const Coef& c) {
+  coef[e] = c;
+  if (c.valid == 2.0f) atomicOr(bits + (e >> 5), 1u << (uint32_t)(e & 31));
+}
+
 // Coefficients from float-float sums: D = AB - C^2 from exact FMA products
 // (relative error ~2^-44 AB, so ~1e-11 of D for AB/D <= 100); the
 // divisions in FP32.  A cell whose D is not clearly positive or whose

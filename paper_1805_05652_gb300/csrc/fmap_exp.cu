@@ -219,8 +219,8 @@ __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t,
 __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
               fmap_grid g, const float4* __restrict__ perm_ant, const TauTab* __restrict__ tauc,
               const int64_t* __restrict__ ax, const int32_t* __restrict__ i0tab,
-              const int32_t* __restrict__ jend, Coef* __restrict__ coef, const uint3 bid,
-              const dim3 gdim) {
+              const int32_t* __restrict__ jend, Coef* __restrict__ coef,
+              uint32_t* __restrict__ bits, const uint3 bid, const dim3 gdim) {
   extern __shared__ float2 s_E[];
   __shared__ float sR[2][kSufThreads / 32];
   __shared__ float sS[3][2][kSufThreads / 32];
@@ -232,8 +232,9 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
   const int64_t tb = n > 0 ? *t_base : 0;
   for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
     const int64_t cell = (int64_t)m * g.n_tau + ni;
-    coef[(int64_t)ta * cells + cell] =
-        exp_cell_coef(rel_t, n, grid_t0(g, ax, m), tt->c2[1], tt->inv_tau, i0tab[m], jend[cell], tb, s_E);
+    store_coef(coef, bits, (int64_t)ta * cells + cell,
+               exp_cell_coef(rel_t, n, grid_t0(g, ax, m), tt->c2[1], tt->inv_tau, i0tab[m],
+                             jend[cell], tb, s_E));
   }
 }
 
@@ -241,8 +242,10 @@ __global__ void __launch_bounds__(kSufThreads)
 k_exp_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
               fmap_grid g, const float4* __restrict__ perm_ant, const TauTab* __restrict__ tauc,
               const int64_t* __restrict__ ax, const int32_t* __restrict__ i0tab,
-              const int32_t* __restrict__ jend, Coef* __restrict__ coef) {
-  exp_antenna_body(rel_t, t_base, n, g, perm_ant, tauc, ax, i0tab, jend, coef, blockIdx, gridDim);
+              const int32_t* __restrict__ jend, Coef* __restrict__ coef,
+              uint32_t* __restrict__ bits) {
+  exp_antenna_body(rel_t, t_base, n, g, perm_ant, tauc, ax, i0tab, jend, coef, bits, blockIdx,
+                   gridDim);
 }
 
 // Chunk-major copies of one instance's atoms for the scans: entry
@@ -317,7 +320,8 @@ __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __r
                            int32_t n, fmap_grid g, int32_t n_lo, int32_t n_chunk,
                            const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
                            const float2* __restrict__ esuf, const TauTab* __restrict__ tauc,
-                           const int64_t* __restrict__ ax, Coef* __restrict__ coef) {
+                           const int64_t* __restrict__ ax, Coef* __restrict__ coef,
+                           uint32_t* __restrict__ bits, int64_t e_base) {
   const int64_t total = (int64_t)g.n_t0 * n_chunk;
   const int64_t np1 = (int64_t)n + 1;
   const int64_t tb = n > 0 ? *t_base : 0;
@@ -327,8 +331,9 @@ __global__ void k_exp_coef(const int32_t* __restrict__ rel_t, const int64_t* __r
     const int32_t nl = (int32_t)(c - m * n_chunk);
     const int64_t nn = n_lo + nl;
     const int64_t cell = m * g.n_tau + nn;
-    coef[cell] = exp_cell_coef(rel_t, n, grid_t0(g, ax, m), tauc[nn].c2[1], tauc[nn].inv_tau, i0tab[m],
-                               jend[cell], tb, esuf + (int64_t)nl * 3 * np1);
+    store_coef(coef, bits, e_base + cell,
+               exp_cell_coef(rel_t, n, grid_t0(g, ax, m), tauc[nn].c2[1], tauc[nn].inv_tau,
+                             i0tab[m], jend[cell], tb, esuf + (int64_t)nl * 3 * np1));
   }
 }
 
@@ -342,7 +347,7 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
     cudaFuncSetAttribute(k_exp_antenna, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_exp_antenna<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), kSufThreads, smem, s>>>(
         p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.tauc, plan_axes(p), p->ws.i0,
-        p->ws.jend, p->ws.coef);
+        p->ws.jend, p->ws.coef, p->ws.flag_bits);
     p->launches += 1;
     return cudaGetLastError();
   }
@@ -358,7 +363,7 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
       const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
       k_exp_coef<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, lo, len, p->ws.i0,
                                         p->ws.jend, p->ws.esuf, p->ws.tauc, plan_axes(p),
-                                        p->ws.coef + ta * cells);
+                                        p->ws.coef, p->ws.flag_bits, ta * cells);
       p->launches += 1;
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
@@ -516,8 +521,7 @@ __global__ void __launch_bounds__(kSufThreads, 3) kb_exp_ant(const BItem* __rest
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.perm_ant, it.tauc, it.ax, it.i0,
-                     it.jend,
-                     it.coef,
+                     it.jend, it.coef, it.flag_bits,
                      make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                      dim3((unsigned)it.g.n_tau, (unsigned)it.n_ant));
   });

@@ -7,8 +7,9 @@
 // step marks cells with AB/D > kCondThreshold (Coef.valid = 2); these are
 // rare (well below 1% of the cells of the workloads) and always short
 // windows in practice.  The fast kernels leave them out, and this file:
-//   1. compacts the marked cells into a list in a deterministic order
-//      (per-block counts, one exclusive scan, ordered writes);
+//   1. compacts the marked cells into a list in a deterministic order: the
+//      coefficient kernels set one bit per marked entry; per-unit counts of
+//      the bits, one exclusive scan, ordered writes;
 //   2. recomputes each listed cell for every template by the plain FP64
 //      definition over its window (Sec. 2: windowed sums, Eq. F_FaFb), writes
 //      its 2F and adds it to per-block reduction partials kept in their own
@@ -25,31 +26,27 @@ constexpr int kFixThreads = 128;
 constexpr int kFixWeights = 256;
 constexpr int kFixCellModeT = 8;    // below: threads over entries, not templates
 
-// Per unit of kFlagUnit entries (kFlagPer per thread, strided by the block):
-// number of entries with valid == 2.
-constexpr int kFlagPer = kFlagUnit / kFlagBlock;
-__device__ __forceinline__ void flag_count_body(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt,
+// Per unit of kFlagUnit entries: the number of entries marked in the
+// bitmask (valid == 2), from the unit's kFlagUnit / 32 words.
+constexpr int kFlagWords = kFlagUnit / 32;
+static_assert(kFlagWords <= kFlagBlock, "one word per thread");
+__device__ __forceinline__ void flag_count_body(const uint32_t* __restrict__ bits, int64_t n_entries, int32_t* __restrict__ blockcnt,
     const uint3 bid, const dim3 gdim) {
   __shared__ int32_t warp_cnt[kFlagBlock / 32];
-  const int64_t base = (int64_t)bid.x * kFlagUnit + threadIdx.x;
-  unsigned c = 0;
-#pragma unroll
-  for (int q = 0; q < kFlagPer; ++q) {
-    const int64_t e = base + q * kFlagBlock;
-    c += (e < n_entries && coef[e].valid == 2.0f) ? 1u : 0u;
-  }
-  c = __reduce_add_sync(0xffffffffu, c);
-  if ((threadIdx.x & 31) == 0) warp_cnt[threadIdx.x >> 5] = (int32_t)c;
+  const int tid = threadIdx.x;
+  const unsigned c = tid < kFlagWords ? (unsigned)__popc(bits[(int64_t)bid.x * kFlagWords + tid]) : 0u;
+  const unsigned wsum = __reduce_add_sync(0xffffffffu, c);
+  if ((tid & 31) == 0) warp_cnt[tid >> 5] = (int32_t)wsum;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const unsigned t = __reduce_add_sync(0xffffffffu, (unsigned)warp_cnt[threadIdx.x]);
-    if (threadIdx.x == 0) blockcnt[bid.x] = (int32_t)t;
+  if (tid < 32) {
+    const unsigned t = __reduce_add_sync(0xffffffffu, (unsigned)warp_cnt[tid]);
+    if (tid == 0) blockcnt[bid.x] = (int32_t)t;
   }
 }
 
 __global__ void __launch_bounds__(kFlagBlock)
-k_flag_count(const Coef* __restrict__ coef, int64_t n_entries, int32_t* __restrict__ blockcnt) {
-  flag_count_body(coef, n_entries, blockcnt, blockIdx, gridDim);
+k_flag_count(const uint32_t* __restrict__ bits, int64_t n_entries, int32_t* __restrict__ blockcnt) {
+  flag_count_body(bits, n_entries, blockcnt, blockIdx, gridDim);
 }
 
 // Exclusive scan of the block counts (one block); total into *n_flag.
@@ -95,48 +92,50 @@ k_flag_scan(int32_t* __restrict__ blockcnt, int64_t n_blocks, int32_t* __restric
   flag_scan_body(blockcnt, n_blocks, n_flag, blockIdx, gridDim);
 }
 
-// Ordered writes of the marked entries of one unit: kFlagPer rounds of
-// kFlagBlock consecutive entries, each placed by a warp ballot and an
-// exclusive scan of the warps' counts.
-__device__ __forceinline__ void flag_write_body(const Coef* __restrict__ coef, int64_t n_entries,
+// Ordered writes of the marked entries of one unit: each of the unit's words
+// (one per thread) places its set bits after the set bits of the words before
+// it (an exclusive scan of the words' counts over the block).
+__device__ __forceinline__ void flag_write_body(const uint32_t* __restrict__ bits, int64_t n_entries,
              const int32_t* __restrict__ blockoff, int64_t* __restrict__ list,
     const uint3 bid, const dim3 gdim) {
   __shared__ int32_t warp_cnt[kFlagBlock / 32];
-  __shared__ int32_t warp_off[kFlagBlock / 32];
-  __shared__ int32_t s_total;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t run = blockoff[bid.x];
-#pragma unroll 1
-  for (int q = 0; q < kFlagPer; ++q) {
-    const int64_t e = (int64_t)bid.x * kFlagUnit + q * kFlagBlock + threadIdx.x;
-    const bool f = e < n_entries && coef[e].valid == 2.0f;
-    const uint32_t bal = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) warp_cnt[warp] = __popc(bal);
-    __syncthreads();
-    if (warp == 0) {
-      const int32_t v = warp_cnt[lane];
-      int32_t x = v;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t w = (int64_t)bid.x * kFlagWords + tid;
+  uint32_t word = tid < kFlagWords ? bits[w] : 0u;
+  const int32_t c = __popc(word);
+  int32_t x = c;   // inclusive scan within the warp
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-      }
-      warp_off[lane] = x - v;
-      if (lane == 31) s_total = x;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_cnt[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int32_t v = warp_cnt[lane];
+    int32_t y = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t z = __shfl_up_sync(0xffffffffu, y, d);
+      if (lane >= d) y += z;
     }
-    __syncthreads();
-    if (f) {
-      const int64_t off = run + warp_off[warp] + __popc(bal & ((1u << lane) - 1u));
-      if (off < n_entries) list[off] = e;   // the list holds at most n_entries
-    }
-    run += s_total;
+    warp_cnt[lane] = y - v;   // exclusive over warps
+  }
+  __syncthreads();
+  int64_t off = blockoff[bid.x] + warp_cnt[warp] + (x - c);
+  while (word) {
+    const int b = __ffs(word) - 1;
+    word &= word - 1;
+    const int64_t e = w * 32 + b;
+    if (e < n_entries && off < n_entries) list[off] = e;   // the list holds at most n_entries
+    ++off;
   }
 }
 
 __global__ void __launch_bounds__(kFlagBlock)
-k_flag_write(const Coef* __restrict__ coef, int64_t n_entries,
+k_flag_write(const uint32_t* __restrict__ bits, int64_t n_entries,
              const int32_t* __restrict__ blockoff, int64_t* __restrict__ list) {
-  flag_write_body(coef, n_entries, blockoff, list, blockIdx, gridDim);
+  flag_write_body(bits, n_entries, blockoff, list, blockIdx, gridDim);
 }
 
 // FP64 recomputation of listed entries.  Entry = cell (shared antenna: every
@@ -317,9 +316,9 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
   const int64_t n_entries = cells * n_ant;
   if (n_entries == 0 || p->n_templates == 0) return cudaSuccess;
   const int64_t n_blocks = (n_entries + kFlagUnit - 1) / kFlagUnit;
-  k_flag_count<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.coef, n_entries, p->ws.flag_blocks);
+  k_flag_count<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.flag_bits, n_entries, p->ws.flag_blocks);
   k_flag_scan<<<1, 1024, 0, s>>>(p->ws.flag_blocks, n_blocks, p->ws.n_flag);
-  k_flag_write<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.coef, n_entries, p->ws.flag_blocks,
+  k_flag_write<<<(unsigned)n_blocks, kFlagBlock, 0, s>>>(p->ws.flag_bits, n_entries, p->ws.flag_blocks,
                                                          p->ws.flag_list);
   dim3 grid((unsigned)kFixSlots, (unsigned)fixup_blocks_y(p->n_templates));
   if (p->n_templates < kFixCellModeT)
@@ -345,7 +344,7 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
 __global__ void __launch_bounds__(kFlagBlock) kb_flag_count(const BItem* __restrict__ items,
                                                             BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    flag_count_body(it.coef, it.flag_entries, it.flag_blocks, make_uint3((unsigned)k, 0, 0),
+    flag_count_body(it.flag_bits, it.flag_entries, it.flag_blocks, make_uint3((unsigned)k, 0, 0),
                     dim3(1));
   });
 }
@@ -358,7 +357,7 @@ __global__ void __launch_bounds__(1024) kb_flag_scan(const BItem* __restrict__ i
 __global__ void __launch_bounds__(kFlagBlock) kb_flag_write(const BItem* __restrict__ items,
                                                             BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    flag_write_body(it.coef, it.flag_entries, it.flag_blocks, it.flag_list,
+    flag_write_body(it.flag_bits, it.flag_entries, it.flag_blocks, it.flag_list,
                     make_uint3((unsigned)k, 0, 0), dim3(1));
   });
 }

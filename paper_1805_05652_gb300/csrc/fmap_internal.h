@@ -62,6 +62,10 @@ __host__ __device__ inline int64_t window_len(const fmap_grid& g, int64_t tau) {
 constexpr int kTabMax = 1024;
 // Entries per count of the marked-entry compaction (1024 threads x 8).
 constexpr int kFlagUnit = 8192;
+// Words of the marked-entry bitmask (whole compaction units).
+__host__ __device__ inline int64_t flag_words(int64_t entries) {
+  return (entries + kFlagUnit - 1) / kFlagUnit * (kFlagUnit / 32);
+}
 // Threads of the exponential-window scans.  Thread t of a scan owns the atoms
 // [t C, t C + C), C = ceil(N / kScanLanes); the scans read the atoms from a
 // chunk-major copy (entry q kScanLanes + t holds atom t C + q), so the loads
@@ -114,6 +118,7 @@ struct Workspace {
   Partial* partials = nullptr;   // [T][n_tiles + kFixSlots]
   void* groups = nullptr;        // [T][reduce_groups_of(n_tiles + kFixSlots)] FP64 group merges
   int32_t* flag_blocks = nullptr;  // [ceil(T_ant cells / kFlagUnit)] counts, then offsets
+  uint32_t* flag_bits = nullptr;   // [flag_words(T_ant cells)] bit e: entry e has valid == 2
   int32_t* n_flag = nullptr;       // [1] number of ill-conditioned entries
   int64_t* flag_list = nullptr;    // [T_ant cells] their indices, ascending
   // rect

@@ -191,7 +191,7 @@ __device__ __forceinline__ Coef rect_cell_coef(const P4* __restrict__ pa, int64_
 
 __device__ __forceinline__ void rect_coef_body(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
                             const P4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
-                            int32_t n_ant, Coef* __restrict__ coef,
+                            int32_t n_ant, Coef* __restrict__ coef, uint32_t* __restrict__ bits,
     const uint3 bid, const dim3 gdim) {
   const int64_t cells = (int64_t)n_t0 * n_tau;
   const int64_t total = cells * n_ant;
@@ -205,21 +205,21 @@ __device__ __forceinline__ void rect_coef_body(const int32_t* __restrict__ i0tab
       const uint32_t ue = (uint32_t)e;
       const uint32_t ta = ue / ucells, cell = ue - ta * ucells;
       const int32_t i0 = i0tab[cell / utau], j = jend[cell];
-      coef[e] = rect_cell_coef(pa, ta * np1 + i0, ta * np1 + j, j - i0);
+      store_coef(coef, bits, e, rect_cell_coef(pa, ta * np1 + i0, ta * np1 + j, j - i0));
     }
     return;
   }
   for (int64_t e = e0; e < total; e += step) {
     const int64_t ta = e / cells, cell = e - ta * cells;
     const int32_t i0 = i0tab[cell / n_tau], j = jend[cell];
-    coef[e] = rect_cell_coef(pa, ta * np1 + i0, ta * np1 + j, j - i0);
+    store_coef(coef, bits, e, rect_cell_coef(pa, ta * np1 + i0, ta * np1 + j, j - i0));
   }
 }
 
 __global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
                             const P4* __restrict__ pa, int32_t n_sft, int32_t n_t0, int32_t n_tau,
-                            int32_t n_ant, Coef* __restrict__ coef) {
-  rect_coef_body(i0tab, jend, pa, n_sft, n_t0, n_tau, n_ant, coef, blockIdx, gridDim);
+                            int32_t n_ant, Coef* __restrict__ coef, uint32_t* __restrict__ bits) {
+  rect_coef_body(i0tab, jend, pa, n_sft, n_t0, n_tau, n_ant, coef, bits, blockIdx, gridDim);
 }
 
 // Cells.  The unit of work is a warp tile of kTileRows t0 rows x kTileCols
@@ -643,7 +643,7 @@ cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s
   const int64_t total = cells * n_ant;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
   k_rect_coef<<<blocks, 256, 0, s>>>(p->ws.i0, p->ws.jend, (const P4*)p->ws.pa, p->n_sft, g.n_t0,
-                                     g.n_tau, n_ant, p->ws.coef);
+                                     g.n_tau, n_ant, p->ws.coef, p->ws.flag_bits);
   p->launches += (p->n_sft > 0) ? 2 : 1;
   return cudaGetLastError();
 }
@@ -707,7 +707,8 @@ __global__ void __launch_bounds__(256) kb_rect_coef(const BItem* __restrict__ it
     const unsigned nb = (unsigned)((it.cells * it.n_ant + 255) / 256);
     for (int q = 0; q < kCoefBlocksPerUnit; ++q)
       rect_coef_body(it.i0, it.jend, (const P4*)it.pa, it.n_sft, it.g.n_t0, it.g.n_tau, it.n_ant,
-                     it.coef, make_uint3((unsigned)(k * kCoefBlocksPerUnit + q), 0, 0), dim3(nb));
+                     it.coef, it.flag_bits, make_uint3((unsigned)(k * kCoefBlocksPerUnit + q), 0, 0),
+                     dim3(nb));
   });
 }
 __global__ void __launch_bounds__(kScanThreads) kb_rect_data(const BItem* __restrict__ items,

@@ -44,7 +44,7 @@ k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t
                 fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab,
                 int32_t n_tab, const float* __restrict__ antenna,
                 const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
-                Coef* __restrict__ coef) {
+                Coef* __restrict__ coef, uint32_t* __restrict__ bits) {
   __shared__ float s_t[kTabKC];
   __shared__ float s_a[3][kTabKC];
   __shared__ float2 s_tab[kTabMax + 1];
@@ -91,7 +91,8 @@ k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t
     }
   }
   if (in_grid)
-    coef[(int64_t)ta * cells + cell] = make_coef_ff(ff_fold(S[0]), ff_fold(S[1]), ff_fold(S[2]), jc - i0);
+    store_coef(coef, bits, (int64_t)ta * cells + cell,
+               make_coef_ff(ff_fold(S[0]), ff_fold(S[1]), ff_fold(S[2]), jc - i0));
 }
 
 cudaError_t launch_table_antenna(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
@@ -101,7 +102,7 @@ cudaError_t launch_table_antenna(fmap_plan_s* p, const fmap_atoms* a, cudaStream
   const int64_t blocks = (int64_t)g.n_t0 * ((g.n_tau + kTabCells - 1) / kTabCells);
   k_table_antenna<<<dim3((unsigned)blocks, (unsigned)n_ant), kTabCells, 0, s>>>(
       p->ws.rel_t, p->ws.t_base, p->n_sft, g, plan_axes(p), p->ws.wtab, p->n_tab, a->antenna,
-      p->ws.i0, p->ws.jend, p->ws.coef);
+      p->ws.i0, p->ws.jend, p->ws.coef, p->ws.flag_bits);
   p->launches += 1;
   return cudaGetLastError();
 }
