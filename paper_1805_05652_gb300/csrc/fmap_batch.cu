@@ -204,7 +204,10 @@ static fmap_status build_wave_tables(fmap_batch_s* B, Wave& wv, const Tuning& tn
         if (ph == BP_EXP_ANT)
           wv.dyn_smem[ph] = std::max(wv.dyn_smem[ph], exp_antenna_smem(p->n_sft));
         if (ph == BP_EXP_REC)
-          wv.dyn_smem[ph] = std::max(wv.dyn_smem[ph], exp_rec_smem(p->n_sft, p->grid.n_t0));
+          wv.dyn_smem[ph] = std::max(
+              wv.dyn_smem[ph],
+              exp_rec_smem(p->n_sft, p->grid.n_t0,
+                           (h[k].T + h[k].groups - 1) / std::max(1, h[k].groups)));
         if (ph == BP_RECT_CELLS)
           wv.dyn_smem[ph] = std::max(wv.dyn_smem[ph], rect_cells_smem(p->n_templates, B->items[i].atoms.shared_antenna));
       }
@@ -438,8 +441,9 @@ fmap_status fmap_batch_plan(fmap_batch_t** out, const fmap_batch_item* items, in
   for (int32_t i = 0; i < n_items; ++i) {
     const fmap_batch_item& it = items[i];
     if (it.grid.window != FMAP_EXP) continue;
-    const size_t sm = std::max(exp_rec_smem(it.atoms.n_sft, it.grid.n_t0),
-                               exp_antenna_smem(it.atoms.n_sft));
+    const size_t sm = std::max(
+        exp_rec_smem(it.atoms.n_sft, it.grid.n_t0, std::min(it.atoms.n_templates, 2)),
+        exp_antenna_smem(it.atoms.n_sft));
     cls[i] = sm <= (56u << 10) ? 0 : sm <= (75u << 10) ? 1 : sm <= (113u << 10) ? 2 : 3;
   }
   std::vector<int32_t> order(n_items);

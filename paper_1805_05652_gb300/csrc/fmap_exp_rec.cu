@@ -42,8 +42,11 @@ constexpr size_t kRecSmemCap = 220 * 1024;
 __host__ __device__ __forceinline__ size_t rec_smem_base(int32_t n_sft) {
   return sizeof(float) * (2 * (size_t)n_sft + 4 * ((size_t)n_sft + 1)) + 16;
 }
-__host__ __device__ __forceinline__ bool rec_stage_cells(int32_t n_sft, int32_t n_t0) {
-  return rec_smem_base(n_sft) + sizeof(CellRec) * (size_t)n_t0 <= kRecSmemCap;
+// Staged only for blocks that run two or more templates (a single template
+// reads each record once, and the staging's shared memory would only lower
+// the blocks per SM).
+__host__ __device__ __forceinline__ bool rec_stage_cells(int32_t n_sft, int32_t n_t0, int32_t tpb) {
+  return tpb >= 2 && rec_smem_base(n_sft) + sizeof(CellRec) * (size_t)n_t0 <= kRecSmemCap;
 }
 
 __device__ __forceinline__ float rec_ex2(float x) {
@@ -121,7 +124,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     r.cf = coef[cell];
     return r;
   };
-  const bool stage = rec_stage_cells(n, g.n_t0);
+  const bool stage = rec_stage_cells(n, g.n_t0, (n_templates + n_groups - 1) / n_groups);
   if (stage)
     for (int32_t m = tid; m < g.n_t0; m += kRecThreads) s_cell[m] = cell_rec(m);
   const int32_t t_lo = (int32_t)((int64_t)bid.y * n_templates / n_groups);
@@ -267,12 +270,13 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
   *tiles_used = 0;
   if ((int64_t)g.n_t0 * g.n_tau == 0 || p->n_templates == 0) return cudaSuccess;
   *tiles_used = g.n_tau;
-  const size_t smem = exp_rec_smem(p->n_sft, g.n_t0);
-  cudaFuncSetAttribute(k_exp_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // split the templates over enough blocks to fill the GPU a few times
   const int64_t want = (int64_t)p->n_sm * 4;
   const int32_t groups = (int32_t)std::max<int64_t>(
       1, std::min<int64_t>(p->n_templates, (want + g.n_tau - 1) / g.n_tau));
+  const size_t smem =
+      exp_rec_smem(p->n_sft, g.n_t0, (p->n_templates + groups - 1) / groups);
+  cudaFuncSetAttribute(k_exp_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)g.n_tau, (unsigned)groups);
   k_exp_rec<<<grid, kRecThreads, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0,
                                             p->ws.jend, p->ws.coef, a->shared_antenna, p->ws.perm_x,
@@ -298,8 +302,9 @@ __global__ void __launch_bounds__(kRecThreads, 3) kb_exp_rec(const BItem* __rest
 const void* batch_kernel_exp_rec(int phase) {
   return phase == BP_EXP_REC ? (const void*)kb_exp_rec : nullptr;
 }
-size_t exp_rec_smem(int32_t n_sft, int32_t n_t0) {
-  return rec_smem_base(n_sft) + (rec_stage_cells(n_sft, n_t0) ? sizeof(CellRec) * (size_t)n_t0 : 0);
+size_t exp_rec_smem(int32_t n_sft, int32_t n_t0, int32_t tpb) {
+  return rec_smem_base(n_sft) +
+         (rec_stage_cells(n_sft, n_t0, tpb) ? sizeof(CellRec) * (size_t)n_t0 : 0);
 }
 
 }  // namespace fmap

@@ -203,7 +203,8 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
 bool exp_rec_supported(int32_t n_sft, int32_t n_t0);
 bool exp_antenna_fits(int32_t n_sft);
 size_t exp_antenna_smem(int32_t n_sft);
-size_t exp_rec_smem(int32_t n_sft, int32_t n_t0);
+// Dynamic shared memory of the recurrence for blocks of up to tpb templates.
+size_t exp_rec_smem(int32_t n_sft, int32_t n_t0, int32_t tpb);
 // Dispatcher kernels of the batch phases, by file (nullptr: not that file's).
 const void* batch_kernel_common(int phase);
 const void* batch_kernel_rect(int phase);
