@@ -86,7 +86,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
-      esuf, xop, perm_ant, perm_x, tauc, ax, wtab, flag_bits, total;
+      esuf, xop, perm_ant, perm_x, perm_gap, tauc, ax, wtab, flag_bits, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -129,7 +129,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
   L.flag_bits = take(sizeof(uint32_t) * (size_t)flag_words((int64_t)entries));
   L.n_flag = take(sizeof(int32_t));
   L.flag_list = take(sizeof(int64_t) * entries);
-  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.tauc = L.wtab = 0;
+  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.perm_gap = L.tauc = L.wtab = 0;
   const size_t np1 = (size_t)n_sft + 1;
   if (g->window == FMAP_RECT) {
     L.pa = take(sizeof(float) * 8 * np1 * (size_t)t_ant);   // (a2, b2, ab, 0) float pairs
@@ -143,7 +143,10 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.esuf = take(exp_antenna_fits(n_sft) ? 8 : per_tau * (size_t)chunk);
     const size_t perm = sizeof(float4) * (size_t)perm_entries(n_sft);
     L.perm_ant = take(perm * (size_t)t_ant);
-    if (flags & FMAP_PLAN_EXP_RECURRENCE) L.perm_x = take(perm * (size_t)std::max<int32_t>(T, 1));
+    if (flags & FMAP_PLAN_EXP_RECURRENCE) {
+      L.perm_x = take(perm * (size_t)std::max<int32_t>(T, 1));
+      L.perm_gap = take(sizeof(int32_t) * (size_t)perm_entries(n_sft));
+    }
     L.tauc = take(sizeof(TauTab) * (size_t)std::max<int32_t>(g->n_tau, 1));
     if (g->window == FMAP_TABLE) L.wtab = take(sizeof(float2) * (kTabMax + 1));
     if (prec == FMAP_TF32 || prec == FMAP_BF16X3)
@@ -267,6 +270,7 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
     w.esuf = (float2*)(b + L.esuf);
     w.perm_ant = (float4*)(b + L.perm_ant);
     if (L.perm_x) w.perm_x = (float4*)(b + L.perm_x);
+    if (L.perm_gap) w.perm_gap = (int32_t*)(b + L.perm_gap);
     if (L.wtab) w.wtab = (float2*)(b + L.wtab);
     w.tauc = (TauTab*)(b + L.tauc);
     if (L.xop) w.xop = (void*)(b + L.xop);

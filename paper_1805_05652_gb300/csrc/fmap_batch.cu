@@ -180,6 +180,7 @@ static BItem make_bitem(const fmap_plan_s* p, const fmap_batch_item& it, uint32_
   b.pa = w.pa;
   b.perm_ant = w.perm_ant;
   b.perm_x = w.perm_x;
+  b.perm_gap = w.perm_gap;
   b.tauc = w.tauc;
   b.ax = nullptr;   // batches take uniform grids
   b.px = w.px;

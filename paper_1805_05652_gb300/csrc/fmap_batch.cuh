@@ -37,6 +37,7 @@ struct BItem {
   float4* pa;
   float4* perm_ant;
   float4* perm_x;
+  int32_t* perm_gap;
   TauTab* tauc;
   int64_t* ax;
   float4* px;

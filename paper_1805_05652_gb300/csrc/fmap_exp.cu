@@ -257,7 +257,8 @@ __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t,
                                               const float* __restrict__ antenna, int32_t n_ant,
                                               const float* __restrict__ fafb, int32_t n_x,
                                               float4* __restrict__ perm_ant,
-                                              float4* __restrict__ perm_x, const fmap_grid& g,
+                                              float4* __restrict__ perm_x,
+                                              int32_t* __restrict__ perm_gap, const fmap_grid& g,
                                               const int64_t* __restrict__ ax,
                                               TauTab* __restrict__ tauc, int64_t e_begin,
                                               int64_t e_end, int64_t e_step) {
@@ -280,6 +281,7 @@ __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t,
         v = make_float4(a[i], a[n + i], a[2 * (int64_t)n + i], __int_as_float(gap));
       }
       perm_ant[e] = v;
+      if (set == 0 && perm_gap) perm_gap[r] = __float_as_int(v.w);
     } else {
       const int64_t tq = set - n_ant;
       const float* x = fafb + tq * 4 * (int64_t)n;
@@ -294,9 +296,10 @@ __global__ void k_exp_perm(const int32_t* __restrict__ rel_t, int32_t n,
                            const float* __restrict__ antenna, int32_t n_ant,
                            const float* __restrict__ fafb, int32_t n_x,
                            float4* __restrict__ perm_ant, float4* __restrict__ perm_x,
-                           fmap_grid g, const int64_t* __restrict__ ax, TauTab* __restrict__ tauc) {
+                           int32_t* __restrict__ perm_gap, fmap_grid g,
+                           const int64_t* __restrict__ ax, TauTab* __restrict__ tauc) {
   const int64_t total = exp_copy_entries(n, n_ant, n_x, g.n_tau);
-  exp_perm_body(rel_t, n, antenna, n_ant, fafb, n_x, perm_ant, perm_x, g, ax, tauc,
+  exp_perm_body(rel_t, n, antenna, n_ant, fafb, n_x, perm_ant, perm_x, perm_gap, g, ax, tauc,
                 (int64_t)blockIdx.x * blockDim.x + threadIdx.x, total,
                 (int64_t)gridDim.x * blockDim.x);
 }
@@ -308,7 +311,8 @@ cudaError_t launch_exp_perm(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
   const int64_t total = exp_copy_entries(p->n_sft, n_ant, n_x, p->grid.n_tau);
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
   k_exp_perm<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->n_sft, a->antenna, n_ant, a->fafb, n_x,
-                                    p->ws.perm_ant, p->ws.perm_x, p->grid, plan_axes(p), p->ws.tauc);
+                                    p->ws.perm_ant, p->ws.perm_x, p->ws.perm_gap, p->grid,
+                                    plan_axes(p), p->ws.tauc);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -514,7 +518,7 @@ __global__ void __launch_bounds__(256) kb_exp_perm(const BItem* __restrict__ ite
     const int64_t total = exp_copy_entries(it.n_sft, it.n_ant, n_x, it.g.n_tau);
     const int64_t e0 = k * kPermPerUnit;
     exp_perm_body(it.rel_t, it.n_sft, it.antenna, it.n_ant, it.fafb, n_x, it.perm_ant, it.perm_x,
-                  it.g, it.ax, it.tauc, e0 + threadIdx.x, min(total, e0 + kPermPerUnit), 256);
+                  it.perm_gap, it.g, it.ax, it.tauc, e0 + threadIdx.x, min(total, e0 + kPermPerUnit), 256);
   });
 }
 __global__ void __launch_bounds__(kSufThreads, 3) kb_exp_ant(const BItem* __restrict__ items,

@@ -12,12 +12,13 @@
 // per-cell differences, which then carry the same ~1e-7 relative error as the
 // rectangular window's prefix differences.
 //
-// One block per (tau_n, group of templates): the per-SFT decays of tau_n are
-// computed once (FP64, split into float pairs) into shared memory; for each
-// template of the group the block scans the 4 data columns into shared memory
-// and evaluates the column of cells (t0_m, tau_n) for every m.  Blocks run
-// tau-fastest, so the blocks writing neighbouring tau of the same map rows run
-// together and their stores merge in L2.
+// One block per (tau_n, group of templates): for each template of the group
+// the block scans the 4 data columns (read from the chunk-major copy with the
+// gaps between atoms; the decays come from the per-tau table of powers of
+// the one-SFT decay) into shared memory and evaluates the column of cells
+// (t0_m, tau_n) for every m.  Blocks run tau-fastest, so the blocks writing
+// neighbouring tau of the same map rows run together and their stores merge
+// in L2.
 #include <math.h>
 
 #include "fmap_batch.cuh"
@@ -27,7 +28,7 @@ namespace fmap {
 
 constexpr int kRecThreads = 256;
 constexpr int kRecChunk = 8;        // SFTs of data prefetched per serial run of the scan
-constexpr int kRecMaxSft = 9000;    // decays + one template's suffix sums in shared memory (216 KB)
+constexpr int kRecMaxSft = 9000;    // one template's suffix sums in shared memory (144 KB)
 
 struct __align__(16) CellRec {
   int32_t i0, j;
@@ -37,10 +38,10 @@ struct __align__(16) CellRec {
 
 constexpr size_t kRecSmemCap = 220 * 1024;
 
-// Shared memory of the recurrence: decays and one template's suffix sums,
-// plus the staged per-cell records of one tau when they fit.
+// Shared memory of the recurrence: one template's suffix sums, plus the
+// staged per-cell records of one tau when they fit.
 __host__ __device__ __forceinline__ size_t rec_smem_base(int32_t n_sft) {
-  return sizeof(float) * (2 * (size_t)n_sft + 4 * ((size_t)n_sft + 1)) + 16;
+  return sizeof(float) * 4 * ((size_t)n_sft + 1) + 16;
 }
 // Staged only for blocks that run two or more templates (a single template
 // reads each record once, and the staging's shared memory would only lower
@@ -58,17 +59,16 @@ __device__ __forceinline__ float rec_ex2(float x) {
 __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          const TauTab* __restrict__ tauc, const int64_t* __restrict__ ax, int32_t n_templates,
-          int32_t n_groups, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
+          const int32_t* __restrict__ perm_gap, const TauTab* __restrict__ tauc,
+          const int64_t* __restrict__ ax, int32_t n_templates, int32_t n_groups,
+          float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
     const uint3 bid, const dim3 gdim) {
   static_assert(kRecThreads == kScanLanes, "chunk-major copy layout");
   extern __shared__ __align__(16) float s_dyn[];
-  float* s_rh = s_dyn;                 // [n] decay after atom i, high part
-  float* s_rl = s_dyn + n;             // [n] low part
-  float* s_e = s_dyn + 2 * (int64_t)n; // [4][n + 1] suffix sums of one template
+  float* s_e = s_dyn;                  // [4][n + 1] suffix sums of one template
   // per cell (t0_m, tau_n): the window [i0, j), prefactor, tail factor and the
   // 2F coefficients -- the same for every template, so staged once
-  CellRec* s_cell = (CellRec*)(s_e + 4 * ((int64_t)n + 1) + ((4 - (6 * n + 4) % 4) % 4));
+  CellRec* s_cell = (CellRec*)(s_e + 4 * ((int64_t)n + 1));
   __shared__ float sR[2][kRecThreads / 32];
   __shared__ float sS[4][2][kRecThreads / 32];
   __shared__ Partial scratch[kRecThreads / 32];
@@ -76,19 +76,11 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TauTab* tt = tauc + ni;
   const int64_t np1 = (int64_t)n + 1;
-  // Decays of this tau, once for all the block's templates: gaps of k whole
-  // SFTs from the tau's table of float-float powers of the one-SFT decay,
-  // other gaps by FP64 exp.
-  {
-    const float inv_tsft = 1.0f / (float)g.t_sft;
-    const double inv_tau = tt->inv_tau;
-    for (int i = tid; i < n; i += kRecThreads) {
-      FF r{0.0f, 0.0f};
-      if (i + 1 < n) r = gap_decay(rel_t[i + 1] - rel_t[i], g.t_sft, inv_tsft, tt->pw[0], inv_tau);
-      s_rh[i] = r.h;
-      s_rl[i] = r.l;
-    }
-  }
+  // Decay after atom i: gaps of k whole SFTs from the tau's table of
+  // float-float powers of the one-SFT decay, other gaps by FP64 exp; the gaps
+  // come from the chunk-major copy with the data.
+  const float inv_tsft = 1.0f / (float)g.t_sft;
+  const double inv_tau = tt->inv_tau;
   const int C = (n + kRecThreads - 1) / kRecThreads;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
@@ -130,7 +122,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   const int32_t t_lo = (int32_t)((int64_t)bid.y * n_templates / n_groups);
   const int32_t t_hi = (int32_t)((int64_t)(bid.y + 1) * n_templates / n_groups);
   for (int32_t tq = t_lo; tq < t_hi; ++tq) {
-    __syncthreads();   // decays ready; previous template's cells done with s_e
+    __syncthreads();   // records staged; previous template's cells done with s_e
     const float4* x = perm_x + (int64_t)tq * perm_entries(n);   // chunk-major data rows
     // phase 1: this thread's chunk as one affine map, E[s0] = S + R E[e0],
     // by the compensated recurrence (folded back every kRecChunk atoms); the
@@ -138,25 +130,31 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     // and positions past the chunk's end are identity steps (x = 0, r = 1)
     float Rh = 1.0f, Rc = 0.0f, Sh[4] = {0.f, 0.f, 0.f, 0.f}, Sc[4] = {0.f, 0.f, 0.f, 0.f};
     float xv[kRecChunk][4];
+    int32_t gq[kRecChunk];
     auto load_chunk = [&](int b0) {
 #pragma unroll
       for (int q = 0; q < kRecChunk; ++q) {
         const int i = b0 + q;
-        const float4 v = (i < e0) ? __ldg(x + (int64_t)(i - s0) * kRecThreads + tid)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int64_t o = (int64_t)(i - s0) * kRecThreads + tid;
+        const float4 v = (i < e0) ? __ldg(x + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        gq[q] = (i < e0) ? __ldg(perm_gap + o) : 0;
         xv[q][0] = v.x;
         xv[q][1] = v.y;
         xv[q][2] = v.z;
         xv[q][3] = v.w;
       }
     };
-    auto decay = [&](int i) { return i < e0 ? FF{s_rh[i], s_rl[i]} : FF{1.0f, 0.0f}; };
+    // identity past the chunk's end (gap 0 there), 0 after the last atom
+    auto decay = [&](int q) -> FF {
+      if (gq[q] > 0) return gap_decay(gq[q], g.t_sft, inv_tsft, tt->pw[0], inv_tau);
+      return gq[q] < 0 ? FF{0.0f, 0.0f} : FF{1.0f, 0.0f};
+    };
     for (int b0 = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk; e0 > s0 && b0 >= s0;
          b0 -= kRecChunk) {
       load_chunk(b0);
 #pragma unroll
       for (int q = kRecChunk - 1; q >= 0; --q) {
-        const FF r = decay(b0 + q);
+        const FF r = decay(q);
 #pragma unroll
         for (int c = 0; c < 4; ++c) ch_step(r, xv[q][c], Sh[c], Sc[c]);
         ch_mul(r, Rh, Rc);
@@ -218,7 +216,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
 #pragma unroll
       for (int q = kRecChunk - 1; q >= 0; --q) {
         const int i = b0 + q;
-        const FF r = decay(i);
+        const FF r = decay(q);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           ch_step(r, xv[q][c], eh[c], ec[c]);
@@ -256,9 +254,10 @@ __global__ void __launch_bounds__(kRecThreads)
 k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          const TauTab* __restrict__ tauc, const int64_t* __restrict__ ax, int32_t n_templates,
+          const int32_t* __restrict__ perm_gap, const TauTab* __restrict__ tauc,
+          const int64_t* __restrict__ ax, int32_t n_templates,
           int32_t n_groups, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
-  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, tauc, ax,
+  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, perm_gap, tauc, ax,
                n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
@@ -280,6 +279,7 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
   dim3 grid((unsigned)g.n_tau, (unsigned)groups);
   k_exp_rec<<<grid, kRecThreads, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0,
                                             p->ws.jend, p->ws.coef, a->shared_antenna, p->ws.perm_x,
+                                            p->ws.perm_gap,
                                             p->ws.tauc, plan_axes(p),
                                             p->n_templates, groups, d_2F, p->ws.partials,
                                             p->part_stride);
@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kRecThreads, 3) kb_exp_rec(const BItem* __rest
                                                           BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     exp_rec_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared, it.perm_x,
+                 it.perm_gap,
                  it.tauc, it.ax,
                  it.T, it.groups, it.map, it.partials, it.part_stride,
                  make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),

@@ -127,6 +127,7 @@ struct Workspace {
   // exp: chunk-major copies of the atoms (perm_entries(N) per set)
   float4* perm_ant = nullptr;    // [T_ant][.] (a2, b2, ab, gap to the next atom as int bits; -1 last)
   float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
+  int32_t* perm_gap = nullptr;   // [.] gap to the next atom (-1 last); recurrence plans
   TauTab* tauc = nullptr;        // [n_tau] per-tau decay constants
   float2* wtab = nullptr;        // table windows: [kTabMax + 1] (w_k, w_{k+1} - w_k), then (0, 0)
   int64_t* ax = nullptr;         // [n_t0 + n_tau] explicit axes: t0 values, then tau values
