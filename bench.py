@@ -547,11 +547,6 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
                 "frac": ach / peaks["hbm_gbs"], "traffic": None,
                 "kernel": "whole batch step (all phases; map bytes / step time)",
                 "peak_source": peak_src}
-        key = (args.workload, precision)
-        plain_workload = not (args.exp_cut8 or args.grid_axes or args.templates or args.window_table)
-        if plain_workload and key in NCU_TRAFFIC:
-            roof["traffic"] = NCU_TRAFFIC[key]
-            roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = uneven_cpu_baseline(fm, insts, counts)

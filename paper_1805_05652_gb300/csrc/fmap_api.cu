@@ -141,11 +141,11 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.tau_chunk = (int32_t)chunk;
     // the suffix sums live in shared memory when the data set fits there
     L.esuf = take(exp_antenna_fits(n_sft) ? 8 : per_tau * (size_t)chunk);
-    const size_t perm = sizeof(float4) * (size_t)perm_entries(n_sft);
+    const size_t perm = sizeof(float4) * (size_t)perm_entries(n_sft, kScanLanes);
     L.perm_ant = take(perm * (size_t)t_ant);
     if (flags & FMAP_PLAN_EXP_RECURRENCE) {
       L.perm_x = take(perm * (size_t)std::max<int32_t>(T, 1));
-      L.perm_gap = take(sizeof(int32_t) * (size_t)perm_entries(n_sft));
+      L.perm_gap = take(sizeof(int32_t) * (size_t)perm_entries(n_sft, kScanLanes));
     }
     L.tauc = take(sizeof(TauTab) * (size_t)std::max<int32_t>(g->n_tau, 1));
     if (g->window == FMAP_TABLE) L.wtab = take(sizeof(float2) * (kTabMax + 1));

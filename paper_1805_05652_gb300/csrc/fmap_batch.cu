@@ -45,20 +45,23 @@ struct Tuning {
 std::mutex g_tune_mu;
 std::map<std::string, Tuning> g_tune_cache;
 
-const void* phase_kernel(int ph) {
+// lanes: the scan width of the wave's exp instances (batch_scan_lanes).
+const void* phase_kernel(int ph, int lanes) {
   if (const void* k = batch_kernel_common(ph)) return k;
   if (const void* k = batch_kernel_rect(ph)) return k;
-  if (const void* k = batch_kernel_exp(ph)) return k;
-  if (const void* k = batch_kernel_exp_rec(ph)) return k;
+  if (const void* k = batch_kernel_exp(ph, lanes)) return k;
+  if (const void* k = batch_kernel_exp_rec(ph, lanes)) return k;
   return batch_kernel_fixup(ph);
 }
 
-int phase_threads(int ph) {
+int phase_threads(int ph, int lanes) {
   switch (ph) {
     case BP_FLAG_COUNT:
     case BP_FLAG_SCAN:
     case BP_FLAG_WRITE: return 1024;
     case BP_FIXUP: return 128;
+    case BP_EXP_ANT:
+    case BP_EXP_REC: return lanes;
     default: return 256;
   }
 }
@@ -67,6 +70,7 @@ int phase_threads(int ph) {
 
 struct Wave {
   std::vector<int32_t> items;            // instance indices (heaviest first)
+  int lanes = kScanLanes;                // scan width of its exp instances
   BItem* d_items = nullptr;
   int64_t* d_offsets = nullptr;          // [BP_COUNT][n + 1]
   std::vector<int64_t> totals;           // units per phase
@@ -115,7 +119,7 @@ static int64_t units_of(const fmap_plan_s* p, const fmap_batch_item& it, int ph,
     case BP_EXP_PERM: {
       if (rect || cells == 0) return 0;
       const int32_t n_x = (p->flags & FMAP_PLAN_EXP_RECURRENCE) ? (int32_t)T : 0;
-      return (exp_copy_entries(p->n_sft, (int32_t)n_ant, n_x, g.n_tau) + kPermPerUnit - 1) /
+      return (exp_copy_entries(p->n_sft, p->lanes, (int32_t)n_ant, n_x, g.n_tau) + kPermPerUnit - 1) /
              kPermPerUnit;
     }
     case BP_RECT_ANT: return rect && cells > 0 && p->n_sft > 0 ? n_ant : 0;
@@ -152,6 +156,7 @@ static BItem make_bitem(const fmap_plan_s* p, const fmap_batch_item& it, uint32_
   b.n_ant = b.shared ? 1 : b.T;
   b.groups = std::max(1, (b.T + rec_tpb - 1) / rec_tpb);
   b.n_alloc = rel_t_entries(p->n_sft);
+  b.lanes = p->lanes;
   b.cells = (int64_t)g.n_t0 * g.n_tau;
   b.n_tiles = p->n_tiles;
   b.part_stride = p->part_stride;
@@ -230,8 +235,10 @@ static fmap_status enqueue_phase(fmap_batch_s* B, int w, int ph, int occ, cudaSt
   Wave& wv = B->waves[w];
   const int64_t total = wv.totals[ph];
   if (total == 0) return FMAP_OK;
-  const void* k = phase_kernel(ph);
-  const int threads = phase_threads(ph);
+  const void* k = phase_kernel(ph, wv.lanes);
+  const int threads = phase_threads(ph, wv.lanes);
+  // narrower exp blocks: the same occupancy candidates in units of 256 threads
+  if (ph == BP_EXP_ANT || ph == BP_EXP_REC) occ *= kScanLanes / wv.lanes;
   const size_t smem = wv.dyn_smem[ph];
   if (smem > 0)
     FMAP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -268,6 +275,7 @@ static fmap_status place_wave(fmap_batch_s* B, int w) {
     st = plan_init(p, &it.grid, it.atoms.n_sft, it.atoms.n_templates, FMAP_FP64, flags,
                    B->ws + off, bytes);
     if (st != FMAP_OK) return st;
+    p->lanes = batch_scan_lanes(it.atoms.n_sft);   // the wave's exp kernels use this width
     off += (bytes + 255) / 256 * 256;
   }
   return FMAP_OK;
@@ -437,15 +445,20 @@ fmap_status fmap_batch_plan(fmap_batch_t** out, const fmap_batch_item* items, in
   // largest dynamic shared memory of their wave, so instances are grouped by
   // the number of blocks per SM that their exp kernels allow (rect instances
   // take the first class).  Within a class, heaviest first; waves are filled
-  // greedily within the budget and never mix classes.
+  // greedily within the budget and never mix classes.  The class also
+  // separates the exp scan widths (batch_scan_lanes), whose kernels differ.
   std::vector<int> cls(n_items, 0);
+  auto lane_index = [](int32_t n) {
+    return batch_scan_lanes(n) == 64 ? 0 : batch_scan_lanes(n) == 128 ? 1 : 2;
+  };
   for (int32_t i = 0; i < n_items; ++i) {
     const fmap_batch_item& it = items[i];
     if (it.grid.window != FMAP_EXP) continue;
     const size_t sm = std::max(
         exp_rec_smem(it.atoms.n_sft, it.grid.n_t0, std::min(it.atoms.n_templates, 2)),
         exp_antenna_smem(it.atoms.n_sft));
-    cls[i] = sm <= (56u << 10) ? 0 : sm <= (75u << 10) ? 1 : sm <= (113u << 10) ? 2 : 3;
+    const int smem_cls = sm <= (56u << 10) ? 0 : sm <= (75u << 10) ? 1 : sm <= (113u << 10) ? 2 : 3;
+    cls[i] = 4 * smem_cls + lane_index(it.atoms.n_sft);
   }
   std::vector<int32_t> order(n_items);
   std::iota(order.begin(), order.end(), 0);
@@ -467,6 +480,7 @@ fmap_status fmap_batch_plan(fmap_batch_t** out, const fmap_batch_item* items, in
       cur_cls = cls[i];
     }
     B->waves.back().items.push_back(i);
+    if (items[i].grid.window == FMAP_EXP) B->waves.back().lanes = batch_scan_lanes(items[i].atoms.n_sft);
     cur += foot[i];
     peak = std::max(peak, cur);
   }

@@ -14,7 +14,7 @@ namespace fmap {
 
 struct BItem {
   fmap_grid g;
-  int32_t n_sft, T, shared, n_ant, groups, n_alloc;
+  int32_t n_sft, T, shared, n_ant, groups, n_alloc, lanes;
   int64_t cells, n_tiles, part_stride, red_groups, tiles_used, flag_entries;
   double log_prior;
   const int64_t* t;

@@ -48,15 +48,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // it): E[c * (n + 1) + i] for c = a2, b2, ab and i = 0..n (E[n] = 0), each as
 // an (h, l) pair.  E may be in global or shared memory; the block must call
 // it together.
+// NT = the plan's scan width: the threads of the block and the width of the
+// chunk-major copy.
+template <int NT>
 __device__ __forceinline__ void antenna_suffix(const float4* __restrict__ perm, int32_t n,
                                                const fmap_grid& g,
                                                const TauTab* __restrict__ tt, float2* E,
-                                               float (*sR)[kSufThreads / 32],
-                                               float (*sS)[2][kSufThreads / 32]) {
-  static_assert(kSufThreads == kScanLanes, "chunk-major copy layout");
+                                               float (*sR)[NT / 32],
+                                               float (*sS)[2][NT / 32]) {
   const double inv_s = 2.0 * tt->inv_tau;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int C = (n + kSufThreads - 1) / kSufThreads;
+  const int C = (n + NT - 1) / NT;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   // Decay over one gap: e^{-2 gap / tau}, from the tau's table of powers of
   // the one-SFT decay (FP64 exp off the T_sft lattice).
@@ -76,7 +78,7 @@ __device__ __forceinline__ void antenna_suffix(const float4* __restrict__ perm, 
     for (int q = 0; q < kSufChunk; ++q) {
       const int i = b0 + q;
       const bool in = i < e0;
-      const float4 v = in ? __ldg(perm + (int64_t)(i - s0) * kSufThreads + tid)
+      const float4 v = in ? __ldg(perm + (int64_t)(i - s0) * NT + tid)
                           : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
       xa[q][0] = v.x;
       xa[q][1] = v.y;
@@ -133,7 +135,7 @@ __device__ __forceinline__ void antenna_suffix(const float4* __restrict__ perm, 
   __syncthreads();
   // composition of the later warps, applied to E[N] = 0: only its S matters
   FF lS[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  for (int v = kSufThreads / 32 - 1; v > warp; --v) {
+  for (int v = NT / 32 - 1; v > warp; --v) {
     const FF Rv{sR[0][v], sR[1][v]};
 #pragma unroll
     for (int c = 0; c < 3; ++c) lS[c] = ff_add(FF{sS[c][0][v], sS[c][1][v]}, ff_mul(Rv, lS[c]));
@@ -168,10 +170,12 @@ __device__ __forceinline__ void antenna_suffix(const float4* __restrict__ perm, 
 __global__ void __launch_bounds__(kSufThreads)
 k_exp_suffix(const float4* __restrict__ perm, const TauTab* __restrict__ tauc, int32_t n,
              fmap_grid g, int32_t n_lo, float2* __restrict__ esuf) {
+  static_assert(kSufThreads == kScanLanes, "data sets past shared memory take the widest scan");
   __shared__ float sR[2][kSufThreads / 32];
   __shared__ float sS[3][2][kSufThreads / 32];
   const int ni = blockIdx.x;
-  antenna_suffix(perm, n, g, tauc + n_lo + ni, esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
+  antenna_suffix<kSufThreads>(perm, n, g, tauc + n_lo + ni,
+                              esuf + (int64_t)ni * 3 * ((int64_t)n + 1), sR, sS);
 }
 
 // Tail factors above this size are taken from FP64 exp as float pairs: the
@@ -216,21 +220,22 @@ __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t,
 // (tau_n, antenna set) keeps the suffix sums in shared memory and writes the
 // coefficients of every cell (t0_m, tau_n).  Blocks run tau-fastest, so their
 // strided coefficient stores merge in L2.
+template <int NT>
 __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
               fmap_grid g, const float4* __restrict__ perm_ant, const TauTab* __restrict__ tauc,
               const int64_t* __restrict__ ax, const int32_t* __restrict__ i0tab,
               const int32_t* __restrict__ jend, Coef* __restrict__ coef,
               uint32_t* __restrict__ bits, const uint3 bid, const dim3 gdim) {
   extern __shared__ float2 s_E[];
-  __shared__ float sR[2][kSufThreads / 32];
-  __shared__ float sS[3][2][kSufThreads / 32];
+  __shared__ float sR[2][NT / 32];
+  __shared__ float sS[3][2][NT / 32];
   const int ni = bid.x, ta = bid.y;
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const TauTab* tt = tauc + ni;
-  antenna_suffix(perm_ant + (int64_t)ta * perm_entries(n), n, g, tt, s_E, sR, sS);
+  antenna_suffix<NT>(perm_ant + (int64_t)ta * perm_entries(n, NT), n, g, tt, s_E, sR, sS);
   __syncthreads();
   const int64_t tb = n > 0 ? *t_base : 0;
-  for (int32_t m = threadIdx.x; m < g.n_t0; m += kSufThreads) {
+  for (int32_t m = threadIdx.x; m < g.n_t0; m += NT) {
     const int64_t cell = (int64_t)m * g.n_tau + ni;
     store_coef(coef, bits, (int64_t)ta * cells + cell,
                exp_cell_coef(rel_t, n, grid_t0(g, ax, m), tt->c2[1], tt->inv_tau, i0tab[m],
@@ -238,22 +243,25 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
   }
 }
 
-__global__ void __launch_bounds__(kSufThreads)
+template <int NT>
+__global__ void __launch_bounds__(NT)
 k_exp_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
               fmap_grid g, const float4* __restrict__ perm_ant, const TauTab* __restrict__ tauc,
               const int64_t* __restrict__ ax, const int32_t* __restrict__ i0tab,
               const int32_t* __restrict__ jend, Coef* __restrict__ coef,
               uint32_t* __restrict__ bits) {
-  exp_antenna_body(rel_t, t_base, n, g, perm_ant, tauc, ax, i0tab, jend, coef, bits, blockIdx,
-                   gridDim);
+  exp_antenna_body<NT>(rel_t, t_base, n, g, perm_ant, tauc, ax, i0tab, jend, coef, bits, blockIdx,
+                       gridDim);
 }
 
 // Chunk-major copies of one instance's atoms for the scans: entry
-// q kScanLanes + t of a set holds atom i = t C + q (zeros past the last atom):
+// q lanes + t of a set holds atom i = t C + q (zeros past the last atom; lanes
+// = the plan's scan width, C = scan_chunk(n, lanes)):
 // sets 0..n_ant-1 the antenna rows with the gap to the next atom, sets
 // n_ant.. the data rows of each template (when perm_x is given); then the
 // per-tau constants (n_tau more entries).
 __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t, int32_t n,
+                                              int32_t lanes,
                                               const float* __restrict__ antenna, int32_t n_ant,
                                               const float* __restrict__ fafb, int32_t n_x,
                                               float4* __restrict__ perm_ant,
@@ -262,7 +270,7 @@ __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t,
                                               const int64_t* __restrict__ ax,
                                               TauTab* __restrict__ tauc, int64_t e_begin,
                                               int64_t e_end, int64_t e_step) {
-  const int64_t P = perm_entries(n), C = scan_chunk(n);
+  const int64_t P = perm_entries(n, lanes), C = scan_chunk(n, lanes);
   const int64_t n_copy = P * (int64_t)(n_ant + n_x);
   for (int64_t e = e_begin; e < e_end; e += e_step) {
     if (e >= n_copy) {   // entries past the copies: the per-tau constants
@@ -270,7 +278,7 @@ __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t,
       continue;
     }
     const int64_t set = e / P, r = e - set * P;
-    const int64_t q = r / kScanLanes, t = r - q * kScanLanes;
+    const int64_t q = r / lanes, t = r - q * lanes;
     const int64_t i = t * C + q;
     const bool in = i < n;
     if (set < n_ant) {
@@ -292,14 +300,14 @@ __device__ __forceinline__ void exp_perm_body(const int32_t* __restrict__ rel_t,
   }
 }
 
-__global__ void k_exp_perm(const int32_t* __restrict__ rel_t, int32_t n,
+__global__ void k_exp_perm(const int32_t* __restrict__ rel_t, int32_t n, int32_t lanes,
                            const float* __restrict__ antenna, int32_t n_ant,
                            const float* __restrict__ fafb, int32_t n_x,
                            float4* __restrict__ perm_ant, float4* __restrict__ perm_x,
                            int32_t* __restrict__ perm_gap, fmap_grid g,
                            const int64_t* __restrict__ ax, TauTab* __restrict__ tauc) {
-  const int64_t total = exp_copy_entries(n, n_ant, n_x, g.n_tau);
-  exp_perm_body(rel_t, n, antenna, n_ant, fafb, n_x, perm_ant, perm_x, perm_gap, g, ax, tauc,
+  const int64_t total = exp_copy_entries(n, lanes, n_ant, n_x, g.n_tau);
+  exp_perm_body(rel_t, n, lanes, antenna, n_ant, fafb, n_x, perm_ant, perm_x, perm_gap, g, ax, tauc,
                 (int64_t)blockIdx.x * blockDim.x + threadIdx.x, total,
                 (int64_t)gridDim.x * blockDim.x);
 }
@@ -308,9 +316,9 @@ cudaError_t launch_exp_perm(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
   if ((int64_t)p->grid.n_t0 * p->grid.n_tau == 0) return cudaSuccess;
   const int32_t n_ant = a->shared_antenna ? 1 : p->n_templates;
   const int32_t n_x = p->ws.perm_x ? p->n_templates : 0;
-  const int64_t total = exp_copy_entries(p->n_sft, n_ant, n_x, p->grid.n_tau);
+  const int64_t total = exp_copy_entries(p->n_sft, p->lanes, n_ant, n_x, p->grid.n_tau);
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->n_sm * 16);
-  k_exp_perm<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->n_sft, a->antenna, n_ant, a->fafb, n_x,
+  k_exp_perm<<<blocks, 256, 0, s>>>(p->ws.rel_t, p->n_sft, p->lanes, a->antenna, n_ant, a->fafb, n_x,
                                     p->ws.perm_ant, p->ws.perm_x, p->ws.perm_gap, p->grid,
                                     plan_axes(p), p->ws.tauc);
   p->launches += 1;
@@ -348,15 +356,22 @@ cudaError_t launch_exp_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s)
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   if (p->n_sft <= kAntennaSmemMaxSft) {
     const size_t smem = exp_antenna_smem(p->n_sft);
-    cudaFuncSetAttribute(k_exp_antenna, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_exp_antenna<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), kSufThreads, smem, s>>>(
-        p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.tauc, plan_axes(p), p->ws.i0,
-        p->ws.jend, p->ws.coef, p->ws.flag_bits);
+    auto run = [&](auto kern, int nt) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<dim3((unsigned)g.n_tau, (unsigned)n_ant), nt, smem, s>>>(
+          p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.perm_ant, p->ws.tauc, plan_axes(p),
+          p->ws.i0, p->ws.jend, p->ws.coef, p->ws.flag_bits);
+    };
+    switch (p->lanes) {
+      case 64: run(k_exp_antenna<64>, 64); break;
+      case 128: run(k_exp_antenna<128>, 128); break;
+      default: run(k_exp_antenna<256>, 256); break;
+    }
     p->launches += 1;
     return cudaGetLastError();
   }
   for (int ta = 0; ta < n_ant; ++ta) {
-    const float4* perm = p->ws.perm_ant + (int64_t)ta * perm_entries(p->n_sft);
+    const float4* perm = p->ws.perm_ant + (int64_t)ta * perm_entries(p->n_sft, p->lanes);
     for (int32_t lo = 0; lo < g.n_tau; lo += p->tau_chunk) {
       const int32_t len = std::min<int32_t>(p->tau_chunk, g.n_tau - lo);
       if (p->n_sft > 0) {
@@ -515,24 +530,28 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
 __global__ void __launch_bounds__(256) kb_exp_perm(const BItem* __restrict__ items, BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     const int32_t n_x = it.perm_x ? it.T : 0;
-    const int64_t total = exp_copy_entries(it.n_sft, it.n_ant, n_x, it.g.n_tau);
+    const int64_t total = exp_copy_entries(it.n_sft, it.lanes, it.n_ant, n_x, it.g.n_tau);
     const int64_t e0 = k * kPermPerUnit;
-    exp_perm_body(it.rel_t, it.n_sft, it.antenna, it.n_ant, it.fafb, n_x, it.perm_ant, it.perm_x,
+    exp_perm_body(it.rel_t, it.n_sft, it.lanes, it.antenna, it.n_ant, it.fafb, n_x, it.perm_ant, it.perm_x,
                   it.perm_gap, it.g, it.ax, it.tauc, e0 + threadIdx.x, min(total, e0 + kPermPerUnit), 256);
   });
 }
-__global__ void __launch_bounds__(kSufThreads, 3) kb_exp_ant(const BItem* __restrict__ items,
-                                                          BUnits u) {
+// (the register budget of 3 blocks of 256 threads per SM, for any width)
+template <int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) kb_exp_ant(const BItem* __restrict__ items,
+                                                        BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    exp_antenna_body(it.rel_t, it.t_base, it.n_sft, it.g, it.perm_ant, it.tauc, it.ax, it.i0,
-                     it.jend, it.coef, it.flag_bits,
-                     make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
-                     dim3((unsigned)it.g.n_tau, (unsigned)it.n_ant));
+    exp_antenna_body<NT>(it.rel_t, it.t_base, it.n_sft, it.g, it.perm_ant, it.tauc, it.ax, it.i0,
+                         it.jend, it.coef, it.flag_bits,
+                         make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
+                         dim3((unsigned)it.g.n_tau, (unsigned)it.n_ant));
   });
 }
-const void* batch_kernel_exp(int phase) {
+const void* batch_kernel_exp(int phase, int lanes) {
   if (phase == BP_EXP_PERM) return (const void*)kb_exp_perm;
-  return phase == BP_EXP_ANT ? (const void*)kb_exp_ant : nullptr;
+  if (phase != BP_EXP_ANT) return nullptr;
+  return lanes == 64 ? (const void*)kb_exp_ant<64>
+                     : lanes == 128 ? (const void*)kb_exp_ant<128> : (const void*)kb_exp_ant<256>;
 }
 size_t exp_antenna_smem(int32_t n_sft) { return sizeof(float2) * 3 * ((size_t)n_sft + 1); }
 bool exp_antenna_fits(int32_t n_sft) { return n_sft <= kAntennaSmemMaxSft; }

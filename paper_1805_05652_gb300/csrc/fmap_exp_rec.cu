@@ -56,6 +56,9 @@ __device__ __forceinline__ float rec_ex2(float x) {
   return y;
 }
 
+// NT = the plan's scan width: threads of the block and width of the
+// chunk-major copy.
+template <int NT>
 __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
@@ -63,15 +66,14 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
           const int64_t* __restrict__ ax, int32_t n_templates, int32_t n_groups,
           float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
     const uint3 bid, const dim3 gdim) {
-  static_assert(kRecThreads == kScanLanes, "chunk-major copy layout");
   extern __shared__ __align__(16) float s_dyn[];
   float* s_e = s_dyn;                  // [4][n + 1] suffix sums of one template
   // per cell (t0_m, tau_n): the window [i0, j), prefactor, tail factor and the
   // 2F coefficients -- the same for every template, so staged once
   CellRec* s_cell = (CellRec*)(s_e + 4 * ((int64_t)n + 1));
-  __shared__ float sR[2][kRecThreads / 32];
-  __shared__ float sS[4][2][kRecThreads / 32];
-  __shared__ Partial scratch[kRecThreads / 32];
+  __shared__ float sR[2][NT / 32];
+  __shared__ float sS[4][2][NT / 32];
+  __shared__ Partial scratch[NT / 32];
   const int ni = bid.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TauTab* tt = tauc + ni;
@@ -81,7 +83,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   // come from the chunk-major copy with the data.
   const float inv_tsft = 1.0f / (float)g.t_sft;
   const double inv_tau = tt->inv_tau;
-  const int C = (n + kRecThreads - 1) / kRecThreads;
+  const int C = (n + NT - 1) / NT;
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const float c2 = tt->c2[0];
@@ -118,12 +120,12 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   };
   const bool stage = rec_stage_cells(n, g.n_t0, (n_templates + n_groups - 1) / n_groups);
   if (stage)
-    for (int32_t m = tid; m < g.n_t0; m += kRecThreads) s_cell[m] = cell_rec(m);
+    for (int32_t m = tid; m < g.n_t0; m += NT) s_cell[m] = cell_rec(m);
   const int32_t t_lo = (int32_t)((int64_t)bid.y * n_templates / n_groups);
   const int32_t t_hi = (int32_t)((int64_t)(bid.y + 1) * n_templates / n_groups);
   for (int32_t tq = t_lo; tq < t_hi; ++tq) {
     __syncthreads();   // records staged; previous template's cells done with s_e
-    const float4* x = perm_x + (int64_t)tq * perm_entries(n);   // chunk-major data rows
+    const float4* x = perm_x + (int64_t)tq * perm_entries(n, NT);   // chunk-major data rows
     // phase 1: this thread's chunk as one affine map, E[s0] = S + R E[e0],
     // by the compensated recurrence (folded back every kRecChunk atoms); the
     // data of each run of kRecChunk SFTs is loaded before its serial chain,
@@ -135,7 +137,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
 #pragma unroll
       for (int q = 0; q < kRecChunk; ++q) {
         const int i = b0 + q;
-        const int64_t o = (int64_t)(i - s0) * kRecThreads + tid;
+        const int64_t o = (int64_t)(i - s0) * NT + tid;
         const float4 v = (i < e0) ? __ldg(x + o) : make_float4(0.f, 0.f, 0.f, 0.f);
         gq[q] = (i < e0) ? __ldg(perm_gap + o) : 0;
         xv[q][0] = v.x;
@@ -197,7 +199,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     __syncthreads();
     // later warps applied to E[N] = 0
     FF lS[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int v = kRecThreads / 32 - 1; v > warp; --v) {
+    for (int v = NT / 32 - 1; v > warp; --v) {
       const FF Rv = {sR[0][v], sR[1][v]};
 #pragma unroll
       for (int c = 0; c < 4; ++c) lS[c] = ff_add({sS[c][0][v], sS[c][1][v]}, ff_mul(Rv, lS[c]));
@@ -230,7 +232,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     __syncthreads();
     // cells (t0_m, tau_n), all m
     Partial acc = partial_empty();
-    for (int32_t m = tid; m < g.n_t0; m += kRecThreads) {
+    for (int32_t m = tid; m < g.n_t0; m += NT) {
       const int64_t cell = (int64_t)m * g.n_tau + ni;
       const CellRec r = stage ? s_cell[m] : cell_rec(m);
       const Coef cf = shared_antenna ? r.cf : coef[(int64_t)tq * cells + cell];
@@ -245,19 +247,20 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
       if (map && cf.valid != 2.0f) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
       partial_add(acc, v, (int32_t)cell, ok);
     }
-    acc = partial_block_reduce<kRecThreads / 32>(acc, scratch);
+    acc = partial_block_reduce<NT / 32>(acc, scratch);
     if (tid == 0) parts[(int64_t)tq * stride + ni] = acc;
   }
 }
 
-__global__ void __launch_bounds__(kRecThreads)
+template <int NT>
+__global__ void __launch_bounds__(NT)
 k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
           const int32_t* __restrict__ perm_gap, const TauTab* __restrict__ tauc,
           const int64_t* __restrict__ ax, int32_t n_templates,
           int32_t n_groups, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
-  exp_rec_body(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, perm_gap, tauc, ax,
+  exp_rec_body<NT>(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, perm_gap, tauc, ax,
                n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
@@ -275,33 +278,41 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
       1, std::min<int64_t>(p->n_templates, (want + g.n_tau - 1) / g.n_tau));
   const size_t smem =
       exp_rec_smem(p->n_sft, g.n_t0, (p->n_templates + groups - 1) / groups);
-  cudaFuncSetAttribute(k_exp_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)g.n_tau, (unsigned)groups);
-  k_exp_rec<<<grid, kRecThreads, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0,
-                                            p->ws.jend, p->ws.coef, a->shared_antenna, p->ws.perm_x,
-                                            p->ws.perm_gap,
-                                            p->ws.tauc, plan_axes(p),
-                                            p->n_templates, groups, d_2F, p->ws.partials,
-                                            p->part_stride);
+  auto run = [&](auto kern, int nt) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, nt, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend,
+                                p->ws.coef, a->shared_antenna, p->ws.perm_x, p->ws.perm_gap,
+                                p->ws.tauc, plan_axes(p), p->n_templates, groups, d_2F,
+                                p->ws.partials, p->part_stride);
+  };
+  switch (p->lanes) {
+    case 64: run(k_exp_rec<64>, 64); break;
+    case 128: run(k_exp_rec<128>, 128); break;
+    default: run(k_exp_rec<256>, 256); break;
+  }
   p->launches += 1;
   return cudaGetLastError();
 }
 
 
 // ---- persistent multi-instance dispatcher (uneven batches) ----
-__global__ void __launch_bounds__(kRecThreads, 3) kb_exp_rec(const BItem* __restrict__ items,
-                                                          BUnits u) {
+// (the register budget of 3 blocks of 256 threads per SM, for any width)
+template <int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) kb_exp_rec(const BItem* __restrict__ items,
+                                                        BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    exp_rec_body(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared, it.perm_x,
-                 it.perm_gap,
-                 it.tauc, it.ax,
-                 it.T, it.groups, it.map, it.partials, it.part_stride,
-                 make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
-                 dim3((unsigned)it.g.n_tau, (unsigned)it.groups));
+    exp_rec_body<NT>(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared,
+                     it.perm_x, it.perm_gap, it.tauc, it.ax, it.T, it.groups, it.map, it.partials,
+                     it.part_stride,
+                     make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
+                     dim3((unsigned)it.g.n_tau, (unsigned)it.groups));
   });
 }
-const void* batch_kernel_exp_rec(int phase) {
-  return phase == BP_EXP_REC ? (const void*)kb_exp_rec : nullptr;
+const void* batch_kernel_exp_rec(int phase, int lanes) {
+  if (phase != BP_EXP_REC) return nullptr;
+  return lanes == 64 ? (const void*)kb_exp_rec<64>
+                     : lanes == 128 ? (const void*)kb_exp_rec<128> : (const void*)kb_exp_rec<256>;
 }
 size_t exp_rec_smem(int32_t n_sft, int32_t n_t0, int32_t tpb) {
   return rec_smem_base(n_sft) +

@@ -66,13 +66,25 @@ constexpr int kFlagUnit = 8192;
 __host__ __device__ inline int64_t flag_words(int64_t entries) {
   return (entries + kFlagUnit - 1) / kFlagUnit * (kFlagUnit / 32);
 }
-// Threads of the exponential-window scans.  Thread t of a scan owns the atoms
-// [t C, t C + C), C = ceil(N / kScanLanes); the scans read the atoms from a
-// chunk-major copy (entry q kScanLanes + t holds atom t C + q), so the loads
-// of a warp at one chunk position are contiguous.
-constexpr int kScanLanes = 256;
-__host__ __device__ inline int64_t scan_chunk(int32_t n_sft) { return ((int64_t)n_sft + kScanLanes - 1) / kScanLanes; }
-__host__ __device__ inline int64_t perm_entries(int32_t n_sft) { return scan_chunk(n_sft) * kScanLanes; }
+// Threads of the exponential-window scans ("lanes", 64, 128 or 256, a plan
+// property): thread t of a scan owns the atoms [t C, t C + C), C =
+// ceil(N / lanes), and the scans read the atoms from a chunk-major copy
+// (entry q lanes + t holds atom t C + q), so the loads of a warp at one chunk
+// position are contiguous.  Single plans scan with 256 threads; batches, whose
+// many short units favour throughput over the latency of one tau, take fewer
+// for short data sets (batch_scan_lanes), so that combining the threads'
+// chunks stays cheap next to the chunks themselves.
+constexpr int kScanLanes = 256;   // the most threads of a scan
+__host__ __device__ inline int32_t batch_scan_lanes(int32_t n_sft) {
+  return n_sft <= 1024 ? 64 : (n_sft <= 2560 ? 128 : 256);
+}
+__host__ __device__ inline int64_t scan_chunk(int32_t n_sft, int32_t lanes) {
+  return ((int64_t)n_sft + lanes - 1) / lanes;
+}
+// (at most perm_entries(n, kScanLanes) for any width: workspaces take that)
+__host__ __device__ inline int64_t perm_entries(int32_t n_sft, int32_t lanes) {
+  return scan_chunk(n_sft, lanes) * lanes;
+}
 // Grid values t0_m and tau_n: Eq. Fmn's uniform grid, or the plan's explicit
 // axes ax (t0 values, then tau values) when given (non-null).
 __host__ __device__ inline int64_t grid_t0(const fmap_grid& g, const int64_t* ax, int64_t m) {
@@ -83,9 +95,9 @@ __host__ __device__ inline int64_t grid_tau(const fmap_grid& g, const int64_t* a
 }
 // Entries of the exp copy step: the chunk-major copies, then one per tau.
 // (plan_axes, after the plan struct: the axes to pass kernels, or null.)
-__host__ __device__ inline int64_t exp_copy_entries(int32_t n_sft, int32_t n_ant, int32_t n_x,
-                                                    int32_t n_tau) {
-  return perm_entries(n_sft) * (int64_t)(n_ant + n_x) + n_tau;
+__host__ __device__ inline int64_t exp_copy_entries(int32_t n_sft, int32_t lanes, int32_t n_ant,
+                                                    int32_t n_x, int32_t n_tau) {
+  return perm_entries(n_sft, lanes) * (int64_t)(n_ant + n_x) + n_tau;
 }
 // Per-tau constants of the exponential window, for the weight w (s = 1) and
 // the antenna weight w^2 (s = 2): the decays over gaps of k = 0..kPowTab-1
@@ -124,7 +136,7 @@ struct Workspace {
   // rect
   float4* pa = nullptr;          // [T_ant][N+1][2] FP64 antenna prefix (a2, b2, ab, 0) as hi4, lo4
   float4* px = nullptr;          // [T][N+1][2] float-float data prefix (hi4, lo4)
-  // exp: chunk-major copies of the atoms (perm_entries(N) per set)
+  // exp: chunk-major copies of the atoms (perm_entries(N, lanes) per set)
   float4* perm_ant = nullptr;    // [T_ant][.] (a2, b2, ab, gap to the next atom as int bits; -1 last)
   float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
   int32_t* perm_gap = nullptr;   // [.] gap to the next atom (-1 last); recurrence plans
@@ -164,6 +176,7 @@ struct fmap_plan_s {
   bool explicit_axes = false;
   std::vector<int64_t> ax_host;
   int32_t n_tab = 0;             // table windows: samples set by fmap_plan_window_table
+  int32_t lanes = fmap::kScanLanes;   // exp scan width (threads per tau)
   // TMA descriptors (CUtensorMap, 128 bytes each) of the split X operands
   alignas(64) unsigned char tmap_hi[128] = {};
   alignas(64) unsigned char tmap_lo[128] = {};
@@ -209,8 +222,9 @@ size_t exp_rec_smem(int32_t n_sft, int32_t n_t0, int32_t tpb);
 // Dispatcher kernels of the batch phases, by file (nullptr: not that file's).
 const void* batch_kernel_common(int phase);
 const void* batch_kernel_rect(int phase);
-const void* batch_kernel_exp(int phase);
-const void* batch_kernel_exp_rec(int phase);
+// The exp scan phases have one dispatcher per scan width.
+const void* batch_kernel_exp(int phase, int lanes);
+const void* batch_kernel_exp_rec(int phase, int lanes);
 const void* batch_kernel_fixup(int phase);
 cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,

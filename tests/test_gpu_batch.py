@@ -85,16 +85,31 @@ def test_batch_equals_single_plans_and_oracle(insts, budget, autotune):
         assert info["waves"] > 1
     # one persistent launch per phase and wave
     assert info["launches_per_run"] <= fm.binding.N_BATCH_PHASES * info["waves"]
+    first = None
     for rep in range(2):                        # graph replays give the same bits
         b.run()
         assert b.status() == fm.FMAP_OK
         torch.cuda.synchronize()
-        for k, inst in enumerate(insts):
-            got = b.maps[k].cpu().numpy()
-            gs = fm.summary_to_numpy(b.sums[k][: inst.n_templates])
-            ref_m, ref_s = _single(inst, devs[k])
-            assert np.array_equal(got, ref_m), k
-            assert gs.tobytes() == ref_s.tobytes(), k
+        out = [(b.maps[k].cpu().numpy(), fm.summary_to_numpy(b.sums[k][: inst.n_templates]))
+               for k, inst in enumerate(insts)]
+        if first is None:
+            first = out
+            continue
+        for (m0, s0), (m1, s1) in zip(first, out):
+            assert np.array_equal(m0, m1) and s0.tobytes() == s1.tobytes()
+    # Single plans give the same maps and summaries up to rounding: a batch
+    # scans short exponential data sets with fewer threads per tau, which
+    # changes only the order of the additions.
+    for k, inst in enumerate(insts):
+        got, gs = first[k]
+        ref_m, ref_s = _single(inst, devs[k])
+        if inst.grid.window == RECT:
+            assert np.array_equal(got, ref_m) and gs.tobytes() == ref_s.tobytes(), k
+            continue
+        assert np.allclose(got, ref_m, rtol=1e-5, atol=1e-5), k
+        assert np.array_equal(gs["n_valid"], ref_s["n_valid"]), k
+        assert np.allclose(gs["max2F"], ref_s["max2F"], rtol=1e-5, atol=1e-5), k
+        assert np.allclose(gs["logB"], ref_s["logB"], rtol=0, atol=1e-5, equal_nan=True), k
     for k in (0, 1, 3, 5, len(insts) - 2):
         inst = insts[k]
         ref, valid, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, inst.grid.as_tuple(),
