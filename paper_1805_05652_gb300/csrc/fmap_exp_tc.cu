@@ -104,20 +104,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+// The three products of one MMA K step, hi*hi (accumulating if acc != 0),
+// hi*lo and lo*hi, into the accumulator at d; the B descriptors are given as
+// their low words (start address) and the common high word.
 template <bool BF16>
-__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
-                                       uint32_t idesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_kstep(uint32_t d, uint32_t a_hi, uint32_t a_lo,
+                                          uint32_t bh_lo, uint32_t bl_lo, uint32_t b_hi32,
+                                          uint32_t idesc, uint32_t acc) {
   if constexpr (BF16) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        "{\n .reg .pred p, t;\n .reg .b64 bh, bl;\n setp.ne.b32 p, %7, 0;\n"
+        " setp.eq.b32 t, %6, %6;\n mov.b64 bh, {%3, %5};\n mov.b64 bl, {%4, %5};\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], bh, %6, p;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], bl, %6, t;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], bh, %6, t;\n}" ::"r"(d),
+        "r"(a_hi), "r"(a_lo), "r"(bh_lo), "r"(bl_lo), "r"(b_hi32), "r"(idesc), "r"(acc)
         : "memory");
   } else {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        "{\n .reg .pred p, t;\n .reg .b64 bh, bl;\n setp.ne.b32 p, %7, 0;\n"
+        " setp.eq.b32 t, %6, %6;\n mov.b64 bh, {%3, %5};\n mov.b64 bl, {%4, %5};\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], bh, %6, p;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], bl, %6, t;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], bh, %6, t;\n}" ::"r"(d),
+        "r"(a_hi), "r"(a_lo), "r"(bh_lo), "r"(bl_lo), "r"(b_hi32), "r"(idesc), "r"(acc)
         : "memory");
   }
 }
@@ -142,6 +152,19 @@ __device__ __forceinline__ uint32_t pack_bf16(float even, float odd) {
   uint32_t y;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(y) : "f"(odd), "f"(even));
   return y;
+}
+__device__ __forceinline__ void mul_x2(float& r0, float& r1, float a0, float a1, float b) {
+  asm("{\n.reg .b64 a, b, d;\nmov.b64 a, {%2, %3};\nmov.b64 b, {%4, %4};\n"
+      "mul.rn.f32x2 d, a, b;\nmov.b64 {%0, %1}, d;\n}"
+      : "=f"(r0), "=f"(r1)
+      : "f"(a0), "f"(a1), "f"(b));
+}
+__device__ __forceinline__ void sub_x2(float& r0, float& r1, float a0, float a1, float b0,
+                                       float b1) {
+  asm("{\n.reg .b64 a, b, d;\nmov.b64 a, {%2, %3};\nmov.b64 b, {%4, %5};\n"
+      "sub.rn.f32x2 d, a, b;\nmov.b64 {%0, %1}, d;\n}"
+      : "=f"(r0), "=f"(r1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
@@ -270,35 +293,41 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
     }
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer ----------------
+    // One thread issues every MMA of the CTA, so its own loop is on the
+    // pipeline's critical path: stage, phase, TMEM column and descriptor
+    // address advance by additions, and no descriptor is rebuilt per K-tile.
     if (lane == 0) {
       const uint32_t idesc = idesc_of(BF16, N);
-      int done = 0;
+      const uint64_t d0 = sdesc_sw128(smem_u32(smem));
+      const uint32_t d_lo0 = (uint32_t)d0, d_hi = (uint32_t)(d0 >> 32);
+      const uint32_t op16 = op_bytes >> 4, stage16 = (2 * op_bytes) >> 4;
+      uint32_t d_lo = d_lo0, a_st = tmem + a_col0, par = 0;
+      int s = 0;
       for (int it = 0; it < n_kt; ++it) {
-        const int s = it % kStages;
-        const uint32_t par = (it / kStages) & 1;
         if (!mbar_wait(&bar_full_b[s], par, &s_abort) || !mbar_wait(&bar_full_a[s], par, &s_abort)) {
           atomicExch(&s_abort, 1);
           break;
         }
         tc_fence_after();
-        const uint32_t a_hi = tmem + a_col0 + (uint32_t)(s * kAColsPerStage);
-        const uint32_t a_lo = a_hi + 32u;
-        const uint32_t sb = smem_u32(smem + (size_t)s * 2 * op_bytes);
-        const uint64_t b_hi = sdesc_sw128(sb);
-        const uint64_t b_lo = sdesc_sw128(sb + op_bytes);
 #pragma unroll
         for (int ks = 0; ks < NKS; ++ks) {
-          const uint32_t ac = (uint32_t)(ks * 8);          // 8 TMEM columns per MMA K step
-          const uint64_t bk = (uint64_t)((ks * 32) >> 4);  // 32 bytes per MMA K step
-          mma_ts<BF16>(tmem, a_hi + ac, b_hi + bk, idesc, (it | ks) != 0);
-          mma_ts<BF16>(tmem, a_hi + ac, b_lo + bk, idesc, 1u);
-          mma_ts<BF16>(tmem, a_lo + ac, b_hi + bk, idesc, 1u);
+          // 8 TMEM columns and 32 bytes of the B rows per MMA K step
+          const uint32_t ac = (uint32_t)(ks * 8), bk = (uint32_t)((ks * 32) >> 4);
+          mma_kstep<BF16>(tmem, a_st + ac, a_st + 32u + ac, d_lo + bk, d_lo + op16 + bk, d_hi,
+                          idesc, (it > 0 || ks > 0) ? 1u : 0u);
         }
         mma_commit(&bar_empty[s]);
-        done = it + 1;
+        if (++s == kStages) {
+          s = 0;
+          par ^= 1u;
+          d_lo = d_lo0;
+          a_st = tmem + a_col0;
+        } else {
+          d_lo += stage16;
+          a_st += (uint32_t)kAColsPerStage;
+        }
       }
       if (n_kt > 0) mma_commit(&bar_acc);
-      (void)done;
     }
   } else {
     // ---------------- W generators, then the epilogue ----------------
@@ -364,10 +393,13 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
             w[4 * v + 2] = tab_weight(su * d4.z, s_tab, p.n_tab);
             w[4 * v + 3] = tab_weight(su * d4.w, s_tab, p.n_tab);
           } else {
-            w[4 * v] = ex2(c2 * d4.x);
-            w[4 * v + 1] = ex2(c2 * d4.y);
-            w[4 * v + 2] = ex2(c2 * d4.z);
-            w[4 * v + 3] = ex2(c2 * d4.w);
+            float e0, e1, e2, e3;
+            mul_x2(e0, e1, d4.x, d4.y, c2);
+            mul_x2(e2, e3, d4.z, d4.w, c2);
+            w[4 * v] = ex2(e0);
+            w[4 * v + 1] = ex2(e1);
+            w[4 * v + 2] = ex2(e2);
+            w[4 * v + 3] = ex2(e3);
           }
         }
         if (!__all_sync(0xffffffffu, cnt >= HALF)) {
@@ -379,8 +411,10 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
           for (int j = 0; j < 16; ++j) {
             const uint32_t hp = pack_bf16(w[2 * j], w[2 * j + 1]);
             const float he = __uint_as_float(hp << 16), ho = __uint_as_float(hp & 0xffff0000u);
+            float le, lo;
+            sub_x2(le, lo, w[2 * j], w[2 * j + 1], he, ho);
             vhi[j] = hp;
-            vlo[j] = pack_bf16(w[2 * j] - he, w[2 * j + 1] - ho);
+            vlo[j] = pack_bf16(le, lo);
           }
         } else {
           // the MMA reads TF32 operands as FP32 bit patterns and ignores the
