@@ -9,8 +9,10 @@
 // The data sums go through the same contraction kernels as the exponential
 // window (W generated from the table instead of exp2).  The antenna sums
 // have no recurrence for a generic w, so this file sums them directly over
-// each window: one block per (t0 row, 128 tau cells, antenna set), the
-// block's atoms staged in shared memory, every cell accumulating its window
+// each window: one block per (t0 row, 128 tau cells, antenna set), each warp
+// staging the atoms of its 32 cells' windows in shared memory (up to the
+// longest of them, so that a warp never waits for another), every cell
+// accumulating its window
 // by cascaded (Sum2) summation with exact products (the FP32 weights act as a
 // slightly perturbed window, the same for A, B and C; the sums carry about
 // twice-working-precision accuracy, enough for D = AB - C^2 up to AB/D = 100).
@@ -22,6 +24,7 @@ namespace fmap {
 
 constexpr int kTabCells = 128;   // tau cells of a block (one t0 row)
 constexpr int kTabKC = 64;       // atoms staged per round
+constexpr int kTabWarps = kTabCells / 32;
 
 // S += a b in the cascaded form of Ogita, Rump and Oishi's Sum2 with an exact
 // product: S.h is the plain FP32 running sum, S.l collects the product's
@@ -45,11 +48,10 @@ k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t
                 int32_t n_tab, const float* __restrict__ antenna,
                 const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
                 Coef* __restrict__ coef, uint32_t* __restrict__ bits) {
-  __shared__ float s_t[kTabKC];
-  __shared__ float s_a[3][kTabKC];
+  __shared__ float s_t[kTabWarps][kTabKC];
+  __shared__ float s_a[kTabWarps][3][kTabKC];
   __shared__ float2 s_tab[kTabMax + 1];
-  __shared__ int32_t s_jmax;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int32_t nblk = (g.n_tau + kTabCells - 1) / kTabCells;
   const int32_t m = (int32_t)(blockIdx.x / nblk);
   const int32_t nn = (int32_t)(blockIdx.x - m * nblk) * kTabCells + tid;
@@ -60,12 +62,8 @@ k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t
   for (int k = tid; k <= n_tab; k += kTabCells) s_tab[k] = wtab[k];
   const int32_t i0 = i0tab[m];
   const int32_t jc = in_grid ? jend[cell] : i0;
-  if (tid == 0) s_jmax = i0;
-  __syncthreads();
-  const int32_t jw = __reduce_max_sync(0xffffffffu, (unsigned)jc);
-  if ((tid & 31) == 0) atomicMax(&s_jmax, jw);
-  __syncthreads();
-  const int32_t jmax = s_jmax;
+  __syncthreads();   // the table is staged
+  const int32_t jmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)jc);   // the warp's
   const int64_t tb = n > 0 ? *t_base : 0;
   const int64_t t0rel = grid_t0(g, ax, m) - tb;
   const float su =
@@ -73,21 +71,21 @@ k_table_antenna(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t
   const float* ant = antenna + (int64_t)ta * 3 * n;
   FF S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   for (int32_t k0 = i0; k0 < jmax; k0 += kTabKC) {
-    __syncthreads();
-    for (int e = tid; e < kTabKC; e += kTabCells) {
+    __syncwarp();   // the warp's previous round is read
+    for (int e = lane; e < kTabKC; e += 32) {
       const int32_t a = k0 + e;
       const bool in = a < jmax;
-      s_t[e] = in ? (float)((int64_t)rel_t[a] - t0rel) : 0.0f;
+      s_t[w][e] = in ? (float)((int64_t)rel_t[a] - t0rel) : 0.0f;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) s_a[c][e] = in ? ant[(int64_t)c * n + a] : 0.0f;
+      for (int c = 0; c < 3; ++c) s_a[w][c][e] = in ? ant[(int64_t)c * n + a] : 0.0f;
     }
-    __syncthreads();
+    __syncwarp();
     const int kend = min(kTabKC, jc - k0);   // this cell's atoms in the round
     for (int kk = 0; kk < kend; ++kk) {
-      const float w = tab_weight(s_t[kk] * su, s_tab, n_tab);
-      const float w2 = w * w;
+      const float wt = tab_weight(s_t[w][kk] * su, s_tab, n_tab);
+      const float w2 = wt * wt;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) ff_add_prod(S[c], w2, s_a[c][kk]);
+      for (int c = 0; c < 3; ++c) ff_add_prod(S[c], w2, s_a[w][c][kk]);
     }
   }
   if (in_grid)
