@@ -52,7 +52,7 @@ typedef enum {
   FMAP_ERR_TIMEOUT = -4,     /* a bounded wait gave up */
   FMAP_ERR_BUSY = -5,        /* server full / ticket unknown */
   FMAP_ERR_DATA = -6,        /* timestamps not strictly increasing or span >= 2^31 s */
-  FMAP_ERR_UNSUPPORTED = -7  /* valid request this build cannot serve */
+  FMAP_ERR_UNSUPPORTED = -7  /* valid request outside what the library supports */
 } fmap_status;
 
 /* FMAP_TABLE: a generic window function w(x), x = (t - t0) / tau, given as a
