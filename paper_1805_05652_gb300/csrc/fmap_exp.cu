@@ -185,11 +185,13 @@ k_exp_suffix(const float4* __restrict__ perm, const TauTab* __restrict__ tauc, i
 constexpr float kTailExact = 1.0f / 32.0f;
 
 // A, B, C of the cell (t0, tau) from the suffix sums E of its tau, then its
-// coefficients; c2 = -2 log2(e) / tau, inv_tau = 1 / tau.
-__device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t, int32_t n,
-                                              int64_t t0, float c2,
-                                              double inv_tau, int32_t i0, int32_t j,
-                                              int64_t t_base, const float2* E) {
+// coefficients; c2 = -2 log2(e) / tau, inv_tau = 1 / tau.  t_i0 and t_j are
+// the relative times of atoms i0 and j (read only when the window holds
+// atoms, and t_j only when j < n).
+__device__ __forceinline__ Coef exp_cell_coef_t(int32_t t_i0, int32_t t_j, int32_t n,
+                                                int64_t t0, float c2,
+                                                double inv_tau, int32_t i0, int32_t j,
+                                                int64_t t_base, const float2* E) {
   const int32_t count = j - i0;
   FF S[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   if (count > 0) {
@@ -199,11 +201,11 @@ __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t,
     // only): FP32 exp2 is accurate enough.  The tail is FP32 exp2 while it is
     // small (~e^{-6} of the window sum for the default 3 tau cut), FP64 exp
     // otherwise.
-    const int64_t d0 = (int64_t)rel_t[i0] - t0rel;
+    const int64_t d0 = (int64_t)t_i0 - t0rel;
     const float pre = d0 == 0 ? 1.0f : ex2_approx(c2 * (float)d0);
     FF tail{0.0f, 0.0f};
     if (j < n) {
-      const int32_t dj = rel_t[j] - rel_t[i0];
+      const int32_t dj = t_j - t_i0;
       tail.h = ex2_approx(c2 * (float)dj);
       if (tail.h > kTailExact) tail = ff_of(exp(-2.0 * (double)dj * inv_tau));
     }
@@ -215,6 +217,19 @@ __device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t,
   }
   return make_coef_ff(S[0], S[1], S[2], count);
 }
+__device__ __forceinline__ Coef exp_cell_coef(const int32_t* __restrict__ rel_t, int32_t n,
+                                              int64_t t0, float c2,
+                                              double inv_tau, int32_t i0, int32_t j,
+                                              int64_t t_base, const float2* E) {
+  const bool any = j > i0;
+  return exp_cell_coef_t(any ? rel_t[i0] : 0, any && j < n ? rel_t[j] : 0, n, t0, c2, inv_tau,
+                         i0, j, t_base, E);
+}
+
+// cells a thread loads ahead in the antenna kernels (fewer for the narrowest
+// scan, whose batch variant runs at the highest occupancy)
+template <int NT>
+constexpr int cells_in_flight() { return NT >= 128 ? 4 : 2; }
 
 // Fused antenna step for data sets that fit shared memory: one block per
 // (tau_n, antenna set) keeps the suffix sums in shared memory and writes the
@@ -235,11 +250,33 @@ __device__ __forceinline__ void exp_antenna_body(const int32_t* __restrict__ rel
   antenna_suffix<NT>(perm_ant + (int64_t)ta * perm_entries(n, NT), n, g, tt, s_E, sR, sS);
   __syncthreads();
   const int64_t tb = n > 0 ? *t_base : 0;
-  for (int32_t m = threadIdx.x; m < g.n_t0; m += NT) {
-    const int64_t cell = (int64_t)m * g.n_tau + ni;
-    store_coef(coef, bits, (int64_t)ta * cells + cell,
-               exp_cell_coef(rel_t, n, grid_t0(g, ax, m), tt->c2[1], tt->inv_tau, i0tab[m],
-                             jend[cell], tb, s_E));
+  // U cells per thread at a time: their window indices, then the atom times
+  // those select, are all loaded before any is used, so the loads' latencies
+  // overlap.
+  constexpr int U = cells_in_flight<NT>();
+  for (int32_t m0 = threadIdx.x; m0 < g.n_t0; m0 += NT * U) {
+    int32_t i0v[U], jv[U], ti[U], tj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int32_t m = m0 + u * NT;
+      const bool in = m < g.n_t0;
+      i0v[u] = in ? i0tab[m] : 0;
+      jv[u] = in ? jend[(int64_t)m * g.n_tau + ni] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool any = jv[u] > i0v[u];
+      ti[u] = any ? rel_t[i0v[u]] : 0;
+      tj[u] = any && jv[u] < n ? rel_t[jv[u]] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int32_t m = m0 + u * NT;
+      if (m < g.n_t0)
+        store_coef(coef, bits, (int64_t)ta * cells + (int64_t)m * g.n_tau + ni,
+                   exp_cell_coef_t(ti[u], tj[u], n, grid_t0(g, ax, m), tt->c2[1], tt->inv_tau,
+                                   i0v[u], jv[u], tb, s_E));
+    }
   }
 }
 

@@ -240,11 +240,24 @@ def test_table_window_api_checks():
     ex.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "rec"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "rec", "tf32", "bf16x3"])
 def test_exp_per_template_antenna(prec):
     grid = Grid(0, T_SFT, 20, T_SFT, T_SFT, 140, EXP)
     inst = synth.make_instance(44, n_det=1, presence=0.9, n_merged=200, n_templates=3,
                                grid=grid, shared_antenna=False)
+    _parity(inst, prec)
+
+
+@pytest.mark.parametrize("shared", [True, False])
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_exp_tensor_core_template_chunks(prec, shared):
+    """70 templates: one full 64-template chunk of the contraction (N = 256
+    data columns, one CTA per SM) and a ragged second chunk of 6 templates,
+    over 2 x 128-cell tiles and a tail of tau."""
+    grid = Grid(0, 2 * T_SFT, 9, T_SFT, T_SFT, 290, EXP)
+    inst = synth.make_instance(46, n_det=2, presence=0.9, n_merged=260, n_templates=70,
+                               grid=grid, shared_antenna=shared,
+                               injections=[(69, EXP, 4 * T_SFT, 40 * T_SFT, 150.0)])
     _parity(inst, prec)
 
 
