@@ -293,9 +293,11 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
     }
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer ----------------
-    // One thread issues every MMA of the CTA, so its own loop is on the
-    // pipeline's critical path: stage, phase, TMEM column and descriptor
-    // address advance by additions, and no descriptor is rebuilt per K-tile.
+    // One thread issues every MMA of the CTA, so work added to its loop delays
+    // them all: stage, phase, TMEM column and descriptor address advance by
+    // additions, and no descriptor is rebuilt per K-tile.  (The descriptor's
+    // start-address field, bits 0-13 = address / 16, cannot carry into the
+    // next field: shared memory ends below 2^18 bytes.)
     if (lane == 0) {
       const uint32_t idesc = idesc_of(BF16, N);
       const uint64_t d0 = sdesc_sw128(smem_u32(smem));
