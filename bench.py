@@ -123,9 +123,18 @@ def load_peaks():
 
 # ------------------------------------------------------------------ clocks --
 
+# default timed steps: about a second of device work, so that the clock
+# samples (every 20 ms) fall inside the timed region
+DEFAULT_STEPS = {"exp16": 1000, "batch_rect": 100, "uneven": 5}
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed
-    region (200 ms period)."""
+    """nvidia-smi samples of SM clock and throttle reasons (every 20 ms).
+    begin() / end() mark the timed region on the host clock; the summary
+    keeps the samples that arrived inside it (falling back to all samples,
+    and saying so, when the region is shorter than the sampling period)."""
+
+    PERIOD_MS = 20
 
     FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -137,12 +146,15 @@ class ClockSampler:
         self.proc = None
         self.thread = None
         self.error = None
+        self.t_begin = None
+        self.t_end = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
         except OSError as e:
             self.error = str(e)
             return
@@ -153,7 +165,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append((time.monotonic(), parts))
+
+    def begin(self):
+        self.t_begin = time.monotonic()
+
+    def end(self):
+        self.t_end = time.monotonic()
 
     def stop(self):
         if self.proc:
@@ -168,9 +186,16 @@ class ClockSampler:
     def summary(self):
         if self.error:
             return {"error": self.error}
-        rows = [r for r in self.rows if not self.uuid or self.uuid in r[0]] or self.rows
+        rows = [(t, r) for t, r in self.rows if not self.uuid or self.uuid in r[0]] or self.rows
         if not rows:
             return {"error": "no nvidia-smi samples"}
+        # a line arrives a few ms after its sample: allow one period of lag
+        lag = self.PERIOD_MS / 1e3
+        inside = [(t, r) for t, r in rows if self.t_begin is not None and self.t_end is not None
+                  and self.t_begin <= t <= self.t_end + lag]
+        scope = "timed region" if inside else "whole run (timed region shorter than a sample)"
+        n_total = len(rows)
+        rows = [r for _, r in (inside or rows)]
 
         def num(x):
             try:
@@ -185,7 +210,8 @@ class ClockSampler:
                           "Not" not in v})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "samples_total": n_total, "scope": scope,
+                "period_ms": self.PERIOD_MS}
 
 
 # ------------------------------------------------------------ cpu baseline --
@@ -239,7 +265,9 @@ def cpu_baseline(inst, target_s=12.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: about a second of work: exp16 1000, "
+                         "batch_rect 100, uneven 5; the reference arm 5)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None)
@@ -264,6 +292,8 @@ def main():
                     help="uneven workload: batch workspace budget (GB)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.steps is None:
+        args.steps = 5 if args.impl == "reference" else DEFAULT_STEPS.get(args.workload, 30)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,7 +357,7 @@ def main():
     def step(p):
         p.compute(t, ant, x, out_map=out_map, out_summary=out_sum, stream=stream)
 
-    def timed(p, steps, warmup):
+    def timed(p, steps, warmup, sampler=None):
         for _ in range(warmup):
             step(p)
         torch.cuda.synchronize()
@@ -337,12 +367,16 @@ def main():
         fm.fmap_plan_enable_timing(p.handle, True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
+        if sampler:
+            sampler.begin()
         for k in range(steps):
             flush.fill_(float(k))                     # untimed: evict the L2
             evs[k][0].record(stream)
             step(p)
             evs[k][1].record(stream)
         torch.cuda.synchronize()
+        if sampler:
+            sampler.end()
         if dist:
             dist.barrier()
         per = [a.elapsed_time(b) for a, b in evs]
@@ -357,7 +391,7 @@ def main():
         pass
     clocks = ClockSampler(uuid)
     clocks.start()
-    per, phase_ms, launches = timed(plan, args.steps, args.warmup)
+    per, phase_ms, launches = timed(plan, args.steps, args.warmup, clocks)
     clocks.stop()
     torch.cuda.synchronize()
     st = plan.status()
@@ -517,12 +551,14 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
     clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    clocks.begin()
     for k in range(args.steps):
         flush.fill_(float(k))
         evs[k][0].record(stream)
         batch.run(stream)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     clocks.stop()
     if dist:
         dist.barrier()
