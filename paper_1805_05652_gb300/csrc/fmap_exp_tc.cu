@@ -33,7 +33,6 @@ constexpr int kGenWarps = 8;
 constexpr int kMmaWarp = 8;
 constexpr int kTmaWarp = 9;
 constexpr int kThreads = 320;
-constexpr int kStages = 3;
 constexpr int kRows = 128;
 constexpr int kAColsPerStage = 64;   // hi (32 columns) + lo (32 columns)
 constexpr int kDtCap = 4096;          // atoms of relative times staged per refill (16 KB)
@@ -199,7 +198,7 @@ struct Params {
   int32_t shared_antenna;
   int32_t n_templates;
   int32_t n_cols;      // N of this launch (multiple of 64, <= 256)
-  int32_t tmem_cols;   // power of two >= n_cols + kStages * kAColsPerStage
+  int32_t tmem_cols;   // power of two >= n_cols + NS * kAColsPerStage
   int32_t nblk;        // 128-cell blocks per t0 row
   float* map;
   Partial* parts;
@@ -209,7 +208,7 @@ struct Params {
 
 // TAB: weights from the window table (FMAP_TABLE grids) instead of exp2; the
 // table sits in shared memory after the staged relative times.
-template <bool BF16, bool TAB>
+template <bool BF16, bool TAB, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
 k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
          const Params p) {
@@ -219,6 +218,7 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
   constexpr int NKS = KT / KSTEP;             // MMAs per product and K-tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int kStages = NS;                 // A/B pipeline stages
   float* s_dt = (float*)(smem + (size_t)kStages * 2 * p.n_cols * 128);
   float2* s_tab = (float2*)(s_dt + kDtCap);   // TAB only
   __shared__ uint64_t bar_full_b[kStages], bar_full_a[kStages], bar_empty[kStages], bar_acc;
@@ -617,18 +617,22 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   prm.shared_antenna = a->shared_antenna;
   prm.n_templates = T;
   prm.n_cols = N;
+  // three stages, or two where that keeps a CTA within half the SM's TMEM
+  // columns (N = 128): two resident CTAs run two MMA streams side by side
+  const bool tab = g.window == FMAP_TABLE;   // (one CTA per SM at any N: three stages)
+  const int NS =
+      (!tab && N + 3 * tc::kAColsPerStage > 256 && N + 2 * tc::kAColsPerStage <= 256) ? 2 : 3;
   int tcols = 32;
-  while (tcols < N + tc::kStages * tc::kAColsPerStage) tcols *= 2;
+  while (tcols < N + NS * tc::kAColsPerStage) tcols *= 2;
   prm.tmem_cols = tcols;
   prm.nblk = (g.n_tau + tc::kRows - 1) / tc::kRows;
   prm.map = d_2F;
   prm.parts = p->ws.partials;
   prm.stride = p->part_stride;
   prm.err = p->ws.dev_err;
-  // shared memory: 3 stages x (hi + lo) x N rows x 128 B; at least enough to
+  // shared memory: NS stages x (hi + lo) x N rows x 128 B; at least enough to
   // keep the resident CTAs within the 512 TMEM columns of an SM
-  const bool tab = g.window == FMAP_TABLE;
-  size_t smem = (size_t)tc::kStages * 2 * N * 128 + sizeof(float) * tc::kDtCap + 1024 +
+  size_t smem = (size_t)NS * 2 * N * 128 + sizeof(float) * tc::kDtCap + 1024 +
                 (tab ? sizeof(float2) * (kTabMax + 1) : 0);
   const size_t min_smem = tcols > 256 ? 120 * 1024 : 80 * 1024;
   smem = std::max(smem, min_smem);
@@ -641,9 +645,13 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
     kern<<<grid, tc::kThreads, smem, s>>>(*mh, *ml, prm);
   };
   if (bf16) {
-    if (tab) run(tc::k_exp_tc<true, true>); else run(tc::k_exp_tc<true, false>);
+    if (tab) run(tc::k_exp_tc<true, true, 3>);
+    else if (NS == 2) run(tc::k_exp_tc<true, false, 2>);
+    else run(tc::k_exp_tc<true, false, 3>);
   } else {
-    if (tab) run(tc::k_exp_tc<false, true>); else run(tc::k_exp_tc<false, false>);
+    if (tab) run(tc::k_exp_tc<false, true, 3>);
+    else if (NS == 2) run(tc::k_exp_tc<false, false, 2>);
+    else run(tc::k_exp_tc<false, false, 3>);
   }
   p->launches += 1;
   return cudaGetLastError();
