@@ -108,7 +108,7 @@ def count_terms(grid, t):
 # DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
 # capture of the unchanged kernel on the workload (a 64-template cut of the
 # rect batch, scaled to its 1024 templates: the traffic grows with them).
-NCU_TRAFFIC = {("exp16", "bf16x3"): 31.4e6,
+NCU_TRAFFIC = {("exp16", "bf16x3"): 31.5e6,
                ("batch_rect", "fp64"): 1078.0e6 * 16}
 
 
