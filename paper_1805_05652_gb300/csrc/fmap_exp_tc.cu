@@ -536,8 +536,14 @@ __global__ void k_split_x(const float* __restrict__ fafb, int32_t n_sft, int32_t
 
 static int n_pad_of(int32_t n_sft) { return ((std::max(n_sft, 1) + 63) / 64) * 64; }
 // N of the MMA: 4 columns per template, a multiple of 64 (the epilogue reads
-// the accumulator 32 columns at a time per half), at most 256.
-static int n_cols_of(int32_t T) { return std::min(256, ((4 * std::max(T, 1) + 63) / 64) * 64); }
+// the accumulator 32 columns at a time per half).  Up to 48 templates one
+// chunk of N <= 192; beyond, chunks of N = 128, which run two CTAs per SM
+// (measured on the exp16 atoms: 64 templates 1.36 ms as two N = 128 chunks
+// against 1.51 ms as one N = 256 chunk; 48 templates 1.25 ms as one N = 192
+// chunk against 1.35 ms as two N = 128 chunks).
+static int n_cols_of(int32_t T) {
+  return T <= 48 ? ((4 * std::max(T, 1) + 63) / 64) * 64 : 128;
+}
 
 bool exp_tc_available(fmap_precision prec) { return prec == FMAP_TF32 || prec == FMAP_BF16X3; }
 

@@ -252,9 +252,9 @@ def test_exp_per_template_antenna(prec):
 @pytest.mark.parametrize("n_templates", [25, 70])
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
 def test_exp_tensor_core_template_chunks(prec, n_templates, shared):
-    """25 templates: one chunk of N = 128 data columns (100 used); 70: one
-    full 64-template chunk (N = 256, one CTA per SM) and a ragged second chunk
-    of 6 templates; over 2 x 128-cell tiles and a tail of tau."""
+    """25 templates: one chunk of N = 128 data columns (100 used); 70: two
+    full 32-template chunks of N = 128 and a ragged third of 6 templates; over
+    2 x 128-cell tiles and a tail of tau."""
     grid = Grid(0, 2 * T_SFT, 9, T_SFT, T_SFT, 290, EXP)
     inst = synth.make_instance(46, n_det=2, presence=0.9, n_merged=260,
                                n_templates=n_templates, grid=grid, shared_antenna=shared,
