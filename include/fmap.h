@@ -26,7 +26,8 @@
  *     its workspace.  Compute calls are asynchronous on the given stream and
  *     never throw; errors are status codes.  Data errors found on the device
  *     (non-increasing timestamps, a time span >= 2^31 s) are latched in the
- *     plan and returned by fmap_plan_status().
+ *     plan and returned by fmap_plan_status(); so are non-finite atoms
+ *     (FMAP_ERR_NONFINITE), which leave that call's outputs undefined.
  *   - A plan serialises its own calls: do not use one plan from two host
  *     threads at once, nor on two streams whose work overlaps.
  */
@@ -52,7 +53,8 @@ typedef enum {
   FMAP_ERR_TIMEOUT = -4,     /* a bounded wait gave up */
   FMAP_ERR_BUSY = -5,        /* server full / ticket unknown */
   FMAP_ERR_DATA = -6,        /* timestamps not strictly increasing or span >= 2^31 s */
-  FMAP_ERR_UNSUPPORTED = -7  /* valid request outside what the library supports */
+  FMAP_ERR_UNSUPPORTED = -7, /* valid request outside what the library supports */
+  FMAP_ERR_NONFINITE = -8    /* an atom (antenna or data row) is NaN or infinite */
 } fmap_status;
 
 /* FMAP_TABLE: a generic window function w(x), x = (t - t0) / tau, given as a
@@ -116,15 +118,24 @@ typedef struct {
 } fmap_atoms;
 
 /* Per-template result (32 bytes).  n_valid = 0 gives max2F = 0, m = n = -1,
- * logB = NaN. */
+ * logB = NaN.  flags: FMAP_SUMMARY_* bits (see fmap_plan_set_refine). */
 typedef struct {
   float max2F;
   int32_t m;
   int32_t n;
-  int32_t reserved;
+  int32_t flags;
   double logB;
   int64_t n_valid;
 } fmap_summary;
+
+enum {
+  /* the cells nearest the maximum were recomputed from their atoms in FP64
+   * and max2F, the argmax and logB use those values */
+  FMAP_SUMMARY_REFINED = 1u,
+  /* every cell whose fast 2F lay within the fast path's error bound of the
+   * maximum was among them: the argmax was decided on FP64 values */
+  FMAP_SUMMARY_ARGMAX_EXACT = 2u
+};
 
 /* fmap_plan flags */
 enum {
@@ -140,7 +151,12 @@ enum {
    * template's suffix sums in shared memory; FMAP_ERR_UNSUPPORTED otherwise);
    * the per-cell window records of one tau are staged there too when
    * 24 n_sft + 32 n_t0 <= ~220 KB, else recomputed per template. */
-  FMAP_PLAN_EXP_RECURRENCE = 2u
+  FMAP_PLAN_EXP_RECURRENCE = 2u,
+  /* the plan holds a [T][n_t0][n_tau] float map of its own (the workspace
+   * grows by 4 T n_t0 n_tau bytes), used by summary-only compute calls
+   * (d_2F = NULL) so that their summaries can be refined (fmap_plan_set_refine);
+   * without it a summary-only call reports the unrefined reductions */
+  FMAP_PLAN_MAP_BUFFER = 4u
 };
 
 typedef struct fmap_plan_s fmap_plan_t;
@@ -179,6 +195,37 @@ size_t fmap_workspace_bytes(const fmap_grid* grid, int32_t n_sft, int32_t n_temp
 
 /* Additive constant of logB (prior normalisation; default 0). */
 fmap_status fmap_plan_set_log_prior(fmap_plan_t* plan, double log_prior_const);
+
+/*
+ * Refinement of the reductions (Sec. 2 Eq. F_OSG: the argmax is the
+ * detection candidate and e^F the odds, so both are decided on FP64 values).
+ * After a compute call's fast map and reductions, per template the cells
+ * whose fast 2F lies within 16 of the fast maximum (at most max_cells of
+ * them, the highest; a histogram of 256 bins picks the cut) are recomputed
+ * from their atoms by the plain FP64 definition (windowed sums, D, Eq.
+ * F_FaFb); their FP64 values replace the fast ones in the map, in max2F, in
+ * the argmax (lowest index on FP64 ties) and in logB (the fast exp-sum has
+ * their fast terms replaced by the FP64 ones).  Summary flags:
+ * FMAP_SUMMARY_REFINED once this ran, FMAP_SUMMARY_ARGMAX_EXACT when the cut
+ * lies below the maximum by more than twice the precision's error bound
+ * (1e-5 relative for FMAP_FP64, 1e-3 otherwise, floor 1), so that no other
+ * cell can hold the maximum.  max_cells: 0 turns refinement off, < 0 selects
+ * the default (64 for FMAP_FP64 plans, 512 otherwise), at most 4096.  Needs
+ * the map: the caller's d_2F, else the plan's own (FMAP_PLAN_MAP_BUFFER).
+ * Batches do not refine.
+ */
+fmap_status fmap_plan_set_refine(fmap_plan_t* plan, int32_t max_cells);
+
+/*
+ * Limit of every bounded device wait of the plan's kernels (mbarrier waits
+ * on bulk copies and tensor-core stages), in nanoseconds; < 0 restores the
+ * default of 2 s.  0 makes a wait give up as soon as its first poll finds
+ * the stage incomplete.  A wait that gives up latches FMAP_ERR_TIMEOUT
+ * (fmap_plan_status) and the kernel winds down: it issues no further copies,
+ * waits (up to 2 s) for those already in flight, releases its tensor memory
+ * and returns; that call's outputs are undefined.
+ */
+fmap_status fmap_plan_set_wait_limit(fmap_plan_t* plan, int64_t limit_ns);
 
 /*
  * fmap_compute_rect / fmap_compute_exp: the F-map of Eq. (Fmn) for every
@@ -329,6 +376,9 @@ fmap_status fmap_poll(fmap_server_t* server, uint64_t ticket, fmap_summary* h_su
                       float* h_2F, int64_t wait_us);
 fmap_status fmap_server_stats(fmap_server_t* server, int64_t* queued, int64_t* running,
                               int64_t* completed);
+/* The most requests that were running at once (on the GPU together) since
+ * the server was created. */
+fmap_status fmap_server_peak(fmap_server_t* server, int64_t* peak_running);
 
 /*
  * Uneven batches: many independent F-map instances (each with its own atoms,
@@ -381,6 +431,23 @@ fmap_status fmap_batch_info(fmap_batch_t* batch, int32_t* n_waves, int64_t* laun
  * run; must not overlap a run of the same batch (they share work counters). */
 fmap_status fmap_batch_profile(fmap_batch_t* batch, fmap_stream stream, float* phase_ms);
 void fmap_batch_destroy(fmap_batch_t* batch);
+
+/*
+ * Combining summaries of an F-map split by t0 rows (templates and t0 rows are
+ * independent pieces of the map, Sec. 3): shard r computed rows
+ * [m_offsets[r], m_offsets[r] + its n_t0) of every template and holds
+ * summaries [n_shards][n_templates] (HOST arrays), m in its own rows.  Per
+ * template: n_valid adds; max2F is the maximum over shards with valid cells
+ * and the argmax the lowest global (m, n) attaining it; logB =
+ * logsumexp_r(logB_r + ln N_r) - ln N (the shards' common prior constant
+ * rides along); flags are those common to the non-empty shards.  Empty
+ * shards (n_valid = 0) are skipped; all empty gives the empty summary
+ * (max2F = 0, m = n = -1, logB = NaN).  Host only, exact up to FP64
+ * rounding.  FMAP_ERR_ARG on NULL pointers or negative counts.
+ */
+fmap_status fmap_combine_summaries(const fmap_summary* shards, int32_t n_shards,
+                                   int32_t n_templates, const int32_t* m_offsets,
+                                   fmap_summary* out);
 
 /* Host-side window bookkeeping for throughput accounting: over all cells,
  * the total number of (cell, SFT) terms (sum of atoms per window, App. A

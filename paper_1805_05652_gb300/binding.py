@@ -23,12 +23,15 @@ c_vp, c_size = ctypes.c_void_p, ctypes.c_size_t
 # fmap_status
 FMAP_OK, FMAP_PENDING = 0, 1
 FMAP_ERR_ARG, FMAP_ERR_NOMEM, FMAP_ERR_CUDA, FMAP_ERR_TIMEOUT = -1, -2, -3, -4
-FMAP_ERR_BUSY, FMAP_ERR_DATA, FMAP_ERR_UNSUPPORTED = -5, -6, -7
+FMAP_ERR_BUSY, FMAP_ERR_DATA, FMAP_ERR_UNSUPPORTED, FMAP_ERR_NONFINITE = -5, -6, -7, -8
 # fmap_window / fmap_precision / plan flags
 FMAP_RECT, FMAP_EXP, FMAP_TABLE = 0, 1, 2
 FMAP_FP64, FMAP_FP32, FMAP_TF32, FMAP_BF16X3 = 0, 1, 2, 3
 FMAP_PLAN_PER_TEMPLATE_ANTENNA = 1
 FMAP_PLAN_EXP_RECURRENCE = 2
+FMAP_PLAN_MAP_BUFFER = 4
+# fmap_summary.flags
+FMAP_SUMMARY_REFINED, FMAP_SUMMARY_ARGMAX_EXACT = 1, 2
 
 PRECISIONS = {"fp64": FMAP_FP64, "fp32": FMAP_FP32, "tf32": FMAP_TF32, "bf16x3": FMAP_BF16X3}
 
@@ -45,7 +48,7 @@ class fmap_atoms(ctypes.Structure):
 
 
 class fmap_summary(ctypes.Structure):
-    _fields_ = [("max2F", c_f32), ("m", c_i32), ("n", c_i32), ("reserved", c_i32),
+    _fields_ = [("max2F", c_f32), ("m", c_i32), ("n", c_i32), ("flags", c_i32),
                 ("logB", c_f64), ("n_valid", c_i64)]
 
 
@@ -53,7 +56,7 @@ class fmap_batch_item(ctypes.Structure):
     _fields_ = [("grid", fmap_grid), ("atoms", fmap_atoms), ("d_2F", c_vp), ("d_summary", c_vp)]
 
 
-SUMMARY_DTYPE = np.dtype([("max2F", "<f4"), ("m", "<i4"), ("n", "<i4"), ("reserved", "<i4"),
+SUMMARY_DTYPE = np.dtype([("max2F", "<f4"), ("m", "<i4"), ("n", "<i4"), ("flags", "<i4"),
                           ("logB", "<f8"), ("n_valid", "<i8")])
 assert SUMMARY_DTYPE.itemsize == ctypes.sizeof(fmap_summary) == 32
 
@@ -65,7 +68,8 @@ EXPORTS = ("fmap_plan", "fmap_plan_destroy", "fmap_workspace_bytes", "fmap_plan_
            "fmap_submit", "fmap_poll", "fmap_server_stats", "fmap_batch_plan", "fmap_batch_run",
            "fmap_batch_status", "fmap_batch_info", "fmap_batch_profile", "fmap_batch_destroy",
            "fmap_plan_axes", "fmap_plan_count_terms", "fmap_plan_window_table",
-           "fmap_compute_table")
+           "fmap_compute_table", "fmap_plan_set_refine", "fmap_plan_set_wait_limit",
+           "fmap_combine_summaries", "fmap_server_peak")
 FMAP_BATCH_AUTOTUNE = 1
 N_BATCH_PHASES = 15
 FMAP_N_PHASES = 4
@@ -126,6 +130,13 @@ def lib():
     L.fmap_poll.restype = ctypes.c_int
     L.fmap_server_stats.argtypes = [c_vp, P(c_i64), P(c_i64), P(c_i64)]
     L.fmap_server_stats.restype = ctypes.c_int
+    L.fmap_server_peak.argtypes = [c_vp, P(c_i64)]
+    L.fmap_server_peak.restype = ctypes.c_int
+    L.fmap_plan_set_refine.argtypes = [c_vp, c_i32]
+    L.fmap_plan_set_wait_limit.argtypes = [c_vp, c_i64]
+    L.fmap_combine_summaries.argtypes = [c_vp, c_i32, c_i32, c_vp, c_vp]
+    for f in ("fmap_plan_set_refine", "fmap_plan_set_wait_limit", "fmap_combine_summaries"):
+        getattr(L, f).restype = ctypes.c_int
     L.fmap_batch_plan.argtypes = [P(c_vp), c_vp, c_i32, c_size, c_u32]
     L.fmap_batch_run.argtypes = [c_vp, c_vp]
     L.fmap_batch_status.argtypes = [c_vp, c_vp]
@@ -281,6 +292,33 @@ def fmap_plan_status(plan: int) -> int:
     return int(lib().fmap_plan_status(c_vp(plan)))
 
 
+def fmap_plan_set_refine(plan: int, max_cells: int):
+    """FP64 refinement of the cells nearest each template's maximum (0: off,
+    < 0: the precision's default)."""
+    _check(lib().fmap_plan_set_refine(c_vp(plan), int(max_cells)), "fmap_plan_set_refine")
+
+
+def fmap_plan_set_wait_limit(plan: int, limit_ns: int):
+    """Limit of the plan kernels' bounded waits (ns; < 0: the default 2 s)."""
+    _check(lib().fmap_plan_set_wait_limit(c_vp(plan), int(limit_ns)), "fmap_plan_set_wait_limit")
+
+
+def fmap_combine_summaries(shards, m_offsets) -> np.ndarray:
+    """Combine row-shard summaries: ``shards`` [n_shards][T] records
+    (SUMMARY_DTYPE), ``m_offsets`` the first global t0 row of each shard."""
+    arr = np.ascontiguousarray(np.asarray(shards, dtype=SUMMARY_DTYPE))
+    if arr.ndim == 1:
+        arr = arr[None]
+    n_shards, T = int(arr.shape[0]), int(arr.shape[1]) if arr.ndim == 2 else 0
+    offs = np.ascontiguousarray(m_offsets, dtype=np.int32)
+    if offs.shape != (n_shards,):
+        raise ValueError("one row offset per shard")
+    out = np.zeros(T, dtype=SUMMARY_DTYPE)
+    _check(lib().fmap_combine_summaries(_ptr(arr), n_shards, T, _ptr(offs), _ptr(out)),
+           "fmap_combine_summaries")
+    return out
+
+
 def fmap_plan_enable_timing(plan: int, enable: bool = True):
     _check(lib().fmap_plan_enable_timing(c_vp(plan), int(bool(enable))), "fmap_plan_enable_timing")
 
@@ -362,6 +400,13 @@ def fmap_server_stats(server: int):
     _check(lib().fmap_server_stats(c_vp(server), ctypes.byref(q), ctypes.byref(r),
                                    ctypes.byref(c)), "fmap_server_stats")
     return int(q.value), int(r.value), int(c.value)
+
+
+def fmap_server_peak(server: int) -> int:
+    """Most requests running at once since the server was created."""
+    p = c_i64()
+    _check(lib().fmap_server_peak(c_vp(server), ctypes.byref(p)), "fmap_server_peak")
+    return int(p.value)
 
 
 def fmap_batch_plan(items, workspace_budget: int = 0, flags: int = 0) -> int:
@@ -486,6 +531,9 @@ class Server:
     def stats(self):
         return fmap_server_stats(self.handle)
 
+    def peak(self) -> int:
+        return fmap_server_peak(self.handle)
+
     def close(self):
         if getattr(self, "handle", None):
             fmap_server_destroy(self.handle)
@@ -592,3 +640,9 @@ class Plan:
 
     def set_log_prior(self, c: float):
         fmap_plan_set_log_prior(self.handle, c)
+
+    def set_refine(self, max_cells: int):
+        fmap_plan_set_refine(self.handle, max_cells)
+
+    def set_wait_limit(self, limit_ns: int):
+        fmap_plan_set_wait_limit(self.handle, limit_ns)

@@ -17,6 +17,15 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+std::string dev_err_message(uint32_t bits) {
+  std::string m;
+  if (bits & DEV_ERR_ORDER) m += "timestamps are not strictly increasing; ";
+  if (bits & DEV_ERR_SPAN) m += "timestamp span is >= 2^31 s; ";
+  if (bits & DEV_ERR_TIMEOUT) m += "a bounded device wait gave up; ";
+  if (bits & DEV_ERR_NONFINITE) m += "an atom is NaN or infinite; ";
+  return m;
+}
+
 fmap_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
   return FMAP_ERR_CUDA;
@@ -86,7 +95,8 @@ static bool precision_supported(int window, fmap_precision prec) {
 
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
-      esuf, xop, perm_ant, perm_x, perm_gap, tauc, ax, wtab, flag_bits, total;
+      esuf, xop, perm_ant, perm_x, perm_gap, tauc, ax, wtab, flag_bits, tstat, ref_hist, ref_bin,
+      ref_n, ref_cell, ref_fast, ref_val, own_map, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -129,6 +139,18 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
   L.flag_bits = take(sizeof(uint32_t) * (size_t)flag_words((int64_t)entries));
   L.n_flag = take(sizeof(int32_t));
   L.flag_list = take(sizeof(int64_t) * entries);
+  if (!(flags & kPlanNoRefine)) {  // refinement of the summaries
+    const size_t Tn = (size_t)std::max<int32_t>(T, 1);
+    L.tstat = take(sizeof(TStat) * Tn);
+    L.ref_hist = take(sizeof(int32_t) * kRefBins * Tn);
+    L.ref_bin = take(sizeof(int32_t) * Tn);
+    L.ref_n = take(sizeof(int32_t) * Tn);
+    L.ref_cell = take(sizeof(int32_t) * kRefMaxCells * Tn);
+    L.ref_fast = take(sizeof(float) * kRefMaxCells * Tn);
+    L.ref_val = take(sizeof(double) * kRefMaxCells * Tn);
+    L.own_map = (flags & FMAP_PLAN_MAP_BUFFER)
+                    ? take(sizeof(float) * (size_t)std::max<int64_t>(cells, 1) * Tn) : 0;
+  }
   L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.perm_gap = L.tauc = L.wtab = 0;
   const size_t np1 = (size_t)n_sft + 1;
   if (g->window == FMAP_RECT) {
@@ -177,6 +199,7 @@ const char* fmap_status_string(fmap_status s) {
     case FMAP_ERR_BUSY: return "FMAP_ERR_BUSY";
     case FMAP_ERR_DATA: return "FMAP_ERR_DATA";
     case FMAP_ERR_UNSUPPORTED: return "FMAP_ERR_UNSUPPORTED";
+    case FMAP_ERR_NONFINITE: return "FMAP_ERR_NONFINITE";
   }
   return "FMAP_UNKNOWN";
 }
@@ -202,7 +225,8 @@ static fmap_status plan_args_ok(const fmap_grid* grid, int32_t n_sft, int32_t n_
   if (n_sft < 0) return arg_fail("n_sft must be >= 0");
   if (n_templates < 0 || n_templates > 65535) return arg_fail("n_templates must be in [0, 65535]");
   if (precision < FMAP_FP64 || precision > FMAP_BF16X3) return arg_fail("unknown precision");
-  if (flags & ~(uint32_t)(FMAP_PLAN_PER_TEMPLATE_ANTENNA | FMAP_PLAN_EXP_RECURRENCE))
+  if (flags & ~(uint32_t)(FMAP_PLAN_PER_TEMPLATE_ANTENNA | FMAP_PLAN_EXP_RECURRENCE |
+                          FMAP_PLAN_MAP_BUFFER | kPlanNoRefine))
     return arg_fail("unknown plan flags");
   if (flags & FMAP_PLAN_EXP_RECURRENCE) {
     if (grid->window != FMAP_EXP) return arg_fail("FMAP_PLAN_EXP_RECURRENCE is for exponential windows");
@@ -263,6 +287,18 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
   w.flag_bits = (uint32_t*)(b + L.flag_bits);
   w.n_flag = (int32_t*)(b + L.n_flag);
   w.flag_list = (int64_t*)(b + L.flag_list);
+  if (!(flags & kPlanNoRefine)) {
+    w.tstat = (TStat*)(b + L.tstat);
+    w.ref_hist = (int32_t*)(b + L.ref_hist);
+    w.ref_bin = (int32_t*)(b + L.ref_bin);
+    w.ref_n = (int32_t*)(b + L.ref_n);
+    w.ref_cell = (int32_t*)(b + L.ref_cell);
+    w.ref_fast = (float*)(b + L.ref_fast);
+    w.ref_val = (double*)(b + L.ref_val);
+    w.own_map = (flags & FMAP_PLAN_MAP_BUFFER) ? (float*)(b + L.own_map) : nullptr;
+  } else {
+    p->refine_cells = 0;
+  }
   if (grid->window == FMAP_RECT) {
     w.pa = (float4*)(b + L.pa);
     w.px = (float4*)(b + L.px);
@@ -392,6 +428,9 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   if (st != FMAP_OK) return st;
   p->last_stream = s;
   if (!d_2F && !d_summary) return FMAP_OK;
+  // summary-only calls write the plan's own map when it has one, so that the
+  // summaries can be refined
+  if (!d_2F && p->ws.own_map) d_2F = p->ws.own_map;
   if (p->needs_err_reset) {
     FMAP_CUDA(cudaMemsetAsync(p->ws.dev_err, 0, sizeof(uint32_t), s));
     p->needs_err_reset = false;
@@ -402,7 +441,7 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
     for (auto e : ev) p->events.push_back(e);
     FMAP_CUDA(cudaEventRecord(ev[0], s));
   }
-  FMAP_CUDA(launch_prep(p, a->t, s));
+  FMAP_CUDA(launch_prep(p, a, s));
   {   // the bitmask of ill-conditioned entries, set by the coefficient kernels
     const int64_t ent = (int64_t)p->grid.n_t0 * p->grid.n_tau *
                         (a->shared_antenna ? 1 : std::max<int32_t>(p->n_templates, 1));
@@ -437,6 +476,7 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   if (ev[3]) FMAP_CUDA(cudaEventRecord(ev[3], s));
   FMAP_CUDA(launch_flag_and_fixup(p, a, d_2F, s));
   FMAP_CUDA(launch_final_reduce(p, tiles, true, d_summary, s));
+  FMAP_CUDA(launch_refine(p, a, d_2F, d_summary, s));
   if (ev[4]) FMAP_CUDA(cudaEventRecord(ev[4], s));
   return FMAP_OK;
 }
@@ -528,12 +568,76 @@ fmap_status fmap_plan_status(fmap_plan_t* p) {
   FMAP_CUDA(cudaMemcpy(&bits, p->ws.dev_err, sizeof(bits), cudaMemcpyDeviceToHost));
   if (bits) {
     FMAP_CUDA(cudaMemset(p->ws.dev_err, 0, sizeof(uint32_t)));
-    std::string m;
-    if (bits & DEV_ERR_ORDER) m += "timestamps are not strictly increasing; ";
-    if (bits & DEV_ERR_SPAN) m += "timestamp span is >= 2^31 s; ";
-    if (bits & DEV_ERR_TIMEOUT) m += "a bounded device wait gave up; ";
-    set_error(m);
-    return (bits & DEV_ERR_TIMEOUT) ? FMAP_ERR_TIMEOUT : FMAP_ERR_DATA;
+    set_error(dev_err_message(bits));
+    return dev_err_status(bits);
+  }
+  return FMAP_OK;
+}
+
+fmap_status fmap_plan_set_refine(fmap_plan_t* p, int32_t max_cells) {
+  set_error("");
+  if (!p) return arg_fail("plan is NULL");
+  if (max_cells > kRefMaxCells) return arg_fail("at most 4096 refined cells per template");
+  p->refine_cells = max_cells < 0 ? -1 : max_cells;
+  return FMAP_OK;
+}
+
+fmap_status fmap_plan_set_wait_limit(fmap_plan_t* p, int64_t limit_ns) {
+  set_error("");
+  if (!p) return arg_fail("plan is NULL");
+  p->wait_ns = limit_ns < 0 ? kDefaultWaitNs : limit_ns;
+  return FMAP_OK;
+}
+
+fmap_status fmap_combine_summaries(const fmap_summary* shards, int32_t n_shards,
+                                   int32_t n_templates, const int32_t* m_offsets,
+                                   fmap_summary* out) {
+  set_error("");
+  if (n_shards < 0 || n_templates < 0) return arg_fail("negative shard or template count");
+  if (n_templates > 0 && (!out || (n_shards > 0 && (!shards || !m_offsets))))
+    return arg_fail("NULL shards, offsets or output");
+  for (int32_t j = 0; j < n_templates; ++j) {
+    int64_t n_tot = 0;
+    bool have = false;
+    float best = 0.0f;
+    int64_t bm = -1, bn = -1;
+    int32_t flags = ~0;
+    double hi = -INFINITY;
+    std::vector<double> terms;
+    terms.reserve((size_t)n_shards);
+    for (int32_t r = 0; r < n_shards; ++r) {
+      const fmap_summary& q = shards[(int64_t)r * n_templates + j];
+      if (q.n_valid <= 0) continue;
+      n_tot += q.n_valid;
+      const int64_t gm = (int64_t)q.m + m_offsets[r], gn = q.n;
+      if (!have || q.max2F > best || (q.max2F == best && (gm < bm || (gm == bm && gn < bn)))) {
+        best = q.max2F;
+        bm = gm;
+        bn = gn;
+      }
+      have = true;
+      flags &= q.flags;
+      const double v = q.logB + std::log((double)q.n_valid);
+      terms.push_back(v);
+      hi = std::max(hi, v);
+    }
+    fmap_summary o;
+    o.n_valid = n_tot;
+    if (!have) {
+      o.max2F = 0.0f;
+      o.m = o.n = -1;
+      o.flags = 0;
+      o.logB = std::nan("");
+    } else {
+      double acc = 0.0;
+      for (double v : terms) acc += std::exp(v - hi);
+      o.max2F = best;
+      o.m = (int32_t)bm;
+      o.n = (int32_t)bn;
+      o.flags = flags;
+      o.logB = hi + std::log(acc) - std::log((double)n_tot);
+    }
+    out[j] = o;
   }
   return FMAP_OK;
 }

@@ -268,7 +268,8 @@ static fmap_status place_wave(fmap_batch_s* B, int w) {
     const fmap_batch_item& it = B->items[i];
     size_t bytes = 0;
     const uint32_t flags = (it.atoms.shared_antenna ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA) |
-                           (it.grid.window == FMAP_EXP ? (uint32_t)FMAP_PLAN_EXP_RECURRENCE : 0u);
+                           (it.grid.window == FMAP_EXP ? (uint32_t)FMAP_PLAN_EXP_RECURRENCE : 0u) |
+                           kPlanNoRefine;
     fmap_status st = plan_footprint(&it.grid, it.atoms.n_sft, it.atoms.n_templates, FMAP_FP64,
                                     flags, &bytes);
     if (st != FMAP_OK) return st;
@@ -424,7 +425,8 @@ fmap_status fmap_batch_plan(fmap_batch_t** out, const fmap_batch_item* items, in
       return batch_fail("instance " + std::to_string(i) + ": bad atoms");
     }
     const uint32_t pf = (it.atoms.shared_antenna ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA) |
-                        (it.grid.window == FMAP_EXP ? (uint32_t)FMAP_PLAN_EXP_RECURRENCE : 0u);
+                        (it.grid.window == FMAP_EXP ? (uint32_t)FMAP_PLAN_EXP_RECURRENCE : 0u) |
+                        kPlanNoRefine;
     fmap_status st = plan_footprint(&it.grid, it.atoms.n_sft, it.atoms.n_templates, FMAP_FP64, pf,
                                     &foot[i]);
     if (st != FMAP_OK) {
@@ -548,8 +550,8 @@ fmap_status fmap_batch_status(fmap_batch_t* B, fmap_stream stream) {
   FMAP_CUDA(cudaMemcpy(&bits, B->d_err, sizeof(bits), cudaMemcpyDeviceToHost));
   if (bits) {
     FMAP_CUDA(cudaMemset(B->d_err, 0, sizeof(uint32_t)));
-    set_error("an instance has non-increasing timestamps, a span >= 2^31 s or a timed-out wait");
-    return (bits & DEV_ERR_TIMEOUT) ? FMAP_ERR_TIMEOUT : FMAP_ERR_DATA;
+    set_error("in an instance: " + dev_err_message(bits));
+    return dev_err_status(bits);
   }
   return FMAP_OK;
 }

@@ -8,12 +8,32 @@
 
 namespace fmap {
 
+// Non-finite check of n values (antenna or data rows): DEV_ERR_NONFINITE
+// is latched if any is NaN or infinite (|x| <= FLT_MAX fails for both; one
+// atomic per warp at most).
+__device__ __forceinline__ void finite_check(const float* __restrict__ v, int64_t n,
+                                             int64_t i0, int64_t step, uint32_t* __restrict__ err) {
+  bool bad = false;
+  for (int64_t i = i0; i < n; i += step) bad |= !(fabsf(v[i]) <= 3.402823466e38f);
+  const unsigned who = __ballot_sync(__activemask(), bad);
+  if (bad && (int)(threadIdx.x & 31) == __ffs(who) - 1) atomicOr(err, DEV_ERR_NONFINITE);
+}
+
 // t -> t - t[0] as int32, with the data checks (strictly increasing,
-// span < 2^31 s) latched into the plan's status word.
+// span < 2^31 s) latched into the plan's status word, and the atoms' values
+// checked for NaN and infinities.
 __device__ __forceinline__ void prep_body(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc,
                        int32_t* __restrict__ rel_t, int64_t* __restrict__ t_base,
-                       uint32_t* __restrict__ err,
+                       uint32_t* __restrict__ err, const float* __restrict__ ant, int64_t n_ant_vals,
+                       const float* __restrict__ x, int64_t n_x_vals,
     const uint3 bid, const dim3 gdim) {
+  {
+    const int64_t g0 = bid.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t step = (int64_t)gdim.x * blockDim.x;
+    if (ant) finite_check(ant, n_ant_vals, g0, step, err);
+    if (x) finite_check(x, n_x_vals, g0, step, err);
+  }
+  if (n <= 0) return;
   const int64_t base = t[0];
   for (int64_t i = n + bid.x * (int64_t)blockDim.x + threadIdx.x; i < n_alloc;
        i += (int64_t)gdim.x * blockDim.x)
@@ -33,8 +53,9 @@ __device__ __forceinline__ void prep_body(const int64_t* __restrict__ t, int32_t
 
 __global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc,
                        int32_t* __restrict__ rel_t, int64_t* __restrict__ t_base,
-                       uint32_t* __restrict__ err) {
-  prep_body(t, n, n_alloc, rel_t, t_base, err, blockIdx, gridDim);
+                       uint32_t* __restrict__ err, const float* __restrict__ ant,
+                       int64_t n_ant_vals, const float* __restrict__ x, int64_t n_x_vals) {
+  prep_body(t, n, n_alloc, rel_t, t_base, err, ant, n_ant_vals, x, n_x_vals, blockIdx, gridDim);
 }
 
 // Window index tables: i0[m] = first atom with t >= t0_m; jend[m][n] = one
@@ -100,12 +121,19 @@ k_index(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, i
     index_body(rel_t, t_base, n_sft, g, ax, i0tab, jend, m);
 }
 
-cudaError_t launch_prep(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
+cudaError_t launch_prep(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
   if (p->n_sft <= 0) return cudaSuccess;
   const int threads = 256;
-  const int blocks = (int)std::min<int64_t>((p->n_sft + threads - 1) / threads, 4096);
-  k_prep<<<blocks, threads, 0, s>>>(d_t, p->n_sft, rel_t_entries(p->n_sft), p->ws.rel_t,
-                                    p->ws.t_base, p->ws.dev_err);
+  const int64_t n = p->n_sft;
+  const int64_t n_ant = 3 * n * (a->shared_antenna ? 1 : std::max<int32_t>(p->n_templates, 1));
+  const int64_t n_x = 4 * n * (int64_t)p->n_templates;
+  // enough threads for the timestamps, and for the value checks at a few
+  // values per thread
+  const int64_t want = std::max<int64_t>(n, (n_ant + n_x) / 8);
+  const int blocks = (int)std::min<int64_t>((want + threads - 1) / threads, (int64_t)p->n_sm * 16);
+  k_prep<<<std::max(blocks, 1), threads, 0, s>>>(a->t, p->n_sft, rel_t_entries(p->n_sft),
+                                                 p->ws.rel_t, p->ws.t_base, p->ws.dev_err,
+                                                 a->antenna, n_ant, a->fafb, n_x);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -237,15 +265,25 @@ k_reduce_groups(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0
   reduce_groups_body(parts, n_tiles, fix0, n_fix, stride, n_groups, groups, blockIdx, gridDim);
 }
 
-// Level 2: one block per template over its groups; writes the summary.
+// Level 2: one block per template over its groups; writes the summary and,
+// when tstat is given, the statistics the refinement starts from.
 __device__ __forceinline__ void reduce_final_body(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n_tau,
-               double log_prior, fmap_summary* __restrict__ out,
+               double log_prior, fmap_summary* __restrict__ out, TStat* __restrict__ tstat,
     const uint3 bid, const dim3 gdim) {
   const Partial64* gp = groups + (int64_t)bid.x * n_groups;
   const Partial64 r = block_merge(n_groups, [&](int64_t b) { return gp[b]; });
   if (threadIdx.x == 0) {
+    if (tstat) {
+      TStat t;
+      t.S = r.sum;
+      t.M = r.max2F;
+      t.arg = r.arg;
+      t.N = r.nvalid;
+      t.pad = 0;
+      tstat[bid.x] = t;
+    }
     fmap_summary o;
-    o.reserved = 0;
+    o.flags = 0;
     o.n_valid = r.nvalid;
     if (r.nvalid == 0) {
       o.max2F = 0.0f;
@@ -264,20 +302,21 @@ __device__ __forceinline__ void reduce_final_body(const Partial64* __restrict__ 
 
 __global__ void __launch_bounds__(kRedThreads)
 k_reduce_final(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n_tau,
-               double log_prior, fmap_summary* __restrict__ out) {
-  reduce_final_body(groups, n_groups, n_tau, log_prior, out, blockIdx, gridDim);
+               double log_prior, fmap_summary* __restrict__ out, TStat* __restrict__ tstat) {
+  reduce_final_body(groups, n_groups, n_tau, log_prior, out, tstat, blockIdx, gridDim);
 }
 
 int64_t reduce_groups_of(int64_t slots) { return std::max<int64_t>(1, (slots + kRedGroup - 1) / kRedGroup); }
 
 static cudaError_t reduce_into(const Partial* parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
                                int64_t stride, int32_t T, int32_t n_tau, double log_prior,
-                               Partial64* groups, fmap_summary* d_summary, cudaStream_t s) {
+                               Partial64* groups, fmap_summary* d_summary, cudaStream_t s,
+                               TStat* tstat = nullptr) {
   const int64_t n_groups = reduce_groups_of(n_tiles + n_fix);
   k_reduce_groups<<<dim3((unsigned)n_groups, (unsigned)T), kRedThreads, 0, s>>>(
       parts, n_tiles, fix0, n_fix, stride, n_groups, groups);
   k_reduce_final<<<T, kRedThreads, 0, s>>>(groups, n_groups, n_tau > 0 ? n_tau : 1, log_prior,
-                                           d_summary);
+                                           d_summary, tstat);
   return cudaGetLastError();
 }
 
@@ -288,7 +327,7 @@ cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, bool with_fix,
   p->launches += 2;
   return reduce_into(p->ws.partials, n_tiles, p->n_tiles, fix ? kFixSlots : 0, p->part_stride,
                      p->n_templates, p->grid.n_tau, p->log_prior, (Partial64*)p->ws.groups,
-                     d_summary, s);
+                     d_summary, s, p->ws.tstat);
 }
 
 // ---------------------------------------------------------------------------
@@ -365,7 +404,8 @@ __global__ void __launch_bounds__(256) kb_prep(const BItem* __restrict__ items, 
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     const int64_t ru = it.n_sft > 0 ? (it.n_alloc + 255) / 256 : 0;
     if (k < ru) {
-      prep_body(it.t, it.n_sft, it.n_alloc, it.rel_t, it.t_base, it.dev_err,
+      prep_body(it.t, it.n_sft, it.n_alloc, it.rel_t, it.t_base, it.dev_err, it.antenna,
+                (int64_t)3 * it.n_sft * it.n_ant, it.fafb, (int64_t)4 * it.n_sft * it.T,
                 make_uint3((unsigned)k, 0, 0), dim3((unsigned)ru));
     } else {
       const int64_t w0 = (k - ru) * kBitsPerUnit;
@@ -395,7 +435,7 @@ __global__ void __launch_bounds__(kRedThreads) kb_red_final(const BItem* __restr
                                                             BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     reduce_final_body((const Partial64*)it.red_buf, it.red_groups, it.g.n_tau > 0 ? it.g.n_tau : 1,
-                      it.log_prior, it.summary, make_uint3((unsigned)k, 0, 0),
+                      it.log_prior, it.summary, nullptr, make_uint3((unsigned)k, 0, 0),
                       dim3((unsigned)it.T));
   });
 }

@@ -12,7 +12,9 @@ namespace fmap {
 constexpr int32_t kNoArg = 0x7fffffff;
 
 // ---- PTX helpers: shared-memory addresses, the global timer, mbarriers ----
-// Every spin on an mbarrier is bounded by kWaitNs of %globaltimer.
+// Every spin on an mbarrier is bounded by a limit in ns of %globaltimer: the
+// plan's wait limit (kWaitNs by default), and kWaitNs for the drains that let
+// copies already in flight land before a block that gave up exits.
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -47,28 +49,48 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait on one phase; false if it did not complete within kWaitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Non-blocking test of one phase (try_wait may suspend the thread for a
+// hardware-defined time; a zero wait limit polls with this instead).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on one phase; false if it did not complete within limit_ns
+// (0: give up when one non-blocking poll finds it incomplete).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitNs) {
+  if (limit_ns == 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity))
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   return true;
 }
 // Bounded wait that also gives up at once when another block has already
 // timed out (DEV_ERR_TIMEOUT set in *err), so a broken phase costs one
 // timeout per launch, not one per block.  Sets the flag on its own timeout.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
-                                                   uint32_t* err) {
+                                                   uint32_t* err, uint64_t limit_ns = kWaitNs) {
+  if (limit_ns == 0) {
+    if (mbar_test_wait(bar, parity)) return true;
+    atomicOr(err, DEV_ERR_TIMEOUT);
+    return false;
+  }
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
     if (*(volatile uint32_t*)err & DEV_ERR_TIMEOUT) return false;
-    if (globaltimer() - t0 > kWaitNs) {
+    if (globaltimer() - t0 > limit_ns) {
       atomicOr(err, DEV_ERR_TIMEOUT);
       return false;
     }
+    if (mbar_try_wait(bar, parity)) return true;
   }
 }
 // Bulk copy global -> shared (16-byte aligned addresses, size a multiple of

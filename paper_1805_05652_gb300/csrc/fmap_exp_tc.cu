@@ -39,14 +39,17 @@ constexpr int kDtCap = 4096;          // atoms of relative times staged per refi
 constexpr float kFar = 1.0e30f;       // relative time of atoms outside every window
 
 // ---------------------------------------------------------------- PTX ------
-// Bounded wait; false on timeout or when another role already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// Bounded wait; false on timeout (limit_ns; 0: at the first incomplete
+// poll) or when another role already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          uint64_t limit_ns) {
+  if (limit_ns == 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
+    if (mbar_try_wait(bar, parity)) return true;
   }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
@@ -204,6 +207,7 @@ struct Params {
   Partial* parts;
   int64_t stride;
   uint32_t* err;
+  uint64_t wait_ns;    // limit of the pipeline's waits (the drains take kWaitNs)
 };
 
 // TAB: weights from the window table (FMAP_TABLE grids) instead of exp2; the
@@ -272,7 +276,8 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
       int issued = 0;
       for (int it = 0; it < n_kt; ++it) {
         const int s = it % kStages;
-        if (it >= kStages && !mbar_wait(&bar_empty[s], ((it / kStages) + 1) & 1, &s_abort)) {
+        if (it >= kStages &&
+            !mbar_wait(&bar_empty[s], ((it / kStages) + 1) & 1, &s_abort, p.wait_ns)) {
           atomicExch(&s_abort, 1);
           break;
         }
@@ -287,7 +292,7 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
         // let the copies already in flight land before the block exits
         for (int it = issued - kStages > 0 ? issued - kStages : 0; it < issued; ++it) {
           volatile int never = 0;
-          mbar_wait(&bar_full_b[it % kStages], (it / kStages) & 1, &never);
+          mbar_wait(&bar_full_b[it % kStages], (it / kStages) & 1, &never, kWaitNs);
         }
       }
     }
@@ -306,7 +311,8 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
       uint32_t d_lo = d_lo0, a_st = tmem + a_col0, par = 0;
       int s = 0;
       for (int it = 0; it < n_kt; ++it) {
-        if (!mbar_wait(&bar_full_b[s], par, &s_abort) || !mbar_wait(&bar_full_a[s], par, &s_abort)) {
+        if (!mbar_wait(&bar_full_b[s], par, &s_abort, p.wait_ns) ||
+            !mbar_wait(&bar_full_a[s], par, &s_abort, p.wait_ns)) {
           atomicExch(&s_abort, 1);
           break;
         }
@@ -329,7 +335,13 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
           a_st += (uint32_t)kAColsPerStage;
         }
       }
-      if (n_kt > 0) mma_commit(&bar_acc);
+      if (n_kt > 0) {
+        mma_commit(&bar_acc);
+        // every MMA this thread issued completes before the block releases its
+        // tensor memory, also after a wait gave up
+        volatile int never = 0;
+        mbar_wait(&bar_acc, 0, &never, kWaitNs);
+      }
     }
   } else {
     // ---------------- W generators, then the epilogue ----------------
@@ -372,7 +384,8 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
       // after a timeout keep looping (without work) so that every generator
       // warp reaches the same shared-memory barriers
       if (!ok_run || s_abort) continue;
-      if (it >= kStages && !mbar_wait(&bar_empty[s], ((it / kStages) + 1) & 1, &s_abort)) {
+      if (it >= kStages &&
+          !mbar_wait(&bar_empty[s], ((it / kStages) + 1) & 1, &s_abort, p.wait_ns)) {
         atomicExch(&s_abort, 1);
         ok_run = false;
         continue;
@@ -441,7 +454,7 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
     bool have_acc = n_kt > 0 && ok_run;
     if (have_acc) {
       volatile int* ab = &s_abort;
-      have_acc = mbar_wait(&bar_acc, 0, ab);
+      have_acc = mbar_wait(&bar_acc, 0, ab, p.wait_ns);
       if (!have_acc) atomicExch(&s_abort, 1);
     }
     tc_fence_after();
@@ -636,6 +649,7 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   prm.parts = p->ws.partials;
   prm.stride = p->part_stride;
   prm.err = p->ws.dev_err;
+  prm.wait_ns = (uint64_t)p->wait_ns;
   // shared memory: NS stages x (hi + lo) x N rows x 128 B; at least enough to
   // keep the resident CTAs within the 512 TMEM columns of an SM
   size_t smem = (size_t)NS * 2 * N * 128 + sizeof(float) * tc::kDtCap + 1024 +

@@ -147,7 +147,7 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
         const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
-    const uint3 bid, const dim3 gdim) {
+        Coef* __restrict__ coef, const uint3 bid, const dim3 gdim) {
   __shared__ double sw[kFixWeights];
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const int64_t cap = shared_antenna ? cells : cells * n_templates;   // list capacity
@@ -206,6 +206,8 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
         v = 2.0 * (B * (far * far + fai * fai) + A * (fbr * fbr + fbi * fbi) -
                    2.0 * C * (far * fbr + fai * fbi)) / D;
       if (map) map[(int64_t)tq * cells + cell] = (float)v;
+      // the FP64 validity decision, recorded once per entry
+      if (coef && (only >= 0 || tq == 0)) coef[entry].valid = ok ? 3.0f : 0.0f;
       partial_add(acc, (float)v, (int32_t)cell, ok);
     }
   }
@@ -223,7 +225,7 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
         fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
-        int32_t b, int32_t tq) {
+        Coef* __restrict__ coef, int32_t b, int32_t tq) {
   __shared__ Partial scratch[kFixThreads / 32];
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const int64_t cap = shared_antenna ? cells : cells * n_templates;
@@ -275,6 +277,7 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
       v = 2.0 * (B * (far * far + fai * fai) + A * (fbr * fbr + fbi * fbi) -
                  2.0 * C * (far * fbr + fai * fbi)) / D;
     if (map) map[(int64_t)tq * cells + cell] = (float)v;
+    if (coef && (!shared_antenna || tq == 0)) coef[entry].valid = ok ? 3.0f : 0.0f;
     partial_add(acc, (float)v, (int32_t)cell, ok);
   }
   acc = partial_block_reduce<kFixThreads / 32>(acc, scratch);
@@ -288,9 +291,9 @@ k_fixup_cells(const int64_t* __restrict__ list, const int32_t* __restrict__ n_fl
               const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
               const float* __restrict__ antenna, const float* __restrict__ fafb,
               int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
-              int64_t stride, int64_t slot0) {
+              int64_t stride, int64_t slot0, Coef* __restrict__ coef) {
   fixup_cells_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, wtab, n_tab, i0tab, jend, antenna,
-                   fafb, n_templates, map, parts, stride, slot0, blockIdx.x, blockIdx.y);
+                   fafb, n_templates, map, parts, stride, slot0, coef, blockIdx.x, blockIdx.y);
 }
 
 // Fix-up blocks of one plan (the y extent: templates, or template blocks).
@@ -305,8 +308,9 @@ k_fixup(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, in
         const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab,
         const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
-        float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0) {
-  fixup_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, wtab, n_tab, i0tab, jend, antenna, fafb, n_templates, map, parts, stride, slot0, blockIdx, gridDim);
+        float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
+        Coef* __restrict__ coef) {
+  fixup_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, wtab, n_tab, i0tab, jend, antenna, fafb, n_templates, map, parts, stride, slot0, coef, blockIdx, gridDim);
 }
 
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
@@ -327,14 +331,15 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
                                                p->n_sft, p->grid, plan_axes(p), p->ws.wtab, p->n_tab,
                                                p->ws.i0, p->ws.jend,
                                                a->antenna, a->fafb, p->n_templates, d_2F,
-                                               p->ws.partials, p->part_stride, p->n_tiles);
+                                               p->ws.partials, p->part_stride, p->n_tiles,
+                                               p->ws.coef);
   else
     k_fixup<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
                                          a->shared_antenna, p->ws.rel_t, p->ws.t_base, p->n_sft,
                                          p->grid, plan_axes(p), p->ws.wtab, p->n_tab, p->ws.i0, p->ws.jend,
                                          a->antenna, a->fafb,
                                          p->n_templates, d_2F, p->ws.partials, p->part_stride,
-                                         p->n_tiles);
+                                         p->n_tiles, p->ws.coef);
   p->launches += 4;
   return cudaGetLastError();
 }
@@ -372,11 +377,11 @@ __global__ void __launch_bounds__(kFixThreads) kb_fixup(const BItem* __restrict_
       if (it.T < kFixCellModeT)
         fixup_cells_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base,
                          it.n_sft, it.g, it.ax, nullptr, 0, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
-                         it.partials, it.part_stride, it.n_tiles, b, y);
+                         it.partials, it.part_stride, it.n_tiles, it.coef, b, y);
       else
         fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft,
                    it.g, it.ax, nullptr, 0, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,
-                   it.part_stride, it.n_tiles, make_uint3((unsigned)b, (unsigned)y, 0),
+                   it.part_stride, it.n_tiles, it.coef, make_uint3((unsigned)b, (unsigned)y, 0),
                    dim3((unsigned)kFixSlots, (unsigned)((it.T + kFixThreads - 1) / kFixThreads)));
       __syncthreads();   // the bodies' shared scratch is reused by the next slot
     }

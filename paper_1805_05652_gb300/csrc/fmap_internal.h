@@ -25,7 +25,19 @@ fmap_status cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 // Device-side error bits latched in the plan's status word.
-enum : uint32_t { DEV_ERR_ORDER = 1u, DEV_ERR_SPAN = 2u, DEV_ERR_TIMEOUT = 4u };
+enum : uint32_t { DEV_ERR_ORDER = 1u, DEV_ERR_SPAN = 2u, DEV_ERR_TIMEOUT = 4u,
+                  DEV_ERR_NONFINITE = 8u };
+// Status of latched device error bits (0 when none): a timeout first, then
+// data errors, then non-finite atoms.
+inline fmap_status dev_err_status(uint32_t bits) {
+  if (bits & DEV_ERR_TIMEOUT) return FMAP_ERR_TIMEOUT;
+  if (bits & (DEV_ERR_ORDER | DEV_ERR_SPAN)) return FMAP_ERR_DATA;
+  if (bits & DEV_ERR_NONFINITE) return FMAP_ERR_NONFINITE;
+  return FMAP_OK;
+}
+std::string dev_err_message(uint32_t bits);
+// Default limit of a bounded device wait (ns).
+constexpr int64_t kDefaultWaitNs = 2000000000ll;
 
 // ---------------------------------------------------------------------------
 // Reduction partial of one tile and one template.  sum = sum over the tile's
@@ -45,10 +57,29 @@ struct __align__(16) Partial {
 // square in Fa).  valid: 0 = invalid (fewer than 2 atoms; k1 = k2 = 0),
 // 1 = evaluated by the fast kernels, 2 = ill-conditioned or undecided
 // (A B / D > kCondThreshold, or D not clearly positive in float-float): left
-// to the FP64 fix-up of fmap_fixup.cu, which also decides D > 0.
+// to the FP64 fix-up of fmap_fixup.cu, which decides D > 0 and then records
+// the outcome in valid (3 = valid by FP64 sums, 0 = invalid).
 constexpr double kCondThreshold = 100.0;
 // Reduction slots per template written by the fix-up kernel.
 constexpr int kFixSlots = 512;
+// Internal plan flag (not part of the C ABI): the plan never refines its
+// summaries and its workspace holds no refinement arrays (batch instances).
+constexpr uint32_t kPlanNoRefine = 1u << 16;
+// Top-cell refinement (fmap_refine.cu): candidates per template (at most),
+// histogram bins over the window of kRefWindow (2F units) below the maximum.
+constexpr int kRefMaxCells = 4096;
+constexpr int kRefBins = 256;
+constexpr float kRefWindow = 16.0f;
+// Per-template statistics of the fast reduction, kept for the refinement:
+// S = sum over valid cells of exp((2F - M) / 2), M = max 2F, arg its lowest
+// cell, N the valid count.
+struct __align__(32) TStat {
+  double S;
+  float M;
+  int32_t arg;
+  long long N;
+  long long pad;
+};
 // Window length L(tau) in seconds: tau (rect) or floor(cut8 tau / 8) (exp,
 // cut8 = 24 by default: Eq. winexp's 3 tau).  An atom belongs to the window
 // of (t0, tau) iff t0 <= t and t + T_sft <= t0 + L(tau).
@@ -137,6 +168,16 @@ struct Workspace {
   float4* pa = nullptr;          // [T_ant][N+1][2] FP64 antenna prefix (a2, b2, ab, 0) as hi4, lo4
   float4* px = nullptr;          // [T][N+1][2] float-float data prefix (hi4, lo4)
   // exp: chunk-major copies of the atoms (perm_entries(N, lanes) per set)
+  // refinement: per-template fast statistics, histogram, chosen cut, the
+  // candidates (cell, fast 2F, FP64 2F) and the plan's own map (if any)
+  TStat* tstat = nullptr;        // [T]
+  int32_t* ref_hist = nullptr;   // [T][kRefBins]
+  int32_t* ref_bin = nullptr;    // [T] last histogram bin taken (-1: none)
+  int32_t* ref_n = nullptr;      // [T] candidates
+  int32_t* ref_cell = nullptr;   // [T][kRefMaxCells]
+  float* ref_fast = nullptr;     // [T][kRefMaxCells]
+  double* ref_val = nullptr;     // [T][kRefMaxCells] (-1: invalid in FP64)
+  float* own_map = nullptr;      // [T][cells] (FMAP_PLAN_MAP_BUFFER)
   float4* perm_ant = nullptr;    // [T_ant][.] (a2, b2, ab, gap to the next atom as int bits; -1 last)
   float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
   int32_t* perm_gap = nullptr;   // [.] gap to the next atom (-1 last); recurrence plans
@@ -164,6 +205,8 @@ struct fmap_plan_s {
   fmap_precision precision = FMAP_FP64;
   uint32_t flags = 0;
   double log_prior = 0.0;
+  int32_t refine_cells = -1;  // fmap_plan_set_refine (< 0: the precision's default)
+  int64_t wait_ns = fmap::kDefaultWaitNs;   // fmap_plan_set_wait_limit
   int device = 0;
   int n_sm = 0;
   int64_t n_tiles = 0;        // partial slots per template of the main kernels
@@ -198,7 +241,7 @@ inline const int64_t* plan_axes(const fmap_plan_s* p) { return p->explicit_axes 
 
 // ---- host launchers (each returns cudaGetLastError of its launches and
 // adds the number of kernels it launched to p->launches) -------------------
-cudaError_t launch_prep(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s);
+cudaError_t launch_prep(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
 cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s);
 // Each compute launcher reports how many partial slots per template it wrote.
 // launch_rect records `mark` (if non-null) between its prefix scans and the
@@ -229,6 +272,12 @@ const void* batch_kernel_fixup(int phase);
 cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s);
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
                                   cudaStream_t s);
+// Top-cell refinement of the summaries (after launch_final_reduce); d_2F is
+// the map the compute call wrote.
+cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
+                          fmap_summary* d_summary, cudaStream_t s);
+// Candidates per template of a plan's refinement (0: off).
+int32_t refine_cells_of(const fmap_plan_s* p);
 // Reduces partial slots [0, n_tiles) and, when with_fix, the fix-up slots.
 cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, bool with_fix,
                                 fmap_summary* d_summary, cudaStream_t s);

@@ -338,7 +338,7 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
     const int32_t* __restrict__ jend, const Coef* __restrict__ coef,
     const float4* __restrict__ px, int32_t n_sft, int32_t n_t0, int32_t n_tau,
     int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
-    uint32_t* __restrict__ err, int64_t blk, unsigned char* smem) {
+    uint32_t* __restrict__ err, uint64_t wait_ns, int64_t blk, unsigned char* smem) {
   __shared__ uint64_t s_bar[kSlots];   // one per slot: warp w owns slot w
   __shared__ int4 s_grp[4];   // per group: first row start, row entries, first end, end entries
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -448,12 +448,25 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
 
   constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
   const uint64_t tiny2 = pk2(1e-30f, 1e-30f);
+  // A warp whose wait gave up (its own limit, or another block's timeout)
+  // first lets the copy of that stage land (bounded by kWaitNs), then issues
+  // no more copies and skips its work; it still meets its pair's named
+  // barrier every stage.  The call's outputs are then undefined and the
+  // plan's status reports the timeout.
+  bool dead = false;
   if (staged) issue(0);
   for (int st = 0; st < n_st; ++st) {
     const uint32_t qs = q_s0 + (uint32_t)((st & 1) * kQBytes);
     if (staged) {
-      if (G.y > 0 && t_begin + st * st_t + wi < t_end) {
-        mbar_wait_or_abort(&s_bar[warp], (uint32_t)(st & 1), err);
+      if (!dead && G.y > 0 && t_begin + st * st_t + wi < t_end) {
+        const bool got = mbar_wait_or_abort(&s_bar[warp], (uint32_t)(st & 1), err, wait_ns);
+        if (!__all_sync(0xffffffffu, got)) {
+          mbar_wait_bounded(&s_bar[warp], (uint32_t)(st & 1), kWaitNs);
+          __syncwarp();
+          dead = true;
+        }
+      }
+      if (!dead && G.y > 0 && t_begin + st * st_t + wi < t_end) {
         const uint32_t rs = raw_s + (uint32_t)(warp * kSlotEntries * 32);
         const uint32_t qd = qs + (uint32_t)(warp * kSlotEntries * 16);
         uint64_t hb0, hb1, lb0, lb1;
@@ -476,7 +489,7 @@ __device__ __forceinline__ void rect_cells_body(const int32_t* __restrict__ i0ta
       }
       asm volatile("bar.sync %0, 64;" ::"r"(pair_bar) : "memory");
     }
-    if (rows == 0) continue;   // warp below the grid: barriers only
+    if (rows == 0 || dead) continue;   // warp below the grid, or given up: barriers only
     for (int g = tlane; g < st_t; g += tl) {
       const int32_t tm = t_begin + st * st_t + g;
       if (tm >= t_end) break;
@@ -577,10 +590,11 @@ __global__ void __launch_bounds__(kCellThreads, 2)
 k_rect_cells(const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
              const Coef* __restrict__ coef, const float4* __restrict__ px, int32_t n_sft,
              int32_t n_t0, int32_t n_tau, int32_t n_templates, float* __restrict__ map,
-             Partial* __restrict__ parts, int64_t stride, uint32_t* __restrict__ err) {
+             Partial* __restrict__ parts, int64_t stride, uint32_t* __restrict__ err,
+             uint64_t wait_ns) {
   extern __shared__ __align__(128) unsigned char s_cells[];
   rect_cells_body<kShared>(i0tab, jend, coef, px, n_sft, n_t0, n_tau, n_templates, map, parts,
-                           stride, err, blockIdx.x, s_cells);
+                           stride, err, wait_ns, blockIdx.x, s_cells);
 }
 
 int64_t rect_partial_slots(const fmap_grid& g, int32_t, int32_t) { return rect_tiles(g); }
@@ -684,11 +698,11 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
   if (sh)
     k_rect_cells<true><<<(unsigned)blocks, kCellThreads, smem, s>>>(
         p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, T,
-        d_2F, p->ws.partials, p->part_stride, p->ws.dev_err);
+        d_2F, p->ws.partials, p->part_stride, p->ws.dev_err, (uint64_t)p->wait_ns);
   else
     k_rect_cells<false><<<(unsigned)blocks, kCellThreads, smem, s>>>(
         p->ws.i0, p->ws.jend, p->ws.coef, p->ws.px, p->n_sft, g.n_t0, g.n_tau, T,
-        d_2F, p->ws.partials, p->part_stride, p->ws.dev_err);
+        d_2F, p->ws.partials, p->part_stride, p->ws.dev_err, (uint64_t)p->wait_ns);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -724,10 +738,12 @@ __global__ void __launch_bounds__(kCellThreads, 2) kb_rect_cells(const BItem* __
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     if (it.shared)
       rect_cells_body<true>(it.i0, it.jend, it.coef, it.px, it.n_sft, it.g.n_t0, it.g.n_tau,
-                            it.T, it.map, it.partials, it.part_stride, it.dev_err, k, s_cells);
+                            it.T, it.map, it.partials, it.part_stride, it.dev_err, kWaitNs, k,
+                            s_cells);
     else
       rect_cells_body<false>(it.i0, it.jend, it.coef, it.px, it.n_sft, it.g.n_t0, it.g.n_tau,
-                             it.T, it.map, it.partials, it.part_stride, it.dev_err, k, s_cells);
+                             it.T, it.map, it.partials, it.part_stride, it.dev_err, kWaitNs, k,
+                             s_cells);
   });
 }
 const void* batch_kernel_rect(int phase) {

@@ -1,0 +1,347 @@
+// Top-cell refinement of the per-template reductions.
+//
+// The detection statistic of a template is its maximum 2F and the cell that
+// holds it, and e^F is the odds of a transient in that cell (Sec. 2, Eq.
+// F_OSG), so the marginalised Bayes factor is dominated by the cells nearest
+// the maximum.  After a compute call has written its fast map, reduced it
+// (max, argmax, exp-sum, count) and recomputed the ill-conditioned cells,
+// this stage, per template:
+//   1. histograms the valid cells whose fast 2F lies within kRefWindow of the
+//      fast maximum M (kRefBins bins, bin 0 at the maximum);
+//   2. cuts the histogram after the last bin that keeps the cell count within
+//      the plan's cap, and collects those cells (sorted by index, so that
+//      every later sum runs in a fixed order);
+//   3. recomputes each collected cell from its atoms by the plain FP64
+//      definition: the windowed sums of Eq. (winrect) / (winexp) with w on
+//      Fa, Fb and w^2 on A, B, C, D = AB - C^2, and 2F of Eq. (F_FaFb); the
+//      FP64 value replaces the fast one in the map;
+//   4. rebuilds the summary: max2F and the argmax (lowest index on FP64
+//      ties) from the FP64 values, and the exp-sum with the collected cells'
+//      fast terms replaced by their FP64 terms,
+//        S' = e^{(M - M')/2} (S - sum_k e^{(f_k - M)/2}) + sum_k e^{(v_k - M')/2},
+//      logB = M'/2 + ln S' - ln N' + c.
+// Every cell outside the cut had a fast 2F more than the cut's distance d
+// below M; when d exceeds twice the fast path's error bound, no such cell
+// can hold the FP64 maximum, and the summary says so (ARGMAX_EXACT).
+#include <math.h>
+
+#include "fmap_device.cuh"
+
+namespace fmap {
+
+constexpr int kRefThreads = 256;
+constexpr int kRefUnroll = 8;        // cells per thread and pass (independent loads)
+constexpr int kRefSortThreads = 1024;
+
+int32_t refine_cells_of(const fmap_plan_s* p) {
+  if (p->refine_cells == 0 || !p->ws.tstat) return 0;
+  if (p->refine_cells > 0) return std::min(p->refine_cells, kRefMaxCells);
+  return p->precision == FMAP_FP64 ? 64 : 512;
+}
+
+// Relative error bound (floor 1) of a plan's fast 2F.
+static double fast_tol(const fmap_plan_s* p) { return p->precision == FMAP_FP64 ? 1e-5 : 1e-3; }
+
+__device__ __forceinline__ bool ref_valid(const Coef* __restrict__ coef, int32_t shared,
+                                          int64_t cells, int32_t j, int64_t c) {
+  const float v = coef[shared ? c : (int64_t)j * cells + c].valid;
+  return v == 1.0f || v == 3.0f;
+}
+
+// Bin of a fast value v against the template's maximum M: floor((M - v)
+// kRefBins / kRefWindow), -1 outside the window (or not a number).
+__device__ __forceinline__ int ref_bin_of(float v, float M) {
+  const float d = (M - v) * ((float)kRefBins / kRefWindow);
+  if (!(d < (float)kRefBins)) return -1;
+  return d > 0.0f ? (int)d : 0;
+}
+
+// Passes 1 and 3 over the map: the histogram (collect = false) or the
+// collection of the cells up to the cut (collect = true).  Grid (x, T).
+template <bool kCollect>
+__global__ void __launch_bounds__(kRefThreads)
+k_ref_scan(const float* __restrict__ map, const Coef* __restrict__ coef, int32_t shared,
+           int64_t cells, const TStat* __restrict__ st, int32_t* __restrict__ hist,
+           const int32_t* __restrict__ cut, int32_t* __restrict__ ref_n,
+           int32_t* __restrict__ ref_cell) {
+  __shared__ int32_t h[kRefBins];
+  const int32_t j = blockIdx.y;
+  if (!kCollect) {
+    for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+  }
+  const TStat s = st[j];
+  const int32_t last = kCollect ? cut[j] : kRefBins - 1;
+  if (s.N > 0 && last >= 0) {
+    const float* mp = map + (int64_t)j * cells;
+    const int64_t span = (int64_t)kRefThreads * kRefUnroll;
+    for (int64_t base = (int64_t)blockIdx.x * span; base < cells; base += (int64_t)gridDim.x * span) {
+      float v[kRefUnroll];
+#pragma unroll
+      for (int u = 0; u < kRefUnroll; ++u) {
+        const int64_t c = base + u * kRefThreads + threadIdx.x;
+        v[u] = c < cells ? mp[c] : -1.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < kRefUnroll; ++u) {
+        const int64_t c = base + u * kRefThreads + threadIdx.x;
+        const int b = ref_bin_of(v[u], s.M);
+        if (b < 0 || b > last || c >= cells || !ref_valid(coef, shared, cells, j, c)) continue;
+        if (kCollect) {
+          const int32_t slot = atomicAdd(ref_n + j, 1);
+          if (slot < kRefMaxCells) ref_cell[(int64_t)j * kRefMaxCells + slot] = (int32_t)c;
+        } else {
+          atomicAdd(&h[b], 1);
+        }
+      }
+    }
+  }
+  if (!kCollect) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < kRefBins; b += blockDim.x)
+      if (h[b]) atomicAdd(hist + (int64_t)j * kRefBins + b, h[b]);
+  }
+}
+
+// Pass 2: per template the last bin whose cumulative count stays within the
+// cap (-1: the top bin alone exceeds it); clears the candidate counter.
+__global__ void k_ref_cut(const int32_t* __restrict__ hist, int32_t cap, int32_t* __restrict__ cut,
+                          int32_t* __restrict__ ref_n) {
+  const int32_t j = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  int32_t cum = 0, b = -1;
+  for (int k = 0; k < kRefBins; ++k) {
+    cum += hist[(int64_t)j * kRefBins + k];
+    if (cum > cap) break;
+    b = k;
+  }
+  cut[j] = b;
+  ref_n[j] = 0;
+}
+
+// Pass 4: the collected cells of a template in ascending index order
+// (bitonic sort in shared memory, padded with INT32_MAX).
+__global__ void __launch_bounds__(kRefSortThreads)
+k_ref_sort(const int32_t* __restrict__ ref_n, int32_t* __restrict__ ref_cell) {
+  __shared__ int32_t v[kRefMaxCells];
+  const int32_t j = blockIdx.x;
+  const int32_t n = min(ref_n[j], kRefMaxCells);
+  int32_t p2 = 1;
+  while (p2 < n) p2 <<= 1;
+  int32_t* cells = ref_cell + (int64_t)j * kRefMaxCells;
+  for (int i = threadIdx.x; i < p2; i += blockDim.x) v[i] = i < n ? cells[i] : 0x7fffffff;
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1) {
+    for (int d = k >> 1; d > 0; d >>= 1) {
+      for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+        const int o = i ^ d;
+        if (o > i) {
+          const bool up = (i & k) == 0;
+          const int32_t a = v[i], b = v[o];
+          if ((a > b) == up) {
+            v[i] = b;
+            v[o] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) cells[i] = v[i];
+}
+
+struct RefArgs {
+  const int32_t* rel_t;
+  const int64_t* t_base;
+  int32_t n_sft;
+  fmap_grid g;
+  const int64_t* ax;
+  const float2* wtab;
+  int32_t n_tab;
+  const int32_t* i0;
+  const int32_t* jend;
+  const float* antenna;
+  const float* fafb;
+  int32_t shared;
+  float* map;
+  int64_t cells;
+  const int32_t* ref_n;
+  const int32_t* ref_cell;
+  float* ref_fast;
+  double* ref_val;
+};
+
+// Pass 5: one warp per collected cell.  The lanes split the window's atoms
+// into 32 contiguous runs; an exponential run takes its first weight from an
+// FP64 exp and the rest as products of per-gap decays (e^{-T_sft/tau} for
+// one-SFT gaps), a table window evaluates w per atom, a rectangular one has
+// w = 1.  The seven FP64 sums meet in a fixed butterfly; lane 0 forms D and
+// 2F, records the fast and FP64 values and writes the FP64 value to the map.
+__global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t j = blockIdx.y;
+  const int32_t k = blockIdx.x * (kRefThreads / 32) + warp;
+  if (k >= min(A.ref_n[j], kRefMaxCells)) return;
+  const fmap_grid& g = A.g;
+  const int64_t slot = (int64_t)j * kRefMaxCells + k;
+  const int32_t c = A.ref_cell[slot];
+  const int32_t m = c / g.n_tau, nn = c - m * g.n_tau;
+  const int32_t i0 = A.i0[m], je = A.jend[c];
+  const int32_t len = max(0, je - i0);
+  const int64_t t0rel = grid_t0(g, A.ax, m) - *A.t_base;
+  const int64_t tau = grid_tau(g, A.ax, nn);
+  const double inv_tau = 1.0 / (double)tau;
+  const int32_t a_lo = i0 + (int32_t)((int64_t)len * lane / 32);
+  const int32_t a_hi = i0 + (int32_t)((int64_t)len * (lane + 1) / 32);
+  const int64_t n = A.n_sft;
+  const float* ant = A.antenna + (A.shared ? 0 : (int64_t)j * 3 * n);
+  const float* x = A.fafb + (int64_t)j * 4 * n;
+  const bool ex = g.window == FMAP_EXP, tw = g.window == FMAP_TABLE;
+  const double su = tw ? tab_scale(A.n_tab, exp_cut8_of(g), tau) : 0.0;
+  double s[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (a_lo < a_hi) {
+    double w = 1.0, rho1 = 1.0;
+    if (ex) {
+      w = exp(-(double)((int64_t)A.rel_t[a_lo] - t0rel) * inv_tau);
+      rho1 = exp(-(double)g.t_sft * inv_tau);
+    }
+    for (int32_t a = a_lo; a < a_hi; ++a) {
+      if (ex && a > a_lo) {
+        const int32_t gap = A.rel_t[a] - A.rel_t[a - 1];
+        w *= gap == (int32_t)g.t_sft ? rho1 : exp(-(double)gap * inv_tau);
+      }
+      if (tw) w = tab_weight64((double)((int64_t)A.rel_t[a] - t0rel) * su, A.wtab, A.n_tab);
+      const double w2 = w * w;
+      s[0] = fma(w2, (double)ant[a], s[0]);
+      s[1] = fma(w2, (double)ant[n + a], s[1]);
+      s[2] = fma(w2, (double)ant[2 * n + a], s[2]);
+      s[3] = fma(w, (double)x[a], s[3]);
+      s[4] = fma(w, (double)x[n + a], s[4]);
+      s[5] = fma(w, (double)x[2 * n + a], s[5]);
+      s[6] = fma(w, (double)x[3 * n + a], s[6]);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+    for (int q = 0; q < 7; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], d);
+  if (lane == 0) {
+    const double Aa = s[0], Bb = s[1], Cc = s[2];
+    const double D = Aa * Bb - Cc * Cc;
+    const bool ok = len >= 2 && D > 0.0;
+    double v = 0.0;
+    if (ok)
+      v = 2.0 * (Bb * (s[3] * s[3] + s[4] * s[4]) + Aa * (s[5] * s[5] + s[6] * s[6]) -
+                 2.0 * Cc * (s[3] * s[5] + s[4] * s[6])) / D;
+    float* mp = A.map + (int64_t)j * A.cells + c;
+    A.ref_fast[slot] = *mp;
+    A.ref_val[slot] = ok ? v : -1.0;
+    *mp = (float)v;
+  }
+}
+
+// Pass 6: one warp per template rebuilds its summary from the fast
+// statistics and the collected cells (fixed per-lane order, fixed butterfly).
+__global__ void __launch_bounds__(32)
+k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ cut,
+            const int32_t* __restrict__ ref_n, const int32_t* __restrict__ ref_cell,
+            const float* __restrict__ ref_fast, const double* __restrict__ ref_val, int32_t n_tau,
+            double log_prior, double tol, fmap_summary* __restrict__ out) {
+  const int32_t j = blockIdx.x;
+  const int lane = threadIdx.x;
+  const TStat s = st[j];
+  const int32_t n = min(ref_n[j], kRefMaxCells);
+  if (s.N <= 0 || n <= 0) return;   // the fast summary stands (flags 0)
+  const int64_t base = (int64_t)j * kRefMaxCells;
+  double mx = -1.0;
+  for (int32_t k = lane; k < n; k += 32) mx = fmax(mx, ref_val[base + k]);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+  if (mx < 0.0) return;   // no collected cell valid in FP64: keep the fast summary
+  double sub = 0.0, add = 0.0;
+  long long nv = 0;
+  int32_t arg = 0x7fffffff;
+  const double M = (double)s.M;
+  for (int32_t k = lane; k < n; k += 32) {
+    sub += exp(0.5 * ((double)ref_fast[base + k] - M));
+    const double v = ref_val[base + k];
+    if (v >= 0.0) {
+      add += exp(0.5 * (v - mx));
+      nv += 1;
+      if (v == mx) arg = min(arg, ref_cell[base + k]);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    sub += __shfl_xor_sync(0xffffffffu, sub, d);
+    add += __shfl_xor_sync(0xffffffffu, add, d);
+    nv += __shfl_xor_sync(0xffffffffu, nv, d);
+    arg = min(arg, __shfl_xor_sync(0xffffffffu, arg, d));
+  }
+  if (lane != 0) return;
+  const double Sp = exp(0.5 * (M - mx)) * fmax(s.S - sub, 0.0) + add;
+  const long long Np = s.N - n + nv;
+  const int32_t b = cut[j];
+  const double depth = b + 1 >= kRefBins ? (double)kRefWindow
+                                         : (double)(b + 1) * (double)kRefWindow / kRefBins;
+  fmap_summary o;
+  o.max2F = (float)mx;
+  o.m = arg / n_tau;
+  o.n = arg % n_tau;
+  o.flags = (int32_t)FMAP_SUMMARY_REFINED |
+            (depth > 2.0 * tol * fmax(mx, 1.0) ? (int32_t)FMAP_SUMMARY_ARGMAX_EXACT : 0);
+  o.logB = 0.5 * mx + log(Sp) - log((double)Np) + log_prior;
+  o.n_valid = Np;
+  out[j] = o;
+}
+
+cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
+                          fmap_summary* d_summary, cudaStream_t s) {
+  const int32_t cap = refine_cells_of(p);
+  const fmap_grid& g = p->grid;
+  const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
+  const int32_t T = p->n_templates;
+  if (cap <= 0 || !d_2F || !d_summary || T == 0 || cells == 0 || p->n_sft == 0)
+    return cudaSuccess;
+  Workspace& w = p->ws;
+  cudaError_t e = cudaMemsetAsync(w.ref_hist, 0, sizeof(int32_t) * kRefBins * (size_t)T, s);
+  if (e != cudaSuccess) return e;
+  const int32_t sh = a->shared_antenna ? 1 : 0;
+  const int64_t span = (int64_t)kRefThreads * kRefUnroll;
+  const int64_t want = std::max<int64_t>(1, ((int64_t)p->n_sm * 8 + T - 1) / T);
+  const unsigned gx = (unsigned)std::min<int64_t>((cells + span - 1) / span, want);
+  const dim3 grid(gx, (unsigned)T);
+  k_ref_scan<false><<<grid, kRefThreads, 0, s>>>(d_2F, w.coef, sh, cells, w.tstat, w.ref_hist,
+                                                 nullptr, nullptr, nullptr);
+  k_ref_cut<<<T, 32, 0, s>>>(w.ref_hist, cap, w.ref_bin, w.ref_n);
+  k_ref_scan<true><<<grid, kRefThreads, 0, s>>>(d_2F, w.coef, sh, cells, w.tstat, nullptr,
+                                                w.ref_bin, w.ref_n, w.ref_cell);
+  k_ref_sort<<<T, kRefSortThreads, 0, s>>>(w.ref_n, w.ref_cell);
+  RefArgs A;
+  A.rel_t = w.rel_t;
+  A.t_base = w.t_base;
+  A.n_sft = p->n_sft;
+  A.g = g;
+  A.ax = plan_axes(p);
+  A.wtab = w.wtab;
+  A.n_tab = p->n_tab;
+  A.i0 = w.i0;
+  A.jend = w.jend;
+  A.antenna = a->antenna;
+  A.fafb = a->fafb;
+  A.shared = sh;
+  A.map = d_2F;
+  A.cells = cells;
+  A.ref_n = w.ref_n;
+  A.ref_cell = w.ref_cell;
+  A.ref_fast = w.ref_fast;
+  A.ref_val = w.ref_val;
+  const int wpb = kRefThreads / 32;
+  k_ref_cells<<<dim3((unsigned)((cap + wpb - 1) / wpb), (unsigned)T), kRefThreads, 0, s>>>(A);
+  k_ref_final<<<T, 32, 0, s>>>(w.tstat, w.ref_bin, w.ref_n, w.ref_cell, w.ref_fast, w.ref_val,
+                               g.n_tau, p->log_prior, fast_tol(p), d_summary);
+  p->launches += 6;
+  return cudaGetLastError();
+}
+
+}  // namespace fmap

@@ -124,23 +124,30 @@ struct fmap_server_s {
   bool stop = false;
   std::thread worker;
   int64_t completed = 0;
+  int64_t peak_running = 0;
 };
 
 namespace fmap {
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-static void request_sizes(const Request& r, size_t* in_bytes, size_t* out_bytes) {
+// Bytes of a request's inputs and outputs.  The device always holds the map
+// (the refinement of the summaries reads and rewrites it); the pinned host
+// arena holds it only when the request asked for it.
+static void request_sizes(const Request& r, size_t* in_bytes, size_t* out_bytes,
+                          size_t* host_out_bytes) {
   const size_t n = (size_t)r.n_sft, T = (size_t)r.T;
   const size_t cells = (size_t)r.grid.n_t0 * (size_t)r.grid.n_tau;
   *in_bytes = align256(8 * n) + align256(4 * 3 * n * (r.shared ? 1 : T)) + align256(4 * 4 * n * T);
-  *out_bytes = align256(sizeof(fmap_summary) * T) + 256 + (r.want_map ? align256(4 * cells * T) : 0);
+  const size_t sums = align256(sizeof(fmap_summary) * T) + 256;
+  *out_bytes = sums + align256(4 * cells * T);
+  *host_out_bytes = sums + (r.want_map ? align256(4 * cells * T) : 0);
 }
 
 // Launch one admitted request on its slot's stream (lock held).
 static fmap_status launch_request(fmap_server_s* s, Request* r) {
-  size_t in_b, out_b;
-  request_sizes(*r, &in_b, &out_b);
+  size_t in_b, out_b, hout_b;
+  request_sizes(*r, &in_b, &out_b, &hout_b);
   char* d = s->dev_pool + r->dev_off;
   const uint32_t flags = r->shared ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA;
   const fmap_precision prec =
@@ -159,7 +166,7 @@ static fmap_status launch_request(fmap_server_s* s, Request* r) {
   q += align256(4 * 4 * n * T);
   fmap_summary* d_sum = (fmap_summary*)q;
   q += align256(sizeof(fmap_summary) * T) + 256;
-  float* d_map = r->want_map ? (float*)q : nullptr;
+  float* d_map = (float*)q;
   cudaStream_t st_ = s->streams[r->slot];
   const size_t cells = (size_t)r->grid.n_t0 * (size_t)r->grid.n_tau;
   if (n > 0) {
@@ -176,7 +183,7 @@ static fmap_status launch_request(fmap_server_s* s, Request* r) {
   if (T > 0)
     FMAP_CUDA(cudaMemcpyAsync(r->h_sum, d_sum, sizeof(fmap_summary) * T, cudaMemcpyDeviceToHost,
                               st_));
-  if (d_map && cells * T > 0)
+  if (r->want_map && cells * T > 0)
     FMAP_CUDA(cudaMemcpyAsync(r->h_map, d_map, 4 * cells * T, cudaMemcpyDeviceToHost, st_));
   FMAP_CUDA(cudaMemcpyAsync(r->h_err, r->plan->ws.dev_err, sizeof(uint32_t),
                             cudaMemcpyDeviceToHost, st_));
@@ -218,9 +225,8 @@ static void worker_loop(fmap_server_s* s) {
         st = FMAP_ERR_CUDA;
         err = cudaGetErrorString(q);
       } else if (*r->h_err) {
-        st = (*r->h_err & DEV_ERR_TIMEOUT) ? FMAP_ERR_TIMEOUT : FMAP_ERR_DATA;
-        err = (*r->h_err & DEV_ERR_TIMEOUT) ? "a bounded device wait gave up"
-                                             : "timestamps not strictly increasing or span >= 2^31 s";
+        st = dev_err_status(*r->h_err);
+        err = dev_err_message(*r->h_err);
       }
       finish_request(s, r, st, err);
       progress = true;
@@ -243,8 +249,18 @@ static void worker_loop(fmap_server_s* s) {
       r->slot = slot;
       s->slots[slot] = r;
       r->state = Request::RUNNING;
+      int64_t run = 0;
+      for (auto* q : s->slots) run += q != nullptr;
+      s->peak_running = std::max(s->peak_running, run);
       const fmap_status st = launch_request(s, r);
-      if (st != FMAP_OK) finish_request(s, r, st, fmap_last_error());
+      if (st != FMAP_OK) {
+        // copies and kernels queued before the failure may still be writing
+        // the request's device range: let them finish before it is reused
+        const std::string why = fmap_last_error();
+        cudaStreamSynchronize(s->streams[slot]);
+        cudaGetLastError();
+        finish_request(s, r, st, why);
+      }
       progress = true;
     }
     if (progress) {
@@ -362,10 +378,10 @@ fmap_status fmap_submit(fmap_server_t* s, const fmap_grid* grid, const fmap_atom
     delete r;
     return st;
   }
-  size_t in_b, out_b;
-  request_sizes(*r, &in_b, &out_b);
+  size_t in_b, out_b, hout_b;
+  request_sizes(*r, &in_b, &out_b, &hout_b);
   r->dev_bytes = align256(r->ws_bytes) + in_b + out_b;
-  r->pin_bytes = in_b + out_b;
+  r->pin_bytes = in_b + hout_b;
   if (r->dev_bytes > s->dev_alloc.capacity()) {
     delete r;
     set_error("request larger than the server's device memory budget");
@@ -442,6 +458,13 @@ fmap_status fmap_poll(fmap_server_t* s, uint64_t ticket, fmap_summary* h_summary
   s->all.erase(it);
   delete r;
   return st;
+}
+
+fmap_status fmap_server_peak(fmap_server_t* s, int64_t* peak_running) {
+  if (!s || !peak_running) return FMAP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *peak_running = s->peak_running;
+  return FMAP_OK;
 }
 
 fmap_status fmap_server_stats(fmap_server_t* s, int64_t* queued, int64_t* running,

@@ -16,7 +16,7 @@ import pytest
 import oracle
 import synth
 from synth import EXP, RECT
-from tests.parity_util import (FP64_CLASS, LOGB_TOL, TOL, check_map, check_summary, rel_err,
+from tests.parity_util import (LOGB_TOL, TOL, check_map, check_summary, rel_err,
                                run_gpu)
 
 pytestmark = pytest.mark.gpu
@@ -46,14 +46,16 @@ def test_exp16_full_map(exp16, prec):
             pytest.skip(f"{prec} not built")
         raise
     worst = check_map(got, ref, valid, TOL[prec])
-    fe = 0.0 if prec in FP64_CLASS else 0.5 * float(np.abs(got - ref)[valid].max())
-    check_summary(gs, ref, valid, TOL[prec], LOGB_TOL, fe)
+    rep = []
+    near, ties, dlogb = check_summary(gs, ref, valid, TOL[prec], LOGB_TOL, report=rep)
+    print("\n".join(rep))
     inj = inst.injections[0]
     # the injected template peaks near its true (t0, tau)
     m_true = inj.t0 // inst.grid.dt0
     n_true = (inj.tau - inst.grid.tau_min) // inst.grid.dtau
     assert abs(int(gs["m"][0]) - m_true) <= 15 and abs(int(gs["n"][0]) - n_true) <= 40
-    print(f"exp16 {prec}: max rel 2F err {worst:.3g}")
+    print(f"exp16 {prec}: max rel 2F err {worst:.3g}, max |dlogB| {dlogb:.2e}, near ties {near}, "
+          f"FP64 ties {ties}")
 
 
 @pytest.fixture(scope="module")
@@ -124,7 +126,7 @@ def test_batched_exp_sampled_cells(batch_exp, prec):
     ref0, valid0, _ = oracle.fmap(sub.t, sub.antenna, sub.fafb, g.as_tuple(), mode="fast")
     got0 = m[0:1].cpu().numpy().astype(np.float64)
     check_map(got0, ref0, valid0, TOL[prec])
-    fe = 0.0 if flags else 0.5 * float(np.abs(got0 - ref0)[valid0].max())
-    check_summary(gs[:1], ref0, valid0, TOL[prec], LOGB_TOL, fe)
+    near, ties, dlogb = check_summary(gs[:1], ref0, valid0, TOL[prec], LOGB_TOL)
+    print(f"batched exp {prec}: injected template |dlogB| {dlogb:.2e}")
     del m
     plan.close()

@@ -11,7 +11,7 @@ import pytest
 import oracle
 import synth
 from synth import EXP, RECT, T_SFT, Grid
-from tests.parity_util import TOL, check_map
+from tests.parity_util import LOGB_TOL, TOL, check_map, check_summary
 
 pytestmark = pytest.mark.gpu
 
@@ -67,13 +67,37 @@ def test_alone_equals_mixed_and_matches_oracle(reqs):
         assert np.array_equal(m, solo[k][1])
     q, r, c = mixed.stats()
     assert q == 0 and r == 0 and c == len(reqs)
+    # the burst really overlapped on the device
+    assert mixed.peak() > 1
     mixed.close()
-    for k in (0, 1, 5):
-        inst = reqs[k]
+    for k, inst in enumerate(reqs):
         ref, valid, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, inst.grid.as_tuple(),
                                     mode="fast")
         prec = "fp64" if inst.grid.window == RECT else "bf16x3"
         check_map(solo[k][1].astype(np.float64), ref, valid, TOL[prec])
+        check_summary(solo[k][0], ref, valid, TOL[prec], LOGB_TOL)
+
+
+def test_nonfinite_atoms_are_reported(reqs):
+    """A request whose atoms hold a NaN (or an infinity) fails with
+    FMAP_ERR_NONFINITE; the server keeps serving."""
+    srv = fm.Server(device_mem_budget=1 << 30, pinned_bytes=64 << 20, max_inflight=2)
+    inst = reqs[2]
+    bad = inst.fafb.copy()
+    bad[0, 1, 7] = np.nan
+    tk = srv.submit(inst.grid, inst.t, inst.antenna, bad)
+    with pytest.raises(fm.FmapError) as e:
+        srv.poll(tk, wait_us=-1)
+    assert e.value.status == fm.FMAP_ERR_NONFINITE
+    ant = inst.antenna.copy()
+    ant[..., 3] = np.inf
+    tk = srv.submit(inst.grid, inst.t, ant, inst.fafb)
+    with pytest.raises(fm.FmapError) as e:
+        srv.poll(tk, wait_us=-1)
+    assert e.value.status == fm.FMAP_ERR_NONFINITE
+    tk = srv.submit(inst.grid, inst.t, inst.antenna, inst.fafb)
+    assert srv.poll(tk, wait_us=-1)[0] == fm.FMAP_OK
+    srv.close()
 
 
 def test_admission_waits_for_memory(reqs):
@@ -83,6 +107,9 @@ def test_admission_waits_for_memory(reqs):
     big = reqs[3]
     need = fm.fmap_workspace_bytes(big.grid, big.n_sft, big.n_templates,
                                    fm.FMAP_BF16X3 if big.grid.window == EXP else fm.FMAP_FP64)
+    # plus its atoms and outputs (the device always holds the request's map)
+    need += (4 * big.grid.n_t0 * big.grid.n_tau + 32 + 16 * big.n_sft + 12) * big.n_templates + \
+        8 * big.n_sft + 12 * big.n_sft + 8192
     srv = fm.Server(device_mem_budget=max(need * 3, 2 << 20), pinned_bytes=256 << 20,
                     max_inflight=8)
     tickets = [_run(srv, reqs[3], want_map=False) for _ in range(10)]

@@ -1,7 +1,10 @@
 """Host logic of a split F-map: per-shard summaries (t0-row shards) combine
-into the summary of the whole map, directly and over a 2-rank gloo process
-group on CPU.  The shard summaries here come from the oracle, so the test
-exercises only the combination rule."""
+into the summary of the whole map through the library's
+fmap_combine_summaries (a host function of the C ABI, no GPU needed),
+directly and over a 2-rank gloo process group on CPU.  The shard summaries
+here come from the oracle, so the test exercises only the combination rule;
+shards without valid cells follow the library's empty-summary convention
+(max2F = 0, m = n = -1, logB = NaN)."""
 
 import math
 import os
@@ -25,7 +28,7 @@ def _records(s, log_prior=0.0):
     for j in range(T):
         nv = int(s["n_valid"][j])
         r[j]["n_valid"] = nv
-        r[j]["max2F"] = np.float32(s["max2F"][j]) if nv else -1.0
+        r[j]["max2F"] = np.float32(s["max2F"][j]) if nv else 0.0
         r[j]["m"] = s["m"][j] if nv else -1
         r[j]["n"] = s["n"][j] if nv else -1
         r[j]["logB"] = s["logB"][j] if nv else float("nan")
@@ -78,6 +81,24 @@ def test_combine_ties_empty_shards_and_all_invalid():
     assert got[0]["n_valid"] == whole[0]["n_valid"]
     assert math.isclose(got[0]["logB"], whole[0]["logB"], rel_tol=0, abs_tol=1e-12)
     assert got[1]["n_valid"] == 0 and got[1]["m"] == -1 and math.isnan(got[1]["logB"])
+    assert got[1]["max2F"] == 0.0 and got[1]["n"] == -1
+
+
+def test_combine_flags_are_common_to_nonempty_shards():
+    from paper_1805_05652_gb300 import FMAP_SUMMARY_ARGMAX_EXACT, FMAP_SUMMARY_REFINED
+
+    a = np.zeros(1, dtype=SUMMARY_DTYPE)
+    b = np.zeros(1, dtype=SUMMARY_DTYPE)
+    e = np.zeros(1, dtype=SUMMARY_DTYPE)
+    a[0] = (5.0, 1, 2, FMAP_SUMMARY_REFINED | FMAP_SUMMARY_ARGMAX_EXACT, 0.5, 10)
+    b[0] = (7.0, 0, 3, FMAP_SUMMARY_REFINED, 1.5, 30)
+    e[0] = (0.0, -1, -1, 0, float("nan"), 0)          # empty shard: ignored
+    got = shards.combine([a, e, b], [0, 4, 9])[0]
+    assert got["flags"] == FMAP_SUMMARY_REFINED
+    assert (got["m"], got["n"]) == (9, 3) and got["max2F"] == np.float32(7.0)
+    assert got["n_valid"] == 40
+    want = math.log((10 * math.exp(0.5) + 30 * math.exp(1.5)) / 40)
+    assert math.isclose(got["logB"], want, rel_tol=0, abs_tol=1e-12)
 
 
 def _free_port():
