@@ -1,23 +1,35 @@
 #!/usr/bin/env python3
-"""Throughput of the transient F-statistic map on GB300.
+"""Throughput and accuracy of the transient F-statistic map on one GB300.
 
 Metric: F-map (t0, tau)-SFT terms per second: over all templates and all
 cells with >= 2 SFTs in their window, the number of SFTs inside the window
 (App. A, Eq. Nsums-exp for the exponential window), per second of device
-time.  One step = one fmap_compute_* call over the whole workload with the
-inputs resident in HBM (map and summaries written).  Default workload: the
-16-template exponential F-map (2000 merged SFTs of 2 detectors, 1000 x 1000
-(t0, tau) cells, 1 injected template); see synth.config_exp16.
+time, with the inputs resident in HBM and the map and summaries written.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--precision bf16x3|tf32|fp32|fp64] [--workload exp16|batch_rect|uneven]
+Default run (no --workload): one JSON line whose headline is the largest
+single-GPU workload, the batched exponential F-map (1024 templates x 5000
+SFTs x 2000 x 2000 (t0, tau) cells) computed by the FP64-class decayed-suffix
+recurrence; beside it (``also``) the tensor-core forms (BF16x3, 3xTF32) and
+the plain FP32 contraction on the same workload, and (``configs``) the other
+four workloads: the small rectangular map, the 16-template exponential map
+(FP32 against FP64), the 1024-template rectangular batch, the uneven batch
+of 4096 instances (one captured graph) and the serving loop (Poisson
+arrivals).  Every result carries its accuracy against the FP64 oracle on
+sampled templates (computed outside the timed regions).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload exp16|batch_exp|batch_rect|small_rect|uneven
+                    [--precision P] [--templates T] ...   (one workload only)
+
 For N > 1 run under torch.distributed.run: every rank computes its own
-workload (different seeds; weak scaling), timing is max over ranks.
+workload (independent replicas with different seeds; weak scaling), timing is
+max over ranks.
 """
 
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -35,19 +47,31 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 WORKLOADS = {
+    "batch_exp": "exp-window F-map, 1024 templates x 5000 SFTs (1 detector, gap-free), "
+                 "2000 x 2000 (t0, tau) cells at T_sft steps, tau in [T_sft, 2000 T_sft], cut at "
+                 "3 tau, 8 templates injected",
     "exp16": "exp-window F-map, 16 templates, 2000 merged SFTs (2 detectors, 10% gaps each), "
              "1000 x 1000 (t0, tau) cells at T_sft steps, tau in [T_sft, 1000 T_sft], cut at 3 tau",
+    "small_rect": "rect-window F-map, 1 template, 200 SFTs (10% gaps), 200 x 200 cells",
     "batch_rect": "rect-window F-map, 1024 templates x 5000 SFTs, 2000 x 2000 (t0, tau) cells",
     "uneven": "uneven batch: 4096 single-template instances, N_SFT log-uniform in [100, 8000], "
               "N_t0, N_tau uniform in {50..2000}, rect/exp 50/50, 5% injected; one captured "
               "graph of persistent per-phase launches (fmap_batch_run), autotuned",
+    "serving": "Poisson arrivals (200/s) of F-map requests with the uneven batch's size mix and "
+               "1-64 templates each, through fmap_submit / fmap_poll",
 }
 L2_FLUSH_BYTES = 256 << 20
+# templates of the batched workloads whose maps are checked against the oracle:
+# two injected (rectangular and exponential envelopes) and two noise-only
+SAMPLE_TEMPLATES = (0, 128, 511, 1023)
+DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16x3": "bf16x3", "rec": "f32x2"}
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
+
+# ------------------------------------------------------------------ inputs --
 
 def jitter_axes(grid, seed):
     """Explicit axes for a uniform grid: every t0 and tau moved later by a
@@ -75,8 +99,8 @@ def window_table(shape, cut8=0, n=1024):
 
 
 def make_workload(name, rank, templates=None, exp_cut8=0, axes=False, table=None):
+    kw = {} if templates is None else {"n_templates": templates}
     if name == "exp16":
-        kw = {} if templates is None else {"n_templates": templates}
         inst = synth.config_exp16(seed=synth.BASE_SEED + 1 + 1000 * rank, **kw)
         inst.grid.exp_cut8 = exp_cut8   # window length exp_cut8 tau / 8 (0: 3 tau)
         if axes:
@@ -86,30 +110,29 @@ def make_workload(name, rank, templates=None, exp_cut8=0, axes=False, table=None
             inst.grid.window_table = window_table(table, exp_cut8)
         return inst
     if name == "batch_rect":
-        kw = {} if templates is None else {"n_templates": templates}
         return synth.config_batched(window=synth.RECT, seed=synth.BASE_SEED + 2 + 1000 * rank, **kw)
+    if name == "batch_exp":
+        return synth.config_batched(window=synth.EXP, seed=synth.BASE_SEED + 2 + 1000 * rank, **kw)
+    if name == "small_rect":
+        return synth.config_small_rect(seed=synth.BASE_SEED + 1000 * rank)
     raise SystemExit(f"unknown workload {name}")
 
 
-def count_terms(grid, t):
-    """(terms, cells with >= 2 SFTs) of a grid: the library's host count for
-    uniform grids; for explicit axes the same rule with numpy searches."""
-    if not grid.has_axes:
-        import paper_1805_05652_gb300 as fm
-        return fm.fmap_count_terms(grid, t)
+def count_terms_np(grid, t):
+    """(terms, cells with >= 2 SFTs) of a grid by the window rule (an SFT at t
+    is inside (t0, tau) iff t0 <= t and t + T_sft <= t0 + L(tau)), with numpy
+    searches; no library code."""
     t0 = grid.t0()
+    L = np.array([grid.window_len(int(v)) for v in grid.tau()], dtype=np.int64)
     i0 = np.searchsorted(t, t0, side="left")
-    lim = t0[:, None] + np.array([grid.window_len(int(v)) for v in grid.tau()])[None, :] - grid.t_sft
-    j = np.maximum(np.searchsorted(t, lim, side="right"), i0[:, None])
-    c = j - i0[:, None]
-    return int(c[c >= 2].sum()), int((c >= 2).sum())
-
-
-# DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
-# capture of the unchanged kernel on the workload (a 64-template cut of the
-# rect batch, scaled to its 1024 templates: the traffic grows with them).
-NCU_TRAFFIC = {("exp16", "bf16x3"): 31.5e6,
-               ("batch_rect", "fp64"): 1078.0e6 * 16}
+    terms, cells2 = 0, 0
+    for a in range(0, len(t0), 256):
+        lim = t0[a:a + 256, None] + L[None, :] - grid.t_sft
+        j = np.maximum(np.searchsorted(t, lim, side="right"), i0[a:a + 256, None])
+        c = j - i0[a:a + 256, None]
+        terms += int(c[c >= 2].sum())
+        cells2 += int((c >= 2).sum())
+    return terms, cells2
 
 
 def load_peaks():
@@ -121,22 +144,23 @@ def load_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+# DRAM bytes (read + written) per launch of a dominant kernel, from one ncu
+# capture of the unchanged kernel (profiles/): a 64-template cut of the rect
+# batch, scaled to its 1024 templates (the traffic grows with them).
+NCU_TRAFFIC = {("batch_rect", "fp64"): 1078.0e6 * 16}
+
+
 # ------------------------------------------------------------------ clocks --
 
-# default timed steps: about a second of device work, so that the clock
-# samples (every 20 ms) fall inside the timed region
-DEFAULT_STEPS = {"exp16": 1000, "batch_rect": 100, "uneven": 5}
-
-
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons (every 20 ms).
-    begin() / end() mark the timed region on the host clock; the summary
-    keeps the samples that arrived inside it (falling back to all samples,
-    and saying so, when the region is shorter than the sampling period)."""
+    """nvidia-smi samples of SM clock and throttle reasons (every 20 ms),
+    each stamped with nvidia-smi's own sample time.  begin() / end() mark the
+    timed region on the wall clock; the summary keeps the samples taken
+    inside it (all samples, and says so, when it is shorter than a period)."""
 
     PERIOD_MS = 20
 
-    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -146,8 +170,8 @@ class ClockSampler:
         self.proc = None
         self.thread = None
         self.error = None
-        self.t_begin = None
-        self.t_end = None
+        self.spans = []
+        self._t0 = None
 
     def start(self):
         try:
@@ -161,17 +185,29 @@ class ClockSampler:
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
 
+    @staticmethod
+    def _stamp(s):
+        """nvidia-smi's 'YYYY/MM/DD HH:MM:SS.mmm' (local time) as epoch seconds."""
+        try:
+            return datetime.datetime.strptime(s.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append((time.monotonic(), parts))
+            if len(parts) >= 10:
+                ts = self._stamp(parts[0])
+                if ts is not None:
+                    self.rows.append((ts, parts[1:]))
 
     def begin(self):
-        self.t_begin = time.monotonic()
+        self._t0 = time.time()
 
     def end(self):
-        self.t_end = time.monotonic()
+        if self._t0 is not None:
+            self.spans.append((self._t0, time.time()))
+        self._t0 = None
 
     def stop(self):
         if self.proc:
@@ -189,11 +225,8 @@ class ClockSampler:
         rows = [(t, r) for t, r in self.rows if not self.uuid or self.uuid in r[0]] or self.rows
         if not rows:
             return {"error": "no nvidia-smi samples"}
-        # a line arrives a few ms after its sample: allow one period of lag
-        lag = self.PERIOD_MS / 1e3
-        inside = [(t, r) for t, r in rows if self.t_begin is not None and self.t_end is not None
-                  and self.t_begin <= t <= self.t_end + lag]
-        scope = "timed region" if inside else "whole run (timed region shorter than a sample)"
+        inside = [(t, r) for t, r in rows if any(a <= t <= b for a, b in self.spans)]
+        scope = "timed regions" if inside else "whole run (timed regions shorter than a sample)"
         n_total = len(rows)
         rows = [r for _, r in (inside or rows)]
 
@@ -211,10 +244,51 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows), "samples_total": n_total, "scope": scope,
-                "period_ms": self.PERIOD_MS}
+                "period_ms": self.PERIOD_MS, "stamp": "nvidia-smi timestamp field"}
+
+
+# ---------------------------------------------------------------- accuracy --
+
+def accuracy(fm, oracle, got_map, summ, ref, valid, templates=None):
+    """Per-result accuracy against the FP64 oracle: max relative 2F error
+    (floor 1) over the checked maps, max |dlogB|, argmax matches (exact cell)
+    and near ties (oracle top-2 gap within 2e-3 of the maximum)."""
+    rs = oracle.summary(ref, valid)
+    err = np.abs(got_map - ref) / np.maximum(np.abs(ref), 1.0)
+    worst = float(err[valid].max()) if valid.any() else 0.0
+    dlogb, match, near, flagged = 0.0, 0, 0, 0
+    want = fm.FMAP_SUMMARY_REFINED | fm.FMAP_SUMMARY_ARGMAX_EXACT
+    n = ref.shape[0]
+    for j in range(n):
+        if rs["n_valid"][j] == 0:
+            match += int(summ["m"][j] == -1)
+            continue
+        dlogb = max(dlogb, abs(float(summ["logB"][j]) - float(rs["logB"][j])))
+        match += int((int(summ["m"][j]), int(summ["n"][j])) == (int(rs["m"][j]), int(rs["n"][j])))
+        flat = np.where(valid[j], ref[j], -np.inf).ravel()
+        top2 = np.partition(flat, -2)[-2:] if flat.size > 1 else np.array([-np.inf, 0.0])
+        near += int(rs["max2F"][j] - top2.min() <= 2e-3 * max(rs["max2F"][j], 1.0))
+        flagged += int((int(summ["flags"][j]) & want) == want)
+    out = {"max_rel_2F_err": worst, "max_abs_dlogB": dlogb, "argmax_match": f"{match}/{n}",
+           "near_ties": near, "refined_exact_argmax": f"{flagged}/{n}"}
+    if templates is not None:
+        out["templates"] = list(templates)
+    return out
 
 
 # ------------------------------------------------------------ cpu baseline --
+
+def sample_grid(g, rows):
+    stride = max(1, g.n_t0 // rows)
+    sg = synth.Grid(g.t0_min + stride // 2 * g.dt0, g.dt0 * stride, min(rows, g.n_t0),
+                    g.tau_min, g.dtau, g.n_tau, g.window, g.t_sft, g.exp_cut8)
+    if g.has_axes:   # every stride-th t0 of the explicit axes
+        sg.t0_values = tuple(g.t0_values[stride // 2::stride][:sg.n_t0])
+        sg.n_t0 = len(sg.t0_values)
+        sg.tau_values = g.tau_values
+    sg.window_table = g.window_table
+    return sg
+
 
 def cpu_baseline(inst, target_s=12.0):
     """The CPU oracle (fast mode, FP64, OpenMP on all host cores) on a bounded
@@ -224,27 +298,13 @@ def cpu_baseline(inst, target_s=12.0):
     oracle.build()
     g = inst.grid
 
-    def sample_grid(rows):
-        stride = max(1, g.n_t0 // rows)
-        sg = synth.Grid(g.t0_min + stride // 2 * g.dt0, g.dt0 * stride,
-                        min(rows, g.n_t0), g.tau_min, g.dtau, g.n_tau, g.window, g.t_sft,
-                        g.exp_cut8)
-        if g.has_axes:   # every stride-th t0 of the explicit axes
-            sg.t0_values = tuple(g.t0_values[stride // 2::stride][:sg.n_t0])
-            sg.n_t0 = len(sg.t0_values)
-            sg.tau_values = g.tau_values
-        sg.window_table = g.window_table
-        return sg
-
     def run(rows):
-        sg = sample_grid(rows)
+        sg = sample_grid(g, rows)
         t0 = time.perf_counter()
         oracle.fmap(inst.t, inst.antenna, inst.fafb, sg.as_tuple(), mode="fast")
         return time.perf_counter() - t0, sg
 
-    import paper_1805_05652_gb300 as fm
-
-    rows = 2
+    rows = 1
     dt, sg = run(rows)
     while dt < 0.5 and rows < g.n_t0:
         rows = min(g.n_t0, rows * 4)
@@ -252,12 +312,163 @@ def cpu_baseline(inst, target_s=12.0):
     per_row = dt / sg.n_t0
     rows = int(min(g.n_t0, max(1, target_s / max(per_row, 1e-9))))
     dt, sg = run(rows)
-    terms = count_terms(sg, inst.t)[0] * inst.n_templates
+    terms = count_terms_np(sg, inst.t)[0] * inst.n_templates
     return {"value": terms / dt, "unit": "terms/s", "cores": oracle.max_threads(),
             "kind": "oracle",
             "sample": f"{sg.n_t0} of {g.n_t0} t0 rows (every {g.n_t0 // max(1, sg.n_t0)}th), "
                       f"all {g.n_tau} tau, all {inst.n_templates} templates; "
                       f"{terms:.3e} terms in {dt:.2f} s"}, sg, terms
+
+
+# ------------------------------------------------------------ one workload --
+
+class Runner:
+    """Times plans of one workload on resident inputs (map and summaries
+    written), L2 flushed between timed steps."""
+
+    def __init__(self, fm, torch, dev, inst, dist, clocks):
+        self.fm, self.torch, self.dev, self.inst, self.dist, self.clocks = \
+            fm, torch, dev, inst, dist, clocks
+        self.stream = torch.cuda.current_stream(dev)
+        self.t = torch.from_numpy(inst.t).to(dev)
+        self.ant = torch.from_numpy(inst.antenna).to(dev)
+        self.x = torch.from_numpy(inst.fafb).to(dev)
+        g = inst.grid
+        T = inst.n_templates
+        self.map = torch.empty((T, g.n_t0, g.n_tau), dtype=torch.float32, device=dev)
+        self.sum = torch.empty((T, 32), dtype=torch.uint8, device=dev)
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def plan(self, prec, extra_flags=0):
+        fm, inst = self.fm, self.inst
+        flags = extra_flags | (0 if inst.shared_antenna else fm.FMAP_PLAN_PER_TEMPLATE_ANTENNA)
+        if prec == "rec":
+            return fm.Plan(inst.grid, inst.n_sft, inst.n_templates, "fp64",
+                           flags | fm.FMAP_PLAN_EXP_RECURRENCE)
+        return fm.Plan(inst.grid, inst.n_sft, inst.n_templates, prec, flags)
+
+    def step(self, p):
+        p.compute(self.t, self.ant, self.x, out_map=self.map, out_summary=self.sum,
+                  stream=self.stream)
+
+    def time(self, p, steps, warmup):
+        """(per-step ms list, per-phase ms of one call, kernels launched)."""
+        torch, fm = self.torch, self.fm
+        for _ in range(warmup):
+            self.step(p)
+        torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        fm.fmap_plan_enable_timing(p.handle, True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        if self.clocks:
+            self.clocks.begin()
+        for k in range(steps):
+            self.flush.fill_(float(k))                     # untimed: evict the L2
+            evs[k][0].record(self.stream)
+            self.step(p)
+            evs[k][1].record(self.stream)
+        torch.cuda.synchronize()
+        if self.clocks:
+            self.clocks.end()
+        if self.dist:
+            self.dist.barrier()
+        per = [a.elapsed_time(b) for a, b in evs]
+        ph, calls, launches = fm.fmap_plan_read_timing(p.handle)
+        fm.fmap_plan_enable_timing(p.handle, False)
+        st = p.status()
+        if st != fm.FMAP_OK:
+            raise SystemExit(f"device status {fm.status_string(st)}")
+        return per, ph / max(calls, 1), launches
+
+    def sampled(self, templates):
+        """Host copies of the map rows and summaries of some templates."""
+        idx = self.torch.tensor(list(templates), device=self.dev)
+        m = self.map.index_select(0, idx).cpu().numpy().astype(np.float64)
+        s = self.fm.summary_to_numpy(self.sum.index_select(0, idx))
+        return m, s
+
+
+def oracle_of(inst, templates=None, mode="fast"):
+    import oracle
+
+    oracle.build()
+    sub = inst if templates is None else inst.templates(list(templates))
+    ref, valid, _ = oracle.fmap(sub.t, sub.antenna, sub.fafb, sub.grid.as_tuple(), mode=mode)
+    return ref, valid
+
+
+def roofline_exp(peaks, peak_src, prec, terms, dom_ms, n_tau, n_sft, T, cells):
+    """Roofline of the exp path's dominant kernel (phase 2).  Tensor forms:
+    8 flops per (cell, SFT, template) term (multiply + add on 4 data
+    columns) against the kind's tensor peak.  FP32 plain: the same flops
+    against the FP32 FMA peak.  Recurrence: FP32-pipe operations, 11 per
+    compensated recurrence step (per tau, data column, template and SFT) plus
+    13 per (cell, template) evaluation, against the FP32 pipe's issue rate."""
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    if prec in ("bf16x3", "tf32"):
+        flops = 8.0 * terms
+        if prec == "bf16x3":
+            peak, src = peaks["bf16_tflops"], f"bf16 dense, {peak_src}"
+        else:
+            peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+            src = f"tf32 = bf16 x 1.1/2.25 nominal, {peak_src}"
+        ach = flops / (dom_ms / 1e3) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": "exp contraction (phase 2)",
+                "peak_source": src, "work": "8 flops per (cell, SFT, template) term"}
+    if prec == "rec":
+        ops = 11.0 * 4 * n_tau * n_sft * T + 13.0 * cells * T
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        ach = ops / (dom_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s",
+                "frac": ach / peak, "traffic": None, "kernel": "exp recurrence (phase 2)",
+                "peak_source": "FP32 pipe: 152 SM x 128 lanes x max SM clock",
+                "work": "11 ops per compensated recurrence step (tau, column, template, SFT) + "
+                        "13 per (cell, template)"}
+    flops = 8.0 * terms
+    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    ach = flops / (dom_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "kernel": "exp contraction (phase 2)",
+            "peak_source": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock",
+            "work": "8 flops per (cell, SFT, template) term"}
+
+
+def time_forms(run, forms, steps, warmup, terms, acc_templates=None, ref=None, valid=None,
+               roof=None):
+    """Times each precision form of a workload and checks its accuracy."""
+    import oracle
+
+    fm = run.fm
+    out = {}
+    for prec in forms:
+        try:
+            p = run.plan(prec)
+        except fm.FmapError as e:
+            out[prec] = {"error": str(e)}
+            continue
+        per, ph, launches = run.time(p, steps, warmup)
+        p.close()
+        ms = statistics.mean(per)
+        rec = {"value": terms / (ms / 1e3), "unit": "terms/s", "ms_per_step": ms,
+               "dtype": DTYPE[prec], "phases_ms": [float(v) for v in ph], "steps": steps,
+               "kernel_launches_per_step": launches / max(steps, 1)}
+        if roof:
+            rec["roofline"] = roof(prec, float(ph[2]))
+        if ref is not None:
+            if acc_templates is None:
+                m = run.map.cpu().numpy().astype(np.float64)
+                s = fm.summary_to_numpy(run.sum)
+            else:
+                m, s = run.sampled(acc_templates)
+            rec["accuracy"] = accuracy(fm, oracle, m, s, ref, valid, acc_templates)
+        out[prec] = rec
+        log(f"  {prec}: {ms:.3f} ms/step, {rec['value']:.3e} terms/s",
+            rec.get("accuracy", {}).get("max_abs_dlogB", ""))
+    return out
 
 
 # -------------------------------------------------------------------- main --
@@ -266,40 +477,48 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: about a second of work: exp16 1000, "
-                         "batch_rect 100, uneven 5; the reference arm 5)")
+                    help="timed steps of the headline (default 20; single workloads about a "
+                         "second of work; the reference arm 5)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="time one workload only (profiling runs)")
     ap.add_argument("--precision", default=None)
-    ap.add_argument("--workload", default="exp16", choices=sorted(WORKLOADS))
     ap.add_argument("--exp-cut8", type=int, default=0,
                     help="exp16: window length in eighths of tau (0: 3 tau, Eq. winexp)")
     ap.add_argument("--grid-axes", action="store_true",
                     help="exp16: explicit non-uniform (t0, tau) axes (seeded jitter of the steps)")
     ap.add_argument("--window-table", default=None, choices=["exp", "bump"],
                     help="exp16: a generic (table) window of 1024 samples instead of exp")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--also", default="fp32,tf32,rec",
-                    help="comma list of extra precisions timed beside the headline")
     ap.add_argument("--templates", type=int, default=None,
                     help="override the workload's template count (profiling runs)")
-    ap.add_argument("--serving-requests", type=int, default=1000,
-                    help="requests of the serving measurement added to the line (0: skip)")
     ap.add_argument("--instances", type=int, default=4096,
                     help="instances of the uneven workload")
+    ap.add_argument("--uneven-window", default="both", choices=["rect", "exp", "both"],
+                    help="uneven workload: keep only instances of one window (profiling runs)")
+    ap.add_argument("--uneven-nsft", type=int, nargs=2, default=(0, 1 << 30),
+                    metavar=("MIN", "MAX"), help="uneven workload: keep MIN <= N_SFT <= MAX")
+    ap.add_argument("--profile-phases", action="store_true",
+                    help="uneven workload: run the batch once phase by phase (no graph) and "
+                         "print the per-phase milliseconds (profiling runs)")
     ap.add_argument("--budget-gb", type=float, default=24.0,
                     help="uneven workload: batch workspace budget (GB)")
+    ap.add_argument("--serving-requests", type=int, default=10_000)
+    ap.add_argument("--serving-warmup-s", type=float, default=5.0)
+    ap.add_argument("--quick", action="store_true",
+                    help="default run with smaller sub-records (development runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    if args.steps is None:
-        args.steps = 5 if args.impl == "reference" else DEFAULT_STEPS.get(args.workload, 30)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
+        if args.steps is None:
+            args.steps = 5
         return reference_arm(args, rank, world)
 
     import torch
@@ -313,77 +532,6 @@ def main():
         import torch.distributed as dist  # noqa: F811
         dist.init_process_group("nccl", device_id=dev)
     fm.build()
-
-    if args.workload == "uneven":
-        result = run_uneven(args, fm, torch, dev, dist, rank, world)
-        if dist:
-            dist.barrier()
-            dist.destroy_process_group()
-        if result is not None:
-            print(json.dumps(result), flush=True)
-        return
-
-    inst = make_workload(args.workload, rank, args.templates, args.exp_cut8, args.grid_axes,
-                         args.window_table)
-    g = inst.grid
-    window = g.window
-    precision = args.precision
-    if precision is None:
-        precision = "fp64" if window == synth.RECT else "bf16x3"
-    def make_plan(prec):
-        if prec == "rec":
-            return fm.Plan(g, inst.n_sft, inst.n_templates, "fp64", fm.FMAP_PLAN_EXP_RECURRENCE)
-        return fm.Plan(g, inst.n_sft, inst.n_templates, prec)
-
-    try:
-        plan = make_plan(precision)
-    except fm.FmapError as e:
-        if e.status != fm.FMAP_ERR_UNSUPPORTED or args.precision is not None:
-            raise
-        precision = "fp32"
-        plan = make_plan(precision)
-
-    stream = torch.cuda.current_stream(dev)
-    t = torch.from_numpy(inst.t).to(dev)
-    ant = torch.from_numpy(inst.antenna).to(dev)
-    x = torch.from_numpy(inst.fafb).to(dev)
-    T = inst.n_templates
-    out_map = torch.empty((T, g.n_t0, g.n_tau), dtype=torch.float32, device=dev)
-    out_sum = torch.empty((T, 32), dtype=torch.uint8, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    terms_per_tmpl, cells2 = plan.count_terms(inst.t)
-    terms = terms_per_tmpl * T
-
-    def step(p):
-        p.compute(t, ant, x, out_map=out_map, out_summary=out_sum, stream=stream)
-
-    def timed(p, steps, warmup, sampler=None):
-        for _ in range(warmup):
-            step(p)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        fm.fmap_plan_enable_timing(p.handle, True)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(steps)]
-        if sampler:
-            sampler.begin()
-        for k in range(steps):
-            flush.fill_(float(k))                     # untimed: evict the L2
-            evs[k][0].record(stream)
-            step(p)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        if sampler:
-            sampler.end()
-        if dist:
-            dist.barrier()
-        per = [a.elapsed_time(b) for a, b in evs]
-        ph, calls, launches = fm.fmap_plan_read_timing(p.handle)
-        fm.fmap_plan_enable_timing(p.handle, False)
-        return per, ph / max(calls, 1), launches
-
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -391,135 +539,235 @@ def main():
         pass
     clocks = ClockSampler(uuid)
     clocks.start()
-    per, phase_ms, launches = timed(plan, args.steps, args.warmup, clocks)
-    clocks.stop()
-    torch.cuda.synchronize()
-    st = plan.status()
-    if st != fm.FMAP_OK:
-        raise SystemExit(f"device status {fm.status_string(st)}")
+    try:
+        if args.workload is None:
+            result = run_default(args, fm, torch, dev, dist, rank, world, clocks)
+        elif args.workload == "uneven":
+            result = run_uneven(args, fm, torch, dev, dist, rank, world, clocks)
+        elif args.workload == "serving":
+            result = {"metric": "serving", **serving(fm, args.serving_requests,
+                                                     warmup_s=args.serving_warmup_s)}
+        else:
+            result = run_single(args, fm, torch, dev, dist, rank, world, clocks)
+    finally:
+        clocks.stop()
+    if result is not None and rank == 0:
+        if "clocks" in result:
+            result["clocks"] = clocks.summary()
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
+
+def headline_line(args, world, value, ms, per, inst, terms, cells2, prec, roof, launches,
+                  workload):
+    g = inst.grid
+    srt = sorted(per)
+    return {
+        "metric": "F-map (t0,tau)-SFT terms/s",
+        "value": value, "unit": "terms/s", "n_gpus": world, "steps": len(per),
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": workload, "description": WORKLOADS[workload], "precision": prec,
+                   "templates": inst.n_templates, "n_sft": inst.n_sft, "n_t0": g.n_t0,
+                   "n_tau": g.n_tau, "terms_per_step": terms, "cells_with_2plus_sft": cells2,
+                   "l2": "flushed between timed steps (256 MiB write, untimed); the map "
+                         "written each step is far larger than L2",
+                   "parallelism": f"replicas x{world} (an independent workload per rank)"},
+        "latency_ms": {"p50": srt[len(srt) // 2],
+                       "p99": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)],
+                       "max": srt[-1]},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": None,
+    }
+
+
+def run_default(args, fm, torch, dev, dist, rank, world, clocks):
+    """The headline (batched exp, recurrence) and every other workload."""
+    peaks, peak_src = load_peaks()
+    steps = args.steps or 20
+    t_start = time.perf_counter()
+    # ---- headline: batched exponential map, FP64-class recurrence ----
+    inst = make_workload("batch_exp", rank)
+    g = inst.grid
+    T = inst.n_templates
+    terms_t, cells2 = count_terms_np(g, inst.t)
+    terms = terms_t * T
+    run = Runner(fm, torch, dev, inst, dist, clocks)
+    p = run.plan("rec")
+    per, ph, launches = run.time(p, steps, args.warmup)
     total_ms = sum(per)
     if dist:
         tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = terms * world * args.steps / (total_ms / 1e3)
+    ms = total_ms / steps
+    value = terms * world / (ms / 1e3)
+    roof_of = lambda prec, dom: roofline_exp(peaks, peak_src, prec, terms, dom, g.n_tau,  # noqa: E731
+                                             inst.n_sft, T, g.n_t0 * g.n_tau)
+    res = headline_line(args, world, value, ms, per, inst, terms, cells2, "rec",
+                        roof_of("rec", float(ph[2])), launches, "batch_exp")
+    res["phases_ms"] = {"checks_index": float(ph[0]), "antenna": float(ph[1]),
+                        "recurrence": float(ph[2]), "fixup_reduce_refine": float(ph[3])}
+    log(f"headline: {ms:.2f} ms/step, {value:.3e} terms/s")
+    if rank != 0 or world > 1:
+        # several GPUs: the headline only (the other workloads are 1-GPU records)
+        p.close()
+        if rank == 0:
+            res["clocks"] = None
+            return res
+        return None
+    # accuracy of the headline on sampled templates (outside the timed region)
+    ref, valid = oracle_of(inst, SAMPLE_TEMPLATES)
+    m, s = run.sampled(SAMPLE_TEMPLATES)
+    import oracle
 
-    extra = {}
-    for alt in [a for a in args.also.split(",") if a and a != precision]:
-        try:
-            p2 = make_plan(alt)
-        except fm.FmapError:
-            continue
-        per2, ph2, _ = timed(p2, max(3, args.steps // 3), 3)
-        extra[alt] = {"value": terms * world / (statistics.mean(per2) / 1e3),
-                      "ms_per_step": statistics.mean(per2),
-                      "contraction_ms": float(ph2[2])}
-        p2.close()
+    res["accuracy"] = accuracy(fm, oracle, m, s, ref, valid, SAMPLE_TEMPLATES)
+    # end to end: host atoms in, summaries out, through fmap_compute_host
+    if not args.no_e2e:
+        res["e2e"] = end_to_end(fm, inst, "rec", terms, max(3, steps // 4))
+    p.close()
+    # ---- the tensor-core forms and the plain FP32 path, same workload ----
+    few = 2 if args.quick else 3
+    res["also"] = time_forms(run, ["bf16x3", "tf32", "fp32"], few, 1, terms, SAMPLE_TEMPLATES,
+                             ref, valid, roof_of)
+    for prec in ("bf16x3", "tf32"):
+        r = res["also"].get(prec, {})
+        if "ms_per_step" in r and "ms_per_step" in res["also"].get("fp32", {}):
+            r["speedup_vs_fp32_plain"] = res["also"]["fp32"]["ms_per_step"] / r["ms_per_step"]
+    del run
+    torch.cuda.empty_cache()
+    # ---- the CPU oracle on a sample of the headline workload ----
+    if world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"], _, _ = cpu_baseline(inst, target_s=6.0 if args.quick else 12.0)
+    del inst
+    configs = {}
+    # ---- small rect (1 template, 200 SFTs) ----
+    sr = make_workload("small_rect", rank)
+    run = Runner(fm, torch, dev, sr, dist, clocks)
+    ref, valid = oracle_of(sr, mode="direct")
+    tt_ = count_terms_np(sr.grid, sr.t)[0]
+    configs["small_rect"] = {"description": WORKLOADS["small_rect"],
+                             "forms": time_forms(run, ["fp64", "fp32"], 200, 5, tt_, None, ref,
+                                                 valid)}
+    del run
+    # ---- exp16: FP32 against FP64 (and the other forms) ----
+    e16 = make_workload("exp16", rank)
+    run = Runner(fm, torch, dev, e16, dist, clocks)
+    ref, valid = oracle_of(e16)
+    tt_ = count_terms_np(e16.grid, e16.t)[0] * e16.n_templates
+    roof16 = lambda prec, dom: roofline_exp(peaks, peak_src, prec, tt_, dom, e16.grid.n_tau,  # noqa: E731
+                                            e16.n_sft, e16.n_templates,
+                                            e16.grid.n_t0 * e16.grid.n_tau)
+    configs["exp16"] = {"description": WORKLOADS["exp16"],
+                        "forms": time_forms(run, ["fp64", "fp32", "rec", "bf16x3", "tf32"], 50, 5,
+                                            tt_, None, ref, valid, roof16)}
+    f = configs["exp16"]["forms"]
+    if "fp32" in f and "fp64" in f and "ms_per_step" in f["fp64"]:
+        configs["exp16"]["fp32_vs_fp64_speedup"] = f["fp64"]["ms_per_step"] / f["fp32"]["ms_per_step"]
+    del run
+    # ---- rect batch: 1024 templates ----
+    br = make_workload("batch_rect", rank)
+    run = Runner(fm, torch, dev, br, dist, clocks)
+    ref, valid = oracle_of(br, SAMPLE_TEMPLATES)
+    tt_ = count_terms_np(br.grid, br.t)[0] * br.n_templates
 
-    result = None
-    if rank == 0:
-        peaks, peak_src = load_peaks()
-        dom_ms = float(phase_ms[2])
-        flops = 2.0 * terms * 4            # multiply + add per (cell, SFT, data column) x 4 columns
-        wname = "table" if window == synth.TABLE else "exp"
-        if window != synth.RECT and precision in ("bf16x3", "tf32"):
-            if precision == "bf16x3":
-                peak, unit_peak = peaks["bf16_tflops"], "TFLOP/s (bf16, %s)" % peak_src
-            else:
-                peak = peaks["bf16_tflops"] * (1.1 / 2.25)
-                unit_peak = "TFLOP/s (tf32 = bf16 x 1.1/2.25 nominal, %s)" % peak_src
-            ach = flops / (dom_ms / 1e3) / 1e12
-            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "kernel": f"{wname} contraction (phase 2)",
-                    "peak_source": unit_peak}
-        elif window != synth.RECT:
-            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-            ach = flops / (dom_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "kernel": f"{wname} contraction (phase 2)",
-                    "peak_source": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock"}
-        else:
-            byts = T * g.n_t0 * g.n_tau * 4.0
-            ach = byts / (dom_ms / 1e3) / 1e9
-            peak = peaks["hbm_gbs"]
-            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "kernel": "rect cells (phase 2)",
-                    "peak_source": peak_src}
-        key = (args.workload, precision)
-        plain_workload = not (args.exp_cut8 or args.grid_axes or args.templates or args.window_table)
-        if plain_workload and key in NCU_TRAFFIC:
-            roof["traffic"] = NCU_TRAFFIC[key]
-            roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            cpu, _, _ = cpu_baseline(inst)
-        e2e = None
-        if not args.no_e2e:
-            e2e = end_to_end(fm, inst, precision, terms, args)
-        serve = None
-        if world == 1 and args.serving_requests > 0:
-            try:
-                serve = serving(fm, n_requests=args.serving_requests)
-            except Exception as e:  # reported, never fatal to the headline
-                serve = {"error": repr(e)}
-        srt = sorted(per)
-        result = {
-            "metric": "F-map (t0,tau)-SFT terms/s",
-            "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16x3": "bf16x3",
-                      "rec": "f32x2"}[precision],
-            "data": "synthetic",
-            "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                       "precision": precision, "templates": T, "n_sft": inst.n_sft,
-                       "n_t0": g.n_t0, "n_tau": g.n_tau, "terms_per_step": terms,
-                       "cells_with_2plus_sft": cells2,
-                       **({"exp_window_len": f"{g.exp_cut8}/8 tau" if g.exp_cut8 else "3 tau"}
-                          if g.window != synth.RECT else {}),
-                       **({"window": f"table ({args.window_table}, 1024 samples)"}
-                          if g.window == synth.TABLE else {}),
-                       **({"grid": "explicit axes (steps jittered by [0, step/2))"}
-                          if g.has_axes else {}),
-                       "l2": "flushed between timed steps (256 MiB write, untimed)",
-                       "parallelism": f"replicas x{world} (templates sharded by rank)"},
-            "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1,
-                                                                  int(math.ceil(0.99 * len(srt))) - 1)],
-                           "max": srt[-1]},
-            "phases_ms": {"index": float(phase_ms[0]), "antenna": float(phase_ms[1]),
-                          "contraction": float(phase_ms[2]), "reduce": float(phase_ms[3])},
-            "roofline": roof,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": int(launches),
-            "clocks": clocks.summary(),
-            "also": extra,
-            "serving": serve,
-        }
-    plan.close()
+    def roof_rect(prec, dom):
+        byts = br.n_templates * br.grid.n_t0 * br.grid.n_tau * 4.0
+        ach = byts / (dom / 1e3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "frac": ach / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC.get(("batch_rect", prec)),
+             "kernel": "rect cells (phase 2)", "peak_source": peak_src,
+             "work": "4 bytes of map written per (cell, template)"}
+        return r
+
+    configs["batch_rect"] = {"description": WORKLOADS["batch_rect"],
+                             "forms": time_forms(run, ["fp64"], 20 if args.quick else 60, 3, tt_,
+                                                 SAMPLE_TEMPLATES, ref, valid, roof_rect)}
+    del run
+    torch.cuda.empty_cache()
+    # ---- uneven batch ----
+    try:
+        configs["uneven"] = run_uneven(args, fm, torch, dev, None, 0, 1, clocks, sub=True)
+    except Exception as e:   # reported, never fatal to the headline
+        configs["uneven"] = {"error": repr(e)}
+    torch.cuda.empty_cache()
+    # ---- serving ----
+    try:
+        n_req = 2000 if args.quick else args.serving_requests
+        configs["serving"] = serving(fm, n_req, warmup_s=1.0 if args.quick else
+                                     args.serving_warmup_s)
+    except Exception as e:
+        configs["serving"] = {"error": repr(e)}
+    res["configs"] = configs
+    res["clocks"] = None
+    res["wall_s"] = time.perf_counter() - t_start
+    return res
+
+
+def run_single(args, fm, torch, dev, dist, rank, world, clocks):
+    """One workload, one precision (profiling and development runs)."""
+    name = args.workload
+    inst = make_workload(name, rank, args.templates, args.exp_cut8, args.grid_axes,
+                         args.window_table)
+    g = inst.grid
+    prec = args.precision or ("fp64" if g.window == synth.RECT else "rec")
+    run = Runner(fm, torch, dev, inst, dist, clocks)
+    if g.has_axes or g.window_table is not None:
+        p = run.plan(prec)
+        terms_t, cells2 = p.count_terms(inst.t)
+        p.close()
+    else:
+        terms_t, cells2 = count_terms_np(g, inst.t)
+    terms = terms_t * inst.n_templates
+    steps = args.steps or {"exp16": 500, "small_rect": 1000}.get(name, 20)
+    p = run.plan(prec)
+    per, ph, launches = run.time(p, steps, args.warmup)
+    p.close()
+    total_ms = sum(per)
     if dist:
-        dist.barrier()
-        dist.destroy_process_group()
-    if result is not None:
-        print(json.dumps(result), flush=True)
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms = total_ms / steps
+    if rank != 0:
+        return None
+    peaks, peak_src = load_peaks()
+    if g.window == synth.RECT:
+        byts = inst.n_templates * g.n_t0 * g.n_tau * 4.0
+        ach = byts / (float(ph[2]) / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "rect cells (phase 2)",
+                "peak_source": peak_src}
+    else:
+        roof = roofline_exp(peaks, peak_src, prec, terms, float(ph[2]), g.n_tau, inst.n_sft,
+                            inst.n_templates, g.n_t0 * g.n_tau)
+    res = headline_line(args, world, terms * world / (ms / 1e3), ms, per, inst, terms, cells2,
+                        prec, roof, launches, name)
+    res["phases_ms"] = [float(v) for v in ph]
+    return res
 
 
-def uneven_instances(n, rank):
-    specs = synth.config_uneven(n_instances=n, seed=synth.BASE_SEED + 3 + 1000 * rank)
+# ------------------------------------------------------------------ uneven --
+
+def uneven_instances(args, rank):
+    keep = {"rect": (synth.RECT,), "exp": (synth.EXP,), "both": (synth.RECT, synth.EXP)}
+    specs = synth.config_uneven(n_instances=args.instances, seed=synth.BASE_SEED + 3 + 1000 * rank)
+    lo, hi = args.uneven_nsft
+    specs = [s for s in specs if s["window"] in keep[args.uneven_window] and lo <= s["n_sft"] <= hi]
     return [synth.instance_from_spec(sp) for sp in specs]
 
 
-def run_uneven(args, fm, torch, dev, dist, rank, world):
+def run_uneven(args, fm, torch, dev, dist, rank, world, clocks, sub=False):
     """The uneven batch through fmap_batch_plan / fmap_batch_run: all
     instances' atoms resident, maps and summaries written, one graph launch
     per step."""
     from concurrent.futures import ThreadPoolExecutor
 
     t_build = time.perf_counter()
-    insts = uneven_instances(args.instances, rank)
+    insts = uneven_instances(args, rank)
     with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
         counts = list(ex.map(lambda i: fm.fmap_count_terms(i.grid, i.t), insts))
     terms = sum(c[0] * i.n_templates for c, i in zip(counts, insts))
@@ -528,13 +776,19 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
               torch.from_numpy(i.fafb).to(dev)) for i in insts]
     t_plan = time.perf_counter()
     batch = fm.Batch(items, want_map=True, workspace_budget=int(args.budget_gb * (1 << 30)),
-                     autotune=True)
+                     autotune=not args.profile_phases)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t_plan
     info = batch.info()
     log(f"uneven: {len(insts)} instances built in {t_plan - t_build:.1f} s, planned+tuned in "
         f"{plan_s:.1f} s; {info}")
     stream = torch.cuda.current_stream(dev)
+    if args.profile_phases:
+        phases = batch.profile(stream)
+        st = batch.status(stream)
+        batch.close()
+        return {"workload": "uneven", "instances": len(insts), "status": fm.status_string(st),
+                "info": info, "phases_ms": {k: round(v, 3) for k, v in phases.items()}}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         batch.run(stream)
@@ -542,24 +796,17 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
-    clocks = ClockSampler(uuid)
-    clocks.start()
+    steps = 5 if sub else (args.steps or 5)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     clocks.begin()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(float(k))
         evs[k][0].record(stream)
         batch.run(stream)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     clocks.end()
-    clocks.stop()
     if dist:
         dist.barrier()
     st = batch.status(stream)
@@ -572,8 +819,8 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
         tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = terms * world * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / steps
+    value = terms * world * steps / (total_ms / 1e3)
     result = None
     if rank == 0:
         peaks, peak_src = load_peaks()
@@ -583,14 +830,11 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
                 "frac": ach / peaks["hbm_gbs"], "traffic": None,
                 "kernel": "whole batch step (all phases; map bytes / step time)",
                 "peak_source": peak_src}
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            cpu = uneven_cpu_baseline(fm, insts, counts)
-        srt = sorted(per)
+        acc = uneven_accuracy(fm, batch, insts, counts)
         n_rect = sum(1 for i in insts if i.grid.window == synth.RECT)
         result = {
             "metric": "F-map (t0,tau)-SFT terms/s",
-            "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+            "value": value, "unit": "terms/s", "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32x2",
             "data": "synthetic",
@@ -605,19 +849,52 @@ def run_uneven(args, fm, torch, dev, dist, rank, world):
                        "plan_and_tune_s": plan_s,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
-            "latency_ms": {"p50": srt[len(srt) // 2], "max": srt[-1]},
+            "latency_ms": {"p50": sorted(per)[len(per) // 2], "max": max(per)},
             "phases_ms": {k: v for k, v in phases.items() if v > 0},
             "roofline": roof,
-            "cpu_baseline": cpu,
-            "e2e": None,
-            "gpu_launches": int(info["launches_per_run"]) * args.steps,
-            "clocks": clocks.summary(),
+            "accuracy": acc,
+            "gpu_launches": int(info["launches_per_run"]) * steps,
         }
+        if not sub:
+            result["clocks"] = None
+            if world == 1 and not args.no_cpu_baseline:
+                result["cpu_baseline"] = uneven_cpu_baseline(insts, counts)
     batch.close()
     return result
 
 
-def uneven_cpu_baseline(fm, insts, counts, target_s=12.0):
+def uneven_accuracy(fm, batch, insts, counts, per_class=2, max_terms=3e8):
+    """Oracle parity of sampled instances of every (window, N_SFT decade)
+    class: maps and (unrefined batch) summaries."""
+    import oracle
+
+    oracle.build()
+    picked, seen = [], {}
+    for k, (inst, c) in enumerate(zip(insts, counts)):
+        key = (inst.grid.window, int(math.log10(max(inst.n_sft, 1))))
+        if c[0] * inst.n_templates > max_terms or seen.get(key, 0) >= per_class:
+            continue
+        seen[key] = seen.get(key, 0) + 1
+        picked.append(k)
+    worst, dlogb, match = 0.0, 0.0, 0
+    for k in picked:
+        inst = insts[k]
+        ref, valid, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, inst.grid.as_tuple(),
+                                    mode="fast")
+        got = batch.maps[k].cpu().numpy().astype(np.float64)
+        gs = fm.summary_to_numpy(batch.sums[k][: inst.n_templates])
+        a = accuracy(fm, oracle, got, gs, ref, valid)
+        worst = max(worst, a["max_rel_2F_err"])
+        dlogb = max(dlogb, a["max_abs_dlogB"])
+        match += int(a["argmax_match"].split("/")[0] == a["argmax_match"].split("/")[1])
+    return {"instances_checked": len(picked), "classes": sorted(f"{'rect' if w == 0 else 'exp'}"
+                                                                f" 1e{d}" for w, d in seen),
+            "max_rel_2F_err": worst, "max_abs_dlogB": dlogb,
+            "argmax_match": f"{match}/{len(picked)}",
+            "note": "batch summaries are not refined"}
+
+
+def uneven_cpu_baseline(insts, counts, target_s=12.0):
     """The oracle (fast mode, all host cores) over the first instances of the
     uneven batch until about target_s of CPU work."""
     import oracle
@@ -637,60 +914,73 @@ def uneven_cpu_baseline(fm, insts, counts, target_s=12.0):
             "sample": f"first {done} of {len(insts)} instances, {terms:.3e} terms in {t_all:.2f} s"}
 
 
-def end_to_end(fm, inst, precision, terms, args):
-    """Same metric through fmap_compute_host: pinned host atoms in, map and
-    summaries out, copies inside the timed region (host wall clock)."""
+# ----------------------------------------------------------------- end to end
+
+def end_to_end(fm, inst, precision, terms, steps):
+    """Same metric through fmap_compute_host: pinned host atoms in, the
+    per-template summaries out (the search result), copies inside the timed
+    region (host wall clock).  The plan keeps its own map (refinement)."""
     import torch
 
     g = inst.grid
     T = inst.n_templates
+    flags = fm.FMAP_PLAN_MAP_BUFFER
     if precision == "rec":
-        plan = fm.Plan(g, inst.n_sft, T, "fp64", fm.FMAP_PLAN_EXP_RECURRENCE)
+        plan = fm.Plan(g, inst.n_sft, T, "fp64", flags | fm.FMAP_PLAN_EXP_RECURRENCE)
     else:
-        plan = fm.Plan(g, inst.n_sft, T, precision)
+        plan = fm.Plan(g, inst.n_sft, T, precision, flags)
     h_t = torch.from_numpy(inst.t).pin_memory()
     h_a = torch.from_numpy(inst.antenna).pin_memory()
     h_x = torch.from_numpy(inst.fafb).pin_memory()
-    h_m = torch.empty((T, g.n_t0, g.n_tau), dtype=torch.float32).pin_memory()
     h_s = torch.empty((T, 32), dtype=torch.uint8).pin_memory()
     stream = torch.cuda.current_stream()
-    atoms = fm.make_atoms(inst.n_sft, T, True, h_t, h_a, h_x)
-    for _ in range(3):
-        fm.fmap_compute_host(plan.handle, atoms, h_m, h_s, stream)
-    n = max(3, args.steps // 2)
+    atoms = fm.make_atoms(inst.n_sft, T, inst.shared_antenna, h_t, h_a, h_x)
+    for _ in range(2):
+        fm.fmap_compute_host(plan.handle, atoms, None, h_s, stream)
     t0 = time.perf_counter()
-    for _ in range(n):
-        fm.fmap_compute_host(plan.handle, atoms, h_m, h_s, stream)
-    dt = (time.perf_counter() - t0) / n
+    for _ in range(steps):
+        fm.fmap_compute_host(plan.handle, atoms, None, h_s, stream)
+    dt = (time.perf_counter() - t0) / steps
     plan.close()
     h2d = h_t.numel() * 8 + h_a.numel() * 4 + h_x.numel() * 4
-    d2h = h_m.numel() * 4 + h_s.numel()
+    d2h = h_s.numel()
     return {"value": terms / dt, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
-            "api": "fmap_compute_host (pinned host buffers)"}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "steps": steps,
+            "api": "fmap_compute_host (pinned host buffers; summaries returned, map kept on "
+                   "the device)"}
 
 
-def serving(fm, n_requests=1000, rate_hz=200.0, max_inflight=8, pool_size=64, seed=None,
-            saturated_hz=2000.0):
+# ----------------------------------------------------------------- serving --
+
+def serving(fm, n_requests=10_000, rate_hz=200.0, max_inflight=8, pool_size=64, seed=None,
+            saturated_hz=2000.0, warmup_s=5.0):
     """Serving workload: Poisson arrivals of F-map requests with the uneven
-    batch's size mix and 1-64 templates each, through fmap_submit/fmap_poll.
-    Latency = scheduled arrival -> the poller sees the request finished."""
+    batch's size mix and 1-64 templates each, through fmap_submit/fmap_poll,
+    after warmup_s seconds of the same stream (untimed).  Latency = scheduled
+    arrival -> the poller sees the request finished.  Continuous batching (up
+    to 8 requests in flight) against one-at-a-time launches; accuracy of the
+    summaries of sampled requests against the oracle."""
     import threading as th
 
+    import oracle
+
     kw = {} if seed is None else {"seed": seed}
-    arrivals, specs = synth.config_serving_stream(n_requests=n_requests, rate_hz=rate_hz, **kw)
+    n_warm = int(warmup_s * rate_hz)
+    arrivals, specs = synth.config_serving_stream(n_requests=n_requests + n_warm,
+                                                  rate_hz=rate_hz, **kw)
     pool = [synth.instance_from_spec(sp) for sp in specs[:pool_size]]
     terms = [fm.fmap_count_terms(inst.grid, inst.t)[0] * inst.n_templates for inst in pool]
 
-    def run(inflight, arrivals=arrivals, n_requests=n_requests):
+    def run(inflight, arrivals, n_total, n_skip):
         srv = fm.Server(device_mem_budget=24 << 30, pinned_bytes=2 << 30, max_inflight=inflight)
-        tickets = [None] * n_requests
-        done = [0.0] * n_requests
+        tickets = [None] * n_total
+        done = [0.0] * n_total
+        sums = {}
         lock = th.Lock()
         t0 = time.perf_counter() + 0.05
 
         def submitter():
-            for i in range(n_requests):
+            for i in range(n_total):
                 dt = t0 + arrivals[i] - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
@@ -708,7 +998,7 @@ def serving(fm, n_requests=1000, rate_hz=200.0, max_inflight=8, pool_size=64, se
 
         sub = th.Thread(target=submitter)
         sub.start()
-        pending = set(range(n_requests))
+        pending = set(range(n_total))
         while pending:
             progressed = False
             for i in list(pending):
@@ -716,42 +1006,72 @@ def serving(fm, n_requests=1000, rate_hz=200.0, max_inflight=8, pool_size=64, se
                     tk = tickets[i]
                 if tk is None:
                     continue
-                st, _, _ = srv.poll(tk, wait_us=0)
+                st, s, _ = srv.poll(tk, wait_us=0)
                 if st == fm.FMAP_OK:
                     done[i] = time.perf_counter()
+                    if i % pool_size == i:
+                        sums[i] = s
                     pending.discard(i)
                     progressed = True
             if not progressed:
                 time.sleep(5e-5)
         sub.join()
+        peak = srv.peak()
         srv.close()
-        lat = np.array([done[i] - (t0 + arrivals[i]) for i in range(n_requests)]) * 1e3
-        span = max(done) - t0
-        tot = sum(terms[i % pool_size] for i in range(n_requests))
+        idx = range(n_skip, n_total)
+        lat = np.array([done[i] - (t0 + arrivals[i]) for i in idx]) * 1e3
+        span = max(done[i] for i in idx) - (t0 + arrivals[n_skip])
+        tot = sum(terms[i % pool_size] for i in idx)
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "throughput_terms_per_s": tot / span,
-                "requests_per_s": n_requests / span, "max_inflight": inflight}
+                "requests_per_s": len(lat) / span, "max_inflight": inflight,
+                "peak_running": peak}, sums
 
-    cont = run(max_inflight)
-    serial = run(1)
+    n_total = n_requests + n_warm
+    cont, sums = run(max_inflight, arrivals, n_total, n_warm)
+    serial, _ = run(1, arrivals, n_total, n_warm)
     # The same request sequence arriving 10x faster than the one-at-a-time
     # server can drain it: continuous batching's overlap shows in throughput
     # and tail latency.
-    n_sat = max(1, n_requests // 2)
+    n_sat = min(500, n_requests)
     sat_arr = arrivals[:n_sat] * (rate_hz / saturated_hz)
     sat = {"rate_hz": saturated_hz, "requests": n_sat,
-           "continuous_batching": run(max_inflight, sat_arr, n_sat),
-           "one_at_a_time": run(1, sat_arr, n_sat)}
-    return {"requests": n_requests, "rate_hz": rate_hz, "distinct_request_shapes": pool_size,
-            "continuous_batching": cont, "one_at_a_time": serial, "saturated": sat,
-            "precision": {"exp": "bf16x3", "rect": "fp64"}}
+           "continuous_batching": run(max_inflight, sat_arr, n_sat, 0)[0],
+           "one_at_a_time": run(1, sat_arr, n_sat, 0)[0]}
+    # accuracy of the summaries of the pool's smaller requests
+    oracle.build()
+    worst, match, checked, ntmpl = 0.0, 0, 0, 0
+    for i, inst in enumerate(pool):
+        if i not in sums or terms[i] > 2e8 or checked >= 12:
+            continue
+        ref, valid, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, inst.grid.as_tuple(),
+                                    mode="fast")
+        rs = oracle.summary(ref, valid)
+        s = sums[i]
+        for j in range(inst.n_templates):
+            if rs["n_valid"][j]:
+                ntmpl += 1
+                worst = max(worst, abs(float(s["logB"][j]) - float(rs["logB"][j])))
+                match += int((int(s["m"][j]), int(s["n"][j])) == (int(rs["m"][j]), int(rs["n"][j])))
+        checked += 1
+    return {"description": WORKLOADS["serving"], "requests": n_requests,
+            "warmup_requests": n_warm, "warmup_s": warmup_s, "rate_hz": rate_hz,
+            "distinct_request_shapes": pool_size, "continuous_batching": cont,
+            "one_at_a_time": serial, "saturated": sat,
+            "precision": {"exp": "bf16x3", "rect": "fp64"},
+            "accuracy": {"requests_checked": checked, "max_abs_dlogB": worst,
+                         "argmax_match": f"{match}/{ntmpl}"}}
 
+
+# --------------------------------------------------------------- reference --
 
 def reference_arm(args, rank, world):
-    """The CPU oracle as the reference implementation, on the host cores."""
+    """The CPU oracle as the reference implementation, on the host cores, on
+    a bounded sample of the headline workload (no library code runs here)."""
     if rank != 0:
         return
-    inst = make_workload(args.workload, 0, None, args.exp_cut8, args.grid_axes, args.window_table)
+    name = args.workload or "batch_exp"
+    inst = make_workload(name, 0, None, args.exp_cut8, args.grid_axes, args.window_table)
     info, sg, terms = cpu_baseline(inst, target_s=min(4.0, 150.0 / (args.steps + args.warmup)))
     import oracle
 
@@ -768,8 +1088,7 @@ def reference_arm(args, rank, world):
            "unit": "terms/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                      "exp_window_len": (f"{args.exp_cut8}/8 tau" if args.exp_cut8 else "3 tau"),
+           "config": {"workload": name, "description": WORKLOADS[name],
                       "sample": info["sample"]},
            "cpu_baseline": info,
            "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0,

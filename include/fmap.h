@@ -202,10 +202,11 @@ fmap_status fmap_plan_set_log_prior(fmap_plan_t* plan, double log_prior_const);
  * After a compute call's fast map and reductions, per template the cells
  * whose fast 2F lies within 16 of the fast maximum (at most max_cells of
  * them, the highest; a histogram of 256 bins picks the cut) are recomputed
- * from their atoms by the plain FP64 definition (windowed sums, D, Eq.
- * F_FaFb); their FP64 values replace the fast ones in the map, in max2F, in
- * the argmax (lowest index on FP64 ties) and in logB (the fast exp-sum has
- * their fast terms replaced by the FP64 ones).  Summary flags:
+ * from their atoms by the plain definition (windowed sums in float-float,
+ * ~2^-44 relative; D and Eq. F_FaFb in FP64); these values replace the fast
+ * ones in the map, in max2F, in the argmax (lowest index on ties) and in
+ * logB (the fast exp-sum has their fast terms replaced by the refined
+ * ones).  Summary flags:
  * FMAP_SUMMARY_REFINED once this ran, FMAP_SUMMARY_ARGMAX_EXACT when the cut
  * lies below the maximum by more than twice the precision's error bound
  * (1e-5 relative for FMAP_FP64, 1e-3 otherwise, floor 1), so that no other
@@ -285,7 +286,10 @@ fmap_status fmap_marginalise(fmap_plan_t* plan, const float* d_2F, const uint8_t
  * small second-level area within 8 MiB, ~500k template-tiles), else
  * FMAP_ERR_ARG with a message.
  * The first call on each device (with that device current) looks up the
- * array's device address; make it before any stream capture.  All calls
+ * array's device address; make it before any stream capture.  After
+ * cudaDeviceReset (which unloads the library's device code) the next call
+ * looks the address up again: make that call outside stream capture too.
+ * All calls
  * share the array, so calls whose work overlaps on the GPU race: serialise
  * them.  Nothing in the array needs clearing between calls.
  *   grid      the map's grid (window field unused); d_2F [T][n_t0][n_tau];
@@ -303,6 +307,9 @@ size_t fmap_noalloc_scratch_bytes(void);
  * copies the atoms to plan-owned device staging (pinned host memory makes
  * the copies asynchronous), runs the window's compute, copies the map
  * (nullable h_2F) and the summaries (nullable h_summary) back, and waits.
+ * The staging is allocated on the first call (the map's on the first call
+ * that asks for the map); a summary-only call refines its summaries when the
+ * plan has FMAP_PLAN_MAP_BUFFER.
  */
 fmap_status fmap_compute_host(fmap_plan_t* plan, const fmap_atoms* host_atoms, float* h_2F,
                               fmap_summary* h_summary, fmap_stream stream);

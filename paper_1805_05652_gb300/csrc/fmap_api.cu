@@ -661,11 +661,19 @@ fmap_status fmap_compute_host(fmap_plan_t* p, const fmap_atoms* h, float* h_2F,
     if (e == cudaSuccess) e = cudaMalloc(&w.st_ant, sizeof(float) * 3 * std::max<size_t>(n, 1) *
                                                         (p->flags & FMAP_PLAN_PER_TEMPLATE_ANTENNA ? std::max<size_t>(T, 1) : 1));
     if (e == cudaSuccess) e = cudaMalloc(&w.st_x, sizeof(float) * 4 * std::max<size_t>(n * T, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&w.st_map, sizeof(float) * std::max<size_t>(cells * T, 1));
     if (e == cudaSuccess) e = cudaMalloc(&w.st_sum, sizeof(fmap_summary) * std::max<size_t>(T, 1));
     if (e != cudaSuccess) {
       cudaGetLastError();
       free_staging(p);
+      set_error("staging allocation failed");
+      return FMAP_ERR_NOMEM;
+    }
+  }
+  // the map staging only when a map is asked for
+  if (h_2F && !w.st_map) {
+    if (cudaMalloc(&w.st_map, sizeof(float) * std::max<size_t>(cells * T, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      w.st_map = nullptr;
       set_error("staging allocation failed");
       return FMAP_ERR_NOMEM;
     }

@@ -266,10 +266,16 @@ k_reduce_groups(const Partial* __restrict__ parts, int64_t n_tiles, int64_t fix0
 }
 
 // Level 2: one block per template over its groups; writes the summary and,
-// when tstat is given, the statistics the refinement starts from.
+// when tstat is given, the statistics the refinement starts from (and clears
+// that template's refinement histogram and candidate count).
 __device__ __forceinline__ void reduce_final_body(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n_tau,
                double log_prior, fmap_summary* __restrict__ out, TStat* __restrict__ tstat,
-    const uint3 bid, const dim3 gdim) {
+    const uint3 bid, const dim3 gdim, int32_t* __restrict__ ref_hist = nullptr,
+    int32_t* __restrict__ ref_n = nullptr) {
+  if (ref_hist) {
+    for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) ref_hist[(int64_t)bid.x * kRefBins + b] = 0;
+    if (threadIdx.x == 0) ref_n[bid.x] = 0;
+  }
   const Partial64* gp = groups + (int64_t)bid.x * n_groups;
   const Partial64 r = block_merge(n_groups, [&](int64_t b) { return gp[b]; });
   if (threadIdx.x == 0) {
@@ -302,8 +308,10 @@ __device__ __forceinline__ void reduce_final_body(const Partial64* __restrict__ 
 
 __global__ void __launch_bounds__(kRedThreads)
 k_reduce_final(const Partial64* __restrict__ groups, int64_t n_groups, int32_t n_tau,
-               double log_prior, fmap_summary* __restrict__ out, TStat* __restrict__ tstat) {
-  reduce_final_body(groups, n_groups, n_tau, log_prior, out, tstat, blockIdx, gridDim);
+               double log_prior, fmap_summary* __restrict__ out, TStat* __restrict__ tstat,
+               int32_t* __restrict__ ref_hist, int32_t* __restrict__ ref_n) {
+  reduce_final_body(groups, n_groups, n_tau, log_prior, out, tstat, blockIdx, gridDim, ref_hist,
+                    ref_n);
 }
 
 int64_t reduce_groups_of(int64_t slots) { return std::max<int64_t>(1, (slots + kRedGroup - 1) / kRedGroup); }
@@ -311,12 +319,13 @@ int64_t reduce_groups_of(int64_t slots) { return std::max<int64_t>(1, (slots + k
 static cudaError_t reduce_into(const Partial* parts, int64_t n_tiles, int64_t fix0, int64_t n_fix,
                                int64_t stride, int32_t T, int32_t n_tau, double log_prior,
                                Partial64* groups, fmap_summary* d_summary, cudaStream_t s,
-                               TStat* tstat = nullptr) {
+                               TStat* tstat = nullptr, int32_t* ref_hist = nullptr,
+                               int32_t* ref_n = nullptr) {
   const int64_t n_groups = reduce_groups_of(n_tiles + n_fix);
   k_reduce_groups<<<dim3((unsigned)n_groups, (unsigned)T), kRedThreads, 0, s>>>(
       parts, n_tiles, fix0, n_fix, stride, n_groups, groups);
   k_reduce_final<<<T, kRedThreads, 0, s>>>(groups, n_groups, n_tau > 0 ? n_tau : 1, log_prior,
-                                           d_summary, tstat);
+                                           d_summary, tstat, ref_hist, ref_n);
   return cudaGetLastError();
 }
 
@@ -327,7 +336,7 @@ cudaError_t launch_final_reduce(fmap_plan_s* p, int64_t n_tiles, bool with_fix,
   p->launches += 2;
   return reduce_into(p->ws.partials, n_tiles, p->n_tiles, fix ? kFixSlots : 0, p->part_stride,
                      p->n_templates, p->grid.n_tau, p->log_prior, (Partial64*)p->ws.groups,
-                     d_summary, s, p->ws.tstat);
+                     d_summary, s, p->ws.tstat, p->ws.ref_hist, p->ws.ref_n);
 }
 
 // ---------------------------------------------------------------------------

@@ -86,6 +86,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
       "r"(v[15])
       : "memory");
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -105,6 +111,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 // The three products of one MMA K step, hi*hi (accumulating if acc != 0),
 // hi*lo and lo*hi, into the accumulator at d; the B descriptors are given as
@@ -201,7 +220,7 @@ struct Params {
   int32_t shared_antenna;
   int32_t n_templates;
   int32_t n_cols;      // N of this launch (multiple of 64, <= 256)
-  int32_t tmem_cols;   // power of two >= n_cols + NS * kAColsPerStage
+  int32_t tmem_cols;   // power of two >= 2 n_cols + NS * kAColsPerStage
   int32_t nblk;        // 128-cell blocks per t0 row
   float* map;
   Partial* parts;
@@ -210,22 +229,41 @@ struct Params {
   uint64_t wait_ns;    // limit of the pipeline's waits (the drains take kWaitNs)
 };
 
+// Accumulation in chunks.  A tensor-core MMA adds its products to the FP32
+// accumulator with truncation (no round to nearest), which biases a long sum
+// towards zero by a few ulp per MMA: over the ~10^2-10^3 MMAs of a long window
+// the sums shrink by ~1e-5 relative, and so does every 2F (measured: the log
+// Bayes factor of pure-noise maps of 5000 SFTs off by 1-3e-4 with 256-atom
+// chunks).  So every K-tile (32 or 64 atoms, 12 MMAs) is a chunk of its own,
+// alternately in two TMEM accumulators; the generator warps add a finished
+// chunk's accumulator, with round-to-nearest FP32 additions, to running sums
+// in shared memory just before they fill the first stage of the chunk two
+// later, which is when the MMA thread needs that accumulator again.
+constexpr int kChunkTiles = 1;
+
 // TAB: weights from the window table (FMAP_TABLE grids) instead of exp2; the
 // table sits in shared memory after the staged relative times.
-template <bool BF16, bool TAB, int NS>
-__global__ void __launch_bounds__(kThreads, 1)
+// (at most 102 registers a thread, so that two CTAs fit an SM's register
+// file where their TMEM and shared memory let them.)  RS: the running sums in
+// registers (N = 64: 32 a thread), else in shared memory.
+template <bool BF16, bool TAB, int NS, bool RS>
+__global__ void __launch_bounds__(kThreads, 2)
 k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
          const Params p) {
   constexpr int KT = BF16 ? 64 : 32;          // atoms per K-tile (128-byte operand rows)
   constexpr int HALF = KT / 2;                // atoms per generator warp and K-tile
   constexpr int KSTEP = BF16 ? 16 : 8;        // atoms per MMA
   constexpr int NKS = KT / KSTEP;             // MMAs per product and K-tile
+  constexpr int P = kChunkTiles;              // K-tiles per accumulation chunk
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int kStages = NS;                 // A/B pipeline stages
   float* s_dt = (float*)(smem + (size_t)kStages * 2 * p.n_cols * 128);
   float2* s_tab = (float2*)(s_dt + kDtCap);   // TAB only
-  __shared__ uint64_t bar_full_b[kStages], bar_full_a[kStages], bar_empty[kStages], bar_acc;
+  // running sums [N / 4][128 rows] float4 (column quads of each row)
+  float4* s_sum = (float4*)(((uintptr_t)(s_tab + (TAB ? kTabMax + 1 : 0)) + 15) & ~(uintptr_t)15);
+  __shared__ uint64_t bar_full_b[kStages], bar_full_a[kStages], bar_empty[kStages];
+  __shared__ uint64_t bar_accf[2], bar_drain[2], bar_final;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   __shared__ int32_t s_jmax;
@@ -248,7 +286,11 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
       mbar_init(&bar_full_a[s], kGenWarps);
       mbar_init(&bar_empty[s], 1);
     }
-    mbar_init(&bar_acc, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_accf[b], 1);
+      mbar_init(&bar_drain[b], kGenWarps);
+    }
+    mbar_init(&bar_final, 1);
     s_abort = 0;
     s_jmax = i0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -268,7 +310,8 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
   const int32_t jmax = s_jmax;
   const int32_t k_begin = (i0 / KT) * KT;
   const int n_kt = jmax > i0 ? (jmax - k_begin + KT - 1) / KT : 0;
-  const uint32_t a_col0 = (uint32_t)N;   // A stages follow the accumulator columns
+  const int n_chunks = (n_kt + P - 1) / P;
+  const uint32_t a_col0 = 2u * (uint32_t)N;   // A stages follow the two accumulators
 
   if (warp == kTmaWarp) {
     // ---------------- TMA producer of the X tiles ----------------
@@ -299,18 +342,26 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer ----------------
     // One thread issues every MMA of the CTA, so work added to its loop delays
-    // them all: stage, phase, TMEM column and descriptor address advance by
-    // additions, and no descriptor is rebuilt per K-tile.  (The descriptor's
-    // start-address field, bits 0-13 = address / 16, cannot carry into the
-    // next field: shared memory ends below 2^18 bytes.)
+    // them all: stage, phase, chunk, TMEM column and descriptor address
+    // advance by additions, and no descriptor is rebuilt per K-tile.  (The
+    // descriptor's start-address field, bits 0-13 = address / 16, cannot
+    // carry into the next field: shared memory ends below 2^18 bytes.)
     if (lane == 0) {
       const uint32_t idesc = idesc_of(BF16, N);
       const uint64_t d0 = sdesc_sw128(smem_u32(smem));
       const uint32_t d_lo0 = (uint32_t)d0, d_hi = (uint32_t)(d0 >> 32);
       const uint32_t op16 = op_bytes >> 4, stage16 = (2 * op_bytes) >> 4;
       uint32_t d_lo = d_lo0, a_st = tmem + a_col0, par = 0;
-      int s = 0;
+      int s = 0, kc = 0, c = 0;                 // stage, K-tile within the chunk, chunk
+      uint32_t acc = tmem;                      // accumulator of chunk c (column (c & 1) N)
+      bool issued = false;
       for (int it = 0; it < n_kt; ++it) {
+        // a chunk reuses the accumulator of chunk c - 2 once it is drained
+        if (kc == 0 && c >= 2 &&
+            !mbar_wait(&bar_drain[c & 1], ((c - 2) >> 1) & 1, &s_abort, p.wait_ns)) {
+          atomicExch(&s_abort, 1);
+          break;
+        }
         if (!mbar_wait(&bar_full_b[s], par, &s_abort, p.wait_ns) ||
             !mbar_wait(&bar_full_a[s], par, &s_abort, p.wait_ns)) {
           atomicExch(&s_abort, 1);
@@ -321,10 +372,17 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
         for (int ks = 0; ks < NKS; ++ks) {
           // 8 TMEM columns and 32 bytes of the B rows per MMA K step
           const uint32_t ac = (uint32_t)(ks * 8), bk = (uint32_t)((ks * 32) >> 4);
-          mma_kstep<BF16>(tmem, a_st + ac, a_st + 32u + ac, d_lo + bk, d_lo + op16 + bk, d_hi,
-                          idesc, (it > 0 || ks > 0) ? 1u : 0u);
+          mma_kstep<BF16>(acc, a_st + ac, a_st + 32u + ac, d_lo + bk, d_lo + op16 + bk, d_hi,
+                          idesc, (kc > 0 || ks > 0) ? 1u : 0u);
         }
+        issued = true;
         mma_commit(&bar_empty[s]);
+        if (++kc == P || it + 1 == n_kt) {
+          mma_commit(&bar_accf[c & 1]);
+          kc = 0;
+          ++c;
+          acc = tmem + (uint32_t)((c & 1) * N);
+        }
         if (++s == kStages) {
           s = 0;
           par ^= 1u;
@@ -335,12 +393,12 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
           a_st += (uint32_t)kAColsPerStage;
         }
       }
-      if (n_kt > 0) {
-        mma_commit(&bar_acc);
+      if (issued) {
         // every MMA this thread issued completes before the block releases its
         // tensor memory, also after a wait gave up
+        mma_commit(&bar_final);
         volatile int never = 0;
-        mbar_wait(&bar_acc, 0, &never, kWaitNs);
+        mbar_wait(&bar_final, 0, &never, kWaitNs);
       }
     }
   } else {
@@ -358,6 +416,8 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
     if (jmax > i0) t0rel = (int32_t)(grid_t0(g, p.ax, m) - *p.t_base);
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int gtid = threadIdx.x;          // 0 .. 255 over the generator warps
+    const int ncol = N / 2;                // this warp's accumulator columns
+    const uint32_t col_h = (uint32_t)(h * ncol);
     float su = 0.0f;                       // TAB: table samples per second of t - t0
     if constexpr (TAB) {
       su = (float)tab_scale(p.n_tab, exp_cut8_of(g), grid_tau(g, p.ax, (in_grid ? n : 0)));
@@ -365,6 +425,53 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
       asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory");
     }
     bool ok_run = true;
+    int drained = 0;                       // chunks added to the running sums
+    float rs[RS ? 32 : 1];                 // RS: this thread's 32 running sums
+#pragma unroll
+    for (int i = 0; i < (RS ? 32 : 1); ++i) rs[i] = 0.0f;
+    // Adds chunk c's accumulator (this thread's row, this warp's columns) to
+    // the running sums (the first chunk initialises them), then releases the
+    // accumulator to the MMA thread.
+    auto drain = [&](int c) -> bool {
+      if (!mbar_wait(&bar_accf[c & 1], (c >> 1) & 1, &s_abort, p.wait_ns)) return false;
+      tc_fence_after();
+      const uint32_t base = tmem + lane_off + (uint32_t)((c & 1) * N) + col_h;
+      if constexpr (RS) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          float v[16];
+          tmem_ld16(base + (uint32_t)(16 * q), v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) rs[16 * q + i] += v[i];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_drain[c & 1]);
+        return true;
+      }
+#pragma unroll 1
+      for (int g8 = 0; g8 < ncol; g8 += 16) {
+        float v[16];
+        tmem_ld16(base + (uint32_t)g8, v);
+        float4* sp = s_sum + (size_t)((col_h + g8) >> 2) * kRows + row;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float4 o = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          if (c > 0) {
+            const float4 r = sp[(size_t)i * kRows];
+            o.x += r.x;
+            o.y += r.y;
+            o.z += r.z;
+            o.w += r.w;
+          }
+          sp[(size_t)i * kRows] = o;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_drain[c & 1]);
+      return true;
+    };
     for (int it = 0; it < n_kt; ++it) {
       const int s = it % kStages;
       const int pos = (it * KT) % kDtCap;
@@ -390,83 +497,129 @@ k_exp_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUte
         ok_run = false;
         continue;
       }
+      // before the first stage of chunk c, add chunk c - 2 to the running
+      // sums: the MMA thread reuses its accumulator for chunk c (its MMAs
+      // only needed stages already filled, so the wait for them ends)
+      if (it % P == 0 && it / P >= 2) {
+        if (!drain(drained)) {
+          atomicExch(&s_abort, 1);
+          ok_run = false;
+          continue;
+        }
+        ++drained;
+      }
       const int32_t a0 = k_begin + it * KT + h * HALF;
       const int32_t cnt = jc - a0;                     // leading atoms inside this row's window
-      uint32_t vhi[16], vlo[16];
-      if (__all_sync(0xffffffffu, cnt <= 0)) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) vhi[j] = vlo[j] = 0u;
-      } else {
-        float w[HALF];
-        const float4* dp = reinterpret_cast<const float4*>(s_dt + pos + h * HALF);
-#pragma unroll
-        for (int v = 0; v < HALF / 4; ++v) {
-          const float4 d4 = dp[v];
-          if constexpr (TAB) {
-            w[4 * v] = tab_weight(su * d4.x, s_tab, p.n_tab);
-            w[4 * v + 1] = tab_weight(su * d4.y, s_tab, p.n_tab);
-            w[4 * v + 2] = tab_weight(su * d4.z, s_tab, p.n_tab);
-            w[4 * v + 3] = tab_weight(su * d4.w, s_tab, p.n_tab);
-          } else {
-            float e0, e1, e2, e3;
-            mul_x2(e0, e1, d4.x, d4.y, c2);
-            mul_x2(e2, e3, d4.z, d4.w, c2);
-            w[4 * v] = ex2(e0);
-            w[4 * v + 1] = ex2(e1);
-            w[4 * v + 2] = ex2(e2);
-            w[4 * v + 3] = ex2(e3);
-          }
-        }
-        if (!__all_sync(0xffffffffu, cnt >= HALF)) {
-#pragma unroll
-          for (int j = 0; j < HALF; ++j) w[j] = j < cnt ? w[j] : 0.0f;
-        }
-        if constexpr (BF16) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const uint32_t hp = pack_bf16(w[2 * j], w[2 * j + 1]);
-            const float he = __uint_as_float(hp << 16), ho = __uint_as_float(hp & 0xffff0000u);
-            float le, lo;
-            sub_x2(le, lo, w[2 * j], w[2 * j + 1], he, ho);
-            vhi[j] = hp;
-            vlo[j] = pack_bf16(le, lo);
-          }
-        } else {
-          // the MMA reads TF32 operands as FP32 bit patterns and ignores the
-          // low 13 bits, so the remainder needs no conversion of its own
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const uint32_t hb = to_tf32(w[j]);
-            vhi[j] = hb;
-            vlo[j] = __float_as_uint(w[j] - __uint_as_float(hb));
-          }
-        }
-      }
       const uint32_t col = a_col0 + (uint32_t)(s * kAColsPerStage + h * 16);
-      tmem_st16(tmem + lane_off + col, vhi);
-      tmem_st16(tmem + lane_off + col + 32u, vlo);
+      // two passes of Q atoms (fewer live registers): W, its hi + lo split,
+      // and QW words of each operand into the stage's columns
+      constexpr int Q = HALF / 2;
+      constexpr int QW = BF16 ? Q / 2 : Q;
+      static_assert(QW == 8, "eight 32-bit words per operand and pass");
+      const bool none = __all_sync(0xffffffffu, cnt <= 0);
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        uint32_t vhi[QW], vlo[QW];
+        if (none) {
+#pragma unroll
+          for (int j = 0; j < QW; ++j) vhi[j] = vlo[j] = 0u;
+        } else {
+          float w[Q];
+          const float4* dp = reinterpret_cast<const float4*>(s_dt + pos + h * HALF + part * Q);
+#pragma unroll
+          for (int v = 0; v < Q / 4; ++v) {
+            const float4 d4 = dp[v];
+            if constexpr (TAB) {
+              w[4 * v] = tab_weight(su * d4.x, s_tab, p.n_tab);
+              w[4 * v + 1] = tab_weight(su * d4.y, s_tab, p.n_tab);
+              w[4 * v + 2] = tab_weight(su * d4.z, s_tab, p.n_tab);
+              w[4 * v + 3] = tab_weight(su * d4.w, s_tab, p.n_tab);
+            } else {
+              float e0, e1, e2, e3;
+              mul_x2(e0, e1, d4.x, d4.y, c2);
+              mul_x2(e2, e3, d4.z, d4.w, c2);
+              w[4 * v] = ex2(e0);
+              w[4 * v + 1] = ex2(e1);
+              w[4 * v + 2] = ex2(e2);
+              w[4 * v + 3] = ex2(e3);
+            }
+          }
+          const int32_t cq = cnt - part * Q;
+          if (!__all_sync(0xffffffffu, cq >= Q)) {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) w[j] = j < cq ? w[j] : 0.0f;
+          }
+          if constexpr (BF16) {
+#pragma unroll
+            for (int j = 0; j < QW; ++j) {
+              const uint32_t hp = pack_bf16(w[2 * j], w[2 * j + 1]);
+              const float he = __uint_as_float(hp << 16), ho = __uint_as_float(hp & 0xffff0000u);
+              float le, lo;
+              sub_x2(le, lo, w[2 * j], w[2 * j + 1], he, ho);
+              vhi[j] = hp;
+              vlo[j] = pack_bf16(le, lo);
+            }
+          } else {
+            // the MMA reads TF32 operands as FP32 bit patterns and ignores the
+            // low 13 bits, so the remainder needs no conversion of its own
+#pragma unroll
+            for (int j = 0; j < QW; ++j) {
+              const uint32_t hb = to_tf32(w[j]);
+              vhi[j] = hb;
+              vlo[j] = __float_as_uint(w[j] - __uint_as_float(hb));
+            }
+          }
+        }
+        tmem_st8(tmem + lane_off + col + (uint32_t)(part * QW), vhi);
+        tmem_st8(tmem + lane_off + col + 32u + (uint32_t)(part * QW), vlo);
+      }
       tmem_wait_st();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_full_a[s]);
     }
-    // ---- epilogue: accumulator -> 2F -> map + partials ----
+    // ---- epilogue: running sums + the chunks still in TMEM -> 2F ----
+    // (the last two chunks are still undrained; their MMAs finish before the
+    // accumulators are read)
     bool have_acc = n_kt > 0 && ok_run;
-    if (have_acc) {
-      volatile int* ab = &s_abort;
-      have_acc = mbar_wait(&bar_acc, 0, ab, p.wait_ns);
-      if (!have_acc) atomicExch(&s_abort, 1);
-    }
+    for (int c = drained; have_acc && c < n_chunks; ++c)
+      if (!mbar_wait(&bar_accf[c & 1], (c >> 1) & 1, &s_abort, p.wait_ns)) {
+        atomicExch(&s_abort, 1);
+        have_acc = false;
+      }
     tc_fence_after();
     const int tmpl_per_warp = N / 8;          // this half's templates
     const Coef cf0 = p.coef[cell];
     for (int g8 = 0; g8 < tmpl_per_warp; g8 += 8) {
       float acc[32];
-      if (have_acc) {
-        tmem_ld32(tmem + lane_off + (uint32_t)(h * (N / 2) + g8 * 4), acc);
-      } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+      for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+      if (have_acc) {
+        if (RS && drained > 0) {
+#pragma unroll
+          for (int i = 0; i < (RS ? 32 : 1); ++i) acc[i] = rs[i];
+        } else if (drained > 0) {
+          const float4* sp = s_sum + (size_t)((col_h + g8 * 4) >> 2) * kRows + row;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float4 r = sp[(size_t)i * kRows];
+            acc[4 * i] = r.x;
+            acc[4 * i + 1] = r.y;
+            acc[4 * i + 2] = r.z;
+            acc[4 * i + 3] = r.w;
+          }
+        }
+#pragma unroll 1
+        for (int c = drained; c < n_chunks; ++c) {
+          const uint32_t ca = tmem + lane_off + (uint32_t)((c & 1) * N) + col_h + (uint32_t)(g8 * 4);
+          float v[16];
+          tmem_ld16(ca, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[i] += v[i];
+          tmem_ld16(ca + 16u, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[16 + i] += v[i];
+        }
       }
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
@@ -636,13 +789,20 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   prm.shared_antenna = a->shared_antenna;
   prm.n_templates = T;
   prm.n_cols = N;
-  // three stages, or two where that keeps a CTA within half the SM's TMEM
-  // columns (N = 128): two resident CTAs run two MMA streams side by side
-  const bool tab = g.window == FMAP_TABLE;   // (one CTA per SM at any N: three stages)
-  const int NS =
-      (!tab && N + 3 * tc::kAColsPerStage > 256 && N + 2 * tc::kAColsPerStage <= 256) ? 2 : 3;
+  // TMEM: two accumulators of N columns, then the A stages.  Two stages where
+  // that keeps a CTA within half the SM's TMEM columns (N = 64): two resident
+  // CTAs run two MMA streams side by side; otherwise three stages where they
+  // fit the SM's 512 columns (one CTA per SM), else two.
+  const bool tab = g.window == FMAP_TABLE;
+  const int acc_cols = 2 * N;
+  int NS;
+  if (!tab && acc_cols + 2 * tc::kAColsPerStage <= 256)
+    NS = 2;
+  else
+    NS = acc_cols + 3 * tc::kAColsPerStage <= 512 ? 3 : 2;
   int tcols = 32;
-  while (tcols < N + NS * tc::kAColsPerStage) tcols *= 2;
+  while (tcols < acc_cols + NS * tc::kAColsPerStage) tcols *= 2;
+  if (tcols > 512) return cudaErrorInvalidConfiguration;
   prm.tmem_cols = tcols;
   prm.nblk = (g.n_tau + tc::kRows - 1) / tc::kRows;
   prm.map = d_2F;
@@ -650,29 +810,54 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   prm.stride = p->part_stride;
   prm.err = p->ws.dev_err;
   prm.wait_ns = (uint64_t)p->wait_ns;
-  // shared memory: NS stages x (hi + lo) x N rows x 128 B; at least enough to
-  // keep the resident CTAs within the 512 TMEM columns of an SM
+  // shared memory: NS stages x (hi + lo) x N rows x 128 B, the staged times,
+  // the table (TAB), the running sums (128 rows x N floats) and the 1 KB
+  // alignment; at least enough to keep the resident CTAs within the 512
+  // TMEM columns of an SM
   size_t smem = (size_t)NS * 2 * N * 128 + sizeof(float) * tc::kDtCap + 1024 +
-                (tab ? sizeof(float2) * (kTabMax + 1) : 0);
+                (tab ? sizeof(float2) * (kTabMax + 1) + 16 : 0) +
+                (N == 64 ? 0 : (size_t)tc::kRows * N * 4);
   const size_t min_smem = tcols > 256 ? 120 * 1024 : 80 * 1024;
   smem = std::max(smem, min_smem);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   const int chunks = (ncols + N - 1) / N;
   dim3 grid((unsigned)tiles, (unsigned)chunks);
   const CUtensorMap* mh = (const CUtensorMap*)p->tmap_hi;
   const CUtensorMap* ml = (const CUtensorMap*)p->tmap_lo;
+  cudaError_t err = cudaSuccess;
   auto run = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, tc::kThreads, smem, s>>>(*mh, *ml, prm);
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) kern<<<grid, tc::kThreads, smem, s>>>(*mh, *ml, prm);
   };
+  // N = 64 keeps the running sums in registers (the kernel's 2-CTA register
+  // budget holds its 32 a thread), wider chunks in shared memory
+  const bool rs = N == 64;
   if (bf16) {
-    if (tab) run(tc::k_exp_tc<true, true, 3>);
-    else if (NS == 2) run(tc::k_exp_tc<true, false, 2>);
-    else run(tc::k_exp_tc<true, false, 3>);
+    if (rs) {
+      if (tab) run(tc::k_exp_tc<true, true, 3, true>);
+      else run(tc::k_exp_tc<true, false, 2, true>);
+    } else if (tab) {
+      if (NS == 2) run(tc::k_exp_tc<true, true, 2, false>);
+      else run(tc::k_exp_tc<true, true, 3, false>);
+    } else if (NS == 2) {
+      run(tc::k_exp_tc<true, false, 2, false>);
+    } else {
+      run(tc::k_exp_tc<true, false, 3, false>);
+    }
   } else {
-    if (tab) run(tc::k_exp_tc<false, true, 3>);
-    else if (NS == 2) run(tc::k_exp_tc<false, false, 2>);
-    else run(tc::k_exp_tc<false, false, 3>);
+    if (rs) {
+      if (tab) run(tc::k_exp_tc<false, true, 3, true>);
+      else run(tc::k_exp_tc<false, false, 2, true>);
+    } else if (tab) {
+      if (NS == 2) run(tc::k_exp_tc<false, true, 2, false>);
+      else run(tc::k_exp_tc<false, true, 3, false>);
+    } else if (NS == 2) {
+      run(tc::k_exp_tc<false, false, 2, false>);
+    } else {
+      run(tc::k_exp_tc<false, false, 3, false>);
+    }
   }
+  if (err != cudaSuccess) return err;
   p->launches += 1;
   return cudaGetLastError();
 }

@@ -13,11 +13,16 @@
 // library holds its kScratchBytes until the process exits.  Host code cannot
 // use the array's name as a device address (in host code that name is a
 // host-side stand-in), so the first call on each device, with that device
-// current, looks its address up with cudaGetSymbolAddress and caches it; make
-// that first call before any stream capture.  All calls share the one array:
+// current, looks its address up with cudaGetSymbolAddress and caches it with
+// the context it belongs to; make that first call before any stream capture.
+// A call in a different context (after cudaDeviceReset, which unloads the
+// library's device code) looks the address up again, so make the first call
+// after a reset outside stream capture too.  All calls share the one array:
 // calls whose work overlaps on the GPU (different streams, or different host
 // threads) race on it and must be serialised by the caller.  Nothing in the
 // array has to start at zero: each call writes every partial it later reads.
+#include <cuda.h>
+
 #include <mutex>
 #include <string>
 
@@ -33,9 +38,28 @@ static __device__ __align__(256) Partial g_scratch[kScratchPartials];
 
 static std::mutex g_scratch_mu;
 static Partial* g_scratch_ptr[kMaxDevices] = {};
+static CUcontext g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once per
-// device).
+// The driver's cuCtxGetCurrent, found through the runtime (the library does
+// not link the driver directly, so it loads on machines without one).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+static CUcontext current_context() {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)f;
+  }
+  CUcontext ctx = nullptr;
+  if (!fn || fn(&ctx) != CUDA_SUCCESS) return nullptr;
+  return ctx;
+}
+
+// Device address of g_scratch on the current device: looked up once per
+// device and context (the context changes when the device is reset).
 static fmap_status scratch_on_current_device(Partial** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -44,12 +68,16 @@ static fmap_status scratch_on_current_device(Partial** out) {
     set_error("device ordinal beyond the no-allocation scratch table");
     return FMAP_ERR_UNSUPPORTED;
   }
+  // (null on a host thread the runtime has not used yet)
+  CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
     void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_scratch);
+    e = cudaGetSymbolAddress(&ptr, g_scratch);   // (makes the device's context current)
     if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    ctx = current_context();
     g_scratch_ptr[dev] = (Partial*)ptr;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return FMAP_OK;

@@ -9,12 +9,14 @@
 //   1. histograms the valid cells whose fast 2F lies within kRefWindow of the
 //      fast maximum M (kRefBins bins, bin 0 at the maximum);
 //   2. cuts the histogram after the last bin that keeps the cell count within
-//      the plan's cap, and collects those cells (sorted by index, so that
-//      every later sum runs in a fixed order);
-//   3. recomputes each collected cell from its atoms by the plain FP64
+//      the plan's cap, and collects those cells (in no fixed order: every
+//      later reduction over them is order-independent -- integer sums of
+//      fixed-point terms and a minimum of cell indices);
+//   3. recomputes each collected cell from its atoms by the plain
 //      definition: the windowed sums of Eq. (winrect) / (winexp) with w on
-//      Fa, Fb and w^2 on A, B, C, D = AB - C^2, and 2F of Eq. (F_FaFb); the
-//      FP64 value replaces the fast one in the map;
+//      Fa, Fb and w^2 on A, B, C (in float-float, ~2^-44 relative), then
+//      D = AB - C^2 and 2F of Eq. (F_FaFb) in FP64; the refined value
+//      replaces the fast one in the map;
 //   4. rebuilds the summary: max2F and the argmax (lowest index on FP64
 //      ties) from the FP64 values, and the exp-sum with the collected cells'
 //      fast terms replaced by their FP64 terms,
@@ -31,7 +33,6 @@ namespace fmap {
 
 constexpr int kRefThreads = 256;
 constexpr int kRefUnroll = 8;        // cells per thread and pass (independent loads)
-constexpr int kRefSortThreads = 1024;
 
 int32_t refine_cells_of(const fmap_plan_s* p) {
   if (p->refine_cells == 0 || !p->ws.tstat) return 0;
@@ -56,22 +57,44 @@ __device__ __forceinline__ int ref_bin_of(float v, float M) {
   return d > 0.0f ? (int)d : 0;
 }
 
-// Passes 1 and 3 over the map: the histogram (collect = false) or the
-// collection of the cells up to the cut (collect = true).  Grid (x, T).
+// The last histogram bin whose cumulative count stays within the cap (-1:
+// the top bin alone exceeds it).
+__device__ __forceinline__ int32_t ref_cut_of(const int32_t* __restrict__ h, int32_t cap) {
+  int32_t cum = 0, b = -1;
+  for (int k = 0; k < kRefBins; ++k) {
+    cum += h[k];
+    if (cum > cap) break;
+    b = k;
+  }
+  return b;
+}
+
+// Passes over the map: the histogram (collect = false), or the cut and the
+// collection of the cells up to it (collect = true; block x = 0 records the
+// cut).  Grid (x, T).  The histogram and the counts were cleared by the final
+// reduction.
 template <bool kCollect>
 __global__ void __launch_bounds__(kRefThreads)
 k_ref_scan(const float* __restrict__ map, const Coef* __restrict__ coef, int32_t shared,
-           int64_t cells, const TStat* __restrict__ st, int32_t* __restrict__ hist,
-           const int32_t* __restrict__ cut, int32_t* __restrict__ ref_n,
+           int64_t cells, const TStat* __restrict__ st, int32_t* __restrict__ hist, int32_t cap,
+           int32_t* __restrict__ cut, int32_t* __restrict__ ref_n,
            int32_t* __restrict__ ref_cell) {
   __shared__ int32_t h[kRefBins];
+  __shared__ int32_t s_last;
   const int32_t j = blockIdx.y;
-  if (!kCollect) {
-    for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = 0;
+  if (kCollect) {
+    for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = hist[(int64_t)j * kRefBins + b];
     __syncthreads();
+    if (threadIdx.x == 0) {
+      s_last = ref_cut_of(h, cap);
+      if (blockIdx.x == 0) cut[j] = s_last;
+    }
+  } else {
+    for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = 0;
   }
+  __syncthreads();
   const TStat s = st[j];
-  const int32_t last = kCollect ? cut[j] : kRefBins - 1;
+  const int32_t last = kCollect ? s_last : kRefBins - 1;
   if (s.N > 0 && last >= 0) {
     const float* mp = map + (int64_t)j * cells;
     const int64_t span = (int64_t)kRefThreads * kRefUnroll;
@@ -85,13 +108,19 @@ k_ref_scan(const float* __restrict__ map, const Coef* __restrict__ coef, int32_t
 #pragma unroll
       for (int u = 0; u < kRefUnroll; ++u) {
         const int64_t c = base + u * kRefThreads + threadIdx.x;
-        const int b = ref_bin_of(v[u], s.M);
-        if (b < 0 || b > last || c >= cells || !ref_valid(coef, shared, cells, j, c)) continue;
+        int b = ref_bin_of(v[u], s.M);
+        if (b > last || c >= cells || (b >= 0 && !ref_valid(coef, shared, cells, j, c))) b = -1;
         if (kCollect) {
-          const int32_t slot = atomicAdd(ref_n + j, 1);
-          if (slot < kRefMaxCells) ref_cell[(int64_t)j * kRefMaxCells + slot] = (int32_t)c;
+          if (b >= 0) {
+            const int32_t slot = atomicAdd(ref_n + j, 1);
+            if (slot < kRefMaxCells) ref_cell[(int64_t)j * kRefMaxCells + slot] = (int32_t)c;
+          }
         } else {
-          atomicAdd(&h[b], 1);
+          // one shared-memory atomic per distinct bin of the warp (noise maps
+          // put most cells of the window in a few bins)
+          const unsigned peers = __match_any_sync(0xffffffffu, b);
+          if (b >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+            atomicAdd(&h[b], __popc(peers));
         }
       }
     }
@@ -101,53 +130,6 @@ k_ref_scan(const float* __restrict__ map, const Coef* __restrict__ coef, int32_t
     for (int b = threadIdx.x; b < kRefBins; b += blockDim.x)
       if (h[b]) atomicAdd(hist + (int64_t)j * kRefBins + b, h[b]);
   }
-}
-
-// Pass 2: per template the last bin whose cumulative count stays within the
-// cap (-1: the top bin alone exceeds it); clears the candidate counter.
-__global__ void k_ref_cut(const int32_t* __restrict__ hist, int32_t cap, int32_t* __restrict__ cut,
-                          int32_t* __restrict__ ref_n) {
-  const int32_t j = blockIdx.x;
-  if (threadIdx.x != 0) return;
-  int32_t cum = 0, b = -1;
-  for (int k = 0; k < kRefBins; ++k) {
-    cum += hist[(int64_t)j * kRefBins + k];
-    if (cum > cap) break;
-    b = k;
-  }
-  cut[j] = b;
-  ref_n[j] = 0;
-}
-
-// Pass 4: the collected cells of a template in ascending index order
-// (bitonic sort in shared memory, padded with INT32_MAX).
-__global__ void __launch_bounds__(kRefSortThreads)
-k_ref_sort(const int32_t* __restrict__ ref_n, int32_t* __restrict__ ref_cell) {
-  __shared__ int32_t v[kRefMaxCells];
-  const int32_t j = blockIdx.x;
-  const int32_t n = min(ref_n[j], kRefMaxCells);
-  int32_t p2 = 1;
-  while (p2 < n) p2 <<= 1;
-  int32_t* cells = ref_cell + (int64_t)j * kRefMaxCells;
-  for (int i = threadIdx.x; i < p2; i += blockDim.x) v[i] = i < n ? cells[i] : 0x7fffffff;
-  __syncthreads();
-  for (int k = 2; k <= p2; k <<= 1) {
-    for (int d = k >> 1; d > 0; d >>= 1) {
-      for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-        const int o = i ^ d;
-        if (o > i) {
-          const bool up = (i & k) == 0;
-          const int32_t a = v[i], b = v[o];
-          if ((a > b) == up) {
-            v[i] = b;
-            v[o] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) cells[i] = v[i];
 }
 
 struct RefArgs {
@@ -171,12 +153,19 @@ struct RefArgs {
   double* ref_val;
 };
 
-// Pass 5: one warp per collected cell.  The lanes split the window's atoms
-// into 32 contiguous runs; an exponential run takes its first weight from an
-// FP64 exp and the rest as products of per-gap decays (e^{-T_sft/tau} for
-// one-SFT gaps), a table window evaluates w per atom, a rectangular one has
-// w = 1.  The seven FP64 sums meet in a fixed butterfly; lane 0 forms D and
-// 2F, records the fast and FP64 values and writes the FP64 value to the map.
+// Pass 3: one warp per collected cell.  The lanes split the window's atoms
+// into 32 contiguous runs and sum them in float-float arithmetic (a value is
+// an unevaluated pair h + l, ~2^-44 relative; GB300 runs FP64 at 1/64 of the
+// FP32 rate): an exponential run takes its first weight from an FP64 exp and
+// the rest as products of per-gap decays (e^{-T_sft/tau} for one-SFT gaps), a
+// table window evaluates w per atom in FP64, a rectangular one has w = 1.  The
+// seven sums meet in a fixed butterfly; lane 0 forms D and 2F in FP64 from
+// them, records the fast and refined values and writes the refined value to
+// the map.
+__device__ __forceinline__ void ff_acc(FF& s, FF w, float x) {
+  s = ff_add(s, ff_mul_f(w, x));
+}
+
 __global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t j = blockIdx.y;
@@ -198,41 +187,59 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
   const float* x = A.fafb + (int64_t)j * 4 * n;
   const bool ex = g.window == FMAP_EXP, tw = g.window == FMAP_TABLE;
   const double su = tw ? tab_scale(A.n_tab, exp_cut8_of(g), tau) : 0.0;
-  double s[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  FF s[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) s[q] = FF{0.0f, 0.0f};
   if (a_lo < a_hi) {
-    double w = 1.0, rho1 = 1.0;
+    FF w{1.0f, 0.0f}, rho1{1.0f, 0.0f};
     if (ex) {
-      w = exp(-(double)((int64_t)A.rel_t[a_lo] - t0rel) * inv_tau);
-      rho1 = exp(-(double)g.t_sft * inv_tau);
+      w = ff_of(exp(-(double)((int64_t)A.rel_t[a_lo] - t0rel) * inv_tau));
+      rho1 = ff_of(exp(-(double)g.t_sft * inv_tau));
     }
     for (int32_t a = a_lo; a < a_hi; ++a) {
       if (ex && a > a_lo) {
         const int32_t gap = A.rel_t[a] - A.rel_t[a - 1];
-        w *= gap == (int32_t)g.t_sft ? rho1 : exp(-(double)gap * inv_tau);
+        w = ff_mul(w, gap == (int32_t)g.t_sft ? rho1 : ff_of(exp(-(double)gap * inv_tau)));
       }
-      if (tw) w = tab_weight64((double)((int64_t)A.rel_t[a] - t0rel) * su, A.wtab, A.n_tab);
-      const double w2 = w * w;
-      s[0] = fma(w2, (double)ant[a], s[0]);
-      s[1] = fma(w2, (double)ant[n + a], s[1]);
-      s[2] = fma(w2, (double)ant[2 * n + a], s[2]);
-      s[3] = fma(w, (double)x[a], s[3]);
-      s[4] = fma(w, (double)x[n + a], s[4]);
-      s[5] = fma(w, (double)x[2 * n + a], s[5]);
-      s[6] = fma(w, (double)x[3 * n + a], s[6]);
+      if (tw) w = ff_of(tab_weight64((double)((int64_t)A.rel_t[a] - t0rel) * su, A.wtab, A.n_tab));
+      if (g.window == FMAP_RECT) {
+        s[0] = ff_add(s[0], FF{ant[a], 0.0f});
+        s[1] = ff_add(s[1], FF{ant[n + a], 0.0f});
+        s[2] = ff_add(s[2], FF{ant[2 * n + a], 0.0f});
+        s[3] = ff_add(s[3], FF{x[a], 0.0f});
+        s[4] = ff_add(s[4], FF{x[n + a], 0.0f});
+        s[5] = ff_add(s[5], FF{x[2 * n + a], 0.0f});
+        s[6] = ff_add(s[6], FF{x[3 * n + a], 0.0f});
+      } else {
+        const FF w2 = ff_mul(w, w);
+        ff_acc(s[0], w2, ant[a]);
+        ff_acc(s[1], w2, ant[n + a]);
+        ff_acc(s[2], w2, ant[2 * n + a]);
+        ff_acc(s[3], w, x[a]);
+        ff_acc(s[4], w, x[n + a]);
+        ff_acc(s[5], w, x[2 * n + a]);
+        ff_acc(s[6], w, x[3 * n + a]);
+      }
     }
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1)
 #pragma unroll
-    for (int q = 0; q < 7; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], d);
+    for (int q = 0; q < 7; ++q) {
+      const FF o{__shfl_xor_sync(0xffffffffu, s[q].h, d), __shfl_xor_sync(0xffffffffu, s[q].l, d)};
+      s[q] = ff_add(s[q], o);
+    }
   if (lane == 0) {
-    const double Aa = s[0], Bb = s[1], Cc = s[2];
+    double v7[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) v7[q] = (double)s[q].h + (double)s[q].l;
+    const double Aa = v7[0], Bb = v7[1], Cc = v7[2];
     const double D = Aa * Bb - Cc * Cc;
     const bool ok = len >= 2 && D > 0.0;
     double v = 0.0;
     if (ok)
-      v = 2.0 * (Bb * (s[3] * s[3] + s[4] * s[4]) + Aa * (s[5] * s[5] + s[6] * s[6]) -
-                 2.0 * Cc * (s[3] * s[5] + s[4] * s[6])) / D;
+      v = 2.0 * (Bb * (v7[3] * v7[3] + v7[4] * v7[4]) + Aa * (v7[5] * v7[5] + v7[6] * v7[6]) -
+                 2.0 * Cc * (v7[3] * v7[5] + v7[4] * v7[6])) / D;
     float* mp = A.map + (int64_t)j * A.cells + c;
     A.ref_fast[slot] = *mp;
     A.ref_val[slot] = ok ? v : -1.0;
@@ -240,8 +247,12 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
   }
 }
 
-// Pass 6: one warp per template rebuilds its summary from the fast
-// statistics and the collected cells (fixed per-lane order, fixed butterfly).
+// Pass 4: one warp per template rebuilds its summary from the fast
+// statistics and the collected cells.  Every exp-term is in (0, 1] (relative
+// to the fast or the refined maximum, both held by a collected cell) and is
+// summed as an integer in 2^-52 units, so the sums do not depend on the
+// order in which the cells were collected (<= 4096 terms: no overflow,
+// relative error < 1e-12).
 __global__ void __launch_bounds__(32)
 k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ cut,
             const int32_t* __restrict__ ref_n, const int32_t* __restrict__ ref_cell,
@@ -258,15 +269,17 @@ k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ cut,
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, d));
   if (mx < 0.0) return;   // no collected cell valid in FP64: keep the fast summary
-  double sub = 0.0, add = 0.0;
+  constexpr double kFix = 4503599627370496.0;   // 2^52
+  unsigned long long sub = 0ull, add = 0ull;
   long long nv = 0;
   int32_t arg = 0x7fffffff;
   const double M = (double)s.M;
   for (int32_t k = lane; k < n; k += 32) {
-    sub += exp(0.5 * ((double)ref_fast[base + k] - M));
+    const double ef = exp(0.5 * fmin((double)ref_fast[base + k] - M, 0.0));
+    sub += (unsigned long long)__double2ull_rn(ef * kFix);
     const double v = ref_val[base + k];
     if (v >= 0.0) {
-      add += exp(0.5 * (v - mx));
+      add += (unsigned long long)__double2ull_rn(exp(0.5 * (v - mx)) * kFix);
       nv += 1;
       if (v == mx) arg = min(arg, ref_cell[base + k]);
     }
@@ -279,7 +292,7 @@ k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ cut,
     arg = min(arg, __shfl_xor_sync(0xffffffffu, arg, d));
   }
   if (lane != 0) return;
-  const double Sp = exp(0.5 * (M - mx)) * fmax(s.S - sub, 0.0) + add;
+  const double Sp = exp(0.5 * (M - mx)) * fmax(s.S - (double)sub / kFix, 0.0) + (double)add / kFix;
   const long long Np = s.N - n + nv;
   const int32_t b = cut[j];
   const double depth = b + 1 >= kRefBins ? (double)kRefWindow
@@ -304,19 +317,16 @@ cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
   if (cap <= 0 || !d_2F || !d_summary || T == 0 || cells == 0 || p->n_sft == 0)
     return cudaSuccess;
   Workspace& w = p->ws;
-  cudaError_t e = cudaMemsetAsync(w.ref_hist, 0, sizeof(int32_t) * kRefBins * (size_t)T, s);
-  if (e != cudaSuccess) return e;
   const int32_t sh = a->shared_antenna ? 1 : 0;
   const int64_t span = (int64_t)kRefThreads * kRefUnroll;
   const int64_t want = std::max<int64_t>(1, ((int64_t)p->n_sm * 8 + T - 1) / T);
   const unsigned gx = (unsigned)std::min<int64_t>((cells + span - 1) / span, want);
   const dim3 grid(gx, (unsigned)T);
+  // (the final reduction cleared the histogram and the candidate counts)
   k_ref_scan<false><<<grid, kRefThreads, 0, s>>>(d_2F, w.coef, sh, cells, w.tstat, w.ref_hist,
-                                                 nullptr, nullptr, nullptr);
-  k_ref_cut<<<T, 32, 0, s>>>(w.ref_hist, cap, w.ref_bin, w.ref_n);
-  k_ref_scan<true><<<grid, kRefThreads, 0, s>>>(d_2F, w.coef, sh, cells, w.tstat, nullptr,
-                                                w.ref_bin, w.ref_n, w.ref_cell);
-  k_ref_sort<<<T, kRefSortThreads, 0, s>>>(w.ref_n, w.ref_cell);
+                                                 cap, nullptr, nullptr, nullptr);
+  k_ref_scan<true><<<grid, kRefThreads, 0, s>>>(d_2F, w.coef, sh, cells, w.tstat, w.ref_hist,
+                                                cap, w.ref_bin, w.ref_n, w.ref_cell);
   RefArgs A;
   A.rel_t = w.rel_t;
   A.t_base = w.t_base;
@@ -340,7 +350,7 @@ cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
   k_ref_cells<<<dim3((unsigned)((cap + wpb - 1) / wpb), (unsigned)T), kRefThreads, 0, s>>>(A);
   k_ref_final<<<T, 32, 0, s>>>(w.tstat, w.ref_bin, w.ref_n, w.ref_cell, w.ref_fast, w.ref_val,
                                g.n_tau, p->log_prior, fast_tol(p), d_summary);
-  p->launches += 6;
+  p->launches += 4;
   return cudaGetLastError();
 }
 
