@@ -43,11 +43,21 @@ constexpr size_t kRecSmemCap = 220 * 1024;
 __host__ __device__ __forceinline__ size_t rec_smem_base(int32_t n_sft) {
   return sizeof(float) * 4 * ((size_t)n_sft + 1) + 16;
 }
+// Blocks of the recurrence an SM holds with a given dynamic shared memory
+// (three at most: the registers of 3 x 256 threads).
+__host__ __device__ __forceinline__ int rec_blocks_per_sm(size_t smem) {
+  const size_t per_sm = 227 * 1024;
+  const size_t k = per_sm / (smem + 1024);
+  return (int)(k < 3 ? k : 3);
+}
 // Staged only for blocks that run two or more templates (a single template
-// reads each record once, and the staging's shared memory would only lower
-// the blocks per SM).
+// reads each record once), and only when the staging's shared memory costs
+// no resident block (long data sets: the suffix rows alone take 80 KB at
+// 5000 SFTs, and with the records an SM would hold one block instead of
+// two; recomputing a record per template is cheaper than that).
 __host__ __device__ __forceinline__ bool rec_stage_cells(int32_t n_sft, int32_t n_t0, int32_t tpb) {
-  return tpb >= 2 && rec_smem_base(n_sft) + sizeof(CellRec) * (size_t)n_t0 <= kRecSmemCap;
+  const size_t base = rec_smem_base(n_sft), with = base + sizeof(CellRec) * (size_t)n_t0;
+  return tpb >= 2 && with <= kRecSmemCap && rec_blocks_per_sm(with) >= rec_blocks_per_sm(base);
 }
 
 __device__ __forceinline__ float rec_ex2(float x) {
