@@ -96,7 +96,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
       esuf, xop, perm_ant, perm_x, perm_gap, tauc, ax, wtab, flag_bits, tstat, ref_hist, ref_bin,
-      ref_n, ref_cell, ref_fast, ref_val, own_map, total;
+      ref_n, ref_cell, ref_fast, ref_val, own_map, ref_ntile, ref_tile, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -143,6 +143,8 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     const size_t Tn = (size_t)std::max<int32_t>(T, 1);
     L.tstat = take(sizeof(TStat) * Tn);
     L.ref_hist = take(sizeof(int32_t) * kRefBins * Tn);
+    L.ref_ntile = take(sizeof(int32_t) * Tn);
+    L.ref_tile = take(sizeof(int32_t) * kRefMaxTiles * Tn);
     L.ref_bin = take(sizeof(int32_t) * Tn);
     L.ref_n = take(sizeof(int32_t) * Tn);
     L.ref_cell = take(sizeof(int32_t) * kRefMaxCells * Tn);
@@ -290,6 +292,8 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
   if (!(flags & kPlanNoRefine)) {
     w.tstat = (TStat*)(b + L.tstat);
     w.ref_hist = (int32_t*)(b + L.ref_hist);
+    w.ref_ntile = (int32_t*)(b + L.ref_ntile);
+    w.ref_tile = (int32_t*)(b + L.ref_tile);
     w.ref_bin = (int32_t*)(b + L.ref_bin);
     w.ref_n = (int32_t*)(b + L.ref_n);
     w.ref_cell = (int32_t*)(b + L.ref_cell);
@@ -476,7 +480,7 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   if (ev[3]) FMAP_CUDA(cudaEventRecord(ev[3], s));
   FMAP_CUDA(launch_flag_and_fixup(p, a, d_2F, s));
   FMAP_CUDA(launch_final_reduce(p, tiles, true, d_summary, s));
-  FMAP_CUDA(launch_refine(p, a, d_2F, d_summary, s));
+  FMAP_CUDA(launch_refine(p, a, d_2F, d_summary, tiles, s));
   if (ev[4]) FMAP_CUDA(cudaEventRecord(ev[4], s));
   return FMAP_OK;
 }

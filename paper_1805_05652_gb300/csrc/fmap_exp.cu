@@ -545,6 +545,7 @@ cudaError_t launch_exp_plain(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, c
   const fmap_grid& g = p->grid;
   const int64_t tiles = exp_tiles(g);
   *tiles_used = tiles;
+  p->tiles = TileGeom{0, 1, kExpCells, g.n_t0, (g.n_tau + kExpCells - 1) / kExpCells};
   if (tiles == 0 || p->n_templates == 0) return cudaSuccess;
   const bool tab = g.window == FMAP_TABLE;
   auto run = [&](auto kern, int tc) {

@@ -282,6 +282,7 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
   *tiles_used = 0;
   if ((int64_t)g.n_t0 * g.n_tau == 0 || p->n_templates == 0) return cudaSuccess;
   *tiles_used = g.n_tau;
+  p->tiles = TileGeom{0, g.n_t0, 1, 1, g.n_tau};   // one tau column per tile
   // split the templates over enough blocks to fill the GPU a few times
   const int64_t want = (int64_t)p->n_sm * 4;
   const int32_t groups = (int32_t)std::max<int64_t>(

@@ -752,6 +752,7 @@ cudaError_t launch_exp_tc(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cuda
   const fmap_grid& g = p->grid;
   const int64_t tiles = exp_tiles(g);
   *tiles_used = tiles;
+  p->tiles = TileGeom{0, 1, tc::kRows, g.n_t0, (g.n_tau + tc::kRows - 1) / tc::kRows};
   if (tiles == 0 || p->n_templates == 0) return cudaSuccess;
   const bool bf16 = p->precision == FMAP_BF16X3;
   const int32_t T = p->n_templates;

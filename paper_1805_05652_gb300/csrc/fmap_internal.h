@@ -70,6 +70,17 @@ constexpr uint32_t kPlanNoRefine = 1u << 16;
 constexpr int kRefMaxCells = 4096;
 constexpr int kRefBins = 256;
 constexpr float kRefWindow = 16.0f;
+// Tiles the refinement may scan per template (those whose fast maximum can
+// bound a top cell; a few more than the cells wanted, ties included).
+constexpr int kRefMaxTiles = 16384;
+// Geometry of the reduction tiles of a plan's main kernel: rectangles of R
+// t0 rows x C tau columns, tile index tr * ntc + tc (row-major) or tc * ntr +
+// tr (column-major), so that a tile's cells can be found from its index.
+struct TileGeom {
+  int32_t col_major;
+  int32_t R, C;
+  int32_t ntr, ntc;
+};
 // Per-template statistics of the fast reduction, kept for the refinement:
 // S = sum over valid cells of exp((2F - M) / 2), M = max 2F, arg its lowest
 // cell, N the valid count.
@@ -172,7 +183,9 @@ struct Workspace {
   // candidates (cell, fast 2F, FP64 2F) and the plan's own map (if any)
   TStat* tstat = nullptr;        // [T]
   int32_t* ref_hist = nullptr;   // [T][kRefBins]
-  int32_t* ref_bin = nullptr;    // [T] last histogram bin taken (-1: none)
+  int32_t* ref_ntile = nullptr;  // [T] tiles selected for the cell scan
+  int32_t* ref_tile = nullptr;   // [T][kRefMaxTiles] their partial slots
+  int32_t* ref_bin = nullptr;    // [T] last bin whose cells all lie in the scanned tiles
   int32_t* ref_n = nullptr;      // [T] candidates
   int32_t* ref_cell = nullptr;   // [T][kRefMaxCells]
   float* ref_fast = nullptr;     // [T][kRefMaxCells]
@@ -206,6 +219,7 @@ struct fmap_plan_s {
   uint32_t flags = 0;
   double log_prior = 0.0;
   int32_t refine_cells = -1;  // fmap_plan_set_refine (< 0: the precision's default)
+  fmap::TileGeom tiles{};      // reduction tiles of the last compute call's main kernel
   int64_t wait_ns = fmap::kDefaultWaitNs;   // fmap_plan_set_wait_limit
   int device = 0;
   int n_sm = 0;
@@ -273,9 +287,10 @@ cudaError_t launch_rect_coef(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s
 cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
                                   cudaStream_t s);
 // Top-cell refinement of the summaries (after launch_final_reduce); d_2F is
-// the map the compute call wrote.
+// the map the compute call wrote, n_tiles the main kernel's partial slots
+// (geometry p->tiles).
 cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
-                          fmap_summary* d_summary, cudaStream_t s);
+                          fmap_summary* d_summary, int64_t n_tiles, cudaStream_t s);
 // Candidates per template of a plan's refinement (0: off).
 int32_t refine_cells_of(const fmap_plan_s* p);
 // Reduces partial slots [0, n_tiles) and, when with_fix, the fix-up slots.

@@ -672,6 +672,7 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
     if (mark) cudaEventRecord(mark, s);
     dim3 grid((unsigned)((g.n_t0 + kRowThreads - 1) / kRowThreads), (unsigned)p->n_templates);
     *tiles_used = grid.x;
+    p->tiles = TileGeom{0, kRowThreads, g.n_tau, (int32_t)grid.x, 1};
     k_rect_rows_fp32<<<grid, kRowThreads, 0, s>>>(p->ws.i0, p->ws.jend, p->ws.coef, a->fafb,
                                                   p->n_sft, g.n_t0, g.n_tau, a->shared_antenna,
                                                   d_2F, p->ws.partials, p->part_stride);
@@ -689,6 +690,8 @@ cudaError_t launch_rect(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cudaSt
   if (mark) cudaEventRecord(mark, s);
   const int32_t T = p->n_templates, sh = a->shared_antenna ? 1 : 0;
   *tiles_used = rect_partial_slots(g, T, sh);
+  p->tiles = TileGeom{1, kTileRows, kTileCols, (g.n_t0 + kTileRows - 1) / kTileRows,
+                      (g.n_tau + kTileCols - 1) / kTileCols};
   const int64_t blocks = rect_cells_blocks(g, T, sh);
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
   const size_t smem = rect_cells_smem(T, sh);

@@ -7,7 +7,10 @@
 // (max, argmax, exp-sum, count) and recomputed the ill-conditioned cells,
 // this stage, per template:
 //   1. histograms the valid cells whose fast 2F lies within kRefWindow of the
-//      fast maximum M (kRefBins bins, bin 0 at the maximum);
+//      fast maximum M (kRefBins bins, bin 0 at the maximum) -- reading only
+//      the tiles whose fast maximum (from the reduction partials) can bound
+//      one of the cells the cut will take, so the cost does not grow with
+//      the map;
 //   2. cuts the histogram after the last bin that keeps the cell count within
 //      the plan's cap, and collects those cells (in no fixed order: every
 //      later reduction over them is order-independent -- integer sums of
@@ -32,7 +35,7 @@
 namespace fmap {
 
 constexpr int kRefThreads = 256;
-constexpr int kRefUnroll = 8;        // cells per thread and pass (independent loads)
+constexpr int kScanShare = 256;   // cells of a listed tile per scanning warp
 
 int32_t refine_cells_of(const fmap_plan_s* p) {
   if (p->refine_cells == 0 || !p->ws.tstat) return 0;
@@ -43,10 +46,11 @@ int32_t refine_cells_of(const fmap_plan_s* p) {
 // Relative error bound (floor 1) of a plan's fast 2F.
 static double fast_tol(const fmap_plan_s* p) { return p->precision == FMAP_FP64 ? 1e-5 : 1e-3; }
 
-__device__ __forceinline__ bool ref_valid(const Coef* __restrict__ coef, int32_t shared,
-                                          int64_t cells, int32_t j, int64_t c) {
-  const float v = coef[shared ? c : (int64_t)j * cells + c].valid;
-  return v == 1.0f || v == 3.0f;
+// Coef.valid of cell c for template j: 1 summed by the main kernel, 3
+// recomputed by the fix-up (and summed in a fix-up slot), else invalid.
+__device__ __forceinline__ float ref_valid_of(const Coef* __restrict__ coef, int32_t shared,
+                                              int64_t cells, int32_t j, int64_t c) {
+  return coef[shared ? c : (int64_t)j * cells + c].valid;
 }
 
 // Bin of a fast value v against the template's maximum M: floor((M - v)
@@ -58,10 +62,12 @@ __device__ __forceinline__ int ref_bin_of(float v, float M) {
 }
 
 // The last histogram bin whose cumulative count stays within the cap (-1:
-// the top bin alone exceeds it).
-__device__ __forceinline__ int32_t ref_cut_of(const int32_t* __restrict__ h, int32_t cap) {
+// the top bin alone exceeds it), at most bt (the last bin whose cells all
+// lie in scanned tiles).
+__device__ __forceinline__ int32_t ref_cut_of(const int32_t* __restrict__ h, int32_t cap,
+                                              int32_t bt) {
   int32_t cum = 0, b = -1;
-  for (int k = 0; k < kRefBins; ++k) {
+  for (int k = 0; k <= bt && k < kRefBins; ++k) {
     cum += h[k];
     if (cum > cap) break;
     b = k;
@@ -69,66 +75,196 @@ __device__ __forceinline__ int32_t ref_cut_of(const int32_t* __restrict__ h, int
   return b;
 }
 
-// Passes over the map: the histogram (collect = false), or the cut and the
-// collection of the cells up to it (collect = true; block x = 0 records the
-// cut).  Grid (x, T).  The histogram and the counts were cleared by the final
-// reduction.
+// Pass 1 (one block per template): which tiles to scan.  The partials give
+// every tile's fast maximum (a main tile's over the cells the main kernel
+// summed, a fix-up slot's over its recomputed cells: disjoint sets); with bt
+// the first bin in which the count of tiles (by their maxima) reaches the
+// cap, at least cap distinct cells lie in bins <= bt (those maxima), so the
+// cut never passes bt, and every cell in a bin <= bt lies in a tile whose
+// maximum is in a bin <= bt: those tiles are listed for the cell passes,
+// and bt is kept in cut[j].
+constexpr int kTileThreads = 1024;
+constexpr int kTileCache = 8;   // slots per thread whose bins stay in registers
+
+__global__ void __launch_bounds__(kTileThreads)
+k_ref_tiles(const Partial* __restrict__ parts, int64_t stride, int64_t n_tiles, int64_t fix0,
+            int64_t n_fix, const TStat* __restrict__ st, int32_t cap,
+            int32_t* __restrict__ ref_ntile, int32_t* __restrict__ ref_tile,
+            int32_t* __restrict__ cut) {
+  __shared__ int32_t h[kRefBins];
+  __shared__ int32_t s_bt, s_n;
+  const int32_t j = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = 0;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  const TStat s = st[j];
+  const Partial* pp = parts + (int64_t)j * stride;
+  const int64_t total = s.N > 0 ? n_tiles + n_fix : 0;
+  auto bin_of = [&](int64_t k) {
+    if (k >= total) return -1;
+    const Partial q = pp[k < n_tiles ? k : fix0 + (k - n_tiles)];
+    return q.nvalid > 0 ? ref_bin_of(q.max2F, s.M) : -1;
+  };
+  // one shared-memory atomic per distinct bin among a warp's lanes
+  auto count = [&](int b, unsigned mask) {
+    const unsigned peers = __match_any_sync(mask, b);
+    if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[b], __popc(peers));
+  };
+  int bins[kTileCache];
+#pragma unroll
+  for (int i = 0; i < kTileCache; ++i) {
+    bins[i] = bin_of(threadIdx.x + (int64_t)i * kTileThreads);
+    count(bins[i], 0xffffffffu);
+  }
+  for (int64_t k = threadIdx.x + (int64_t)kTileCache * kTileThreads; k < total; k += kTileThreads)
+    count(bin_of(k), __activemask());
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t cum = 0, bt = kRefBins - 1;
+    for (int k = 0; k < kRefBins; ++k) {
+      cum += h[k];
+      if (cum >= cap) {
+        bt = k;
+        break;
+      }
+    }
+    s_bt = bt;
+  }
+  __syncthreads();
+  const int32_t bt = s_bt;
+  int32_t* list = ref_tile + (int64_t)j * kRefMaxTiles;
+  auto put = [&](int64_t k, int b, unsigned mask) {
+    const bool take = b >= 0 && b <= bt;
+    const unsigned sel = __ballot_sync(mask, take);
+    if (!sel) return;
+    const int leader = __ffs(sel) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(&s_n, __popc(sel));
+    base = __shfl_sync(mask, base, leader);
+    const int32_t at = base + __popc(sel & ((1u << lane) - 1u));
+    if (take && at < kRefMaxTiles) list[at] = (int32_t)k;
+  };
+#pragma unroll
+  for (int i = 0; i < kTileCache; ++i)
+    put(threadIdx.x + (int64_t)i * kTileThreads, bins[i], 0xffffffffu);
+  for (int64_t k = threadIdx.x + (int64_t)kTileCache * kTileThreads; k < total; k += kTileThreads)
+    put(k, bin_of(k), __activemask());
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ref_ntile[j] = s_n;   // (more than kRefMaxTiles: truncated)
+    cut[j] = bt;
+  }
+}
+
+struct ScanArgs {
+  const float* map;
+  const Coef* coef;
+  int32_t shared;
+  int32_t n_t0, n_tau;
+  int64_t cells;
+  TileGeom geo;
+  int64_t n_tiles;
+  int32_t parts;   // warps per listed tile (each takes one share of its cells)
+  const int64_t* flag_list;
+  const int32_t* n_flag;
+  int32_t n_templates;
+  const TStat* st;
+  const int32_t* ref_ntile;
+  const int32_t* ref_tile;
+  int32_t* hist;
+  int32_t cap;
+  const int32_t* cut;   // [T] bt of the tile pass
+  int32_t* ref_n;
+  int32_t* ref_cell;
+};
+
+// Calls f(cell, owned) for every cell of share `part` (of A.parts) of listed
+// tile k (lanes of one warp): a main tile by its geometry, a fix-up slot by
+// its share of the fix-up list;
+// owned says whether the tile's partial summed the cell (a main tile's
+// cells of Coef.valid 1, a fix-up slot's of 3), so that no cell is taken
+// twice.
+template <typename F>
+__device__ __forceinline__ void ref_tile_cells(const ScanArgs& A, int32_t j, int64_t k,
+                                               int32_t part, int lane, F f) {
+  if (k < A.n_tiles) {
+    const TileGeom& g = A.geo;
+    const int64_t tr = g.col_major ? k % g.ntr : k / g.ntc;
+    const int64_t tc = g.col_major ? k / g.ntr : k % g.ntc;
+    const int64_t r0 = tr * g.R, c0 = tc * g.C;
+    const int64_t rows = min((int64_t)g.R, (int64_t)A.n_t0 - r0);
+    const int64_t cols = min((int64_t)g.C, (int64_t)A.n_tau - c0);
+    const int64_t n = rows * cols;
+    for (int64_t q = n * part / A.parts + lane; q < n * (part + 1) / A.parts; q += 32) {
+      const int64_t r = q / cols, cc = q - r * cols;
+      const int64_t c = (r0 + r) * A.n_tau + c0 + cc;
+      f(c, ref_valid_of(A.coef, A.shared, A.cells, j, c) == 1.0f);
+    }
+  } else {
+    const int64_t cap = A.shared ? A.cells : A.cells * A.n_templates;
+    const int64_t n = min((int64_t)*A.n_flag, cap);
+    const int64_t b = k - A.n_tiles;
+    const int64_t lo = b * n / kFixSlots, hi = (b + 1) * n / kFixSlots;
+    const int64_t m = hi - lo;
+    for (int64_t e = lo + m * part / A.parts + lane; e < lo + m * (part + 1) / A.parts; e += 32) {
+      const int64_t entry = A.flag_list[e];
+      if (!A.shared && entry / A.cells != j) continue;
+      const int64_t c = A.shared ? entry : entry % A.cells;
+      f(c, ref_valid_of(A.coef, A.shared, A.cells, j, c) == 3.0f);
+    }
+  }
+}
+
+// Passes 2 and 3 over the listed tiles' cells: the histogram (collect =
+// false), then the cut and the collection of the cells up to it (collect =
+// true).  Grid (x, T), one warp per tile.  The histogram and the counts were
+// cleared by the final reduction.
 template <bool kCollect>
-__global__ void __launch_bounds__(kRefThreads)
-k_ref_scan(const float* __restrict__ map, const Coef* __restrict__ coef, int32_t shared,
-           int64_t cells, const TStat* __restrict__ st, int32_t* __restrict__ hist, int32_t cap,
-           int32_t* __restrict__ cut, int32_t* __restrict__ ref_n,
-           int32_t* __restrict__ ref_cell) {
+__global__ void __launch_bounds__(kRefThreads) k_ref_scan(const ScanArgs A) {
   __shared__ int32_t h[kRefBins];
   __shared__ int32_t s_last;
   const int32_t j = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (kCollect) {
-    for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = hist[(int64_t)j * kRefBins + b];
+    for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = A.hist[(int64_t)j * kRefBins + b];
     __syncthreads();
-    if (threadIdx.x == 0) {
-      s_last = ref_cut_of(h, cap);
-      if (blockIdx.x == 0) cut[j] = s_last;
-    }
+    if (threadIdx.x == 0) s_last = ref_cut_of(h, A.cap, A.cut[j]);
   } else {
     for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = 0;
   }
   __syncthreads();
-  const TStat s = st[j];
+  const TStat s = A.st[j];
   const int32_t last = kCollect ? s_last : kRefBins - 1;
+  const int32_t nt = min(A.ref_ntile[j], kRefMaxTiles);
   if (s.N > 0 && last >= 0) {
-    const float* mp = map + (int64_t)j * cells;
-    const int64_t span = (int64_t)kRefThreads * kRefUnroll;
-    for (int64_t base = (int64_t)blockIdx.x * span; base < cells; base += (int64_t)gridDim.x * span) {
-      float v[kRefUnroll];
-#pragma unroll
-      for (int u = 0; u < kRefUnroll; ++u) {
-        const int64_t c = base + u * kRefThreads + threadIdx.x;
-        v[u] = c < cells ? mp[c] : -1.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < kRefUnroll; ++u) {
-        const int64_t c = base + u * kRefThreads + threadIdx.x;
-        int b = ref_bin_of(v[u], s.M);
-        if (b > last || c >= cells || (b >= 0 && !ref_valid(coef, shared, cells, j, c))) b = -1;
+    const float* mp = A.map + (int64_t)j * A.cells;
+    const int64_t items = (int64_t)nt * A.parts;
+    for (int64_t it = blockIdx.x * (kRefThreads / 32) + warp; it < items;
+         it += gridDim.x * (kRefThreads / 32)) {
+      const int64_t k = it / A.parts;
+      ref_tile_cells(A, j, A.ref_tile[(int64_t)j * kRefMaxTiles + k], (int32_t)(it - k * A.parts),
+                     lane, [&](int64_t c, bool owned) {
+        int b = owned ? ref_bin_of(mp[c], s.M) : -1;
+        if (b > last) b = -1;
         if (kCollect) {
           if (b >= 0) {
-            const int32_t slot = atomicAdd(ref_n + j, 1);
-            if (slot < kRefMaxCells) ref_cell[(int64_t)j * kRefMaxCells + slot] = (int32_t)c;
+            const int32_t slot = atomicAdd(A.ref_n + j, 1);
+            if (slot < kRefMaxCells) A.ref_cell[(int64_t)j * kRefMaxCells + slot] = (int32_t)c;
           }
         } else {
-          // one shared-memory atomic per distinct bin of the warp (noise maps
-          // put most cells of the window in a few bins)
-          const unsigned peers = __match_any_sync(0xffffffffu, b);
-          if (b >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
-            atomicAdd(&h[b], __popc(peers));
+          // one shared-memory atomic per distinct bin among the lanes here
+          // (noise maps put most cells of the window in a few bins)
+          const unsigned peers = __match_any_sync(__activemask(), b);
+          if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[b], __popc(peers));
         }
-      }
+      });
     }
   }
   if (!kCollect) {
     __syncthreads();
     for (int b = threadIdx.x; b < kRefBins; b += blockDim.x)
-      if (h[b]) atomicAdd(hist + (int64_t)j * kRefBins + b, h[b]);
+      if (h[b]) atomicAdd(A.hist + (int64_t)j * kRefBins + b, h[b]);
   }
 }
 
@@ -254,7 +390,8 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
 // order in which the cells were collected (<= 4096 terms: no overflow,
 // relative error < 1e-12).
 __global__ void __launch_bounds__(32)
-k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ cut,
+k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ hist,
+            const int32_t* __restrict__ cut, int32_t cap, const int32_t* __restrict__ ref_ntile,
             const int32_t* __restrict__ ref_n, const int32_t* __restrict__ ref_cell,
             const float* __restrict__ ref_fast, const double* __restrict__ ref_val, int32_t n_tau,
             double log_prior, double tol, fmap_summary* __restrict__ out) {
@@ -294,22 +431,24 @@ k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ cut,
   if (lane != 0) return;
   const double Sp = exp(0.5 * (M - mx)) * fmax(s.S - (double)sub / kFix, 0.0) + (double)add / kFix;
   const long long Np = s.N - n + nv;
-  const int32_t b = cut[j];
+  const int32_t b = ref_cut_of(hist + (int64_t)j * kRefBins, cap, cut[j]);
   const double depth = b + 1 >= kRefBins ? (double)kRefWindow
                                          : (double)(b + 1) * (double)kRefWindow / kRefBins;
   fmap_summary o;
   o.max2F = (float)mx;
   o.m = arg / n_tau;
   o.n = arg % n_tau;
+  const bool complete = ref_ntile[j] <= kRefMaxTiles;   // every candidate tile scanned
   o.flags = (int32_t)FMAP_SUMMARY_REFINED |
-            (depth > 2.0 * tol * fmax(mx, 1.0) ? (int32_t)FMAP_SUMMARY_ARGMAX_EXACT : 0);
+            (complete && depth > 2.0 * tol * fmax(mx, 1.0) ? (int32_t)FMAP_SUMMARY_ARGMAX_EXACT
+                                                            : 0);
   o.logB = 0.5 * mx + log(Sp) - log((double)Np) + log_prior;
   o.n_valid = Np;
   out[j] = o;
 }
 
 cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
-                          fmap_summary* d_summary, cudaStream_t s) {
+                          fmap_summary* d_summary, int64_t n_tiles, cudaStream_t s) {
   const int32_t cap = refine_cells_of(p);
   const fmap_grid& g = p->grid;
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
@@ -318,15 +457,40 @@ cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
     return cudaSuccess;
   Workspace& w = p->ws;
   const int32_t sh = a->shared_antenna ? 1 : 0;
-  const int64_t span = (int64_t)kRefThreads * kRefUnroll;
-  const int64_t want = std::max<int64_t>(1, ((int64_t)p->n_sm * 8 + T - 1) / T);
-  const unsigned gx = (unsigned)std::min<int64_t>((cells + span - 1) / span, want);
-  const dim3 grid(gx, (unsigned)T);
-  // (the final reduction cleared the histogram and the candidate counts)
-  k_ref_scan<false><<<grid, kRefThreads, 0, s>>>(d_2F, w.coef, sh, cells, w.tstat, w.ref_hist,
-                                                 cap, nullptr, nullptr, nullptr);
-  k_ref_scan<true><<<grid, kRefThreads, 0, s>>>(d_2F, w.coef, sh, cells, w.tstat, w.ref_hist,
-                                                cap, w.ref_bin, w.ref_n, w.ref_cell);
+  // (the final reduction cleared the cell histogram and the candidate counts)
+  k_ref_tiles<<<T, kTileThreads, 0, s>>>(w.partials, p->part_stride, n_tiles, p->n_tiles, kFixSlots,
+                                        w.tstat, cap, w.ref_ntile, w.ref_tile, w.ref_bin);
+  ScanArgs S;
+  S.map = d_2F;
+  S.coef = w.coef;
+  S.shared = sh;
+  S.n_t0 = g.n_t0;
+  S.n_tau = g.n_tau;
+  S.cells = cells;
+  S.geo = p->tiles;
+  S.n_tiles = n_tiles;
+  S.flag_list = w.flag_list;
+  S.n_flag = w.n_flag;
+  S.n_templates = T;
+  S.st = w.tstat;
+  S.ref_ntile = w.ref_ntile;
+  S.ref_tile = w.ref_tile;
+  S.hist = w.ref_hist;
+  S.cap = cap;
+  S.cut = w.ref_bin;
+  S.ref_n = w.ref_n;
+  S.ref_cell = w.ref_cell;
+  // a warp per share of about kScanShare cells of a listed tile (about cap
+  // tiles per template), at least a few blocks over the GPU
+  const int64_t tile_cells = (int64_t)S.geo.R * S.geo.C;
+  S.parts = (int32_t)std::min<int64_t>(std::max<int64_t>((tile_cells + kScanShare - 1) / kScanShare, 1),
+                                       1024);
+  const int wpb = kRefThreads / 32;
+  const unsigned gx = (unsigned)std::max<int64_t>(
+      (2 * (int64_t)cap * S.parts + wpb - 1) / wpb, ((int64_t)p->n_sm * 4 + T - 1) / T);
+  const dim3 grid(std::min<unsigned>(gx, 4096u), (unsigned)T);
+  k_ref_scan<false><<<grid, kRefThreads, 0, s>>>(S);
+  k_ref_scan<true><<<grid, kRefThreads, 0, s>>>(S);
   RefArgs A;
   A.rel_t = w.rel_t;
   A.t_base = w.t_base;
@@ -346,11 +510,11 @@ cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
   A.ref_cell = w.ref_cell;
   A.ref_fast = w.ref_fast;
   A.ref_val = w.ref_val;
-  const int wpb = kRefThreads / 32;
   k_ref_cells<<<dim3((unsigned)((cap + wpb - 1) / wpb), (unsigned)T), kRefThreads, 0, s>>>(A);
-  k_ref_final<<<T, 32, 0, s>>>(w.tstat, w.ref_bin, w.ref_n, w.ref_cell, w.ref_fast, w.ref_val,
-                               g.n_tau, p->log_prior, fast_tol(p), d_summary);
-  p->launches += 4;
+  k_ref_final<<<T, 32, 0, s>>>(w.tstat, w.ref_hist, w.ref_bin, cap, w.ref_ntile, w.ref_n,
+                               w.ref_cell, w.ref_fast, w.ref_val, g.n_tau, p->log_prior,
+                               fast_tol(p), d_summary);
+  p->launches += 5;
   return cudaGetLastError();
 }
 
