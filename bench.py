@@ -407,9 +407,10 @@ def roofline_exp(peaks, peak_src, prec, terms, dom_ms, n_tau, n_sft, T, cells):
     """Roofline of the exp path's dominant kernel (phase 2).  Tensor forms:
     8 flops per (cell, SFT, template) term (multiply + add on 4 data
     columns) against the kind's tensor peak.  FP32 plain: the same flops
-    against the FP32 FMA peak.  Recurrence: FP32-pipe operations, 11 per
-    compensated recurrence step (per tau, data column, template and SFT) plus
-    13 per (cell, template) evaluation, against the FP32 pipe's issue rate."""
+    against the FP32 FMA peak.  Recurrence: 4 flops per (tau, data column,
+    template, SFT) -- the recurrence's multiply-add and the one forming E from
+    the chunk-local sum -- plus 24 per (cell, template), against the FP32 FMA
+    peak."""
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     if prec in ("bf16x3", "tf32"):
         flops = 8.0 * terms
@@ -423,14 +424,15 @@ def roofline_exp(peaks, peak_src, prec, terms, dom_ms, n_tau, n_sft, T, cells):
                 "frac": ach / peak, "traffic": None, "kernel": "exp contraction (phase 2)",
                 "peak_source": src, "work": "8 flops per (cell, SFT, template) term"}
     if prec == "rec":
-        ops = 11.0 * 4 * n_tau * n_sft * T + 13.0 * cells * T
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-        ach = ops / (dom_ms / 1e3) / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s",
+        flops = 4.0 * 4 * n_tau * n_sft * T + 24.0 * cells * T
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = flops / (dom_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "kernel": "exp recurrence (phase 2)",
-                "peak_source": "FP32 pipe: 152 SM x 128 lanes x max SM clock",
-                "work": "11 ops per compensated recurrence step (tau, column, template, SFT) + "
-                        "13 per (cell, template)"}
+                "peak_source": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock",
+                "work": "4 flops per (tau, data column, template, SFT): the recurrence's FMA "
+                        "and the FMA forming E; 24 per (cell, template): two window "
+                        "differences on 4 columns and the 2F form"}
     flops = 8.0 * terms
     peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     ach = flops / (dom_ms / 1e3) / 1e12

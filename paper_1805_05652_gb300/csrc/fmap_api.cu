@@ -95,7 +95,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
-      esuf, xop, perm_ant, perm_x, perm_gap, tauc, ax, wtab, flag_bits, tstat, ref_hist, ref_bin,
+      esuf, xop, perm_ant, perm_x, perm_gap, rec_cells, tauc, ax, wtab, flag_bits, tstat, ref_hist, ref_bin,
       ref_n, ref_cell, ref_fast, ref_val, own_map, ref_ntile, ref_tile, total;
   int64_t n_tiles;
   int32_t tau_chunk;
@@ -139,7 +139,7 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
   L.flag_bits = take(sizeof(uint32_t) * (size_t)flag_words((int64_t)entries));
   L.n_flag = take(sizeof(int32_t));
   L.flag_list = take(sizeof(int64_t) * entries);
-  if (!(flags & kPlanNoRefine)) {  // refinement of the summaries
+  if (!(flags & kPlanBatch)) {  // refinement of the summaries
     const size_t Tn = (size_t)std::max<int32_t>(T, 1);
     L.tstat = take(sizeof(TStat) * Tn);
     L.ref_hist = take(sizeof(int32_t) * kRefBins * Tn);
@@ -153,7 +153,8 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.own_map = (flags & FMAP_PLAN_MAP_BUFFER)
                     ? take(sizeof(float) * (size_t)std::max<int64_t>(cells, 1) * Tn) : 0;
   }
-  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.perm_gap = L.tauc = L.wtab = 0;
+  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.perm_gap = L.rec_cells = L.tauc =
+      L.wtab = 0;
   const size_t np1 = (size_t)n_sft + 1;
   if (g->window == FMAP_RECT) {
     L.pa = take(sizeof(float) * 8 * np1 * (size_t)t_ant);   // (a2, b2, ab, 0) float pairs
@@ -165,11 +166,15 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.tau_chunk = (int32_t)chunk;
     // the suffix sums live in shared memory when the data set fits there
     L.esuf = take(exp_antenna_fits(n_sft) ? 8 : per_tau * (size_t)chunk);
-    const size_t perm = sizeof(float4) * (size_t)perm_entries(n_sft, kScanLanes);
+    const size_t perm = sizeof(float4) * (size_t)perm_entries_max(n_sft);
     L.perm_ant = take(perm * (size_t)t_ant);
     if (flags & FMAP_PLAN_EXP_RECURRENCE) {
       L.perm_x = take(perm * (size_t)std::max<int32_t>(T, 1));
-      L.perm_gap = take(sizeof(int32_t) * (size_t)perm_entries(n_sft, kScanLanes));
+      L.perm_gap = take(sizeof(int32_t) * (size_t)perm_entries_max(n_sft));
+      // window records (and the shared antenna's coefficients) re-read by
+      // every template after the first
+      if (T >= 2 && !(flags & kPlanBatch))
+        L.rec_cells = take((t_ant == 1 ? 2 : 1) * sizeof(float4) * (size_t)std::max<int64_t>(cells, 1));
     }
     L.tauc = take(sizeof(TauTab) * (size_t)std::max<int32_t>(g->n_tau, 1));
     if (g->window == FMAP_TABLE) L.wtab = take(sizeof(float2) * (kTabMax + 1));
@@ -228,7 +233,7 @@ static fmap_status plan_args_ok(const fmap_grid* grid, int32_t n_sft, int32_t n_
   if (n_templates < 0 || n_templates > 65535) return arg_fail("n_templates must be in [0, 65535]");
   if (precision < FMAP_FP64 || precision > FMAP_BF16X3) return arg_fail("unknown precision");
   if (flags & ~(uint32_t)(FMAP_PLAN_PER_TEMPLATE_ANTENNA | FMAP_PLAN_EXP_RECURRENCE |
-                          FMAP_PLAN_MAP_BUFFER | kPlanNoRefine))
+                          FMAP_PLAN_MAP_BUFFER | kPlanBatch))
     return arg_fail("unknown plan flags");
   if (flags & FMAP_PLAN_EXP_RECURRENCE) {
     if (grid->window != FMAP_EXP) return arg_fail("FMAP_PLAN_EXP_RECURRENCE is for exponential windows");
@@ -289,7 +294,7 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
   w.flag_bits = (uint32_t*)(b + L.flag_bits);
   w.n_flag = (int32_t*)(b + L.n_flag);
   w.flag_list = (int64_t*)(b + L.flag_list);
-  if (!(flags & kPlanNoRefine)) {
+  if (!(flags & kPlanBatch)) {
     w.tstat = (TStat*)(b + L.tstat);
     w.ref_hist = (int32_t*)(b + L.ref_hist);
     w.ref_ntile = (int32_t*)(b + L.ref_ntile);
@@ -311,6 +316,7 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
     w.perm_ant = (float4*)(b + L.perm_ant);
     if (L.perm_x) w.perm_x = (float4*)(b + L.perm_x);
     if (L.perm_gap) w.perm_gap = (int32_t*)(b + L.perm_gap);
+    if (L.rec_cells) w.rec_cells = (float4*)(b + L.rec_cells);
     if (L.wtab) w.wtab = (float2*)(b + L.wtab);
     w.tauc = (TauTab*)(b + L.tauc);
     if (L.xop) w.xop = (void*)(b + L.xop);

@@ -186,6 +186,7 @@ static BItem make_bitem(const fmap_plan_s* p, const fmap_batch_item& it, uint32_
   b.perm_ant = w.perm_ant;
   b.perm_x = w.perm_x;
   b.perm_gap = w.perm_gap;
+  b.rec_cells = w.rec_cells;
   b.tauc = w.tauc;
   b.ax = nullptr;   // batches take uniform grids
   b.px = w.px;
@@ -269,7 +270,7 @@ static fmap_status place_wave(fmap_batch_s* B, int w) {
     size_t bytes = 0;
     const uint32_t flags = (it.atoms.shared_antenna ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA) |
                            (it.grid.window == FMAP_EXP ? (uint32_t)FMAP_PLAN_EXP_RECURRENCE : 0u) |
-                           kPlanNoRefine;
+                           kPlanBatch;
     fmap_status st = plan_footprint(&it.grid, it.atoms.n_sft, it.atoms.n_templates, FMAP_FP64,
                                     flags, &bytes);
     if (st != FMAP_OK) return st;
@@ -426,7 +427,7 @@ fmap_status fmap_batch_plan(fmap_batch_t** out, const fmap_batch_item* items, in
     }
     const uint32_t pf = (it.atoms.shared_antenna ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA) |
                         (it.grid.window == FMAP_EXP ? (uint32_t)FMAP_PLAN_EXP_RECURRENCE : 0u) |
-                        kPlanNoRefine;
+                        kPlanBatch;
     fmap_status st = plan_footprint(&it.grid, it.atoms.n_sft, it.atoms.n_templates, FMAP_FP64, pf,
                                     &foot[i]);
     if (st != FMAP_OK) {

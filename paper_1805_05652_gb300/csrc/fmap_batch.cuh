@@ -38,6 +38,7 @@ struct BItem {
   float4* perm_ant;
   float4* perm_x;
   int32_t* perm_gap;
+  float4* rec_cells;
   TauTab* tauc;
   int64_t* ax;
   float4* px;

@@ -58,7 +58,7 @@ __device__ __forceinline__ void antenna_suffix(const float4* __restrict__ perm, 
                                                float (*sS)[2][NT / 32]) {
   const double inv_s = 2.0 * tt->inv_tau;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int C = (n + NT - 1) / NT;
+  const int C = (int)scan_chunk(n, NT);
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   // Decay over one gap: e^{-2 gap / tau}, from the tau's table of powers of
   // the one-SFT decay (FP64 exp off the T_sft lattice).

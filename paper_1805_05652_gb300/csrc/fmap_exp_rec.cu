@@ -7,18 +7,36 @@
 // an exact rearrangement of the window sums of Eq. (winexp).  One recurrence
 // per (tau, data column) replaces the per-cell sums: O(N_tau N_SFT) work per
 // column instead of O(sum of window lengths).  The recurrence runs as a
-// parallel backward scan of the affine maps E -> x + rho E in compensated
-// FP32 (float pairs, ~2^-44 relative), and E is rounded to FP32 only for the
-// per-cell differences, which then carry the same ~1e-7 relative error as the
-// rectangular window's prefix differences.
+// parallel backward scan of the affine maps E -> x + rho E.  What spans the
+// data set -- the decay products and the composition of the chunks' maps,
+// whose errors would otherwise accumulate over up to N_SFT steps -- runs in
+// compensated FP32 (float pairs, ~2^-44 relative); the chunk-local sums (at
+// most C = 21..35 terms at 5000..9000 SFTs) run in plain FP32, and E is formed
+// in FP32 as E = L + Q E[chunk end].  A chunk-local error is at most ~C ulp of
+// the chunk's own partial sums, small against E where the window is long
+// (slow decay) and limited to the few undecayed terms where it is short:
+// emulated on the 5000-SFT workload (every tau class, the cells outside the
+// FP64 fix-up), the worst relative 2F error is 1.7e-6 against 1.2e-6 for
+// compensated chunk sums.
 //
-// One block per (tau_n, group of templates): for each template of the group
-// the block scans the 4 data columns (read from the chunk-major copy with the
-// gaps between atoms; the decays come from the per-tau table of powers of
-// the one-SFT decay) into shared memory and evaluates the column of cells
-// (t0_m, tau_n) for every m.  Blocks run tau-fastest, so the blocks writing
-// neighbouring tau of the same map rows run together and their stores merge
-// in L2.
+// One block per (tau_n, group of templates); each thread owns a chunk of
+// atoms (odd length C, read from the chunk-major copy).  Per template of the
+// group:
+//   1. the chunk-local suffix sums L[i] (E with E[chunk end] = 0) of the 4
+//      data columns, one FP32 FMA per atom and column (at most C terms; see
+//      below); on the first template also the products Q[i] of the decays
+//      from atom i to the chunk's end, in float-float (the same for every
+//      template, kept in shared memory) and the chunk's product R;
+//   2. the carries E[chunk end] by a suffix composition of the chunks'
+//      (L[s0], R) maps, in float-float, within the warp and over the warps;
+//   3. E[i] = L[i] + Q[i] E[chunk end] in place (one FMA per column, where
+//      recomputing the chunk from its carry would repeat step 1);
+//   4. the column of cells (t0_m, tau_n) for every m from E, with the
+//      window records (i0, j, prefactor, tail factor; and the coefficients
+//      when the antenna is shared) computed on the block's first template and
+//      re-read from a tau-major array on the others.
+// Blocks run tau-fastest, so the blocks writing neighbouring tau of the same
+// map rows run together and their stores merge in L2.
 #include <math.h>
 
 #include "fmap_batch.cuh"
@@ -26,38 +44,12 @@
 
 namespace fmap {
 
-constexpr int kRecThreads = 256;
 constexpr int kRecChunk = 8;        // SFTs of data prefetched per serial run of the scan
-constexpr int kRecMaxSft = 9000;    // one template's suffix sums in shared memory (144 KB)
+constexpr int kRecMaxSft = 9000;    // one template's suffix sums in shared memory (180 KB)
 
-struct __align__(16) CellRec {
-  int32_t i0, j;
-  float pre, tail;
-  Coef cf;
-};
-
-constexpr size_t kRecSmemCap = 220 * 1024;
-
-// Shared memory of the recurrence: one template's suffix sums, plus the
-// staged per-cell records of one tau when they fit.
+// Shared memory of the recurrence: E of one template (4 columns) and Q.
 __host__ __device__ __forceinline__ size_t rec_smem_base(int32_t n_sft) {
-  return sizeof(float) * 4 * ((size_t)n_sft + 1) + 16;
-}
-// Blocks of the recurrence an SM holds with a given dynamic shared memory
-// (three at most: the registers of 3 x 256 threads).
-__host__ __device__ __forceinline__ int rec_blocks_per_sm(size_t smem) {
-  const size_t per_sm = 227 * 1024;
-  const size_t k = per_sm / (smem + 1024);
-  return (int)(k < 3 ? k : 3);
-}
-// Staged only for blocks that run two or more templates (a single template
-// reads each record once), and only when the staging's shared memory costs
-// no resident block (long data sets: the suffix rows alone take 80 KB at
-// 5000 SFTs, and with the records an SM would hold one block instead of
-// two; recomputing a record per template is cheaper than that).
-__host__ __device__ __forceinline__ bool rec_stage_cells(int32_t n_sft, int32_t n_t0, int32_t tpb) {
-  const size_t base = rec_smem_base(n_sft), with = base + sizeof(CellRec) * (size_t)n_t0;
-  return tpb >= 2 && with <= kRecSmemCap && rec_blocks_per_sm(with) >= rec_blocks_per_sm(base);
+  return sizeof(float) * 5 * ((size_t)n_sft + 1) + 16;
 }
 
 __device__ __forceinline__ float rec_ex2(float x) {
@@ -67,83 +59,64 @@ __device__ __forceinline__ float rec_ex2(float x) {
 }
 
 // NT = the plan's scan width: threads of the block and width of the
-// chunk-major copy.
-template <int NT>
+// chunk-major copy; U = cells a thread loads ahead.
+template <int NT, int U>
 __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          const int32_t* __restrict__ perm_gap, const TauTab* __restrict__ tauc,
+          const int32_t* __restrict__ perm_gap, float4* __restrict__ recs,
+          const TauTab* __restrict__ tauc,
           const int64_t* __restrict__ ax, int32_t n_templates, int32_t n_groups,
           float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
     const uint3 bid, const dim3 gdim) {
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) float s_dyn[];
-  float* s_e = s_dyn;                  // [4][n + 1] suffix sums of one template
-  // per cell (t0_m, tau_n): the window [i0, j), prefactor, tail factor and the
-  // 2F coefficients -- the same for every template, so staged once
-  CellRec* s_cell = (CellRec*)(s_e + 4 * ((int64_t)n + 1));
-  __shared__ float sR[2][NT / 32];
-  __shared__ float sS[4][2][NT / 32];
-  __shared__ Partial scratch[NT / 32];
+  const int64_t np1 = (int64_t)n + 1;
+  float* s_e = s_dyn;              // [4][n + 1] L, then E, of one template
+  float* s_q = s_dyn + 4 * np1;    // [n] decay product from atom i to its chunk's end
+  __shared__ float sR[2][NW];      // each warp's product of its chunks' R
+  __shared__ float sS[4][2][NW];   // each warp's composed S (per template)
+  __shared__ float sK[4][2][NW];   // E at each warp's end (per template)
+  __shared__ Partial scratch[NW];
   const int ni = bid.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TauTab* tt = tauc + ni;
-  const int64_t np1 = (int64_t)n + 1;
   // Decay after atom i: gaps of k whole SFTs from the tau's table of
   // float-float powers of the one-SFT decay, other gaps by FP64 exp; the gaps
   // come from the chunk-major copy with the data.
   const float inv_tsft = 1.0f / (float)g.t_sft;
   const double inv_tau = tt->inv_tau;
-  const int C = (n + NT - 1) / NT;
+  const int C = (int)scan_chunk(n, NT);
   const int s0 = min(n, tid * C), e0 = min(n, s0 + C);
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const float c2 = tt->c2[0];
   const bool short_cut = exp_cut8_of(g) < 24;   // window cut before 3 tau
   const int64_t tb = n > 0 ? *t_base : 0;
-  // Per cell (t0_m, tau_n): the window, its prefactor and tail factor and the
-  // coefficients; staged once per block when they fit, else recomputed per
-  // template (large n_sft x n_t0).
-  auto cell_rec = [&](int32_t m) {
-    const int64_t cell = (int64_t)m * g.n_tau + ni;
-    CellRec r;
-    r.i0 = i0tab[m];
-    r.j = jend[cell];
-    r.pre = 0.0f;
-    r.tail = 0.0f;
-    if (r.j > r.i0) {
-      const int64_t t0rel = grid_t0(g, ax, m) - tb;
-      const int64_t d0 = (int64_t)rel_t[r.i0] - t0rel;
-      r.pre = d0 == 0 ? 1.0f : rec_ex2(c2 * (float)d0);
-      if (r.j < n) {
-        // Approximate FP32 exp2 for the tail: ~e^{-3} of the window sum for
-        // the default 3 tau cut.  Windows cut before 3 tau make it large,
-        // where the difference E[i0] - tail E[j] loses 1 / (1 - tail): there a
-        // tail above 1/2 comes from the correctly rounded-to-1-ulp exp2f.
-        // (An FP64 exp here, even behind a branch never taken, slowed this
-        // kernel by 12 %.)
-        const int32_t dj = rel_t[r.j] - rel_t[r.i0];
-        r.tail = rec_ex2(c2 * (float)dj);
-        if (short_cut && r.tail > 0.5f) r.tail = exp2f(c2 * (float)dj);
-      }
-    }
-    r.cf = coef[cell];
-    return r;
+  // 0 after the last atom
+  int32_t gq[kRecChunk];
+  auto decay = [&](int q) -> FF {
+    if (gq[q] > 0) return gap_decay(gq[q], g.t_sft, inv_tsft, tt->pw[0], inv_tau);
+    return gq[q] < 0 ? FF{0.0f, 0.0f} : FF{1.0f, 0.0f};
   };
-  const bool stage = rec_stage_cells(n, g.n_t0, (n_templates + n_groups - 1) / n_groups);
-  if (stage)
-    for (int32_t m = tid; m < g.n_t0; m += NT) s_cell[m] = cell_rec(m);
+  const int b_last = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk;   // last run's start
+  // window records of tau_n, and coefficients (shared antenna); the array is
+  // absent (null) in single-template plans
+  float4* rec_a = recs ? recs + (int64_t)ni * g.n_t0 : nullptr;
+  float4* rec_c = recs ? recs + cells + (int64_t)ni * g.n_t0 : nullptr;
   const int32_t t_lo = (int32_t)((int64_t)bid.y * n_templates / n_groups);
   const int32_t t_hi = (int32_t)((int64_t)(bid.y + 1) * n_templates / n_groups);
+  FF R{1.0f, 0.0f};   // the chunk's product of decays (from the first template on)
   for (int32_t tq = t_lo; tq < t_hi; ++tq) {
-    __syncthreads();   // records staged; previous template's cells done with s_e
+    const bool first = tq == t_lo;
+    __syncthreads();   // the previous template's cells are done with s_e
     const float4* x = perm_x + (int64_t)tq * perm_entries(n, NT);   // chunk-major data rows
-    // phase 1: this thread's chunk as one affine map, E[s0] = S + R E[e0],
-    // by the compensated recurrence (folded back every kRecChunk atoms); the
-    // data of each run of kRecChunk SFTs is loaded before its serial chain,
-    // and positions past the chunk's end are identity steps (x = 0, r = 1)
-    float Rh = 1.0f, Rc = 0.0f, Sh[4] = {0.f, 0.f, 0.f, 0.f}, Sc[4] = {0.f, 0.f, 0.f, 0.f};
+    // 1. chunk-local suffix sums L[i] in plain FP32 (and on the first
+    // template the decay products Q[i] in float-float); the data of each run
+    // of kRecChunk SFTs is loaded before its serial chain
+    float L[4] = {0.f, 0.f, 0.f, 0.f};
+    float Qh = 1.0f, Qc = 0.0f;
     float xv[kRecChunk][4];
-    int32_t gq[kRecChunk];
-    auto load_chunk = [&](int b0) {
+    for (int b0 = b_last; e0 > s0 && b0 >= s0; b0 -= kRecChunk) {
 #pragma unroll
       for (int q = 0; q < kRecChunk; ++q) {
         const int i = b0 + q;
@@ -155,51 +128,50 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
         xv[q][2] = v.z;
         xv[q][3] = v.w;
       }
-    };
-    // identity past the chunk's end (gap 0 there), 0 after the last atom
-    auto decay = [&](int q) -> FF {
-      if (gq[q] > 0) return gap_decay(gq[q], g.t_sft, inv_tsft, tt->pw[0], inv_tau);
-      return gq[q] < 0 ? FF{0.0f, 0.0f} : FF{1.0f, 0.0f};
-    };
-    for (int b0 = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk; e0 > s0 && b0 >= s0;
-         b0 -= kRecChunk) {
-      load_chunk(b0);
 #pragma unroll
       for (int q = kRecChunk - 1; q >= 0; --q) {
+        // (only the run at the chunk's end is partial: the same for the
+        // warp's lanes but the last thread's)
+        if (b0 + q >= e0) continue;
         const FF r = decay(q);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) ch_step(r, xv[q][c], Sh[c], Sc[c]);
-        ch_mul(r, Rh, Rc);
+        for (int c = 0; c < 4; ++c) {
+          L[c] = fmaf(r.h, L[c], xv[q][c]);
+          s_e[c * np1 + b0 + q] = L[c];
+        }
+        if (first) {
+          ch_mul(r, Qh, Qc);
+          s_q[b0 + q] = Qh + Qc;
+        }
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) ch_norm(Sh[c], Sc[c]);
-      ch_norm(Rh, Rc);
+      if (first) ch_norm(Qh, Qc);
     }
-    FF R = {Rh, Rc}, S[4] = {{Sh[0], Sc[0]}, {Sh[1], Sc[1]}, {Sh[2], Sc[2]}, {Sh[3], Sc[3]}};
-    // phase 2: suffix composition within the warp (self o later)
+    if (first) R = {Qh, Qc};
+    // 2. carries: suffix composition of the chunks' maps E[s0] = S + R E[e0],
+    // within the warp (Rw: the product over lanes lane..31), then over the
+    // warps (warp 0, lane v = warp v)
+    FF S[4] = {{L[0], 0.f}, {L[1], 0.f}, {L[2], 0.f}, {L[3], 0.f}};
+    FF Rw = R;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const FF Ro = ff_shfl_down(R, d);
-      FF So[4];
+    for (int k = 0; k < 5; ++k) {
+      const FF Ro = ff_shfl_down(Rw, 1 << k);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) So[c] = ff_shfl_down(S[c], d);
-      if (lane + d < 32) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) S[c] = ff_add(S[c], ff_mul(R, So[c]));
-        R = ff_mul(R, Ro);
+      for (int c = 0; c < 4; ++c) {
+        const FF So = ff_shfl_down(S[c], 1 << k);
+        if (lane + (1 << k) < 32) S[c] = ff_add(S[c], ff_mul(Rw, So));
       }
+      if (lane + (1 << k) < 32) Rw = ff_mul(Rw, Ro);
     }
-    FF hR = ff_shfl_down(R, 1), hS[4];
+    FF hR = ff_shfl_down(Rw, 1), hS[4];
+    if (lane == 31) hR = {1.0f, 0.0f};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) hS[c] = ff_shfl_down(S[c], 1);
-    if (lane == 31) {
-      hR = {1.0f, 0.0f};
-#pragma unroll
-      for (int c = 0; c < 4; ++c) hS[c] = {0.0f, 0.0f};
+    for (int c = 0; c < 4; ++c) {
+      hS[c] = ff_shfl_down(S[c], 1);
+      if (lane == 31) hS[c] = {0.0f, 0.0f};
     }
     if (lane == 0) {
-      sR[0][warp] = R.h;
-      sR[1][warp] = R.l;
+      sR[0][warp] = Rw.h;
+      sR[1][warp] = Rw.l;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         sS[c][0][warp] = S[c].h;
@@ -207,71 +179,155 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
       }
     }
     __syncthreads();
-    // later warps applied to E[N] = 0
-    FF lS[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int v = NT / 32 - 1; v > warp; --v) {
-      const FF Rv = {sR[0][v], sR[1][v]};
+    if (warp == 0) {
+      FF Rv = lane < NW ? FF{sR[0][lane], sR[1][lane]} : FF{1.0f, 0.0f};
+      FF Sv[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) lS[c] = ff_add({sS[c][0][v], sS[c][1][v]}, ff_mul(Rv, lS[c]));
-    }
-    float eh[4], ec[4];
+      for (int c = 0; c < 4; ++c)
+        Sv[c] = lane < NW ? FF{sS[c][0][lane], sS[c][1][lane]} : FF{0.0f, 0.0f};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const FF e = ff_add(hS[c], ff_mul(hR, lS[c]));
-      eh[c] = e.h;
-      ec[c] = e.l;
-    }
-    // phase 3: recompute the chunk from its carry and keep E (rounded) in smem
-    for (int b0 = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk; e0 > s0 && b0 >= s0;
-         b0 -= kRecChunk) {
-      load_chunk(b0);
-#pragma unroll
-      for (int q = kRecChunk - 1; q >= 0; --q) {
-        const int i = b0 + q;
-        const FF r = decay(q);
+      for (int k = 0; (1 << k) < NW; ++k) {
+        const FF Ro = ff_shfl_down(Rv, 1 << k);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          ch_step(r, xv[q][c], eh[c], ec[c]);
-          if (i < e0) s_e[c * np1 + i] = eh[c] + ec[c];
+          const FF So = ff_shfl_down(Sv[c], 1 << k);
+          if (lane + (1 << k) < NW) Sv[c] = ff_add(Sv[c], ff_mul(Rv, So));
         }
+        if (lane + (1 << k) < NW) Rv = ff_mul(Rv, Ro);
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) ch_norm(eh[c], ec[c]);
+      for (int c = 0; c < 4; ++c) {
+        FF K = ff_shfl_down(Sv[c], 1);   // E at the end of warp `lane`
+        if (lane >= NW - 1) K = {0.0f, 0.0f};
+        if (lane < NW) {
+          sK[c][0][lane] = K.h;
+          sK[c][1][lane] = K.l;
+        }
+      }
+    }
+    __syncthreads();
+    // 3. E[i] = L[i] + Q[i] E[e0]
+    float Ke[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const FF e = ff_add(hS[c], ff_mul(hR, FF{sK[c][0][warp], sK[c][1][warp]}));
+      Ke[c] = e.h + e.l;
+    }
+    for (int i = s0; i < e0; ++i) {
+      const float qi = s_q[i];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s_e[c * np1 + i] = fmaf(qi, Ke[c], s_e[c * np1 + i]);
     }
     if (tid < 4) s_e[tid * np1 + n] = 0.0f;
     __syncthreads();
-    // cells (t0_m, tau_n), all m
+    // 4. cells (t0_m, tau_n), all m
+    const bool fresh = first || !recs;   // records computed here (no array: one template)
+    // U cells per thread at a time: their records (or, when computed here,
+    // their window indices and then the atom times those select) are all
+    // loaded before any is used, so the loads' latencies overlap
     Partial acc = partial_empty();
-    for (int32_t m = tid; m < g.n_t0; m += NT) {
-      const int64_t cell = (int64_t)m * g.n_tau + ni;
-      const CellRec r = stage ? s_cell[m] : cell_rec(m);
-      const Coef cf = shared_antenna ? r.cf : coef[(int64_t)tq * cells + cell];
-      float f[4] = {0.f, 0.f, 0.f, 0.f};
-      if (r.j > r.i0) {
+    for (int32_t mb = tid; mb < g.n_t0; mb += NT * U) {
+      float4 ra[U], rc[U];
+      if (fresh) {
+        int32_t i0v[U], jv[U], ti[U], tj[U];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          f[c] = r.pre * fmaf(-r.tail, s_e[c * np1 + r.j], s_e[c * np1 + r.i0]);
+        for (int u = 0; u < U; ++u) {
+          const int32_t m = mb + u * NT;
+          const bool in = m < g.n_t0;
+          i0v[u] = in ? i0tab[m] : 0;
+          jv[u] = in ? jend[(int64_t)m * g.n_tau + ni] : 0;
+          if (shared_antenna) {
+            const Coef cf = in ? coef[(int64_t)m * g.n_tau + ni] : Coef{0.f, 0.f, 0.f, 0.f};
+            rc[u] = make_float4(cf.k1, cf.beta, cf.k2, cf.valid);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const bool any = jv[u] > i0v[u];
+          ti[u] = any ? rel_t[i0v[u]] : 0;
+          tj[u] = any && jv[u] < n ? rel_t[jv[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          // the window [i0, j), its prefactor and its tail factor
+          const int32_t m = mb + u * NT;
+          float pre = 0.0f, tail = 0.0f;
+          if (jv[u] > i0v[u]) {
+            const int64_t d0 = (int64_t)ti[u] - (grid_t0(g, ax, m) - tb);
+            pre = d0 == 0 ? 1.0f : rec_ex2(c2 * (float)d0);
+            if (jv[u] < n) {
+              // Approximate FP32 exp2 for the tail: ~e^{-3} of the window
+              // sum for the default 3 tau cut.  Windows cut before 3 tau make
+              // it large, where the difference E[i0] - tail E[j] loses 1 / (1
+              // - tail): there a tail above 1/2 comes from the correctly
+              // rounded-to-1-ulp exp2f.  (An FP64 exp here, even behind a
+              // branch never taken, slowed this kernel by 12 %.)
+              const float dj = (float)(tj[u] - ti[u]);
+              tail = rec_ex2(c2 * dj);
+              if (short_cut && tail > 0.5f) tail = exp2f(c2 * dj);
+            }
+          }
+          ra[u] = make_float4(__int_as_float(i0v[u]), __int_as_float(jv[u]), pre, tail);
+          if (recs && m < g.n_t0) {   // (read back by this same thread on later templates)
+            rec_a[m] = ra[u];
+            if (shared_antenna) rec_c[m] = rc[u];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int32_t m = mb + u * NT;
+          const bool in = m < g.n_t0;
+          ra[u] = in ? rec_a[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (shared_antenna) rc[u] = in ? rec_c[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
-      const float v = two_f(cf, f[0], f[1], f[2], f[3]);
-      const bool ok = cf.valid == 1.0f;
-      if (map && cf.valid != 2.0f) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
-      partial_add(acc, v, (int32_t)cell, ok);
+      if (!shared_antenna) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int32_t m = mb + u * NT;
+          const Coef cf = m < g.n_t0 ? coef[(int64_t)tq * cells + (int64_t)m * g.n_tau + ni]
+                                     : Coef{0.f, 0.f, 0.f, 0.f};
+          rc[u] = make_float4(cf.k1, cf.beta, cf.k2, cf.valid);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t m = mb + u * NT;
+        if (m >= g.n_t0) break;
+        const int64_t cell = (int64_t)m * g.n_tau + ni;
+        const int32_t i0 = __float_as_int(ra[u].x), j = __float_as_int(ra[u].y);
+        float f[4] = {0.f, 0.f, 0.f, 0.f};
+        if (j > i0) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            f[c] = ra[u].z * fmaf(-ra[u].w, s_e[c * np1 + j], s_e[c * np1 + i0]);
+        }
+        const Coef cf{rc[u].x, rc[u].y, rc[u].z, rc[u].w};
+        const float v = two_f(cf, f[0], f[1], f[2], f[3]);
+        const bool ok = cf.valid == 1.0f;
+        if (map && cf.valid != 2.0f) map[(int64_t)tq * cells + cell] = ok ? v : 0.0f;
+        partial_add(acc, v, (int32_t)cell, ok);
+      }
     }
-    acc = partial_block_reduce<NT / 32>(acc, scratch);
+    acc = partial_block_reduce<NW>(acc, scratch);
     if (tid == 0) parts[(int64_t)tq * stride + ni] = acc;
   }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT)
+// MB blocks of 256 threads' register budget per SM, for any width: MB = 3
+// where shared memory lets three blocks reside, else 2 (more registers, no
+// occupancy lost).
+template <int NT, int MB>
+__global__ void __launch_bounds__(NT, MB * 256 / NT)
 k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          const int32_t* __restrict__ perm_gap, const TauTab* __restrict__ tauc,
-          const int64_t* __restrict__ ax, int32_t n_templates,
+          const int32_t* __restrict__ perm_gap, float4* __restrict__ recs,
+          const TauTab* __restrict__ tauc, const int64_t* __restrict__ ax, int32_t n_templates,
           int32_t n_groups, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
-  exp_rec_body<NT>(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, perm_gap, tauc, ax,
-               n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
+  exp_rec_body<NT, MB == 2 ? 4 : 2>(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, perm_gap, recs,
+                   tauc, ax, n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
 bool exp_rec_supported(int32_t n_sft, int32_t) { return n_sft <= kRecMaxSft; }
@@ -287,20 +343,20 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
   const int64_t want = (int64_t)p->n_sm * 4;
   const int32_t groups = (int32_t)std::max<int64_t>(
       1, std::min<int64_t>(p->n_templates, (want + g.n_tau - 1) / g.n_tau));
-  const size_t smem =
-      exp_rec_smem(p->n_sft, g.n_t0, (p->n_templates + groups - 1) / groups);
+  const size_t smem = exp_rec_smem(p->n_sft, g.n_t0, (p->n_templates + groups - 1) / groups);
   dim3 grid((unsigned)g.n_tau, (unsigned)groups);
   auto run = [&](auto kern, int nt) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, nt, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend,
                                 p->ws.coef, a->shared_antenna, p->ws.perm_x, p->ws.perm_gap,
-                                p->ws.tauc, plan_axes(p), p->n_templates, groups, d_2F,
+                                p->ws.rec_cells, p->ws.tauc, plan_axes(p), p->n_templates, groups, d_2F,
                                 p->ws.partials, p->part_stride);
   };
+  const bool three = smem + 1024 <= 227 * 1024 / 3;
   switch (p->lanes) {
-    case 64: run(k_exp_rec<64>, 64); break;
-    case 128: run(k_exp_rec<128>, 128); break;
-    default: run(k_exp_rec<256>, 256); break;
+    case 64: three ? run(k_exp_rec<64, 3>, 64) : run(k_exp_rec<64, 2>, 64); break;
+    case 128: three ? run(k_exp_rec<128, 3>, 128) : run(k_exp_rec<128, 2>, 128); break;
+    default: three ? run(k_exp_rec<256, 3>, 256) : run(k_exp_rec<256, 2>, 256); break;
   }
   p->launches += 1;
   return cudaGetLastError();
@@ -313,8 +369,8 @@ template <int NT>
 __global__ void __launch_bounds__(NT, 768 / NT) kb_exp_rec(const BItem* __restrict__ items,
                                                         BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    exp_rec_body<NT>(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared,
-                     it.perm_x, it.perm_gap, it.tauc, it.ax, it.T, it.groups, it.map, it.partials,
+    exp_rec_body<NT, 2>(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared,
+                     it.perm_x, it.perm_gap, it.rec_cells, it.tauc, it.ax, it.T, it.groups, it.map, it.partials,
                      it.part_stride,
                      make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                      dim3((unsigned)it.g.n_tau, (unsigned)it.groups));
@@ -325,9 +381,6 @@ const void* batch_kernel_exp_rec(int phase, int lanes) {
   return lanes == 64 ? (const void*)kb_exp_rec<64>
                      : lanes == 128 ? (const void*)kb_exp_rec<128> : (const void*)kb_exp_rec<256>;
 }
-size_t exp_rec_smem(int32_t n_sft, int32_t n_t0, int32_t tpb) {
-  return rec_smem_base(n_sft) +
-         (rec_stage_cells(n_sft, n_t0, tpb) ? sizeof(CellRec) * (size_t)n_t0 : 0);
-}
+size_t exp_rec_smem(int32_t n_sft, int32_t, int32_t) { return rec_smem_base(n_sft); }
 
 }  // namespace fmap

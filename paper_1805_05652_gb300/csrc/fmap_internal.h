@@ -62,9 +62,11 @@ struct __align__(16) Partial {
 constexpr double kCondThreshold = 100.0;
 // Reduction slots per template written by the fix-up kernel.
 constexpr int kFixSlots = 512;
-// Internal plan flag (not part of the C ABI): the plan never refines its
-// summaries and its workspace holds no refinement arrays (batch instances).
-constexpr uint32_t kPlanNoRefine = 1u << 16;
+// Internal plan flag (not part of the C ABI) of batch instances, whose
+// workspaces are kept lean: the plan never refines its summaries (no
+// refinement arrays), and the recurrence recomputes its window records per
+// template (no record array).
+constexpr uint32_t kPlanBatch = 1u << 16;
 // Top-cell refinement (fmap_refine.cu): candidates per template (at most),
 // histogram bins over the window of kRefWindow (2F units) below the maximum.
 constexpr int kRefMaxCells = 4096;
@@ -120,12 +122,19 @@ constexpr int kScanLanes = 256;   // the most threads of a scan
 __host__ __device__ inline int32_t batch_scan_lanes(int32_t n_sft) {
   return n_sft <= 1024 ? 64 : (n_sft <= 2560 ? 128 : 256);
 }
+// Atoms per thread: odd, so that the threads' chunk starts (stride C) fall
+// in distinct shared-memory banks across a warp.
 __host__ __device__ inline int64_t scan_chunk(int32_t n_sft, int32_t lanes) {
-  return ((int64_t)n_sft + lanes - 1) / lanes;
+  return (((int64_t)n_sft + lanes - 1) / lanes) | 1;
 }
-// (at most perm_entries(n, kScanLanes) for any width: workspaces take that)
 __host__ __device__ inline int64_t perm_entries(int32_t n_sft, int32_t lanes) {
   return scan_chunk(n_sft, lanes) * lanes;
+}
+// The most entries of any scan width (workspaces take this).
+__host__ __device__ inline int64_t perm_entries_max(int32_t n_sft) {
+  int64_t e = perm_entries(n_sft, 64);
+  e = e > perm_entries(n_sft, 128) ? e : perm_entries(n_sft, 128);
+  return e > perm_entries(n_sft, 256) ? e : perm_entries(n_sft, 256);
 }
 // Grid values t0_m and tau_n: Eq. Fmn's uniform grid, or the plan's explicit
 // axes ax (t0 values, then tau values) when given (non-null).
@@ -194,6 +203,11 @@ struct Workspace {
   float4* perm_ant = nullptr;    // [T_ant][.] (a2, b2, ab, gap to the next atom as int bits; -1 last)
   float4* perm_x = nullptr;      // [T][.] (Fa re, Fa im, Fb re, Fb im); recurrence plans
   int32_t* perm_gap = nullptr;   // [.] gap to the next atom (-1 last); recurrence plans
+  // recurrence plans: per cell, tau-major ([n_tau][n_t0]), the window record
+  // (i0, j as int bits, prefactor, tail factor), then a copy of the
+  // coefficients (shared antenna): written by the recurrence kernel's first
+  // template, read by the rest (absent with one template)
+  float4* rec_cells = nullptr;   // [2][cells]
   TauTab* tauc = nullptr;        // [n_tau] per-tau decay constants
   float2* wtab = nullptr;        // table windows: [kTabMax + 1] (w_k, w_{k+1} - w_k), then (0, 0)
   int64_t* ax = nullptr;         // [n_t0 + n_tau] explicit axes: t0 values, then tau values
