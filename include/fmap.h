@@ -201,7 +201,9 @@ fmap_status fmap_plan_set_log_prior(fmap_plan_t* plan, double log_prior_const);
  * detection candidate and e^F the odds, so both are decided on FP64 values).
  * After a compute call's fast map and reductions, per template the cells
  * whose fast 2F lies within 16 of the fast maximum (at most max_cells of
- * them, the highest; a histogram of 256 bins picks the cut) are recomputed
+ * them, the highest; a histogram of 256 bins picks the cut; when more than
+ * max_cells lie within 1/16 of the maximum, all of those, up to 4096, else
+ * none and the flags stay 0) are recomputed
  * from their atoms by the plain definition (windowed sums in float-float,
  * ~2^-44 relative; D and Eq. F_FaFb in FP64); these values replace the fast
  * ones in the map, in max2F, in the argmax (lowest index on ties) and in
@@ -347,8 +349,17 @@ fmap_status fmap_plan_status(fmap_plan_t* plan);
  * atoms, outputs) fits in the pool; each admitted request runs on its own
  * stream, so requests arriving while others are on the GPU overlap with
  * them.  A request's results do not depend on what else is in flight.
- * Precisions: exp_precision for exponential windows, rect_precision for
- * rectangular ones (fmap_precision values valid for that window).
+ * Precisions: rect_precision for rectangular windows; exponential windows
+ * by exp_mode: FMAP_SERVER_EXP_FIXED takes exp_precision,
+ * FMAP_SERVER_EXP_RECURRENCE the FP64-class decayed-suffix recurrence
+ * (FMAP_FP64 with FMAP_PLAN_EXP_RECURRENCE), FMAP_SERVER_EXP_AUTO per request
+ * whichever of the two a cost model of the form of App. A's timing model
+ * (terms in N_SFT N_tau, N_sums and N_t0 N_tau per template, constants fitted
+ * on GB300) estimates faster -- never less accurate than exp_precision
+ * (data sets past the recurrence's 9000 SFTs take exp_precision).
+ * Requests whose estimated GPU time is below 1 ms run on high-priority
+ * streams, so their blocks are scheduled ahead of those still waiting from
+ * larger requests in flight (the results do not change).
  * The paper computes one F-map per template on demand (Sec. 3, Sec. 4.2);
  * the server is the request loop around that operation.
  */
@@ -358,7 +369,13 @@ typedef struct {
   int32_t max_inflight;        /* 1..64 */
   fmap_precision exp_precision;
   fmap_precision rect_precision;
+  uint32_t exp_mode;           /* FMAP_SERVER_EXP_* */
 } fmap_server_config;
+enum {
+  FMAP_SERVER_EXP_FIXED = 0,
+  FMAP_SERVER_EXP_RECURRENCE = 1,
+  FMAP_SERVER_EXP_AUTO = 2
+};
 
 /* fmap_submit flags */
 enum { FMAP_SUBMIT_MAP = 1u /* also return the 2F map */ };

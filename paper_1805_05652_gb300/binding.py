@@ -74,11 +74,15 @@ FMAP_BATCH_AUTOTUNE = 1
 N_BATCH_PHASES = 15
 FMAP_N_PHASES = 4
 FMAP_SUBMIT_MAP = 1
+FMAP_SERVER_EXP_FIXED, FMAP_SERVER_EXP_RECURRENCE, FMAP_SERVER_EXP_AUTO = 0, 1, 2
+SERVER_EXP_MODES = {"fixed": FMAP_SERVER_EXP_FIXED, "rec": FMAP_SERVER_EXP_RECURRENCE,
+                    "auto": FMAP_SERVER_EXP_AUTO}
 
 
 class fmap_server_config(ctypes.Structure):
     _fields_ = [("device_mem_budget", c_size), ("pinned_bytes", c_size), ("max_inflight", c_i32),
-                ("exp_precision", ctypes.c_int), ("rect_precision", ctypes.c_int)]
+                ("exp_precision", ctypes.c_int), ("rect_precision", ctypes.c_int),
+                ("exp_mode", ctypes.c_uint32)]
 
 
 class FmapError(RuntimeError):
@@ -361,13 +365,16 @@ def fmap_count_terms(grid, t_host: np.ndarray):
 
 
 def fmap_server_create(device_mem_budget: int, pinned_bytes: int, max_inflight: int,
-                       exp_precision=FMAP_BF16X3, rect_precision=FMAP_FP64) -> int:
+                       exp_precision=FMAP_BF16X3, rect_precision=FMAP_FP64,
+                       exp_mode=FMAP_SERVER_EXP_FIXED) -> int:
     if isinstance(exp_precision, str):
         exp_precision = PRECISIONS[exp_precision]
     if isinstance(rect_precision, str):
         rect_precision = PRECISIONS[rect_precision]
+    if isinstance(exp_mode, str):
+        exp_mode = SERVER_EXP_MODES[exp_mode]
     cfg = fmap_server_config(int(device_mem_budget), int(pinned_bytes), int(max_inflight),
-                             int(exp_precision), int(rect_precision))
+                             int(exp_precision), int(rect_precision), int(exp_mode))
     h = c_vp()
     _check(lib().fmap_server_create(ctypes.byref(h), ctypes.byref(cfg)), "fmap_server_create")
     return h.value
@@ -503,9 +510,9 @@ class Server:
     """Owns one fmap server; submit() takes host numpy atoms."""
 
     def __init__(self, device_mem_budget=8 << 30, pinned_bytes=512 << 20, max_inflight=8,
-                 exp_precision="bf16x3", rect_precision="fp64"):
+                 exp_precision="bf16x3", rect_precision="fp64", exp_mode="fixed"):
         self.handle = fmap_server_create(device_mem_budget, pinned_bytes, max_inflight,
-                                         exp_precision, rect_precision)
+                                         exp_precision, rect_precision, exp_mode)
         self.meta = {}
 
     def submit(self, grid, t, antenna, fafb, want_map=False) -> int:

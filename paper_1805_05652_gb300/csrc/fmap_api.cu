@@ -95,7 +95,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
-      esuf, xop, perm_ant, perm_x, perm_gap, rec_cells, tauc, ax, wtab, flag_bits, tstat, ref_hist, ref_bin,
+      esuf, xop, perm_ant, perm_x, perm_gap, rec_cells, rec_decay, tauc, ax, wtab, flag_bits, tstat, ref_hist, ref_bin,
       ref_n, ref_cell, ref_fast, ref_val, own_map, ref_ntile, ref_tile, total;
   int64_t n_tiles;
   int32_t tau_chunk;
@@ -153,8 +153,8 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.own_map = (flags & FMAP_PLAN_MAP_BUFFER)
                     ? take(sizeof(float) * (size_t)std::max<int64_t>(cells, 1) * Tn) : 0;
   }
-  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.perm_gap = L.rec_cells = L.tauc =
-      L.wtab = 0;
+  L.pa = L.px = L.esuf = L.xop = L.perm_ant = L.perm_x = L.perm_gap = L.rec_cells =
+      L.rec_decay = L.tauc = L.wtab = 0;
   const size_t np1 = (size_t)n_sft + 1;
   if (g->window == FMAP_RECT) {
     L.pa = take(sizeof(float) * 8 * np1 * (size_t)t_ant);   // (a2, b2, ab, 0) float pairs
@@ -173,8 +173,11 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
       L.perm_gap = take(sizeof(int32_t) * (size_t)perm_entries_max(n_sft));
       // window records (and the shared antenna's coefficients) re-read by
       // every template after the first
-      if (T >= 2 && !(flags & kPlanBatch))
+      if (T >= 2 && !(flags & kPlanBatch)) {
         L.rec_cells = take((t_ant == 1 ? 2 : 1) * sizeof(float4) * (size_t)std::max<int64_t>(cells, 1));
+        L.rec_decay = take(sizeof(float) * (size_t)perm_entries_max(n_sft) *
+                           (size_t)std::max<int32_t>(g->n_tau, 1));
+      }
     }
     L.tauc = take(sizeof(TauTab) * (size_t)std::max<int32_t>(g->n_tau, 1));
     if (g->window == FMAP_TABLE) L.wtab = take(sizeof(float2) * (kTabMax + 1));
@@ -317,6 +320,7 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
     if (L.perm_x) w.perm_x = (float4*)(b + L.perm_x);
     if (L.perm_gap) w.perm_gap = (int32_t*)(b + L.perm_gap);
     if (L.rec_cells) w.rec_cells = (float4*)(b + L.rec_cells);
+    if (L.rec_decay) w.rec_decay = (float*)(b + L.rec_decay);
     if (L.wtab) w.wtab = (float2*)(b + L.wtab);
     w.tauc = (TauTab*)(b + L.tauc);
     if (L.xop) w.xop = (void*)(b + L.xop);

@@ -56,7 +56,7 @@ struct BUnits {
 // coefficients in 256-entry blocks, index-table rows, fix-up slots.
 constexpr int kCoefBlocksPerUnit = 8;
 constexpr int kIdxRowsPerUnit = 4;
-constexpr int kFixSlotsPerUnit = 16;
+constexpr int kFixSlotsPerUnit = 4;
 constexpr int kPermPerUnit = 4096;   // chunk-major copy entries per unit
 constexpr int kBitsPerUnit = 4096;   // marked-entry bitmask words cleared per unit
 static_assert(kFixSlots % kFixSlotsPerUnit == 0, "fix-up slot groups");

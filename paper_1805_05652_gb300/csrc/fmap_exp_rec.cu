@@ -65,7 +65,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
           const int32_t* __restrict__ perm_gap, float4* __restrict__ recs,
-          const TauTab* __restrict__ tauc,
+          float* __restrict__ rdec, const TauTab* __restrict__ tauc,
           const int64_t* __restrict__ ax, int32_t n_templates, int32_t n_groups,
           float* __restrict__ map, Partial* __restrict__ parts, int64_t stride,
     const uint3 bid, const dim3 gdim) {
@@ -103,6 +103,9 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   // absent (null) in single-template plans
   float4* rec_a = recs ? recs + (int64_t)ni * g.n_t0 : nullptr;
   float4* rec_c = recs ? recs + cells + (int64_t)ni * g.n_t0 : nullptr;
+  // FP32 decays of tau_n in the chunk-major order (absent: computed from the
+  // gaps every template)
+  float* rd = rdec ? rdec + (int64_t)ni * perm_entries(n, NT) : nullptr;
   const int32_t t_lo = (int32_t)((int64_t)bid.y * n_templates / n_groups);
   const int32_t t_hi = (int32_t)((int64_t)(bid.y + 1) * n_templates / n_groups);
   FF R{1.0f, 0.0f};   // the chunk's product of decays (from the first template on)
@@ -116,13 +119,16 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     float L[4] = {0.f, 0.f, 0.f, 0.f};
     float Qh = 1.0f, Qc = 0.0f;
     float xv[kRecChunk][4];
+    const bool cached = rd && !first;   // decays from the first template's pass
     for (int b0 = b_last; e0 > s0 && b0 >= s0; b0 -= kRecChunk) {
 #pragma unroll
       for (int q = 0; q < kRecChunk; ++q) {
         const int i = b0 + q;
         const int64_t o = (int64_t)(i - s0) * NT + tid;
         const float4 v = (i < e0) ? __ldg(x + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-        gq[q] = (i < e0) ? __ldg(perm_gap + o) : 0;
+        // gq holds the gap, or the cached decay's bits (written by this same
+        // thread: a plain load)
+        gq[q] = (i < e0) ? (cached ? __float_as_int(rd[o]) : __ldg(perm_gap + o)) : 0;
         xv[q][0] = v.x;
         xv[q][1] = v.y;
         xv[q][2] = v.z;
@@ -133,15 +139,22 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
         // (only the run at the chunk's end is partial: the same for the
         // warp's lanes but the last thread's)
         if (b0 + q >= e0) continue;
-        const FF r = decay(q);
+        float rh;
+        if (cached) {
+          rh = __int_as_float(gq[q]);
+        } else {
+          const FF r = decay(q);
+          rh = r.h;
+          if (first) {
+            ch_mul(r, Qh, Qc);
+            s_q[b0 + q] = Qh + Qc;
+            if (rd) rd[(int64_t)(b0 + q - s0) * NT + tid] = r.h;
+          }
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          L[c] = fmaf(r.h, L[c], xv[q][c]);
+          L[c] = fmaf(rh, L[c], xv[q][c]);
           s_e[c * np1 + b0 + q] = L[c];
-        }
-        if (first) {
-          ch_mul(r, Qh, Qc);
-          s_q[b0 + q] = Qh + Qc;
         }
       }
       if (first) ch_norm(Qh, Qc);
@@ -323,11 +336,11 @@ __global__ void __launch_bounds__(NT, MB * 256 / NT)
 k_exp_rec(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n,
           fmap_grid g, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
           const Coef* __restrict__ coef, int32_t shared_antenna, const float4* __restrict__ perm_x,
-          const int32_t* __restrict__ perm_gap, float4* __restrict__ recs,
+          const int32_t* __restrict__ perm_gap, float4* __restrict__ recs, float* __restrict__ rdec,
           const TauTab* __restrict__ tauc, const int64_t* __restrict__ ax, int32_t n_templates,
           int32_t n_groups, float* __restrict__ map, Partial* __restrict__ parts, int64_t stride) {
   exp_rec_body<NT, MB == 2 ? 4 : 2>(rel_t, t_base, n, g, i0tab, jend, coef, shared_antenna, perm_x, perm_gap, recs,
-                   tauc, ax, n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
+                   rdec, tauc, ax, n_templates, n_groups, map, parts, stride, blockIdx, gridDim);
 }
 
 bool exp_rec_supported(int32_t n_sft, int32_t) { return n_sft <= kRecMaxSft; }
@@ -349,7 +362,7 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, nt, smem, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, g, p->ws.i0, p->ws.jend,
                                 p->ws.coef, a->shared_antenna, p->ws.perm_x, p->ws.perm_gap,
-                                p->ws.rec_cells, p->ws.tauc, plan_axes(p), p->n_templates, groups, d_2F,
+                                p->ws.rec_cells, p->ws.rec_decay, p->ws.tauc, plan_axes(p), p->n_templates, groups, d_2F,
                                 p->ws.partials, p->part_stride);
   };
   const bool three = smem + 1024 <= 227 * 1024 / 3;
@@ -370,7 +383,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) kb_exp_rec(const BItem* __restri
                                                         BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
     exp_rec_body<NT, 2>(it.rel_t, it.t_base, it.n_sft, it.g, it.i0, it.jend, it.coef, it.shared,
-                     it.perm_x, it.perm_gap, it.rec_cells, it.tauc, it.ax, it.T, it.groups, it.map, it.partials,
+                     it.perm_x, it.perm_gap, it.rec_cells, nullptr, it.tauc, it.ax, it.T, it.groups, it.map, it.partials,
                      it.part_stride,
                      make_uint3((unsigned)(k % it.g.n_tau), (unsigned)(k / it.g.n_tau), 0),
                      dim3((unsigned)it.g.n_tau, (unsigned)it.groups));

@@ -23,8 +23,8 @@ namespace fmap {
 
 constexpr int kFlagBlock = 1024;
 constexpr int kFixThreads = 128;
+static_assert(kFixPerSlot == kFixThreads, "one entry per thread in a slot of the cell mode");
 constexpr int kFixWeights = 256;
-constexpr int kFixCellModeT = 8;    // below: threads over entries, not templates
 
 // Per unit of kFlagUnit entries: the number of entries marked in the
 // bitmask (valid == 2), from the unit's kFlagUnit / 32 words.
@@ -140,7 +140,7 @@ k_flag_write(const uint32_t* __restrict__ bits, int64_t n_entries,
 
 // FP64 recomputation of listed entries.  Entry = cell (shared antenna: every
 // template) or template * cells + cell (per-template antenna: that template).
-// Block (b, y): entries [b n / G, (b + 1) n / G), templates y*128 + tid.
+// Block (b, y): the entries of slot b (fix_slot_range), templates y*128 + tid.
 __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
         int32_t shared_antenna, const int32_t* __restrict__ rel_t,
         const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab,
@@ -152,7 +152,8 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const int64_t cap = shared_antenna ? cells : cells * n_templates;   // list capacity
   const int64_t n = min((int64_t)*n_flag, cap);
-  const int64_t lo = (int64_t)bid.x * n / G, hi = (int64_t)(bid.x + 1) * n / G;
+  int64_t lo, hi;
+  fix_slot_range(bid.x, n, G, n_templates, &lo, &hi);
   const int32_t tq = bid.y * kFixThreads + threadIdx.x;
   const bool active_t = tq < n_templates;
   Partial acc = partial_empty();
@@ -215,7 +216,8 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
 }
 
 // Few templates (T < kFixCellModeT): threads over the listed entries
-// instead of templates.  Block (b, tq): entries [b n / G, (b + 1) n / G) for
+// instead of templates.  Block (b, tq): the entries of slot b (about
+// kFixPerSlot of them, fix_slot_range) for
 // template tq, one thread per entry summing its own window in FP64 (the
 // windows of ill-conditioned cells are a few SFTs long), then a fixed-order
 // block reduction of the thread partials.
@@ -225,12 +227,13 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
         fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab, const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
-        Coef* __restrict__ coef, int32_t b, int32_t tq) {
+        Coef* __restrict__ coef, const TauTab* __restrict__ tauc, int32_t b, int32_t tq) {
   __shared__ Partial scratch[kFixThreads / 32];
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const int64_t cap = shared_antenna ? cells : cells * n_templates;
   const int64_t n = min((int64_t)*n_flag, cap);
-  const int64_t lo = (int64_t)b * n / G, hi = (int64_t)(b + 1) * n / G;
+  int64_t lo, hi;
+  fix_slot_range(b, n, G, n_templates, &lo, &hi);
   const int64_t tb = n_sft > 0 ? *t_base : 0;
   const float* ant = antenna + (int64_t)(shared_antenna ? 0 : tq) * 3 * n_sft;
   const float* x = fafb + (int64_t)tq * 4 * n_sft;
@@ -245,21 +248,23 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
     const double inv_tau = 1.0 / (double)grid_tau(g, ax, nn);
     double A = 0, B = 0, C = 0, far = 0, fai = 0, fbr = 0, fbi = 0;
     // Exponential weights along the window by products of the per-gap
-    // decays (one exp for the first atom and one for the one-SFT decay;
-    // relative error ~(j - i0) ulp), the FP64 pipe being 1/64 of FP32 rate.
+    // decays: one FP64 exp for the first atom, then for gaps of k < kPowTab
+    // whole SFTs the tau's float-float powers of the one-SFT decay (exact
+    // sums in FP64, ~2^-48 relative), FP64 exp for other gaps; relative error
+    // ~(j - i0) ulp, the FP64 pipe being 1/64 of the FP32 rate.
     const bool ex = g.window == FMAP_EXP;
     const bool tb_win = g.window == FMAP_TABLE;
     const double su = tb_win ? tab_scale(n_tab, exp_cut8_of(g), grid_tau(g, ax, nn)) : 0.0;
-    double w = 1.0, rho1 = 0.0;
-    if (ex && j > i0) {
-      w = exp(-(double)((int64_t)rel_t[i0] - t0rel) * inv_tau);
-      rho1 = exp(-(double)g.t_sft * inv_tau);
-    }
+    const float2* pw = ex && tauc ? tauc[nn].pw[0] : nullptr;
+    auto gap_w = [&](int32_t gap) -> double {
+      const int32_t k = gap / g.t_sft;
+      if (pw && k < kPowTab && k * g.t_sft == gap) return (double)pw[k].x + (double)pw[k].y;
+      return exp(-(double)gap * inv_tau);
+    };
+    double w = 1.0;
+    if (ex && j > i0) w = exp(-(double)((int64_t)rel_t[i0] - t0rel) * inv_tau);
     for (int32_t a = i0; a < j; ++a) {
-      if (ex && a > i0) {
-        const int32_t gap = rel_t[a] - rel_t[a - 1];
-        w *= gap == g.t_sft ? rho1 : (gap == 2 * g.t_sft ? rho1 * rho1 : exp(-(double)gap * inv_tau));
-      }
+      if (ex && a > i0) w *= gap_w(rel_t[a] - rel_t[a - 1]);
       if (tb_win) w = tab_weight64((double)((int64_t)rel_t[a] - t0rel) * su, wtab, n_tab);
       const double w2 = w * w;
       A += w2 * (double)ant[a];
@@ -291,9 +296,10 @@ k_fixup_cells(const int64_t* __restrict__ list, const int32_t* __restrict__ n_fl
               const int32_t* __restrict__ i0tab, const int32_t* __restrict__ jend,
               const float* __restrict__ antenna, const float* __restrict__ fafb,
               int32_t n_templates, float* __restrict__ map, Partial* __restrict__ parts,
-              int64_t stride, int64_t slot0, Coef* __restrict__ coef) {
+              int64_t stride, int64_t slot0, Coef* __restrict__ coef,
+              const TauTab* __restrict__ tauc) {
   fixup_cells_body(list, n_flag, G, shared_antenna, rel_t, t_base, n_sft, g, ax, wtab, n_tab, i0tab, jend, antenna,
-                   fafb, n_templates, map, parts, stride, slot0, coef, blockIdx.x, blockIdx.y);
+                   fafb, n_templates, map, parts, stride, slot0, coef, tauc, blockIdx.x, blockIdx.y);
 }
 
 // Fix-up blocks of one plan (the y extent: templates, or template blocks).
@@ -332,7 +338,8 @@ cudaError_t launch_flag_and_fixup(fmap_plan_s* p, const fmap_atoms* a, float* d_
                                                p->ws.i0, p->ws.jend,
                                                a->antenna, a->fafb, p->n_templates, d_2F,
                                                p->ws.partials, p->part_stride, p->n_tiles,
-                                               p->ws.coef);
+                                               p->ws.coef,
+                                               p->grid.window == FMAP_EXP ? p->ws.tauc : nullptr);
   else
     k_fixup<<<grid, kFixThreads, 0, s>>>(p->ws.flag_list, p->ws.n_flag, kFixSlots,
                                          a->shared_antenna, p->ws.rel_t, p->ws.t_base, p->n_sft,
@@ -377,7 +384,8 @@ __global__ void __launch_bounds__(kFixThreads) kb_fixup(const BItem* __restrict_
       if (it.T < kFixCellModeT)
         fixup_cells_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base,
                          it.n_sft, it.g, it.ax, nullptr, 0, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map,
-                         it.partials, it.part_stride, it.n_tiles, it.coef, b, y);
+                         it.partials, it.part_stride, it.n_tiles, it.coef,
+                         it.g.window == FMAP_EXP ? it.tauc : nullptr, b, y);
       else
         fixup_body(it.flag_list, it.n_flag, kFixSlots, it.shared, it.rel_t, it.t_base, it.n_sft,
                    it.g, it.ax, nullptr, 0, it.i0, it.jend, it.antenna, it.fafb, it.T, it.map, it.partials,

@@ -62,6 +62,22 @@ struct __align__(16) Partial {
 constexpr double kCondThreshold = 100.0;
 // Reduction slots per template written by the fix-up kernel.
 constexpr int kFixSlots = 512;
+// Below this many templates the fix-up runs one thread per listed entry
+// (else one per template), and spreads the list over just enough slots for
+// about kFixPerSlot entries each (else over all kFixSlots).
+constexpr int kFixCellModeT = 8;
+constexpr int kFixPerSlot = 128;
+// Entries [lo, hi) of fix-up slot b (of G) for a list of n entries and T
+// templates; every slot past the used ones is empty.  The fix-up kernels
+// and the refinement's scan of a slot's cells share this partition.
+__host__ __device__ inline void fix_slot_range(int64_t b, int64_t n, int32_t G, int32_t T,
+                                               int64_t* lo, int64_t* hi) {
+  const int64_t per = T < kFixCellModeT ? kFixPerSlot : 1;
+  int64_t used = (n + per - 1) / per;
+  used = used < 1 ? 1 : (used > G ? G : used);
+  *lo = b < used ? b * n / used : n;
+  *hi = b < used ? (b + 1) * n / used : n;
+}
 // Internal plan flag (not part of the C ABI) of batch instances, whose
 // workspaces are kept lean: the plan never refines its summaries (no
 // refinement arrays), and the recurrence recomputes its window records per
@@ -208,6 +224,10 @@ struct Workspace {
   // coefficients (shared antenna): written by the recurrence kernel's first
   // template, read by the rest (absent with one template)
   float4* rec_cells = nullptr;   // [2][cells]
+  // recurrence plans with two or more templates: the FP32 decay after each
+  // atom, per tau in the chunk-major order (first template writes, the rest
+  // read)
+  float* rec_decay = nullptr;    // [n_tau][perm_entries]
   TauTab* tauc = nullptr;        // [n_tau] per-tau decay constants
   float2* wtab = nullptr;        // table windows: [kTabMax + 1] (w_k, w_{k+1} - w_k), then (0, 0)
   int64_t* ax = nullptr;         // [n_t0 + n_tau] explicit axes: t0 values, then tau values

@@ -12,7 +12,8 @@
 //      one of the cells the cut will take, so the cost does not grow with
 //      the map;
 //   2. cuts the histogram after the last bin that keeps the cell count within
-//      the plan's cap, and collects those cells (in no fixed order: every
+//      the plan's cap (or after the top bin, when it alone holds more, up to
+//      kRefMaxCells), and collects those cells (in no fixed order: every
 //      later reduction over them is order-independent -- integer sums of
 //      fixed-point terms and a minimum of cell indices);
 //   3. recomputes each collected cell from its atoms by the plain
@@ -61,9 +62,11 @@ __device__ __forceinline__ int ref_bin_of(float v, float M) {
   return d > 0.0f ? (int)d : 0;
 }
 
-// The last histogram bin whose cumulative count stays within the cap (-1:
-// the top bin alone exceeds it), at most bt (the last bin whose cells all
-// lie in scanned tiles).
+// The last histogram bin whose cumulative count stays within the cap, at
+// most bt (the last bin whose cells all lie in scanned tiles).  When the top
+// bin alone holds more than the cap (a maximum shared by many cells within
+// 1/16 of 2F, e.g. windows truncated at the data's end), the top bin as a
+// whole while it fits the candidate buffer; else -1 (no refinement).
 __device__ __forceinline__ int32_t ref_cut_of(const int32_t* __restrict__ h, int32_t cap,
                                               int32_t bt) {
   int32_t cum = 0, b = -1;
@@ -72,6 +75,7 @@ __device__ __forceinline__ int32_t ref_cut_of(const int32_t* __restrict__ h, int
     if (cum > cap) break;
     b = k;
   }
+  if (b < 0 && h[0] <= kRefMaxCells) b = 0;
   return b;
 }
 
@@ -205,7 +209,8 @@ __device__ __forceinline__ void ref_tile_cells(const ScanArgs& A, int32_t j, int
     const int64_t cap = A.shared ? A.cells : A.cells * A.n_templates;
     const int64_t n = min((int64_t)*A.n_flag, cap);
     const int64_t b = k - A.n_tiles;
-    const int64_t lo = b * n / kFixSlots, hi = (b + 1) * n / kFixSlots;
+    int64_t lo, hi;
+    fix_slot_range(b, n, kFixSlots, A.n_templates, &lo, &hi);
     const int64_t m = hi - lo;
     for (int64_t e = lo + m * part / A.parts + lane; e < lo + m * (part + 1) / A.parts; e += 32) {
       const int64_t entry = A.flag_list[e];
@@ -302,11 +307,7 @@ __device__ __forceinline__ void ff_acc(FF& s, FF w, float x) {
   s = ff_add(s, ff_mul_f(w, x));
 }
 
-__global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t j = blockIdx.y;
-  const int32_t k = blockIdx.x * (kRefThreads / 32) + warp;
-  if (k >= min(A.ref_n[j], kRefMaxCells)) return;
+__device__ __forceinline__ void ref_cell_one(const RefArgs& A, int32_t j, int32_t k, int lane) {
   const fmap_grid& g = A.g;
   const int64_t slot = (int64_t)j * kRefMaxCells + k;
   const int32_t c = A.ref_cell[slot];
@@ -383,11 +384,20 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
   }
 }
 
+__global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t j = blockIdx.y;
+  const int32_t n_cand = min(A.ref_n[j], kRefMaxCells);
+  for (int32_t k = blockIdx.x * (kRefThreads / 32) + warp; k < n_cand;
+       k += gridDim.x * (kRefThreads / 32))
+    ref_cell_one(A, j, k, lane);
+}
+
 // Pass 4: one warp per template rebuilds its summary from the fast
 // statistics and the collected cells.  Every exp-term is in (0, 1] (relative
 // to the fast or the refined maximum, both held by a collected cell) and is
-// summed as an integer in 2^-52 units, so the sums do not depend on the
-// order in which the cells were collected (<= 4096 terms: no overflow,
+// summed as an integer in 2^-51 units, so the sums do not depend on the
+// order in which the cells were collected (<= 4096 terms <= 2^63: no overflow,
 // relative error < 1e-12).
 __global__ void __launch_bounds__(32)
 k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ hist,
@@ -406,7 +416,7 @@ k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ hist,
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, d));
   if (mx < 0.0) return;   // no collected cell valid in FP64: keep the fast summary
-  constexpr double kFix = 4503599627370496.0;   // 2^52
+  constexpr double kFix = 2251799813685248.0;   // 2^51
   unsigned long long sub = 0ull, add = 0ull;
   long long nv = 0;
   int32_t arg = 0x7fffffff;

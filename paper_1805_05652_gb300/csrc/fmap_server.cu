@@ -92,6 +92,10 @@ struct Request {
   // device pool region
   size_t dev_off = 0, dev_bytes = 0, ws_bytes = 0;
   fmap_plan_s* plan = nullptr;
+  fmap_precision prec = FMAP_FP64;   // the plan's precision and flags
+  uint32_t pflags = 0;
+  bool urgent = false;               // runs on the slot's high-priority stream
+  cudaStream_t stream = nullptr;
   int slot = -1;
   enum { QUEUED, RUNNING, DONE } state = QUEUED;
   fmap_status status = FMAP_OK;
@@ -113,7 +117,8 @@ struct fmap_server_s {
   char* dev_pool = nullptr;
   char* pin_pool = nullptr;
   fmap::RangeAllocator dev_alloc, pin_alloc;
-  std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> streams;    // per slot: normal priority
+  std::vector<cudaStream_t> ustreams;   // per slot: high priority (small requests)
   std::vector<cudaEvent_t> events;
   std::vector<fmap::Request*> slots;   // running request per stream slot
   std::mutex mu;
@@ -130,6 +135,47 @@ struct fmap_server_s {
 namespace fmap {
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Estimated GPU milliseconds of a request, in the form of App. A's timing
+// model (per template: a term in the atoms scanned, one in the windowed
+// sums N_sums and one in the cells N_t0 N_tau, plus a constant), with the
+// constants fitted on GB300 to the serving mix (summaries refined; median
+// error ~20 %).  Used only to choose between the exponential forms and the
+// stream priority: a poor estimate costs speed, never accuracy.
+struct CostModel {
+  // N_sums of an exponential / rectangular grid, from a 64 x 64 sample of
+  // its cells: a window holds min(L, data end - max(t0, first atom)) of the
+  // data span, at the data set's mean atom density.
+  static double n_sums(const fmap_grid& g, const int64_t* t, int32_t n) {
+    if (n <= 0 || g.n_t0 <= 0 || g.n_tau <= 0) return 0.0;
+    const double first = (double)t[0], end = (double)t[n - 1] + (double)g.t_sft;
+    const double density = (double)n / ((end - first) / (double)g.t_sft);
+    const int km = std::min<int32_t>(g.n_t0, 64), kn = std::min<int32_t>(g.n_tau, 64);
+    double acc = 0.0;
+    for (int a = 0; a < km; ++a) {
+      const int64_t m = (int64_t)(g.n_t0 - 1) * a / std::max(km - 1, 1);
+      const double t0 = (double)(g.t0_min + m * g.dt0);
+      const double room = std::max(0.0, end - std::max(t0, first));
+      for (int b = 0; b < kn; ++b) {
+        const int64_t nn = (int64_t)(g.n_tau - 1) * b / std::max(kn - 1, 1);
+        const double L = (double)window_len(g, g.tau_min + nn * g.dtau);
+        acc += std::min(L, room) / (double)g.t_sft * density;
+      }
+    }
+    return acc / ((double)km * kn) * (double)g.n_t0 * (double)g.n_tau;
+  }
+  static double rect_ms(const fmap_grid& g, int32_t n, int32_t T) {
+    return 3.48e-9 * T * (double)g.n_t0 * g.n_tau + 5.78e-7 * T * (double)n + 0.29;
+  }
+  static double exp_tc_ms(const fmap_grid& g, double sums, int32_t T) {
+    return 3.98e-11 * T * sums + 1.58e-8 * T * (double)g.n_t0 * g.n_tau + 0.85;
+  }
+  static double exp_rec_ms(const fmap_grid& g, int32_t n, int32_t T) {
+    return 8.25e-9 * T * (double)g.n_tau * n + 1.21e-8 * T * (double)g.n_t0 * g.n_tau +
+           5.85e-6 * T * (double)g.n_tau + 0.30;
+  }
+};
+constexpr double kUrgentMs = 1.0;
 
 // Bytes of a request's inputs and outputs.  The device always holds the map
 // (the refinement of the summaries reads and rewrites it); the pinned host
@@ -149,12 +195,9 @@ static fmap_status launch_request(fmap_server_s* s, Request* r) {
   size_t in_b, out_b, hout_b;
   request_sizes(*r, &in_b, &out_b, &hout_b);
   char* d = s->dev_pool + r->dev_off;
-  const uint32_t flags = r->shared ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA;
-  const fmap_precision prec =
-      r->grid.window == FMAP_RECT ? s->cfg.rect_precision : s->cfg.exp_precision;
   r->plan = new (std::nothrow) fmap_plan_s();
   if (!r->plan) return FMAP_ERR_NOMEM;
-  fmap_status st = plan_init(r->plan, &r->grid, r->n_sft, r->T, prec, flags, d, r->ws_bytes);
+  fmap_status st = plan_init(r->plan, &r->grid, r->n_sft, r->T, r->prec, r->pflags, d, r->ws_bytes);
   if (st != FMAP_OK) return st;
   char* q = d + align256(r->ws_bytes);
   const size_t n = (size_t)r->n_sft, T = (size_t)r->T;
@@ -167,7 +210,8 @@ static fmap_status launch_request(fmap_server_s* s, Request* r) {
   fmap_summary* d_sum = (fmap_summary*)q;
   q += align256(sizeof(fmap_summary) * T) + 256;
   float* d_map = (float*)q;
-  cudaStream_t st_ = s->streams[r->slot];
+  cudaStream_t st_ = r->urgent ? s->ustreams[r->slot] : s->streams[r->slot];
+  r->stream = st_;
   const size_t cells = (size_t)r->grid.n_t0 * (size_t)r->grid.n_tau;
   if (n > 0) {
     FMAP_CUDA(cudaMemcpyAsync(d_t, r->h_t, 8 * n, cudaMemcpyHostToDevice, st_));
@@ -257,7 +301,7 @@ static void worker_loop(fmap_server_s* s) {
         // copies and kernels queued before the failure may still be writing
         // the request's device range: let them finish before it is reused
         const std::string why = fmap_last_error();
-        cudaStreamSynchronize(s->streams[slot]);
+        cudaStreamSynchronize(r->stream ? r->stream : s->streams[slot]);
         cudaGetLastError();
         finish_request(s, r, st, why);
       }
@@ -287,8 +331,9 @@ fmap_status fmap_server_create(fmap_server_t** out, const fmap_server_config* cf
   }
   *out = nullptr;
   if (cfg->max_inflight < 1 || cfg->max_inflight > 64 || cfg->device_mem_budget < (1u << 20) ||
-      cfg->pinned_bytes < (1u << 20)) {
-    set_error("max_inflight must be in [1, 64]; device and pinned budgets >= 1 MiB");
+      cfg->pinned_bytes < (1u << 20) || cfg->exp_mode > FMAP_SERVER_EXP_AUTO) {
+    set_error("max_inflight must be in [1, 64]; device and pinned budgets >= 1 MiB; "
+              "exp_mode FMAP_SERVER_EXP_*");
     return FMAP_ERR_ARG;
   }
   fmap_server_s* s = new (std::nothrow) fmap_server_s();
@@ -307,10 +352,14 @@ fmap_status fmap_server_create(fmap_server_t** out, const fmap_server_config* cf
   s->dev_alloc.reset(cfg->device_mem_budget);
   s->pin_alloc.reset(cfg->pinned_bytes);
   s->streams.resize(cfg->max_inflight);
+  s->ustreams.resize(cfg->max_inflight);
   s->events.resize(cfg->max_inflight);
   s->slots.assign(cfg->max_inflight, nullptr);
+  int lo_prio = 0, hi_prio = 0;   // (numerically lower = higher priority)
+  cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
   for (int k = 0; k < cfg->max_inflight; ++k) {
-    cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+    cudaStreamCreateWithPriority(&s->streams[k], cudaStreamNonBlocking, lo_prio);
+    cudaStreamCreateWithPriority(&s->ustreams[k], cudaStreamNonBlocking, hi_prio);
     cudaEventCreateWithFlags(&s->events[k], cudaEventDisableTiming);
   }
   s->worker = std::thread(worker_loop, s);
@@ -327,6 +376,7 @@ void fmap_server_destroy(fmap_server_t* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   for (auto st : s->streams) cudaStreamSynchronize(st);
+  for (auto st : s->ustreams) cudaStreamSynchronize(st);
   for (auto& kv : s->all) {
     Request* r = kv.second;
     if (r->plan) {
@@ -336,6 +386,7 @@ void fmap_server_destroy(fmap_server_t* s) {
     delete r;
   }
   for (auto st : s->streams) cudaStreamDestroy(st);
+  for (auto st : s->ustreams) cudaStreamDestroy(st);
   for (auto ev : s->events) cudaEventDestroy(ev);
   cudaFree(s->dev_pool);
   cudaFreeHost(s->pin_pool);
@@ -371,9 +422,29 @@ fmap_status fmap_submit(fmap_server_t* s, const fmap_grid* grid, const fmap_atom
     set_error("table windows are not served");
     return FMAP_ERR_ARG;
   }
-  const fmap_precision prec = grid->window == FMAP_RECT ? s->cfg.rect_precision : s->cfg.exp_precision;
-  const uint32_t pflags = r->shared ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA;
-  fmap_status st = plan_footprint(grid, r->n_sft, r->T, prec, pflags, &r->ws_bytes);
+  // the form of the request, and its priority, by the cost model
+  r->pflags = r->shared ? 0u : (uint32_t)FMAP_PLAN_PER_TEMPLATE_ANTENNA;
+  double est = 0.0;
+  if (grid->window == FMAP_RECT) {
+    r->prec = s->cfg.rect_precision;
+    est = CostModel::rect_ms(*grid, r->n_sft, r->T);
+  } else {
+    // (data sets past the recurrence's shared-memory limit take exp_precision)
+    const bool rec_ok = exp_rec_supported(r->n_sft, grid->n_t0);
+    const double rec = CostModel::exp_rec_ms(*grid, r->n_sft, r->T);
+    bool use_rec = rec_ok && s->cfg.exp_mode == FMAP_SERVER_EXP_RECURRENCE;
+    double other = rec;
+    if (!use_rec) {
+      const double sums = r->n_sft > 0 ? CostModel::n_sums(*grid, h->t, r->n_sft) : 0.0;
+      other = CostModel::exp_tc_ms(*grid, sums, r->T);
+      use_rec = rec_ok && s->cfg.exp_mode == FMAP_SERVER_EXP_AUTO && rec < other;
+    }
+    r->prec = use_rec ? FMAP_FP64 : s->cfg.exp_precision;
+    if (use_rec) r->pflags |= (uint32_t)FMAP_PLAN_EXP_RECURRENCE;
+    est = use_rec ? rec : other;
+  }
+  r->urgent = est < kUrgentMs;
+  fmap_status st = plan_footprint(grid, r->n_sft, r->T, r->prec, r->pflags, &r->ws_bytes);
   if (st != FMAP_OK) {
     delete r;
     return st;

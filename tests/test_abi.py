@@ -50,6 +50,21 @@ def test_struct_sizes_match_header(L):
     assert ctypes.sizeof(fm.binding.fmap_server_config) == 32
 
 
+@pytest.mark.parametrize("bad", [dict(max_inflight=0), dict(max_inflight=65),
+                                 dict(exp_mode=3), dict(pinned_bytes=1024)])
+def test_server_rejects_bad_config(L, bad):
+    """The configuration is checked before any device memory is touched."""
+    cfg = dict(device_mem_budget=1 << 30, pinned_bytes=1 << 24, max_inflight=4,
+               exp_precision=fm.FMAP_BF16X3, rect_precision=fm.FMAP_FP64,
+               exp_mode=fm.FMAP_SERVER_EXP_AUTO)
+    cfg.update(bad)
+    with pytest.raises(fm.FmapError) as e:
+        fm.fmap_server_create(cfg["device_mem_budget"], cfg["pinned_bytes"], cfg["max_inflight"],
+                              cfg["exp_precision"], cfg["rect_precision"], cfg["exp_mode"])
+    assert e.value.status == fm.FMAP_ERR_ARG
+    assert "exp_mode" in fm.last_error() or "max_inflight" in fm.last_error()
+
+
 def test_status_strings(L):
     assert fm.status_string(0) == "FMAP_OK"
     assert fm.status_string(fm.FMAP_ERR_DATA) == "FMAP_ERR_DATA"

@@ -447,3 +447,23 @@ def test_refinement_summary_only_and_off(window, prec):
     assert changed.sum() <= inst.n_templates * 512
     err = np.abs(got[changed] - ref[changed]) / np.maximum(np.abs(ref[changed]), 1.0)
     assert err.size == 0 or err.max() <= 1e-6
+
+
+@pytest.mark.parametrize("window,prec", [(RECT, "fp64"), (EXP, "rec")])
+def test_refinement_flat_maximum(window, prec):
+    """Windows that run past the data's end hold the same atoms for every
+    longer tau: more cells than the cap (64 for the FP64 class) lie within
+    1/16 of the maximum, and the refinement takes that whole top bin (up to
+    4096 cells), so every template is still refined with an exact argmax."""
+    # (exponential: tau far beyond the data span, so that the weights, and
+    # 2F, barely change along tau)
+    grid = Grid(0, T_SFT, 12, 2 * T_SFT if window == RECT else 2000 * T_SFT, T_SFT, 400, window)
+    inst = synth.make_instance(83, n_det=1, presence=1.0, n_merged=60, n_templates=3,
+                               grid=grid, injections=[(1, RECT, 0, 60 * T_SFT, 400.0)])
+    ref, valid, _ = oracle_map(inst)
+    rs = oracle.summary(ref, valid)
+    top = [(valid[j] & (ref[j] >= rs["max2F"][j] - 1.0 / 16)).sum() for j in range(3)]
+    assert max(top) > 64   # the case this test is for
+    got, gs = run_gpu(inst, prec)
+    check_map(got, ref, valid, TOL[prec])
+    check_summary(gs, ref, valid, TOL[prec], LOGB_TOL)

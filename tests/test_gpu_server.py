@@ -49,8 +49,13 @@ def reqs():
     return _requests(24)
 
 
-def test_alone_equals_mixed_and_matches_oracle(reqs):
-    alone = fm.Server(device_mem_budget=1 << 30, pinned_bytes=256 << 20, max_inflight=1)
+@pytest.mark.parametrize("exp_mode", ["fixed", "rec", "auto"])
+def test_alone_equals_mixed_and_matches_oracle(reqs, exp_mode):
+    """exp_mode: exponential requests by BF16x3 (fixed), by the recurrence,
+    or per request by the server's cost model (auto); mixes of high- and
+    normal-priority streams in the burst."""
+    kw = dict(device_mem_budget=1 << 30, pinned_bytes=256 << 20, exp_mode=exp_mode)
+    alone = fm.Server(max_inflight=1, **kw)
     solo = []
     for inst in reqs:
         tk = _run(alone, inst)
@@ -58,7 +63,7 @@ def test_alone_equals_mixed_and_matches_oracle(reqs):
         assert st == fm.FMAP_OK
         solo.append((s, m))
     alone.close()
-    mixed = fm.Server(device_mem_budget=1 << 30, pinned_bytes=256 << 20, max_inflight=6)
+    mixed = fm.Server(max_inflight=6, **kw)
     tickets = [_run(mixed, inst) for inst in reqs]
     for k, tk in enumerate(tickets):
         st, s, m = mixed.poll(tk, wait_us=-1)
@@ -73,7 +78,7 @@ def test_alone_equals_mixed_and_matches_oracle(reqs):
     for k, inst in enumerate(reqs):
         ref, valid, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, inst.grid.as_tuple(),
                                     mode="fast")
-        prec = "fp64" if inst.grid.window == RECT else "bf16x3"
+        prec = "fp64" if inst.grid.window == RECT else ("rec" if exp_mode == "rec" else "bf16x3")
         check_map(solo[k][1].astype(np.float64), ref, valid, TOL[prec])
         check_summary(solo[k][0], ref, valid, TOL[prec], LOGB_TOL)
 
