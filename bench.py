@@ -646,7 +646,7 @@ def run_default(args, fm, torch, dev, dist, rank, world, clocks):
     torch.cuda.empty_cache()
     # ---- the CPU oracle on a sample of the headline workload ----
     if world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(inst, target_s=6.0 if args.quick else 12.0)[0]
+        res["cpu_baseline"] = cpu_baseline(inst, target_s=6.0 if args.quick else 8.0)[0]
     del inst
     configs = {}
     # ---- small rect (1 template, 200 SFTs) ----
