@@ -72,7 +72,9 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) float s_dyn[];
   const int64_t np1 = (int64_t)n + 1;
-  float* s_e = s_dyn;              // [4][n + 1] L, then E, of one template
+  // [n + 1] L, then E, of one template: the 4 data columns of an atom as one
+  // float4 (one 16-byte access where four 4-byte ones would be)
+  float4* s_e = reinterpret_cast<float4*>(s_dyn);
   float* s_q = s_dyn + 4 * np1;    // [n] decay product from atom i to its chunk's end
   __shared__ float sR[2][NW];      // each warp's product of its chunks' R
   __shared__ float sS[4][2][NW];   // each warp's composed S (per template)
@@ -152,10 +154,8 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
           }
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          L[c] = fmaf(rh, L[c], xv[q][c]);
-          s_e[c * np1 + b0 + q] = L[c];
-        }
+        for (int c = 0; c < 4; ++c) L[c] = fmaf(rh, L[c], xv[q][c]);
+        s_e[b0 + q] = make_float4(L[0], L[1], L[2], L[3]);
       }
       if (first) ch_norm(Qh, Qc);
     }
@@ -228,10 +228,14 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     }
     for (int i = s0; i < e0; ++i) {
       const float qi = s_q[i];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) s_e[c * np1 + i] = fmaf(qi, Ke[c], s_e[c * np1 + i]);
+      float4 e = s_e[i];
+      e.x = fmaf(qi, Ke[0], e.x);
+      e.y = fmaf(qi, Ke[1], e.y);
+      e.z = fmaf(qi, Ke[2], e.z);
+      e.w = fmaf(qi, Ke[3], e.w);
+      s_e[i] = e;
     }
-    if (tid < 4) s_e[tid * np1 + n] = 0.0f;
+    if (tid == 0) s_e[n] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     // 4. cells (t0_m, tau_n), all m
     const bool fresh = first || !recs;   // records computed here (no array: one template)
@@ -312,9 +316,11 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
         const int32_t i0 = __float_as_int(ra[u].x), j = __float_as_int(ra[u].y);
         float f[4] = {0.f, 0.f, 0.f, 0.f};
         if (j > i0) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            f[c] = ra[u].z * fmaf(-ra[u].w, s_e[c * np1 + j], s_e[c * np1 + i0]);
+          const float4 ej = s_e[j], ei = s_e[i0];
+          f[0] = ra[u].z * fmaf(-ra[u].w, ej.x, ei.x);
+          f[1] = ra[u].z * fmaf(-ra[u].w, ej.y, ei.y);
+          f[2] = ra[u].z * fmaf(-ra[u].w, ej.z, ei.z);
+          f[3] = ra[u].z * fmaf(-ra[u].w, ej.w, ei.w);
         }
         const Coef cf{rc[u].x, rc[u].y, rc[u].z, rc[u].w};
         const float v = two_f(cf, f[0], f[1], f[2], f[3]);

@@ -393,35 +393,46 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_cells(const RefArgs A) {
     ref_cell_one(A, j, k, lane);
 }
 
-// Pass 4: one warp per template rebuilds its summary from the fast
+// Pass 4: one block per template rebuilds its summary from the fast
 // statistics and the collected cells.  Every exp-term is in (0, 1] (relative
 // to the fast or the refined maximum, both held by a collected cell) and is
 // summed as an integer in 2^-51 units, so the sums do not depend on the
 // order in which the cells were collected (<= 4096 terms <= 2^63: no overflow,
 // relative error < 1e-12).
-__global__ void __launch_bounds__(32)
+constexpr int kFinalThreads = 256;
+
+__global__ void __launch_bounds__(kFinalThreads)
 k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ hist,
             const int32_t* __restrict__ cut, int32_t cap, const int32_t* __restrict__ ref_ntile,
             const int32_t* __restrict__ ref_n, const int32_t* __restrict__ ref_cell,
             const float* __restrict__ ref_fast, const double* __restrict__ ref_val, int32_t n_tau,
             double log_prior, double tol, fmap_summary* __restrict__ out) {
+  constexpr int NW = kFinalThreads / 32;
+  __shared__ double s_mx[NW];
+  __shared__ unsigned long long s_sub[NW], s_add[NW];
+  __shared__ long long s_nv[NW];
+  __shared__ int32_t s_arg[NW];
   const int32_t j = blockIdx.x;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TStat s = st[j];
   const int32_t n = min(ref_n[j], kRefMaxCells);
   if (s.N <= 0 || n <= 0) return;   // the fast summary stands (flags 0)
   const int64_t base = (int64_t)j * kRefMaxCells;
   double mx = -1.0;
-  for (int32_t k = lane; k < n; k += 32) mx = fmax(mx, ref_val[base + k]);
+  for (int32_t k = threadIdx.x; k < n; k += kFinalThreads) mx = fmax(mx, ref_val[base + k]);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+  if (lane == 0) s_mx[warp] = mx;
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < NW; ++w) mx = fmax(mx, s_mx[w]);
   if (mx < 0.0) return;   // no collected cell valid in FP64: keep the fast summary
   constexpr double kFix = 2251799813685248.0;   // 2^51
   unsigned long long sub = 0ull, add = 0ull;
   long long nv = 0;
   int32_t arg = 0x7fffffff;
   const double M = (double)s.M;
-  for (int32_t k = lane; k < n; k += 32) {
+  for (int32_t k = threadIdx.x; k < n; k += kFinalThreads) {
     const double ef = exp(0.5 * fmin((double)ref_fast[base + k] - M, 0.0));
     sub += (unsigned long long)__double2ull_rn(ef * kFix);
     const double v = ref_val[base + k];
@@ -438,7 +449,20 @@ k_ref_final(const TStat* __restrict__ st, const int32_t* __restrict__ hist,
     nv += __shfl_xor_sync(0xffffffffu, nv, d);
     arg = min(arg, __shfl_xor_sync(0xffffffffu, arg, d));
   }
-  if (lane != 0) return;
+  if (lane == 0) {
+    s_sub[warp] = sub;
+    s_add[warp] = add;
+    s_nv[warp] = nv;
+    s_arg[warp] = arg;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < NW; ++w) {   // (integer sums: the order does not matter)
+    sub += s_sub[w];
+    add += s_add[w];
+    nv += s_nv[w];
+    arg = min(arg, s_arg[w]);
+  }
   const double Sp = exp(0.5 * (M - mx)) * fmax(s.S - (double)sub / kFix, 0.0) + (double)add / kFix;
   const long long Np = s.N - n + nv;
   const int32_t b = ref_cut_of(hist + (int64_t)j * kRefBins, cap, cut[j]);
@@ -521,7 +545,7 @@ cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
   A.ref_fast = w.ref_fast;
   A.ref_val = w.ref_val;
   k_ref_cells<<<dim3((unsigned)((cap + wpb - 1) / wpb), (unsigned)T), kRefThreads, 0, s>>>(A);
-  k_ref_final<<<T, 32, 0, s>>>(w.tstat, w.ref_hist, w.ref_bin, cap, w.ref_ntile, w.ref_n,
+  k_ref_final<<<T, kFinalThreads, 0, s>>>(w.tstat, w.ref_hist, w.ref_bin, cap, w.ref_ntile, w.ref_n,
                                w.ref_cell, w.ref_fast, w.ref_val, g.n_tau, p->log_prior,
                                fast_tol(p), d_summary);
   p->launches += 5;
