@@ -386,6 +386,30 @@ class Runner:
             raise SystemExit(f"device status {fm.status_string(st)}")
         return per, ph / max(calls, 1), launches
 
+    def time_graph(self, prec, steps, warmup):
+        """ms per step of a plan replaying one captured CUDA graph per call
+        (FMAP_PLAN_GRAPH; the plan's phase timing is off, so no phases)."""
+        torch, fm = self.torch, self.fm
+        p = self.plan(prec, fm.FMAP_PLAN_GRAPH)
+        for _ in range(warmup):
+            self.step(p)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for k in range(steps):
+            self.flush.fill_(float(k))
+            evs[k][0].record(self.stream)
+            self.step(p)
+            evs[k][1].record(self.stream)
+        torch.cuda.synchronize()
+        st = p.status()
+        p.close()
+        if st != fm.FMAP_OK:
+            raise SystemExit(f"device status {fm.status_string(st)}")
+        per = [a.elapsed_time(b) for a, b in evs]
+        return {"ms_per_step": sum(per) / steps, "steps": steps,
+                "note": "the same step replayed as one CUDA graph (FMAP_PLAN_GRAPH)"}
+
     def sampled(self, templates):
         """Host copies of the map rows and summaries of some templates."""
         idx = self.torch.tensor(list(templates), device=self.dev)
@@ -656,7 +680,8 @@ def run_default(args, fm, torch, dev, dist, rank, world, clocks):
     tt_ = count_terms_np(sr.grid, sr.t)[0]
     configs["small_rect"] = {"description": WORKLOADS["small_rect"],
                              "forms": time_forms(run, ["fp64", "fp32"], 200, 5, tt_, None, ref,
-                                                 valid)}
+                                                 valid),
+                             "fp64_graph": run.time_graph("fp64", 200, 5)}
     del run
     # ---- exp16: FP32 against FP64 (and the other forms) ----
     e16 = make_workload("exp16", rank)
@@ -669,7 +694,8 @@ def run_default(args, fm, torch, dev, dist, rank, world, clocks):
     forms16 = time_forms(run, ["fp64"], 3, 1, tt_, None, ref, valid, roof16)
     forms16.update(time_forms(run, ["fp32", "rec", "bf16x3", "tf32"], 50, 5, tt_, None, ref,
                               valid, roof16))
-    configs["exp16"] = {"description": WORKLOADS["exp16"], "forms": forms16}
+    configs["exp16"] = {"description": WORKLOADS["exp16"], "forms": forms16,
+                        "rec_graph": run.time_graph("rec", 50, 5)}
     f = configs["exp16"]["forms"]
     if "fp32" in f and "fp64" in f and "ms_per_step" in f["fp64"]:
         configs["exp16"]["fp32_vs_fp64_speedup"] = f["fp64"]["ms_per_step"] / f["fp32"]["ms_per_step"]

@@ -149,14 +149,22 @@ enum {
    * (tau, data column) in compensated FP32 instead of a sum per cell:
    * O(N_tau N_SFT + cells) per template.  Needs n_sft <= 9000 (one
    * template's suffix sums in shared memory; FMAP_ERR_UNSUPPORTED otherwise);
-   * the per-cell window records of one tau are staged there too when
-   * 24 n_sft + 32 n_t0 <= ~220 KB, else recomputed per template. */
+   * with two or more templates the workspace also holds the per-cell window
+   * records and per-atom decays of every tau (32 B per cell, 4 B per atom
+   * and tau), formed by a block's first template and re-read by the rest. */
   FMAP_PLAN_EXP_RECURRENCE = 2u,
   /* the plan holds a [T][n_t0][n_tau] float map of its own (the workspace
    * grows by 4 T n_t0 n_tau bytes), used by summary-only compute calls
    * (d_2F = NULL) so that their summaries can be refined (fmap_plan_set_refine);
    * without it a summary-only call reports the unrefined reductions */
-  FMAP_PLAN_MAP_BUFFER = 4u
+  FMAP_PLAN_MAP_BUFFER = 4u,
+  /* repeated compute calls replay one CUDA graph of the call's launches: the
+   * first call with a given set of atom, map and summary pointers captures
+   * its launches (on a stream of the plan's own) and launches the graph on
+   * the caller's stream; later calls with the same pointers launch it again
+   * (the data behind the pointers may change between calls), other pointers
+   * capture anew.  Plans with timing enabled launch directly. */
+  FMAP_PLAN_GRAPH = 8u
 };
 
 typedef struct fmap_plan_s fmap_plan_t;

@@ -30,6 +30,7 @@ FMAP_FP64, FMAP_FP32, FMAP_TF32, FMAP_BF16X3 = 0, 1, 2, 3
 FMAP_PLAN_PER_TEMPLATE_ANTENNA = 1
 FMAP_PLAN_EXP_RECURRENCE = 2
 FMAP_PLAN_MAP_BUFFER = 4
+FMAP_PLAN_GRAPH = 8
 # fmap_summary.flags
 FMAP_SUMMARY_REFINED, FMAP_SUMMARY_ARGMAX_EXACT = 1, 2
 

@@ -236,7 +236,7 @@ static fmap_status plan_args_ok(const fmap_grid* grid, int32_t n_sft, int32_t n_
   if (n_templates < 0 || n_templates > 65535) return arg_fail("n_templates must be in [0, 65535]");
   if (precision < FMAP_FP64 || precision > FMAP_BF16X3) return arg_fail("unknown precision");
   if (flags & ~(uint32_t)(FMAP_PLAN_PER_TEMPLATE_ANTENNA | FMAP_PLAN_EXP_RECURRENCE |
-                          FMAP_PLAN_MAP_BUFFER | kPlanBatch))
+                          FMAP_PLAN_MAP_BUFFER | FMAP_PLAN_GRAPH | kPlanBatch))
     return arg_fail("unknown plan flags");
   if (flags & FMAP_PLAN_EXP_RECURRENCE) {
     if (grid->window != FMAP_EXP) return arg_fail("FMAP_PLAN_EXP_RECURRENCE is for exponential windows");
@@ -338,6 +338,7 @@ fmap_status fmap_plan(fmap_plan_t** out, const fmap_grid* grid, int32_t n_sft,
   set_error("");
   if (!out) return arg_fail("plan output pointer is NULL");
   *out = nullptr;
+  if (flags & kPlanBatch) return arg_fail("unknown plan flags");   // (internal to batches)
   size_t total = 0;
   fmap_status st = plan_footprint(grid, n_sft, n_templates, precision, flags, &total);
   if (st != FMAP_OK) return st;
@@ -385,6 +386,10 @@ namespace fmap {
 void plan_release(fmap_plan_s* p) {
   drop_events(p);
   free_staging(p);
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  p->graph = nullptr;
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  p->cap_stream = nullptr;
 }
 }  // namespace fmap
 
@@ -428,6 +433,10 @@ static fmap_status check_device(const fmap_plan_s* p) {
   return FMAP_OK;
 }
 
+static fmap_status enqueue(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
+                           fmap_summary* d_summary, cudaStream_t s, int window,
+                           const cudaEvent_t* evp);
+
 static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
                            fmap_summary* d_summary, cudaStream_t s, int window) {
   set_error("");
@@ -445,9 +454,47 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
   // summary-only calls write the plan's own map when it has one, so that the
   // summaries can be refined
   if (!d_2F && p->ws.own_map) d_2F = p->ws.own_map;
-  if (p->needs_err_reset) {
+  if (p->needs_err_reset) {   // (outside any graph: an unread error is kept)
     FMAP_CUDA(cudaMemsetAsync(p->ws.dev_err, 0, sizeof(uint32_t), s));
     p->needs_err_reset = false;
+  }
+  if ((p->flags & FMAP_PLAN_GRAPH) && !p->timing) {
+    const void* key[6] = {a->t, a->antenna, a->fafb, (const void*)(intptr_t)a->shared_antenna,
+                          d_2F, d_summary};
+    bool same = p->graph && p->graph_key_window == window;
+    for (int k = 0; k < 6 && same; ++k) same = key[k] == p->graph_key[k];
+    if (!same) {
+      if (p->graph) {   // (the old graph may still be running)
+        FMAP_CUDA(cudaStreamSynchronize(p->graph_stream));
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+      }
+      if (!p->cap_stream) FMAP_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+      FMAP_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int64_t l0 = p->launches;
+      const fmap_status st_e = enqueue(p, a, d_2F, d_summary, p->cap_stream, window, nullptr);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+      if (st_e != FMAP_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st_e != FMAP_OK ? st_e : cuda_fail(e, "cudaStreamEndCapture");
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&p->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        p->graph = nullptr;
+        return cuda_fail(ei, "cudaGraphInstantiate");
+      }
+      for (int k = 0; k < 6; ++k) p->graph_key[k] = key[k];
+      p->graph_key_window = window;
+      p->graph_launches = p->launches - l0;
+      p->launches = l0;
+    }
+    FMAP_CUDA(cudaGraphLaunch(p->graph, s));
+    p->graph_stream = s;
+    p->launches += p->graph_launches;
+    return FMAP_OK;
   }
   cudaEvent_t ev[FMAP_N_PHASES + 1] = {};
   if (p->timing) {
@@ -455,6 +502,17 @@ static fmap_status compute(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
     for (auto e : ev) p->events.push_back(e);
     FMAP_CUDA(cudaEventRecord(ev[0], s));
   }
+  return enqueue(p, a, d_2F, d_summary, s, window, ev);
+}
+
+// The launches of one compute call on stream s (ev: the phase events of a
+// timed call, else null).
+static fmap_status enqueue(fmap_plan_t* p, const fmap_atoms* a, float* d_2F,
+                           fmap_summary* d_summary, cudaStream_t s, int window,
+                           const cudaEvent_t* evp) {
+  cudaEvent_t ev[FMAP_N_PHASES + 1] = {};
+  if (evp)
+    for (int k = 0; k <= FMAP_N_PHASES; ++k) ev[k] = evp[k];
   FMAP_CUDA(launch_prep(p, a, s));
   {   // the bitmask of ill-conditioned entries, set by the coefficient kernels
     const int64_t ent = (int64_t)p->grid.n_t0 * p->grid.n_tau *

@@ -274,6 +274,15 @@ struct fmap_plan_s {
   bool tmaps_ready = false;
   bool owns_ws = false;          // workspace allocated by fmap_plan (else caller-provided)
   bool needs_err_reset = true;   // status word not yet cleared on the device
+  // FMAP_PLAN_GRAPH: the captured call, the pointers it was captured with
+  // (atoms t, antenna, fafb, shared flag, map, summaries, window) and its
+  // launch count
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;   // where the graph was last launched
+  const void* graph_key[6] = {};
+  int32_t graph_key_window = -1;
+  int64_t graph_launches = 0;
   cudaStream_t last_stream = nullptr;
   fmap::Workspace ws;
   // timing (fmap_plan_enable_timing)

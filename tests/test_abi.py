@@ -101,7 +101,8 @@ def test_plan_rejects_tensor_precision_for_rect(L):
 
 def test_plan_rejects_bad_sizes_and_flags(L):
     grid = (0, T_SFT, 10, T_SFT, T_SFT, 10, T_SFT, EXP)
-    for args in ((-1, 1, 0, 0), (10, -1, 0, 0), (10, 70000, 0, 0), (10, 1, 9, 0), (10, 1, 0, 8)):
+    for args in ((-1, 1, 0, 0), (10, -1, 0, 0), (10, 70000, 0, 0), (10, 1, 9, 0), (10, 1, 0, 16),
+                 (10, 1, 0, 1 << 16)):
         with pytest.raises(fm.FmapError) as e:
             fm.fmap_plan(grid, *args)
         assert e.value.status == fm.FMAP_ERR_ARG

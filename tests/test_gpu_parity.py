@@ -467,3 +467,45 @@ def test_refinement_flat_maximum(window, prec):
     got, gs = run_gpu(inst, prec)
     check_map(got, ref, valid, TOL[prec])
     check_summary(gs, ref, valid, TOL[prec], LOGB_TOL)
+
+
+@pytest.mark.parametrize("window,prec", [(RECT, "fp64"), (EXP, "rec"), (EXP, "bf16x3")])
+def test_graph_replay(window, prec):
+    """FMAP_PLAN_GRAPH: the first call captures its launches, later calls with
+    the same pointers replay them (bit-identical to direct launches, reading
+    the atoms as they are at each call), other pointers capture anew."""
+    import torch
+
+    g = Grid(-2000, T_SFT, 60, 2 * T_SFT if window == RECT else T_SFT, T_SFT, 150, window)
+    insts = [synth.make_instance(90 + k, n_det=2, presence=0.9, n_merged=300, n_templates=5,
+                                 grid=g, injections=[(1, window, 10 * T_SFT, 40 * T_SFT, 150.0)])
+             for k in range(2)]
+    dev = torch.device("cuda:0")
+    flags = fm.FMAP_PLAN_EXP_RECURRENCE if prec == "rec" else 0
+    p_prec = "fp64" if prec == "rec" else prec
+    direct = fm.Plan(g, insts[0].n_sft, 5, p_prec, flags)
+    graph = fm.Plan(g, insts[0].n_sft, 5, p_prec, flags | fm.FMAP_PLAN_GRAPH)
+    t = torch.from_numpy(insts[0].t).to(dev)
+    a = torch.from_numpy(np.ascontiguousarray(insts[0].antenna)).to(dev)
+    x = torch.from_numpy(np.ascontiguousarray(insts[0].fafb)).to(dev)
+    m = torch.empty((5, g.n_t0, g.n_tau), device=dev)
+    s = torch.empty((5, 32), dtype=torch.uint8, device=dev)
+    for inst in insts + insts[:1]:   # the same buffers, the data replaced in place
+        t.copy_(torch.from_numpy(inst.t))
+        a.copy_(torch.from_numpy(np.ascontiguousarray(inst.antenna)))
+        x.copy_(torch.from_numpy(np.ascontiguousarray(inst.fafb)))
+        m_ref, s_ref = direct.compute(t, a, x)
+        graph.compute(t, a, x, out_map=m, out_summary=s)
+        torch.cuda.synchronize()
+        assert graph.status() == fm.FMAP_OK and direct.status() == fm.FMAP_OK
+        assert torch.equal(m, m_ref) and torch.equal(s, s_ref)
+    # another output buffer: captured again, same results
+    m2 = torch.empty_like(m)
+    graph.compute(t, a, x, out_map=m2, out_summary=s)
+    torch.cuda.synchronize()
+    assert torch.equal(m2, m)
+    ref, valid, _ = oracle_map(insts[0])
+    check_map(m2.cpu().numpy().astype(np.float64), ref, valid, TOL[prec])
+    check_summary(fm.summary_to_numpy(s), ref, valid, TOL[prec], LOGB_TOL)
+    direct.close()
+    graph.close()
