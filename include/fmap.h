@@ -163,7 +163,9 @@ enum {
    * its launches (on a stream of the plan's own) and launches the graph on
    * the caller's stream; later calls with the same pointers launch it again
    * (the data behind the pointers may change between calls), other pointers
-   * capture anew.  Plans with timing enabled launch directly. */
+   * capture anew, and so does the first call after a setting of the plan
+   * changes (log prior, refinement, wait limit, axes, window table).  Plans
+   * with timing enabled launch directly. */
   FMAP_PLAN_GRAPH = 8u
 };
 

@@ -411,6 +411,7 @@ fmap_status fmap_plan_set_log_prior(fmap_plan_t* p, double c) {
   if (!p) return arg_fail("plan is NULL");
   if (!std::isfinite(c)) return arg_fail("log prior constant must be finite");
   p->log_prior = c;
+  p->graph_key_window = -1;   // (a captured graph holds the old value)
   return FMAP_OK;
 }
 
@@ -583,6 +584,7 @@ fmap_status fmap_plan_window_table(fmap_plan_t* p, const float* w, int32_t n_poi
   tab[n_points] = make_float2(0.0f, 0.0f);
   FMAP_CUDA(cudaMemcpy(p->ws.wtab, tab.data(), sizeof(float2) * tab.size(), cudaMemcpyHostToDevice));
   p->n_tab = n_points;
+  p->graph_key_window = -1;   // (a captured graph holds the old table size)
   return FMAP_OK;
 }
 
@@ -651,6 +653,7 @@ fmap_status fmap_plan_set_refine(fmap_plan_t* p, int32_t max_cells) {
   if (!p) return arg_fail("plan is NULL");
   if (max_cells > kRefMaxCells) return arg_fail("at most 4096 refined cells per template");
   p->refine_cells = max_cells < 0 ? -1 : max_cells;
+  p->graph_key_window = -1;   // (a captured graph holds the old value)
   return FMAP_OK;
 }
 
@@ -658,6 +661,7 @@ fmap_status fmap_plan_set_wait_limit(fmap_plan_t* p, int64_t limit_ns) {
   set_error("");
   if (!p) return arg_fail("plan is NULL");
   p->wait_ns = limit_ns < 0 ? kDefaultWaitNs : limit_ns;
+  p->graph_key_window = -1;   // (a captured graph holds the old value)
   return FMAP_OK;
 }
 
@@ -801,6 +805,7 @@ fmap_status fmap_plan_axes(fmap_plan_t* p, const int64_t* t0_values, const int64
   if (!p) return arg_fail("plan is NULL");
   if (!t0_values != !tau_values) return arg_fail("give both axes or neither");
   if (p->last_stream) FMAP_CUDA(cudaStreamSynchronize(p->last_stream));
+  p->graph_key_window = -1;   // (a captured graph holds the old axes argument)
   if (!t0_values) {
     p->explicit_axes = false;
     p->ax_host.clear();

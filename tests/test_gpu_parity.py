@@ -504,6 +504,16 @@ def test_graph_replay(window, prec):
     graph.compute(t, a, x, out_map=m2, out_summary=s)
     torch.cuda.synchronize()
     assert torch.equal(m2, m)
+    # a setting changed after the capture: the next call captures anew
+    logb = fm.summary_to_numpy(s)["logB"].copy()
+    graph.set_log_prior(1.5)
+    graph.compute(t, a, x, out_map=m2, out_summary=s)
+    torch.cuda.synchronize()
+    assert np.allclose(fm.summary_to_numpy(s)["logB"], logb + 1.5, rtol=0, atol=1e-12,
+                       equal_nan=True)
+    graph.set_log_prior(0.0)
+    graph.compute(t, a, x, out_map=m2, out_summary=s)
+    torch.cuda.synchronize()
     ref, valid, _ = oracle_map(insts[0])
     check_map(m2.cpu().numpy().astype(np.float64), ref, valid, TOL[prec])
     check_summary(fm.summary_to_numpy(s), ref, valid, TOL[prec], LOGB_TOL)
