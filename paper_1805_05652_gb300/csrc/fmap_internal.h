@@ -136,7 +136,7 @@ __host__ __device__ inline int64_t flag_words(int64_t entries) {
 // chunks stays cheap next to the chunks themselves.
 constexpr int kScanLanes = 256;   // the most threads of a scan
 __host__ __device__ inline int32_t batch_scan_lanes(int32_t n_sft) {
-  return n_sft <= 1024 ? 64 : (n_sft <= 2560 ? 128 : 256);
+  return n_sft <= 1024 ? 128 : 256;
 }
 // Atoms per thread: odd, so that the threads' chunk starts (stride C) fall
 // in distinct shared-memory banks across a warp.
