@@ -450,7 +450,7 @@ fmap_status fmap_batch_status(fmap_batch_t* batch, fmap_stream stream);
  * input checks, index tables, exp chunk-major atom copies, rect antenna
  * prefixes, exp antenna sums and coefficients, rect coefficients, rect data
  * prefixes, exp recurrence and cells, rect cells, three steps of the
- * ill-conditioned cell compaction, FP64 fix-up, two reduction levels. */
+ * ill-conditioned cell compaction, float-float fix-up, two reduction levels. */
 #define FMAP_BATCH_N_PHASES 15
 /* Waves, kernel launches per run, workspace bytes, chosen occupancy per phase
  * (FMAP_BATCH_N_PHASES entries, nullable) and templates per block of the

@@ -137,6 +137,11 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   return fast_two_sum(s.h, s.l + a.l + b.l);
 }
 __device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.h, -b.l}); }
+// s <- s + w x: the product by FMA-based TwoProd, then a float-float addition
+// (~2^-47 relative to the running sum per step).
+__device__ __forceinline__ void ff_acc(FF& s, FF w, float x) {
+  s = ff_add(s, ff_mul_f(w, x));
+}
 // x + r e
 __device__ __forceinline__ FF ff_axpy(FF r, FF e, float x) {
   const float p = r.h * e.h;

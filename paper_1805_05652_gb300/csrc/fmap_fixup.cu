@@ -10,10 +10,13 @@
 //   1. compacts the marked cells into a list in a deterministic order: the
 //      coefficient kernels set one bit per marked entry; per-unit counts of
 //      the bits, one exclusive scan, ordered writes;
-//   2. recomputes each listed cell for every template by the plain FP64
-//      definition over its window (Sec. 2: windowed sums, Eq. F_FaFb), writes
-//      its 2F and adds it to per-block reduction partials kept in their own
-//      slots, merged by the final reduction.
+//   2. recomputes each listed cell for every template from the definition
+//      over its window (Sec. 2: windowed sums, Eq. F_FaFb) in float-float
+//      arithmetic (a value is an unevaluated pair of FP32 numbers, ~2^-47
+//      relative per operation; GB300 runs FP64 at 1/64 of the FP32 rate),
+//      with D = A B - C^2 and the numerator of 2F formed in float-float too,
+//      writes its 2F and adds it to per-block reduction partials kept in
+//      their own slots, merged by the final reduction.
 #include <math.h>
 
 #include "fmap_batch.cuh"
@@ -138,9 +141,42 @@ k_flag_write(const uint32_t* __restrict__ bits, int64_t n_entries,
   flag_write_body(bits, n_entries, blockoff, list, blockIdx, gridDim);
 }
 
-// FP64 recomputation of listed entries.  Entry = cell (shared antenna: every
-// template) or template * cells + cell (per-template antenna: that template).
-// Block (b, y): the entries of slot b (fix_slot_range), templates y*128 + tid.
+// One atom's terms added to the seven float-float sums of a cell: A, B, C
+// with weight w^2, Re/Im Fa and Re/Im Fb with weight w (Sec. 2).
+__device__ __forceinline__ void fix_add_atom(FF* s, FF w, FF w2, const float* __restrict__ ant,
+                                             const float* __restrict__ x, int64_t n, int32_t a) {
+  ff_acc(s[0], w2, ant[a]);
+  ff_acc(s[1], w2, ant[n + a]);
+  ff_acc(s[2], w2, ant[2 * n + a]);
+  ff_acc(s[3], w, x[a]);
+  ff_acc(s[4], w, x[n + a]);
+  ff_acc(s[5], w, x[2 * n + a]);
+  ff_acc(s[6], w, x[3 * n + a]);
+}
+
+// 2F of a cell from its seven float-float sums (Eq. F_FaFb times two).
+// D = A B - C^2 and the numerator B |Fa|^2 + A |Fb|^2 - 2 C Re(Fa Fb*) are
+// formed in float-float, so their cancellations cost ~2^-46 A B / D of
+// relative accuracy (< 1e-6 at the A B / D ~ 1e7 of the worst cells), then
+// divided in FP32.  *ok: at least two atoms and D > 0 (the sign of a
+// normalised pair is the sign of its high part).
+__device__ __forceinline__ float fix_two_f(const FF* s, int32_t count, bool* ok) {
+  const FF D = ff_sub(ff_mul(s[0], s[1]), ff_mul(s[2], s[2]));
+  *ok = count >= 2 && D.h > 0.0f;
+  if (!*ok) return 0.0f;
+  const FF fa2 = ff_add(ff_mul(s[3], s[3]), ff_mul(s[4], s[4]));
+  const FF fb2 = ff_add(ff_mul(s[5], s[5]), ff_mul(s[6], s[6]));
+  const FF fab = ff_add(ff_mul(s[3], s[5]), ff_mul(s[4], s[6]));
+  const FF c2 = {2.0f * s[2].h, 2.0f * s[2].l};
+  const FF num = ff_sub(ff_add(ff_mul(s[1], fa2), ff_mul(s[0], fb2)), ff_mul(c2, fab));
+  return 2.0f * (num.h / D.h);
+}
+
+// Float-float recomputation of listed entries.  Entry = cell (shared antenna:
+// every template) or template * cells + cell (per-template antenna: that
+// template).  Block (b, y): the entries of slot b (fix_slot_range), templates
+// y*128 + tid; the window's weights (w, w^2) are evaluated once per block in
+// FP64 and shared as float pairs.
 __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, const int32_t* __restrict__ n_flag, int32_t G,
         int32_t shared_antenna, const int32_t* __restrict__ rel_t,
         const int64_t* __restrict__ t_base, int32_t n_sft, fmap_grid g, const int64_t* __restrict__ ax, const float2* __restrict__ wtab, int32_t n_tab,
@@ -148,7 +184,7 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
         const float* __restrict__ antenna, const float* __restrict__ fafb, int32_t n_templates,
         float* __restrict__ map, Partial* __restrict__ parts, int64_t stride, int64_t slot0,
         Coef* __restrict__ coef, const uint3 bid, const dim3 gdim) {
-  __shared__ double sw[kFixWeights];
+  __shared__ float4 sw[kFixWeights];   // per atom (w, w^2) as float pairs
   const int64_t cells = (int64_t)g.n_t0 * g.n_tau;
   const int64_t cap = shared_antenna ? cells : cells * n_templates;   // list capacity
   const int64_t n = min((int64_t)*n_flag, cap);
@@ -169,47 +205,40 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
     const int32_t ta = shared_antenna ? 0 : tq;
     const float* ant = antenna + (int64_t)ta * 3 * n_sft;
     const float* x = fafb + (int64_t)(active_t ? tq : 0) * 4 * n_sft;
-    double A = 0, B = 0, C = 0, far = 0, fai = 0, fbr = 0, fbi = 0;
+    FF sums[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) sums[q] = FF{0.0f, 0.0f};
     for (int32_t a0 = i0; a0 < j; a0 += kFixWeights) {
       __syncthreads();
       for (int32_t u = threadIdx.x; u < kFixWeights; u += kFixThreads) {
         const int32_t a = a0 + u;
-        double w = 0.0;
+        float4 wv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (a < j) {
           const double d = (double)((int64_t)rel_t[a] - t0rel);
-          w = g.window == FMAP_RECT ? 1.0
+          const double w = g.window == FMAP_RECT ? 1.0
               : g.window == FMAP_TABLE ? tab_weight64(d * tab_scale(n_tab, exp_cut8_of(g), grid_tau(g, ax, nn)), wtab, n_tab)
                                        : exp(-d / tau);
+          const FF wf = ff_of(w), w2f = ff_of(w * w);
+          wv = make_float4(wf.h, wf.l, w2f.h, w2f.l);
         }
-        sw[u] = w;
+        sw[u] = wv;
       }
       __syncthreads();
       if (mine) {
         const int32_t len = min(kFixWeights, j - a0);
         for (int32_t u = 0; u < len; ++u) {
-          const int32_t a = a0 + u;
-          const double w = sw[u], w2 = w * w;
-          A += w2 * (double)ant[a];
-          B += w2 * (double)ant[n_sft + a];
-          C += w2 * (double)ant[2 * (int64_t)n_sft + a];
-          far += w * (double)x[a];
-          fai += w * (double)x[n_sft + a];
-          fbr += w * (double)x[2 * (int64_t)n_sft + a];
-          fbi += w * (double)x[3 * (int64_t)n_sft + a];
+          const float4 wv = sw[u];
+          fix_add_atom(sums, FF{wv.x, wv.y}, FF{wv.z, wv.w}, ant, x, n_sft, a0 + u);
         }
       }
     }
     if (mine) {
-      const double D = A * B - C * C;
-      const bool ok = (j - i0) >= 2 && D > 0.0;
-      double v = 0.0;
-      if (ok)
-        v = 2.0 * (B * (far * far + fai * fai) + A * (fbr * fbr + fbi * fbi) -
-                   2.0 * C * (far * fbr + fai * fbi)) / D;
-      if (map) map[(int64_t)tq * cells + cell] = (float)v;
-      // the FP64 validity decision, recorded once per entry
+      bool ok;
+      const float v = fix_two_f(sums, j - i0, &ok);
+      if (map) map[(int64_t)tq * cells + cell] = v;
+      // the validity decision, recorded once per entry
       if (coef && (only >= 0 || tq == 0)) coef[entry].valid = ok ? 3.0f : 0.0f;
-      partial_add(acc, (float)v, (int32_t)cell, ok);
+      partial_add(acc, v, (int32_t)cell, ok);
     }
   }
   if (active_t) parts[(int64_t)tq * stride + slot0 + bid.x] = acc;
@@ -218,9 +247,9 @@ __device__ __forceinline__ void fixup_body(const int64_t* __restrict__ list, con
 // Few templates (T < kFixCellModeT): threads over the listed entries
 // instead of templates.  Block (b, tq): the entries of slot b (about
 // kFixPerSlot of them, fix_slot_range) for
-// template tq, one thread per entry summing its own window in FP64 (the
-// windows of ill-conditioned cells are a few SFTs long), then a fixed-order
-// block reduction of the thread partials.
+// template tq, one thread per entry summing its own window in float-float
+// (the windows of ill-conditioned cells are a few SFTs long), then a
+// fixed-order block reduction of the thread partials.
 __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ list,
         const int32_t* __restrict__ n_flag, int32_t G, int32_t shared_antenna,
         const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n_sft,
@@ -245,45 +274,36 @@ __device__ __forceinline__ void fixup_cells_body(const int64_t* __restrict__ lis
     const int32_t m = (int32_t)(cell / g.n_tau), nn = (int32_t)(cell % g.n_tau);
     const int32_t i0 = i0tab[m], j = jend[cell];
     const int64_t t0rel = grid_t0(g, ax, m) - tb;
-    const double inv_tau = 1.0 / (double)grid_tau(g, ax, nn);
-    double A = 0, B = 0, C = 0, far = 0, fai = 0, fbr = 0, fbi = 0;
-    // Exponential weights along the window by products of the per-gap
-    // decays: one FP64 exp for the first atom, then for gaps of k < kPowTab
-    // whole SFTs the tau's float-float powers of the one-SFT decay (exact
-    // sums in FP64, ~2^-48 relative), FP64 exp for other gaps; relative error
-    // ~(j - i0) ulp, the FP64 pipe being 1/64 of the FP32 rate.
+    const int64_t tau = grid_tau(g, ax, nn);
+    // Exponential weights along the window as products of per-gap decays,
+    // the first one being the decay from t0 to the first atom: for gaps of
+    // k < kPowTab whole SFTs the tau's float-float powers of the one-SFT
+    // decay (~2^-48), an FP64 exp split into a float pair for other gaps;
+    // relative error ~(j - i0) 2^-47.
     const bool ex = g.window == FMAP_EXP;
     const bool tb_win = g.window == FMAP_TABLE;
-    const double su = tb_win ? tab_scale(n_tab, exp_cut8_of(g), grid_tau(g, ax, nn)) : 0.0;
-    const float2* pw = ex && tauc ? tauc[nn].pw[0] : nullptr;
-    auto gap_w = [&](int32_t gap) -> double {
-      const int32_t k = gap / g.t_sft;
-      if (pw && k < kPowTab && k * g.t_sft == gap) return (double)pw[k].x + (double)pw[k].y;
-      return exp(-(double)gap * inv_tau);
+    const double su = tb_win ? tab_scale(n_tab, exp_cut8_of(g), tau) : 0.0;
+    const TauTab* tc = ex && tauc ? tauc + nn : nullptr;
+    auto decay = [&](int64_t gap) -> FF {
+      const int64_t k = gap / g.t_sft;
+      if (tc && k < kPowTab && k * g.t_sft == gap) return FF{tc->pw[0][k].x, tc->pw[0][k].y};
+      return ff_of(exp(-(double)gap * (tc ? tc->inv_tau : 1.0 / (double)tau)));
     };
-    double w = 1.0;
-    if (ex && j > i0) w = exp(-(double)((int64_t)rel_t[i0] - t0rel) * inv_tau);
+    FF sums[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) sums[q] = FF{0.0f, 0.0f};
+    FF w{1.0f, 0.0f};
+    if (ex && j > i0) w = decay((int64_t)rel_t[i0] - t0rel);
     for (int32_t a = i0; a < j; ++a) {
-      if (ex && a > i0) w *= gap_w(rel_t[a] - rel_t[a - 1]);
-      if (tb_win) w = tab_weight64((double)((int64_t)rel_t[a] - t0rel) * su, wtab, n_tab);
-      const double w2 = w * w;
-      A += w2 * (double)ant[a];
-      B += w2 * (double)ant[n_sft + a];
-      C += w2 * (double)ant[2 * (int64_t)n_sft + a];
-      far += w * (double)x[a];
-      fai += w * (double)x[n_sft + a];
-      fbr += w * (double)x[2 * (int64_t)n_sft + a];
-      fbi += w * (double)x[3 * (int64_t)n_sft + a];
+      if (ex && a > i0) w = ff_mul(w, decay(rel_t[a] - rel_t[a - 1]));
+      if (tb_win) w = ff_of(tab_weight64((double)((int64_t)rel_t[a] - t0rel) * su, wtab, n_tab));
+      fix_add_atom(sums, w, ff_mul(w, w), ant, x, n_sft, a);
     }
-    const double D = A * B - C * C;
-    const bool ok = (j - i0) >= 2 && D > 0.0;
-    double v = 0.0;
-    if (ok)
-      v = 2.0 * (B * (far * far + fai * fai) + A * (fbr * fbr + fbi * fbi) -
-                 2.0 * C * (far * fbr + fai * fbi)) / D;
-    if (map) map[(int64_t)tq * cells + cell] = (float)v;
+    bool ok;
+    const float v = fix_two_f(sums, j - i0, &ok);
+    if (map) map[(int64_t)tq * cells + cell] = v;
     if (coef && (!shared_antenna || tq == 0)) coef[entry].valid = ok ? 3.0f : 0.0f;
-    partial_add(acc, (float)v, (int32_t)cell, ok);
+    partial_add(acc, v, (int32_t)cell, ok);
   }
   acc = partial_block_reduce<kFixThreads / 32>(acc, scratch);
   if (threadIdx.x == 0) parts[(int64_t)tq * stride + slot0 + b] = acc;

@@ -303,9 +303,6 @@ struct RefArgs {
 // seven sums meet in a fixed butterfly; lane 0 forms D and 2F in FP64 from
 // them, records the fast and refined values and writes the refined value to
 // the map.
-__device__ __forceinline__ void ff_acc(FF& s, FF w, float x) {
-  s = ff_add(s, ff_mul_f(w, x));
-}
 
 __device__ __forceinline__ void ref_cell_one(const RefArgs& A, int32_t j, int32_t k, int lane) {
   const fmap_grid& g = A.g;
