@@ -34,10 +34,14 @@
 //   4. the column of cells (t0_m, tau_n) for every m from E, with the
 //      window records (i0, j, prefactor, tail factor; and the coefficients
 //      when the antenna is shared) computed on the block's first template and
-//      re-read from a tau-major array on the others.
+//      re-read from a tau-major array on the others (the groups of one tau
+//      each write the same values there).
 // Blocks run tau-fastest, so the blocks writing neighbouring tau of the same
 // map rows run together and their stores merge in L2.
 #include <math.h>
+
+#include <algorithm>
+#include <cmath>
 
 #include "fmap_batch.cuh"
 #include "fmap_device.cuh"
@@ -45,6 +49,7 @@
 namespace fmap {
 
 constexpr int kRecChunk = 8;        // SFTs of data prefetched per serial run of the scan
+constexpr int kRecMaxGroups = 32;   // template groups per tau (blocks per tau)
 constexpr int kRecMaxSft = 9000;    // one template's suffix sums in shared memory (180 KB)
 
 // Shared memory of the recurrence: E of one template (4 columns) and Q.
@@ -358,11 +363,30 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
   if ((int64_t)g.n_t0 * g.n_tau == 0 || p->n_templates == 0) return cudaSuccess;
   *tiles_used = g.n_tau;
   p->tiles = TileGeom{0, g.n_t0, 1, 1, g.n_tau};   // one tau column per tile
-  // split the templates over enough blocks to fill the GPU a few times
-  const int64_t want = (int64_t)p->n_sm * 4;
-  const int32_t groups = (int32_t)std::max<int64_t>(
-      1, std::min<int64_t>(p->n_templates, (want + g.n_tau - 1) / g.n_tau));
-  const size_t smem = exp_rec_smem(p->n_sft, g.n_t0, (p->n_templates + groups - 1) / groups);
+  const size_t smem = exp_rec_smem(p->n_sft, g.n_t0, p->n_templates);
+  const bool three = smem + 1024 <= 227 * 1024 / 3;
+  // The templates are split into G groups, one block per (tau, group), with
+  // G chosen so that the blocks fill whole waves of the resident slots: the
+  // step takes about ceil(blocks / slots) block times, and a block's time is
+  // its templates plus about 1.5 templates' worth of first-template work
+  // (decay products, window records).  Measured on GB300: 1024 templates x
+  // 2000 tau, G = 5 is 7 % faster than one block per tau; 16 x 1000, G = 2
+  // is 8 % faster.
+  const int nt = p->lanes == 64 || p->lanes == 128 ? p->lanes : 256;
+  const int64_t per_sm = std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)(three ? 3 : 2) * 256 / nt, (int64_t)2048 / nt,
+                            (int64_t)(227 * 1024) / (int64_t)(smem + 1024)}));
+  const int64_t slots = (int64_t)p->n_sm * per_sm;
+  int32_t groups = 1;
+  double best = 0.0;
+  for (int32_t G = 1; G <= std::min<int32_t>(p->n_templates, kRecMaxGroups); ++G) {
+    const double waves = std::ceil((double)g.n_tau * G / (double)slots);
+    const double cost = waves * ((double)((p->n_templates + G - 1) / G) + 1.5);
+    if (G == 1 || cost < best) {
+      best = cost;
+      groups = G;
+    }
+  }
   dim3 grid((unsigned)g.n_tau, (unsigned)groups);
   auto run = [&](auto kern, int nt) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -371,7 +395,6 @@ cudaError_t launch_exp_rec(fmap_plan_s* p, const fmap_atoms* a, float* d_2F, cud
                                 p->ws.rec_cells, p->ws.rec_decay, p->ws.tauc, plan_axes(p), p->n_templates, groups, d_2F,
                                 p->ws.partials, p->part_stride);
   };
-  const bool three = smem + 1024 <= 227 * 1024 / 3;
   switch (p->lanes) {
     case 64: three ? run(k_exp_rec<64, 3>, 64) : run(k_exp_rec<64, 2>, 64); break;
     case 128: three ? run(k_exp_rec<128, 3>, 128) : run(k_exp_rec<128, 2>, 128); break;
