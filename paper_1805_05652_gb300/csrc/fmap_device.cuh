@@ -142,6 +142,17 @@ __device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.h, -b.
 __device__ __forceinline__ void ff_acc(FF& s, FF w, float x) {
   s = ff_add(s, ff_mul_f(w, x));
 }
+// s + r e with the product's low part folded into the sum's (no separate
+// normalisation of r e): TwoProd of the high parts, TwoSum with s, one
+// final renormalisation; ~2^-46 relative, as ff_add(s, ff_mul(r, e)).
+__device__ __forceinline__ FF ff_fma_sum(FF s, FF r, FF e) {
+  const float p = r.h * e.h;
+  const float pe = fmaf(r.h, e.h, -p);
+  const float t = s.h + p;
+  const float bb = t - s.h;
+  const float te = (s.h - (t - bb)) + (p - bb);
+  return fast_two_sum(t, (s.l + fmaf(r.h, e.l, fmaf(r.l, e.h, pe))) + te);
+}
 // x + r e
 __device__ __forceinline__ FF ff_axpy(FF r, FF e, float x) {
   const float p = r.h * e.h;
@@ -327,6 +338,26 @@ __device__ __forceinline__ Partial partial_block_reduce(Partial p, Partial* scra
     r = partial_warp_reduce(r);
   }
   __syncthreads();
+  return r;
+}
+
+// The same over consecutive calls of one loop with a single barrier:
+// scratch holds 2 x NWARPS entries, used alternately by parity, so a call's
+// warp partials never overwrite those warp 0 may still read from the call
+// before (the barrier of the call in between orders them).
+template <int NWARPS>
+__device__ __forceinline__ Partial partial_block_reduce_alt(Partial p, Partial* scratch,
+                                                            int parity) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Partial* sc = scratch + (parity & 1) * NWARPS;
+  p = partial_warp_reduce(p);
+  if (lane == 0) sc[warp] = p;
+  __syncthreads();
+  Partial r = partial_empty();
+  if (warp == 0) {
+    r = lane < NWARPS ? sc[lane] : partial_empty();
+    r = partial_warp_reduce(r);
+  }
   return r;
 }
 

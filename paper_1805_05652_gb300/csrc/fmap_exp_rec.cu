@@ -84,7 +84,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   __shared__ float sR[2][NW];      // each warp's product of its chunks' R
   __shared__ float sS[4][2][NW];   // each warp's composed S (per template)
   __shared__ float sK[4][2][NW];   // E at each warp's end (per template)
-  __shared__ Partial scratch[NW];
+  __shared__ Partial scratch[2 * NW];   // the block reductions, alternately
   const int ni = bid.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TauTab* tt = tauc + ni;
@@ -118,7 +118,8 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   FF R{1.0f, 0.0f};   // the chunk's product of decays (from the first template on)
   for (int32_t tq = t_lo; tq < t_hi; ++tq) {
     const bool first = tq == t_lo;
-    __syncthreads();   // the previous template's cells are done with s_e
+    // (the previous template's cells are done with s_e: its block reduction
+    // passed a barrier after every warp's cells)
     const float4* x = perm_x + (int64_t)tq * perm_entries(n, NT);   // chunk-major data rows
     // 1. chunk-local suffix sums L[i] in plain FP32 (and on the first
     // template the decay products Q[i] in float-float); the data of each run
@@ -176,7 +177,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const FF So = ff_shfl_down(S[c], 1 << k);
-        if (lane + (1 << k) < 32) S[c] = ff_add(S[c], ff_mul(Rw, So));
+        if (lane + (1 << k) < 32) S[c] = ff_fma_sum(S[c], Rw, So);
       }
       if (lane + (1 << k) < 32) Rw = ff_mul(Rw, Ro);
     }
@@ -209,7 +210,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const FF So = ff_shfl_down(Sv[c], 1 << k);
-          if (lane + (1 << k) < NW) Sv[c] = ff_add(Sv[c], ff_mul(Rv, So));
+          if (lane + (1 << k) < NW) Sv[c] = ff_fma_sum(Sv[c], Rv, So);
         }
         if (lane + (1 << k) < NW) Rv = ff_mul(Rv, Ro);
       }
@@ -228,7 +229,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
     float Ke[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const FF e = ff_add(hS[c], ff_mul(hR, FF{sK[c][0][warp], sK[c][1][warp]}));
+      const FF e = ff_fma_sum(hS[c], hR, FF{sK[c][0][warp], sK[c][1][warp]});
       Ke[c] = e.h + e.l;
     }
     for (int i = s0; i < e0; ++i) {
@@ -334,7 +335,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
         partial_add(acc, v, (int32_t)cell, ok);
       }
     }
-    acc = partial_block_reduce<NW>(acc, scratch);
+    acc = partial_block_reduce_alt<NW>(acc, scratch, tq - t_lo);
     if (tid == 0) parts[(int64_t)tq * stride + ni] = acc;
   }
 }
