@@ -96,7 +96,7 @@ static bool precision_supported(int window, fmap_precision prec) {
 struct Layout {
   size_t rel_t, t_base, dev_err, i0, jend, coef, parts, groups, flag_blocks, n_flag, flag_list, pa, px,
       esuf, xop, perm_ant, perm_x, perm_gap, rec_cells, rec_decay, tauc, ax, wtab, flag_bits, tstat, ref_hist, ref_bin,
-      ref_n, ref_cell, ref_fast, ref_val, own_map, ref_ntile, ref_tile, total;
+      ref_n, ref_cell, ref_fast, ref_val, own_map, ref_ntile, ref_tile, ref_ncand, ref_cand, total;
   int64_t n_tiles;
   int32_t tau_chunk;
 };
@@ -147,6 +147,8 @@ static Layout layout_of(const fmap_grid* g, int32_t n_sft, int32_t T, fmap_preci
     L.ref_tile = take(sizeof(int32_t) * kRefMaxTiles * Tn);
     L.ref_bin = take(sizeof(int32_t) * Tn);
     L.ref_n = take(sizeof(int32_t) * Tn);
+    L.ref_ncand = take(sizeof(int32_t) * Tn);
+    L.ref_cand = take(sizeof(int32_t) * kRefCandCap * Tn);
     L.ref_cell = take(sizeof(int32_t) * kRefMaxCells * Tn);
     L.ref_fast = take(sizeof(float) * kRefMaxCells * Tn);
     L.ref_val = take(sizeof(double) * kRefMaxCells * Tn);
@@ -304,6 +306,8 @@ fmap_status plan_init(fmap_plan_s* p, const fmap_grid* grid, int32_t n_sft, int3
     w.ref_tile = (int32_t*)(b + L.ref_tile);
     w.ref_bin = (int32_t*)(b + L.ref_bin);
     w.ref_n = (int32_t*)(b + L.ref_n);
+    w.ref_ncand = (int32_t*)(b + L.ref_ncand);
+    w.ref_cand = (int32_t*)(b + L.ref_cand);
     w.ref_cell = (int32_t*)(b + L.ref_cell);
     w.ref_fast = (float*)(b + L.ref_fast);
     w.ref_val = (double*)(b + L.ref_val);

@@ -86,6 +86,10 @@ constexpr uint32_t kPlanBatch = 1u << 16;
 // Top-cell refinement (fmap_refine.cu): candidates per template (at most),
 // histogram bins over the window of kRefWindow (2F units) below the maximum.
 constexpr int kRefMaxCells = 4096;
+// Cells per template the histogram pass may keep for the cut (those in a bin
+// <= the tile pass's bound); a template with more is collected by a second
+// scan of its tiles.
+constexpr int kRefCandCap = 8192;
 constexpr int kRefBins = 256;
 constexpr float kRefWindow = 16.0f;
 // Tiles the refinement may scan per template (those whose fast maximum can
@@ -212,6 +216,8 @@ struct Workspace {
   int32_t* ref_tile = nullptr;   // [T][kRefMaxTiles] their partial slots
   int32_t* ref_bin = nullptr;    // [T] last bin whose cells all lie in the scanned tiles
   int32_t* ref_n = nullptr;      // [T] candidates
+  int32_t* ref_ncand = nullptr;  // [T] cells kept by the histogram pass (more than kRefCandCap: overflow)
+  int32_t* ref_cand = nullptr;   // [T][kRefCandCap] those cells
   int32_t* ref_cell = nullptr;   // [T][kRefMaxCells]
   float* ref_fast = nullptr;     // [T][kRefMaxCells]
   double* ref_val = nullptr;     // [T][kRefMaxCells] (-1: invalid in FP64)

@@ -15,7 +15,9 @@
 //      the plan's cap (or after the top bin, when it alone holds more, up to
 //      kRefMaxCells), and collects those cells (in no fixed order: every
 //      later reduction over them is order-independent -- integer sums of
-//      fixed-point terms and a minimum of cell indices);
+//      fixed-point terms and a minimum of cell indices): from the cells the
+//      histogram pass kept (those in bins up to the tile pass's bound, at
+//      most kRefCandCap per template), else by a second scan of the tiles;
 //   3. recomputes each collected cell from its atoms by the plain
 //      definition: the windowed sums of Eq. (winrect) / (winexp) with w on
 //      Fa, Fb and w^2 on A, B, C (in float-float, ~2^-44 relative), then
@@ -94,13 +96,16 @@ __global__ void __launch_bounds__(kTileThreads)
 k_ref_tiles(const Partial* __restrict__ parts, int64_t stride, int64_t n_tiles, int64_t fix0,
             int64_t n_fix, const TStat* __restrict__ st, int32_t cap,
             int32_t* __restrict__ ref_ntile, int32_t* __restrict__ ref_tile,
-            int32_t* __restrict__ cut) {
+            int32_t* __restrict__ cut, int32_t* __restrict__ ref_ncand) {
   __shared__ int32_t h[kRefBins];
   __shared__ int32_t s_bt, s_n;
   const int32_t j = blockIdx.x;
   const int lane = threadIdx.x & 31;
   for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = 0;
-  if (threadIdx.x == 0) s_n = 0;
+  if (threadIdx.x == 0) {
+    s_n = 0;
+    ref_ncand[j] = 0;   // (the histogram pass after this one counts its kept cells)
+  }
   __syncthreads();
   const TStat s = st[j];
   const Partial* pp = parts + (int64_t)j * stride;
@@ -181,6 +186,8 @@ struct ScanArgs {
   const int32_t* cut;   // [T] bt of the tile pass
   int32_t* ref_n;
   int32_t* ref_cell;
+  int32_t* ref_ncand;
+  int32_t* ref_cand;
 };
 
 // Calls f(cell, owned) for every cell of share `part` (of A.parts) of listed
@@ -222,14 +229,20 @@ __device__ __forceinline__ void ref_tile_cells(const ScanArgs& A, int32_t j, int
 }
 
 // Passes 2 and 3 over the listed tiles' cells: the histogram (collect =
-// false), then the cut and the collection of the cells up to it (collect =
-// true).  Grid (x, T), one warp per tile.  The histogram and the counts were
-// cleared by the final reduction.
+// false), which also keeps the cells in bins up to the tile pass's bound
+// (cut[j]) while they fit kRefCandCap, then the cut and the collection of
+// the cells up to it (collect = true): by block (0, j) from the kept cells
+// when they fit (the same set: every cell the cut takes lies in a bin <=
+// cut[j]), else by a second scan of the tiles.  Grid (x, T), one warp per
+// tile.  The histogram and the counts were cleared by the final reduction,
+// the kept-cell count by the tile pass.
 template <bool kCollect>
 __global__ void __launch_bounds__(kRefThreads) k_ref_scan(const ScanArgs A) {
   __shared__ int32_t h[kRefBins];
   __shared__ int32_t s_last;
   const int32_t j = blockIdx.y;
+  const bool from_kept = kCollect && A.ref_ncand[j] <= kRefCandCap;
+  if (from_kept && blockIdx.x > 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (kCollect) {
     for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = A.hist[(int64_t)j * kRefBins + b];
@@ -241,6 +254,22 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_scan(const ScanArgs A) {
   __syncthreads();
   const TStat s = A.st[j];
   const int32_t last = kCollect ? s_last : kRefBins - 1;
+  const int32_t keep = kCollect ? -1 : A.cut[j];   // bins the histogram pass keeps
+  if (from_kept) {
+    if (s.N <= 0 || last < 0) return;
+    const float* mp = A.map + (int64_t)j * A.cells;
+    const int32_t n = A.ref_ncand[j];
+    const int32_t* cand = A.ref_cand + (int64_t)j * kRefCandCap;
+    for (int32_t k = threadIdx.x; k < n; k += kRefThreads) {
+      const int32_t c = cand[k];
+      const int b = ref_bin_of(mp[c], s.M);
+      if (b >= 0 && b <= last) {
+        const int32_t slot = atomicAdd(A.ref_n + j, 1);
+        if (slot < kRefMaxCells) A.ref_cell[(int64_t)j * kRefMaxCells + slot] = c;
+      }
+    }
+    return;
+  }
   const int32_t nt = min(A.ref_ntile[j], kRefMaxTiles);
   if (s.N > 0 && last >= 0) {
     const float* mp = A.map + (int64_t)j * A.cells;
@@ -260,8 +289,20 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_scan(const ScanArgs A) {
         } else {
           // one shared-memory atomic per distinct bin among the lanes here
           // (noise maps put most cells of the window in a few bins)
-          const unsigned peers = __match_any_sync(__activemask(), b);
+          const unsigned act = __activemask();
+          const unsigned peers = __match_any_sync(act, b);
           if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[b], __popc(peers));
+          // keep the cells of bins <= keep: one global atomic per warp step
+          const bool kept = b >= 0 && b <= keep;
+          const unsigned sel = __ballot_sync(act, kept);
+          if (sel) {
+            const int leader = __ffs(sel) - 1;
+            int32_t base = 0;
+            if (lane == leader) base = atomicAdd(A.ref_ncand + j, __popc(sel));
+            base = __shfl_sync(act, base, leader);
+            const int32_t at = base + __popc(sel & ((1u << lane) - 1u));
+            if (kept && at < kRefCandCap) A.ref_cand[(int64_t)j * kRefCandCap + at] = (int32_t)c;
+          }
         }
       });
     }
@@ -490,7 +531,8 @@ cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
   const int32_t sh = a->shared_antenna ? 1 : 0;
   // (the final reduction cleared the cell histogram and the candidate counts)
   k_ref_tiles<<<T, kTileThreads, 0, s>>>(w.partials, p->part_stride, n_tiles, p->n_tiles, kFixSlots,
-                                        w.tstat, cap, w.ref_ntile, w.ref_tile, w.ref_bin);
+                                        w.tstat, cap, w.ref_ntile, w.ref_tile, w.ref_bin,
+                                        w.ref_ncand);
   ScanArgs S;
   S.map = d_2F;
   S.coef = w.coef;
@@ -511,6 +553,8 @@ cudaError_t launch_refine(fmap_plan_s* p, const fmap_atoms* a, float* d_2F,
   S.cut = w.ref_bin;
   S.ref_n = w.ref_n;
   S.ref_cell = w.ref_cell;
+  S.ref_ncand = w.ref_ncand;
+  S.ref_cand = w.ref_cand;
   // a warp per share of about kScanShare cells of a listed tile (about cap
   // tiles per template), at least a few blocks over the GPU
   const int64_t tile_cells = (int64_t)S.geo.R * S.geo.C;

@@ -469,6 +469,40 @@ def test_refinement_flat_maximum(window, prec):
     check_summary(gs, ref, valid, TOL[prec], LOGB_TOL)
 
 
+@pytest.mark.parametrize("window,prec", [(RECT, "fp64"), (EXP, "rec")])
+@pytest.mark.parametrize("cap", [64, 4096])
+def test_refinement_kept_cells_overflow(window, prec, cap):
+    """The histogram pass keeps the cells of the bins the cut may take (at
+    most 8192 per template) and the cut is applied to them; a template that
+    kept more is collected by a second scan of its tiles.  With a cap of 4096
+    the bound covers the whole window below the maximum, so the noise
+    template (maximum ~20: nearly every cell within 16 of it) overflows while
+    the injected one keeps a few cells: both paths in one call, each against
+    the oracle."""
+    import torch
+
+    g = Grid(0, T_SFT, 300, 2 * T_SFT if window == RECT else T_SFT, T_SFT, 300, window)
+    inst = synth.make_instance(77, n_det=1, presence=1.0, n_merged=350, n_templates=2, grid=g,
+                               injections=[(0, window, 20 * T_SFT, 100 * T_SFT, 3000.0)])
+    ref, valid, _ = oracle_map(inst)
+    rs = oracle.summary(ref, valid)
+    within = [int((valid[j] & (ref[j] >= rs["max2F"][j] - 16.0)).sum()) for j in range(2)]
+    assert within[1] > 8192 and within[0] < 8192, within   # the case this test is for
+    dev = torch.device("cuda:0")
+    flags = fm.FMAP_PLAN_EXP_RECURRENCE if prec == "rec" else 0
+    plan = fm.Plan(g, inst.n_sft, 2, "fp64", flags)
+    plan.set_refine(cap)
+    m, s = plan.compute(torch.from_numpy(inst.t).to(dev), torch.from_numpy(inst.antenna).to(dev),
+                        torch.from_numpy(inst.fafb).to(dev))
+    torch.cuda.synchronize()
+    assert plan.status() == fm.FMAP_OK
+    plan.close()
+    gs = fm.summary_to_numpy(s)
+    assert np.all(gs["flags"] & fm.FMAP_SUMMARY_REFINED), gs["flags"]
+    check_map(m.cpu().numpy().astype(np.float64), ref, valid, TOL[prec])
+    check_summary(gs, ref, valid, TOL[prec], LOGB_TOL)
+
+
 @pytest.mark.parametrize("window,prec", [(RECT, "fp64"), (EXP, "rec"), (EXP, "bf16x3")])
 def test_graph_replay(window, prec):
     """FMAP_PLAN_GRAPH: the first call captures its launches, later calls with
