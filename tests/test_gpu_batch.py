@@ -111,7 +111,7 @@ def test_batch_equals_single_plans_and_oracle(insts, budget, autotune):
         assert np.array_equal(gs["n_valid"], ref_s["n_valid"]), k
         assert np.allclose(gs["max2F"], ref_s["max2F"], rtol=1e-5, atol=1e-5), k
         assert np.allclose(gs["logB"], ref_s["logB"], rtol=0, atol=1e-5, equal_nan=True), k
-    for k in (0, 1, 3, 5, len(insts) - 2):
+    for k in range(len(insts) - 1):   # every instance but the empty grid, against the oracle
         inst = insts[k]
         ref, valid, _ = oracle.fmap(inst.t, inst.antenna, inst.fafb, inst.grid.as_tuple(),
                                     mode="fast")
