@@ -5,7 +5,7 @@
 // windows take the FP64 prefix path, exponential windows the decayed-suffix
 // recurrence (FP64-class accuracy).  The single-plan pipeline -- input
 // checks, index tables, antenna sums and 2F coefficients, data sums and
-// cells, FP64 fix-up of ill-conditioned cells, reductions -- runs phase by
+// cells, fix-up of ill-conditioned cells, reductions -- runs phase by
 // phase, and each phase is ONE persistent launch over the work units of all
 // instances (fmap_batch.cuh): a grid of (SMs x occupancy) blocks pulls units
 // from an atomic counter, heaviest instances first, and runs the same device

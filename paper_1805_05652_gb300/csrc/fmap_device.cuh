@@ -372,7 +372,7 @@ __device__ __forceinline__ float two_f(const Coef& c, float fa_re, float fa_im, 
 }
 
 // Stores the coefficients of entry e and marks it in the bitmask of the
-// ill-conditioned entries when it goes to the FP64 fix-up (valid == 2).
+// ill-conditioned entries when it goes to the fix-up (valid == 2).
 __device__ __forceinline__ void store_coef(Coef* __restrict__ coef, uint32_t* __restrict__ bits,
                                            int64_t e, const Coef& c) {
   coef[e] = c;
@@ -382,8 +382,8 @@ __device__ __forceinline__ void store_coef(Coef* __restrict__ coef, uint32_t* __
 // Coefficients from float-float sums: D = AB - C^2 from exact FMA products
 // (relative error ~2^-44 AB, so ~1e-11 of D for AB/D <= 100); the
 // divisions in FP32.  A cell whose D is not clearly positive or whose
-// AB/D > 100 goes to the FP64 fix-up, which decides its validity from
-// FP64 sums.
+// AB/D > 100 goes to the fix-up, which decides its validity from
+// float-float sums of the window.
 __device__ __forceinline__ Coef make_coef_ff(FF A, FF B, FF C, int32_t count) {
   Coef c{0.0f, 0.0f, 0.0f, 0.0f};
   if (count < 2) return c;

@@ -16,7 +16,7 @@
 // the chunk's own partial sums, small against E where the window is long
 // (slow decay) and limited to the few undecayed terms where it is short:
 // emulated on the 5000-SFT workload (every tau class, the cells outside the
-// FP64 fix-up), the worst relative 2F error is 1.7e-6 against 1.2e-6 for
+// fix-up), the worst relative 2F error is 1.7e-6 against 1.2e-6 for
 // compensated chunk sums.
 //
 // One block per (tau_n, group of templates); each thread owns a chunk of
@@ -101,9 +101,9 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
   const int64_t tb = n > 0 ? *t_base : 0;
   // 0 after the last atom
   int32_t gq[kRecChunk];
-  auto decay = [&](int q) -> FF {
-    if (gq[q] > 0) return gap_decay(gq[q], g.t_sft, inv_tsft, tt->pw[0], inv_tau);
-    return gq[q] < 0 ? FF{0.0f, 0.0f} : FF{1.0f, 0.0f};
+  auto decay = [&](int32_t gap) -> FF {
+    if (gap > 0) return gap_decay(gap, g.t_sft, inv_tsft, tt->pw[0], inv_tau);
+    return gap < 0 ? FF{0.0f, 0.0f} : FF{1.0f, 0.0f};
   };
   const int b_last = s0 + ((e0 - s0 - 1) / kRecChunk) * kRecChunk;   // last run's start
   // window records of tau_n, and coefficients (shared antenna); the array is
@@ -151,7 +151,7 @@ __device__ __forceinline__ void exp_rec_body(const int32_t* __restrict__ rel_t, 
         if (cached) {
           rh = __int_as_float(gq[q]);
         } else {
-          const FF r = decay(q);
+          const FF r = decay(gq[q]);
           rh = r.h;
           if (first) {
             ch_mul(r, Qh, Qc);

@@ -57,8 +57,8 @@ struct __align__(16) Partial {
 // square in Fa).  valid: 0 = invalid (fewer than 2 atoms; k1 = k2 = 0),
 // 1 = evaluated by the fast kernels, 2 = ill-conditioned or undecided
 // (A B / D > kCondThreshold, or D not clearly positive in float-float): left
-// to the FP64 fix-up of fmap_fixup.cu, which decides D > 0 and then records
-// the outcome in valid (3 = valid by FP64 sums, 0 = invalid).
+// to the fix-up of fmap_fixup.cu, which decides D > 0 from float-float sums
+// and then records the outcome in valid (3 = valid, 0 = invalid).
 constexpr double kCondThreshold = 100.0;
 // Reduction slots per template written by the fix-up kernel.
 constexpr int kFixSlots = 512;
@@ -371,7 +371,7 @@ inline int32_t rel_t_entries(int32_t n_sft) { return ((n_sft + 63) / 64) * 64 + 
 
 // Tile counts of each kernel family (partials per template).
 int64_t rect_tiles(const fmap_grid& g);
-// y extent of the FP64 fix-up grid (kFixSlots x this) for a template count.
+// y extent of the fix-up grid (kFixSlots x this) for a template count.
 int64_t fixup_blocks_y(int32_t n_templates);
 // The rectangular cells phase: partial slots per template, blocks and
 // dynamic shared memory of its kernel.

@@ -6,7 +6,7 @@
 //   to the window sum itself and not to the (possibly much larger) prefix.
 //   The antenna sums A, B, C are differenced in float-float (~2^-44 of the
 //   prefix) and D = AB - C^2 formed from exact FMA products; cells with
-//   AB > 100 D go to the FP64 fix-up.  (GB300 runs FP64 at 1/64 of the FP32
+//   AB > 100 D go to the fix-up.  (GB300 runs FP64 at 1/64 of the FP32
 //   rate, so the per-cell work stays off the FP64 pipe.)
 // FMAP_FP32: the paper's rectangular kernel (Sec. 3): one thread per t0 row
 //   adds atom after atom to FP32 running sums as tau grows.
@@ -249,7 +249,7 @@ __global__ void k_rect_coef(const int32_t* __restrict__ i0tab, const int32_t* __
 // it, the lowest cell index attaining it and the valid count.  Invalid and
 // ill-conditioned cells carry k1 = -inf (|Fa|^2 is kept >= 1e-30 so the
 // product is -inf, never NaN): the maximum ignores them, their exp-term is
-// 0, they never equal the maximum, and the map gets 0 (the FP64 fix-up later
+// 0, they never equal the maximum, and the map gets 0 (the fix-up later
 // rewrites the ill-conditioned ones).  The quadratic form runs on packed
 // f32x2 arithmetic (re, im pairs).
 constexpr int kLaneCells = kTileRows * (kTileCols / 32);
