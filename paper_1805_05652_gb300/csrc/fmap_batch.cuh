@@ -55,7 +55,7 @@ struct BUnits {
 // per-unit claim and instance lookup stay a small share): rectangular
 // coefficients in 256-entry blocks, index-table rows, fix-up slots.
 constexpr int kCoefBlocksPerUnit = 8;
-constexpr int kIdxRowsPerUnit = 4;
+constexpr int kIdxRowsPerUnit = 8;
 constexpr int kFixSlotsPerUnit = 4;
 constexpr int kPermPerUnit = 4096;   // chunk-major copy entries per unit
 constexpr int kBitsPerUnit = 4096;   // marked-entry bitmask words cleared per unit

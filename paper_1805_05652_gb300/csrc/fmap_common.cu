@@ -61,10 +61,12 @@ __global__ void k_prep(const int64_t* __restrict__ t, int32_t n, int32_t n_alloc
 // Window index tables: i0[m] = first atom with t >= t0_m; jend[m][n] = one
 // past the last atom whose SFT ends by t0_m + L_n (L = window_len(tau_n)),
 // clamped to >= i0[m], so the window holds atoms [i0, jend).  One block per
-// t0 row: the row's atom range [i0, j(n_tau - 1)) of relative times is
-// staged in shared memory (coalesced) and every tau searches it there;
-// longer ranges search the relative times in global memory.
+// group of kIdxGroup t0 rows: each warp finds one row's atom range
+// [i0, j(n_tau - 1)) by a warp-wide search, the union of the group's ranges
+// of relative times is staged in shared memory once (coalesced), and every
+// (row, tau) searches it there; longer unions search global memory.
 constexpr int kIdxThreads = 256;
+constexpr int kIdxGroup = kIdxThreads / 32;   // t0 rows per block pass (one warp each)
 constexpr int kIdxCap = 8192;   // staged relative times (32 KB)
 
 // First index in [lo, hi) of the ascending int32 times with t > x (int64).
@@ -102,43 +104,51 @@ __device__ __forceinline__ void index_body(const int32_t* __restrict__ rel_t,
                                            const int64_t* __restrict__ t_base, int32_t n_sft,
                                            fmap_grid g, const int64_t* __restrict__ ax,
                                            int32_t* __restrict__ i0tab,
-                                           int32_t* __restrict__ jend, int32_t m) {
+                                           int32_t* __restrict__ jend, int32_t m0, int32_t R) {
   __shared__ int32_t s_t[kIdxCap];
-  __shared__ int32_t s_lo, s_hi;
-  const int tid = threadIdx.x;
+  __shared__ int32_t s_lo[kIdxGroup], s_hi[kIdxGroup];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t tb = n_sft > 0 ? *t_base : 0;
-  const int64_t t0rel = grid_t0(g, ax, m) - tb;
-  if (tid < 32) {   // warp 0: the first atom with t >= t0, and the last any window takes
-    const int32_t lo = warp_upper_bound_i32(rel_t, 0, n_sft, t0rel - 1, tid);
-    const int64_t lim = t0rel + window_len(g, grid_tau(g, ax, g.n_tau - 1)) - g.t_sft;
-    const int32_t hi = max(lo, warp_upper_bound_i32(rel_t, lo, n_sft, lim, tid));
-    if (tid == 0) {
-      s_lo = lo;
-      s_hi = hi;
+  const int64_t lmax = window_len(g, grid_tau(g, ax, g.n_tau - 1)) - g.t_sft;
+  if (warp < R) {   // warp r: row m0 + r's first atom with t >= t0 and the last any window takes
+    const int32_t m = m0 + warp;
+    const int64_t t0rel = grid_t0(g, ax, m) - tb;
+    const int32_t lo = warp_upper_bound_i32(rel_t, 0, n_sft, t0rel - 1, lane);
+    const int32_t hi = max(lo, warp_upper_bound_i32(rel_t, lo, n_sft, t0rel + lmax, lane));
+    if (lane == 0) {
+      s_lo[warp] = lo;
+      s_hi[warp] = hi;
       i0tab[m] = lo;
     }
   }
   __syncthreads();
-  const int32_t i0 = s_lo, span = s_hi - s_lo;
+  // Both ends grow with t0, so the group's rows search within [lo of its
+  // first row, hi of its last), staged once when it fits.
+  const int32_t base = s_lo[0], span = s_hi[R - 1] - base;
   const bool staged = span <= kIdxCap;
   if (staged)
-    for (int k = tid; k < span; k += kIdxThreads) s_t[k] = rel_t[i0 + k];
+    for (int k = tid; k < span; k += kIdxThreads) s_t[k] = rel_t[base + k];
   __syncthreads();
-  int32_t* row = jend + (int64_t)m * g.n_tau;
-  for (int32_t nn = tid; nn < g.n_tau; nn += kIdxThreads) {
-    const int64_t lim = t0rel + window_len(g, grid_tau(g, ax, nn)) - g.t_sft;
-    row[nn] = staged ? i0 + upper_bound_i32(s_t, 0, span, lim)
-                     : upper_bound_i32(rel_t, i0, i0 + span, lim);
+  for (int32_t r = 0; r < R; ++r) {   // no barrier between rows: their searches overlap
+    const int32_t m = m0 + r, lo = s_lo[r], hi = s_hi[r];
+    const int64_t t0rel = grid_t0(g, ax, m) - tb;
+    int32_t* row = jend + (int64_t)m * g.n_tau;
+    for (int32_t nn = tid; nn < g.n_tau; nn += kIdxThreads) {
+      const int64_t lim = t0rel + window_len(g, grid_tau(g, ax, nn)) - g.t_sft;
+      row[nn] = staged ? base + upper_bound_i32(s_t, lo - base, hi - base, lim)
+                       : upper_bound_i32(rel_t, lo, hi, lim);
+    }
   }
-  __syncthreads();   // s_t, s_lo and s_hi are reused by the block's next row
+  __syncthreads();   // s_t, s_lo and s_hi are reused by the block's next group
 }
 
 __global__ void __launch_bounds__(kIdxThreads)
 k_index(const int32_t* __restrict__ rel_t, const int64_t* __restrict__ t_base, int32_t n_sft,
         fmap_grid g, const int64_t* __restrict__ ax, int32_t* __restrict__ i0tab,
-        int32_t* __restrict__ jend) {
-  for (int32_t m = blockIdx.x; m < g.n_t0; m += gridDim.x)
-    index_body(rel_t, t_base, n_sft, g, ax, i0tab, jend, m);
+        int32_t* __restrict__ jend, int32_t grp) {
+  const int32_t n_grp = (g.n_t0 + grp - 1) / grp;
+  for (int32_t q = blockIdx.x; q < n_grp; q += gridDim.x)
+    index_body(rel_t, t_base, n_sft, g, ax, i0tab, jend, q * grp, min(grp, g.n_t0 - q * grp));
 }
 
 cudaError_t launch_prep(fmap_plan_s* p, const fmap_atoms* a, cudaStream_t s) {
@@ -162,9 +172,12 @@ cudaError_t launch_index(fmap_plan_s* p, const int64_t* d_t, cudaStream_t s) {
   (void)d_t;
   const int64_t cells = (int64_t)p->grid.n_t0 * p->grid.n_tau;
   if (cells == 0) return cudaSuccess;
-  const int blocks = (int)std::min<int64_t>(p->grid.n_t0, (int64_t)p->n_sm * 8);
+  // rows per group: as many as keep about four blocks per SM busy (1..8)
+  const int32_t grp = (int32_t)std::max<int64_t>(
+      1, std::min<int64_t>(kIdxGroup, p->grid.n_t0 / ((int64_t)p->n_sm * 4)));
+  const int blocks = (int)std::min<int64_t>((p->grid.n_t0 + grp - 1) / grp, (int64_t)p->n_sm * 8);
   k_index<<<blocks, kIdxThreads, 0, s>>>(p->ws.rel_t, p->ws.t_base, p->n_sft, p->grid, plan_axes(p),
-                                         p->ws.i0, p->ws.jend);
+                                         p->ws.i0, p->ws.jend, grp);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -443,11 +456,12 @@ __global__ void __launch_bounds__(256) kb_prep(const BItem* __restrict__ items, 
     }
   });
 }
+static_assert(kIdxRowsPerUnit == kIdxGroup, "a batch index unit is one row group");
 __global__ void __launch_bounds__(kIdxThreads) kb_index(const BItem* __restrict__ items, BUnits u) {
   batch_loop(items, u, [&](const BItem& it, int64_t k) {
-    const int32_t m_end = min(it.g.n_t0, (int32_t)(k + 1) * kIdxRowsPerUnit);
-    for (int32_t m = (int32_t)k * kIdxRowsPerUnit; m < m_end; ++m)
-      index_body(it.rel_t, it.t_base, it.n_sft, it.g, it.ax, it.i0, it.jend, m);
+    const int32_t m0 = (int32_t)k * kIdxRowsPerUnit;
+    index_body(it.rel_t, it.t_base, it.n_sft, it.g, it.ax, it.i0, it.jend, m0,
+               min(kIdxRowsPerUnit, it.g.n_t0 - m0));
   });
 }
 __global__ void __launch_bounds__(kRedThreads) kb_red_groups(const BItem* __restrict__ items,
