@@ -124,8 +124,9 @@ __host__ __device__ inline int64_t window_len(const fmap_grid& g, int64_t tau) {
 }
 // Largest window table (samples) of FMAP_TABLE grids.
 constexpr int kTabMax = 1024;
-// Entries per count of the marked-entry compaction (1024 threads x 8).
-constexpr int kFlagUnit = 8192;
+// Entries per count of the marked-entry compaction: one bitmask word per
+// thread of a 1024-thread block.
+constexpr int kFlagUnit = 32768;
 // Words of the marked-entry bitmask (whole compaction units).
 __host__ __device__ inline int64_t flag_words(int64_t entries) {
   return (entries + kFlagUnit - 1) / kFlagUnit * (kFlagUnit / 32);
