@@ -231,9 +231,9 @@ __device__ __forceinline__ void ref_tile_cells(const ScanArgs& A, int32_t j, int
 // Passes 2 and 3 over the listed tiles' cells: the histogram (collect =
 // false), which also keeps the cells in bins up to the tile pass's bound
 // (cut[j]) while they fit kRefCandCap, then the cut and the collection of
-// the cells up to it (collect = true): by block (0, j) from the kept cells
-// when they fit (the same set: every cell the cut takes lies in a bin <=
-// cut[j]), else by a second scan of the tiles.  Grid (x, T), one warp per
+// the cells up to it (collect = true): by the blocks (x, j) from the kept
+// cells when they fit (the same set: every cell the cut takes lies in a bin
+// <= cut[j]), else by a second scan of the tiles.  Grid (x, T), one warp per
 // tile.  The histogram and the counts were cleared by the final reduction,
 // the kept-cell count by the tile pass.
 template <bool kCollect>
@@ -241,8 +241,9 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_scan(const ScanArgs A) {
   __shared__ int32_t h[kRefBins];
   __shared__ int32_t s_last;
   const int32_t j = blockIdx.y;
-  const bool from_kept = kCollect && A.ref_ncand[j] <= kRefCandCap;
-  if (from_kept && blockIdx.x > 0) return;
+  const int32_t n_kept = kCollect ? A.ref_ncand[j] : 0;
+  const bool from_kept = kCollect && n_kept <= kRefCandCap;
+  if (from_kept && (int64_t)blockIdx.x * kRefThreads >= n_kept) return;   // (past the list)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (kCollect) {
     for (int b = threadIdx.x; b < kRefBins; b += blockDim.x) h[b] = A.hist[(int64_t)j * kRefBins + b];
@@ -255,12 +256,12 @@ __global__ void __launch_bounds__(kRefThreads) k_ref_scan(const ScanArgs A) {
   const TStat s = A.st[j];
   const int32_t last = kCollect ? s_last : kRefBins - 1;
   const int32_t keep = kCollect ? -1 : A.cut[j];   // bins the histogram pass keeps
-  if (from_kept) {
+  if (from_kept) {   // the template's blocks share its kept list
     if (s.N <= 0 || last < 0) return;
     const float* mp = A.map + (int64_t)j * A.cells;
-    const int32_t n = A.ref_ncand[j];
     const int32_t* cand = A.ref_cand + (int64_t)j * kRefCandCap;
-    for (int32_t k = threadIdx.x; k < n; k += kRefThreads) {
+    for (int32_t k = blockIdx.x * kRefThreads + threadIdx.x; k < n_kept;
+         k += gridDim.x * kRefThreads) {
       const int32_t c = cand[k];
       const int b = ref_bin_of(mp[c], s.M);
       if (b >= 0 && b <= last) {
