@@ -63,9 +63,11 @@ typedef enum {
 typedef enum { FMAP_RECT = 0, FMAP_EXP = 1, FMAP_TABLE = 2 } fmap_window;
 
 /*
- * Arithmetic of the windowed sums.  In every mode the antenna sums A, B, C,
- * the determinant D = AB - C^2, the 2F coefficients and the log-Bayes
- * reduction are FP64 (D and the coefficients once per cell):
+ * Arithmetic of the windowed sums.  In every mode the antenna sums A, B, C
+ * and the determinant D = AB - C^2 are float-float (pairs of FP32 numbers
+ * with error-free FMA products, ~2^-44 relative: GB300 runs FP64 at 1/64 of
+ * the FP32 rate), the 2F coefficients FP32 from them (once per cell), and
+ * the log-Bayes reduction FP64:
  *   FMAP_FP64   rect: FP64 prefix sums over SFTs (data rows kept as float
  *               pairs), O(1) compensated differences per cell;
  *               exp:  FP64 contraction on the CUDA cores.
@@ -78,8 +80,9 @@ typedef enum { FMAP_RECT = 0, FMAP_EXP = 1, FMAP_TABLE = 2 } fmap_window;
  *               with hi*hi + hi*lo + lo*hi, FP32 accumulate.
  * Cells whose antenna matrix is ill-conditioned (A B / D > 100: windows of a
  * few SFTs of one detector, where any FP32 sum loses ~1e-7 sqrt(AB/D) of
- * relative accuracy in 2F) are recomputed in FP64 from their atoms in every
- * mode.
+ * relative accuracy in 2F) are recomputed from their atoms in every mode:
+ * windowed sums, D and the numerator of 2F in float-float (~2^-46 A B / D
+ * relative), one FP32 quotient.
  */
 typedef enum { FMAP_FP64 = 0, FMAP_FP32 = 1, FMAP_TF32 = 2, FMAP_BF16X3 = 3 } fmap_precision;
 
@@ -129,8 +132,9 @@ typedef struct {
 } fmap_summary;
 
 enum {
-  /* the cells nearest the maximum were recomputed from their atoms in FP64
-   * and max2F, the argmax and logB use those values */
+  /* the cells nearest the maximum were recomputed from their atoms
+   * (float-float window sums, D and 2F in FP64) and max2F, the argmax and
+   * logB use those values */
   FMAP_SUMMARY_REFINED = 1u,
   /* every cell whose fast 2F lay within the fast path's error bound of the
    * maximum was among them: the argmax was decided on FP64 values */
@@ -329,12 +333,12 @@ fmap_status fmap_compute_host(fmap_plan_t* plan, const fmap_atoms* host_atoms, f
 /* Per-phase device timing of a plan's compute calls, taken with CUDA events
  * recorded on each call's stream.  Phases (FMAP_N_PHASES):
  *   0 input checks and window index tables,
- *   1 antenna sums / prefix sums (rect: FP64 scans; exp: FP64 suffix sums and
- *     the per-cell 2F coefficients),
+ *   1 antenna sums / prefix sums (rect: FP64 scans; exp: float-float suffix
+ *     sums and the per-cell 2F coefficients),
  *   2 the windowed contraction with the fused 2F epilogue (the dominant
  *     kernel),
- *   3 the FP64 recomputation of ill-conditioned cells and the final
- *     per-template reduction.
+ *   3 the recomputation of ill-conditioned cells, the final per-template
+ *     reduction and the refinement of the summaries.
  * fmap_plan_enable_timing(plan, 1) starts recording (and clears the totals);
  * fmap_plan_read_timing waits for the recorded calls and returns the summed
  * milliseconds per phase, the number of timed calls and the number of
